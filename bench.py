@@ -1,0 +1,318 @@
+"""Benchmark of the RBSOG NPT step on GB300.
+
+Default workload (N=1): the water-like box of 10,000 flexible 3-site
+molecules (30,000 sites, 66.88 A, r_c = 10 A, P = 100), FP32 math with FP64
+accumulation, isotropic Langevin NPT.  One "step" is one full NPT step of
+Algorithm 1 (binning, pair, sampling, S(k), estimators, force scatter,
+molecules, integrator) replayed as a CUDA graph.  Metric: atom-steps/s.
+
+Under torchrun with N ranks every rank runs its own independent replica
+(different Philox key); value = all atoms x steps / max over ranks of the time.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the same workload, a bounded number of steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RBSOG atom-steps/s on 1 GB300 (plain vs batched); p50/p99 step latency"
+UNIT = "atom-steps/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+MUFU_PER_SM_CLK = 16          # special-function results per SM per clock
+FP32_LANES = 128              # FP32 FMA lanes per SM
+# algorithmic work per half-pair inside r_c (M~ = 10): 10 exp + 1 rsqrt on the
+# special-function unit, ~67 FP32 operations
+PAIR_MUFU_PER_UNIT = 11
+PAIR_FP32_PER_UNIT = 67
+
+
+def workload(name: str, rank: int = 0):
+    import workloads as W
+    if name == "water":
+        s = W.water()
+        desc = ("water-like box: 10,000 flexible 3-site molecules (30,000 sites, SPC/E charges), "
+                "L=66.88 A, rc=10 A, P=100, isotropic Langevin NPT")
+        return [s], desc
+    if name == "electrolyte":
+        s = W.electrolyte()
+        return [s], "1000-ion electrolyte, L=30 A, rc=10 A, P=100, isotropic Langevin NPT"
+    if name == "ionic_liquid":
+        s = W.ionic_liquid()
+        return [s], "ionic-liquid-like mix, 64,000 sites, L=110.85 A, rc=10 A, P=100"
+    if name == "membrane":
+        s = W.membrane()
+        return [s], "membrane-like slab 64x64x96 A, 120,000 sites, semi-isotropic, rc=10 A, P=100"
+    if name == "big_water":
+        s = W.big_water()
+        return [s], "water-like box, 10,000,002 sites (3,333,334 molecules), L=463.7 A, rc=10 A, P=100"
+    raise ValueError(name)
+
+
+def clock_sampler(path):
+    """Start nvidia-smi sampling every 200 ms; returns (proc, path)."""
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clock_summary(path, dev_index):
+    rows = []
+    try:
+        for line in open(path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9 or v[0] != str(dev_index):
+                continue
+            rows.append(v)
+    except Exception:
+        return None
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    reasons = set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        for k, nm in enumerate(names):
+            if r[5 + k].lower().startswith("active"):
+                reasons.add(nm)
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(systems, budget_s=15.0):
+    """The FP64 oracle (all-pairs short range, random batch long range,
+    Langevin NPT) on the same workload, as many steps as fit the budget."""
+    from oracle import oracle as O
+    s = systems[0]
+    p = O.Params.row2(P=100)
+    t0 = time.perf_counter()
+    out = O.force_eval(s, p, 0)
+    t_eval = time.perf_counter() - t0
+    st = dict(r=s.pos.copy(), p=np.zeros_like(s.pos), L=s.box.copy(), ph=np.zeros(3),
+              F=out["F"], W=out["W"].reshape(-1).copy())
+    ig = O.Integ(dt=0.5, T=300.0, Pext_atm=1.0, Mbox=(0.0, 0.0, 0.0))
+    steps = max(1, min(20, int(budget_s / max(t_eval, 1e-3))))
+    t0 = time.perf_counter()
+    O.npt_run(s, p, ig, st, 0, steps)
+    dt = time.perf_counter() - t0
+    return {"value": s.n * steps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{steps} NPT steps of the {s.n}-site workload (all-pairs short range, FP64), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    systems, desc = workload(args.workload)
+    s = systems[0]
+    from oracle import oracle as O
+    budget = max(5.0, 60.0 / max(args.steps + args.warmup, 1))
+    times = []
+    p = O.Params.row2(P=100)
+    out = O.force_eval(s, p, 0)
+    st = dict(r=s.pos.copy(), p=np.zeros_like(s.pos), L=s.box.copy(), ph=np.zeros(3),
+              F=out["F"], W=out["W"].reshape(-1).copy())
+    ig = O.Integ(dt=0.5, T=300.0, Pext_atm=1.0, Mbox=(0.0, 0.0, 0.0))
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.npt_run(s, p, ig, st, k, 1)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+        if sum(times) > budget * 3:
+            break
+    total = sum(times)
+    value = s.n * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "engine": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{len(times)} NPT steps of the {s.n}-site workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--workload", default="water")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2602_23582_gb300 import rbsog as R
+    systems, desc = workload(args.workload, rank)
+    for k, s in enumerate(systems):
+        s.rng_id = 1000 * rank + k
+    prec = R.RBSOG_FP32 if args.precision == "fp32" else R.RBSOG_FP64
+    stream = torch.cuda.Stream(device=dev)
+    p = R.rbsog_default_params(10.0, precision=prec)
+    ctx = R.Context(systems, p, stream=stream.cuda_stream)
+    n_atoms = ctx.n_atoms
+
+    # ---- per-kernel breakdown of one evaluation (events between kernels)
+    R.rbsog_set_timing(ctx.ctx, True)
+    kt = {}
+    for k in range(5):
+        ctx.step(10_000 + k)
+        for name, ms in R.rbsog_get_timing(ctx.ctx):
+            kt.setdefault(name, []).append(ms)
+    R.rbsog_set_timing(ctx.ctx, False)
+    kernel_ms = {k: float(np.median(v[1:])) for k, v in kt.items()}
+
+    # ---- NPT steps: warm-up, then K steps timed one by one with an L2 flush between
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    R.rbsog_run(ctx.ctx, args.warmup)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    proc, fh = clock_sampler(clk_path) if rank == 0 else (None, None)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            R.rbsog_run_async(ctx.ctx, 1)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    R.rbsog_sync(ctx.ctx)
+    if world > 1:
+        dist.barrier()
+    if proc is not None:
+        time.sleep(0.3)
+        proc.terminate()
+        fh.close()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+
+    # ---- e2e through the C ABI with host buffers (positions in, forces out)
+    e2e = None
+    if not args.no_e2e:
+        pos = torch.empty((n_atoms, 3), dtype=torch.float64).pin_memory()
+        frc = torch.empty((n_atoms, 3), dtype=torch.float64).pin_memory()
+        R.rbsog_get_positions(ctx.ctx, pos.numpy())
+        res = (R.rbsog_result * ctx.S)()
+        ne = max(10, min(200, args.steps // 2))
+        for k in range(3):
+            R.rbsog_set_positions(ctx.ctx, pos.numpy())
+            R.rbsog_step(ctx.ctx, 20_000 + k, frc.numpy(), res)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(ne):
+            R.rbsog_set_positions(ctx.ctx, pos.numpy())
+            R.rbsog_step(ctx.ctx, 30_000 + k, frc.numpy(), res)
+        t1 = time.perf_counter()
+        e2e = {"value": n_atoms * ne / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": 24 * n_atoms,
+               "d2h_bytes_per_step": 24 * n_atoms + 632 * ctx.S,
+               "call": "rbsog_set_positions(host) + rbsog_step(host forces, results)"}
+        if world > 1:
+            t = torch.tensor([e2e["value"]], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            e2e["value"] = float(t.item())
+
+    value = n_atoms * world * args.steps / total_s
+    # ---- roofline of the dominant kernel (pair): algorithmic half-pairs per launch
+    s0 = systems[0]
+    rho_n = s0.n / float(np.prod(s0.box))
+    half_pairs = 0.5 * s0.n * (4.0 / 3.0 * math.pi * p.rc ** 3 * rho_n)
+    pair_ms = kernel_ms.get("pair")
+    peaks = load_peaks()
+    sm_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    clocks = clock_summary(clk_path, local) if rank == 0 else None
+    roof = None
+    if pair_ms:
+        mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clk / 1e12
+        achieved = half_pairs * PAIR_MUFU_PER_UNIT / (pair_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_pair_f32" if prec == R.RBSOG_FP32 else "k_pair_f64",
+                "achieved": achieved, "peak": mufu_peak, "unit": "Top/s (MUFU)",
+                "frac": achieved / mufu_peak, "traffic": None,
+                "units_per_launch": half_pairs, "per_unit": f"{PAIR_MUFU_PER_UNIT} MUFU + "
+                f"{PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c",
+                "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {sm_clk / 1e6:.0f} MHz (max clock)",
+                "launch_ms": pair_ms}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(systems)
+        except Exception as ex:   # reported, not fatal
+            cpu = {"error": str(ex)}
+    kernels_per_step = 16   # box_half .. step_advance, one graph replay
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == R.RBSOG_FP32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "path": "plain (one system per context), NPT step as a CUDA graph",
+                       "precision": "FP32 math, FP64 accumulation" if prec == R.RBSOG_FP32 else "FP64",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+                       "ns_per_day": (p.dt * 1e-6) / (float(step_ms.mean()) / 1e3 / 86400.0),
+                       "kernel_ms": kernel_ms},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": kernels_per_step * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

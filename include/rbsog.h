@@ -1,0 +1,248 @@
+/*
+ * rbsog.h -- C ABI of the GB300 (sm_103a) implementation of the random batch
+ * sum-of-Gaussians (RBSOG) electrostatics for NPT molecular dynamics,
+ * arXiv 2602.23582 (Jiang, Liang, Zhou).
+ *
+ * The library computes, per MD step and per system, Algorithm 1 of the paper:
+ *   - the SOG short-range pair forces, energy and virial (sec. 2.2, 3.1;
+ *     eqs. force_SOG, U_short, P_short) over cell lists rebuilt every step;
+ *   - P Fourier modes drawn from the radial proposal by Metropolis-Hastings
+ *     (App. D) and recalibrated for the non-radial target (sec. 3.2);
+ *   - the structure factors rho(k) (eq. rho_k) of the distinct modes;
+ *   - the random-batch force (App. B, eq. f_approx), energy and pressure
+ *     estimators (eqs. P_approx_r, P_approx_nr);
+ *   - a Langevin NPT integrator (eq. Langevin_NPT).
+ *
+ * Units are LAMMPS "real": Angstrom, fs, kcal/mol, e, g/mol, K, atm.  The
+ * paper writes Coulomb in Gaussian units; every Coulomb energy, force and
+ * virial is multiplied by params.ke.
+ *
+ * Conventions:
+ *   - Every function returns an rbsog_status; rbsog_last_error() gives text.
+ *     No exception crosses the ABI.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Device
+ *     pointers (on_device != 0) must be CUDA device memory of the current
+ *     device, valid for the duration of the call; the library does not keep
+ *     them.  The context owns every other device allocation.
+ *   - Arrays of atoms are row-major N x 3 FP64 unless stated; atoms of all
+ *     systems of a context are concatenated in system order.
+ *   - The cell h is orthorhombic: box[3] are its edge lengths.  A box edge
+ *     shorter than 3 r_c is rejected (RBSOG_EBOX).
+ *   - Results depend only on (inputs, seed, rng_id, step): Philox4x64-10
+ *     counters (step, purpose, index) under the key (seed, rng_id).
+ */
+#ifndef RBSOG_H
+#define RBSOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RBSOG_OK = 0,
+    RBSOG_EINVAL = -1,        /* bad argument */
+    RBSOG_ENOMEM = -2,        /* device or host allocation failed */
+    RBSOG_EBOX = -3,          /* box edge < 3 r_c, or non-positive */
+    RBSOG_ENONFINITE = -4,    /* non-finite force, energy or pressure */
+    RBSOG_EUNSUPPORTED = -5,  /* option not supported */
+    RBSOG_ETIMEOUT = -6,      /* a bounded device wait gave up */
+    RBSOG_ECUDA = -7,         /* CUDA runtime error */
+    RBSOG_EOVERFLOW = -8      /* a cell holds more atoms than the kernels take */
+} rbsog_status;
+
+/* Sampler kinds (sec. 3.2, App. D). */
+enum {
+    RBSOG_SAMPLER_PAPER = 0,      /* MH radial chain (App. D) + recalibration chain */
+    RBSOG_SAMPLER_IID = 1,        /* independent exact draws from P^r and P^nr */
+    RBSOG_SAMPLER_IID_RECAL = 2   /* exact radial draws + recalibration chain */
+};
+
+/* Precision of the hot kernels. */
+enum {
+    RBSOG_FP64 = 0,               /* every step in FP64 */
+    RBSOG_FP32 = 1                /* FP32 pair/sincos math, FP64 accumulation */
+};
+
+/* Pressure coupling of the barostat (eq. Langevin_NPT for a diagonal h). */
+enum {
+    RBSOG_COUPLE_ISO = 0,         /* one box momentum for x, y, z */
+    RBSOG_COUPLE_SEMI_ISO = 1,    /* x = y coupled, z free */
+    RBSOG_COUPLE_FIXED = 2        /* box held fixed (NVT) */
+};
+
+typedef struct {
+    /* SOG split (sec. 2.2 / 3.1; Table 2 gives (b, sigma, omega) at r_c = 9 A,
+     * sigma scales linearly with r_c) */
+    double rc;              /* cutoff, A */
+    double b, sigma, omega;
+    int M;                  /* Gaussians of the force/pressure split (M = M~) */
+    int M_energy;           /* Gaussians of the energy split, >= M */
+    /* random batch (sec. 3.2) */
+    int P;                  /* batch size, 1..4096 */
+    int sampler;            /* RBSOG_SAMPLER_* */
+    uint64_t seed;
+    int precision;          /* RBSOG_FP64 or RBSOG_FP32 */
+    double ke;              /* Coulomb constant, 332.06371 kcal A/(mol e^2) in real units */
+    /* Langevin NPT (eq. Langevin_NPT) */
+    double dt;              /* fs */
+    double T;               /* K */
+    double P_ext;           /* atm */
+    double gamma;           /* 1/fs, particle friction */
+    double gamma_box;       /* 1/fs, box friction */
+    double tau_box;         /* fs, barostat period used to set the box mass */
+    double compressibility; /* 1/atm, used to set the box mass */
+    int coupling;           /* RBSOG_COUPLE_* */
+    int cell_sub;           /* cells per cutoff length along an axis: 1 or 2 */
+} rbsog_params;
+
+typedef struct {
+    int n_atoms;
+    const double *q;        /* N charges, e */
+    const double *mass;     /* N masses, g/mol */
+    const int *type;        /* N LJ types in [0, ntypes) */
+    const int *mol;         /* N molecule ids: atoms of a molecule contiguous; pairs
+                               with equal ids are excluded from the pair sums */
+    int ntypes;
+    const double *lj_eps;   /* ntypes^2, kcal/mol (12-6, cut unshifted at rc) */
+    const double *lj_sig;   /* ntypes^2, A */
+    int n_bonds;
+    const int *bonds;       /* n_bonds x 2 atom indices (within the system) */
+    const double *bond_k;   /* U = k (r - r0)^2 */
+    const double *bond_r0;
+    int n_angles;
+    const int *angles;      /* n_angles x 3, centre atom in the middle */
+    const double *angle_k;  /* U = k (theta - theta0)^2 */
+    const double *angle_t0;
+    int n_excl;
+    const int *excl;        /* n_excl x 2 intramolecular pairs whose Fourier-part
+                               interaction is removed (all pairs of a molecule) */
+    const double *r0;       /* N x 3 initial positions, A */
+    const double *v0;       /* N x 3 initial velocities, A/fs, or NULL (zero) */
+    double box[3];          /* edge lengths, A */
+    uint64_t rng_id;        /* second word of this system's Philox key (seed, rng_id):
+                               results do not depend on the system's place in a batch */
+} rbsog_system_desc;
+
+/* Energies, kcal/mol: indices into rbsog_result.energy */
+enum {
+    RBSOG_E_COUL_SHORT = 0,  /* U^N (eq. U_short) */
+    RBSOG_E_COUL_LONG = 1,   /* U^F* estimated with the radial samples */
+    RBSOG_E_COUL_SELF = 2,   /* U_self (App. A) */
+    RBSOG_E_COUL_EXCL = 3,   /* removed intramolecular Fourier-part energy */
+    RBSOG_E_LJ = 4,
+    RBSOG_E_BOND = 5,
+    RBSOG_E_ANGLE = 6,
+    RBSOG_E_COUL = 7,        /* short + long - self + excl */
+    RBSOG_E_KIN = 8          /* kinetic energy */
+};
+
+typedef struct {
+    double energy[9];        /* RBSOG_E_* */
+    double virial[9];        /* total virial V P (no kinetic part), kcal/mol, row-major */
+    double virial_coul_short[9];
+    double virial_long_r[9]; /* V P^F,r*  (eq. P_approx_r) */
+    double virial_long_nr[9];/* V P^F,nr* (eq. P_approx_nr) */
+    double virial_lj[9];
+    double virial_bonded[9]; /* bonds + angles + exclusion corrections */
+    double pressure[9];      /* (kinetic + virial) / V, atm */
+    double box[3];
+    double volume;
+    int n_distinct_modes;
+    int n_accept_r, n_accept_nr;
+    uint64_t step;
+} rbsog_result;
+
+typedef struct rbsog_ctx rbsog_ctx;
+
+/* Fill *p with the paper's working parameters: Table 2 row 2 (b =
+ * 1.62976708826776469, omega = 1.007806979343806, sigma = 3.270345668108471
+ * r_c / 9), M = M_energy = 10, P = 100, the paper MH sampler, FP32, and the
+ * Langevin NPT settings of sec. 4.3 (0.1 ps / 0.5 ps, 4.5e-5 bar^-1). */
+void rbsog_default_params(rbsog_params *p, double rc);
+
+/* Create a context holding n_systems independent systems (the batched path:
+ * every kernel launch covers all systems).  stream: cudaStream_t to run on
+ * (NULL: a stream the context creates; it orders with the legacy stream).  Runs one force evaluation at step 0
+ * so that rbsog_run can start. */
+rbsog_status rbsog_create(const rbsog_params *params, int n_systems,
+                          const rbsog_system_desc *systems, void *stream,
+                          rbsog_ctx **out);
+
+void rbsog_destroy(rbsog_ctx *ctx);
+
+const char *rbsog_last_error(const rbsog_ctx *ctx);
+
+/* Total atoms of all systems, and atom offset / count of system s. */
+int rbsog_n_atoms(const rbsog_ctx *ctx);
+rbsog_status rbsog_system_range(const rbsog_ctx *ctx, int s, int *atom0, int *n);
+
+/* Replace the box of system s; rescale_positions != 0 scales its positions
+ * affinely (r -> r L'/L). */
+rbsog_status rbsog_set_box(rbsog_ctx *ctx, int s, const double box[3], int rescale_positions);
+
+/* Copy positions (all systems, N_total x 3) in or out.  on_device: r is a
+ * device pointer. */
+rbsog_status rbsog_set_positions(rbsog_ctx *ctx, const double *r, int on_device);
+rbsog_status rbsog_get_positions(rbsog_ctx *ctx, double *r, int on_device);
+rbsog_status rbsog_get_velocities(rbsog_ctx *ctx, double *v, int on_device);
+
+/* One force, energy and pressure evaluation of every system at the current
+ * positions and boxes (Algorithm 1, steps 2-7) with Philox step counter
+ * `step`.  forces (N_total x 3, kcal/(mol A)) may be NULL; results is an
+ * array of n_systems entries or NULL.  The integrator state is not touched. */
+rbsog_status rbsog_step(rbsog_ctx *ctx, uint64_t step, double *forces, int on_device,
+                        rbsog_result *results);
+
+/* Advance every system by nsteps Langevin NPT steps (Algorithm 1 step 8),
+ * replaying a captured CUDA graph of one step.  last: n_systems results of
+ * the final step, or NULL. */
+rbsog_status rbsog_run(rbsog_ctx *ctx, int nsteps, rbsog_result *last);
+
+/* Enqueue nsteps NPT steps on the context stream and return without waiting
+ * or checking flags; rbsog_sync() waits and reports the flags (box too small,
+ * cell overflow, non-finite results) raised since the last check. */
+rbsog_status rbsog_run_async(rbsog_ctx *ctx, int nsteps);
+rbsog_status rbsog_sync(rbsog_ctx *ctx);
+
+/* The context stream (cudaStream_t) the library launches on. */
+void *rbsog_stream(rbsog_ctx *ctx);
+
+/* Checkpoint: the integrator state (positions, momenta, boxes, box momenta,
+ * step counter).  buf == NULL returns the size in *len. */
+rbsog_status rbsog_get_state(rbsog_ctx *ctx, void *buf, size_t *len);
+rbsog_status rbsog_set_state(rbsog_ctx *ctx, const void *buf, size_t len);
+
+/* Introspection of the last evaluation (for tests and diagnostics).
+ * cells: ncell[3] and, per atom of system s, its cell index (x fastest).
+ * modes: m^r (P x 3), m^nr (P x 3), distinct modes D (nD x 3) in
+ * lexicographic order with multiplicities c_r, c_nr (arrays of >= P+1), the
+ * normalizers S^r, S^nr and rho(k_d) (2 nD doubles, re/im interleaved). */
+rbsog_status rbsog_debug_cells(rbsog_ctx *ctx, int s, int *ncell, int *cell_of_atom);
+rbsog_status rbsog_debug_modes(rbsog_ctx *ctx, int s, int *mr, int *mnr, int *D, int *cr,
+                               int *cnr, int *nD, double *S, double *rho);
+
+/* Kernel timings of the last rbsog_step / rbsog_run call with timing enabled:
+ * enable != 0 records CUDA events around each kernel of one step (slower). */
+rbsog_status rbsog_set_timing(rbsog_ctx *ctx, int enable);
+rbsog_status rbsog_get_timing(rbsog_ctx *ctx, int max, char *names, double *ms, int *count);
+
+/* Stateless structure factor (eq. rho_k) on device buffers:
+ *   r    device, N x 3 FP64 positions (any image)
+ *   q    device, N FP64 charges
+ *   m    device, nD x 3 int modes; k = 2 pi m / box
+ *   rho  device, 2 nD FP64 (re, im), overwritten
+ *   work device scratch of rbsog_structure_factor_workspace(N, nD) bytes
+ * precision: RBSOG_FP64 or RBSOG_FP32.  Runs on `stream`. */
+size_t rbsog_structure_factor_workspace(int n_atoms, int nD);
+rbsog_status rbsog_structure_factor(const double *r, const double *q, int n_atoms,
+                                    const double box[3], const int *m, int nD,
+                                    double *rho, void *work, int precision, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBSOG_H */

@@ -1,0 +1,132 @@
+// common.cuh -- shared device definitions of the RBSOG CUDA path (sm_103a).
+//
+// Device layout of a context (all systems concatenated):
+//   per atom (original order): r, p, F (FP64 x3), q, mass (FP64), type, mol,
+//     sys (int); binning products cell, rank (int), loc (cell-local coordinates,
+//     float4/double4), su (fixed-point fractional coordinates + charge, uint4).
+//   per cell (global index = cell0 of the system + local index, x fastest):
+//     count, start; cell-sorted copies pos4 / posd, qt / aux, sidx.
+//   per system: DevSys (box, box momenta, cell grid, normalizers, flags).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rbsog {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.283185307179586;
+constexpr int kMaxGauss = 64;      // Gaussians of the split, M and M_energy
+constexpr int kMaxP = 4096;        // batch size
+constexpr int kCellCap = 2048;     // atoms per cell the kernels accept
+constexpr int kChunk = 1024;       // atoms per chunk of the per-atom kernels
+constexpr int kMaxTypes = 16;
+
+// status flags written by kernels (bit mask in DevSys::flags)
+enum : int {
+    FLAG_BOX = 1,          // box edge below 3 cells of r_c
+    FLAG_OVERFLOW = 2,     // a cell holds more than kCellCap atoms
+    FLAG_NONFINITE = 4,
+};
+
+// Per-system device record.
+struct DevSys {
+    double L[3];          // box edges
+    double ph[3];         // box momenta per coupling group (g/mol A/fs)
+    double Mbox[3];       // box masses per group (<= 0: fixed)
+    double V;
+    double w[3];          // cell widths L / n
+    double Sr, Snr;       // normalizers (eqs. Sr, Snr)
+    double Lh[3];         // box after the first half drift (integrator)
+    double Lp[3];         // box before the step (integrator)
+    int ncell[3];         // current cells per axis
+    int ncap[3];          // allocated cells per axis
+    int cell0;            // first global cell
+    int ncell_cap_total;  // ncap[0]*ncap[1]*ncap[2]
+    int atom0, n;
+    int nD;               // distinct modes of the last evaluation
+    int nacc_r, nacc_nr;
+    int coupling;
+    int flags;
+    unsigned long long rng_id;   // second word of the Philox key
+};
+
+// Per-distinct-mode data handed from the estimator to the force kernel.
+struct ModeCoef {
+    double a[3];          // alpha_d k_d: force on i is q_i a (rho_im cos - rho_re sin)
+    double re, im;        // rho(k_d)
+    int m[3];
+    int pad;
+};
+
+// Philox4x64-10 (Salmon et al., SC'11), written from its published definition.
+__host__ __device__ inline void philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+#ifdef __CUDA_ARCH__
+        uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+        uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+#else
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+#endif
+        uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+// Philox counter purposes: counter = (step, purpose, index, 0), key = (seed, system).
+enum : uint64_t { PUR_START = 1, PUR_PROPOSAL = 2, PUR_ACCEPT = 3, PUR_NR_IID = 4, PUR_ATOM = 5, PUR_BOX = 6 };
+
+__host__ __device__ inline void draw4(uint64_t seed, uint64_t sys, uint64_t step, uint64_t purpose,
+                                      uint64_t index, uint64_t out[4])
+{
+    const uint64_t ctr[4] = {step, purpose, index, 0};
+    const uint64_t key[2] = {seed, sys};
+    philox4x64(ctr, key, out);
+}
+
+// uniform in (0,1): ((x >> 12) + 1/2) 2^-52
+__host__ __device__ inline double u01(uint64_t x)
+{
+    return ((double)(x >> 12) + 0.5) * 2.220446049250313e-16;
+}
+
+__device__ inline unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ inline double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of an FP64 value (all threads get it).  smem >= 32 doubles.
+__device__ inline double block_sum(double v, double *smem)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane_id() == 0) smem[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += smem[i];
+    __syncthreads();
+    return t;
+}
+
+}  // namespace rbsog

@@ -1,0 +1,140 @@
+// internal.h -- host-side launchers of the RBSOG kernels (one per .cu file).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rbsog {
+
+// Constants of the SOG split, passed by value (kernel parameter space).
+struct SogConsts {
+    int M, ME;                  // Gaussians of force/pressure, energy
+    double rc, ke;
+    double w[kMaxGauss], s[kMaxGauss], wt[kMaxGauss], st[kMaxGauss];
+};
+
+struct PairConstsF {           // FP32 pair kernel constants
+    int M, ME, ntypes;
+    float rc2, ke;
+    float beta[kMaxGauss];      // log2(e) / s_l^2
+    float wt[kMaxGauss];        // w~_l
+    float w[kMaxGauss];         // w_l
+    float lj_a[kMaxTypes * kMaxTypes];   // 4 eps sig^12
+    float lj_b[kMaxTypes * kMaxTypes];   // 4 eps sig^6
+};
+
+struct PairConstsD {           // FP64 pair kernel constants
+    int M, ME, ntypes;
+    double rc2, ke;
+    double inv_s2[kMaxGauss];   // 1 / s_l^2
+    double wt[kMaxGauss];
+    double w[kMaxGauss];
+    double lj_a[kMaxTypes * kMaxTypes];
+    double lj_b[kMaxTypes * kMaxTypes];
+};
+
+// Everything a kernel needs about the batch of systems.
+struct Batch {
+    int S;                      // systems
+    int N;                      // atoms
+    int C;                      // total cells (capacity)
+    int sub;                    // cells per cutoff
+    double rc;
+    DevSys *sys;                // [S]
+    const int *atom_sys;        // [N]
+    const int *cell_sys;        // [C]
+    const int *chunk_sys, *chunk_a0, *chunk_n;   // atom chunks
+    int nchunks;
+};
+
+struct AtomArrays {
+    double *r, *p, *F;          // [3N]
+    const double *q, *mass;     // [N]
+    const int *type, *mol;      // [N]
+    int *cell, *rank;           // [N]
+    float4 *locf;               // [N] cell-local coords + mol bits (FP32)
+    double4 *locd;              // [N] cell-local coords + q (FP64)
+    uint4 *su;                  // [N] fixed-point fractional coords + q bits
+    int *count, *start;         // [C], [C + 1]
+    int *sidx;                  // [N] cell-sorted original index
+    float4 *pos4;               // [N] sorted, FP32
+    float2 *qt;                 // [N] sorted (q, type bits)
+    double4 *posd;              // [N] sorted, FP64
+    int2 *aux;                  // [N] sorted (mol, type)
+};
+
+// ---- k_bin.cu
+void launch_box_prep(const Batch &b, cudaStream_t st);
+void launch_clear_flags(const Batch &b, cudaStream_t st);
+void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
+void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st);
+void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
+
+// ---- k_pair.cu: partial = per-cell (Ucoul, Ulj, Wc[6], Wl[6]) as 14 doubles
+void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
+                 const PairConstsD &cd, double *partial, int warps_per_block, cudaStream_t st);
+
+// ---- k_sampler.cu
+struct SamplerArgs {
+    int P, M, kind;
+    uint64_t seed;
+    const unsigned long long *step;   // the evaluation uses *step + 1
+    double wt[kMaxGauss], st[kMaxGauss];
+    double cr[kMaxGauss], cn[kMaxGauss], st2q[kMaxGauss];
+    double sig_u;
+};
+void launch_sampler(const Batch &b, const SamplerArgs &sa, int *mr, int *mnr, int *D, int *cr,
+                    int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, int Dcap,
+                    cudaStream_t st);
+
+// ---- k_kspace.cu
+void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
+               double *part, cudaStream_t st);
+void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_sys, const int *D,
+                     const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
+                     double *rho, ModeCoef *coef, double *lr_out, cudaStream_t st);
+void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
+                     int Dcap, cudaStream_t st);
+size_t sk_stateless_workspace(int n, int nD);
+cudaError_t sk_stateless(const double *r, const double *q, int n, const double box[3], const int *m,
+                         int nD, double *rho, void *work, int precision, cudaStream_t st);
+
+// ---- k_mol.cu
+struct MolArrays {
+    int nmol;
+    const int *mol_start, *mol_n;       // [nmol]
+    const int *b_start, *a_start, *e_start;   // [nmol + 1] CSR of bonds / angles / exclusions
+    const int *bonds;  const double *bk, *br0;
+    const int *angles; const double *ak, *at0;
+    const int *excl;
+    const int *mol_sys;                 // [nmol]
+    const int *mchunk_sys, *mchunk_m0, *mchunk_n;
+    int nmchunks;
+};
+void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc,
+                double *partial /* per mol chunk: Ue, Ub, Ua, W[6] excl, W[6] bonded */, int precision,
+                cudaStream_t st);
+
+// ---- k_integrate.cu
+struct IntegArgs {
+    double dt, T, Pext, gamma, gamma_box, kB, ftm2v, nktv2p;
+    uint64_t seed;
+    const unsigned long long *step;   // device counter of the last evaluation; a step uses *step + 1
+};
+void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st);
+void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st);
+void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int kick,
+                         double *kin_part, cudaStream_t st);
+// per-system reduction of every partial into sysred[S x kRed]; advances *step
+constexpr int kRed = 64;
+void launch_finalize(const Batch &b, const double *pair_part, const double *lr_out,
+                     const double *mol_part, const int *mchunk_first, const int *mchunk_count,
+                     const double *kin_part, const int *chunk_first, const int *chunk_count,
+                     const double *self_energy, const IntegArgs &ia, int do_box_kick,
+                     double *sysred, unsigned long long *step, cudaStream_t st);
+size_t pair_smem_bytes(int precision, int nw);
+cudaError_t prepare_pair(int precision, int nw);
+cudaError_t prepare_sampler(int P);
+
+}  // namespace rbsog

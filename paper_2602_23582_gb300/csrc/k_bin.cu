@@ -1,0 +1,201 @@
+// k_bin.cu -- cell lists rebuilt every step (the box rescales each step).
+//
+// Binning convention (matches the oracle's definition bit for bit; no FMA in
+// the decision arithmetic): s = r / L, s -= floor(s), s = 0 if s >= 1;
+// n = floor(L * sub / r_c) cells per axis; cell = min(floor(s n), n - 1),
+// x fastest.  A warp-aggregated counting sort (match_any + one atomicAdd per
+// distinct cell in the warp) gives every atom a rank in its cell; an
+// exclusive scan gives the cell starts; atoms are scattered to their cell and
+// each cell's list is then sorted by original index, so the cell-sorted order
+// (and every sum over it) is deterministic.
+#include "internal.h"
+
+namespace rbsog {
+
+__global__ void k_box_prep(DevSys *sys, int S, int sub, double rc)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    DevSys &d = sys[s];
+    int minc = 2 * sub + 1;
+    for (int a = 0; a < 3; ++a) {
+        double L = d.L[a];
+        int n = (int)floor(__ddiv_rn(__dmul_rn(L, (double)sub), rc));
+        if (!(L > 0.0) || n < minc) d.flags |= FLAG_BOX;
+        if (n > d.ncap[a]) n = d.ncap[a];
+        if (n < 1) n = 1;
+        d.ncell[a] = n;
+        d.w[a] = L / n;
+    }
+    d.V = d.L[0] * d.L[1] * d.L[2];
+}
+
+__global__ void k_clear_flags(DevSys *sys, int S)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) sys[s].flags = 0;
+}
+
+void launch_clear_flags(const Batch &b, cudaStream_t st)
+{
+    k_clear_flags<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S);
+}
+
+void launch_box_prep(const Batch &b, cudaStream_t st)
+{
+    k_box_prep<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, b.sub, b.rc);
+}
+
+__global__ void k_bin(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys,
+                      const double *__restrict__ r, const double *__restrict__ q,
+                      const int *__restrict__ mol, int N, int *__restrict__ cell,
+                      int *__restrict__ rank, int *__restrict__ count, float4 *__restrict__ locf,
+                      double4 *__restrict__ locd, uint4 *__restrict__ su, int precision)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned act = __ballot_sync(0xffffffffu, i < N);
+    if (i >= N) return;
+    const DevSys &d = sys[atom_sys[i]];
+    int c[3];
+    double sf[3], xl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double L = d.L[a];
+        double s = __ddiv_rn(r[3 * i + a], L);
+        s = __dsub_rn(s, floor(s));
+        if (s >= 1.0) s = 0.0;
+        int n = d.ncell[a];
+        int k = (int)floor(__dmul_rn(s, (double)n));
+        if (k > n - 1) k = n - 1;
+        c[a] = k;
+        sf[a] = s;
+        xl[a] = s * L - k * d.w[a];
+    }
+    const int gc = d.cell0 + c[0] + d.ncell[0] * (c[1] + d.ncell[1] * c[2]);
+    cell[i] = gc;
+    // warp-aggregated atomic: one atomicAdd per distinct cell in the warp
+    const unsigned peers = __match_any_sync(act, gc);
+    const int leader = __ffs(peers) - 1;
+    const unsigned lane = lane_id();
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(&count[gc], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    rank[i] = base + __popc(peers & ((1u << lane) - 1u));
+    const double qi = q[i];
+    if (precision == 1) {
+        locf[i] = make_float4((float)xl[0], (float)xl[1], (float)xl[2], __int_as_float(mol[i]));
+        su[i] = make_uint4(__double2uint_rz(sf[0] * 4294967296.0), __double2uint_rz(sf[1] * 4294967296.0),
+                           __double2uint_rz(sf[2] * 4294967296.0), __float_as_uint((float)qi));
+    } else {
+        locd[i] = make_double4(xl[0], xl[1], xl[2], qi);
+    }
+}
+
+void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
+{
+    cudaMemsetAsync(a.count, 0, sizeof(int) * b.C, st);
+    k_bin<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.r, a.q, a.mol, b.N, a.cell, a.rank,
+                                             a.count, a.locf, a.locd, a.su, precision);
+}
+
+// Exclusive scan of the cell counts (all systems, global cell order): the
+// atoms of system s occupy [atom0, atom0 + n) of the sorted arrays.
+__global__ void k_scan(const int *__restrict__ count, int *__restrict__ start, int C,
+                       const int *__restrict__ cell_sys, DevSys *sys)
+{
+    __shared__ int tsum[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int per = (C + T - 1) / T;
+    const int c0 = t * per, c1 = min(C, c0 + per);
+    int s = 0;
+    for (int c = c0; c < c1; ++c) {
+        int v = count[c];
+        if (v > kCellCap) atomicOr(&sys[cell_sys[c]].flags, (int)FLAG_OVERFLOW);
+        s += v;
+    }
+    tsum[t] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the thread sums
+    for (int o = 1; o < T; o <<= 1) {
+        int v = (t >= o) ? tsum[t - o] : 0;
+        __syncthreads();
+        tsum[t] += v;
+        __syncthreads();
+    }
+    int run = tsum[t] - s;
+    for (int c = c0; c < c1; ++c) {
+        start[c] = run;
+        run += count[c];
+    }
+    if (t == T - 1) start[C] = tsum[T - 1];
+}
+
+void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st)
+{
+    k_scan<<<1, 1024, 0, st>>>(a.count, a.start, b.C, b.cell_sys, b.sys);
+}
+
+__global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ rank,
+                          const int *__restrict__ start, int *__restrict__ sidx, int N)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    sidx[start[cell[i]] + rank[i]] = i;
+}
+
+// One warp per cell: bitonic sort of the cell's atom list by original index,
+// then gather the cell-sorted copies used by the pair kernel.
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSortWarps)
+k_cell_sort(const int *__restrict__ start, int C, int *__restrict__ sidx,
+            const float4 *__restrict__ locf, const double4 *__restrict__ locd,
+            const double *__restrict__ q, const int *__restrict__ type, const int *__restrict__ mol,
+            float4 *__restrict__ pos4, float2 *__restrict__ qt, double4 *__restrict__ posd,
+            int2 *__restrict__ aux, int precision)
+{
+    __shared__ int buf[kSortWarps][kCellCap];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int c = blockIdx.x * kSortWarps + w;
+    if (c >= C) return;
+    const int base = start[c];
+    const int n = min(start[c + 1] - base, kCellCap);
+    if (n == 0) return;
+    int *s = buf[w];
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int k = lane; k < p2; k += 32) s[k] = (k < n) ? sidx[base + k] : 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < p2 / 2; t += 32) {
+                int lo = 2 * j * (t / j) + (t % j);
+                int hi = lo + j;
+                bool up = (lo & k) == 0;
+                int x = s[lo], y = s[hi];
+                if ((x > y) == up) { s[lo] = y; s[hi] = x; }
+            }
+            __syncwarp();
+        }
+    }
+    for (int k = lane; k < n; k += 32) {
+        int i = s[k];
+        sidx[base + k] = i;
+        if (precision == 1) {
+            pos4[base + k] = locf[i];
+            qt[base + k] = make_float2((float)q[i], __int_as_float(type[i]));
+        } else {
+            posd[base + k] = locd[i];
+            aux[base + k] = make_int2(mol[i], type[i]);
+        }
+    }
+}
+
+void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
+{
+    k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(a.cell, a.rank, a.start, a.sidx, b.N);
+    k_cell_sort<<<(b.C + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, st>>>(
+        a.start, b.C, a.sidx, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
+}
+
+}  // namespace rbsog

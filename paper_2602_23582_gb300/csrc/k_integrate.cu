@@ -1,0 +1,271 @@
+// k_integrate.cu -- Langevin NPT integrator (paper eq. Langevin_NPT, Algorithm 1
+// step 8) for an orthorhombic h whose coupled axes share one box momentum, and
+// the per-system reductions of every partial sum.
+//
+// Splitting (BAOAB; the paper defers its integrator to another work, so this
+// is our reading), per step n:
+//   B  p^h += dt/2 G(K, W) ftm2v;   p += dt/2 F ftm2v
+//   A  dt/2 exact drift: L' = L + v tau, r' = (L'/L) r + (p/m) tau, p' = (L/L') p
+//   O  p <- c p + sqrt((1 - c^2) m kB T ftm2v) xi, c = exp(-gamma dt); same for p^h
+//   A  dt/2 drift; wrap r into [0, L)
+//   force evaluation (counter n)
+//   B  p += dt/2 F ftm2v;  K = sum p (x) p / m;  p^h += dt/2 G(K, W) ftm2v
+// with the generalised box force G_g = sum_{a in g} (K_aa + W_aa - P_ext V - kB T) / L_a.
+#include "internal.h"
+
+namespace rbsog {
+
+namespace {
+
+__device__ __forceinline__ int axis_group(int coupling, int a)
+{
+    if (coupling == 0) return 0;
+    if (coupling == 1) return a == 2 ? 1 : 0;
+    return a;
+}
+
+__device__ void box_muller2(uint64_t a, uint64_t b, double &z0, double &z1)
+{
+    double u1 = u01(a), u2 = u01(b);
+    double rr = sqrt(-2.0 * log(u1));
+    double ang = kTwoPi * u2;
+    z0 = rr * cos(ang);
+    z1 = rr * sin(ang);
+}
+
+__device__ void box_force(const DevSys &d, const double *red, const IntegArgs &ia, double G[3])
+{
+    const double V = d.L[0] * d.L[1] * d.L[2];
+    const double pext = ia.Pext / ia.nktv2p;
+    G[0] = G[1] = G[2] = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        // red: W total at [9 + a], K at [45 + a] (diagonal entries)
+        double Kaa = red[45 + a], Waa = red[9 + a];
+        G[axis_group(d.coupling, a)] += (Kaa + Waa - pext * V - ia.kB * ia.T) / d.L[a];
+    }
+}
+
+}  // namespace
+
+// Box part of B (first half), A, O, A.  One thread per system.
+__global__ void k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    DevSys &d = sys[s];
+    const double *red = sysred + (size_t)s * kRed;
+    double G[3];
+    box_force(d, red, ia, G);
+    const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
+    for (int g = 0; g < ng; ++g)
+        if (d.Mbox[g] > 0.0) d.ph[g] += 0.5 * ia.dt * G[g] * ia.ftm2v;
+    const double tau = 0.5 * ia.dt;
+    for (int a = 0; a < 3; ++a) {
+        int g = axis_group(d.coupling, a);
+        double v = d.Mbox[g] > 0.0 ? d.ph[g] / d.Mbox[g] : 0.0;
+        d.Lp[a] = d.L[a];
+        d.Lh[a] = d.L[a] + v * tau;
+    }
+    uint64_t wds[4];
+    draw4(ia.seed, d.rng_id, *ia.step + 1, PUR_BOX, 0, wds);
+    double z[4];
+    box_muller2(wds[0], wds[1], z[0], z[1]);
+    box_muller2(wds[2], wds[3], z[2], z[3]);
+    const double ch = exp(-ia.gamma_box * ia.dt);
+    for (int g = 0; g < ng; ++g) {
+        if (d.Mbox[g] <= 0.0) continue;
+        double sdv = sqrt((1.0 - ch * ch) * d.Mbox[g] * ia.kB * ia.T * ia.ftm2v);
+        d.ph[g] = ch * d.ph[g] + sdv * z[g];
+    }
+    for (int a = 0; a < 3; ++a) {
+        int g = axis_group(d.coupling, a);
+        double v = d.Mbox[g] > 0.0 ? d.ph[g] / d.Mbox[g] : 0.0;
+        d.L[a] = d.Lh[a] + v * tau;
+    }
+}
+
+void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st)
+{
+    k_box_half<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, ia, sysred);
+}
+
+// Atom part of B (first half), A, O, A and the wrap.
+__global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys, int N,
+                              double *__restrict__ r, double *__restrict__ p, const double *__restrict__ F,
+                              const double *__restrict__ mass, const IntegArgs ia)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int s = atom_sys[i];
+    const DevSys &d = sys[s];
+    const double m = mass[i], tau = 0.5 * ia.dt;
+    double x[3], v[3];
+    for (int a = 0; a < 3; ++a) {
+        x[a] = r[3 * i + a];
+        v[a] = p[3 * i + a] + 0.5 * ia.dt * F[3 * i + a] * ia.ftm2v;
+    }
+    for (int a = 0; a < 3; ++a) {
+        double sc = d.Lh[a] / d.Lp[a];
+        x[a] = sc * x[a] + v[a] / m * tau;
+        v[a] = v[a] / sc;
+    }
+    uint64_t wds[4];
+    draw4(ia.seed, d.rng_id, *ia.step + 1, PUR_ATOM, (uint64_t)(i - d.atom0), wds);
+    double z[4];
+    box_muller2(wds[0], wds[1], z[0], z[1]);
+    box_muller2(wds[2], wds[3], z[2], z[3]);
+    const double c = exp(-ia.gamma * ia.dt);
+    const double sdv = sqrt((1.0 - c * c) * m * ia.kB * ia.T * ia.ftm2v);
+    for (int a = 0; a < 3; ++a) v[a] = c * v[a] + sdv * z[a];
+    for (int a = 0; a < 3; ++a) {
+        double sc = d.L[a] / d.Lh[a];
+        x[a] = sc * x[a] + v[a] / m * tau;
+        v[a] = v[a] / sc;
+        double L = d.L[a];
+        x[a] -= L * floor(x[a] / L);
+        if (x[a] >= L) x[a] -= L;
+        r[3 * i + a] = x[a];
+        p[3 * i + a] = v[a];
+    }
+}
+
+void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st)
+{
+    k_atom_update<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, a.mass, ia);
+}
+
+// Second half kick (optional) and the kinetic tensor per atom chunk:
+// kin_part[chunk][6] = sum p (x) p / m (kcal/mol).
+__global__ void __launch_bounds__(256)
+k_kick_kinetic(const int *__restrict__ chunk_a0, const int *__restrict__ chunk_n, double *__restrict__ p,
+               const double *__restrict__ F, const double *__restrict__ mass, double kick, double mvv2e,
+               double *__restrict__ kin_part)
+{
+    __shared__ double red[32];
+    const int c = blockIdx.x, a0 = chunk_a0[c], na = chunk_n[c];
+    double k6[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+        const int i = a0 + k;
+        double v[3];
+        for (int a = 0; a < 3; ++a) {
+            v[a] = p[3 * i + a];
+            if (kick != 0.0) {
+                v[a] += kick * F[3 * i + a];
+                p[3 * i + a] = v[a];
+            }
+        }
+        const double im = 1.0 / mass[i];
+        k6[0] += v[0] * v[0] * im; k6[1] += v[1] * v[1] * im; k6[2] += v[2] * v[2] * im;
+        k6[3] += v[0] * v[1] * im; k6[4] += v[0] * v[2] * im; k6[5] += v[1] * v[2] * im;
+    }
+    for (int a = 0; a < 6; ++a) {
+        double t = block_sum(k6[a], red);
+        if (threadIdx.x == 0) kin_part[(size_t)c * 6 + a] = t * mvv2e;
+    }
+}
+
+void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int do_kick,
+                         double *kin_part, cudaStream_t st)
+{
+    const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0;
+    k_kick_kinetic<<<b.nchunks, 256, 0, st>>>(b.chunk_a0, b.chunk_n, a.p, a.F, a.mass, kick, 1.0 / ia.ftm2v,
+                                              kin_part);
+}
+
+// Per-system reduction of all partials (fixed order) into sysred[s][kRed]:
+//  [0..8] energies (RBSOG_E_*), [9..14] W total (xx yy zz xy xz yz),
+//  [15..20] W short Coulomb, [21..26] W^F,r*, [27..32] W^F,nr*, [33..38] W LJ,
+//  [39..44] W bonded + exclusions, [45..50] K, [51] V, [52..54] L,
+//  [55] nD, [56] acc r, [57] acc nr, [58] flags, [59..61] box momenta.
+__global__ void __launch_bounds__(128)
+k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__restrict__ lr_out,
+           const double *__restrict__ mol_part, const int *__restrict__ mchunk_first,
+           const int *__restrict__ mchunk_count, const double *__restrict__ kin_part,
+           const int *__restrict__ chunk_first, const int *__restrict__ chunk_count,
+           const double *__restrict__ self_energy, const IntegArgs ia, int do_box_kick,
+           double *__restrict__ sysred, unsigned long long *step)
+{
+    __shared__ double red[32];
+    __shared__ double acc[64];
+    const int s = blockIdx.x, tid = threadIdx.x;
+    DevSys &d = sys[s];
+    double *o = sysred + (size_t)s * kRed;
+    // pair partials: 14 per cell
+    const int nc = d.ncell_cap_total;
+    for (int k = 0; k < 14; ++k) {
+        double v = 0.0;
+        for (int c = tid; c < nc; c += blockDim.x) v += pair_part[(size_t)(d.cell0 + c) * 14 + k];
+        v = block_sum(v, red);
+        if (tid == 0) acc[k] = v;
+    }
+    for (int k = 0; k < 15; ++k) {
+        double v = 0.0;
+        for (int c = tid; c < mchunk_count[s]; c += blockDim.x) v += mol_part[(size_t)(mchunk_first[s] + c) * 15 + k];
+        v = block_sum(v, red);
+        if (tid == 0) acc[14 + k] = v;
+    }
+    for (int k = 0; k < 6; ++k) {
+        double v = 0.0;
+        for (int c = tid; c < chunk_count[s]; c += blockDim.x) v += kin_part[(size_t)(chunk_first[s] + c) * 6 + k];
+        v = block_sum(v, red);
+        if (tid == 0) acc[29 + k] = v;
+    }
+    if (tid != 0) return;
+    const double *lr = lr_out + (size_t)s * 16;
+    const double us = self_energy[s];
+    double e[9];
+    e[0] = acc[0];                 // U^N Coulomb
+    e[1] = lr[0];                  // U^F*
+    e[2] = us;
+    e[3] = acc[14];                // exclusions
+    e[4] = acc[1];                 // LJ
+    e[5] = acc[15];                // bonds
+    e[6] = acc[16];                // angles
+    e[7] = e[0] + e[1] - e[2] + e[3];
+    double K[6];
+    for (int a = 0; a < 6; ++a) K[a] = acc[29 + a];
+    e[8] = 0.5 * (K[0] + K[1] + K[2]);
+    double Wc[6], Wr[6], Wnr[6], Wl[6], Wb[6], W[6];
+    for (int a = 0; a < 6; ++a) {
+        Wc[a] = acc[2 + a];
+        Wl[a] = acc[8 + a];
+        Wr[a] = a < 3 ? lr[1] : 0.0;
+        Wnr[a] = lr[2 + a];
+        Wb[a] = acc[17 + a] + acc[23 + a];
+        W[a] = Wc[a] + Wr[a] + Wnr[a] + Wl[a] + Wb[a];
+    }
+    bool finite = true;
+    for (int a = 0; a < 9; ++a) { o[a] = e[a]; finite = finite && isfinite(e[a]); }
+    for (int a = 0; a < 6; ++a) {
+        o[9 + a] = W[a]; o[15 + a] = Wc[a]; o[21 + a] = Wr[a]; o[27 + a] = Wnr[a];
+        o[33 + a] = Wl[a]; o[39 + a] = Wb[a]; o[45 + a] = K[a];
+        finite = finite && isfinite(W[a]);
+    }
+    if (!finite) d.flags |= FLAG_NONFINITE;
+    if (do_box_kick) {
+        double G[3];
+        box_force(d, o, ia, G);
+        const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
+        for (int g = 0; g < ng; ++g)
+            if (d.Mbox[g] > 0.0) d.ph[g] += 0.5 * ia.dt * G[g] * ia.ftm2v;
+    }
+    o[51] = d.L[0] * d.L[1] * d.L[2];
+    o[52] = d.L[0]; o[53] = d.L[1]; o[54] = d.L[2];
+    o[55] = d.nD; o[56] = d.nacc_r; o[57] = d.nacc_nr; o[58] = d.flags;
+    o[59] = d.ph[0]; o[60] = d.ph[1]; o[61] = d.ph[2];
+}
+
+__global__ void k_step_advance(unsigned long long *step) { *step += 1ull; }
+
+void launch_finalize(const Batch &b, const double *pair_part, const double *lr_out, const double *mol_part,
+                     const int *mchunk_first, const int *mchunk_count, const double *kin_part,
+                     const int *chunk_first, const int *chunk_count, const double *self_energy,
+                     const IntegArgs &ia, int do_box_kick, double *sysred, unsigned long long *step,
+                     cudaStream_t st)
+{
+    k_finalize<<<b.S, 128, 0, st>>>(b.sys, pair_part, lr_out, mol_part, mchunk_first, mchunk_count, kin_part,
+                                    chunk_first, chunk_count, self_energy, ia, do_box_kick, sysred, step);
+    k_step_advance<<<1, 1, 0, st>>>(step);
+}
+
+}  // namespace rbsog

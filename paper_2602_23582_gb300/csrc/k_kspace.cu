@@ -1,0 +1,374 @@
+// k_kspace.cu -- random-batch Fourier part (paper sec. 3.2, App. B).
+//
+//   rho(k_d) = sum_j q_j e^{i k_d . r_j} = sum_j q_j e^{2 pi i m_d . s_j}   (eq. rho_k)
+//   U^F*     = ke S^r /(4 V P) sum_d c_r |rho_d|^2 / k_d^2                  (App. A with App. B's proposal)
+//   V P^F,r* = ke S^r /(4 V P) sum_d c_r |rho_d|^2 / k_d^2 I                (eq. P_approx_r)
+//   V P^F,nr*= -ke S^nr/(8 V P) sum_d c_nr |rho_d|^2 k_d (x) k_d / k_d^4   (eq. P_approx_nr)
+//   F_i     += q_i sum_d alpha_d k_d Im(e^{-i k_d . r_i} rho_d),
+//              alpha_d = -ke (S^r / 2) c_r / (P V k_d^2)                   (eq. f_approx)
+// with the force proposal of App. B equal to P^r and its normaliser S = S^r/2
+// for the consistent split (w_l = w~_l s~_l^2 / 2, App. C).
+//
+// FP32 build: the phase m.s mod 1 is formed exactly in 32-bit integer
+// arithmetic on fixed-point fractional coordinates (s 2^32), then sincospif
+// on a reduced argument in [-1, 1); per-lane sums are compensated FP32,
+// lane/chunk sums FP64.  FP64 build: phases and sums in FP64.
+#include "internal.h"
+
+namespace rbsog {
+
+namespace {
+
+constexpr int kModeGroup = 16;   // modes per block of the S(k) kernel
+constexpr int kSkThreads = 256;
+
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ void phase_sincos_f(const int m[3], uint4 su, float &sn, float &cs)
+{
+    unsigned ph = (unsigned)m[0] * su.x + (unsigned)m[1] * su.y + (unsigned)m[2] * su.z;
+    float f = (float)(int)ph * 4.656612873077393e-10f;   // 2^-31: turns*2 in [-1, 1)
+    sincospif(f, &sn, &cs);
+}
+
+__device__ __forceinline__ void phase_sincos_d(const int m[3], double sx, double sy, double sz,
+                                               double &sn, double &cs)
+{
+    double t = (double)m[0] * sx + (double)m[1] * sy + (double)m[2] * sz;
+    t -= rint(t);
+    sincospi(2.0 * t, &sn, &cs);
+}
+
+// rho partial sums of one chunk of atoms for a group of modes.
+// su: FP32 atom data (fixed-point s, q bits); r/q/L: FP64 atom data.
+template <bool F32>
+__device__ void sk_chunk(const uint4 *su, const double *r, const double *q, const double L[3],
+                         int a0, int na, const int *D, int d0, int nd_here, double *out /* [nd_here][2] */)
+{
+    __shared__ uint4 s_su[F32 ? kChunk : 1];
+    __shared__ double s_sd[F32 ? 1 : kChunk][4];
+    const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = tid; k < na; k += blockDim.x) {
+        if (F32) {
+            s_su[k] = su[a0 + k];
+        } else {
+            const int i = a0 + k;
+            s_sd[k][0] = r[3 * i] / L[0];
+            s_sd[k][1] = r[3 * i + 1] / L[1];
+            s_sd[k][2] = r[3 * i + 2] / L[2];
+            s_sd[k][3] = q[i];
+        }
+    }
+    __syncthreads();
+    for (int dd = warp; dd < nd_here; dd += nw) {
+        const int m[3] = {D[3 * (d0 + dd)], D[3 * (d0 + dd) + 1], D[3 * (d0 + dd) + 2]};
+        double re, im;
+        if (F32) {
+            Kahan kr, ki;
+            for (int k = lane; k < na; k += 32) {
+                uint4 v = s_su[k];
+                float sn, cs;
+                phase_sincos_f(m, v, sn, cs);
+                float qq = __uint_as_float(v.w);
+                kr.add(qq * cs);
+                ki.add(qq * sn);
+            }
+            re = warp_sum(kr.value());
+            im = warp_sum(ki.value());
+        } else {
+            double sr = 0.0, si = 0.0;
+            for (int k = lane; k < na; k += 32) {
+                double sn, cs;
+                phase_sincos_d(m, s_sd[k][0], s_sd[k][1], s_sd[k][2], sn, cs);
+                sr += s_sd[k][3] * cs;
+                si += s_sd[k][3] * sn;
+            }
+            re = warp_sum(sr);
+            im = warp_sum(si);
+        }
+        if (lane == 0) {
+            out[2 * dd] = re;
+            out[2 * dd + 1] = im;
+        }
+    }
+}
+
+}  // namespace
+
+// grid: (nchunks, ceil(Dcap / kModeGroup)); part[chunk][Dcap][2]
+template <bool F32>
+__global__ void __launch_bounds__(kSkThreads)
+k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
+     const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
+     const double *__restrict__ q, const int *__restrict__ D, int Dcap, double *__restrict__ part)
+{
+    const int c = blockIdx.x, s = chunk_sys[c];
+    const DevSys &d = sys[s];
+    const int d0 = blockIdx.y * kModeGroup;
+    if (d0 >= d.nD) return;
+    const int nd_here = min(kModeGroup, d.nD - d0);
+    const double L[3] = {d.L[0], d.L[1], d.L[2]};
+    sk_chunk<F32>(su, r, q, L, chunk_a0[c], chunk_n[c], D + (size_t)s * Dcap * 3, d0, nd_here,
+                  part + ((size_t)c * Dcap + d0) * 2);
+}
+
+void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
+               double *part, cudaStream_t st)
+{
+    dim3 grid(b.nchunks, (Dcap + kModeGroup - 1) / kModeGroup);
+    if (precision == 1)
+        k_sk<true><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
+                                               D, Dcap, part);
+    else
+        k_sk<false><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
+                                                D, Dcap, part);
+}
+
+// One block per system: rho = sum of chunk partials (fixed order), estimators,
+// per-mode force coefficients.  lr_out[s][16] = {U^F*, V P^F,r* (scalar),
+// V P^F,nr* xx yy zz xy xz yz, Sr, Snr}.
+__global__ void __launch_bounds__(256)
+k_estimate(DevSys *sys, const int *__restrict__ first_chunk, const int *__restrict__ nchunk_sys,
+           const int *__restrict__ D_all, const int *__restrict__ cr_all, const int *__restrict__ cnr_all,
+           int Dcap, int P, double ke, const double *__restrict__ part, double *__restrict__ rho_all,
+           ModeCoef *__restrict__ coef_all, double *__restrict__ lr_out)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    DevSys &d = sys[s];
+    const int nD = d.nD, c0 = first_chunk[s], nc = nchunk_sys[s];
+    const int *D = D_all + (size_t)s * Dcap * 3, *cr = cr_all + (size_t)s * Dcap, *cnr = cnr_all + (size_t)s * Dcap;
+    double *rho = rho_all + (size_t)s * Dcap * 2;
+    ModeCoef *coef = coef_all + (size_t)s * Dcap;
+    const double V = d.L[0] * d.L[1] * d.L[2];
+    double ar = 0.0, b[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < nD; k += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            re += part[((size_t)(c0 + c) * Dcap + k) * 2];
+            im += part[((size_t)(c0 + c) * Dcap + k) * 2 + 1];
+        }
+        rho[2 * k] = re;
+        rho[2 * k + 1] = im;
+        double kv[3];
+        for (int a = 0; a < 3; ++a) kv[a] = kTwoPi * D[3 * k + a] / d.L[a];
+        double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+        double r2 = re * re + im * im;
+        ar += cr[k] * r2 / k2;
+        double g = cnr[k] * r2 / (k2 * k2);
+        b[0] += g * kv[0] * kv[0]; b[1] += g * kv[1] * kv[1]; b[2] += g * kv[2] * kv[2];
+        b[3] += g * kv[0] * kv[1]; b[4] += g * kv[0] * kv[2]; b[5] += g * kv[1] * kv[2];
+        double alpha = -ke * (0.5 * d.Sr) / P * cr[k] / (V * k2);
+        ModeCoef mc;
+        mc.a[0] = alpha * kv[0]; mc.a[1] = alpha * kv[1]; mc.a[2] = alpha * kv[2];
+        mc.re = re; mc.im = im;
+        mc.m[0] = D[3 * k]; mc.m[1] = D[3 * k + 1]; mc.m[2] = D[3 * k + 2];
+        mc.pad = 0;
+        coef[k] = mc;
+    }
+    ar = block_sum(ar, red);
+    for (int a = 0; a < 6; ++a) b[a] = block_sum(b[a], red);
+    if (threadIdx.x == 0) {
+        double *o = lr_out + (size_t)s * 16;
+        o[0] = ke * d.Sr / (4.0 * V * P) * ar;
+        o[1] = o[0];
+        for (int a = 0; a < 6; ++a) o[2 + a] = -ke * d.Snr / (8.0 * V * P) * b[a];
+        o[8] = d.Sr;
+        o[9] = d.Snr;
+    }
+}
+
+void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_sys, const int *D,
+                     const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
+                     double *rho, ModeCoef *coef, double *lr_out, cudaStream_t st)
+{
+    k_estimate<<<b.S, 256, 0, st>>>(b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho,
+                                    coef, lr_out);
+}
+
+// Long-range force (eq. f_approx) added to F.  One block per atom chunk; the
+// system's mode coefficients are staged in shared memory in tiles.
+constexpr int kModeTile = 256;
+
+template <bool F32>
+__global__ void __launch_bounds__(256)
+k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
+           const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
+           const double *__restrict__ q, const ModeCoef *__restrict__ coef_all, int Dcap,
+           double *__restrict__ F)
+{
+    __shared__ float4 tf[kModeTile];      // a (FP32)
+    __shared__ float2 tr[kModeTile];      // re, im
+    __shared__ int4 tm[kModeTile];
+    __shared__ double td[F32 ? 1 : kModeTile][5];
+    const int c = blockIdx.x, s = chunk_sys[c];
+    const DevSys &d = sys[s];
+    const int nD = d.nD, a0 = chunk_a0[c], na = chunk_n[c];
+    const ModeCoef *coef = coef_all + (size_t)s * Dcap;
+    constexpr int PER = kChunk / 256;
+    float fx[PER], fy[PER], fz[PER];
+    double gx[PER], gy[PER], gz[PER];
+    uint4 v[PER];
+    double sx[PER], sy[PER], sz[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        fx[u] = fy[u] = fz[u] = 0.f;
+        gx[u] = gy[u] = gz[u] = 0.0;
+        const int k = threadIdx.x + u * 256;
+        if (k < na) {
+            const int i = a0 + k;
+            if (F32) v[u] = su[i];
+            else { sx[u] = r[3 * i] / d.L[0]; sy[u] = r[3 * i + 1] / d.L[1]; sz[u] = r[3 * i + 2] / d.L[2]; }
+        }
+    }
+    for (int t0 = 0; t0 < nD; t0 += kModeTile) {
+        const int nt = min(kModeTile, nD - t0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+            const ModeCoef &mc = coef[t0 + k];
+            if (F32) {
+                tf[k] = make_float4((float)mc.a[0], (float)mc.a[1], (float)mc.a[2], 0.f);
+                tr[k] = make_float2((float)mc.re, (float)mc.im);
+            } else {
+                td[k][0] = mc.a[0]; td[k][1] = mc.a[1]; td[k][2] = mc.a[2];
+                td[k][3] = mc.re; td[k][4] = mc.im;
+            }
+            tm[k] = make_int4(mc.m[0], mc.m[1], mc.m[2], 0);
+        }
+        __syncthreads();
+        for (int k = 0; k < nt; ++k) {
+            const int4 mm = tm[k];
+            const int m[3] = {mm.x, mm.y, mm.z};
+            if (F32) {
+                const float4 a = tf[k];
+                const float2 rr = tr[k];
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    float sn, cs;
+                    phase_sincos_f(m, v[u], sn, cs);
+                    float g = rr.y * cs - rr.x * sn;
+                    fx[u] = fmaf(a.x, g, fx[u]);
+                    fy[u] = fmaf(a.y, g, fy[u]);
+                    fz[u] = fmaf(a.z, g, fz[u]);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    double sn, cs;
+                    phase_sincos_d(m, sx[u], sy[u], sz[u], sn, cs);
+                    double g = td[k][4] * cs - td[k][3] * sn;
+                    gx[u] += td[k][0] * g;
+                    gy[u] += td[k][1] * g;
+                    gz[u] += td[k][2] * g;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int k = threadIdx.x + u * 256;
+        if (k < na) {
+            const int i = a0 + k;
+            const double qi = q[i];
+            if (F32) {
+                F[3 * i] += qi * (double)fx[u];
+                F[3 * i + 1] += qi * (double)fy[u];
+                F[3 * i + 2] += qi * (double)fz[u];
+            } else {
+                F[3 * i] += qi * gx[u];
+                F[3 * i + 1] += qi * gy[u];
+                F[3 * i + 2] += qi * gz[u];
+            }
+        }
+    }
+}
+
+void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
+                     cudaStream_t st)
+{
+    if (precision == 1)
+        k_lr_force<true><<<b.nchunks, 256, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
+                                                   coef, Dcap, a.F);
+    else
+        k_lr_force<false><<<b.nchunks, 256, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
+                                                    coef, Dcap, a.F);
+}
+
+// ---------------------------------------------------------------------------
+// stateless structure factor on caller buffers
+// ---------------------------------------------------------------------------
+__global__ void k_su_from_r(const double *__restrict__ r, const double *__restrict__ q, int n, double L0,
+                            double L1, double L2, uint4 *__restrict__ su)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double L[3] = {L0, L1, L2};
+    unsigned f[3];
+    for (int a = 0; a < 3; ++a) {
+        double s = r[3 * i + a] / L[a];
+        s -= floor(s);
+        if (s >= 1.0) s = 0.0;
+        f[a] = __double2uint_rz(s * 4294967296.0);
+    }
+    su[i] = make_uint4(f[0], f[1], f[2], __float_as_uint((float)q[i]));
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kSkThreads)
+k_sk_stateless(const uint4 *__restrict__ su, const double *__restrict__ r, const double *__restrict__ q,
+               int n, double L0, double L1, double L2, const int *__restrict__ m, int nD,
+               double *__restrict__ part)
+{
+    const int c = blockIdx.x, d0 = blockIdx.y * kModeGroup;
+    if (d0 >= nD) return;
+    const int a0 = c * kChunk, na = min(kChunk, n - a0);
+    const double L[3] = {L0, L1, L2};
+    sk_chunk<F32>(su, r, q, L, a0, na, m, d0, min(kModeGroup, nD - d0), part + ((size_t)c * nD + d0) * 2);
+}
+
+__global__ void k_sk_reduce(const double *__restrict__ part, int nchunks, int nD, double *__restrict__ rho)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * nD) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * nD * 2 + k];
+    rho[k] = s;
+}
+
+size_t sk_stateless_workspace(int n, int nD)
+{
+    const size_t nch = (size_t)(n + kChunk - 1) / kChunk;
+    size_t part = nch * (size_t)nD * 2 * sizeof(double);
+    size_t su = (size_t)n * sizeof(uint4);
+    return ((part + 255) / 256) * 256 + su;
+}
+
+cudaError_t sk_stateless(const double *r, const double *q, int n, const double box[3], const int *m, int nD,
+                         double *rho, void *work, int precision, cudaStream_t st)
+{
+    const int nch = (n + kChunk - 1) / kChunk;
+    double *part = static_cast<double *>(work);
+    size_t part_b = ((nch * (size_t)nD * 2 * sizeof(double) + 255) / 256) * 256;
+    uint4 *su = reinterpret_cast<uint4 *>(static_cast<char *>(work) + part_b);
+    dim3 grid(nch, (nD + kModeGroup - 1) / kModeGroup);
+    if (precision == 1) {
+        k_su_from_r<<<(n + 255) / 256, 256, 0, st>>>(r, q, n, box[0], box[1], box[2], su);
+        k_sk_stateless<true><<<grid, kSkThreads, 0, st>>>(su, r, q, n, box[0], box[1], box[2], m, nD, part);
+    } else {
+        k_sk_stateless<false><<<grid, kSkThreads, 0, st>>>(su, r, q, n, box[0], box[1], box[2], m, nD, part);
+    }
+    k_sk_reduce<<<(2 * nD + 255) / 256, 256, 0, st>>>(part, nch, nD, rho);
+    return cudaGetLastError();
+}
+
+}  // namespace rbsog

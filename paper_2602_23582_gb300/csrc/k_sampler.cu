@@ -1,0 +1,426 @@
+// k_sampler.cu -- Fourier-mode sampling for the random batch (paper sec. 3.2,
+// App. D) and the normalizers S^r, S^nr (eqs. Sr, Snr).  One block per
+// system.  Built with -fmad=false: every accept/reject and rounding decision
+// is made with the same IEEE operations, in the same order, as the CPU oracle,
+// so sampled mode indices agree bit for bit (barring ties within a rounding
+// error of libm vs CUDA transcendentals).
+//
+// Steps (orthorhombic h, k = 2 pi m / L):
+//  1. 1D lattice sums per Gaussian l and axis a (warp-parallel, FP64):
+//     S_n = sum_m m^n e^{-a m^2}, a = (pi s~_l / L_a)^2, |m| <= ceil(sqrt(46/a)) + 2;
+//     T0 = S0, T2 = (2pi/L)^2 S2, T4 = (2pi/L)^4 S4.  H^r_l and H^nr_l are sums
+//     of products of these (e^{-s~^2 k^2/4} factorises over the axes).
+//  2. exact draws from P^r (mixture over (l, axis) with weights c_l T2_a T0 T0)
+//     or P^nr (six components per l), by warp-parallel inverse CDF scans.
+//  3. radial MH chain (App. D): the proposal m* = round(L u), u ~ N(0, 1/(2 pi^2
+//     s~0^2)), depends on no state, so the weights w(m*) = P^r(m*) / q(m*)
+//     (q from eq. proposal, factorised with erf/erfc) of all P proposals are
+//     evaluated in parallel; one thread then runs the accept test
+//     u_t w(x) < w(m*), i.e. u_t < P^r(m*) q(x) / (P^r(x) q(m*)) (eq. acc_Gaussian).
+//  4. recalibration chain (sec. 3.2): proposals are the radial samples;
+//     accept iff u'_t g(y) < g(x_t) with g = P^nr / P^r.
+//  5. distinct modes of the union, lexicographic order, multiplicities.
+#include "internal.h"
+
+namespace rbsog {
+
+namespace {
+
+struct Shared {
+    double T0[kMaxGauss][3], T2[kMaxGauss][3], T4[kMaxGauss][3];
+    double Hr[kMaxGauss], Hnr[kMaxGauss];
+    double Sr, Snr;
+    double L[3];
+    int sel_l, sel_c;
+    int nd;
+};
+
+__device__ int axis_mmax(double a) { return (int)ceil(sqrt(46.0 / a)) + 2; }
+
+// unnormalised targets (eqs. samplingP, samplingPnr)
+__device__ void targets(const SamplerArgs &sa, const double L[3], const int m[3], double &pr, double &pnr)
+{
+    double kx = (kTwoPi * (double)m[0]) / L[0];
+    double ky = (kTwoPi * (double)m[1]) / L[1];
+    double kz = (kTwoPi * (double)m[2]) / L[2];
+    double k2 = kx * kx + ky * ky + kz * kz;
+    double a = 0.0, b = 0.0;
+    for (int l = 0; l < sa.M; ++l) {
+        double e = exp(-(sa.st2q[l] * k2));
+        a += sa.cr[l] * e;
+        b += sa.cn[l] * e;
+    }
+    pr = k2 * a;
+    pnr = (k2 * k2) * b;
+}
+
+__device__ double q1d(int m, double L, double st0)
+{
+    double c = kPi * st0 / L;
+    int am = m < 0 ? -m : m;
+    if (am == 0) return erf(c * 0.5);
+    double lo = c * ((double)am - 0.5), hi = c * ((double)am + 0.5);
+    return 0.5 * (erfc(lo) - erfc(hi));
+}
+
+__device__ double qprop(const SamplerArgs &sa, const double L[3], const int m[3])
+{
+    return q1d(m[0], L[0], sa.st[0]) * q1d(m[1], L[1], sa.st[0]) * q1d(m[2], L[2], sa.st[0]);
+}
+
+// one coordinate from m^{2n} e^{-a m^2}: inverse CDF over m = 0, 1, -1, 2, -2, ...
+// (warp-parallel prefix sums; returns the same m on every lane)
+__device__ int draw_axis_warp(double u, double stl, double L, int n, double total)
+{
+    const int lane = lane_id();
+    double c = kPi * stl / L, a = c * c;
+    int mm = axis_mmax(a);
+    double target = u * total, cum = 0.0;
+    const int kmax = 2 * mm;
+    for (int k0 = 0; k0 <= kmax; k0 += 32) {
+        int k = k0 + lane;
+        int m = (k == 0) ? 0 : ((k & 1) ? (k + 1) / 2 : -(k / 2));
+        double m2 = (double)m * (double)m;
+        double wgt = 0.0;
+        if (k <= kmax) {
+            wgt = exp(-(a * m2));
+            if (n >= 1) wgt *= m2;
+            if (n >= 2) wgt *= m2;
+        }
+        double incl = wgt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        unsigned hit = __ballot_sync(0xffffffffu, k <= kmax && cum + incl > target);
+        if (hit) return __shfl_sync(0xffffffffu, m, __ffs(hit) - 1);
+        cum += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    int k = kmax;
+    return (k == 0) ? 0 : ((k & 1) ? (k + 1) / 2 : -(k / 2));
+}
+
+__device__ double axis_total(const Shared &sh, int l, int a, int n)
+{
+    double g = kTwoPi / sh.L[a];
+    if (n == 0) return sh.T0[l][a];
+    if (n == 1) return sh.T2[l][a] / (g * g);
+    return sh.T4[l][a] / (g * g * g * g);
+}
+
+// exact draw from P^r (nr = false) or P^nr (nr = true) by one warp
+__device__ void exact_draw_warp(const SamplerArgs &sa, Shared &sh, const uint64_t wds[4], bool nr, int m[3])
+{
+    const int lane = lane_id();
+    if (lane == 0) {
+        double tot = 0.0;
+        for (int l = 0; l < sa.M; ++l) tot += nr ? sh.Hnr[l] : sh.Hr[l];
+        double target = u01(wds[0]) * tot, cum = 0.0;
+        int lsel = sa.M - 1, csel = nr ? 5 : 2;
+        bool done = false;
+        for (int l = 0; l < sa.M && !done; ++l) {
+            const double *T0 = sh.T0[l], *T2 = sh.T2[l], *T4 = sh.T4[l];
+            double comp[6];
+            int nc;
+            if (!nr) {
+                comp[0] = sa.cr[l] * T2[0] * T0[1] * T0[2];
+                comp[1] = sa.cr[l] * T0[0] * T2[1] * T0[2];
+                comp[2] = sa.cr[l] * T0[0] * T0[1] * T2[2];
+                nc = 3;
+            } else {
+                comp[0] = sa.cn[l] * T4[0] * T0[1] * T0[2];
+                comp[1] = sa.cn[l] * T0[0] * T4[1] * T0[2];
+                comp[2] = sa.cn[l] * T0[0] * T0[1] * T4[2];
+                comp[3] = 2.0 * sa.cn[l] * T2[0] * T2[1] * T0[2];
+                comp[4] = 2.0 * sa.cn[l] * T2[0] * T0[1] * T2[2];
+                comp[5] = 2.0 * sa.cn[l] * T0[0] * T2[1] * T2[2];
+                nc = 6;
+            }
+            for (int t = 0; t < nc; ++t) {
+                cum += comp[t];
+                if (cum > target) { lsel = l; csel = t; done = true; break; }
+            }
+        }
+        sh.sel_l = lsel;
+        sh.sel_c = csel;
+    }
+    __syncwarp();
+    const int lsel = sh.sel_l, csel = sh.sel_c;
+    __syncwarp();
+    static const int pr_pw[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    static const int pn_pw[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    for (int a = 0; a < 3; ++a) {
+        int n = nr ? pn_pw[csel][a] : pr_pw[csel][a];
+        m[a] = draw_axis_warp(u01(wds[1 + a]), sa.st[lsel], sh.L[a], n, axis_total(sh, lsel, a, n));
+    }
+}
+
+__device__ inline uint64_t mode_key(const int m[3])
+{
+    const uint64_t B = 1u << 20;
+    return ((uint64_t)(m[0] + B) << 42) | ((uint64_t)(m[1] + B) << 21) | (uint64_t)(m[2] + B);
+}
+
+__device__ inline void key_mode(uint64_t k, int m[3])
+{
+    const int B = 1 << 20;
+    m[0] = (int)((k >> 42) & 0x1fffff) - B;
+    m[1] = (int)((k >> 21) & 0x1fffff) - B;
+    m[2] = (int)(k & 0x1fffff) - B;
+}
+
+}  // namespace
+
+// scratch per system: [P] proposal modes (int4) + w, g, u_r, u_nr (double)
+__global__ void __launch_bounds__(256)
+k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__restrict__ mnr_out,
+          int *__restrict__ D_out, int *__restrict__ cr_out, int *__restrict__ cnr_out,
+          int4 *__restrict__ pm, double *__restrict__ pw, double *__restrict__ pg,
+          double *__restrict__ pu, double *__restrict__ pun, int Dcap)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    uint64_t *keys = reinterpret_cast<uint64_t *>(dyn);         // [2 * P2]
+    __shared__ Shared sh;
+    __shared__ int start_m[3], nrstart_m[3];
+    __shared__ double start_w, start_g, nrstart_g;
+    __shared__ int cnt_r, cnt_nr;
+    const int s = blockIdx.x;
+    DevSys &d = sys[s];
+    const uint64_t step = *sa.step + 1;
+    const int P = sa.P, tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
+    int *mr = mr_out + (size_t)s * P * 3, *mnr = mnr_out + (size_t)s * P * 3;
+    int *D = D_out + (size_t)s * Dcap * 3, *cr = cr_out + (size_t)s * Dcap, *cnr = cnr_out + (size_t)s * Dcap;
+    int4 *pm_s = pm + (size_t)s * P;
+    double *pw_s = pw + (size_t)s * P, *pg_s = pg + (size_t)s * P;
+    double *pu_s = pu + (size_t)s * P, *pun_s = pun + (size_t)s * P;
+    if (tid < 3) sh.L[tid] = d.L[tid];
+    __syncthreads();
+
+    // 1. 1D lattice sums
+    for (int idx = warp; idx < 3 * sa.M; idx += nw) {
+        const int l = idx / 3, ax = idx % 3;
+        double c = kPi * sa.st[l] / sh.L[ax], a = c * c;
+        int mm = axis_mmax(a);
+        double s0 = 0.0, s2 = 0.0, s4 = 0.0;
+        for (int m = -mm + lane; m <= mm; m += 32) {
+            double m2 = (double)m * (double)m;
+            double e = exp(-(a * m2));
+            s0 += e; s2 += m2 * e; s4 += m2 * m2 * e;
+        }
+        s0 = warp_sum(s0); s2 = warp_sum(s2); s4 = warp_sum(s4);
+        if (lane == 0) {
+            double g = kTwoPi / sh.L[ax];
+            sh.T0[l][ax] = s0;
+            sh.T2[l][ax] = g * g * s2;
+            sh.T4[l][ax] = g * g * g * g * s4;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double sr = 0.0, snr = 0.0;
+        for (int l = 0; l < sa.M; ++l) {
+            const double *T0 = sh.T0[l], *T2 = sh.T2[l], *T4 = sh.T4[l];
+            sh.Hr[l] = sa.cr[l] * (T2[0] * T0[1] * T0[2] + T0[0] * T2[1] * T0[2] + T0[0] * T0[1] * T2[2]);
+            sh.Hnr[l] = sa.cn[l] * (T4[0] * T0[1] * T0[2] + T0[0] * T4[1] * T0[2] + T0[0] * T0[1] * T4[2]
+                                    + 2.0 * (T2[0] * T2[1] * T0[2] + T2[0] * T0[1] * T2[2] + T0[0] * T2[1] * T2[2]));
+            sr += sh.Hr[l];
+            snr += sh.Hnr[l];
+        }
+        sh.Sr = sr; sh.Snr = snr;
+        d.Sr = sr; d.Snr = snr;
+        cnt_r = 0; cnt_nr = 0;
+    }
+    __syncthreads();
+
+    // 2. exact draws
+    if (sa.kind == 0) {
+        if (warp == 0) {
+            uint64_t wds[4];
+            draw4(sa.seed, d.rng_id, step, PUR_START, 0, wds);
+            int m[3];
+            exact_draw_warp(sa, sh, wds, false, m);
+            if (lane == 0) {
+                double pr, pnr;
+                targets(sa, sh.L, m, pr, pnr);
+                start_m[0] = m[0]; start_m[1] = m[1]; start_m[2] = m[2];
+                start_w = pr / qprop(sa, sh.L, m);
+                start_g = pnr / pr;
+            }
+        }
+    } else {
+        for (int t = warp; t < P; t += nw) {
+            uint64_t wds[4];
+            int m[3];
+            draw4(sa.seed, d.rng_id, step, PUR_START, (uint64_t)t, wds);
+            exact_draw_warp(sa, sh, wds, false, m);
+            if (lane == 0) { mr[3 * t] = m[0]; mr[3 * t + 1] = m[1]; mr[3 * t + 2] = m[2]; }
+            if (sa.kind == 1) {
+                draw4(sa.seed, d.rng_id, step, PUR_NR_IID, (uint64_t)t, wds);
+                exact_draw_warp(sa, sh, wds, true, m);
+                if (lane == 0) { mnr[3 * t] = m[0]; mnr[3 * t + 1] = m[1]; mnr[3 * t + 2] = m[2]; }
+            }
+        }
+        if (sa.kind == 2 && warp == 0) {
+            uint64_t wds[4];
+            int m[3];
+            draw4(sa.seed, d.rng_id, step, PUR_NR_IID, 0, wds);
+            exact_draw_warp(sa, sh, wds, true, m);
+            if (lane == 0) {
+                double pr, pnr;
+                targets(sa, sh.L, m, pr, pnr);
+                nrstart_m[0] = m[0]; nrstart_m[1] = m[1]; nrstart_m[2] = m[2];
+                nrstart_g = pnr / pr;
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. proposal weights (parallel) and uniforms
+    for (int t = tid; t < P; t += blockDim.x) {
+        uint64_t wds[4];
+        int m[3];
+        if (sa.kind == 0) {
+            draw4(sa.seed, d.rng_id, step, PUR_PROPOSAL, (uint64_t)t, wds);
+            double z[3];
+            {
+                double u1 = u01(wds[0]), u2 = u01(wds[1]);
+                double rr = sqrt(-2.0 * log(u1)), ang = kTwoPi * u2;
+                z[0] = rr * cos(ang);
+                z[1] = rr * sin(ang);
+                u1 = u01(wds[2]); u2 = u01(wds[3]);
+                rr = sqrt(-2.0 * log(u1)); ang = kTwoPi * u2;
+                z[2] = rr * cos(ang);
+            }
+            for (int a = 0; a < 3; ++a) m[a] = (int)floor(sh.L[a] * (z[a] * sa.sig_u) + 0.5);
+            double w = 0.0, g = 0.0;
+            if (m[0] || m[1] || m[2]) {
+                double pr, pnr;
+                targets(sa, sh.L, m, pr, pnr);
+                w = pr / qprop(sa, sh.L, m);
+                g = pnr / pr;
+            }
+            pm_s[t] = make_int4(m[0], m[1], m[2], 0);
+            pw_s[t] = w;
+            pg_s[t] = g;
+        } else if (sa.kind == 2) {
+            m[0] = mr[3 * t]; m[1] = mr[3 * t + 1]; m[2] = mr[3 * t + 2];
+            double pr, pnr;
+            targets(sa, sh.L, m, pr, pnr);
+            pg_s[t] = pnr / pr;
+        }
+        draw4(sa.seed, d.rng_id, step, PUR_ACCEPT, (uint64_t)t, wds);
+        pu_s[t] = u01(wds[0]);
+        pun_s[t] = u01(wds[1]);
+    }
+    __syncthreads();
+
+    // 4. chains (one thread)
+    if (tid == 0) {
+        if (sa.kind == 0) {
+            int cur = -1;
+            double wcur = start_w;
+            int nacc = 0;
+            for (int t = 0; t < P; ++t) {
+                if (pu_s[t] * wcur < pw_s[t]) { cur = t; wcur = pw_s[t]; ++nacc; }
+                int4 mm = cur < 0 ? make_int4(start_m[0], start_m[1], start_m[2], 0) : pm_s[cur];
+                mr[3 * t] = mm.x; mr[3 * t + 1] = mm.y; mr[3 * t + 2] = mm.z;
+                pm_s[t].w = cur;              // which proposal (-1: the start) is state t
+            }
+            cnt_r = nacc;
+            // recalibration chain: y_0 = x_1, proposals x_t, g of a state = g of its source
+            int src0 = pm_s[0].w;
+            double gcur = src0 < 0 ? start_g : pg_s[src0];
+            int ym[3] = {mr[0], mr[1], mr[2]};
+            int nn = 0;
+            for (int t = 0; t < P; ++t) {
+                int src = pm_s[t].w;
+                double gt = src < 0 ? start_g : pg_s[src];
+                if (pun_s[t] * gcur < gt) {
+                    ym[0] = mr[3 * t]; ym[1] = mr[3 * t + 1]; ym[2] = mr[3 * t + 2];
+                    gcur = gt;
+                    ++nn;
+                }
+                mnr[3 * t] = ym[0]; mnr[3 * t + 1] = ym[1]; mnr[3 * t + 2] = ym[2];
+            }
+            cnt_nr = nn;
+        } else if (sa.kind == 2) {
+            int ym[3] = {nrstart_m[0], nrstart_m[1], nrstart_m[2]};
+            double gcur = nrstart_g;
+            int nn = 0;
+            for (int t = 0; t < P; ++t) {
+                if (pun_s[t] * gcur < pg_s[t]) {
+                    ym[0] = mr[3 * t]; ym[1] = mr[3 * t + 1]; ym[2] = mr[3 * t + 2];
+                    gcur = pg_s[t];
+                    ++nn;
+                }
+                mnr[3 * t] = ym[0]; mnr[3 * t + 1] = ym[1]; mnr[3 * t + 2] = ym[2];
+            }
+            cnt_nr = nn;
+        }
+    }
+    __syncthreads();
+
+    // 5. distinct modes: sort 2P keys (mode key << 1 | tag), bitonic in shared memory
+    int n2 = 2 * P, p2 = 1;
+    while (p2 < n2) p2 <<= 1;
+    for (int k = tid; k < p2; k += blockDim.x) {
+        uint64_t key = ~0ull;
+        if (k < P) key = (mode_key(mr + 3 * k) << 1);
+        else if (k < n2) key = (mode_key(mnr + 3 * (k - P)) << 1) | 1ull;
+        keys[k] = key;
+    }
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < p2 / 2; t += blockDim.x) {
+                int lo = 2 * j * (t / j) + (t % j), hi = lo + j;
+                bool up = (lo & k) == 0;
+                uint64_t x = keys[lo], y = keys[hi];
+                if ((x > y) == up) { keys[lo] = y; keys[hi] = x; }
+            }
+            __syncthreads();
+        }
+    }
+    // segment heads and compaction (one thread: at most 2P <= 8192 keys)
+    if (tid == 0) {
+        int nd = -1;
+        uint64_t prev = ~0ull;
+        for (int k = 0; k < n2; ++k) {
+            uint64_t mk = keys[k] >> 1;
+            if (mk != prev) {
+                ++nd;
+                int m[3];
+                key_mode(mk, m);
+                D[3 * nd] = m[0]; D[3 * nd + 1] = m[1]; D[3 * nd + 2] = m[2];
+                cr[nd] = 0; cnr[nd] = 0;
+                prev = mk;
+            }
+            if (keys[k] & 1ull) cnr[nd] += 1; else cr[nd] += 1;
+        }
+        d.nD = nd + 1;
+        d.nacc_r = cnt_r;
+        d.nacc_nr = cnt_nr;
+    }
+}
+
+static size_t sampler_smem(int P)
+{
+    int p2 = 1;
+    while (p2 < 2 * P) p2 <<= 1;
+    return (size_t)p2 * sizeof(uint64_t);
+}
+
+cudaError_t prepare_sampler(int P)
+{
+    return cudaFuncSetAttribute(k_sampler, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sampler_smem(P));
+}
+
+void launch_sampler(const Batch &b, const SamplerArgs &sa, int *mr, int *mnr, int *D, int *cr,
+                    int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, int Dcap,
+                    cudaStream_t st)
+{
+    k_sampler<<<b.S, 256, sampler_smem(sa.P), st>>>(b.sys, sa, mr, mnr, D, cr, cnr, pm, pw, pg, pu, pun, Dcap);
+}
+
+}  // namespace rbsog

@@ -1,0 +1,363 @@
+"""Thin ctypes binding of ``include/rbsog.h`` (argument marshalling only).
+
+Every computation runs in ``librbsog.so`` (hand-written sm_103a kernels).  If
+the library is missing this module raises: there is no CPU fallback.
+
+Functions keep the C names; ``Context`` is a small convenience holder that
+keeps the host arrays of a ``rbsog_create`` call alive and converts results
+to numpy.  Device buffers may be passed as torch CUDA tensors (their
+``data_ptr()`` is forwarded) -- PyTorch serves as device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbsog.so")
+
+RBSOG_OK = 0
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EBOX", -4: "ENONFINITE", -5: "EUNSUPPORTED",
+          -6: "ETIMEOUT", -7: "ECUDA", -8: "EOVERFLOW"}
+RBSOG_SAMPLER_PAPER, RBSOG_SAMPLER_IID, RBSOG_SAMPLER_IID_RECAL = 0, 1, 2
+RBSOG_FP64, RBSOG_FP32 = 0, 1
+RBSOG_COUPLE_ISO, RBSOG_COUPLE_SEMI_ISO, RBSOG_COUPLE_FIXED = 0, 1, 2
+E_NAMES = ("coul_short", "coul_long", "coul_self", "coul_excl", "lj", "bond", "angle", "coul", "kinetic")
+
+EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_error", "rbsog_n_atoms",
+           "rbsog_system_range", "rbsog_set_box", "rbsog_set_positions", "rbsog_get_positions",
+           "rbsog_get_velocities", "rbsog_step", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
+           "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_set_timing", "rbsog_get_timing",
+           "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
+           "rbsog_sync", "rbsog_stream")
+
+
+class RbsogError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"rbsog status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class rbsog_params(C.Structure):
+    _fields_ = [("rc", C.c_double), ("b", C.c_double), ("sigma", C.c_double), ("omega", C.c_double),
+                ("M", C.c_int), ("M_energy", C.c_int), ("P", C.c_int), ("sampler", C.c_int),
+                ("seed", C.c_uint64), ("precision", C.c_int), ("ke", C.c_double),
+                ("dt", C.c_double), ("T", C.c_double), ("P_ext", C.c_double), ("gamma", C.c_double),
+                ("gamma_box", C.c_double), ("tau_box", C.c_double), ("compressibility", C.c_double),
+                ("coupling", C.c_int), ("cell_sub", C.c_int)]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+class rbsog_system_desc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("q", _D), ("mass", _D), ("type", _I), ("mol", _I),
+                ("ntypes", C.c_int), ("lj_eps", _D), ("lj_sig", _D),
+                ("n_bonds", C.c_int), ("bonds", _I), ("bond_k", _D), ("bond_r0", _D),
+                ("n_angles", C.c_int), ("angles", _I), ("angle_k", _D), ("angle_t0", _D),
+                ("n_excl", C.c_int), ("excl", _I), ("r0", _D), ("v0", _D), ("box", C.c_double * 3),
+                ("rng_id", C.c_uint64)]
+
+
+class rbsog_result(C.Structure):
+    _fields_ = [("energy", C.c_double * 9), ("virial", C.c_double * 9),
+                ("virial_coul_short", C.c_double * 9), ("virial_long_r", C.c_double * 9),
+                ("virial_long_nr", C.c_double * 9), ("virial_lj", C.c_double * 9),
+                ("virial_bonded", C.c_double * 9), ("pressure", C.c_double * 9),
+                ("box", C.c_double * 3), ("volume", C.c_double), ("n_distinct_modes", C.c_int),
+                ("n_accept_r", C.c_int), ("n_accept_nr", C.c_int), ("step", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load librbsog.so (building it first if a source is newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2602_23582_gb300/build.py")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.rbsog_default_params.argtypes = [C.POINTER(rbsog_params), C.c_double]
+    L.rbsog_default_params.restype = None
+    L.rbsog_create.argtypes = [C.POINTER(rbsog_params), C.c_int, C.POINTER(rbsog_system_desc), P, C.POINTER(P)]
+    L.rbsog_destroy.argtypes = [P]
+    L.rbsog_destroy.restype = None
+    L.rbsog_last_error.argtypes = [P]
+    L.rbsog_last_error.restype = C.c_char_p
+    L.rbsog_n_atoms.argtypes = [P]
+    L.rbsog_system_range.argtypes = [P, C.c_int, _I, _I]
+    L.rbsog_set_box.argtypes = [P, C.c_int, _D, C.c_int]
+    L.rbsog_set_positions.argtypes = [P, P, C.c_int]
+    L.rbsog_get_positions.argtypes = [P, P, C.c_int]
+    L.rbsog_get_velocities.argtypes = [P, P, C.c_int]
+    L.rbsog_step.argtypes = [P, C.c_uint64, P, C.c_int, C.POINTER(rbsog_result)]
+    L.rbsog_run.argtypes = [P, C.c_int, C.POINTER(rbsog_result)]
+    L.rbsog_run_async.argtypes = [P, C.c_int]
+    L.rbsog_sync.argtypes = [P]
+    L.rbsog_stream.argtypes = [P]
+    L.rbsog_stream.restype = C.c_void_p
+    L.rbsog_get_state.argtypes = [P, P, C.POINTER(C.c_size_t)]
+    L.rbsog_set_state.argtypes = [P, P, C.c_size_t]
+    L.rbsog_debug_cells.argtypes = [P, C.c_int, _I, _I]
+    L.rbsog_debug_modes.argtypes = [P, C.c_int, _I, _I, _I, _I, _I, _I, _D, _D]
+    L.rbsog_set_timing.argtypes = [P, C.c_int]
+    L.rbsog_get_timing.argtypes = [P, C.c_int, C.c_char_p, _D, _I]
+    L.rbsog_structure_factor_workspace.argtypes = [C.c_int, C.c_int]
+    L.rbsog_structure_factor_workspace.restype = C.c_size_t
+    L.rbsog_structure_factor.argtypes = [P, P, C.c_int, _D, P, C.c_int, P, P, C.c_int, P]
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != RBSOG_OK:
+        msg = lib().rbsog_last_error(ctx).decode() if ctx else ""
+        raise RbsogError(status, msg)
+
+
+def _ptr(x):
+    """Pointer of a numpy array (host) or a torch CUDA tensor (device)."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        return C.c_void_p(x.data_ptr()), int(bool(x.is_cuda))
+    return x.ctypes.data_as(C.c_void_p), 0
+
+
+def rbsog_default_params(rc=10.0, **kw) -> rbsog_params:
+    p = rbsog_params()
+    lib().rbsog_default_params(C.byref(p), rc)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _desc(sys, hold, index):
+    def d(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        hold.append(a)
+        return a.ctypes.data_as(_D)
+
+    def i(a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        hold.append(a)
+        return a.ctypes.data_as(_I)
+    v0 = getattr(sys, "vel", None)
+    desc = rbsog_system_desc()
+    desc.n_atoms = sys.n
+    desc.q, desc.mass, desc.type, desc.mol = d(sys.q), d(sys.mass), i(sys.type), i(sys.mol)
+    desc.ntypes = sys.ntypes
+    desc.lj_eps, desc.lj_sig = d(sys.lj_eps), d(sys.lj_sig)
+    desc.n_bonds = len(sys.bonds)
+    desc.bonds, desc.bond_k, desc.bond_r0 = i(sys.bonds), d(sys.bond_k), d(sys.bond_r0)
+    desc.n_angles = len(sys.angles)
+    desc.angles, desc.angle_k, desc.angle_t0 = i(sys.angles), d(sys.angle_k), d(sys.angle_t0)
+    desc.n_excl = len(sys.excl)
+    desc.excl = i(sys.excl)
+    desc.r0 = d(sys.pos)
+    desc.v0 = d(v0) if v0 is not None else None
+    for a in range(3):
+        desc.box[a] = float(sys.box[a])
+    desc.rng_id = int(getattr(sys, "rng_id", index))
+    return desc
+
+
+def rbsog_create(params: rbsog_params, systems, stream=None):
+    """Create a context over a list of systems (duck-typed: pos, q, mass,
+    type, mol, box, lj_eps, lj_sig, bonds, bond_k, bond_r0, angles, angle_k,
+    angle_t0, excl; optional vel and rng_id -- the Philox key word, default
+    the system's index).  Returns the opaque context pointer."""
+    hold = []
+    arr = (rbsog_system_desc * len(systems))()
+    for k, s in enumerate(systems):
+        arr[k] = _desc(s, hold, k)
+    ctx = C.c_void_p()
+    st = C.c_void_p(stream) if stream else None
+    status = lib().rbsog_create(C.byref(params), len(systems), arr, st, C.byref(ctx))
+    if status != RBSOG_OK:
+        raise RbsogError(status, "rbsog_create")
+    return ctx
+
+
+def rbsog_destroy(ctx):
+    lib().rbsog_destroy(ctx)
+
+
+def rbsog_step(ctx, step, forces=None, results=None):
+    p, dev = _ptr(forces)
+    _check(lib().rbsog_step(ctx, step, p, dev, results), ctx)
+
+
+def rbsog_run(ctx, nsteps, results=None):
+    _check(lib().rbsog_run(ctx, nsteps, results), ctx)
+
+
+def rbsog_run_async(ctx, nsteps):
+    _check(lib().rbsog_run_async(ctx, nsteps), ctx)
+
+
+def rbsog_sync(ctx):
+    _check(lib().rbsog_sync(ctx), ctx)
+
+
+def rbsog_stream(ctx):
+    return lib().rbsog_stream(ctx)
+
+
+def rbsog_set_positions(ctx, r):
+    p, dev = _ptr(r)
+    _check(lib().rbsog_set_positions(ctx, p, dev), ctx)
+
+
+def rbsog_get_positions(ctx, r):
+    p, dev = _ptr(r)
+    _check(lib().rbsog_get_positions(ctx, p, dev), ctx)
+
+
+def rbsog_get_velocities(ctx, v):
+    p, dev = _ptr(v)
+    _check(lib().rbsog_get_velocities(ctx, p, dev), ctx)
+
+
+def rbsog_set_box(ctx, s, box, rescale=False):
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    _check(lib().rbsog_set_box(ctx, s, b, int(rescale)), ctx)
+
+
+def rbsog_get_state(ctx) -> bytes:
+    n = C.c_size_t()
+    _check(lib().rbsog_get_state(ctx, None, C.byref(n)), ctx)
+    buf = (C.c_char * n.value)()
+    _check(lib().rbsog_get_state(ctx, buf, C.byref(n)), ctx)
+    return bytes(buf)
+
+
+def rbsog_set_state(ctx, state: bytes):
+    buf = (C.c_char * len(state)).from_buffer_copy(state)
+    _check(lib().rbsog_set_state(ctx, buf, len(state)), ctx)
+
+
+def rbsog_debug_cells(ctx, s, n_atoms):
+    nc = np.zeros(3, np.int32)
+    cell = np.zeros(n_atoms, np.int32)
+    _check(lib().rbsog_debug_cells(ctx, s, nc.ctypes.data_as(_I), cell.ctypes.data_as(_I)), ctx)
+    return nc, cell
+
+
+def rbsog_debug_modes(ctx, s, P, Dcap):
+    mr, mnr = np.zeros((P, 3), np.int32), np.zeros((P, 3), np.int32)
+    D, cr, cnr = np.zeros((Dcap, 3), np.int32), np.zeros(Dcap, np.int32), np.zeros(Dcap, np.int32)
+    nD = C.c_int()
+    S2 = np.zeros(2)
+    rho = np.zeros(2 * Dcap)
+    _check(lib().rbsog_debug_modes(ctx, s, mr.ctypes.data_as(_I), mnr.ctypes.data_as(_I),
+                                   D.ctypes.data_as(_I), cr.ctypes.data_as(_I), cnr.ctypes.data_as(_I),
+                                   C.byref(nD), S2.ctypes.data_as(_D), rho.ctypes.data_as(_D)), ctx)
+    n = nD.value
+    return dict(mr=mr, mnr=mnr, D=D[:n].copy(), cr=cr[:n].copy(), cnr=cnr[:n].copy(), Sr=S2[0],
+                Snr=S2[1], rho=rho[0:2 * n:2] + 1j * rho[1:2 * n:2])
+
+
+def rbsog_set_timing(ctx, enable=True):
+    _check(lib().rbsog_set_timing(ctx, int(enable)), ctx)
+
+
+def rbsog_get_timing(ctx, max_n=64):
+    names = C.create_string_buffer(32 * max_n)
+    ms = np.zeros(max_n)
+    n = C.c_int()
+    _check(lib().rbsog_get_timing(ctx, max_n, names, ms.ctypes.data_as(_D), C.byref(n)), ctx)
+    raw = names.raw
+    return [(raw[32 * k:32 * k + 32].split(b"\0")[0].decode(), ms[k]) for k in range(n.value)]
+
+
+def rbsog_structure_factor_workspace(n_atoms, nD):
+    return lib().rbsog_structure_factor_workspace(n_atoms, nD)
+
+
+def rbsog_structure_factor(r, q, box, m, rho, work, precision=RBSOG_FP32, stream=None):
+    """r, q, m, rho, work: torch CUDA tensors (device buffers)."""
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    st = C.c_void_p(stream) if stream else None
+    status = lib().rbsog_structure_factor(C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()), int(q.numel()),
+                                          b, C.c_void_p(m.data_ptr()), int(m.shape[0]),
+                                          C.c_void_p(rho.data_ptr()), C.c_void_p(work.data_ptr()),
+                                          precision, st)
+    if status != RBSOG_OK:
+        raise RbsogError(status, "rbsog_structure_factor")
+
+
+def result_dict(r: rbsog_result) -> dict:
+    """rbsog_result -> numpy/dict (energies by name, 3x3 tensors)."""
+    def t(x):
+        return np.array(x[:]).reshape(3, 3)
+    out = {k: r.energy[i] for i, k in enumerate(E_NAMES)}
+    out.update(virial=t(r.virial), virial_coul_short=t(r.virial_coul_short),
+               virial_long_r=t(r.virial_long_r), virial_long_nr=t(r.virial_long_nr),
+               virial_lj=t(r.virial_lj), virial_bonded=t(r.virial_bonded), pressure=t(r.pressure),
+               box=np.array(r.box[:]), volume=r.volume, n_distinct_modes=r.n_distinct_modes,
+               n_accept_r=r.n_accept_r, n_accept_nr=r.n_accept_nr, step=r.step)
+    return out
+
+
+class Context:
+    """Owner of one rbsog context (n systems)."""
+
+    def __init__(self, systems, params: rbsog_params | None = None, stream=None, **kw):
+        self.params = params if params is not None else rbsog_default_params(**kw)
+        self.systems = list(systems)
+        self.ctx = rbsog_create(self.params, self.systems, stream)
+        self.n_atoms = lib().rbsog_n_atoms(self.ctx)
+        self.S = len(self.systems)
+        self.Dcap = 2 * self.params.P if self.params.sampler == RBSOG_SAMPLER_IID else self.params.P + 1
+
+    def close(self):
+        if self.ctx:
+            rbsog_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, step, forces=None):
+        res = (rbsog_result * self.S)()
+        if forces is None:
+            forces = np.zeros((self.n_atoms, 3))
+        rbsog_step(self.ctx, step, forces, res)
+        return forces, [result_dict(res[k]) for k in range(self.S)]
+
+    def run(self, nsteps):
+        res = (rbsog_result * self.S)()
+        rbsog_run(self.ctx, nsteps, res)
+        return [result_dict(res[k]) for k in range(self.S)]
+
+    def positions(self):
+        r = np.zeros((self.n_atoms, 3))
+        rbsog_get_positions(self.ctx, r)
+        return r
+
+    def velocities(self):
+        v = np.zeros((self.n_atoms, 3))
+        rbsog_get_velocities(self.ctx, v)
+        return v
+
+    def set_positions(self, r):
+        rbsog_set_positions(self.ctx, np.ascontiguousarray(r, dtype=np.float64))
+
+    def cells(self, s=0):
+        return rbsog_debug_cells(self.ctx, s, self.systems[s].n)
+
+    def modes(self, s=0):
+        return rbsog_debug_modes(self.ctx, s, self.params.P, self.Dcap)

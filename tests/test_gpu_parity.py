@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+identical seeded inputs and identical Philox counters.
+
+Bars (from the contract of this build):
+* cell membership and sampled mode indices: bit-exact;
+* FP64 build: forces, virial/pressure and energies within 1e-10 relative;
+* FP32 build (FP32 math, FP64 accumulation): forces within 1e-5 relative RMS,
+  pressure tensor (Frobenius) and energies within 1e-6 relative;
+* batched path: each system bit-identical alone and in a mix.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2602_23582_gb300 import rbsog as R  # noqa: E402
+
+
+def _ctx(systems, prec, **kw):
+    p = R.rbsog_default_params(kw.pop("rc", 10.0), precision=prec, **kw)
+    return R.Context(systems, p), p
+
+
+def _oracle_params(p, sysid=0):
+    # the binding keys system k with rng_id = k unless the system sets one
+    return O.Params(rc=p.rc, b=p.b, sigma=p.sigma, omega=p.omega, ke=p.ke, M=p.M, ME=p.M_energy,
+                    P=p.P, kind=p.sampler, seed=int(p.seed), sysid=sysid)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+SYSTEMS = {
+    "electrolyte": lambda: W.electrolyte(n_ions=1000, L=30.0, seed=1),
+    "water_small": lambda: W.water(n_mol=1200, L=33.0, lattice=11, seed=2),
+    "ragged": lambda: W.random_charges(n=1333, box=(31.0, 34.5, 40.25), seed=5, min_dist=1.6, lj=True),
+}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("sub", [1, 2])
+def test_cells_bit_exact(name, sub):
+    s = SYSTEMS[name]()
+    ctx, p = _ctx([s], R.RBSOG_FP64, cell_sub=sub)
+    nc, cell = ctx.cells(0)
+    onc, ocell = O.cell_bin(s.pos, s.box, p.rc, sub)
+    assert np.array_equal(nc, onc)
+    assert np.array_equal(cell, ocell)
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("box", [(30.0, 30.0, 30.0), (31.0, 44.0, 66.88), (110.85, 110.85, 110.85)])
+def test_modes_bit_exact(kind, box):
+    s = W.random_charges(n=64, box=box, seed=3, min_dist=1.5)
+    ctx, p = _ctx([s], R.RBSOG_FP64, sampler=kind, P=100)
+    op = _oracle_params(p)
+    for step in (1, 2, 17):
+        ctx.step(step)
+        g = ctx.modes(0)
+        mr, mn, _ = O.sample_modes(s.box, op, step)
+        assert np.array_equal(g["mr"], mr), (kind, box, step)
+        assert np.array_equal(g["mnr"], mn), (kind, box, step)
+        D, cr, cnr = O.distinct(mr, mn)
+        assert np.array_equal(g["D"], D) and np.array_equal(g["cr"], cr) and np.array_equal(g["cnr"], cnr)
+        w, sg, wt, st = O.sog_terms(p.b, p.sigma, p.omega, p.M)
+        Hr, Hnr, *_ = O.normalizers(s.box, wt, st)
+        assert abs(g["Sr"] - Hr.sum()) < 1e-13 * Hr.sum()
+        assert abs(g["Snr"] - Hnr.sum()) < 1e-13 * Hnr.sum()
+    ctx.close()
+
+
+def _compare_eval(s, prec, step=5, **kw):
+    ctx, p = _ctx([s], prec, **kw)
+    F, res = ctx.step(step)
+    ref = O.force_eval(s, _oracle_params(p), step)
+    r = res[0]
+    ctx.close()
+    return F, r, ref
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_eval_fp64_matches_oracle(name):
+    s = SYSTEMS[name]()
+    F, r, ref = _compare_eval(s, R.RBSOG_FP64)
+    assert _rel(F, ref["F"]) < 1e-10
+    assert _rel(r["virial"], ref["W"]) < 1e-10
+    assert _rel(r["virial_coul_short"], ref["W_parts"][0]) < 1e-10
+    assert _rel(r["virial_long_r"], ref["W_parts"][1]) < 1e-10
+    assert _rel(r["virial_long_nr"], ref["W_parts"][2]) < 1e-10
+    for k in ("coul_short", "coul_long", "coul_self", "lj", "bond", "angle"):
+        assert abs(r[k] - ref[k]) <= 1e-10 * max(abs(ref[k]), 1.0), k
+    assert abs(r["coul"] - ref["coul"]) <= 1e-10 * abs(ref["coul"])
+    assert r["n_distinct_modes"] == int(ref["n_distinct"])
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_eval_fp32_matches_oracle(name):
+    s = SYSTEMS[name]()
+    F, r, ref = _compare_eval(s, R.RBSOG_FP32)
+    V = float(np.prod(s.box))
+    assert _rel(F, ref["F"]) < 1e-5
+    P_gpu = r["virial"] / V
+    P_ref = ref["W"] / V
+    assert _rel(P_gpu, P_ref) < 1e-6
+    assert abs(r["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
+    assert abs(r["lj"] - ref["lj"]) <= 1e-6 * max(abs(ref["lj"]), 1.0)
+
+
+def test_eval_fp32_full_water_box():
+    # the benchmark workload (10,000 molecules, 30,000 sites) at full size
+    s = W.water()
+    ctx, p = _ctx([s], R.RBSOG_FP32)
+    F, res = ctx.step(11)
+    ref = O.force_eval(s, _oracle_params(p), 11)
+    ctx.close()
+    assert _rel(F, ref["F"]) < 1e-5
+    assert _rel(res[0]["virial"], ref["W"]) < 1e-6
+    assert abs(res[0]["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
+
+
+def test_npt_fp64_trajectory_matches_oracle():
+    s = W.electrolyte(n_ions=300, L=30.0, seed=9)
+    rng = np.random.default_rng(0)
+    s.vel = rng.normal(size=s.pos.shape) * np.sqrt(O.KB * 300.0 * O.FTM2V / s.mass[:, None])
+    ctx, p = _ctx([s], R.RBSOG_FP64, P=50, dt=1.0)
+    op = _oracle_params(p)
+    # oracle state after the priming evaluation at counter 0
+    out0 = O.force_eval(s, op, 0)
+    st = dict(r=s.pos.copy(), p=s.vel * s.mass[:, None], L=s.box.copy(), ph=np.zeros(3),
+              F=out0["F"], W=out0["W"].reshape(-1).copy())
+    # box mass as the library sets it (isotropic group)
+    kap = p.compressibility * O.NKTV2P
+    om = 2 * np.pi / p.tau_box
+    Mb = 9.0 * np.prod(s.box) * O.FTM2V / (kap * s.box[0] ** 2 * om ** 2)
+    ig = O.Integ(dt=p.dt, T=p.T, Pext_atm=p.P_ext, gamma=p.gamma, gamma_box=p.gamma_box,
+                 coupling=0, Mbox=(Mb, 0.0, 0.0))
+    res = ctx.run(5)
+    O.npt_run(s, op, ig, st, 0, 5)
+    r_gpu = ctx.positions()
+    v_gpu = ctx.velocities()
+    assert np.allclose(res[0]["box"], st["L"], rtol=1e-11, atol=0)
+    d = r_gpu - st["r"]
+    d -= st["L"] * np.rint(d / st["L"])
+    assert np.abs(d).max() < 1e-8
+    assert _rel(v_gpu * s.mass[:, None], st["p"]) < 1e-8
+    ctx.close()
+
+
+def test_batched_alone_equals_mixed():
+    systems = [W.electrolyte(n_ions=600, L=31.0, seed=11), W.water(n_mol=1500, L=36.0, lattice=12, seed=12),
+               W.random_charges(n=777, box=(32.0, 35.0, 38.0), seed=13, min_dist=1.6, lj=True)]
+    for k, s in enumerate(systems):
+        s.rng_id = 100 + k
+    for prec in (R.RBSOG_FP32, R.RBSOG_FP64):
+        mix, p = _ctx(systems, prec)
+        Fm, rm = mix.step(4)
+        rr = mix.run(3)
+        pos_m = mix.positions()
+        mix.close()
+        off = 0
+        for k, s in enumerate(systems):
+            alone, _ = _ctx([s], prec)
+            Fa, ra = alone.step(4)
+            assert np.array_equal(Fa, Fm[off:off + s.n]), (prec, k)
+            for key in ("coul", "lj", "bond", "angle"):
+                assert ra[0][key] == rm[k][key], (prec, k, key)
+            assert np.array_equal(ra[0]["virial"], rm[k]["virial"]), (prec, k)
+            ra2 = alone.run(3)
+            assert np.array_equal(alone.positions(), pos_m[off:off + s.n]), (prec, k)
+            assert np.array_equal(ra2[0]["pressure"], rr[k]["pressure"]), (prec, k)
+            alone.close()
+            off += s.n
+
+
+def test_structure_factor_stateless():
+    s = W.water(n_mol=3000, L=45.0, lattice=15, seed=21)
+    rng = np.random.default_rng(2)
+    m = rng.integers(-9, 10, size=(57, 3)).astype(np.int32)
+    m[np.all(m == 0, axis=1)] = [1, 0, 0]
+    ref = O.rho(s.pos, s.q, s.box, m)
+    dev = torch.device("cuda:0")
+    r = torch.tensor(s.pos, device=dev)
+    q = torch.tensor(s.q, device=dev)
+    mt = torch.tensor(m, device=dev)
+    for prec, tol in ((R.RBSOG_FP64, 1e-11), (R.RBSOG_FP32, 2e-6)):
+        rho = torch.zeros(2 * len(m), dtype=torch.float64, device=dev)
+        nb = R.rbsog_structure_factor_workspace(s.n, len(m))
+        work = torch.zeros(nb, dtype=torch.uint8, device=dev)
+        R.rbsog_structure_factor(r, q, s.box, mt, rho, work, precision=prec)
+        torch.cuda.synchronize()
+        g = rho.cpu().numpy()
+        g = g[0::2] + 1j * g[1::2]
+        scale = np.abs(s.q).sum()
+        assert np.abs(g - ref).max() < tol * scale, prec
+
+
+def test_box_too_small_is_rejected():
+    s = W.random_charges(n=50, box=(25.0, 30.0, 30.0), seed=1)
+    p = R.rbsog_default_params(10.0)
+    with pytest.raises(R.RbsogError) as e:
+        R.Context([s], p)
+    assert e.value.status == -3
+
+
+def test_checkpoint_resume_is_bit_identical():
+    s = W.electrolyte(n_ions=500, L=30.0, seed=4)
+    ctx, p = _ctx([s], R.RBSOG_FP32, P=64)
+    ctx.run(3)
+    state = R.rbsog_get_state(ctx.ctx)
+    ctx.run(4)
+    a = ctx.positions()
+    R.rbsog_set_state(ctx.ctx, state)
+    ctx.run(4)
+    b = ctx.positions()
+    ctx.close()
+    assert np.array_equal(a, b)
+
+
+def test_run_is_deterministic():
+    s = W.water(n_mol=1200, L=33.0, lattice=11, seed=2)
+    out = []
+    for _ in range(2):
+        ctx, p = _ctx([s], R.RBSOG_FP32)
+        ctx.run(5)
+        out.append(ctx.positions())
+        ctx.close()
+    assert np.array_equal(out[0], out[1])
