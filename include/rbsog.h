@@ -173,6 +173,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems,
 
 void rbsog_destroy(rbsog_ctx *ctx);
 
+/* Text of the last error of ctx; with ctx == NULL, of the calling thread's
+ * last failed rbsog_create. */
 const char *rbsog_last_error(const rbsog_ctx *ctx);
 
 /* Total atoms of all systems, and atom offset / count of system s. */

@@ -238,12 +238,16 @@ __global__ void k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict
                                     ++tail;
                                 }
                             }
+                            // rounds in which every lane holding an atom has a hit queued;
+                            // lanes without an atom have nothing queued and sit them out
                             int pend = tail - head;
                             int mn = __reduce_min_sync(0xffffffffu, vi ? pend : QCAP);
                             for (int t = 0; t < mn; ++t) {
-                                unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                ++head;
-                                pair_eval_f<NG>(pc, pi.x, pi.y, pi.z, pq.x, ti, Jp[j], Jq[j], acc);
+                                if (vi) {
+                                    unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
+                                    ++head;
+                                    pair_eval_f<NG>(pc, pi.x, pi.y, pi.z, pq.x, ti, Jp[j], Jq[j], acc);
+                                }
                             }
                             while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
                                 if (tail > head) {
@@ -382,9 +386,11 @@ __global__ void k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict
                             int pend = tail - head;
                             int mn = __reduce_min_sync(0xffffffffu, vi ? pend : QCAP);
                             for (int t = 0; t < mn; ++t) {
-                                unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                ++head;
-                                pair_eval_d(pc, pi.x, pi.y, pi.z, pi.w, ai.y, Jp[j], Ja[j].y, acc);
+                                if (vi) {
+                                    unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
+                                    ++head;
+                                    pair_eval_d(pc, pi.x, pi.y, pi.z, pi.w, ai.y, Jp[j], Ja[j].y, acc);
+                                }
                             }
                             while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
                                 if (tail > head) {

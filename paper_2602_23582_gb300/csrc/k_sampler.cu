@@ -31,7 +31,7 @@ struct Shared {
     double Hr[kMaxGauss], Hnr[kMaxGauss];
     double Sr, Snr;
     double L[3];
-    int sel_l, sel_c;
+    int sel_l[8], sel_c[8];   // per warp (256-thread blocks)
     int nd;
 };
 
@@ -142,11 +142,11 @@ __device__ void exact_draw_warp(const SamplerArgs &sa, Shared &sh, const uint64_
                 if (cum > target) { lsel = l; csel = t; done = true; break; }
             }
         }
-        sh.sel_l = lsel;
-        sh.sel_c = csel;
+        sh.sel_l[threadIdx.x >> 5] = lsel;
+        sh.sel_c[threadIdx.x >> 5] = csel;
     }
     __syncwarp();
-    const int lsel = sh.sel_l, csel = sh.sel_c;
+    const int lsel = sh.sel_l[threadIdx.x >> 5], csel = sh.sel_c[threadIdx.x >> 5];
     __syncwarp();
     static const int pr_pw[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     static const int pn_pw[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};

@@ -86,9 +86,12 @@ struct rbsog_ctx {
 
 namespace {
 
+thread_local std::string g_create_err;   // error text of a failed rbsog_create
+
 rbsog_status fail(rbsog_ctx *c, rbsog_status s, const std::string &msg)
 {
     if (c) c->err = msg;
+    g_create_err = msg;
     return s;
 }
 
@@ -303,7 +306,7 @@ void rbsog_default_params(rbsog_params *p, double rc)
     p->cell_sub = 1;
 }
 
-const char *rbsog_last_error(const rbsog_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char *rbsog_last_error(const rbsog_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
 int rbsog_n_atoms(const rbsog_ctx *ctx) { return ctx ? ctx->N : 0; }
 

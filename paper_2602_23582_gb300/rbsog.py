@@ -184,7 +184,7 @@ def rbsog_create(params: rbsog_params, systems, stream=None):
     st = C.c_void_p(stream) if stream else None
     status = lib().rbsog_create(C.byref(params), len(systems), arr, st, C.byref(ctx))
     if status != RBSOG_OK:
-        raise RbsogError(status, "rbsog_create")
+        raise RbsogError(status, "rbsog_create: " + lib().rbsog_last_error(None).decode())
     return ctx
 
 
