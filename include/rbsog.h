@@ -27,7 +27,7 @@
  *   - Arrays of atoms are row-major N x 3 FP64 unless stated; atoms of all
  *     systems of a context are concatenated in system order.
  *   - The cell h is orthorhombic: box[3] are its edge lengths.  A box edge
- *     shorter than 3 r_c is rejected (RBSOG_EBOX).
+ *     shorter than (2 cell_sub + 1) r_c / cell_sub is rejected (RBSOG_EBOX).
  *   - Results depend only on (inputs, seed, rng_id, step): Philox4x64-10
  *     counters (step, purpose, index) under the key (seed, rng_id).
  */
@@ -95,7 +95,8 @@ typedef struct {
     double tau_box;         /* fs, barostat period used to set the box mass */
     double compressibility; /* 1/atm, used to set the box mass */
     int coupling;           /* RBSOG_COUPLE_* */
-    int cell_sub;           /* cells per cutoff length along an axis: 1 or 2 */
+    int cell_sub;           /* cells per cutoff length along an axis: 1 or 2; 0 = choose
+                               (2 when a box edge is below 3.3 r_c, else 1) */
 } rbsog_params;
 
 typedef struct {

@@ -6,6 +6,7 @@
 //     float4/double4), su (fixed-point fractional coordinates + charge, uint4).
 //   per cell (global index = cell0 of the system + local index, x fastest):
 //     count, start; cell-sorted copies pos4 / posd, qt / aux, sidx.
+//   pair work items (cell, 32-atom group), per system in [item0, item0 + item_cap).
 //   per system: DevSys (box, box momenta, cell grid, normalizers, flags).
 #pragma once
 #include <cstdint>
@@ -19,6 +20,7 @@ constexpr int kMaxGauss = 64;      // Gaussians of the split, M and M_energy
 constexpr int kMaxP = 4096;        // batch size
 constexpr int kCellCap = 2048;     // atoms per cell the kernels accept
 constexpr int kChunk = 1024;       // atoms per chunk of the per-atom kernels
+constexpr int kMolChunk = 64;      // molecules per block of the molecule kernel
 constexpr int kMaxTypes = 16;
 
 // status flags written by kernels (bit mask in DevSys::flags)
@@ -47,6 +49,8 @@ struct DevSys {
     int nacc_r, nacc_nr;
     int coupling;
     int flags;
+    int item0, item_cap;  // pair-kernel work items: [item0, item0 + item_cap)
+    int nitems;           // items of the current cell list
     unsigned long long rng_id;   // second word of the Philox key
 };
 

@@ -46,6 +46,7 @@ struct Batch {
     const int *cell_sys;        // [C]
     const int *chunk_sys, *chunk_a0, *chunk_n;   // atom chunks
     int nchunks;
+    int item_cap;               // pair work items, all systems
 };
 
 struct AtomArrays {
@@ -62,6 +63,7 @@ struct AtomArrays {
     float2 *qt;                 // [N] sorted (q, type bits)
     double4 *posd;              // [N] sorted, FP64
     int2 *aux;                  // [N] sorted (mol, type)
+    int2 *items;                // [item_cap] (cell, group) pair work items
 };
 
 // ---- k_bin.cu
@@ -71,9 +73,9 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
 void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st);
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 
-// ---- k_pair.cu: partial = per-cell (Ucoul, Ulj, Wc[6], Wl[6]) as 14 doubles
+// ---- k_pair.cu: partial = per work item (Ucoul, Ulj, Wc[6], Wl[6]) as 14 doubles
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
-                 const PairConstsD &cd, double *partial, int warps_per_block, cudaStream_t st);
+                 const PairConstsD &cd, double *partial, cudaStream_t st);
 
 // ---- k_sampler.cu
 struct SamplerArgs {
@@ -133,8 +135,6 @@ void launch_finalize(const Batch &b, const double *pair_part, const double *lr_o
                      const double *kin_part, const int *chunk_first, const int *chunk_count,
                      const double *self_energy, const IntegArgs &ia, int do_box_kick,
                      double *sysred, unsigned long long *step, cudaStream_t st);
-size_t pair_smem_bytes(int precision, int nw);
-cudaError_t prepare_pair(int precision, int nw);
 cudaError_t prepare_sampler(int P);
 
 }  // namespace rbsog

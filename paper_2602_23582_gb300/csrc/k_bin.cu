@@ -98,41 +98,53 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
                                              a.count, a.locf, a.locd, a.su, precision);
 }
 
-// Exclusive scan of the cell counts (all systems, global cell order): the
-// atoms of system s occupy [atom0, atom0 + n) of the sorted arrays.
-__global__ void k_scan(const int *__restrict__ count, int *__restrict__ start, int C,
-                       const int *__restrict__ cell_sys, DevSys *sys)
+// Per-system exclusive scan of the cell counts (one block per system): the
+// atoms of system s occupy [atom0, atom0 + n) of the sorted arrays.  The same
+// pass lists the pair kernel's work items (cell, 32-atom group) of the system
+// in [item0, item0 + nitems) and marks the rest of its item range unused.
+__global__ void __launch_bounds__(1024)
+k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, DevSys *sys)
 {
-    __shared__ int tsum[1024];
+    __shared__ int ta[1024], tg[1024];
+    DevSys &d = sys[blockIdx.x];
     const int t = threadIdx.x, T = blockDim.x;
-    const int per = (C + T - 1) / T;
-    const int c0 = t * per, c1 = min(C, c0 + per);
-    int s = 0;
+    const int C0 = d.cell0, nc = d.ncell_cap_total;
+    const int per = (nc + T - 1) / T;
+    const int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
+    int sa = 0, sg = 0;
     for (int c = c0; c < c1; ++c) {
-        int v = count[c];
-        if (v > kCellCap) atomicOr(&sys[cell_sys[c]].flags, (int)FLAG_OVERFLOW);
-        s += v;
+        const int v = count[C0 + c];
+        if (v > kCellCap) atomicOr(&d.flags, (int)FLAG_OVERFLOW);
+        sa += v;
+        sg += (v + 31) >> 5;
     }
-    tsum[t] = s;
+    ta[t] = sa;
+    tg[t] = sg;
     __syncthreads();
-    // Hillis-Steele inclusive scan of the thread sums
     for (int o = 1; o < T; o <<= 1) {
-        int v = (t >= o) ? tsum[t - o] : 0;
+        int va = (t >= o) ? ta[t - o] : 0, vg = (t >= o) ? tg[t - o] : 0;
         __syncthreads();
-        tsum[t] += v;
+        ta[t] += va;
+        tg[t] += vg;
         __syncthreads();
     }
-    int run = tsum[t] - s;
+    int ra = d.atom0 + ta[t] - sa, rg = d.item0 + tg[t] - sg;
     for (int c = c0; c < c1; ++c) {
-        start[c] = run;
-        run += count[c];
+        const int v = count[C0 + c];
+        start[C0 + c] = ra;
+        ra += v;
+        const int ng = (v + 31) >> 5;
+        for (int g = 0; g < ng; ++g) items[rg + g] = make_int2(C0 + c, g);
+        rg += ng;
     }
-    if (t == T - 1) start[C] = tsum[T - 1];
+    const int total = tg[T - 1];
+    if (t == T - 1) d.nitems = total;
+    for (int k = total + t; k < d.item_cap; k += T) items[d.item0 + k] = make_int2(-1, -1);
 }
 
 void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(a.count, a.start, b.C, b.cell_sys, b.sys);
+    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys);
 }
 
 __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ rank,
@@ -148,7 +160,7 @@ __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ 
 constexpr int kSortWarps = 4;
 
 __global__ void __launch_bounds__(32 * kSortWarps)
-k_cell_sort(const int *__restrict__ start, int C, int *__restrict__ sidx,
+k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C, int *__restrict__ sidx,
             const float4 *__restrict__ locf, const double4 *__restrict__ locd,
             const double *__restrict__ q, const int *__restrict__ type, const int *__restrict__ mol,
             float4 *__restrict__ pos4, float2 *__restrict__ qt, double4 *__restrict__ posd,
@@ -159,7 +171,7 @@ k_cell_sort(const int *__restrict__ start, int C, int *__restrict__ sidx,
     const int c = blockIdx.x * kSortWarps + w;
     if (c >= C) return;
     const int base = start[c];
-    const int n = min(start[c + 1] - base, kCellCap);
+    const int n = min(count[c], kCellCap);
     if (n == 0) return;
     int *s = buf[w];
     int p2 = 1;
@@ -195,7 +207,7 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 {
     k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(a.cell, a.rank, a.start, a.sidx, b.N);
     k_cell_sort<<<(b.C + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, st>>>(
-        a.start, b.C, a.sidx, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
+        a.start, a.count, b.C, a.sidx, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
 }
 
 }  // namespace rbsog

@@ -185,39 +185,48 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
            const double *__restrict__ self_energy, const IntegArgs ia, int do_box_kick,
            double *__restrict__ sysred, unsigned long long *step)
 {
-    __shared__ double red[32];
+    constexpr int NV = 35;           // 14 pair + 15 molecule + 6 kinetic partial sums
+    __shared__ double wsum[NV][4];   // 128 threads = 4 warps
     __shared__ double acc[64];
-    const int s = blockIdx.x, tid = threadIdx.x;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     DevSys &d = sys[s];
     double *o = sysred + (size_t)s * kRed;
-    // pair partials: 14 per cell
-    const int nc = d.ncell_cap_total;
-    for (int k = 0; k < 14; ++k) {
-        double v = 0.0;
-        for (int c = tid; c < nc; c += blockDim.x) v += pair_part[(size_t)(d.cell0 + c) * 14 + k];
-        v = block_sum(v, red);
-        if (tid == 0) acc[k] = v;
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    const int ni = d.nitems;
+    for (int c = tid; c < ni; c += blockDim.x) {
+        const double *pp = pair_part + (size_t)(d.item0 + c) * 14;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) v[k] += pp[k];
     }
-    for (int k = 0; k < 15; ++k) {
-        double v = 0.0;
-        for (int c = tid; c < mchunk_count[s]; c += blockDim.x) v += mol_part[(size_t)(mchunk_first[s] + c) * 15 + k];
-        v = block_sum(v, red);
-        if (tid == 0) acc[14 + k] = v;
+    for (int c = tid; c < mchunk_count[s]; c += blockDim.x) {
+        const double *pp = mol_part + (size_t)(mchunk_first[s] + c) * 15;
+#pragma unroll
+        for (int k = 0; k < 15; ++k) v[14 + k] += pp[k];
     }
-    for (int k = 0; k < 6; ++k) {
-        double v = 0.0;
-        for (int c = tid; c < chunk_count[s]; c += blockDim.x) v += kin_part[(size_t)(chunk_first[s] + c) * 6 + k];
-        v = block_sum(v, red);
-        if (tid == 0) acc[29 + k] = v;
+    for (int c = tid; c < chunk_count[s]; c += blockDim.x) {
+        const double *pp = kin_part + (size_t)(chunk_first[s] + c) * 6;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[29 + k] += pp[k];
     }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = warp_sum(v[k]);
+        if (lane == 0) wsum[k][warp] = x;
+    }
+    __syncthreads();
+    if (tid < NV) acc[tid] = wsum[tid][0] + wsum[tid][1] + wsum[tid][2] + wsum[tid][3];
+    __syncthreads();
     if (tid != 0) return;
     const double *lr = lr_out + (size_t)s * 16;
-    const double us = self_energy[s];
+    const double us = self_energy[2 * s];        // U_self (App. A)
+    const double uxc = self_energy[2 * s + 1];   // FP32 build: sum over exclusions of ke q_i q_j F_E(0)
     double e[9];
     e[0] = acc[0];                 // U^N Coulomb
     e[1] = lr[0];                  // U^F*
     e[2] = us;
-    e[3] = acc[14];                // exclusions
+    e[3] = acc[14] - uxc;          // exclusions
     e[4] = acc[1];                 // LJ
     e[5] = acc[15];                // bonds
     e[6] = acc[16];                // angles

@@ -7,7 +7,10 @@
 //
 // One thread per molecule: a molecule's atoms belong to that thread only, so
 // forces are added without atomics.  Geometry differences are formed in FP64;
-// in the FP32 build the Gaussians of the exclusion term run in FP32.
+// in the FP32 build the terms run in FP32 and the exclusion energy is split as
+// -ke q_i q_j F_E(0) (a per-system constant summed on the host in FP64) plus
+// ke q_i q_j (F_E(0) - F_E(r)) = ke q_i q_j sum_l w_l (1 - e^{-r^2/s_l^2}),
+// evaluated with expm1 so that the FP32 error scales with the small remainder.
 #include "internal.h"
 
 namespace rbsog {
@@ -25,8 +28,15 @@ __device__ __forceinline__ void min_image(double d[3], const double L[3])
 
 }  // namespace
 
-template <bool F32>
-__global__ void __launch_bounds__(128)
+template <typename R>
+__device__ __forceinline__ R sqrt_r(R x);
+template <> __device__ __forceinline__ float sqrt_r<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double sqrt_r<double>(double x) { return sqrt(x); }
+
+// One thread per molecule.  R is the arithmetic type of the terms (float in
+// the FP32 build): differences of positions are formed in FP64, then rounded.
+template <typename R>
+__global__ void __launch_bounds__(kMolChunk)
 k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const int *__restrict__ mchunk_m0,
       const int *__restrict__ mchunk_n, const int *__restrict__ b_start, const int *__restrict__ a_start,
       const int *__restrict__ e_start, const int *__restrict__ bonds, const double *__restrict__ bk,
@@ -38,92 +48,102 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     const int c = blockIdx.x;
     const DevSys &d = sys[mchunk_sys[c]];
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
-    double ue = 0.0, ub = 0.0, ua = 0.0, wx[6] = {0, 0, 0, 0, 0, 0}, wb[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = threadIdx.x; k < mchunk_n[c]; k += blockDim.x) {
-        const int m = mchunk_m0[c] + k;
-        // bonds
-        for (int e = b_start[m]; e < b_start[m + 1]; ++e) {
+    R ub = 0, ua = 0, wb[6] = {0, 0, 0, 0, 0, 0}, wx[6] = {0, 0, 0, 0, 0, 0};
+    R ue_rem = 0;      // sum ke q_i q_j (F_E(0) - F_E(r)) (the constant part is added on the host)
+    double ue = 0.0;   // FP64 build: the full exclusion energy
+    const int k = threadIdx.x;
+    if (k < mchunk_n[c]) {
+        const int mi = mchunk_m0[c] + k;
+        for (int e = b_start[mi]; e < b_start[mi + 1]; ++e) {
             const int i = bonds[2 * e], j = bonds[2 * e + 1];
-            double dv[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
-            min_image(dv, L);
-            double rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-            double dr = rr - br0[e];
-            ub += bk[e] * dr * dr;
-            double cf = -2.0 * bk[e] * dr / rr;
-            double f[3] = {cf * dv[0], cf * dv[1], cf * dv[2]};
-            for (int a = 0; a < 3; ++a) { F[3 * i + a] += f[a]; F[3 * j + a] -= f[a]; }
+            double dd[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+            min_image(dd, L);
+            const R dv[3] = {(R)dd[0], (R)dd[1], (R)dd[2]};
+            const R rr = sqrt_r<R>(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            const R dr = rr - (R)br0[e];
+            ub += (R)bk[e] * dr * dr;
+            const R cf = (R)(-2) * (R)bk[e] * dr / rr;
+            const R f[3] = {cf * dv[0], cf * dv[1], cf * dv[2]};
+            for (int a = 0; a < 3; ++a) { F[3 * i + a] += (double)f[a]; F[3 * j + a] -= (double)f[a]; }
             wb[0] += f[0] * dv[0]; wb[1] += f[1] * dv[1]; wb[2] += f[2] * dv[2];
             wb[3] += f[0] * dv[1]; wb[4] += f[0] * dv[2]; wb[5] += f[1] * dv[2];
         }
-        // angles (i, j centre, k)
-        for (int e = a_start[m]; e < a_start[m + 1]; ++e) {
+        for (int e = a_start[mi]; e < a_start[mi + 1]; ++e) {
             const int i = angles[3 * e], j = angles[3 * e + 1], kk = angles[3 * e + 2];
-            double d1[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
-            double d2[3] = {r[3 * kk] - r[3 * j], r[3 * kk + 1] - r[3 * j + 1], r[3 * kk + 2] - r[3 * j + 2]};
-            min_image(d1, L);
-            min_image(d2, L);
-            double r1 = sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
-            double r2 = sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
-            double cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
-            cs = fmin(1.0, fmax(-1.0, cs));
-            double th = acos(cs), sn = fmax(sqrt(1.0 - cs * cs), 1e-12);
-            double dth = th - at0[e];
-            ua += ak[e] * dth * dth;
-            double g = 2.0 * ak[e] * dth / sn;
-            double fi[3], fk[3];
+            double e1[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+            double e2[3] = {r[3 * kk] - r[3 * j], r[3 * kk + 1] - r[3 * j + 1], r[3 * kk + 2] - r[3 * j + 2]};
+            min_image(e1, L);
+            min_image(e2, L);
+            const R d1[3] = {(R)e1[0], (R)e1[1], (R)e1[2]}, d2[3] = {(R)e2[0], (R)e2[1], (R)e2[2]};
+            const R r1 = sqrt_r<R>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+            const R r2 = sqrt_r<R>(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+            R cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
+            cs = cs > (R)1 ? (R)1 : (cs < (R)(-1) ? (R)(-1) : cs);
+            const R th = acos(cs);
+            R sn = sqrt_r<R>((R)1 - cs * cs);
+            if (sn < (R)1e-12) sn = (R)1e-12;
+            const R dth = th - (R)at0[e];
+            ua += (R)ak[e] * dth * dth;
+            const R g = (R)2 * (R)ak[e] * dth / sn;
+            R fi[3], fk[3];
             for (int a = 0; a < 3; ++a) {
                 fi[a] = g * (d2[a] / (r1 * r2) - cs * d1[a] / (r1 * r1));
                 fk[a] = g * (d1[a] / (r1 * r2) - cs * d2[a] / (r2 * r2));
             }
             for (int a = 0; a < 3; ++a) {
-                F[3 * i + a] += fi[a];
-                F[3 * kk + a] += fk[a];
-                F[3 * j + a] -= fi[a] + fk[a];
+                F[3 * i + a] += (double)fi[a];
+                F[3 * kk + a] += (double)fk[a];
+                F[3 * j + a] -= (double)(fi[a] + fk[a]);
             }
             wb[0] += fi[0] * d1[0] + fk[0] * d2[0]; wb[1] += fi[1] * d1[1] + fk[1] * d2[1];
             wb[2] += fi[2] * d1[2] + fk[2] * d2[2]; wb[3] += fi[0] * d1[1] + fk[0] * d2[1];
             wb[4] += fi[0] * d1[2] + fk[0] * d2[2]; wb[5] += fi[1] * d1[2] + fk[1] * d2[2];
         }
-        // exclusion corrections
-        for (int e = e_start[m]; e < e_start[m + 1]; ++e) {
+        for (int e = e_start[mi]; e < e_start[mi + 1]; ++e) {
             const int i = excl[2 * e], j = excl[2 * e + 1];
-            double dv[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
-            min_image(dv, L);
-            double r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
-            double fe, ft;
-            if (F32) {
-                float r2f = (float)r2, a = 0.f, bsum = 0.f;
+            double dd[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+            min_image(dd, L);
+            const R dv[3] = {(R)dd[0], (R)dd[1], (R)dd[2]};
+            const R r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+            R ft = 0;
+            const R qq = (R)(sc.ke * q[i] * q[j]);
+            if constexpr (sizeof(R) == 4) {
+                // F_E(0) - F_E(r) = sum_l w_l (1 - e^{-r^2/s_l^2}): small, formed without cancellation
+                float rem = 0.f;
                 for (int l = 0; l < sc.M; ++l) {
-                    float ex = __expf(-r2f / (float)(sc.st[l] * sc.st[l]));
-                    a = fmaf((float)sc.wt[l], ex, a);
-                    bsum = fmaf((float)sc.w[l], ex, bsum);
+                    const float x = (float)r2 / (float)(sc.st[l] * sc.st[l]);
+                    const float ex = expf(-x);
+                    ft = fmaf((float)sc.wt[l], ex, (float)ft);
+                    rem = fmaf((float)sc.w[l], -expm1f(-x), rem);
                 }
                 for (int l = sc.M; l < sc.ME; ++l)
-                    bsum = fmaf((float)sc.w[l], __expf(-r2f / (float)(sc.s[l] * sc.s[l])), bsum);
-                ft = a;
-                fe = bsum;
+                    rem = fmaf((float)sc.w[l], -expm1f(-(float)r2 / (float)(sc.s[l] * sc.s[l])), rem);
+                ue_rem += qq * (R)rem;
             } else {
-                ft = 0.0; fe = 0.0;
+                double fe = 0.0, ftd = 0.0;
                 for (int l = 0; l < sc.M; ++l) {
-                    double ex = exp(-r2 / (sc.st[l] * sc.st[l]));
-                    ft += sc.wt[l] * ex;
+                    const double ex = exp(-(double)r2 / (sc.st[l] * sc.st[l]));
+                    ftd += sc.wt[l] * ex;
                     fe += sc.w[l] * ex;
                 }
-                for (int l = sc.M; l < sc.ME; ++l) fe += sc.w[l] * exp(-r2 / (sc.s[l] * sc.s[l]));
+                for (int l = sc.M; l < sc.ME; ++l) fe += sc.w[l] * exp(-(double)r2 / (sc.s[l] * sc.s[l]));
+                ft = (R)ftd;
+                ue -= sc.ke * q[i] * q[j] * fe;
             }
-            double qq = sc.ke * q[i] * q[j];
-            ue -= qq * fe;
-            double f[3] = {-qq * ft * dv[0], -qq * ft * dv[1], -qq * ft * dv[2]};
-            for (int a = 0; a < 3; ++a) { F[3 * i + a] += f[a]; F[3 * j + a] -= f[a]; }
+            const R f[3] = {-qq * ft * dv[0], -qq * ft * dv[1], -qq * ft * dv[2]};
+            for (int a = 0; a < 3; ++a) { F[3 * i + a] += (double)f[a]; F[3 * j + a] -= (double)f[a]; }
             wx[0] += f[0] * dv[0]; wx[1] += f[1] * dv[1]; wx[2] += f[2] * dv[2];
             wx[3] += f[0] * dv[1]; wx[4] += f[0] * dv[2]; wx[5] += f[1] * dv[2];
         }
     }
-    double v[15] = {ue, ub, ua, wx[0], wx[1], wx[2], wx[3], wx[4], wx[5],
-                    wb[0], wb[1], wb[2], wb[3], wb[4], wb[5]};
-    for (int k = 0; k < 15; ++k) {
-        double t = block_sum(v[k], red);
-        if (threadIdx.x == 0) partial[(size_t)c * 15 + k] = t;
+    // FP32 build: ue carries the remainder; the host adds -sum ke q_i q_j F_E(0)
+    if constexpr (sizeof(R) == 4) ue = (double)ue_rem;
+    const double v[15] = {ue, (double)ub, (double)ua, (double)wx[0], (double)wx[1], (double)wx[2],
+                          (double)wx[3], (double)wx[4], (double)wx[5], (double)wb[0], (double)wb[1],
+                          (double)wb[2], (double)wb[3], (double)wb[4], (double)wb[5]};
+    for (int t = 0; t < 15; ++t) {
+        double s = block_sum(v[t], red);
+        if (threadIdx.x == 0) partial[(size_t)c * 15 + t] = s;
     }
 }
 
@@ -132,11 +152,11 @@ void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const S
 {
     if (m.nmchunks == 0) return;
     if (precision == 1)
-        k_mol<true><<<m.nmchunks, 128, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
+        k_mol<float><<<m.nmchunks, kMolChunk, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
                                                m.a_start, m.e_start, m.bonds, m.bk, m.br0, m.angles, m.ak,
                                                m.at0, m.excl, a.r, a.q, a.F, partial, sc);
     else
-        k_mol<false><<<m.nmchunks, 128, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
+        k_mol<double><<<m.nmchunks, kMolChunk, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
                                                 m.a_start, m.e_start, m.bonds, m.bk, m.br0, m.angles, m.ak,
                                                 m.at0, m.excl, a.r, a.q, a.F, partial, sc);
 }

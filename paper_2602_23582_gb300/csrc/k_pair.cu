@@ -6,25 +6,28 @@
 //   f   = ke q_i q_j (1/r^3 - sum_{l<M} w~_l e^{-r^2/s~_l^2}) r_vec   (kernel N~)
 //   U  += ke q_i q_j (1/r   - sum_{l<ME} w_l e^{-r^2/s_l^2})          (kernel N)
 //   W  += f (x) r_vec  (eq. P_short: P^N = W / V)
-// Full pairs: every atom's block sums all its neighbours (no atomics, so the
-// result does not depend on scheduling); energies and virials take half.
+// Full pairs: each atom sums all its neighbours itself (no atomics, so results
+// do not depend on scheduling); energies and virials take half.
 //
-// One block per home cell.  Each warp owns 32 i-atoms (one per lane, in
-// registers).  For each row of neighbour cells (fixed dy, dz; dx in
-// [-sub, sub]) the block stages the row's atoms into shared memory with the
-// periodic offset already added (coordinates are cell-local, so FP32 keeps
-// ~1e-6 A).  Lanes test candidates (distance and molecule id only) and push
-// the hits into per-lane queues; the warp evaluates queued hits in rounds in
-// which every lane has one, so the 11-transcendental SOG kernel never runs
-// with idle lanes except when queues are drained at the end of a tile.
+// Work item = one warp = a group of up to 32 atoms of one cell (lane = atom,
+// in registers).  The warp walks the (2 sub + 1)^3 neighbour cells; candidate
+// neighbours are read with warp-broadcast loads (every lane the same address,
+// served by L1), four at a time.  A candidate that passes the cheap test
+// (r^2 < r_c^2, different molecule) is pushed, with the code of its
+// neighbour cell, into the lane's queue in shared memory; the warp evaluates
+// the 11-transcendental SOG kernel in rounds in which every lane with an atom
+// has a queued hit, so the expensive part runs with full lanes.
+//
+// Coordinates are cell-local (FP32 keeps ~1e-6 A); a neighbour cell's
+// periodic offset (d_a w_a) is subtracted from the i coordinate.
 #include "internal.h"
 
 namespace rbsog {
 
 namespace {
 
-constexpr int QCAP = 64;   // per-lane hit queue (power of two); pending <= 32 before a batch
-constexpr int JT = 512;    // atoms per staged tile
+constexpr int QCAP = 64;    // per-lane queue (power of two); pending <= 32 before a batch
+constexpr int WPB = 4;      // warps (work items) per block
 
 __device__ __forceinline__ float ex2f(float x)
 {
@@ -33,17 +36,30 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 struct AccF {
     float fx, fy, fz;
-    float uc, ul;
+    float uc, ul, cuc, cul;   // energies with compensation terms
     float wc[6], wl[6];
 };
 
+struct AccD {
+    double fx, fy, fz;
+    double uc, ul;
+    double wc[6], wl[6];
+};
+
 template <int NG>
-__device__ __forceinline__ void pair_eval_f(const PairConstsF &pc, float xi, float yi, float zi,
-                                            float qi, int ti, float4 pj, float2 qj, AccF &acc)
+__device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float dy, float dz, float qi,
+                                          int ti, float2 qj, AccF &acc)
 {
-    const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float rinv = rsqrtf(r2);
     const float r2inv = rinv * rinv;
@@ -75,8 +91,8 @@ __device__ __forceinline__ void pair_eval_f(const PairConstsF &pc, float xi, flo
     acc.fx = fmaf(f, dx, acc.fx);
     acc.fy = fmaf(f, dy, acc.fy);
     acc.fz = fmaf(f, dz, acc.fz);
-    acc.uc += ec;
-    acc.ul += el;
+    kahan_add(acc.uc, acc.cuc, ec);
+    kahan_add(acc.ul, acc.cul, el);
     const float cx = fc * dx, cy = fc * dy, lx = fl * dx, ly = fl * dy;
     acc.wc[0] = fmaf(cx, dx, acc.wc[0]); acc.wc[1] = fmaf(cy, dy, acc.wc[1]);
     acc.wc[2] = fmaf(fc * dz, dz, acc.wc[2]); acc.wc[3] = fmaf(cx, dy, acc.wc[3]);
@@ -86,16 +102,9 @@ __device__ __forceinline__ void pair_eval_f(const PairConstsF &pc, float xi, flo
     acc.wl[4] = fmaf(lx, dz, acc.wl[4]); acc.wl[5] = fmaf(ly, dz, acc.wl[5]);
 }
 
-struct AccD {
-    double fx, fy, fz;
-    double uc, ul;
-    double wc[6], wl[6];
-};
-
-__device__ __forceinline__ void pair_eval_d(const PairConstsD &pc, double xi, double yi, double zi,
-                                            double qi, int ti, double4 pj, int tj, AccD &acc)
+__device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, double dy, double dz, double qi,
+                                          int ti, double qj, int tj, AccD &acc)
 {
-    const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double rinv = rsqrt(r2);
     const double r2inv = rinv * rinv;
@@ -106,7 +115,7 @@ __device__ __forceinline__ void pair_eval_d(const PairConstsD &pc, double xi, do
         se = fma(pc.w[l], e, se);
     }
     for (int l = pc.M; l < pc.ME; ++l) se = fma(pc.w[l], exp(-r2 * pc.inv_s2[l]), se);
-    const double qq = pc.ke * qi * pj.w;
+    const double qq = pc.ke * qi * qj;
     const double fc = qq * (r2inv * rinv - st);
     const double ec = qq * (rinv - se);
     const double la = pc.lj_a[ti * pc.ntypes + tj], lb = pc.lj_b[ti * pc.ntypes + tj];
@@ -125,352 +134,269 @@ __device__ __forceinline__ void pair_eval_d(const PairConstsD &pc, double xi, do
     acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
 }
 
-// Row of neighbour cells: up to 5 cells (sub <= 2).
-struct RowInfo {
-    int start[5], count[5], cum[6];
-    float offx[5];
-    double offxd[5];
-};
-
-__device__ __forceinline__ int find_cell(const RowInfo &ri, int ncr, int k)
-{
-    int c = 0;
-#pragma unroll
-    for (int t = 1; t < 5; ++t)
-        if (t < ncr && k >= ri.cum[t]) c = t;
-    return c;
-}
+__device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP32 kernel
+// FP32 kernel.  Neighbour cell code: (dx + sub) | (dy + sub) << 3 | (dz + sub) << 6.
 // ---------------------------------------------------------------------------
 template <int NG>
-__global__ void k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys,
-                           const int *__restrict__ start, const float4 *__restrict__ pos4,
-                           const float2 *__restrict__ qt, const int *__restrict__ sidx, int sub,
-                           double *__restrict__ F, double *__restrict__ partial, const PairConstsF pc)
+__global__ void __launch_bounds__(32 * WPB)
+k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
+           const int *__restrict__ count, const int2 *__restrict__ items, int n_items,
+           const float4 *__restrict__ pos4, const float2 *__restrict__ qt, const int *__restrict__ sidx, int sub,
+           double *__restrict__ F, double *__restrict__ partial, const PairConstsF pc)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int nw = blockDim.x >> 5;
-    float4 *Jp = reinterpret_cast<float4 *>(smem);
-    float2 *Jq = reinterpret_cast<float2 *>(Jp + JT);
-    unsigned *queue = reinterpret_cast<unsigned *>(Jq + JT);     // [nw][QCAP][32]
-    __shared__ RowInfo ri;
-    __shared__ double grp[14][kCellCap / 32];
-
-    const int gc = blockIdx.x;
+    __shared__ unsigned queue[WPB][QCAP * 32];
+    __shared__ unsigned char qcode[WPB][QCAP * 32];
     const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int it = blockIdx.x * WPB + warp;
+    if (it >= n_items) return;
+    const int2 item = items[it];
+    if (item.x < 0) return;
+    const int gc = item.x;
     const DevSys &d = sys[cell_sys[gc]];
     const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
     const int lc = gc - d.cell0;
+    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+    const float wx = (float)d.w[0], wy = (float)d.w[1], wz = (float)d.w[2];
+    const int i0 = start[gc] + 32 * item.y;
+    const int ni = min(32, count[gc] - 32 * item.y);
+    const bool vi = lane < ni;
+    float4 pi = make_float4(0.f, 0.f, 0.f, __int_as_float(-0x7fffffff));
+    float2 pq = make_float2(0.f, 0.f);
+    if (vi) { pi = pos4[i0 + lane]; pq = qt[i0 + lane]; }
+    const int moli = vi ? __float_as_int(pi.w) : -0x7fffffff;
+    const int ti = __float_as_int(pq.y);
+    const float rc2 = pc.rc2;
+    unsigned *q = queue[warp];
+    unsigned char *qc = qcode[warp];
     AccF acc;
-    int ngroups = 0;
-
-    if (lc < n0 * n1 * n2) {
-        const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-        const int i0 = start[gc], ni = start[gc + 1] - i0;
-        const float wx = (float)d.w[0], wy = (float)d.w[1], wz = (float)d.w[2];
-        const int ncr = 2 * sub + 1;
-        unsigned *q = queue + warp * QCAP * 32;
-        const int rounds = (ni + 32 * nw - 1) / (32 * nw);
-        ngroups = (min(ni, kCellCap) + 31) / 32;
-        for (int rd = 0; rd < rounds; ++rd) {
-            const int il = rd * 32 * nw + warp * 32 + lane;
-            const bool vi = il < ni;
-            acc.uc = acc.ul = 0.f;
+    acc.fx = acc.fy = acc.fz = 0.f;
+    acc.uc = acc.ul = acc.cuc = acc.cul = 0.f;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.f;
-            float4 pi = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-            float2 pq = make_float2(0.f, 0.f);
-            if (vi) { pi = pos4[i0 + il]; pq = qt[i0 + il]; }
-            const int moli = vi ? __float_as_int(pi.w) : -0x7fffffff;
-            const int ti = __float_as_int(pq.y);
-            acc.fx = acc.fy = acc.fz = 0.f;
-            for (int dz = -sub; dz <= sub; ++dz) {
-                for (int dy = -sub; dy <= sub; ++dy) {
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        int yy = cy + dy, zz = cz + dz;
-                        yy += (yy < 0) ? n1 : ((yy >= n1) ? -n1 : 0);
-                        zz += (zz < 0) ? n2 : ((zz >= n2) ? -n2 : 0);
-                        ri.cum[0] = 0;
-                        for (int t = 0; t < ncr; ++t) {
-                            int xx = cx + t - sub;
-                            xx += (xx < 0) ? n0 : ((xx >= n0) ? -n0 : 0);
-                            int g = d.cell0 + xx + n0 * (yy + n1 * zz);
-                            ri.start[t] = start[g];
-                            ri.count[t] = start[g + 1] - start[g];
-                            ri.cum[t + 1] = ri.cum[t] + ri.count[t];
-                            ri.offx[t] = (float)((t - sub) * d.w[0]);
-                        }
-                    }
-                    __syncthreads();
-                    const int total = ri.cum[ncr];
-                    const float oy = dy * wy, oz = dz * wz;
-                    for (int base = 0; base < total; base += JT) {
-                        const int nj = min(JT, total - base);
-                        __syncthreads();
-                        for (int k = threadIdx.x; k < nj; k += blockDim.x) {
-                            int kk = base + k;
-                            int c = find_cell(ri, ncr, kk);
-                            int src = ri.start[c] + (kk - ri.cum[c]);
-                            float4 p = pos4[src];
-                            p.x += ri.offx[c];
-                            p.y += oy;
-                            p.z += oz;
-                            Jp[k] = p;
-                            Jq[k] = qt[src];
-                        }
-                        __syncthreads();
-                        // candidates + queued evaluation (per warp)
-                        int head = 0, tail = 0;
-                        if (!__any_sync(0xffffffffu, vi)) continue;
-                        for (int jb = 0; jb < nj; jb += 32) {
-                            const int je = min(jb + 32, nj);
-                            for (int j = jb; j < je; ++j) {
-                                const float4 pj = Jp[j];
-                                const float dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
-                                const float r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-                                if (vi && r2 < pc.rc2 && __float_as_int(pj.w) != moli) {
-                                    q[(tail & (QCAP - 1)) * 32 + lane] = (unsigned)j;
-                                    ++tail;
-                                }
-                            }
-                            // rounds in which every lane holding an atom has a hit queued;
-                            // lanes without an atom have nothing queued and sit them out
-                            int pend = tail - head;
-                            int mn = __reduce_min_sync(0xffffffffu, vi ? pend : QCAP);
-                            for (int t = 0; t < mn; ++t) {
-                                if (vi) {
-                                    unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                    ++head;
-                                    pair_eval_f<NG>(pc, pi.x, pi.y, pi.z, pq.x, ti, Jp[j], Jq[j], acc);
-                                }
-                            }
-                            while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
-                                if (tail > head) {
-                                    unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                    ++head;
-                                    pair_eval_f<NG>(pc, pi.x, pi.y, pi.z, pq.x, ti, Jp[j], Jq[j], acc);
-                                }
-                            }
-                        }
-                        while (__any_sync(0xffffffffu, tail > head)) {
-                            if (tail > head) {
-                                unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                ++head;
-                                pair_eval_f<NG>(pc, pi.x, pi.y, pi.z, pq.x, ti, Jp[j], Jq[j], acc);
-                            }
-                        }
+    for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.f;
+    int head = 0, tail = 0;
+
+    auto eval_one = [&](unsigned j, int code) {
+        const float4 pj = pos4[j];
+        const float2 qj = qt[j];
+        const float ox = (float)((code & 7) - sub) * wx;
+        const float oy = (float)(((code >> 3) & 7) - sub) * wy;
+        const float oz = (float)((code >> 6) - sub) * wz;
+        pair_eval<NG>(pc, (pi.x - ox) - pj.x, (pi.y - oy) - pj.y, (pi.z - oz) - pj.z, pq.x, ti, qj, acc);
+    };
+
+    const int span = 2 * sub + 1;
+    for (int nb = 0; nb < span * span * span; ++nb) {
+        const int ddx = nb % span - sub, ddy = (nb / span) % span - sub, ddz = nb / (span * span) - sub;
+        const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + ddz, n2));
+        const int j0 = start[g], nj = count[g];
+        const int code = (ddx + sub) | ((ddy + sub) << 3) | ((ddz + sub) << 6);
+        const float xi = pi.x - ddx * wx, yi = pi.y - ddy * wy, zi = pi.z - ddz * wz;
+        for (int jb = 0; jb < nj; jb += 32) {
+            const int je = min(jb + 32, nj);
+            int j = jb;
+            for (; j + 4 <= je; j += 4) {
+                float4 p[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) p[u] = __ldg(&pos4[j0 + j + u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float dx = xi - p[u].x, dy = yi - p[u].y, dz = zi - p[u].z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2 && __float_as_int(p[u].w) != moli) {
+                        const int slot = (tail & (QCAP - 1)) * 32 + lane;
+                        q[slot] = (unsigned)(j0 + j + u);
+                        qc[slot] = (unsigned char)code;
+                        ++tail;
                     }
                 }
             }
-            if (vi) {
-                const int ia = sidx[i0 + il];
-                F[3 * ia] = acc.fx;
-                F[3 * ia + 1] = acc.fy;
-                F[3 * ia + 2] = acc.fz;
+            for (; j < je; ++j) {
+                const float4 pj = __ldg(&pos4[j0 + j]);
+                const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2 && __float_as_int(pj.w) != moli) {
+                    const int slot = (tail & (QCAP - 1)) * 32 + lane;
+                    q[slot] = (unsigned)(j0 + j);
+                    qc[slot] = (unsigned char)code;
+                    ++tail;
+                }
             }
-            // per 32-atom group: FP32 warp sum, kept per group index so that the
-            // cell total does not depend on the warps per block
-            const int g = rd * nw + warp;
-            const float v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
-                                 acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
-#pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                float x = warp_sumf(v[k]);
-                if (lane == 0 && g < ngroups) grp[k][g] = (double)x;
+            // full-warp rounds: every lane with an atom has a hit queued (lanes
+            // without an atom never queue anything and sit these rounds out)
+            const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
+            for (int t = 0; t < mn; ++t) {
+                if (vi) {
+                    const int slot = (head & (QCAP - 1)) * 32 + lane;
+                    ++head;
+                    eval_one(q[slot], qc[slot]);
+                }
+            }
+            // keep room for the next batch of 32 candidates
+            while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
+                if (tail > head) {
+                    const int slot = (head & (QCAP - 1)) * 32 + lane;
+                    ++head;
+                    eval_one(q[slot], qc[slot]);
+                }
             }
         }
     }
-    __syncthreads();
-    if (threadIdx.x < 14) {
-        double s = 0.0;
-        for (int g = 0; g < ngroups; ++g) s += grp[threadIdx.x][g];
-        partial[(size_t)gc * 14 + threadIdx.x] = 0.5 * s;
+    while (__any_sync(0xffffffffu, tail > head)) {
+        if (tail > head) {
+            const int slot = (head & (QCAP - 1)) * 32 + lane;
+            ++head;
+            eval_one(q[slot], qc[slot]);
+        }
+    }
+    if (vi) {
+        const int ia = sidx[i0 + lane];
+        F[3 * ia] = acc.fx;
+        F[3 * ia + 1] = acc.fy;
+        F[3 * ia + 2] = acc.fz;
+    }
+    // per-item sums: energies in FP64 (compensated lanes), virials FP32 warp sums
+    const double u0 = warp_sum((double)acc.uc - (double)acc.cuc);
+    const double u1 = warp_sum((double)acc.ul - (double)acc.cul);
+    float wv[12] = {acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4], acc.wc[5],
+                    acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) wv[k] = warp_sumf(wv[k]);
+    if (lane == 0) {
+        double *o = partial + (size_t)it * 14;
+        o[0] = 0.5 * u0;
+        o[1] = 0.5 * u1;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) o[2 + k] = 0.5 * (double)wv[k];
     }
 }
 
 // ---------------------------------------------------------------------------
 // FP64 kernel (same structure)
 // ---------------------------------------------------------------------------
-__global__ void k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys,
-                           const int *__restrict__ start, const double4 *__restrict__ posd,
-                           const int2 *__restrict__ aux, const int *__restrict__ sidx, int sub,
-                           double *__restrict__ F, double *__restrict__ partial, const PairConstsD pc)
+__global__ void __launch_bounds__(32 * WPB)
+k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
+           const int *__restrict__ count, const int2 *__restrict__ items, int n_items,
+           const double4 *__restrict__ posd, const int2 *__restrict__ aux, const int *__restrict__ sidx, int sub,
+           double *__restrict__ F, double *__restrict__ partial, const PairConstsD pc)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int nw = blockDim.x >> 5;
-    double4 *Jp = reinterpret_cast<double4 *>(smem);
-    int2 *Ja = reinterpret_cast<int2 *>(Jp + JT);
-    unsigned *queue = reinterpret_cast<unsigned *>(Ja + JT);
-    __shared__ RowInfo ri;
-    __shared__ double grp[14][kCellCap / 32];
-
-    const int gc = blockIdx.x;
+    __shared__ unsigned queue[WPB][QCAP * 32];
+    __shared__ unsigned char qcode[WPB][QCAP * 32];
     const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int it = blockIdx.x * WPB + warp;
+    if (it >= n_items) return;
+    const int2 item = items[it];
+    if (item.x < 0) return;
+    const int gc = item.x;
     const DevSys &d = sys[cell_sys[gc]];
     const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
     const int lc = gc - d.cell0;
+    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+    const double wx = d.w[0], wy = d.w[1], wz = d.w[2];
+    const int i0 = start[gc] + 32 * item.y;
+    const int ni = min(32, count[gc] - 32 * item.y);
+    const bool vi = lane < ni;
+    double4 pi = make_double4(0, 0, 0, 0);
+    int2 ai = make_int2(-0x7fffffff, 0);
+    if (vi) { pi = posd[i0 + lane]; ai = aux[i0 + lane]; }
+    const double rc2 = pc.rc2;
+    unsigned *q = queue[warp];
+    unsigned char *qc = qcode[warp];
     AccD acc;
-    int ngroups = 0;
-
-    if (lc < n0 * n1 * n2) {
-        const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-        const int i0 = start[gc], ni = start[gc + 1] - i0;
-        const int ncr = 2 * sub + 1;
-        unsigned *q = queue + warp * QCAP * 32;
-        const int rounds = (ni + 32 * nw - 1) / (32 * nw);
-        ngroups = (min(ni, kCellCap) + 31) / 32;
-        for (int rd = 0; rd < rounds; ++rd) {
-            const int il = rd * 32 * nw + warp * 32 + lane;
-            const bool vi = il < ni;
-            acc.uc = acc.ul = 0.0;
+    acc.fx = acc.fy = acc.fz = 0.0;
+    acc.uc = acc.ul = 0.0;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.0;
-            double4 pi = make_double4(0, 0, 0, 0);
-            int2 ai = make_int2(-0x7fffffff, 0);
-            if (vi) { pi = posd[i0 + il]; ai = aux[i0 + il]; }
-            acc.fx = acc.fy = acc.fz = 0.0;
-            for (int dz = -sub; dz <= sub; ++dz) {
-                for (int dy = -sub; dy <= sub; ++dy) {
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        int yy = cy + dy, zz = cz + dz;
-                        yy += (yy < 0) ? n1 : ((yy >= n1) ? -n1 : 0);
-                        zz += (zz < 0) ? n2 : ((zz >= n2) ? -n2 : 0);
-                        ri.cum[0] = 0;
-                        for (int t = 0; t < ncr; ++t) {
-                            int xx = cx + t - sub;
-                            xx += (xx < 0) ? n0 : ((xx >= n0) ? -n0 : 0);
-                            int g = d.cell0 + xx + n0 * (yy + n1 * zz);
-                            ri.start[t] = start[g];
-                            ri.count[t] = start[g + 1] - start[g];
-                            ri.cum[t + 1] = ri.cum[t] + ri.count[t];
-                            ri.offxd[t] = (t - sub) * d.w[0];
-                        }
-                    }
-                    __syncthreads();
-                    const int total = ri.cum[ncr];
-                    const double oy = dy * d.w[1], oz = dz * d.w[2];
-                    for (int base = 0; base < total; base += JT) {
-                        const int nj = min(JT, total - base);
-                        __syncthreads();
-                        for (int k = threadIdx.x; k < nj; k += blockDim.x) {
-                            int kk = base + k;
-                            int c = find_cell(ri, ncr, kk);
-                            int src = ri.start[c] + (kk - ri.cum[c]);
-                            double4 p = posd[src];
-                            p.x += ri.offxd[c];
-                            p.y += oy;
-                            p.z += oz;
-                            Jp[k] = p;
-                            Ja[k] = aux[src];
-                        }
-                        __syncthreads();
-                        int head = 0, tail = 0;
-                        if (!__any_sync(0xffffffffu, vi)) continue;
-                        for (int jb = 0; jb < nj; jb += 32) {
-                            const int je = min(jb + 32, nj);
-                            for (int j = jb; j < je; ++j) {
-                                const double4 pj = Jp[j];
-                                const double dx = pi.x - pj.x, dy2 = pi.y - pj.y, dz2 = pi.z - pj.z;
-                                const double r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-                                if (vi && r2 < pc.rc2 && Ja[j].x != ai.x) {
-                                    q[(tail & (QCAP - 1)) * 32 + lane] = (unsigned)j;
-                                    ++tail;
-                                }
-                            }
-                            int pend = tail - head;
-                            int mn = __reduce_min_sync(0xffffffffu, vi ? pend : QCAP);
-                            for (int t = 0; t < mn; ++t) {
-                                if (vi) {
-                                    unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                    ++head;
-                                    pair_eval_d(pc, pi.x, pi.y, pi.z, pi.w, ai.y, Jp[j], Ja[j].y, acc);
-                                }
-                            }
-                            while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
-                                if (tail > head) {
-                                    unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                    ++head;
-                                    pair_eval_d(pc, pi.x, pi.y, pi.z, pi.w, ai.y, Jp[j], Ja[j].y, acc);
-                                }
-                            }
-                        }
-                        while (__any_sync(0xffffffffu, tail > head)) {
-                            if (tail > head) {
-                                unsigned j = q[(head & (QCAP - 1)) * 32 + lane];
-                                ++head;
-                                pair_eval_d(pc, pi.x, pi.y, pi.z, pi.w, ai.y, Jp[j], Ja[j].y, acc);
-                            }
-                        }
-                    }
+    for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.0;
+    int head = 0, tail = 0;
+
+    auto eval_one = [&](unsigned j, int code) {
+        const double4 pj = posd[j];
+        const int tj = aux[j].y;
+        const double ox = (double)((code & 7) - sub) * wx;
+        const double oy = (double)(((code >> 3) & 7) - sub) * wy;
+        const double oz = (double)((code >> 6) - sub) * wz;
+        pair_eval(pc, (pi.x - ox) - pj.x, (pi.y - oy) - pj.y, (pi.z - oz) - pj.z, pi.w, ai.y, pj.w, tj, acc);
+    };
+
+    const int span = 2 * sub + 1;
+    for (int nb = 0; nb < span * span * span; ++nb) {
+        const int ddx = nb % span - sub, ddy = (nb / span) % span - sub, ddz = nb / (span * span) - sub;
+        const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + ddz, n2));
+        const int j0 = start[g], nj = count[g];
+        const int code = (ddx + sub) | ((ddy + sub) << 3) | ((ddz + sub) << 6);
+        const double xi = pi.x - ddx * wx, yi = pi.y - ddy * wy, zi = pi.z - ddz * wz;
+        for (int jb = 0; jb < nj; jb += 32) {
+            const int je = min(jb + 32, nj);
+            for (int j = jb; j < je; ++j) {
+                const double4 pj = posd[j0 + j];
+                const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2 && aux[j0 + j].x != ai.x) {
+                    const int slot = (tail & (QCAP - 1)) * 32 + lane;
+                    q[slot] = (unsigned)(j0 + j);
+                    qc[slot] = (unsigned char)code;
+                    ++tail;
                 }
             }
-            if (vi) {
-                const int ia = sidx[i0 + il];
-                F[3 * ia] = acc.fx;
-                F[3 * ia + 1] = acc.fy;
-                F[3 * ia + 2] = acc.fz;
+            const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
+            for (int t = 0; t < mn; ++t) {
+                if (vi) {
+                    const int slot = (head & (QCAP - 1)) * 32 + lane;
+                    ++head;
+                    eval_one(q[slot], qc[slot]);
+                }
             }
-            const int g = rd * nw + warp;
-            const double v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
-                                  acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
-#pragma unroll
-            for (int k = 0; k < 14; ++k) {
-                double x = warp_sum(v[k]);
-                if (lane == 0 && g < ngroups) grp[k][g] = x;
+            while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
+                if (tail > head) {
+                    const int slot = (head & (QCAP - 1)) * 32 + lane;
+                    ++head;
+                    eval_one(q[slot], qc[slot]);
+                }
             }
         }
     }
-    __syncthreads();
-    if (threadIdx.x < 14) {
-        double s = 0.0;
-        for (int g = 0; g < ngroups; ++g) s += grp[threadIdx.x][g];
-        partial[(size_t)gc * 14 + threadIdx.x] = 0.5 * s;
+    while (__any_sync(0xffffffffu, tail > head)) {
+        if (tail > head) {
+            const int slot = (head & (QCAP - 1)) * 32 + lane;
+            ++head;
+            eval_one(q[slot], qc[slot]);
+        }
     }
-}
-
-size_t pair_smem_bytes(int precision, int nw)
-{
-    size_t tile = precision == 1 ? (size_t)JT * (sizeof(float4) + sizeof(float2))
-                                 : (size_t)JT * (sizeof(double4) + sizeof(int2));
-    return tile + (size_t)nw * QCAP * 32 * sizeof(unsigned);
-}
-
-// Opt the pair kernels into the dynamic shared memory they need (called once
-// per context, outside any stream capture).
-cudaError_t prepare_pair(int precision, int nw)
-{
-    const int sm = (int)pair_smem_bytes(precision, nw);
-    cudaError_t e;
-    if (precision == 1) {
-        e = cudaFuncSetAttribute(k_pair_f32<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pair_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    } else {
-        e = cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (vi) {
+        const int ia = sidx[i0 + lane];
+        F[3 * ia] = acc.fx;
+        F[3 * ia + 1] = acc.fy;
+        F[3 * ia + 2] = acc.fz;
     }
-    return e;
+    const double v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
+                          acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
+    double red[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) red[k] = warp_sum(v[k]);
+    if (lane == 0) {
+        double *o = partial + (size_t)it * 14;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) o[k] = 0.5 * red[k];
+    }
 }
 
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
-                 const PairConstsD &cd, double *partial, int nw, cudaStream_t st)
+                 const PairConstsD &cd, double *partial, cudaStream_t st)
 {
-    const size_t sm = pair_smem_bytes(precision, nw);
+    const int blocks = (b.item_cap + WPB - 1) / WPB;
     if (precision == 1) {
         if (cf.M == 10)
-            k_pair_f32<10><<<b.C, 32 * nw, sm, st>>>(b.sys, b.cell_sys, a.start, a.pos4, a.qt, a.sidx,
-                                                      b.sub, a.F, partial, cf);
+            k_pair_f32<10><<<blocks, 32 * WPB, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
+                                                        a.pos4, a.qt, a.sidx, b.sub, a.F, partial, cf);
         else
-            k_pair_f32<0><<<b.C, 32 * nw, sm, st>>>(b.sys, b.cell_sys, a.start, a.pos4, a.qt, a.sidx,
-                                                     b.sub, a.F, partial, cf);
+            k_pair_f32<0><<<blocks, 32 * WPB, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
+                                                       a.pos4, a.qt, a.sidx, b.sub, a.F, partial, cf);
     } else {
-        k_pair_f64<<<b.C, 32 * nw, sm, st>>>(b.sys, b.cell_sys, a.start, a.posd, a.aux, a.sidx, b.sub,
-                                             a.F, partial, cd);
+        k_pair_f64<<<blocks, 32 * WPB, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap, a.posd,
+                                                a.aux, a.sidx, b.sub, a.F, partial, cd);
     }
 }
 

@@ -37,7 +37,7 @@ struct DevBuf {
 
 struct rbsog_ctx {
     rbsog_params prm{};
-    int S = 0, N = 0, C = 0, Dcap = 0, nchunks = 0, nmol = 0, nmchunks = 0, nw = 4;
+    int S = 0, N = 0, C = 0, Dcap = 0, nchunks = 0, nmol = 0, nmchunks = 0, item_cap = 0;
     cudaStream_t st = nullptr, st2 = nullptr;
     bool own_st = false, own_st2 = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -53,7 +53,7 @@ struct rbsog_ctx {
     uint4 *su = nullptr;
     int *count = nullptr, *start = nullptr, *sidx = nullptr, *cell_sys = nullptr;
     float2 *qt = nullptr;
-    int2 *aux = nullptr;
+    int2 *aux = nullptr, *items = nullptr;
     int *chunk_sys = nullptr, *chunk_a0 = nullptr, *chunk_n = nullptr, *first_chunk = nullptr, *nchunk_sys = nullptr;
     int *mchunk_sys = nullptr, *mchunk_m0 = nullptr, *mchunk_n = nullptr, *mchunk_first = nullptr, *mchunk_count = nullptr;
     int *b_start = nullptr, *a_start = nullptr, *e_start = nullptr, *bonds = nullptr, *angles = nullptr, *excl = nullptr;
@@ -166,7 +166,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick)
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
-    launch_pair(c->b, c->a, prec, c->pcf, c->pcd, c->pair_part, c->nw, c->st);
+    launch_pair(c->b, c->a, prec, c->pcf, c->pcd, c->pair_part, c->st);
     record(c, "pair");
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
@@ -264,7 +264,7 @@ rbsog_status validate(const rbsog_params *p, int S, const rbsog_system_desc *sy)
     if (!(p->rc > 0) || !(p->b > 1) || !(p->sigma > 0) || p->M < 1 || p->M > kMaxGauss ||
         p->M_energy < p->M || p->M_energy > kMaxGauss || p->P < 1 || p->P > kMaxP ||
         p->sampler < 0 || p->sampler > 2 || (p->precision != 0 && p->precision != 1) ||
-        (p->cell_sub != 1 && p->cell_sub != 2) || p->coupling < 0 || p->coupling > 2)
+        (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2)
         return RBSOG_EINVAL;
     for (int s = 0; s < S; ++s) {
         const rbsog_system_desc &d = sy[s];
@@ -303,7 +303,7 @@ void rbsog_default_params(rbsog_params *p, double rc)
     p->tau_box = 500.0;
     p->compressibility = 4.5e-5 * 1.01325;   // 4.5e-5 bar^-1 in atm^-1
     p->coupling = RBSOG_COUPLE_ISO;
-    p->cell_sub = 1;
+    p->cell_sub = 0;
 }
 
 const char *rbsog_last_error(const rbsog_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
@@ -331,6 +331,14 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
     if (!c) return RBSOG_ENOMEM;
     try {
         c->prm = *params;
+        if (c->prm.cell_sub == 0) {
+            // cells of r_c/2 when a box edge leaves little room above 3 r_c (the
+            // box fluctuates in NPT), else cells of r_c
+            c->prm.cell_sub = 1;
+            for (int k = 0; k < n_systems; ++k)
+                for (int a2 = 0; a2 < 3; ++a2)
+                    if (systems[k].box[a2] < 3.3 * c->prm.rc) c->prm.cell_sub = 2;
+        }
         const rbsog_params &P = c->prm;
         c->S = n_systems;
         c->st = static_cast<cudaStream_t>(stream);
@@ -354,12 +362,11 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         std::vector<DevSys> hsys(S);
         std::vector<int> atom_sys, cell_sys, chunk_sys, chunk_a0, chunk_n, first_chunk(S), nchunk(S);
         std::vector<int> mchunk_sys, mchunk_m0, mchunk_n, mchunk_first(S), mchunk_count(S);
-        std::vector<double> r, p, q, mass, self_e(S);
+        std::vector<double> r, p, q, mass, self_e(2 * S);
         std::vector<int> type, mol;
         std::vector<int> b_start{0}, a_start{0}, e_start{0}, bonds, angles, excl;
         std::vector<double> bk, br0, ak, at0;
-        int N = 0, C = 0, nmol = 0;
-        double avg_cell = 0.0;
+        int N = 0, C = 0, nmol = 0, item_cap = 0;
         std::vector<double> w, s, wt, st;
         const int MM = std::max(P.M, P.M_energy);
         sog_terms(P, MM, w, s, wt, st);
@@ -385,6 +392,10 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             ds.V = d.box[0] * d.box[1] * d.box[2];
             ds.cell0 = C;
             ds.ncell_cap_total = ncap_t;
+            // pair work items: at most one partial 32-atom group per cell
+            ds.item0 = item_cap;
+            ds.item_cap = (d.n_atoms + 31) / 32 + ncap_t;
+            item_cap += ds.item_cap;
             ds.atom0 = N;
             ds.n = d.n_atoms;
             ds.coupling = P.coupling == RBSOG_COUPLE_SEMI_ISO ? 1 : 0;
@@ -402,9 +413,6 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             c->h_atom0[k] = N; c->h_n[k] = d.n_atoms; c->h_cell0[k] = C; c->h_ncap_total[k] = ncap_t;
             for (int i = 0; i < ncap_t; ++i) cell_sys.push_back(k);
             C += ncap_t;
-            avg_cell = std::max(avg_cell, (double)d.n_atoms / ((double)std::floor(d.box[0] * P.cell_sub / P.rc) *
-                                                               std::floor(d.box[1] * P.cell_sub / P.rc) *
-                                                               std::floor(d.box[2] * P.cell_sub / P.rc)));
             // atoms
             double sq = 0.0;
             for (int i = 0; i < d.n_atoms; ++i) {
@@ -424,8 +432,16 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                 mol.push_back(d.mol[i]);
                 sq += d.q[i] * d.q[i];
             }
-            self_e[k] = P.ke * std::log(P.b) / (std::sqrt(2.0 * kPi) * P.sigma) *
-                        (P.omega + (1.0 - std::pow(P.b, -(P.M_energy - 1.0))) / (P.b - 1.0)) * sq;
+            // App. A: U_self = ln b / (sqrt(2 pi) sigma) (omega + (1 - b^{-(M-1)})/(b - 1)) sum q^2
+            self_e[2 * k] = P.ke * std::log(P.b) / (std::sqrt(2.0 * kPi) * P.sigma) *
+                            (P.omega + (1.0 - std::pow(P.b, -(P.M_energy - 1.0))) / (P.b - 1.0)) * sq;
+            // FP32 build: the constant part sum_excl ke q_i q_j F_E(0) of the exclusion energy
+            if (P.precision == RBSOG_FP32) {
+                double fe0 = 0.0, sx = 0.0;
+                for (int l = 0; l < P.M_energy; ++l) fe0 += w[l];
+                for (int e2 = 0; e2 < d.n_excl; ++e2) sx += d.q[d.excl[2 * e2]] * d.q[d.excl[2 * e2 + 1]];
+                self_e[2 * k + 1] = P.ke * fe0 * sx;
+            }
             // chunks
             first_chunk[k] = (int)chunk_sys.size();
             for (int a0 = 0; a0 < d.n_atoms; a0 += kChunk) {
@@ -460,10 +476,10 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                 me[mol_of[i]].push_back(e2);
             }
             mchunk_first[k] = (int)mchunk_sys.size();
-            for (int m0 = 0; m0 < nm; m0 += 512) {
+            for (int m0 = 0; m0 < nm; m0 += kMolChunk) {
                 mchunk_sys.push_back(k);
                 mchunk_m0.push_back(nmol + m0);
-                mchunk_n.push_back(std::min(512, nm - m0));
+                mchunk_n.push_back(std::min(kMolChunk, nm - m0));
             }
             mchunk_count[k] = (int)mchunk_sys.size() - mchunk_first[k];
             for (int mm = 0; mm < nm; ++mm) {
@@ -485,10 +501,9 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             nmol += nm;
             N += d.n_atoms;
         }
-        c->N = N; c->C = C; c->nmol = nmol;
+        c->N = N; c->C = C; c->nmol = nmol; c->item_cap = item_cap;
         c->nchunks = (int)chunk_sys.size();
         c->nmchunks = (int)mchunk_sys.size();
-        c->nw = std::min(16, std::max(2, (int)std::ceil(avg_cell * 1.25 / 32.0)));
 
         // ---- device buffers
         bool ok = upload(c, c->sys, hsys) && upload(c, c->r, r) && upload(c, c->p, p) && upload(c, c->q, q) &&
@@ -504,7 +519,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                   upload(c, c->bk, bk) && upload(c, c->br0, br0) && upload(c, c->ak, ak) && upload(c, c->at0, at0) &&
                   upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
-                  dalloc(c, c->start, C + 1) && dalloc(c, c->pair_part, (size_t)C * 14) &&
+                  dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
+                  dalloc(c, c->pair_part, (size_t)item_cap * 14) &&
                   dalloc(c, c->lr_out, (size_t)S * 16) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
                   dalloc(c, c->kin_part, (size_t)c->nchunks * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
                   dalloc(c, c->mr, (size_t)S * P.P * 3) && dalloc(c, c->mnr, (size_t)S * P.P * 3) &&
@@ -578,18 +594,17 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         c->b.S = S; c->b.N = N; c->b.C = C; c->b.sub = P.cell_sub; c->b.rc = P.rc; c->b.sys = c->sys;
         c->b.atom_sys = c->atom_sys; c->b.cell_sys = c->cell_sys; c->b.chunk_sys = c->chunk_sys;
         c->b.chunk_a0 = c->chunk_a0; c->b.chunk_n = c->chunk_n; c->b.nchunks = c->nchunks;
+        c->b.item_cap = item_cap;
         c->a.r = c->r; c->a.p = c->p; c->a.F = c->F; c->a.q = c->q; c->a.mass = c->mass; c->a.type = c->type;
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
         c->a.su = c->su; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
-        c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux;
+        c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
         c->m.nmol = nmol; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
         c->m.mchunk_n = c->mchunk_n; c->m.nmchunks = c->nmchunks;
 
-        if (pair_smem_bytes(P.precision, c->nw) + 8192 > 227 * 1024) c->nw = 4;
-        e = prepare_pair(P.precision, c->nw);
-        if (e == cudaSuccess) e = prepare_sampler(P.P);
+        e = prepare_sampler(P.P);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { rbsog_status rr = cuda_fail(c, e, "create"); free_ctx(c); return rr; }
         // the first evaluation (counter 0) primes forces, virial and kinetic tensor
