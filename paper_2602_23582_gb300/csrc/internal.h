@@ -136,5 +136,6 @@ void launch_finalize(const Batch &b, const double *pair_part, const double *lr_o
                      const double *self_energy, const IntegArgs &ia, int do_box_kick,
                      double *sysred, unsigned long long *step, cudaStream_t st);
 cudaError_t prepare_sampler(int P);
+cudaError_t prepare_pair();
 
 }  // namespace rbsog

@@ -28,6 +28,12 @@ namespace {
 
 constexpr int QCAP = 64;    // per-lane queue (power of two); pending <= 32 before a batch
 constexpr int WPB = 4;      // warps (work items) per block
+constexpr int kMaxNb = 128; // neighbour cells of the stencil (125 for cells of r_c/2)
+
+size_t pair_smem(int precision)
+{
+    return (size_t)WPB * (QCAP * 32 * (sizeof(unsigned) + 1) + kMaxNb * (precision == 1 ? 16 : 32));
+}
 
 __device__ __forceinline__ float ex2f(float x)
 {
@@ -139,7 +145,8 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP32 kernel.  Neighbour cell code: (dx + sub) | (dy + sub) << 3 | (dz + sub) << 6.
+// FP32 kernel.  A queued hit carries its neighbour-cell index nb (< 125); the
+// warp keeps the offsets of the (2 sub + 1)^3 neighbour cells in shared memory.
 // ---------------------------------------------------------------------------
 template <int NG>
 __global__ void __launch_bounds__(32 * WPB)
@@ -148,9 +155,11 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
            const float4 *__restrict__ pos4, const float2 *__restrict__ qt, const int *__restrict__ sidx, int sub,
            double *__restrict__ F, double *__restrict__ partial, const PairConstsF pc)
 {
-    __shared__ unsigned queue[WPB][QCAP * 32];
-    __shared__ unsigned char qcode[WPB][QCAP * 32];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
+    unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
+    float4 *off = reinterpret_cast<float4 *>(smem + WPB * QCAP * 32 * sizeof(unsigned)) + warp * kMaxNb;
+    unsigned char *qc = smem + WPB * QCAP * 32 * sizeof(unsigned) + WPB * kMaxNb * sizeof(float4) + warp * QCAP * 32;
     const int it = blockIdx.x * WPB + warp;
     if (it >= n_items) return;
     const int2 item = items[it];
@@ -161,6 +170,11 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     const int lc = gc - d.cell0;
     const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
     const float wx = (float)d.w[0], wy = (float)d.w[1], wz = (float)d.w[2];
+    const int span = 2 * sub + 1;
+    for (int nb = lane; nb < span * span * span; nb += 32)
+        off[nb] = make_float4((nb % span - sub) * wx, ((nb / span) % span - sub) * wy,
+                              (nb / (span * span) - sub) * wz, 0.f);
+    __syncwarp();
     const int i0 = start[gc] + 32 * item.y;
     const int ni = min(32, count[gc] - 32 * item.y);
     const bool vi = lane < ni;
@@ -170,8 +184,6 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     const int moli = vi ? __float_as_int(pi.w) : -0x7fffffff;
     const int ti = __float_as_int(pq.y);
     const float rc2 = pc.rc2;
-    unsigned *q = queue[warp];
-    unsigned char *qc = qcode[warp];
     AccF acc;
     acc.fx = acc.fy = acc.fz = 0.f;
     acc.uc = acc.ul = acc.cuc = acc.cul = 0.f;
@@ -182,19 +194,17 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     auto eval_one = [&](unsigned j, int code) {
         const float4 pj = pos4[j];
         const float2 qj = qt[j];
-        const float ox = (float)((code & 7) - sub) * wx;
-        const float oy = (float)(((code >> 3) & 7) - sub) * wy;
-        const float oz = (float)((code >> 6) - sub) * wz;
-        pair_eval<NG>(pc, (pi.x - ox) - pj.x, (pi.y - oy) - pj.y, (pi.z - oz) - pj.z, pq.x, ti, qj, acc);
+        const float4 o = off[code];
+        pair_eval<NG>(pc, (pi.x - o.x) - pj.x, (pi.y - o.y) - pj.y, (pi.z - o.z) - pj.z, pq.x, ti, qj, acc);
     };
 
-    const int span = 2 * sub + 1;
     for (int nb = 0; nb < span * span * span; ++nb) {
         const int ddx = nb % span - sub, ddy = (nb / span) % span - sub, ddz = nb / (span * span) - sub;
         const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + ddz, n2));
         const int j0 = start[g], nj = count[g];
-        const int code = (ddx + sub) | ((ddy + sub) << 3) | ((ddz + sub) << 6);
-        const float xi = pi.x - ddx * wx, yi = pi.y - ddy * wy, zi = pi.z - ddz * wz;
+        const int code = nb;
+        const float4 o = off[nb];
+        const float xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - o.z;
         for (int jb = 0; jb < nj; jb += 32) {
             const int je = min(jb + 32, nj);
             int j = jb;
@@ -206,7 +216,7 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
                 for (int u = 0; u < 4; ++u) {
                     const float dx = xi - p[u].x, dy = yi - p[u].y, dz = zi - p[u].z;
                     const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < rc2 && __float_as_int(p[u].w) != moli) {
+                    if (vi && r2 < rc2 && __float_as_int(p[u].w) != moli) {
                         const int slot = (tail & (QCAP - 1)) * 32 + lane;
                         q[slot] = (unsigned)(j0 + j + u);
                         qc[slot] = (unsigned char)code;
@@ -218,7 +228,7 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
                 const float4 pj = __ldg(&pos4[j0 + j]);
                 const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2 && __float_as_int(pj.w) != moli) {
+                if (vi && r2 < rc2 && __float_as_int(pj.w) != moli) {
                     const int slot = (tail & (QCAP - 1)) * 32 + lane;
                     q[slot] = (unsigned)(j0 + j);
                     qc[slot] = (unsigned char)code;
@@ -283,9 +293,11 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
            const double4 *__restrict__ posd, const int2 *__restrict__ aux, const int *__restrict__ sidx, int sub,
            double *__restrict__ F, double *__restrict__ partial, const PairConstsD pc)
 {
-    __shared__ unsigned queue[WPB][QCAP * 32];
-    __shared__ unsigned char qcode[WPB][QCAP * 32];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
+    unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
+    double4 *off = reinterpret_cast<double4 *>(smem + WPB * QCAP * 32 * sizeof(unsigned)) + warp * kMaxNb;
+    unsigned char *qc = smem + WPB * QCAP * 32 * sizeof(unsigned) + WPB * kMaxNb * sizeof(double4) + warp * QCAP * 32;
     const int it = blockIdx.x * WPB + warp;
     if (it >= n_items) return;
     const int2 item = items[it];
@@ -296,6 +308,11 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     const int lc = gc - d.cell0;
     const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
     const double wx = d.w[0], wy = d.w[1], wz = d.w[2];
+    const int span = 2 * sub + 1;
+    for (int nb = lane; nb < span * span * span; nb += 32)
+        off[nb] = make_double4((nb % span - sub) * wx, ((nb / span) % span - sub) * wy,
+                               (nb / (span * span) - sub) * wz, 0.0);
+    __syncwarp();
     const int i0 = start[gc] + 32 * item.y;
     const int ni = min(32, count[gc] - 32 * item.y);
     const bool vi = lane < ni;
@@ -303,8 +320,6 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     int2 ai = make_int2(-0x7fffffff, 0);
     if (vi) { pi = posd[i0 + lane]; ai = aux[i0 + lane]; }
     const double rc2 = pc.rc2;
-    unsigned *q = queue[warp];
-    unsigned char *qc = qcode[warp];
     AccD acc;
     acc.fx = acc.fy = acc.fz = 0.0;
     acc.uc = acc.ul = 0.0;
@@ -315,26 +330,24 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     auto eval_one = [&](unsigned j, int code) {
         const double4 pj = posd[j];
         const int tj = aux[j].y;
-        const double ox = (double)((code & 7) - sub) * wx;
-        const double oy = (double)(((code >> 3) & 7) - sub) * wy;
-        const double oz = (double)((code >> 6) - sub) * wz;
-        pair_eval(pc, (pi.x - ox) - pj.x, (pi.y - oy) - pj.y, (pi.z - oz) - pj.z, pi.w, ai.y, pj.w, tj, acc);
+        const double4 o = off[code];
+        pair_eval(pc, (pi.x - o.x) - pj.x, (pi.y - o.y) - pj.y, (pi.z - o.z) - pj.z, pi.w, ai.y, pj.w, tj, acc);
     };
 
-    const int span = 2 * sub + 1;
     for (int nb = 0; nb < span * span * span; ++nb) {
         const int ddx = nb % span - sub, ddy = (nb / span) % span - sub, ddz = nb / (span * span) - sub;
         const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + ddz, n2));
         const int j0 = start[g], nj = count[g];
-        const int code = (ddx + sub) | ((ddy + sub) << 3) | ((ddz + sub) << 6);
-        const double xi = pi.x - ddx * wx, yi = pi.y - ddy * wy, zi = pi.z - ddz * wz;
+        const int code = nb;
+        const double4 o = off[nb];
+        const double xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - o.z;
         for (int jb = 0; jb < nj; jb += 32) {
             const int je = min(jb + 32, nj);
             for (int j = jb; j < je; ++j) {
                 const double4 pj = posd[j0 + j];
                 const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
                 const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2 && aux[j0 + j].x != ai.x) {
+                if (vi && r2 < rc2 && aux[j0 + j].x != ai.x) {
                     const int slot = (tail & (QCAP - 1)) * 32 + lane;
                     q[slot] = (unsigned)(j0 + j);
                     qc[slot] = (unsigned char)code;
@@ -383,19 +396,32 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     }
 }
 
+// Opt the pair kernels into their dynamic shared memory (once per context,
+// outside any stream capture).
+cudaError_t prepare_pair()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_pair_f32<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(0));
+    return e;
+}
+
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, double *partial, cudaStream_t st)
 {
     const int blocks = (b.item_cap + WPB - 1) / WPB;
+    const size_t sm = pair_smem(precision);
     if (precision == 1) {
         if (cf.M == 10)
-            k_pair_f32<10><<<blocks, 32 * WPB, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
+            k_pair_f32<10><<<blocks, 32 * WPB, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
                                                         a.pos4, a.qt, a.sidx, b.sub, a.F, partial, cf);
         else
-            k_pair_f32<0><<<blocks, 32 * WPB, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
+            k_pair_f32<0><<<blocks, 32 * WPB, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
                                                        a.pos4, a.qt, a.sidx, b.sub, a.F, partial, cf);
     } else {
-        k_pair_f64<<<blocks, 32 * WPB, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap, a.posd,
+        k_pair_f64<<<blocks, 32 * WPB, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap, a.posd,
                                                 a.aux, a.sidx, b.sub, a.F, partial, cd);
     }
 }

@@ -605,6 +605,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         c->m.mchunk_n = c->mchunk_n; c->m.nmchunks = c->nmchunks;
 
         e = prepare_sampler(P.P);
+        if (e == cudaSuccess) e = prepare_pair();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { rbsog_status rr = cuda_fail(c, e, "create"); free_ctx(c); return rr; }
         // the first evaluation (counter 0) primes forces, virial and kinetic tensor

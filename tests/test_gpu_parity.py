@@ -204,7 +204,8 @@ def test_structure_factor_stateless():
 
 
 def test_box_too_small_is_rejected():
-    s = W.random_charges(n=50, box=(25.0, 30.0, 30.0), seed=1)
+    # below 2.5 r_c even cells of r_c/2 cannot hold the 5 x 5 x 5 stencil
+    s = W.random_charges(n=50, box=(24.0, 30.0, 30.0), seed=1)
     p = R.rbsog_default_params(10.0)
     with pytest.raises(R.RbsogError) as e:
         R.Context([s], p)
