@@ -97,6 +97,14 @@ typedef struct {
     int coupling;           /* RBSOG_COUPLE_* */
     int cell_sub;           /* cells per cutoff length along an axis: 1 or 2; 0 = choose
                                (2 when a box edge is below 3.3 r_c, else 1) */
+    int thermo_every;       /* inside rbsog_run / rbsog_run_async, energies (and the
+                               Coulomb/LJ split of the short-range virial) are evaluated
+                               on the last step of each call and on steps whose counter
+                               is a multiple of thermo_every (0: last step only); the
+                               other steps compute forces and the total virial only,
+                               which is all the dynamics uses.  rbsog_step always
+                               evaluates energies.  Forces and the total virial do not
+                               depend on this setting.  Default 1 (every step). */
 } rbsog_params;
 
 typedef struct {

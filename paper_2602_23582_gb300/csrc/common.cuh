@@ -40,6 +40,9 @@ struct DevSys {
     double Sr, Snr;       // normalizers (eqs. Sr, Snr)
     double Lh[3];         // box after the first half drift (integrator)
     double Lp[3];         // box before the step (integrator)
+    double sc1[3], sc2[3];   // drift scalings Lh / Lp and L / Lh of the current step
+    double isc1[3], isc2[3]; // their inverses Lp / Lh and Lh / L
+    double invL[3];          // 1 / L after the step
     int ncell[3];         // current cells per axis
     int ncap[3];          // allocated cells per axis
     int cell0;            // first global cell
@@ -51,6 +54,7 @@ struct DevSys {
     int flags;
     int item0, item_cap;  // pair-kernel work items: [item0, item0 + item_cap)
     int nitems;           // items of the current cell list
+    int ntypes, lj0;      // LJ types of the system and its first entry in the context's LJ table
     unsigned long long rng_id;   // second word of the Philox key
 };
 
@@ -131,6 +135,32 @@ __device__ inline double block_sum(double v, double *smem)
     for (int i = 0; i < nw; ++i) t += smem[i];
     __syncthreads();
     return t;
+}
+
+// Block-wide sums of V FP64 values per thread (NT threads), written to
+// out[0..V) (fixed order: deterministic).  FP64 arithmetic is slow on
+// this GPU, so the sums run lane-parallel (each FP64 instruction adds for 32
+// lanes) instead of as a shuffle tree.  smem: V * (NT + 1) + 4 V doubles;
+// every thread of the block must call it.
+template <int V, int NT>
+__device__ inline void block_reduce_lanes(const double (&v)[V], double *smem, double *out)
+{
+    static_assert(NT % 4 == 0, "NT must be a multiple of 4");
+    constexpr int G = 4, SEG = NT / G, ROW = NT + 1;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < V; ++k) smem[k * ROW + t] = v[k];
+    __syncthreads();
+    double *s2 = smem + V * ROW;
+    for (int idx = t; idx < V * G; idx += NT) {
+        const int k = idx / G, g = idx % G;
+        const double *p = smem + k * ROW + g * SEG;
+        double a = 0.0;
+        for (int i = 0; i < SEG; ++i) a += p[i];
+        s2[k * G + g] = a;
+    }
+    __syncthreads();
+    for (int k = t; k < V; k += NT) out[k] = (s2[k * G] + s2[k * G + 1]) + (s2[k * G + 2] + s2[k * G + 3]);
 }
 
 }  // namespace rbsog

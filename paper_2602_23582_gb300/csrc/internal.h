@@ -14,24 +14,35 @@ struct SogConsts {
     double w[kMaxGauss], s[kMaxGauss], wt[kMaxGauss], st[kMaxGauss];
 };
 
-struct PairConstsF {           // FP32 pair kernel constants
-    int M, ME, ntypes;
+constexpr int kTail = 7;        // degree (in u = r^2) of the Taylor tail of the wide Gaussians
+
+// FP32 pair kernel constants.  Gaussians with s_l >= 2.5 r_c vary little over
+// r <= r_c: their sum is a Taylor polynomial in u = r^2 (remainder below
+// 0.16^8 / 8! of w_l); the narrower ones are exponentials.  The energy path
+// keeps its coefficients as FP32 hi + lo pairs: a rounding shared by every
+// pair would otherwise be multiplied by sum q_i q_j / r, which is far larger
+// than the short-range energy itself.
+struct PairConstsF {
+    int M, ME;
+    int nff, nfe;               // exponentials for the force (l < nff) and the energy (l < nfe)
     float rc2, ke;
-    float beta[kMaxGauss];      // log2(e) / s_l^2
+    float rc2_hi, rc2_lo;       // r_c^2 (1 +- 1e-5): pairs in between are decided in FP64
+    double rc2d;                // r_c^2 in FP64
+    float beta[kMaxGauss];      // log2(e) / s~_l^2 (force)
     float wt[kMaxGauss];        // w~_l
-    float w[kMaxGauss];         // w_l
-    float lj_a[kMaxTypes * kMaxTypes];   // 4 eps sig^12
-    float lj_b[kMaxTypes * kMaxTypes];   // 4 eps sig^6
+    float tt[kTail + 1];        // sum_{nff <= l < M} w~_l e^{-u / s~_l^2} = sum_k tt[k] u^k
+    float be_hi[kMaxGauss], be_lo[kMaxGauss];   // log2(e) / s_l^2 (energy)
+    float w_hi[kMaxGauss], w_lo[kMaxGauss];     // w_l
+    float te[kTail + 1];        // energy tail without its constant (te[0] = 0)
+    double te0;                 // sum_{nfe <= l < ME} w_l, applied in FP64 to the per-atom sum of q_i q_j
 };
 
 struct PairConstsD {           // FP64 pair kernel constants
-    int M, ME, ntypes;
+    int M, ME;
     double rc2, ke;
     double inv_s2[kMaxGauss];   // 1 / s_l^2
     double wt[kMaxGauss];
     double w[kMaxGauss];
-    double lj_a[kMaxTypes * kMaxTypes];
-    double lj_b[kMaxTypes * kMaxTypes];
 };
 
 // Everything a kernel needs about the batch of systems.
@@ -53,7 +64,8 @@ struct AtomArrays {
     double *r, *p, *F;          // [3N]
     const double *q, *mass;     // [N]
     const int *type, *mol;      // [N]
-    int *cell, *rank;           // [N]
+    int *cell;                  // [N]
+    int *rank;                  // [N] rank in its cell after binning; cell-sorted position after sorting
     float4 *locf;               // [N] cell-local coords + mol bits (FP32)
     double4 *locd;              // [N] cell-local coords + q (FP64)
     uint4 *su;                  // [N] fixed-point fractional coords + q bits
@@ -64,6 +76,12 @@ struct AtomArrays {
     double4 *posd;              // [N] sorted, FP64
     int2 *aux;                  // [N] sorted (mol, type)
     int2 *items;                // [item_cap] (cell, group) pair work items
+    float4 *fpart4;             // [(2 sub + 1) N] pair forces per dz plane, cell-sorted (FP32 build)
+    double4 *fpartd;            // same storage, FP64 build
+    // LJ table: system s owns entries [lj0, lj0 + ntypes^2) (DevSys), entry
+    // ti * ntypes + tj = (4 eps sig^12, 4 eps sig^6); ljf_lo: FP32 remainders
+    const float2 *ljf, *ljf_lo;
+    const double2 *ljd;
 };
 
 // ---- k_bin.cu
@@ -73,9 +91,15 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
 void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st);
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 
-// ---- k_pair.cu: partial = per work item (Ucoul, Ulj, Wc[6], Wl[6]) as 14 doubles
+// ---- k_pair.cu: partial = per block of kPairWarps work units (item x dz plane):
+// (Ucoul, Ulj, Wc[6], Wl[6], W[6]) as kPairRec doubles; energies and the
+// Coulomb/LJ split only when `energy` is set (W, the total, always).  Each
+// system's item range is a multiple of kPairWarps items, so a block never
+// mixes systems.
+constexpr int kPairWarps = 4;
+constexpr int kPairRec = 20;
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
-                 const PairConstsD &cd, double *partial, cudaStream_t st);
+                 const PairConstsD &cd, int energy, double *partial, cudaStream_t st);
 
 // ---- k_sampler.cu
 struct SamplerArgs {
@@ -121,11 +145,15 @@ void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const S
 // ---- k_integrate.cu
 struct IntegArgs {
     double dt, T, Pext, gamma, gamma_box, kB, ftm2v, nktv2p;
+    double c_atom;                    // exp(-gamma dt)
+    const double *inv_m, *sdv;        // per atom: 1 / m, sqrt((1 - c^2) m kB T ftm2v)
+    int noise_f32;                    // 1: Gaussian noise drawn in FP32 (FP32 build)
     uint64_t seed;
     const unsigned long long *step;   // device counter of the last evaluation; a step uses *step + 1
 };
 void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st);
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st);
+constexpr int kKinSplit = 4;   // kinetic partials per atom chunk
 void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int kick,
                          double *kin_part, cudaStream_t st);
 // per-system reduction of every partial into sysred[S x kRed]; advances *step

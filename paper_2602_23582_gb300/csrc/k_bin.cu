@@ -17,13 +17,16 @@ __global__ void k_box_prep(DevSys *sys, int S, int sub, double rc)
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     DevSys &d = sys[s];
-    int minc = 2 * sub + 1;
+    const int minc = 2 * sub + 1;
     for (int a = 0; a < 3; ++a) {
         double L = d.L[a];
-        int n = (int)floor(__ddiv_rn(__dmul_rn(L, (double)sub), rc));
-        if (!(L > 0.0) || n < minc) d.flags |= FLAG_BOX;
+        double x = floor(__ddiv_rn(__dmul_rn(L, (double)sub), rc));
+        // a box that is too small, not finite or beyond the allocated grid is
+        // flagged; the grid stays within [2 sub + 1, ncap] so that every
+        // neighbour-cell index remains valid while the step is discarded
+        if (!(L > 0.0) || !(x < 1e9) || x < (double)minc) d.flags |= FLAG_BOX;
+        int n = (x < 1e9 && x >= (double)minc) ? (int)x : minc;
         if (n > d.ncap[a]) n = d.ncap[a];
-        if (n < 1) n = 1;
         d.ncell[a] = n;
         d.w[a] = L / n;
     }
@@ -67,6 +70,7 @@ __global__ void k_bin(const DevSys *__restrict__ sys, const int *__restrict__ at
         int n = d.ncell[a];
         int k = (int)floor(__dmul_rn(s, (double)n));
         if (k > n - 1) k = n - 1;
+        if (!(k >= 0)) k = 0;        // non-finite coordinates (flagged by the step checks)
         c[a] = k;
         sf[a] = s;
         xl[a] = s * L - k * d.w[a];
@@ -161,7 +165,7 @@ constexpr int kSortWarps = 4;
 
 __global__ void __launch_bounds__(32 * kSortWarps)
 k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C, int *__restrict__ sidx,
-            const float4 *__restrict__ locf, const double4 *__restrict__ locd,
+            int *__restrict__ rank, const float4 *__restrict__ locf, const double4 *__restrict__ locd,
             const double *__restrict__ q, const int *__restrict__ type, const int *__restrict__ mol,
             float4 *__restrict__ pos4, float2 *__restrict__ qt, double4 *__restrict__ posd,
             int2 *__restrict__ aux, int precision)
@@ -193,6 +197,7 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
     for (int k = lane; k < n; k += 32) {
         int i = s[k];
         sidx[base + k] = i;
+        rank[i] = base + k;          // from here on: cell-sorted position of atom i
         if (precision == 1) {
             pos4[base + k] = locf[i];
             qt[base + k] = make_float2((float)q[i], __int_as_float(type[i]));
@@ -207,7 +212,7 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 {
     k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(a.cell, a.rank, a.start, a.sidx, b.N);
     k_cell_sort<<<(b.C + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, st>>>(
-        a.start, a.count, b.C, a.sidx, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
+        a.start, a.count, b.C, a.sidx, a.rank, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
 }
 
 }  // namespace rbsog

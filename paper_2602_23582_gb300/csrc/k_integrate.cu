@@ -81,6 +81,11 @@ __global__ void k_box_half(DevSys *sys, int S, const IntegArgs ia, const double 
         int g = axis_group(d.coupling, a);
         double v = d.Mbox[g] > 0.0 ? d.ph[g] / d.Mbox[g] : 0.0;
         d.L[a] = d.Lh[a] + v * tau;
+        d.sc1[a] = d.Lh[a] / d.Lp[a];
+        d.sc2[a] = d.L[a] / d.Lh[a];
+        d.isc1[a] = d.Lp[a] / d.Lh[a];
+        d.isc2[a] = d.Lh[a] / d.L[a];
+        d.invL[a] = 1.0 / d.L[a];
     }
 }
 
@@ -89,41 +94,56 @@ void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, 
     k_box_half<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, ia, sysred);
 }
 
-// Atom part of B (first half), A, O, A and the wrap.
+// Atom part of B (first half), A, O, A and the wrap.  Per-system drift
+// scalings come from k_box_half; 1/m and the noise amplitude are per-atom
+// constants.  NF32: the Gaussian noise is drawn in FP32 (FP32 build), else in
+// FP64 (Box-Muller on the same Philox words as the CPU reference).
+template <bool NF32>
 __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys, int N,
                               double *__restrict__ r, double *__restrict__ p, const double *__restrict__ F,
-                              const double *__restrict__ mass, const IntegArgs ia)
+                              const IntegArgs ia)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int s = atom_sys[i];
     const DevSys &d = sys[s];
-    const double m = mass[i], tau = 0.5 * ia.dt;
+    const double im = ia.inv_m[i], tau = 0.5 * ia.dt, kick = 0.5 * ia.dt * ia.ftm2v;
     double x[3], v[3];
     for (int a = 0; a < 3; ++a) {
         x[a] = r[3 * i + a];
-        v[a] = p[3 * i + a] + 0.5 * ia.dt * F[3 * i + a] * ia.ftm2v;
+        v[a] = p[3 * i + a] + kick * F[3 * i + a];
     }
     for (int a = 0; a < 3; ++a) {
-        double sc = d.Lh[a] / d.Lp[a];
-        x[a] = sc * x[a] + v[a] / m * tau;
-        v[a] = v[a] / sc;
+        x[a] = d.sc1[a] * x[a] + v[a] * im * tau;
+        v[a] = v[a] * d.isc1[a];
     }
     uint64_t wds[4];
     draw4(ia.seed, d.rng_id, *ia.step + 1, PUR_ATOM, (uint64_t)(i - d.atom0), wds);
     double z[4];
-    box_muller2(wds[0], wds[1], z[0], z[1]);
-    box_muller2(wds[2], wds[3], z[2], z[3]);
-    const double c = exp(-ia.gamma * ia.dt);
-    const double sdv = sqrt((1.0 - c * c) * m * ia.kB * ia.T * ia.ftm2v);
+    if (NF32) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float u1 = ((float)(wds[2 * k] >> 40) + 0.5f) * 5.9604644775390625e-8f;   // 2^-24
+            const float u2 = ((float)(wds[2 * k + 1] >> 40) + 0.5f) * 5.9604644775390625e-8f;
+            const float rr = sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+            z[2 * k] = (double)(rr * cs);
+            z[2 * k + 1] = (double)(rr * sn);
+        }
+    } else {
+        box_muller2(wds[0], wds[1], z[0], z[1]);
+        box_muller2(wds[2], wds[3], z[2], z[3]);
+    }
+    const double c = ia.c_atom, sdv = ia.sdv[i];
     for (int a = 0; a < 3; ++a) v[a] = c * v[a] + sdv * z[a];
     for (int a = 0; a < 3; ++a) {
-        double sc = d.L[a] / d.Lh[a];
-        x[a] = sc * x[a] + v[a] / m * tau;
-        v[a] = v[a] / sc;
-        double L = d.L[a];
-        x[a] -= L * floor(x[a] / L);
+        x[a] = d.sc2[a] * x[a] + v[a] * im * tau;
+        v[a] = v[a] * d.isc2[a];
+        const double L = d.L[a];
+        x[a] -= L * floor(x[a] * d.invL[a]);
         if (x[a] >= L) x[a] -= L;
+        if (x[a] < 0.0) x[a] += L;
         r[3 * i + a] = x[a];
         p[3 * i + a] = v[a];
     }
@@ -131,20 +151,25 @@ __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restr
 
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st)
 {
-    k_atom_update<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, a.mass, ia);
+    if (ia.noise_f32)
+        k_atom_update<true><<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia);
+    else
+        k_atom_update<false><<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia);
 }
 
-// Second half kick (optional) and the kinetic tensor per atom chunk:
-// kin_part[chunk][6] = sum p (x) p / m (kcal/mol).
-__global__ void __launch_bounds__(256)
+// Second half kick (optional) and the kinetic tensor per quarter of an atom
+// chunk: kin_part[chunk][kKinSplit][6] = sum p (x) p / m (kcal/mol).
+__global__ void __launch_bounds__(kChunk / kKinSplit)
 k_kick_kinetic(const int *__restrict__ chunk_a0, const int *__restrict__ chunk_n, double *__restrict__ p,
-               const double *__restrict__ F, const double *__restrict__ mass, double kick, double mvv2e,
+               const double *__restrict__ F, const double *__restrict__ inv_m, double kick, double mvv2e,
                double *__restrict__ kin_part)
 {
-    __shared__ double red[32];
+    __shared__ double red[6 * (kChunk / kKinSplit + 1) + 24];
     const int c = blockIdx.x, a0 = chunk_a0[c], na = chunk_n[c];
     double k6[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+    constexpr int per = kChunk / kKinSplit;
+    const int k_end = min(na, (int)(blockIdx.y + 1) * per);
+    for (int k = blockIdx.y * per + threadIdx.x; k < k_end; k += blockDim.x) {
         const int i = a0 + k;
         double v[3];
         for (int a = 0; a < 3; ++a) {
@@ -154,21 +179,19 @@ k_kick_kinetic(const int *__restrict__ chunk_a0, const int *__restrict__ chunk_n
                 p[3 * i + a] = v[a];
             }
         }
-        const double im = 1.0 / mass[i];
+        const double im = inv_m[i];
         k6[0] += v[0] * v[0] * im; k6[1] += v[1] * v[1] * im; k6[2] += v[2] * v[2] * im;
         k6[3] += v[0] * v[1] * im; k6[4] += v[0] * v[2] * im; k6[5] += v[1] * v[2] * im;
     }
-    for (int a = 0; a < 6; ++a) {
-        double t = block_sum(k6[a], red);
-        if (threadIdx.x == 0) kin_part[(size_t)c * 6 + a] = t * mvv2e;
-    }
+    for (int a = 0; a < 6; ++a) k6[a] *= mvv2e;
+    block_reduce_lanes<6, kChunk / kKinSplit>(k6, red, kin_part + ((size_t)c * kKinSplit + blockIdx.y) * 6);
 }
 
 void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int do_kick,
                          double *kin_part, cudaStream_t st)
 {
     const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0;
-    k_kick_kinetic<<<b.nchunks, 256, 0, st>>>(b.chunk_a0, b.chunk_n, a.p, a.F, a.mass, kick, 1.0 / ia.ftm2v,
+    k_kick_kinetic<<<dim3(b.nchunks, kKinSplit), kChunk / kKinSplit, 0, st>>>(b.chunk_a0, b.chunk_n, a.p, a.F, ia.inv_m, kick, 1.0 / ia.ftm2v,
                                               kin_part);
 }
 
@@ -177,62 +200,63 @@ void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &i
 //  [15..20] W short Coulomb, [21..26] W^F,r*, [27..32] W^F,nr*, [33..38] W LJ,
 //  [39..44] W bonded + exclusions, [45..50] K, [51] V, [52..54] L,
 //  [55] nD, [56] acc r, [57] acc nr, [58] flags, [59..61] box momenta.
-__global__ void __launch_bounds__(128)
+constexpr int kFinThreads = 128;
+
+__global__ void __launch_bounds__(kFinThreads)
 k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__restrict__ lr_out,
            const double *__restrict__ mol_part, const int *__restrict__ mchunk_first,
            const int *__restrict__ mchunk_count, const double *__restrict__ kin_part,
            const int *__restrict__ chunk_first, const int *__restrict__ chunk_count,
            const double *__restrict__ self_energy, const IntegArgs ia, int do_box_kick,
-           double *__restrict__ sysred, unsigned long long *step)
+           double *__restrict__ sysred, unsigned long long *step, int span)
 {
-    constexpr int NV = 35;           // 14 pair + 15 molecule + 6 kinetic partial sums
-    __shared__ double wsum[NV][4];   // 128 threads = 4 warps
-    __shared__ double acc[64];
-    const int s = blockIdx.x, tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    constexpr int NV = kPairRec + 21;   // pair records + 15 molecule + 6 kinetic partial sums
+    __shared__ double buf[NV * (kFinThreads + 1) + 4 * NV];
+    __shared__ double acc[NV];
+    const int s = blockIdx.x, tid = threadIdx.x;
     DevSys &d = sys[s];
     double *o = sysred + (size_t)s * kRed;
     double v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = 0.0;
-    const int ni = d.nitems;
-    for (int c = tid; c < ni; c += blockDim.x) {
-        const double *pp = pair_part + (size_t)(d.item0 + c) * 14;
+    // pair records: one per block of kPairWarps units (items x dz planes)
+    const int b0 = d.item0 * span / kPairWarps;
+    const int nb = (d.nitems * span + kPairWarps - 1) / kPairWarps;
+    for (int c = tid; c < nb; c += blockDim.x) {
+        const double *pp = pair_part + (size_t)(b0 + c) * kPairRec;
 #pragma unroll
-        for (int k = 0; k < 14; ++k) v[k] += pp[k];
+        for (int k = 0; k < kPairRec; ++k) v[k] += pp[k];
     }
+    constexpr int M0 = kPairRec, K0 = kPairRec + 15;
     for (int c = tid; c < mchunk_count[s]; c += blockDim.x) {
         const double *pp = mol_part + (size_t)(mchunk_first[s] + c) * 15;
 #pragma unroll
-        for (int k = 0; k < 15; ++k) v[14 + k] += pp[k];
+        for (int k = 0; k < 15; ++k) v[M0 + k] += pp[k];
     }
-    for (int c = tid; c < chunk_count[s]; c += blockDim.x) {
-        const double *pp = kin_part + (size_t)(chunk_first[s] + c) * 6;
+    for (int c = tid; c < chunk_count[s] * kKinSplit; c += blockDim.x) {
+        const double *pp = kin_part + ((size_t)chunk_first[s] * kKinSplit + c) * 6;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[29 + k] += pp[k];
+        for (int k = 0; k < 6; ++k) v[K0 + k] += pp[k];
     }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double x = warp_sum(v[k]);
-        if (lane == 0) wsum[k][warp] = x;
-    }
-    __syncthreads();
-    if (tid < NV) acc[tid] = wsum[tid][0] + wsum[tid][1] + wsum[tid][2] + wsum[tid][3];
+    block_reduce_lanes<NV, kFinThreads>(v, buf, acc);
     __syncthreads();
     if (tid != 0) return;
     const double *lr = lr_out + (size_t)s * 16;
     const double us = self_energy[2 * s];        // U_self (App. A)
     const double uxc = self_energy[2 * s + 1];   // FP32 build: sum over exclusions of ke q_i q_j F_E(0)
+    // energies and the Coulomb/LJ virial split come from the pair kernel only
+    // on energy steps (zero otherwise); the total short-range virial always
     double e[9];
     e[0] = acc[0];                 // U^N Coulomb
     e[1] = lr[0];                  // U^F*
     e[2] = us;
-    e[3] = acc[14] - uxc;          // exclusions
+    e[3] = acc[M0] - uxc;          // exclusions
     e[4] = acc[1];                 // LJ
-    e[5] = acc[15];                // bonds
-    e[6] = acc[16];                // angles
+    e[5] = acc[M0 + 1];            // bonds
+    e[6] = acc[M0 + 2];            // angles
     e[7] = e[0] + e[1] - e[2] + e[3];
     double K[6];
-    for (int a = 0; a < 6; ++a) K[a] = acc[29 + a];
+    for (int a = 0; a < 6; ++a) K[a] = acc[K0 + a];
     e[8] = 0.5 * (K[0] + K[1] + K[2]);
     double Wc[6], Wr[6], Wnr[6], Wl[6], Wb[6], W[6];
     for (int a = 0; a < 6; ++a) {
@@ -240,8 +264,8 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
         Wl[a] = acc[8 + a];
         Wr[a] = a < 3 ? lr[1] : 0.0;
         Wnr[a] = lr[2 + a];
-        Wb[a] = acc[17 + a] + acc[23 + a];
-        W[a] = Wc[a] + Wr[a] + Wnr[a] + Wl[a] + Wb[a];
+        Wb[a] = acc[M0 + 3 + a] + acc[M0 + 9 + a];
+        W[a] = acc[14 + a] + Wr[a] + Wnr[a] + Wb[a];
     }
     bool finite = true;
     for (int a = 0; a < 9; ++a) { o[a] = e[a]; finite = finite && isfinite(e[a]); }
@@ -272,8 +296,9 @@ void launch_finalize(const Batch &b, const double *pair_part, const double *lr_o
                      const IntegArgs &ia, int do_box_kick, double *sysred, unsigned long long *step,
                      cudaStream_t st)
 {
-    k_finalize<<<b.S, 128, 0, st>>>(b.sys, pair_part, lr_out, mol_part, mchunk_first, mchunk_count, kin_part,
-                                    chunk_first, chunk_count, self_energy, ia, do_box_kick, sysred, step);
+    k_finalize<<<b.S, kFinThreads, 0, st>>>(b.sys, pair_part, lr_out, mol_part, mchunk_first, mchunk_count,
+                                            kin_part, chunk_first, chunk_count, self_energy, ia, do_box_kick,
+                                            sysred, step, 2 * b.sub + 1);
     k_step_advance<<<1, 1, 0, st>>>(step);
 }
 

@@ -137,13 +137,16 @@ void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D,
 // One block per system: rho = sum of chunk partials (fixed order), estimators,
 // per-mode force coefficients.  lr_out[s][16] = {U^F*, V P^F,r* (scalar),
 // V P^F,nr* xx yy zz xy xz yz, Sr, Snr}.
-__global__ void __launch_bounds__(256)
+constexpr int kEstThreads = 128;
+
+__global__ void __launch_bounds__(kEstThreads)
 k_estimate(DevSys *sys, const int *__restrict__ first_chunk, const int *__restrict__ nchunk_sys,
            const int *__restrict__ D_all, const int *__restrict__ cr_all, const int *__restrict__ cnr_all,
            int Dcap, int P, double ke, const double *__restrict__ part, double *__restrict__ rho_all,
            ModeCoef *__restrict__ coef_all, double *__restrict__ lr_out)
 {
-    __shared__ double red[32];
+    __shared__ double red[7 * (kEstThreads + 1) + 28];
+    __shared__ double sums[7];
     const int s = blockIdx.x;
     DevSys &d = sys[s];
     const int nD = d.nD, c0 = first_chunk[s], nc = nchunk_sys[s];
@@ -154,10 +157,16 @@ k_estimate(DevSys *sys, const int *__restrict__ first_chunk, const int *__restri
     double ar = 0.0, b[6] = {0, 0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < nD; k += blockDim.x) {
         double re = 0.0, im = 0.0;
-        for (int c = 0; c < nc; ++c) {
-            re += part[((size_t)(c0 + c) * Dcap + k) * 2];
-            im += part[((size_t)(c0 + c) * Dcap + k) * 2 + 1];
+        const double2 *pk = reinterpret_cast<const double2 *>(part) + (size_t)c0 * Dcap + k;
+        int c = 0;
+        for (; c + 8 <= nc; c += 8) {          // loads issued together, sums in chunk order
+            double2 t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = pk[(size_t)(c + u) * Dcap];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { re += t[u].x; im += t[u].y; }
         }
+        for (; c < nc; ++c) { const double2 t = pk[(size_t)c * Dcap]; re += t.x; im += t.y; }
         rho[2 * k] = re;
         rho[2 * k + 1] = im;
         double kv[3];
@@ -176,13 +185,14 @@ k_estimate(DevSys *sys, const int *__restrict__ first_chunk, const int *__restri
         mc.pad = 0;
         coef[k] = mc;
     }
-    ar = block_sum(ar, red);
-    for (int a = 0; a < 6; ++a) b[a] = block_sum(b[a], red);
+    const double v7[7] = {ar, b[0], b[1], b[2], b[3], b[4], b[5]};
+    block_reduce_lanes<7, kEstThreads>(v7, red, sums);
+    __syncthreads();
     if (threadIdx.x == 0) {
         double *o = lr_out + (size_t)s * 16;
-        o[0] = ke * d.Sr / (4.0 * V * P) * ar;
+        o[0] = ke * d.Sr / (4.0 * V * P) * sums[0];
         o[1] = o[0];
-        for (int a = 0; a < 6; ++a) o[2 + a] = -ke * d.Snr / (8.0 * V * P) * b[a];
+        for (int a = 0; a < 6; ++a) o[2 + a] = -ke * d.Snr / (8.0 * V * P) * sums[1 + a];
         o[8] = d.Sr;
         o[9] = d.Snr;
     }
@@ -192,116 +202,121 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
                      const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
                      double *rho, ModeCoef *coef, double *lr_out, cudaStream_t st)
 {
-    k_estimate<<<b.S, 256, 0, st>>>(b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho,
+    k_estimate<<<b.S, kEstThreads, 0, st>>>(b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho,
                                     coef, lr_out);
 }
 
-// Long-range force (eq. f_approx) added to F.  One block per atom chunk; the
-// system's mode coefficients are staged in shared memory in tiles.
+// Force assembly: F_i = sum over the pair kernel's dz-plane partials (fixed
+// order) + q_i sum_d alpha_d k_d Im(e^{-i k_d.r_i} rho_d) (eq. f_approx).
+// Molecule terms are added afterwards by k_mol.  Blocks of kLrAtoms atoms of
+// one chunk (grid: chunks x kChunk / kLrAtoms); the system's mode
+// coefficients are staged in shared memory in tiles.
 constexpr int kModeTile = 256;
+constexpr int kLrAtoms = 128;
 
 template <bool F32>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kLrAtoms)
 k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
            const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
            const double *__restrict__ q, const ModeCoef *__restrict__ coef_all, int Dcap,
+           const int *__restrict__ pos_sorted, const void *__restrict__ fpart, int nparts, int N,
            double *__restrict__ F)
 {
-    __shared__ float4 tf[kModeTile];      // a (FP32)
-    __shared__ float2 tr[kModeTile];      // re, im
+    __shared__ float4 tf[F32 ? kModeTile : 1];      // a (FP32)
+    __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
     __shared__ int4 tm[kModeTile];
     __shared__ double td[F32 ? 1 : kModeTile][5];
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int nD = d.nD, a0 = chunk_a0[c], na = chunk_n[c];
     const ModeCoef *coef = coef_all + (size_t)s * Dcap;
-    constexpr int PER = kChunk / 256;
-    float fx[PER], fy[PER], fz[PER];
-    double gx[PER], gy[PER], gz[PER];
-    uint4 v[PER];
-    double sx[PER], sy[PER], sz[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        fx[u] = fy[u] = fz[u] = 0.f;
-        gx[u] = gy[u] = gz[u] = 0.0;
-        const int k = threadIdx.x + u * 256;
-        if (k < na) {
-            const int i = a0 + k;
-            if (F32) v[u] = su[i];
-            else { sx[u] = r[3 * i] / d.L[0]; sy[u] = r[3 * i + 1] / d.L[1]; sz[u] = r[3 * i + 2] / d.L[2]; }
-        }
-    }
+    const int k = blockIdx.y * kLrAtoms + threadIdx.x;
+    if (blockIdx.y * kLrAtoms >= na) return;          // whole block beyond the chunk
+    const bool act = k < na;
+    const int i = a0 + (act ? k : 0);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    if (F32) v = su[i];
+    else { sx = r[3 * i] / d.L[0]; sy = r[3 * i + 1] / d.L[1]; sz = r[3 * i + 2] / d.L[2]; }
     for (int t0 = 0; t0 < nD; t0 += kModeTile) {
         const int nt = min(kModeTile, nD - t0);
         __syncthreads();
-        for (int k = threadIdx.x; k < nt; k += blockDim.x) {
-            const ModeCoef &mc = coef[t0 + k];
+        for (int u = threadIdx.x; u < nt; u += blockDim.x) {
+            const ModeCoef &mc = coef[t0 + u];
             if (F32) {
-                tf[k] = make_float4((float)mc.a[0], (float)mc.a[1], (float)mc.a[2], 0.f);
-                tr[k] = make_float2((float)mc.re, (float)mc.im);
+                tf[u] = make_float4((float)mc.a[0], (float)mc.a[1], (float)mc.a[2], 0.f);
+                tr[u] = make_float2((float)mc.re, (float)mc.im);
             } else {
-                td[k][0] = mc.a[0]; td[k][1] = mc.a[1]; td[k][2] = mc.a[2];
-                td[k][3] = mc.re; td[k][4] = mc.im;
+                td[u][0] = mc.a[0]; td[u][1] = mc.a[1]; td[u][2] = mc.a[2];
+                td[u][3] = mc.re; td[u][4] = mc.im;
             }
-            tm[k] = make_int4(mc.m[0], mc.m[1], mc.m[2], 0);
+            tm[u] = make_int4(mc.m[0], mc.m[1], mc.m[2], 0);
         }
         __syncthreads();
-        for (int k = 0; k < nt; ++k) {
-            const int4 mm = tm[k];
-            const int m[3] = {mm.x, mm.y, mm.z};
-            if (F32) {
-                const float4 a = tf[k];
-                const float2 rr = tr[k];
-#pragma unroll
-                for (int u = 0; u < PER; ++u) {
-                    float sn, cs;
-                    phase_sincos_f(m, v[u], sn, cs);
-                    float g = rr.y * cs - rr.x * sn;
-                    fx[u] = fmaf(a.x, g, fx[u]);
-                    fy[u] = fmaf(a.y, g, fy[u]);
-                    fz[u] = fmaf(a.z, g, fz[u]);
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < PER; ++u) {
-                    double sn, cs;
-                    phase_sincos_d(m, sx[u], sy[u], sz[u], sn, cs);
-                    double g = td[k][4] * cs - td[k][3] * sn;
-                    gx[u] += td[k][0] * g;
-                    gy[u] += td[k][1] * g;
-                    gz[u] += td[k][2] * g;
-                }
+        if (F32) {
+#pragma unroll 4
+            for (int u = 0; u < nt; ++u) {
+                const int4 mm = tm[u];
+                const int m[3] = {mm.x, mm.y, mm.z};
+                const float4 a = tf[u];
+                const float2 rr = tr[u];
+                float sn, cs;
+                phase_sincos_f(m, v, sn, cs);
+                const float g = rr.y * cs - rr.x * sn;
+                fx = fmaf(a.x, g, fx);
+                fy = fmaf(a.y, g, fy);
+                fz = fmaf(a.z, g, fz);
+            }
+        } else {
+            for (int u = 0; u < nt; ++u) {
+                const int4 mm = tm[u];
+                const int m[3] = {mm.x, mm.y, mm.z};
+                double sn, cs;
+                phase_sincos_d(m, sx, sy, sz, sn, cs);
+                const double g = td[u][4] * cs - td[u][3] * sn;
+                gx += td[u][0] * g;
+                gy += td[u][1] * g;
+                gz += td[u][2] * g;
             }
         }
     }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int k = threadIdx.x + u * 256;
-        if (k < na) {
-            const int i = a0 + k;
-            const double qi = q[i];
-            if (F32) {
-                F[3 * i] += qi * (double)fx[u];
-                F[3 * i + 1] += qi * (double)fy[u];
-                F[3 * i + 2] += qi * (double)fz[u];
-            } else {
-                F[3 * i] += qi * gx[u];
-                F[3 * i + 1] += qi * gy[u];
-                F[3 * i + 2] += qi * gz[u];
-            }
+    if (!act) return;
+    const double qi = q[i];
+    const int ks = pos_sorted[i];
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int p = 0; p < nparts; ++p) {
+        if (F32) {
+            const float4 e = reinterpret_cast<const float4 *>(fpart)[(size_t)p * N + ks];
+            f[0] += (double)e.x; f[1] += (double)e.y; f[2] += (double)e.z;
+        } else {
+            const double4 e = reinterpret_cast<const double4 *>(fpart)[(size_t)p * N + ks];
+            f[0] += e.x; f[1] += e.y; f[2] += e.z;
         }
+    }
+    if (F32) {
+        F[3 * i] = f[0] + qi * (double)fx;
+        F[3 * i + 1] = f[1] + qi * (double)fy;
+        F[3 * i + 2] = f[2] + qi * (double)fz;
+    } else {
+        F[3 * i] = f[0] + qi * gx;
+        F[3 * i + 1] = f[1] + qi * gy;
+        F[3 * i + 2] = f[2] + qi * gz;
     }
 }
 
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
                      cudaStream_t st)
 {
+    const dim3 grid(b.nchunks, kChunk / kLrAtoms);
+    const int nparts = 2 * b.sub + 1;
     if (precision == 1)
-        k_lr_force<true><<<b.nchunks, 256, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                   coef, Dcap, a.F);
+        k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
+                                                    coef, Dcap, a.rank, a.fpart4, nparts, b.N, a.F);
     else
-        k_lr_force<false><<<b.nchunks, 256, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                    coef, Dcap, a.F);
+        k_lr_force<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
+                                                     coef, Dcap, a.rank, a.fpartd, nparts, b.N, a.F);
 }
 
 // ---------------------------------------------------------------------------

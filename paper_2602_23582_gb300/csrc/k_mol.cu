@@ -6,8 +6,10 @@
 // (F'(r)/r = -F~(r) for the consistent split w_l = w~_l s~_l^2 / 2, App. C).
 //
 // One thread per molecule: a molecule's atoms belong to that thread only, so
-// forces are added without atomics.  Geometry differences are formed in FP64;
-// in the FP32 build the terms run in FP32 and the exclusion energy is split as
+// forces are added without atomics.  Bonds and angles run in FP64 in both
+// builds (few terms; near equilibrium they are small differences of O(1)
+// numbers).  In the FP32 build the exclusion terms run in FP32 from FP64
+// geometry differences, and the exclusion energy is split as
 // -ke q_i q_j F_E(0) (a per-system constant summed on the host in FP64) plus
 // ke q_i q_j (F_E(0) - F_E(r)) = ke q_i q_j sum_l w_l (1 - e^{-r^2/s_l^2}),
 // evaluated with expm1 so that the FP32 error scales with the small remainder.
@@ -28,11 +30,6 @@ __device__ __forceinline__ void min_image(double d[3], const double L[3])
 
 }  // namespace
 
-template <typename R>
-__device__ __forceinline__ R sqrt_r(R x);
-template <> __device__ __forceinline__ float sqrt_r<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double sqrt_r<double>(double x) { return sqrt(x); }
-
 // One thread per molecule.  R is the arithmetic type of the terms (float in
 // the FP32 build): differences of positions are formed in FP64, then rounded.
 template <typename R>
@@ -44,56 +41,58 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
       const double *__restrict__ at0, const int *__restrict__ excl, const double *__restrict__ r,
       const double *__restrict__ q, double *__restrict__ F, double *__restrict__ partial, const SogConsts sc)
 {
-    __shared__ double red[32];
+    __shared__ double red[15 * (kMolChunk + 1) + 60];
     const int c = blockIdx.x;
     const DevSys &d = sys[mchunk_sys[c]];
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
-    R ub = 0, ua = 0, wb[6] = {0, 0, 0, 0, 0, 0}, wx[6] = {0, 0, 0, 0, 0, 0};
+    double ub = 0, ua = 0, wb[6] = {0, 0, 0, 0, 0, 0};
+    R wx[6] = {0, 0, 0, 0, 0, 0};
     R ue_rem = 0;      // sum ke q_i q_j (F_E(0) - F_E(r)) (the constant part is added on the host)
     double ue = 0.0;   // FP64 build: the full exclusion energy
     const int k = threadIdx.x;
     if (k < mchunk_n[c]) {
         const int mi = mchunk_m0[c] + k;
+        // bonds and angles in FP64 in both builds: near equilibrium r - r0 and
+        // theta - theta0 are small differences of O(1) numbers, and FP32
+        // rounding there would dominate the bonded virial
         for (int e = b_start[mi]; e < b_start[mi + 1]; ++e) {
             const int i = bonds[2 * e], j = bonds[2 * e + 1];
-            double dd[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
-            min_image(dd, L);
-            const R dv[3] = {(R)dd[0], (R)dd[1], (R)dd[2]};
-            const R rr = sqrt_r<R>(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-            const R dr = rr - (R)br0[e];
-            ub += (R)bk[e] * dr * dr;
-            const R cf = (R)(-2) * (R)bk[e] * dr / rr;
-            const R f[3] = {cf * dv[0], cf * dv[1], cf * dv[2]};
-            for (int a = 0; a < 3; ++a) { F[3 * i + a] += (double)f[a]; F[3 * j + a] -= (double)f[a]; }
+            double dv[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+            min_image(dv, L);
+            const double rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            const double dr = rr - br0[e];
+            ub += bk[e] * dr * dr;
+            const double cf = -2.0 * bk[e] * dr / rr;
+            const double f[3] = {cf * dv[0], cf * dv[1], cf * dv[2]};
+            for (int a = 0; a < 3; ++a) { F[3 * i + a] += f[a]; F[3 * j + a] -= f[a]; }
             wb[0] += f[0] * dv[0]; wb[1] += f[1] * dv[1]; wb[2] += f[2] * dv[2];
             wb[3] += f[0] * dv[1]; wb[4] += f[0] * dv[2]; wb[5] += f[1] * dv[2];
         }
         for (int e = a_start[mi]; e < a_start[mi + 1]; ++e) {
             const int i = angles[3 * e], j = angles[3 * e + 1], kk = angles[3 * e + 2];
-            double e1[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
-            double e2[3] = {r[3 * kk] - r[3 * j], r[3 * kk + 1] - r[3 * j + 1], r[3 * kk + 2] - r[3 * j + 2]};
-            min_image(e1, L);
-            min_image(e2, L);
-            const R d1[3] = {(R)e1[0], (R)e1[1], (R)e1[2]}, d2[3] = {(R)e2[0], (R)e2[1], (R)e2[2]};
-            const R r1 = sqrt_r<R>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
-            const R r2 = sqrt_r<R>(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
-            R cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
-            cs = cs > (R)1 ? (R)1 : (cs < (R)(-1) ? (R)(-1) : cs);
-            const R th = acos(cs);
-            R sn = sqrt_r<R>((R)1 - cs * cs);
-            if (sn < (R)1e-12) sn = (R)1e-12;
-            const R dth = th - (R)at0[e];
-            ua += (R)ak[e] * dth * dth;
-            const R g = (R)2 * (R)ak[e] * dth / sn;
-            R fi[3], fk[3];
+            double d1[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+            double d2[3] = {r[3 * kk] - r[3 * j], r[3 * kk + 1] - r[3 * j + 1], r[3 * kk + 2] - r[3 * j + 2]};
+            min_image(d1, L);
+            min_image(d2, L);
+            const double r1 = sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+            const double r2 = sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+            double cs = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
+            cs = cs > 1.0 ? 1.0 : (cs < -1.0 ? -1.0 : cs);
+            const double th = acos(cs);
+            double sn = sqrt(1.0 - cs * cs);
+            if (sn < 1e-12) sn = 1e-12;
+            const double dth = th - at0[e];
+            ua += ak[e] * dth * dth;
+            const double g = 2.0 * ak[e] * dth / sn;
+            double fi[3], fk[3];
             for (int a = 0; a < 3; ++a) {
                 fi[a] = g * (d2[a] / (r1 * r2) - cs * d1[a] / (r1 * r1));
                 fk[a] = g * (d1[a] / (r1 * r2) - cs * d2[a] / (r2 * r2));
             }
             for (int a = 0; a < 3; ++a) {
-                F[3 * i + a] += (double)fi[a];
-                F[3 * kk + a] += (double)fk[a];
-                F[3 * j + a] -= (double)(fi[a] + fk[a]);
+                F[3 * i + a] += fi[a];
+                F[3 * kk + a] += fk[a];
+                F[3 * j + a] -= fi[a] + fk[a];
             }
             wb[0] += fi[0] * d1[0] + fk[0] * d2[0]; wb[1] += fi[1] * d1[1] + fk[1] * d2[1];
             wb[2] += fi[2] * d1[2] + fk[2] * d2[2]; wb[3] += fi[0] * d1[1] + fk[0] * d2[1];
@@ -138,13 +137,10 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     }
     // FP32 build: ue carries the remainder; the host adds -sum ke q_i q_j F_E(0)
     if constexpr (sizeof(R) == 4) ue = (double)ue_rem;
-    const double v[15] = {ue, (double)ub, (double)ua, (double)wx[0], (double)wx[1], (double)wx[2],
-                          (double)wx[3], (double)wx[4], (double)wx[5], (double)wb[0], (double)wb[1],
-                          (double)wb[2], (double)wb[3], (double)wb[4], (double)wb[5]};
-    for (int t = 0; t < 15; ++t) {
-        double s = block_sum(v[t], red);
-        if (threadIdx.x == 0) partial[(size_t)c * 15 + t] = s;
-    }
+    const double v[15] = {ue, ub, ua, (double)wx[0], (double)wx[1], (double)wx[2],
+                          (double)wx[3], (double)wx[4], (double)wx[5], wb[0], wb[1],
+                          wb[2], wb[3], wb[4], wb[5]};
+    block_reduce_lanes<15, kMolChunk>(v, red, partial + (size_t)c * 15);
 }
 
 void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc,

@@ -9,30 +9,36 @@
 // Full pairs: each atom sums all its neighbours itself (no atomics, so results
 // do not depend on scheduling); energies and virials take half.
 //
-// Work item = one warp = a group of up to 32 atoms of one cell (lane = atom,
-// in registers).  The warp walks the (2 sub + 1)^3 neighbour cells; candidate
-// neighbours are read with warp-broadcast loads (every lane the same address,
-// served by L1), four at a time.  A candidate that passes the cheap test
-// (r^2 < r_c^2, different molecule) is pushed, with the code of its
-// neighbour cell, into the lane's queue in shared memory; the warp evaluates
-// the 11-transcendental SOG kernel in rounds in which every lane with an atom
-// has a queued hit, so the expensive part runs with full lanes.
+// Work unit = one warp = a group of up to 32 atoms of one cell (lane = atom,
+// in registers) and one dz plane of its neighbour cells (the (2 sub + 1)
+// planes of a group run as separate warps, which keeps enough warps in flight;
+// their partial forces are summed in a fixed order by the force assembly
+// kernel).  The warp walks the (2 sub + 1)^2 neighbour cells of its plane;
+// candidate neighbours are read with warp-broadcast loads (every lane the same
+// address, served by L1), 32 at a time, and each lane records its hits
+// (r^2 < r_c^2, different molecule) in a bit mask, then pushes them, with the
+// index of their neighbour cell, into its queue in shared memory.  The warp
+// evaluates the SOG kernel in rounds in which every lane with an atom has a
+// queued hit, so the expensive part runs with full lanes.  Each block writes
+// one record of energy and virial sums (its warps belong to one system).
 //
-// Coordinates are cell-local (FP32 keeps ~1e-6 A); a neighbour cell's
-// periodic offset (d_a w_a) is subtracted from the i coordinate.
+// Coordinates are cell-local.  A neighbour cell's periodic offset d_a w_a is
+// split into FP32 hi + lo parts: the cutoff test uses hi, the evaluation
+// subtracts both, so that the rounding of w_a does not shift every
+// cross-cell distance the same way (a systematic error that the r^-12 and
+// 1/r - F(r) terms would amplify).
 #include "internal.h"
 
 namespace rbsog {
 
 namespace {
 
-constexpr int QCAP = 64;    // per-lane queue (power of two); pending <= 32 before a batch
-constexpr int WPB = 4;      // warps (work items) per block
-constexpr int kMaxNb = 128; // neighbour cells of the stencil (125 for cells of r_c/2)
+constexpr int QCAP = 64;      // per-lane queue (power of two); pending <= 32 before a batch
+constexpr int kMaxPlane = 32; // neighbour cells of one dz plane (25 for cells of r_c/2)
 
 size_t pair_smem(int precision)
 {
-    return (size_t)WPB * (QCAP * 32 * (sizeof(unsigned) + 1) + kMaxNb * (precision == 1 ? 16 : 32));
+    return (size_t)kPairWarps * (QCAP * 32 * sizeof(unsigned) + kMaxPlane * 16);
 }
 
 __device__ __forceinline__ float ex2f(float x)
@@ -52,8 +58,9 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 
 struct AccF {
     float fx, fy, fz;
-    float uc, ul, cuc, cul;   // energies with compensation terms
-    float wc[6], wl[6];
+    float w[6];               // total virial (every step)
+    float uc, ul, uq, cuc, cul, cuq;   // energies and sum q_i q_j, with compensation terms
+    float wc[6], wl[6];       // Coulomb / LJ split of the virial (energy steps)
 };
 
 struct AccD {
@@ -62,54 +69,105 @@ struct AccD {
     double wc[6], wl[6];
 };
 
-template <int NG>
-__device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float dy, float dz, float qi,
-                                          int ti, float2 qj, AccF &acc)
+// Cutoff decision for a pair close to r_c, in FP64 from the original
+// positions with the minimum image, as the CPU reference decides it.
+__device__ __forceinline__ bool inside_cutoff_fp64(const double *__restrict__ r, int i, int j, const double L[3],
+                                                double rc2)
 {
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float rinv = rsqrtf(r2);
-    const float r2inv = rinv * rinv;
-    float st = 0.f, se = 0.f;
-    if (NG > 0) {
-#pragma unroll
-        for (int l = 0; l < NG; ++l) {
-            float e = ex2f(-r2 * pc.beta[l]);
-            st = fmaf(pc.wt[l], e, st);
-            se = fmaf(pc.w[l], e, se);
-        }
-    } else {
-        for (int l = 0; l < pc.M; ++l) {
-            float e = ex2f(-r2 * pc.beta[l]);
-            st = fmaf(pc.wt[l], e, st);
-            se = fmaf(pc.w[l], e, se);
-        }
+    double r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double dd = r[3 * i + a] - r[3 * j + a];
+        dd = L[a] * (dd / L[a] - rint(dd / L[a]));
+        r2 += dd * dd;
     }
-    for (int l = pc.M; l < pc.ME; ++l) se = fmaf(pc.w[l], ex2f(-r2 * pc.beta[l]), se);
+    return r2 < rc2;
+}
+
+// 2^x for x <= 0 without the MUFU approximation: x = n + f, n = rint(x),
+// |f| <= 1/2, 2^f from its Taylor series sum_k (f ln 2)^k / k! to degree 9
+// (remainder < 0.35^10 / 10! ~ 8e-12), Horner with FMA (rounding errors of
+// either sign), 2^n by an exponent add.  Used where a bias shared by all
+// pairs would accumulate (the energy path).
+__device__ __forceinline__ float exp2_poly(float x)
+{
+    x = fmaxf(x, -125.f);
+    const float n = rintf(x);
+    const float f = x - n;
+    float p = 1.0178086e-07f;                 // (ln 2)^9 / 9!
+    p = fmaf(p, f, 1.3215487e-06f);           // (ln 2)^8 / 8!
+    p = fmaf(p, f, 1.5252734e-05f);           // (ln 2)^7 / 7!
+    p = fmaf(p, f, 1.5403530e-04f);           // (ln 2)^6 / 6!
+    p = fmaf(p, f, 1.3333558e-03f);           // (ln 2)^5 / 5!
+    p = fmaf(p, f, 9.6181291e-03f);           // (ln 2)^4 / 4!
+    p = fmaf(p, f, 5.5504109e-02f);           // (ln 2)^3 / 3!
+    p = fmaf(p, f, 2.4022651e-01f);           // (ln 2)^2 / 2!
+    p = fmaf(p, f, 6.9314718e-01f);           // ln 2
+    p = fmaf(p, f, 1.0f);
+    return __int_as_float(__float_as_int(p) + ((int)n << 23));
+}
+
+// One pair from the i side.  NF: exponentials of the force kernel (0: pc.nff
+// at run time); EN: energies and the Coulomb/LJ virial split.  The force and
+// the total virial are computed the same way in both modes.
+template <int NF, bool EN>
+__device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float dy, float dz, float r2, float qi,
+                                          const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlo,
+                                          float2 qj, AccF &acc)
+{
+    float rinv = rsqrtf(r2);
+    rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);   // one Newton step: the approximate
+    const float r2inv = rinv * rinv;                     // rsqrt error would bias r^-12 terms
+    // force kernel: F~(r) = tail polynomial in r^2 + narrow Gaussians
+    float st = pc.tt[kTail];
+#pragma unroll
+    for (int k = kTail - 1; k >= 0; --k) st = fmaf(st, r2, pc.tt[k]);
+    if (NF > 0) {
+#pragma unroll
+        for (int l = 0; l < NF; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
+    } else {
+        for (int l = 0; l < pc.nff; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
+    }
     const float qq = pc.ke * qi * qj.x;
     const float fc = qq * (r2inv * rinv - st);
-    const float ec = qq * (rinv - se);
     const int tj = __float_as_int(qj.y);
-    const float la = pc.lj_a[ti * pc.ntypes + tj], lb = pc.lj_b[ti * pc.ntypes + tj];
+    const float2 lab = __ldg(&ljrow[tj]);
     const float r6inv = r2inv * r2inv * r2inv;
-    const float fl = (12.f * la * r6inv - 6.f * lb) * r6inv * r2inv;
-    const float el = (la * r6inv - lb) * r6inv;
+    const float fl = (12.f * lab.x * r6inv - 6.f * lab.y) * r6inv * r2inv;
     const float f = fc + fl;
     acc.fx = fmaf(f, dx, acc.fx);
     acc.fy = fmaf(f, dy, acc.fy);
     acc.fz = fmaf(f, dz, acc.fz);
-    kahan_add(acc.uc, acc.cuc, ec);
-    kahan_add(acc.ul, acc.cul, el);
-    const float cx = fc * dx, cy = fc * dy, lx = fl * dx, ly = fl * dy;
-    acc.wc[0] = fmaf(cx, dx, acc.wc[0]); acc.wc[1] = fmaf(cy, dy, acc.wc[1]);
-    acc.wc[2] = fmaf(fc * dz, dz, acc.wc[2]); acc.wc[3] = fmaf(cx, dy, acc.wc[3]);
-    acc.wc[4] = fmaf(cx, dz, acc.wc[4]); acc.wc[5] = fmaf(cy, dz, acc.wc[5]);
-    acc.wl[0] = fmaf(lx, dx, acc.wl[0]); acc.wl[1] = fmaf(ly, dy, acc.wl[1]);
-    acc.wl[2] = fmaf(fl * dz, dz, acc.wl[2]); acc.wl[3] = fmaf(lx, dy, acc.wl[3]);
-    acc.wl[4] = fmaf(lx, dz, acc.wl[4]); acc.wl[5] = fmaf(ly, dz, acc.wl[5]);
+    const float gx = f * dx, gy = f * dy;
+    acc.w[0] = fmaf(gx, dx, acc.w[0]); acc.w[1] = fmaf(gy, dy, acc.w[1]);
+    acc.w[2] = fmaf(f * dz, dz, acc.w[2]); acc.w[3] = fmaf(gx, dy, acc.w[3]);
+    acc.w[4] = fmaf(gx, dz, acc.w[4]); acc.w[5] = fmaf(gy, dz, acc.w[5]);
+    if (EN) {
+        // energy kernel N(r) = 1/r - F(r); the constant of the tail is applied
+        // to sum q_i q_j in FP64 by the caller
+        float se = pc.te[kTail];
+#pragma unroll
+        for (int k = kTail - 1; k >= 1; --k) se = fmaf(se, r2, pc.te[k]);
+        se *= r2;
+        for (int l = 0; l < pc.nfe; ++l) {
+            const float e = exp2_poly(fmaf(-r2, pc.be_hi[l], -r2 * pc.be_lo[l]));
+            se = fmaf(pc.w_hi[l], e, fmaf(pc.w_lo[l], e, se));
+        }
+        kahan_add(acc.uc, acc.cuc, qq * (rinv - se));
+        kahan_add(acc.uq, acc.cuq, qq);
+        const float2 lo = __ldg(&ljlo[tj]);
+        kahan_add(acc.ul, acc.cul, (fmaf(lab.x, r6inv, -lab.y) + fmaf(lo.x, r6inv, -lo.y)) * r6inv);
+        const float cx = fc * dx, cy = fc * dy, lx = fl * dx, ly = fl * dy;
+        acc.wc[0] = fmaf(cx, dx, acc.wc[0]); acc.wc[1] = fmaf(cy, dy, acc.wc[1]);
+        acc.wc[2] = fmaf(fc * dz, dz, acc.wc[2]); acc.wc[3] = fmaf(cx, dy, acc.wc[3]);
+        acc.wc[4] = fmaf(cx, dz, acc.wc[4]); acc.wc[5] = fmaf(cy, dz, acc.wc[5]);
+        acc.wl[0] = fmaf(lx, dx, acc.wl[0]); acc.wl[1] = fmaf(ly, dy, acc.wl[1]);
+        acc.wl[2] = fmaf(fl * dz, dz, acc.wl[2]); acc.wl[3] = fmaf(lx, dy, acc.wl[3]);
+        acc.wl[4] = fmaf(lx, dz, acc.wl[4]); acc.wl[5] = fmaf(ly, dz, acc.wl[5]);
+    }
 }
 
 __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, double dy, double dz, double qi,
-                                          int ti, double qj, int tj, AccD &acc)
+                                          const double2 *__restrict__ ljrow, double qj, int tj, AccD &acc)
 {
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double rinv = rsqrt(r2);
@@ -124,7 +182,8 @@ __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, doub
     const double qq = pc.ke * qi * qj;
     const double fc = qq * (r2inv * rinv - st);
     const double ec = qq * (rinv - se);
-    const double la = pc.lj_a[ti * pc.ntypes + tj], lb = pc.lj_b[ti * pc.ntypes + tj];
+    const double2 lab = __ldg(&ljrow[tj]);
+    const double la = lab.x, lb = lab.y;
     const double r6inv = r2inv * r2inv * r2inv;
     const double fl = (12.0 * la * r6inv - 6.0 * lb) * r6inv * r2inv;
     const double el = (la * r6inv - lb) * r6inv;
@@ -145,254 +204,267 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP32 kernel.  A queued hit carries its neighbour-cell index nb (< 125); the
-// warp keeps the offsets of the (2 sub + 1)^3 neighbour cells in shared memory.
+// FP32 kernel.  A queued hit carries the index (< 25) of its neighbour cell
+// within the plane; the warp keeps the plane's offsets in shared memory.
 // ---------------------------------------------------------------------------
-template <int NG>
-__global__ void __launch_bounds__(32 * WPB)
+template <int NF, bool EN>
+__global__ void __launch_bounds__(32 * kPairWarps, 5)
 k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
-           const int *__restrict__ count, const int2 *__restrict__ items, int n_items,
-           const float4 *__restrict__ pos4, const float2 *__restrict__ qt, const int *__restrict__ sidx, int sub,
-           double *__restrict__ F, double *__restrict__ partial, const PairConstsF pc)
+           const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4,
+           const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
+           const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N,
+           float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double rec[kPairWarps][kPairRec];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
-    float4 *off = reinterpret_cast<float4 *>(smem + WPB * QCAP * 32 * sizeof(unsigned)) + warp * kMaxNb;
-    unsigned char *qc = smem + WPB * QCAP * 32 * sizeof(unsigned) + WPB * kMaxNb * sizeof(float4) + warp * QCAP * 32;
-    const int it = blockIdx.x * WPB + warp;
-    if (it >= n_items) return;
-    const int2 item = items[it];
-    if (item.x < 0) return;
-    const int gc = item.x;
-    const DevSys &d = sys[cell_sys[gc]];
-    const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
-    const int lc = gc - d.cell0;
-    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-    const float wx = (float)d.w[0], wy = (float)d.w[1], wz = (float)d.w[2];
+    float4 *offp = reinterpret_cast<float4 *>(smem + kPairWarps * QCAP * 32 * sizeof(unsigned)) + warp * kMaxPlane;
     const int span = 2 * sub + 1;
-    for (int nb = lane; nb < span * span * span; nb += 32)
-        off[nb] = make_float4((nb % span - sub) * wx, ((nb / span) % span - sub) * wy,
-                              (nb / (span * span) - sub) * wz, 0.f);
-    __syncwarp();
-    const int i0 = start[gc] + 32 * item.y;
-    const int ni = min(32, count[gc] - 32 * item.y);
-    const bool vi = lane < ni;
-    float4 pi = make_float4(0.f, 0.f, 0.f, __int_as_float(-0x7fffffff));
-    float2 pq = make_float2(0.f, 0.f);
-    if (vi) { pi = pos4[i0 + lane]; pq = qt[i0 + lane]; }
-    const int moli = vi ? __float_as_int(pi.w) : -0x7fffffff;
-    const int ti = __float_as_int(pq.y);
-    const float rc2 = pc.rc2;
-    AccF acc;
-    acc.fx = acc.fy = acc.fz = 0.f;
-    acc.uc = acc.ul = acc.cuc = acc.cul = 0.f;
+    const int unit = blockIdx.x * kPairWarps + warp;   // (group, dz plane)
+    const int2 item = items[unit / span];
+    const int part = unit % span;
+    double u0 = 0.0, u1 = 0.0;
+    float wv[18];                                      // Wc, Wl (energy steps), W
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.f;
-    int head = 0, tail = 0;
-
-    auto eval_one = [&](unsigned j, int code) {
-        const float4 pj = pos4[j];
-        const float2 qj = qt[j];
-        const float4 o = off[code];
-        pair_eval<NG>(pc, (pi.x - o.x) - pj.x, (pi.y - o.y) - pj.y, (pi.z - o.z) - pj.z, pq.x, ti, qj, acc);
-    };
-
-    for (int nb = 0; nb < span * span * span; ++nb) {
-        const int ddx = nb % span - sub, ddy = (nb / span) % span - sub, ddz = nb / (span * span) - sub;
-        const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + ddz, n2));
-        const int j0 = start[g], nj = count[g];
-        const int code = nb;
-        const float4 o = off[nb];
-        const float xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - o.z;
-        for (int jb = 0; jb < nj; jb += 32) {
-            const int je = min(jb + 32, nj);
-            int j = jb;
-            for (; j + 4 <= je; j += 4) {
-                float4 p[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) p[u] = __ldg(&pos4[j0 + j + u]);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float dx = xi - p[u].x, dy = yi - p[u].y, dz = zi - p[u].z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (vi && r2 < rc2 && __float_as_int(p[u].w) != moli) {
-                        const int slot = (tail & (QCAP - 1)) * 32 + lane;
-                        q[slot] = (unsigned)(j0 + j + u);
-                        qc[slot] = (unsigned char)code;
-                        ++tail;
-                    }
-                }
-            }
-            for (; j < je; ++j) {
-                const float4 pj = __ldg(&pos4[j0 + j]);
-                const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (vi && r2 < rc2 && __float_as_int(pj.w) != moli) {
-                    const int slot = (tail & (QCAP - 1)) * 32 + lane;
-                    q[slot] = (unsigned)(j0 + j);
-                    qc[slot] = (unsigned char)code;
-                    ++tail;
-                }
-            }
-            // full-warp rounds: every lane with an atom has a hit queued (lanes
-            // without an atom never queue anything and sit these rounds out)
-            const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
-            for (int t = 0; t < mn; ++t) {
-                if (vi) {
-                    const int slot = (head & (QCAP - 1)) * 32 + lane;
-                    ++head;
-                    eval_one(q[slot], qc[slot]);
-                }
-            }
-            // keep room for the next batch of 32 candidates
-            while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
-                if (tail > head) {
-                    const int slot = (head & (QCAP - 1)) * 32 + lane;
-                    ++head;
-                    eval_one(q[slot], qc[slot]);
-                }
-            }
+    for (int k = 0; k < 18; ++k) wv[k] = 0.f;
+    if (item.x >= 0) {                                 // warp-uniform
+        const int gc = item.x;
+        const DevSys &d = sys[cell_sys[gc]];
+        const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
+        const int lc = gc - d.cell0;
+        const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+        const int ddz = part - sub;
+        const double ozd = ddz * d.w[2];
+        const float ozh = (float)ozd, ozl = (float)(ozd - (double)ozh);
+        for (int nb = lane; nb < span * span; nb += 32) {
+            const double ox = (nb % span - sub) * d.w[0], oy = (nb / span - sub) * d.w[1];
+            const float oxh = (float)ox, oyh = (float)oy;
+            offp[nb] = make_float4(oxh, oyh, (float)(ox - (double)oxh), (float)(oy - (double)oyh));
         }
-    }
-    while (__any_sync(0xffffffffu, tail > head)) {
-        if (tail > head) {
+        __syncwarp();
+        const int i0 = start[gc] + 32 * item.y;
+        const int ni = min(32, count[gc] - 32 * item.y);
+        const bool vi = lane < ni;
+        // lanes without an atom sit far away: their cutoff test never passes
+        float4 pi = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-0x7fffffff));
+        float2 pq = make_float2(0.f, 0.f);
+        if (vi) { pi = pos4[i0 + lane]; pq = qt[i0 + lane]; }
+        const int moli = __float_as_int(pi.w);
+        const int rowi = d.lj0 + __float_as_int(pq.y) * d.ntypes;
+        const float2 *ljrow = lj + rowi, *ljlorow = ljlo + rowi;
+        AccF acc;
+        acc.fx = acc.fy = acc.fz = 0.f;
+        acc.uc = acc.ul = acc.uq = acc.cuc = acc.cul = acc.cuq = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.w[k] = acc.wc[k] = acc.wl[k] = 0.f;
+        int head = 0, tail = 0;
+
+        // queue entry: neighbour atom index (25 bits) | neighbour cell in the plane (7 bits)
+        // pairs within a relative 1e-5 of r_c^2 are queued and decided in FP64
+        // from the original positions (the energy kernel N is about 2e-3 / A
+        // at r_c, so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
+        auto eval_one = [&](unsigned e) {
+            const unsigned j = e & 0x1ffffffu;
+            const float4 pj = pos4[j];
+            const float2 qj = qt[j];
+            const float4 o = offp[e >> 25];
+            const float dx = ((pi.x - o.x) - pj.x) - o.z, dy = ((pi.y - o.y) - pj.y) - o.w,
+                        dz = ((pi.z - ozh) - pj.z) - ozl;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= pc.rc2_lo && !inside_cutoff_fp64(r, sidx[i0 + lane], sidx[j], d.L, pc.rc2d)) return;
+            pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qj, acc);
+        };
+        auto pop = [&]() {
             const int slot = (head & (QCAP - 1)) * 32 + lane;
             ++head;
-            eval_one(q[slot], qc[slot]);
+            eval_one(q[slot]);
+        };
+
+        const int gz = wrapi(cz + ddz, n2);
+        for (int nb = 0; nb < span * span; ++nb) {
+            const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
+            const int j0 = start[g], nj = count[g];
+            const float4 o = offp[nb];
+            const float xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - ozh;
+            for (int jb = 0; jb < nj; jb += 32) {
+                const float4 *pc4 = pos4 + j0 + jb;
+                unsigned hm = 0;                       // hits among these 32 candidates
+                if (nj - jb >= 32) {
+#pragma unroll
+                    for (int ub = 0; ub < 32; ub += 4) {
+                        float4 p[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) p[u] = __ldg(pc4 + ub + u);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float dx = xi - p[u].x, dy = yi - p[u].y, dz = zi - p[u].z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < pc.rc2_hi && __float_as_int(p[u].w) != moli) hm |= 1u << (ub + u);
+                        }
+                    }
+                } else {
+                    for (int u = 0; u < nj - jb; ++u) {
+                        const float4 pj = __ldg(pc4 + u);
+                        const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < pc.rc2_hi && __float_as_int(pj.w) != moli) hm |= 1u << u;
+                    }
+                }
+                const unsigned base = (unsigned)(j0 + jb) | ((unsigned)nb << 25);
+                while (hm) {
+                    q[(tail & (QCAP - 1)) * 32 + lane] = base + (unsigned)(__ffs(hm) - 1);
+                    hm &= hm - 1u;
+                    ++tail;
+                }
+                // full-warp rounds: every lane with an atom has a hit queued
+                const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
+                for (int t = 0; t < mn; ++t)
+                    if (vi) pop();
+                // keep room for the next 32 candidates
+                while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32)
+                    if (tail > head) pop();
+            }
+        }
+        while (__any_sync(0xffffffffu, tail > head))
+            if (tail > head) pop();
+        if (vi) Fpart[(size_t)part * N + i0 + lane] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);
+        // virials: FP32 warp sums; energies: FP64 (compensated lanes), with the
+        // constant of the energy tail applied to sum q_i q_j here
+#pragma unroll
+        for (int k = 0; k < 6; ++k) wv[12 + k] = warp_sumf(acc.w[k]);
+        if (EN) {
+            u0 = warp_sum((double)acc.uc - (double)acc.cuc - pc.te0 * ((double)acc.uq - (double)acc.cuq));
+            u1 = warp_sum((double)acc.ul - (double)acc.cul);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                wv[k] = warp_sumf(acc.wc[k]);
+                wv[6 + k] = warp_sumf(acc.wl[k]);
+            }
         }
     }
-    if (vi) {
-        const int ia = sidx[i0 + lane];
-        F[3 * ia] = acc.fx;
-        F[3 * ia + 1] = acc.fy;
-        F[3 * ia + 2] = acc.fz;
-    }
-    // per-item sums: energies in FP64 (compensated lanes), virials FP32 warp sums
-    const double u0 = warp_sum((double)acc.uc - (double)acc.cuc);
-    const double u1 = warp_sum((double)acc.ul - (double)acc.cul);
-    float wv[12] = {acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4], acc.wc[5],
-                    acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
-#pragma unroll
-    for (int k = 0; k < 12; ++k) wv[k] = warp_sumf(wv[k]);
     if (lane == 0) {
-        double *o = partial + (size_t)it * 14;
-        o[0] = 0.5 * u0;
-        o[1] = 0.5 * u1;
+        rec[warp][0] = u0;
+        rec[warp][1] = u1;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) o[2 + k] = 0.5 * (double)wv[k];
+        for (int k = 0; k < 18; ++k) rec[warp][2 + k] = (double)wv[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kPairRec) {
+        const int t = threadIdx.x;
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kPairWarps; ++w) s += rec[w][t];
+        partial[(size_t)blockIdx.x * kPairRec + t] = 0.5 * s;   // each pair was seen from both atoms
     }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 kernel (same structure)
+// FP64 kernel (same structure; plane offsets in FP64 need no lo part)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * WPB)
+__global__ void __launch_bounds__(32 * kPairWarps)
 k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
-           const int *__restrict__ count, const int2 *__restrict__ items, int n_items,
-           const double4 *__restrict__ posd, const int2 *__restrict__ aux, const int *__restrict__ sidx, int sub,
-           double *__restrict__ F, double *__restrict__ partial, const PairConstsD pc)
+           const int *__restrict__ count, const int2 *__restrict__ items, const double4 *__restrict__ posd,
+           const int2 *__restrict__ aux, const double2 *__restrict__ lj, int sub, int N,
+           double4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsD pc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double rec[kPairWarps][kPairRec];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
-    double4 *off = reinterpret_cast<double4 *>(smem + WPB * QCAP * 32 * sizeof(unsigned)) + warp * kMaxNb;
-    unsigned char *qc = smem + WPB * QCAP * 32 * sizeof(unsigned) + WPB * kMaxNb * sizeof(double4) + warp * QCAP * 32;
-    const int it = blockIdx.x * WPB + warp;
-    if (it >= n_items) return;
-    const int2 item = items[it];
-    if (item.x < 0) return;
-    const int gc = item.x;
-    const DevSys &d = sys[cell_sys[gc]];
-    const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
-    const int lc = gc - d.cell0;
-    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-    const double wx = d.w[0], wy = d.w[1], wz = d.w[2];
+    double2 *offp = reinterpret_cast<double2 *>(smem + kPairWarps * QCAP * 32 * sizeof(unsigned)) + warp * kMaxPlane;
     const int span = 2 * sub + 1;
-    for (int nb = lane; nb < span * span * span; nb += 32)
-        off[nb] = make_double4((nb % span - sub) * wx, ((nb / span) % span - sub) * wy,
-                               (nb / (span * span) - sub) * wz, 0.0);
-    __syncwarp();
-    const int i0 = start[gc] + 32 * item.y;
-    const int ni = min(32, count[gc] - 32 * item.y);
-    const bool vi = lane < ni;
-    double4 pi = make_double4(0, 0, 0, 0);
-    int2 ai = make_int2(-0x7fffffff, 0);
-    if (vi) { pi = posd[i0 + lane]; ai = aux[i0 + lane]; }
-    const double rc2 = pc.rc2;
-    AccD acc;
-    acc.fx = acc.fy = acc.fz = 0.0;
-    acc.uc = acc.ul = 0.0;
+    const int unit = blockIdx.x * kPairWarps + warp;
+    const int2 item = items[unit / span];
+    const int part = unit % span;
+    double red[kPairRec];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.0;
-    int head = 0, tail = 0;
+    for (int k = 0; k < kPairRec; ++k) red[k] = 0.0;
+    if (item.x >= 0) {
+        const int gc = item.x;
+        const DevSys &d = sys[cell_sys[gc]];
+        const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
+        const int lc = gc - d.cell0;
+        const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+        const int ddz = part - sub;
+        const double oz = ddz * d.w[2];
+        for (int nb = lane; nb < span * span; nb += 32)
+            offp[nb] = make_double2((nb % span - sub) * d.w[0], (nb / span - sub) * d.w[1]);
+        __syncwarp();
+        const int i0 = start[gc] + 32 * item.y;
+        const int ni = min(32, count[gc] - 32 * item.y);
+        const bool vi = lane < ni;
+        double4 pi = make_double4(0, 0, 0, 0);
+        int2 ai = make_int2(-0x7fffffff, 0);
+        if (vi) { pi = posd[i0 + lane]; ai = aux[i0 + lane]; }
+        const double2 *ljrow = lj + d.lj0 + ai.y * d.ntypes;
+        const double rc2 = pc.rc2;
+        AccD acc;
+        acc.fx = acc.fy = acc.fz = 0.0;
+        acc.uc = acc.ul = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.0;
+        int head = 0, tail = 0;
 
-    auto eval_one = [&](unsigned j, int code) {
-        const double4 pj = posd[j];
-        const int tj = aux[j].y;
-        const double4 o = off[code];
-        pair_eval(pc, (pi.x - o.x) - pj.x, (pi.y - o.y) - pj.y, (pi.z - o.z) - pj.z, pi.w, ai.y, pj.w, tj, acc);
-    };
-
-    for (int nb = 0; nb < span * span * span; ++nb) {
-        const int ddx = nb % span - sub, ddy = (nb / span) % span - sub, ddz = nb / (span * span) - sub;
-        const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + ddz, n2));
-        const int j0 = start[g], nj = count[g];
-        const int code = nb;
-        const double4 o = off[nb];
-        const double xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - o.z;
-        for (int jb = 0; jb < nj; jb += 32) {
-            const int je = min(jb + 32, nj);
-            for (int j = jb; j < je; ++j) {
-                const double4 pj = posd[j0 + j];
-                const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (vi && r2 < rc2 && aux[j0 + j].x != ai.x) {
-                    const int slot = (tail & (QCAP - 1)) * 32 + lane;
-                    q[slot] = (unsigned)(j0 + j);
-                    qc[slot] = (unsigned char)code;
-                    ++tail;
-                }
-            }
-            const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
-            for (int t = 0; t < mn; ++t) {
-                if (vi) {
-                    const int slot = (head & (QCAP - 1)) * 32 + lane;
-                    ++head;
-                    eval_one(q[slot], qc[slot]);
-                }
-            }
-            while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32) {
-                if (tail > head) {
-                    const int slot = (head & (QCAP - 1)) * 32 + lane;
-                    ++head;
-                    eval_one(q[slot], qc[slot]);
-                }
-            }
-        }
-    }
-    while (__any_sync(0xffffffffu, tail > head)) {
-        if (tail > head) {
+        auto eval_one = [&](unsigned e) {
+            const unsigned j = e & 0x1ffffffu;
+            const double4 pj = posd[j];
+            const int tj = aux[j].y;
+            const double2 o = offp[e >> 25];
+            pair_eval(pc, (pi.x - o.x) - pj.x, (pi.y - o.y) - pj.y, (pi.z - oz) - pj.z, pi.w, ljrow, pj.w, tj, acc);
+        };
+        auto pop = [&]() {
             const int slot = (head & (QCAP - 1)) * 32 + lane;
             ++head;
-            eval_one(q[slot], qc[slot]);
+            eval_one(q[slot]);
+        };
+
+        const int gz = wrapi(cz + ddz, n2);
+        for (int nb = 0; nb < span * span; ++nb) {
+            const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
+            const int j0 = start[g], nj = count[g];
+            const double2 o = offp[nb];
+            const double xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - oz;
+            const unsigned code = (unsigned)nb << 25;
+            for (int jb = 0; jb < nj; jb += 32) {
+                const int je = min(jb + 32, nj);
+                for (int j = jb; j < je; ++j) {
+                    const double4 pj = posd[j0 + j];
+                    const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (vi && r2 < rc2 && aux[j0 + j].x != ai.x) {
+                        q[(tail & (QCAP - 1)) * 32 + lane] = (unsigned)(j0 + j) | code;
+                        ++tail;
+                    }
+                }
+                const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
+                for (int t = 0; t < mn; ++t)
+                    if (vi) pop();
+                while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32)
+                    if (tail > head) pop();
+            }
         }
-    }
-    if (vi) {
-        const int ia = sidx[i0 + lane];
-        F[3 * ia] = acc.fx;
-        F[3 * ia + 1] = acc.fy;
-        F[3 * ia + 2] = acc.fz;
-    }
-    const double v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
-                          acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
-    double red[14];
+        while (__any_sync(0xffffffffu, tail > head))
+            if (tail > head) pop();
+        if (vi) Fpart[(size_t)part * N + i0 + lane] = make_double4(acc.fx, acc.fy, acc.fz, 0.0);
+        const double v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
+                              acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
 #pragma unroll
-    for (int k = 0; k < 14; ++k) red[k] = warp_sum(v[k]);
+        for (int k = 0; k < 14; ++k) red[k] = warp_sum(v[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[14 + k] = red[2 + k] + red[8 + k];
+    }
     if (lane == 0) {
-        double *o = partial + (size_t)it * 14;
 #pragma unroll
-        for (int k = 0; k < 14; ++k) o[k] = 0.5 * red[k];
+        for (int k = 0; k < kPairRec; ++k) rec[warp][k] = red[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kPairRec) {
+        const int t = threadIdx.x;
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kPairWarps; ++w) s += rec[w][t];
+        partial[(size_t)blockIdx.x * kPairRec + t] = 0.5 * s;
     }
 }
 
@@ -400,30 +472,36 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
 // outside any stream capture).
 cudaError_t prepare_pair()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_f32<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(1));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pair_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(1));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(0));
+    const int sf = (int)pair_smem(1), sd = (int)pair_smem(0);
+    cudaError_t e = cudaFuncSetAttribute(k_pair_f32<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f32<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
     return e;
 }
 
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
-                 const PairConstsD &cd, double *partial, cudaStream_t st)
+                 const PairConstsD &cd, int energy, double *partial, cudaStream_t st)
 {
-    const int blocks = (b.item_cap + WPB - 1) / WPB;
+    // item_cap is a multiple of kPairWarps per system, so every block lies in one system
+    const int blocks = b.item_cap * (2 * b.sub + 1) / kPairWarps;
     const size_t sm = pair_smem(precision);
+    const dim3 th(32 * kPairWarps);
+#define RBSOG_PAIR_F32(NF, EN)                                                                              \
+    k_pair_f32<NF, EN><<<blocks, th, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, a.qt,  \
+                                               a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, b.N, a.fpart4, partial, cf)
     if (precision == 1) {
-        if (cf.M == 10)
-            k_pair_f32<10><<<blocks, 32 * WPB, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
-                                                        a.pos4, a.qt, a.sidx, b.sub, a.F, partial, cf);
-        else
-            k_pair_f32<0><<<blocks, 32 * WPB, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap,
-                                                       a.pos4, a.qt, a.sidx, b.sub, a.F, partial, cf);
+        if (cf.nff == 4) {
+            if (energy) RBSOG_PAIR_F32(4, true); else RBSOG_PAIR_F32(4, false);
+        } else {
+            if (energy) RBSOG_PAIR_F32(0, true); else RBSOG_PAIR_F32(0, false);
+        }
     } else {
-        k_pair_f64<<<blocks, 32 * WPB, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, b.item_cap, a.posd,
-                                                a.aux, a.sidx, b.sub, a.F, partial, cd);
+        k_pair_f64<<<blocks, th, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.posd, a.aux, a.ljd,
+                                           b.sub, b.N, a.fpartd, partial, cd);
     }
+#undef RBSOG_PAIR_F32
 }
 
 }  // namespace rbsog

@@ -35,7 +35,13 @@ struct Shared {
     int nd;
 };
 
-__device__ int axis_mmax(double a) { return (int)ceil(sqrt(46.0 / a)) + 2; }
+// terms beyond |m| = ceil(sqrt(46 / a)) + 2 are below e^-46 of the largest;
+// capped so that a non-finite box (flagged, step discarded) cannot run away
+__device__ int axis_mmax(double a)
+{
+    const double x = ceil(sqrt(46.0 / a));
+    return (x < 65536.0 ? (int)x : 65536) + 2;
+}
 
 // unnormalised targets (eqs. samplingP, samplingPnr)
 __device__ void targets(const SamplerArgs &sa, const double L[3], const int m[3], double &pr, double &pnr)
@@ -185,6 +191,7 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__re
     __shared__ int start_m[3], nrstart_m[3];
     __shared__ double start_w, start_g, nrstart_g;
     __shared__ int cnt_r, cnt_nr;
+    __shared__ int scan_w[8];
     const int s = blockIdx.x;
     DevSys &d = sys[s];
     const uint64_t step = *sa.step + 1;
@@ -196,6 +203,10 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__re
     double *pu_s = pu + (size_t)s * P, *pun_s = pun + (size_t)s * P;
     if (tid < 3) sh.L[tid] = d.L[tid];
     __syncthreads();
+    if (d.flags & FLAG_BOX) {                 // invalid box: no modes; the step is reported as failed
+        if (tid == 0) { d.nD = 0; d.nacc_r = 0; d.nacc_nr = 0; }
+        return;
+    }
 
     // 1. 1D lattice sums
     for (int idx = warp; idx < 3 * sa.M; idx += nw) {
@@ -315,49 +326,57 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__re
     }
     __syncthreads();
 
-    // 4. chains (one thread)
-    if (tid == 0) {
-        if (sa.kind == 0) {
-            int cur = -1;
-            double wcur = start_w;
-            int nacc = 0;
-            for (int t = 0; t < P; ++t) {
-                if (pu_s[t] * wcur < pw_s[t]) { cur = t; wcur = pw_s[t]; ++nacc; }
-                int4 mm = cur < 0 ? make_int4(start_m[0], start_m[1], start_m[2], 0) : pm_s[cur];
-                mr[3 * t] = mm.x; mr[3 * t + 1] = mm.y; mr[3 * t + 2] = mm.z;
-                pm_s[t].w = cur;              // which proposal (-1: the start) is state t
-            }
-            cnt_r = nacc;
-            // recalibration chain: y_0 = x_1, proposals x_t, g of a state = g of its source
-            int src0 = pm_s[0].w;
-            double gcur = src0 < 0 ? start_g : pg_s[src0];
-            int ym[3] = {mr[0], mr[1], mr[2]};
-            int nn = 0;
-            for (int t = 0; t < P; ++t) {
-                int src = pm_s[t].w;
-                double gt = src < 0 ? start_g : pg_s[src];
-                if (pun_s[t] * gcur < gt) {
-                    ym[0] = mr[3 * t]; ym[1] = mr[3 * t + 1]; ym[2] = mr[3 * t + 2];
-                    gcur = gt;
-                    ++nn;
+    // 4. chains, warp 0: a block of 32 states is loaded at once (one lane per
+    // state); the accept tests then run in order with the uniforms and weights
+    // broadcast by shuffles, so every decision sees the same operands as a
+    // sequential loop.
+    if (warp == 0 && sa.kind != 1) {
+        int cur = -1;                         // kind 0: proposal index of the current radial state
+        double wcur = start_w, gcur = 0.0;
+        int nacc = 0, nn = 0;
+        int ym0 = 0, ym1 = 0, ym2 = 0;        // current recalibration state
+        if (sa.kind == 2) { ym0 = nrstart_m[0]; ym1 = nrstart_m[1]; ym2 = nrstart_m[2]; gcur = nrstart_g; }
+        for (int t0 = 0; t0 < P; t0 += 32) {
+            const int t = t0 + lane, nt = min(32, P - t0);
+            const bool valid = t < P;
+            int m0, m1, m2;
+            double gt;
+            if (sa.kind == 0) {
+                const double u = valid ? pu_s[t] : 0.0, w = valid ? pw_s[t] : 0.0;
+                int mysrc = -1;
+                for (int j = 0; j < nt; ++j) {
+                    const double uj = __shfl_sync(0xffffffffu, u, j), wj = __shfl_sync(0xffffffffu, w, j);
+                    if (uj * wcur < wj) { cur = t0 + j; wcur = wj; ++nacc; }
+                    if (lane == j) mysrc = cur;
                 }
-                mnr[3 * t] = ym[0]; mnr[3 * t + 1] = ym[1]; mnr[3 * t + 2] = ym[2];
-            }
-            cnt_nr = nn;
-        } else if (sa.kind == 2) {
-            int ym[3] = {nrstart_m[0], nrstart_m[1], nrstart_m[2]};
-            double gcur = nrstart_g;
-            int nn = 0;
-            for (int t = 0; t < P; ++t) {
-                if (pun_s[t] * gcur < pg_s[t]) {
-                    ym[0] = mr[3 * t]; ym[1] = mr[3 * t + 1]; ym[2] = mr[3 * t + 2];
-                    gcur = pg_s[t];
-                    ++nn;
+                int4 mm = make_int4(start_m[0], start_m[1], start_m[2], 0);
+                gt = start_g;
+                if (valid && mysrc >= 0) { mm = pm_s[mysrc]; gt = pg_s[mysrc]; }
+                m0 = mm.x; m1 = mm.y; m2 = mm.z;
+                if (valid) { mr[3 * t] = m0; mr[3 * t + 1] = m1; mr[3 * t + 2] = m2; }
+                if (t0 == 0) {                // y_0 = x_1: the first radial state
+                    gcur = __shfl_sync(0xffffffffu, gt, 0);
+                    ym0 = __shfl_sync(0xffffffffu, m0, 0);
+                    ym1 = __shfl_sync(0xffffffffu, m1, 0);
+                    ym2 = __shfl_sync(0xffffffffu, m2, 0);
                 }
-                mnr[3 * t] = ym[0]; mnr[3 * t + 1] = ym[1]; mnr[3 * t + 2] = ym[2];
+            } else {
+                m0 = valid ? mr[3 * t] : 0; m1 = valid ? mr[3 * t + 1] : 0; m2 = valid ? mr[3 * t + 2] : 0;
+                gt = valid ? pg_s[t] : 0.0;
             }
-            cnt_nr = nn;
+            // recalibration chain: proposals are the radial states x_t
+            const double un = valid ? pun_s[t] : 0.0;
+            int y0 = 0, y1 = 0, y2 = 0;
+            for (int j = 0; j < nt; ++j) {
+                const double uj = __shfl_sync(0xffffffffu, un, j), gj = __shfl_sync(0xffffffffu, gt, j);
+                const int c0 = __shfl_sync(0xffffffffu, m0, j), c1 = __shfl_sync(0xffffffffu, m1, j),
+                          c2 = __shfl_sync(0xffffffffu, m2, j);
+                if (uj * gcur < gj) { ym0 = c0; ym1 = c1; ym2 = c2; gcur = gj; ++nn; }
+                if (lane == j) { y0 = ym0; y1 = ym1; y2 = ym2; }
+            }
+            if (valid) { mnr[3 * t] = y0; mnr[3 * t + 1] = y1; mnr[3 * t + 2] = y2; }
         }
+        if (lane == 0) { cnt_r = nacc; cnt_nr = nn; }
     }
     __syncthreads();
 
@@ -382,23 +401,39 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__re
             __syncthreads();
         }
     }
-    // segment heads and compaction (one thread: at most 2P <= 8192 keys)
-    if (tid == 0) {
-        int nd = -1;
-        uint64_t prev = ~0ull;
-        for (int k = 0; k < n2; ++k) {
-            uint64_t mk = keys[k] >> 1;
-            if (mk != prev) {
-                ++nd;
-                int m[3];
-                key_mode(mk, m);
-                D[3 * nd] = m[0]; D[3 * nd + 1] = m[1]; D[3 * nd + 2] = m[2];
-                cr[nd] = 0; cnr[nd] = 0;
-                prev = mk;
-            }
-            if (keys[k] & 1ull) cnr[nd] += 1; else cr[nd] += 1;
+    // 6. segment heads, their ranks by a block scan, multiplicities by a walk
+    // over each (short) segment: within a segment the radial entries (tag 0)
+    // precede the recalibrated ones (tag 1)
+    const int per = (n2 + blockDim.x - 1) / blockDim.x;
+    const int k0 = min(n2, tid * per), k1 = min(n2, k0 + per);
+    int nh = 0;
+    for (int k = k0; k < k1; ++k) nh += (k == 0 || (keys[k] >> 1) != (keys[k - 1] >> 1));
+    int incl = nh;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) scan_w[warp] = incl;
+    __syncthreads();
+    int base = incl - nh;
+    for (int w = 0; w < warp; ++w) base += scan_w[w];
+    for (int k = k0; k < k1; ++k) {
+        const uint64_t mk = keys[k] >> 1;
+        if (k > 0 && mk == (keys[k - 1] >> 1)) continue;
+        int e = k, nr0 = 0, nr1 = 0;
+        while (e < n2 && (keys[e] >> 1) == mk) {
+            if (keys[e] & 1ull) ++nr1; else ++nr0;
+            ++e;
         }
-        d.nD = nd + 1;
+        int m[3];
+        key_mode(mk, m);
+        D[3 * base] = m[0]; D[3 * base + 1] = m[1]; D[3 * base + 2] = m[2];
+        cr[base] = nr0; cnr[base] = nr1;
+        ++base;
+    }
+    if (tid == blockDim.x - 1) {
+        d.nD = base;                          // the last thread ends after every head
         d.nacc_r = cnt_r;
         d.nacc_nr = cnt_nr;
     }

@@ -60,6 +60,10 @@ struct rbsog_ctx {
     double *bk = nullptr, *br0 = nullptr, *ak = nullptr, *at0 = nullptr;
     double *pair_part = nullptr, *lr_out = nullptr, *mol_part = nullptr, *kin_part = nullptr, *sysred = nullptr;
     double *self_e = nullptr;
+    double4 *fpart = nullptr;   // pair forces per dz plane (FP32 build reads it as float4)
+    double *inv_m = nullptr, *sdv = nullptr;   // per-atom integrator constants
+    double2 *ljd = nullptr;     // LJ blocks per system
+    float2 *ljf = nullptr, *ljf_lo = nullptr;
     int *mr = nullptr, *mnr = nullptr, *D = nullptr, *cr = nullptr, *cnr = nullptr;
     int4 *pm = nullptr;
     double *pw = nullptr, *pg = nullptr, *pu = nullptr, *pun = nullptr;
@@ -75,8 +79,9 @@ struct rbsog_ctx {
     SogConsts sc{};
     SamplerArgs sa{};
     IntegArgs ia{};
-    // graph of one NPT step
-    cudaGraphExec_t graph = nullptr;
+    // graphs of one NPT step: [0] forces and virial, [1] also energies
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned long long h_step = 0;   // host copy of the device step counter
     // timing
     bool timing = false;
     std::vector<std::string> t_names;
@@ -149,7 +154,7 @@ void record(rbsog_ctx *c, const char *name)
 }
 
 // One force evaluation of every system (Algorithm 1 steps 2-7).
-void enqueue_eval(rbsog_ctx *c, int kick, int box_kick)
+void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy)
 {
     const int prec = c->prm.precision;
     record(c, "start");
@@ -166,7 +171,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick)
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
-    launch_pair(c->b, c->a, prec, c->pcf, c->pcd, c->pair_part, c->st);
+    launch_pair(c->b, c->a, prec, c->pcf, c->pcd, energy, c->pair_part, c->st);
     record(c, "pair");
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
@@ -186,11 +191,11 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick)
     record(c, "finalize");
 }
 
-void enqueue_npt_step(rbsog_ctx *c)
+void enqueue_npt_step(rbsog_ctx *c, int energy)
 {
     launch_box_half(c->b, c->ia, c->sysred, c->st);
     launch_atom_update(c->b, c->a, c->ia, c->st);
-    enqueue_eval(c, 1, 1);
+    enqueue_eval(c, 1, 1, energy);
 }
 
 rbsog_status check_flags(rbsog_ctx *c)
@@ -248,7 +253,8 @@ rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
 void free_ctx(rbsog_ctx *c)
 {
     if (!c) return;
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
     for (auto e : c->t_events) cudaEventDestroy(e);
     for (void *v : c->allocs) cudaFree(v);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -264,7 +270,7 @@ rbsog_status validate(const rbsog_params *p, int S, const rbsog_system_desc *sy)
     if (!(p->rc > 0) || !(p->b > 1) || !(p->sigma > 0) || p->M < 1 || p->M > kMaxGauss ||
         p->M_energy < p->M || p->M_energy > kMaxGauss || p->P < 1 || p->P > kMaxP ||
         p->sampler < 0 || p->sampler > 2 || (p->precision != 0 && p->precision != 1) ||
-        (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2)
+        (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2 || p->thermo_every < 0)
         return RBSOG_EINVAL;
     for (int s = 0; s < S; ++s) {
         const rbsog_system_desc &d = sy[s];
@@ -273,6 +279,8 @@ rbsog_status validate(const rbsog_params *p, int S, const rbsog_system_desc *sy)
             return RBSOG_EINVAL;
         for (int a = 0; a < 3; ++a)
             if (!(d.box[a] > 0)) return RBSOG_EBOX;
+        for (int i = 0; i < d.n_atoms; ++i)
+            if (!(d.mass[i] > 0) || !std::isfinite(d.mass[i])) return RBSOG_EINVAL;
     }
     return RBSOG_OK;
 }
@@ -294,6 +302,7 @@ void rbsog_default_params(rbsog_params *p, double rc)
     p->sampler = RBSOG_SAMPLER_PAPER;
     p->seed = 1;
     p->precision = RBSOG_FP32;
+    p->thermo_every = 1;
     p->ke = 332.06371;
     p->dt = 0.5;
     p->T = 300.0;
@@ -366,6 +375,10 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         std::vector<int> type, mol;
         std::vector<int> b_start{0}, a_start{0}, e_start{0}, bonds, angles, excl;
         std::vector<double> bk, br0, ak, at0;
+        std::vector<double2> ljd;
+        std::vector<double> inv_m, sdv;
+        const double c_atom = std::exp(-P.gamma * P.dt);
+        std::vector<float2> ljf, ljf_lo;
         int N = 0, C = 0, nmol = 0, item_cap = 0;
         std::vector<double> w, s, wt, st;
         const int MM = std::max(P.M, P.M_energy);
@@ -381,7 +394,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                 int n = (int)std::floor(d.box[a] * P.cell_sub / P.rc);
                 if (n < 2 * P.cell_sub + 1) {
                     rbsog_status rr = fail(c, RBSOG_EBOX, "system " + std::to_string(k) + ": box edge " +
-                                                              std::to_string(d.box[a]) + " < 3 r_c");
+                                                              std::to_string(d.box[a]) + " too small for the cell stencil");
                     free_ctx(c);
                     return rr;
                 }
@@ -392,14 +405,26 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             ds.V = d.box[0] * d.box[1] * d.box[2];
             ds.cell0 = C;
             ds.ncell_cap_total = ncap_t;
-            // pair work items: at most one partial 32-atom group per cell
+            // pair work items: at most one partial 32-atom group per cell; a
+            // multiple of kPairWarps so that no pair-kernel block spans two systems
             ds.item0 = item_cap;
-            ds.item_cap = (d.n_atoms + 31) / 32 + ncap_t;
+            ds.item_cap = ((d.n_atoms + 31) / 32 + ncap_t + kPairWarps - 1) / kPairWarps * kPairWarps;
             item_cap += ds.item_cap;
             ds.atom0 = N;
             ds.n = d.n_atoms;
             ds.coupling = P.coupling == RBSOG_COUPLE_SEMI_ISO ? 1 : 0;
             ds.rng_id = d.rng_id;
+            // LJ block of this system: (4 eps sig^12, 4 eps sig^6) per type pair
+            ds.ntypes = d.ntypes;
+            ds.lj0 = (int)ljd.size();
+            for (int t = 0; t < d.ntypes * d.ntypes; ++t) {
+                const double eps = d.lj_eps[t], sg = d.lj_sig[t];
+                const double s6 = sg * sg * sg * sg * sg * sg;
+                ljd.push_back(make_double2(4.0 * eps * s6 * s6, 4.0 * eps * s6));
+                ljf.push_back(make_float2((float)ljd.back().x, (float)ljd.back().y));
+                ljf_lo.push_back(make_float2((float)(ljd.back().x - (double)ljf.back().x),
+                                             (float)(ljd.back().y - (double)ljf.back().y)));
+            }
             // box masses: M_g = n_g^2 V ftm2v / (kappa L_g^2 omega^2), kappa in (kcal/mol/A^3)^-1
             if (P.coupling != RBSOG_COUPLE_FIXED && P.tau_box > 0 && P.compressibility > 0) {
                 const double kap = P.compressibility * kNktv2p, om = 2.0 * kPi / P.tau_box;
@@ -423,6 +448,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                 }
                 q.push_back(d.q[i]);
                 mass.push_back(d.mass[i]);
+                inv_m.push_back(1.0 / d.mass[i]);
+                sdv.push_back(std::sqrt((1.0 - c_atom * c_atom) * d.mass[i] * kKB * P.T * kFtm2v));
                 if (d.type[i] < 0 || d.type[i] >= d.ntypes) {
                     rbsog_status rr = fail(c, RBSOG_EINVAL, "atom type out of range");
                     free_ctx(c);
@@ -501,6 +528,12 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             nmol += nm;
             N += d.n_atoms;
         }
+        if (N >= (1 << 25)) {
+            // the pair kernel's queue packs a neighbour index into 25 bits
+            rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "more than 2^25 - 1 atoms in one context");
+            free_ctx(c);
+            return rr;
+        }
         c->N = N; c->C = C; c->nmol = nmol; c->item_cap = item_cap;
         c->nchunks = (int)chunk_sys.size();
         c->nmchunks = (int)mchunk_sys.size();
@@ -520,9 +553,10 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                   upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
-                  dalloc(c, c->pair_part, (size_t)item_cap * 14) &&
+                  dalloc(c, c->pair_part, (size_t)item_cap * (2 * P.cell_sub + 1) / kPairWarps * kPairRec) &&
+                  dalloc(c, c->fpart, (size_t)N * (2 * P.cell_sub + 1)) &&
                   dalloc(c, c->lr_out, (size_t)S * 16) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
-                  dalloc(c, c->kin_part, (size_t)c->nchunks * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
+                  dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
                   dalloc(c, c->mr, (size_t)S * P.P * 3) && dalloc(c, c->mnr, (size_t)S * P.P * 3) &&
                   dalloc(c, c->D, (size_t)S * c->Dcap * 3) && dalloc(c, c->cr, (size_t)S * c->Dcap) &&
                   dalloc(c, c->cnr, (size_t)S * c->Dcap) && dalloc(c, c->pm, (size_t)S * P.P) &&
@@ -530,7 +564,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                   dalloc(c, c->pu, (size_t)S * P.P) && dalloc(c, c->pun, (size_t)S * P.P) &&
                   dalloc(c, c->sk_part, (size_t)c->nchunks * c->Dcap * 2) &&
                   dalloc(c, c->rho, (size_t)S * c->Dcap * 2) && dalloc(c, c->coef, (size_t)S * c->Dcap) &&
-                  dalloc(c, c->d_step, 1);
+                  dalloc(c, c->d_step, 1) && upload(c, c->ljd, ljd) && upload(c, c->ljf, ljf) && upload(c, c->ljf_lo, ljf_lo) &&
+                  upload(c, c->inv_m, inv_m) && upload(c, c->sdv, sdv);
         if (ok) {
             if (P.precision == 1)
                 ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, N) && dalloc(c, c->qt, N) && dalloc(c, c->su, N);
@@ -545,38 +580,48 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         // ---- constants
         c->sc.M = P.M; c->sc.ME = P.M_energy; c->sc.rc = P.rc; c->sc.ke = P.ke;
         for (int l = 0; l < MM; ++l) { c->sc.w[l] = w[l]; c->sc.s[l] = s[l]; c->sc.wt[l] = wt[l]; c->sc.st[l] = st[l]; }
-        const rbsog_system_desc &d0 = systems[0];
-        int nt = d0.ntypes;
-        for (int k = 1; k < S; ++k) nt = std::max(nt, systems[k].ntypes);
         c->pcf.M = c->pcd.M = P.M;
         c->pcf.ME = c->pcd.ME = P.M_energy;
-        c->pcf.ntypes = c->pcd.ntypes = nt;
-        c->pcf.rc2 = (float)(P.rc * P.rc); c->pcd.rc2 = P.rc * P.rc;
+        c->pcf.rc2 = (float)(P.rc * P.rc); c->pcd.rc2 = P.rc * P.rc; c->pcf.rc2d = P.rc * P.rc;
+        c->pcf.rc2_hi = (float)(P.rc * P.rc * (1.0 + 1e-5));
+        c->pcf.rc2_lo = (float)(P.rc * P.rc * (1.0 - 1e-5));
         c->pcf.ke = (float)P.ke; c->pcd.ke = P.ke;
         for (int l = 0; l < MM; ++l) {
-            c->pcf.beta[l] = (float)(1.4426950408889634 / (s[l] * s[l]));
-            c->pcf.w[l] = (float)w[l];
-            c->pcf.wt[l] = l < P.M ? (float)wt[l] : 0.f;
             c->pcd.inv_s2[l] = 1.0 / (s[l] * s[l]);
             c->pcd.w[l] = w[l];
             c->pcd.wt[l] = l < P.M ? wt[l] : 0.0;
         }
-        // LJ: one table per context (systems with fewer types use the leading block)
-        for (int i = 0; i < nt; ++i)
-            for (int j = 0; j < nt; ++j) {
-                double eps = 0, sg = 0;
-                for (int k = 0; k < S; ++k)
-                    if (i < systems[k].ntypes && j < systems[k].ntypes) {
-                        eps = systems[k].lj_eps[i * systems[k].ntypes + j];
-                        sg = systems[k].lj_sig[i * systems[k].ntypes + j];
-                        break;
-                    }
-                double s6 = sg * sg * sg * sg * sg * sg;
-                c->pcd.lj_a[i * nt + j] = 4.0 * eps * s6 * s6;
-                c->pcd.lj_b[i * nt + j] = 4.0 * eps * s6;
-                c->pcf.lj_a[i * nt + j] = (float)c->pcd.lj_a[i * nt + j];
-                c->pcf.lj_b[i * nt + j] = (float)c->pcd.lj_b[i * nt + j];
+        {
+            // FP32 split: Gaussians with s_l >= 2.5 r_c go into a Taylor tail in u = r^2
+            const double swide = 2.5 * P.rc, log2e = 1.4426950408889634;
+            int nff = 0, nfe = 0;
+            while (nff < P.M && st[nff] < swide) ++nff;
+            while (nfe < P.M_energy && s[nfe] < swide) ++nfe;
+            c->pcf.nff = nff;
+            c->pcf.nfe = nfe;
+            for (int l = 0; l < MM; ++l) {
+                c->pcf.beta[l] = (float)(log2e / (st[l] * st[l]));
+                c->pcf.wt[l] = l < P.M ? (float)wt[l] : 0.f;
+                const double be = log2e / (s[l] * s[l]);
+                c->pcf.be_hi[l] = (float)be;
+                c->pcf.be_lo[l] = (float)(be - (double)c->pcf.be_hi[l]);
+                c->pcf.w_hi[l] = (float)w[l];
+                c->pcf.w_lo[l] = (float)(w[l] - (double)c->pcf.w_hi[l]);
             }
+            // sum_l w_l e^{-u/s_l^2} = sum_k u^k sum_l w_l (-1/s_l^2)^k / k!
+            double te0 = 0.0;
+            for (int k = 0; k <= kTail; ++k) {
+                double tk = 0.0, ek = 0.0, fact = 1.0;
+                for (int i = 2; i <= k; ++i) fact *= i;
+                for (int l = nff; l < P.M; ++l) tk += wt[l] * std::pow(-1.0 / (st[l] * st[l]), k) / fact;
+                for (int l = nfe; l < P.M_energy; ++l) ek += w[l] * std::pow(-1.0 / (s[l] * s[l]), k) / fact;
+                c->pcf.tt[k] = (float)tk;
+                c->pcf.te[k] = k == 0 ? 0.f : (float)ek;
+                if (k == 0) te0 = ek;
+            }
+            c->pcf.te0 = te0;
+        }
+        // LJ: one ntypes x ntypes block per system (uploaded with the buffers above)
         // sampler (the same expressions as the paper's formulas, FP64 on the host)
         c->sa.P = P.P; c->sa.M = P.M; c->sa.kind = P.sampler; c->sa.seed = P.seed; c->sa.step = c->d_step;
         const double pi15 = std::pow(kPi, 1.5);
@@ -590,6 +635,9 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         c->sa.sig_u = 1.0 / (std::sqrt(2.0) * kPi * st[0]);
         c->ia.dt = P.dt; c->ia.T = P.T; c->ia.Pext = P.P_ext; c->ia.gamma = P.gamma; c->ia.gamma_box = P.gamma_box;
         c->ia.kB = kKB; c->ia.ftm2v = kFtm2v; c->ia.nktv2p = kNktv2p; c->ia.seed = P.seed; c->ia.step = c->d_step;
+        c->ia.c_atom = std::exp(-P.gamma * P.dt);
+        c->ia.inv_m = c->inv_m; c->ia.sdv = c->sdv;
+        c->ia.noise_f32 = P.precision == RBSOG_FP32 ? 1 : 0;
 
         c->b.S = S; c->b.N = N; c->b.C = C; c->b.sub = P.cell_sub; c->b.rc = P.rc; c->b.sys = c->sys;
         c->b.atom_sys = c->atom_sys; c->b.cell_sys = c->cell_sys; c->b.chunk_sys = c->chunk_sys;
@@ -599,6 +647,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
         c->a.su = c->su; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
+        c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
+        c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
         c->m.nmol = nmol; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
@@ -612,7 +662,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         unsigned long long minus1 = ~0ull;
         cudaMemcpyAsync(c->d_step, &minus1, sizeof(minus1), cudaMemcpyHostToDevice, c->st);
         launch_clear_flags(c->b, c->st);
-        enqueue_eval(c, 0, 0);
+        enqueue_eval(c, 0, 0, 1);
+        c->h_step = 0;
         e = cudaStreamSynchronize(c->st);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) { rbsog_status rr = cuda_fail(c, e, "first evaluation"); free_ctx(c); return rr; }
@@ -692,7 +743,8 @@ rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_devi
     c->t_events.clear();
     c->t_names.clear();
     launch_clear_flags(c->b, c->st);
-    enqueue_eval(c, 0, 0);
+    enqueue_eval(c, 0, 0, 1);
+    c->h_step = (unsigned long long)step;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     if (forces) {
@@ -714,20 +766,20 @@ rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_devi
     return RBSOG_OK;
 }
 
-static rbsog_status ensure_graph(rbsog_ctx *c)
+static rbsog_status ensure_graph(rbsog_ctx *c, int energy)
 {
     cudaError_t e;
-    if (!c->graph) {
+    if (!c->graph[energy]) {
         bool t = c->timing;
         c->timing = false;
         cudaGraph_t g;
         e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "capture");
-        enqueue_npt_step(c);
+        enqueue_npt_step(c, energy);
         e = cudaStreamEndCapture(c->st, &g);
         c->timing = t;
         if (e != cudaSuccess) return cuda_fail(c, e, "capture end");
-        e = cudaGraphInstantiate(&c->graph, g, 0);
+        e = cudaGraphInstantiate(&c->graph[energy], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
     }
@@ -738,11 +790,15 @@ rbsog_status rbsog_run_async(rbsog_ctx *c, int nsteps)
 {
     if (!c || nsteps < 0) return RBSOG_EINVAL;
     if (c->prm.dt <= 0) return fail(c, RBSOG_EINVAL, "dt must be positive");
-    rbsog_status gs = ensure_graph(c);
-    if (gs != RBSOG_OK) return gs;
     for (int n = 0; n < nsteps; ++n) {
-        cudaError_t e = cudaGraphLaunch(c->graph, c->st);
+        // energies on the last step of the call and on every thermo_every-th step
+        const unsigned long long next = c->h_step + 1ull;
+        const int en = (n == nsteps - 1) || (c->prm.thermo_every > 0 && next % c->prm.thermo_every == 0);
+        rbsog_status gs = ensure_graph(c, en);
+        if (gs != RBSOG_OK) return gs;
+        cudaError_t e = cudaGraphLaunch(c->graph[en], c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+        c->h_step = next;
     }
     return RBSOG_OK;
 }
@@ -818,6 +874,7 @@ rbsog_status rbsog_set_state(rbsog_ctx *c, const void *buf, size_t len)
     if (e == cudaSuccess) e = cudaMemcpy(c->sysred, o, sizeof(double) * c->S * kRed, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_step, &step, sizeof(step), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    c->h_step = step;
     return RBSOG_OK;
 }
 

@@ -46,7 +46,7 @@ class rbsog_params(C.Structure):
                 ("seed", C.c_uint64), ("precision", C.c_int), ("ke", C.c_double),
                 ("dt", C.c_double), ("T", C.c_double), ("P_ext", C.c_double), ("gamma", C.c_double),
                 ("gamma_box", C.c_double), ("tau_box", C.c_double), ("compressibility", C.c_double),
-                ("coupling", C.c_int), ("cell_sub", C.c_int)]
+                ("coupling", C.c_int), ("cell_sub", C.c_int), ("thermo_every", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -136,7 +136,10 @@ def _ptr(x):
 def rbsog_default_params(rc=10.0, **kw) -> rbsog_params:
     p = rbsog_params()
     lib().rbsog_default_params(C.byref(p), rc)
+    names = {f[0] for f in rbsog_params._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"rbsog_params has no field {k!r}")
         setattr(p, k, v)
     return p
 
