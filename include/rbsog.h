@@ -50,7 +50,8 @@ typedef enum {
     RBSOG_EUNSUPPORTED = -5,  /* option not supported */
     RBSOG_ETIMEOUT = -6,      /* a bounded device wait gave up */
     RBSOG_ECUDA = -7,         /* CUDA runtime error */
-    RBSOG_EOVERFLOW = -8      /* a cell holds more atoms than the kernels take */
+    RBSOG_EOVERFLOW = -8      /* a cell holds more atoms than the kernels take, or a
+                                 request exceeds a fixed scratch */
 } rbsog_status;
 
 /* Sampler kinds (sec. 3.2, App. D). */
@@ -251,6 +252,31 @@ size_t rbsog_structure_factor_workspace(int n_atoms, int nD);
 rbsog_status rbsog_structure_factor(const double *r, const double *q, int n_atoms,
                                     const double box[3], const int *m, int nD,
                                     double *rho, void *work, int precision, void *stream);
+
+/* Allocation-free variant of rbsog_structure_factor (the paper has no
+ * counterpart: this is an interface for host programs, not part of the
+ * method).  Same arguments and results as rbsog_structure_factor, without
+ * `work`: the scratch is a fixed 4 MiB device array inside the library, one
+ * per device.  For callers that may not allocate device memory while they
+ * run -- an MD engine that has handed all device memory to its own pool, or
+ * that keeps work in flight on other streams, cannot let a call reach
+ * cudaMalloc (which may fail mid-run) or cudaFree (which waits for the whole
+ * device).  This call performs no device allocation or free.
+ *   - Size limit: rbsog_structure_factor_workspace(n_atoms, nD) must not
+ *     exceed 4 MiB (e.g. 100,000 atoms with up to ~1,600 modes); larger
+ *     requests return RBSOG_EOVERFLOW before anything is launched, with the
+ *     reason in rbsog_last_error(NULL).
+ *   - The first call on a device does a one-time set-up (it looks up the
+ *     scratch address with that device current); make that first call before
+ *     any stream capture begins.
+ *   - Calls on the same device must not overlap in time: two calls running at
+ *     once on different streams share the scratch and race.
+ *   - Nothing in the scratch needs clearing between calls.
+ * Errors: RBSOG_EINVAL (null pointer, n_atoms < 1, nD < 1, bad precision),
+ * RBSOG_EBOX (box edge <= 0), RBSOG_EOVERFLOW (too large), RBSOG_ECUDA. */
+rbsog_status rbsog_structure_factor_noalloc(const double *r, const double *q, int n_atoms,
+                                            const double box[3], const int *m, int nD,
+                                            double *rho, int precision, void *stream);
 
 #ifdef __cplusplus
 }

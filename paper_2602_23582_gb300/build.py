@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librbsog.so")
 SOURCES = ["k_bin.cu", "k_pair.cu", "k_sampler.cu", "k_kspace.cu", "k_mol.cu", "k_integrate.cu",
-           "rbsog_api.cu"]
+           "k_sk_static.cu", "rbsog_api.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Wno-deprecated-declarations",

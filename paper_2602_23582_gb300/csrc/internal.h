@@ -123,6 +123,9 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
                      int Dcap, cudaStream_t st);
 size_t sk_stateless_workspace(int n, int nD);
+// k_sk_static.cu: a fixed scratch for the allocation-free variant
+constexpr size_t kSkStaticBytes = (size_t)4 << 20;
+cudaError_t sk_static_scratch(void **ptr);
 cudaError_t sk_stateless(const double *r, const double *q, int n, const double box[3], const int *m,
                          int nD, double *rho, void *work, int precision, cudaStream_t st);
 

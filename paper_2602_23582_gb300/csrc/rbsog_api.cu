@@ -951,4 +951,28 @@ rbsog_status rbsog_structure_factor(const double *r, const double *q, int n_atom
     return e == cudaSuccess ? RBSOG_OK : RBSOG_ECUDA;
 }
 
+rbsog_status rbsog_structure_factor_noalloc(const double *r, const double *q, int n_atoms, const double box[3],
+                                            const int *m, int nD, double *rho, int precision, void *stream)
+{
+    if (!r || !q || !box || !m || !rho || n_atoms < 1 || nD < 1 || (precision != 0 && precision != 1))
+        return RBSOG_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0)) return RBSOG_EBOX;
+    const size_t need = sk_stateless_workspace(n_atoms, nD);
+    if (need > kSkStaticBytes) {
+        g_create_err = "rbsog_structure_factor_noalloc: " + std::to_string(n_atoms) + " atoms and " +
+                       std::to_string(nD) + " modes need " + std::to_string(need) +
+                       " bytes of scratch; the fixed scratch holds " + std::to_string(kSkStaticBytes);
+        return RBSOG_EOVERFLOW;
+    }
+    void *work = nullptr;
+    cudaError_t e = sk_static_scratch(&work);
+    if (e != cudaSuccess) {
+        g_create_err = std::string("rbsog_structure_factor_noalloc: scratch set-up: ") + cudaGetErrorString(e);
+        return RBSOG_ECUDA;
+    }
+    e = sk_stateless(r, q, n_atoms, box, m, nD, rho, work, precision, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RBSOG_OK : RBSOG_ECUDA;
+}
+
 }  // extern "C"

@@ -31,7 +31,7 @@ EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_
            "rbsog_get_velocities", "rbsog_step", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
            "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_set_timing", "rbsog_get_timing",
            "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
-           "rbsog_sync", "rbsog_stream")
+           "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc")
 
 
 class RbsogError(RuntimeError):
@@ -114,6 +114,7 @@ def lib():
     L.rbsog_structure_factor_workspace.argtypes = [C.c_int, C.c_int]
     L.rbsog_structure_factor_workspace.restype = C.c_size_t
     L.rbsog_structure_factor.argtypes = [P, P, C.c_int, _D, P, C.c_int, P, P, C.c_int, P]
+    L.rbsog_structure_factor_noalloc.argtypes = [P, P, C.c_int, _D, P, C.c_int, P, C.c_int, P]
     _lib = L
     return L
 
@@ -297,6 +298,19 @@ def rbsog_structure_factor(r, q, box, m, rho, work, precision=RBSOG_FP32, stream
                                           precision, st)
     if status != RBSOG_OK:
         raise RbsogError(status, "rbsog_structure_factor")
+
+
+def rbsog_structure_factor_noalloc(r, q, box, m, rho, precision=RBSOG_FP32, stream=None):
+    """As rbsog_structure_factor, with the library's fixed scratch instead of a
+    caller workspace (no device allocation; calls on one device must not
+    overlap in time)."""
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    st = C.c_void_p(stream) if stream else None
+    status = lib().rbsog_structure_factor_noalloc(C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()),
+                                                  int(q.numel()), b, C.c_void_p(m.data_ptr()), int(m.shape[0]),
+                                                  C.c_void_p(rho.data_ptr()), precision, st)
+    if status != RBSOG_OK:
+        raise RbsogError(status, lib().rbsog_last_error(None).decode())
 
 
 def result_dict(r: rbsog_result) -> dict:
