@@ -32,7 +32,7 @@ METRIC = "RBSOG atom-steps/s on 1 GB300 (plain vs batched); p50/p99 step latency
 UNIT = "atom-steps/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
-MUFU_PER_SM_CLK = 16          # special-function results per SM per clock
+MUFU_PER_SM_CLK = 32          # ex2 results per SM per clock on this part (probe: 30.3 at 2070 MHz)
 FP32_LANES = 128              # FP32 FMA lanes per SM
 # algorithmic work per half-pair inside r_c (M~ = 10): 10 exp + 1 rsqrt on the
 # special-function unit, ~67 FP32 operations
@@ -98,6 +98,22 @@ def clock_summary(path, dev_index):
                 reasons.add(nm)
     return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
             "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def pair_traffic(workload_name, prec):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary,
+    or None when the kernel source has changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "pair_kernel.json")
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_2602_23582_gb300", "csrc", "k_pair.cu"), "rb").read()
+        if rec.get("k_pair_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        key = f"{workload_name}_{'fp32' if prec == 1 else 'fp64'}"
+        return rec["dram_bytes_per_launch"].get(key)
+    except Exception:
+        return None
 
 
 def load_peaks():
@@ -171,6 +187,9 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--thermo", type=int, default=100,
+                    help="energies every this many steps (as MD thermo output); forces and the "
+                         "virial are computed every step either way")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -195,7 +214,7 @@ def main():
         s.rng_id = 1000 * rank + k
     prec = R.RBSOG_FP32 if args.precision == "fp32" else R.RBSOG_FP64
     stream = torch.cuda.Stream(device=dev)
-    p = R.rbsog_default_params(10.0, precision=prec)
+    p = R.rbsog_default_params(10.0, precision=prec, thermo_every=args.thermo)
     ctx = R.Context(systems, p, stream=stream.cuda_stream)
     n_atoms = ctx.n_atoms
 
@@ -221,6 +240,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    R.rbsog_trace_pair(ctx.ctx, args.steps)      # events around the pair kernel of each timed step
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.fill_(float(k))
@@ -229,6 +249,8 @@ def main():
             ev[k][1].record(stream)
     torch.cuda.synchronize()
     R.rbsog_sync(ctx.ctx)
+    pair_trace = R.rbsog_trace_pair_times(ctx.ctx, args.steps)
+    R.rbsog_trace_pair(ctx.ctx, 0)
     if world > 1:
         dist.barrier()
     if proc is not None:
@@ -241,6 +263,25 @@ def main():
         t = torch.tensor([total_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
+
+    # ---- the same steps with energies evaluated every step
+    n_en = min(args.steps, 200)
+    R.rbsog_set_thermo_every(ctx.ctx, 1)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_en)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(n_en):
+            flush.fill_(float(k))
+            ev2[k][0].record(stream)
+            R.rbsog_run_async(ctx.ctx, 1)
+            ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    R.rbsog_sync(ctx.ctx)
+    R.rbsog_set_thermo_every(ctx.ctx, args.thermo)
+    en_ms = np.array([a.elapsed_time(b) for a, b in ev2])
+    energy_every_step = {"value": n_atoms * world * n_en / (float(en_ms.sum()) / 1e3), "unit": UNIT,
+                         "ms_per_step": float(en_ms.mean()), "steps": n_en,
+                         "p50_ms": float(np.percentile(en_ms, 50)), "p99_ms": float(np.percentile(en_ms, 99))}
 
     # ---- e2e through the C ABI with host buffers (positions in, forces out)
     e2e = None
@@ -272,28 +313,39 @@ def main():
     s0 = systems[0]
     rho_n = s0.n / float(np.prod(s0.box))
     half_pairs = 0.5 * s0.n * (4.0 / 3.0 * math.pi * p.rc ** 3 * rho_n)
-    pair_ms = kernel_ms.get("pair")
+    pair_ms = float(np.mean(pair_trace)) if len(pair_trace) else None
     peaks = load_peaks()
     sm_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     clocks = clock_summary(clk_path, local) if rank == 0 else None
     roof = None
     if pair_ms:
+        # bound: max(MUFU work / MUFU peak, FP32 work / FP32 peak); on this part the FP32 side binds
         mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clk / 1e12
-        achieved = half_pairs * PAIR_MUFU_PER_UNIT / (pair_ms * 1e-3) / 1e12
+        fp32_peak = SM_COUNT * FP32_LANES * sm_clk / 1e12
+        t_mufu = half_pairs * PAIR_MUFU_PER_UNIT / (mufu_peak * 1e12)
+        t_fp32 = half_pairs * PAIR_FP32_PER_UNIT / (fp32_peak * 1e12)
+        fp32_bound = t_fp32 >= t_mufu
+        per = PAIR_FP32_PER_UNIT if fp32_bound else PAIR_MUFU_PER_UNIT
+        peak = fp32_peak if fp32_bound else mufu_peak
+        achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_pair_f32" if prec == R.RBSOG_FP32 else "k_pair_f64",
-                "achieved": achieved, "peak": mufu_peak, "unit": "Top/s (MUFU)",
-                "frac": achieved / mufu_peak, "traffic": None,
+                "achieved": achieved, "peak": peak,
+                "unit": "Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)",
+                "frac": achieved / peak, "traffic": pair_traffic(args.workload, prec),
                 "units_per_launch": half_pairs, "per_unit": f"{PAIR_MUFU_PER_UNIT} MUFU + "
                 f"{PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c",
-                "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU/clk x {sm_clk / 1e6:.0f} MHz (max clock)",
-                "launch_ms": pair_ms}
+                "peak_basis": f"{SM_COUNT} SMs x ({FP32_LANES} FP32 lanes, {MUFU_PER_SM_CLK} MUFU)/clk x "
+                              f"{sm_clk / 1e6:.0f} MHz (max clock); roofline time MUFU {t_mufu * 1e6:.1f} us, "
+                              f"FP32 {t_fp32 * 1e6:.1f} us",
+                "launch_ms": pair_ms, "launch_ms_p50": float(np.percentile(pair_trace, 50)),
+                "timing": "CUDA events recorded by the step graph around each timed pair launch"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             cpu = cpu_baseline(systems)
         except Exception as ex:   # reported, not fatal
             cpu = {"error": str(ex)}
-    kernels_per_step = 16   # box_half .. step_advance, one graph replay
+    kernels_per_step = 17   # box_half .. step_advance, one graph replay
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == R.RBSOG_FP32 else "f64",
@@ -304,7 +356,9 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write)",
                        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                        "ns_per_day": (p.dt * 1e-6) / (float(step_ms.mean()) / 1e3 / 86400.0),
-                       "kernel_ms": kernel_ms},
+                       "energies": f"every {args.thermo} steps (thermo output); forces and virial every step",
+                       "energy_every_step": energy_every_step,
+                       "kernel_ms_eager_step": kernel_ms},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": kernels_per_step * args.steps, "clocks": clocks}
     if rank == 0:

@@ -98,14 +98,13 @@ typedef struct {
     int coupling;           /* RBSOG_COUPLE_* */
     int cell_sub;           /* cells per cutoff length along an axis: 1 or 2; 0 = choose
                                (2 when a box edge is below 3.3 r_c, else 1) */
-    int thermo_every;       /* inside rbsog_run / rbsog_run_async, energies (and the
-                               Coulomb/LJ split of the short-range virial) are evaluated
-                               on the last step of each call and on steps whose counter
-                               is a multiple of thermo_every (0: last step only); the
-                               other steps compute forces and the total virial only,
-                               which is all the dynamics uses.  rbsog_step always
-                               evaluates energies.  Forces and the total virial do not
-                               depend on this setting.  Default 1 (every step). */
+    int thermo_every;       /* energies (and the Coulomb/LJ split of the short-range
+                               virial) are evaluated on steps whose counter is a
+                               multiple of thermo_every (0: none), on the last step of
+                               each rbsog_run call and by every rbsog_step; the other
+                               steps compute forces and the total virial only, which is
+                               all the dynamics uses.  Forces and the total virial do
+                               not depend on this setting.  Default 1 (every step). */
 } rbsog_params;
 
 typedef struct {
@@ -219,6 +218,9 @@ rbsog_status rbsog_run(rbsog_ctx *ctx, int nsteps, rbsog_result *last);
 rbsog_status rbsog_run_async(rbsog_ctx *ctx, int nsteps);
 rbsog_status rbsog_sync(rbsog_ctx *ctx);
 
+/* Change thermo_every (rbsog_params) of a live context; every >= 0. */
+rbsog_status rbsog_set_thermo_every(rbsog_ctx *ctx, int every);
+
 /* The context stream (cudaStream_t) the library launches on. */
 void *rbsog_stream(rbsog_ctx *ctx);
 
@@ -240,6 +242,15 @@ rbsog_status rbsog_debug_modes(rbsog_ctx *ctx, int s, int *mr, int *mnr, int *D,
  * enable != 0 records CUDA events around each kernel of one step (slower). */
 rbsog_status rbsog_set_timing(rbsog_ctx *ctx, int enable);
 rbsog_status rbsog_get_timing(rbsog_ctx *ctx, int max, char *names, double *ms, int *count);
+
+/* Pair-kernel trace for profiling inside a run: the next nsteps graph steps of
+ * rbsog_run / rbsog_run_async record CUDA events immediately before and after
+ * their pair kernel, on the context stream; rbsog_trace_pair_times waits for
+ * the stream and returns the durations (ms) of the steps traced so far, in
+ * order (at most max).  nsteps = 0 disarms.  Host cost: two graph-node
+ * updates per traced launch; device cost: two event records. */
+rbsog_status rbsog_trace_pair(rbsog_ctx *ctx, int nsteps);
+rbsog_status rbsog_trace_pair_times(rbsog_ctx *ctx, int max, double *ms, int *count);
 
 /* Stateless structure factor (eq. rho_k) on device buffers:
  *   r    device, N x 3 FP64 positions (any image)

@@ -95,9 +95,12 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 // (Ucoul, Ulj, Wc[6], Wl[6], W[6]) as kPairRec doubles; energies and the
 // Coulomb/LJ split only when `energy` is set (W, the total, always).  Each
 // system's item range is a multiple of kPairWarps items, so a block never
-// mixes systems.
-constexpr int kPairWarps = 4;
+// mixes systems.  launch_reduce_pair (k_integrate.cu) sums each system's
+// records into kPairRedBlocks records in a fixed order.
+constexpr int kPairWarps = 1;       // one warp per block: no block-level wait on a slower warp
 constexpr int kPairRec = 20;
+constexpr int kPairRedBlocks = 8;   // second-stage reduction of the unit records, per system
+void launch_reduce_pair(const Batch &b, const double *pair_part, double *pair_red, cudaStream_t st);
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st);
 

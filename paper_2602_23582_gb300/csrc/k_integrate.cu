@@ -200,6 +200,38 @@ void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &i
 //  [15..20] W short Coulomb, [21..26] W^F,r*, [27..32] W^F,nr*, [33..38] W LJ,
 //  [39..44] W bonded + exclusions, [45..50] K, [51] V, [52..54] L,
 //  [55] nD, [56] acc r, [57] acc nr, [58] flags, [59..61] box momenta.
+// Second stage of the pair records: system s's unit records (items x dz
+// planes of its active items) in kPairRedBlocks contiguous ranges, each summed
+// in a fixed order.  grid (S, kPairRedBlocks).
+constexpr int kRedThreads = 128;
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_pair(const DevSys *__restrict__ sys, int span, const double *__restrict__ part,
+              double *__restrict__ red)
+{
+    __shared__ double buf[kPairRec * (kRedThreads + 1) + 4 * kPairRec];
+    const int s = blockIdx.x;
+    const DevSys &d = sys[s];
+    const int u0 = d.item0 * span / kPairWarps;
+    const int nu = (d.nitems * span + kPairWarps - 1) / kPairWarps;
+    const int per = (nu + kPairRedBlocks - 1) / kPairRedBlocks;
+    const int a = min(nu, (int)blockIdx.y * per), e = min(nu, a + per);
+    double v[kPairRec];
+#pragma unroll
+    for (int k = 0; k < kPairRec; ++k) v[k] = 0.0;
+    for (int r = a + threadIdx.x; r < e; r += kRedThreads) {
+        const double *pp = part + (size_t)(u0 + r) * kPairRec;
+#pragma unroll
+        for (int k = 0; k < kPairRec; ++k) v[k] += pp[k];
+    }
+    block_reduce_lanes<kPairRec, kRedThreads>(v, buf, red + ((size_t)s * kPairRedBlocks + blockIdx.y) * kPairRec);
+}
+
+void launch_reduce_pair(const Batch &b, const double *pair_part, double *pair_red, cudaStream_t st)
+{
+    k_reduce_pair<<<dim3(b.S, kPairRedBlocks), kRedThreads, 0, st>>>(b.sys, 2 * b.sub + 1, pair_part, pair_red);
+}
+
 constexpr int kFinThreads = 128;
 
 __global__ void __launch_bounds__(kFinThreads)
@@ -219,11 +251,9 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
     double v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = 0.0;
-    // pair records: one per block of kPairWarps units (items x dz planes)
-    const int b0 = d.item0 * span / kPairWarps;
-    const int nb = (d.nitems * span + kPairWarps - 1) / kPairWarps;
-    for (int c = tid; c < nb; c += blockDim.x) {
-        const double *pp = pair_part + (size_t)(b0 + c) * kPairRec;
+    // pair records, already reduced to kPairRedBlocks per system
+    for (int c = tid; c < kPairRedBlocks; c += blockDim.x) {
+        const double *pp = pair_part + ((size_t)s * kPairRedBlocks + c) * kPairRec;
 #pragma unroll
         for (int k = 0; k < kPairRec; ++k) v[k] += pp[k];
     }

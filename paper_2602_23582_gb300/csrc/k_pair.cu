@@ -208,7 +208,7 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // within the plane; the warp keeps the plane's offsets in shared memory.
 // ---------------------------------------------------------------------------
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kPairWarps, 5)
+__global__ void __launch_bounds__(32 * kPairWarps, 20 / kPairWarps)
 k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
            const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4,
            const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,

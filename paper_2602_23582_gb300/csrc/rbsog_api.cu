@@ -61,6 +61,7 @@ struct rbsog_ctx {
     double *pair_part = nullptr, *lr_out = nullptr, *mol_part = nullptr, *kin_part = nullptr, *sysred = nullptr;
     double *self_e = nullptr;
     double4 *fpart = nullptr;   // pair forces per dz plane (FP32 build reads it as float4)
+    double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
     double *inv_m = nullptr, *sdv = nullptr;   // per-atom integrator constants
     double2 *ljd = nullptr;     // LJ blocks per system
     float2 *ljf = nullptr, *ljf_lo = nullptr;
@@ -81,6 +82,15 @@ struct rbsog_ctx {
     IntegArgs ia{};
     // graphs of one NPT step: [0] forces and virial, [1] also energies
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraph_t graph_src[2] = {nullptr, nullptr};
+    // pair-kernel trace: event-record nodes around the pair kernel in each
+    // graph; their events are swapped per launch to a ring of caller-visible
+    // timings (placeholders when no trace is armed)
+    cudaEvent_t ev_pair_ph[2] = {nullptr, nullptr};
+    cudaGraphNode_t pair_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool pair_node_live[2] = {false, false};
+    std::vector<cudaEvent_t> ring_s, ring_e;
+    int ring_pos = 0;
     unsigned long long h_step = 0;   // host copy of the device step counter
     // timing
     bool timing = false;
@@ -171,7 +181,14 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy)
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
+    // in a graph capture: event-record nodes around the pair kernel (external
+    // records, not dependencies), retargeted per launch by arm_pair_trace
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->st, &cap);
+    const bool trace = cap == cudaStreamCaptureStatusActive && c->ev_pair_ph[0] && c->ev_pair_ph[1];
+    if (trace) cudaEventRecordWithFlags(c->ev_pair_ph[0], c->st, cudaEventRecordExternal);
     launch_pair(c->b, c->a, prec, c->pcf, c->pcd, energy, c->pair_part, c->st);
+    if (trace) cudaEventRecordWithFlags(c->ev_pair_ph[1], c->st, cudaEventRecordExternal);
     record(c, "pair");
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
@@ -186,7 +203,8 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy)
     record(c, "molecules");
     launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
     record(c, "kick_kinetic");
-    launch_finalize(c->b, c->pair_part, c->lr_out, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
+    launch_reduce_pair(c->b, c->pair_part, c->pair_red, c->st);
+    launch_finalize(c->b, c->pair_red, c->lr_out, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, c->sysred, c->d_step, c->st);
     record(c, "finalize");
 }
@@ -255,6 +273,12 @@ void free_ctx(rbsog_ctx *c)
     if (!c) return;
     for (auto g : c->graph)
         if (g) cudaGraphExecDestroy(g);
+    for (auto g : c->graph_src)
+        if (g) cudaGraphDestroy(g);
+    for (auto e : c->ring_s) cudaEventDestroy(e);
+    for (auto e : c->ring_e) cudaEventDestroy(e);
+    for (auto e : c->ev_pair_ph)
+        if (e) cudaEventDestroy(e);
     for (auto e : c->t_events) cudaEventDestroy(e);
     for (void *v : c->allocs) cudaFree(v);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -364,6 +388,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         c->own_st2 = true;
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        cudaEventCreate(&c->ev_pair_ph[0]);
+        cudaEventCreate(&c->ev_pair_ph[1]);
         c->Dcap = (P.sampler == RBSOG_SAMPLER_IID) ? 2 * P.P : P.P + 1;
 
         // ---- host layout
@@ -555,6 +581,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
                   dalloc(c, c->pair_part, (size_t)item_cap * (2 * P.cell_sub + 1) / kPairWarps * kPairRec) &&
                   dalloc(c, c->fpart, (size_t)N * (2 * P.cell_sub + 1)) &&
+                  dalloc(c, c->pair_red, (size_t)S * kPairRedBlocks * kPairRec) &&
                   dalloc(c, c->lr_out, (size_t)S * 16) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
                   dalloc(c, c->mr, (size_t)S * P.P * 3) && dalloc(c, c->mnr, (size_t)S * P.P * 3) &&
@@ -780,26 +807,68 @@ static rbsog_status ensure_graph(rbsog_ctx *c, int energy)
         c->timing = t;
         if (e != cudaSuccess) return cuda_fail(c, e, "capture end");
         e = cudaGraphInstantiate(&c->graph[energy], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "graph instantiate"); }
+        c->graph_src[energy] = g;
+        // the event-record nodes around the pair kernel
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+            for (int k = 0; k < 2; ++k)
+                if (ev == c->ev_pair_ph[k]) c->pair_node[energy][k] = nd;
+        }
     }
     return RBSOG_OK;
 }
 
-rbsog_status rbsog_run_async(rbsog_ctx *c, int nsteps)
+// Point the pair-kernel event nodes of graph `en` at the next ring entry (or
+// back at the placeholders once the ring is used up).
+static void arm_pair_trace(rbsog_ctx *c, int en)
+{
+    if (!c->pair_node[en][0] || !c->pair_node[en][1]) return;
+    if (c->ring_pos < (int)c->ring_s.size()) {
+        cudaGraphExecEventRecordNodeSetEvent(c->graph[en], c->pair_node[en][0], c->ring_s[c->ring_pos]);
+        cudaGraphExecEventRecordNodeSetEvent(c->graph[en], c->pair_node[en][1], c->ring_e[c->ring_pos]);
+        c->pair_node_live[en] = true;
+        ++c->ring_pos;
+    } else if (c->pair_node_live[en]) {
+        cudaGraphExecEventRecordNodeSetEvent(c->graph[en], c->pair_node[en][0], c->ev_pair_ph[0]);
+        cudaGraphExecEventRecordNodeSetEvent(c->graph[en], c->pair_node[en][1], c->ev_pair_ph[1]);
+        c->pair_node_live[en] = false;
+    }
+}
+
+// Enqueue nsteps graph steps; energies on steps whose counter is a multiple
+// of thermo_every, and on the last one when last_energy is set.
+static rbsog_status run_steps(rbsog_ctx *c, int nsteps, bool last_energy)
 {
     if (!c || nsteps < 0) return RBSOG_EINVAL;
     if (c->prm.dt <= 0) return fail(c, RBSOG_EINVAL, "dt must be positive");
     for (int n = 0; n < nsteps; ++n) {
-        // energies on the last step of the call and on every thermo_every-th step
         const unsigned long long next = c->h_step + 1ull;
-        const int en = (n == nsteps - 1) || (c->prm.thermo_every > 0 && next % c->prm.thermo_every == 0);
+        const int en = (last_energy && n == nsteps - 1) ||
+                       (c->prm.thermo_every > 0 && next % (unsigned long long)c->prm.thermo_every == 0);
         rbsog_status gs = ensure_graph(c, en);
         if (gs != RBSOG_OK) return gs;
+        arm_pair_trace(c, en);
         cudaError_t e = cudaGraphLaunch(c->graph[en], c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
         c->h_step = next;
     }
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_run_async(rbsog_ctx *c, int nsteps) { return run_steps(c, nsteps, false); }
+
+rbsog_status rbsog_set_thermo_every(rbsog_ctx *c, int every)
+{
+    if (!c || every < 0) return RBSOG_EINVAL;
+    c->prm.thermo_every = every;
     return RBSOG_OK;
 }
 
@@ -817,7 +886,7 @@ rbsog_status rbsog_run(rbsog_ctx *c, int nsteps, rbsog_result *last)
 {
     if (!c || nsteps < 0) return RBSOG_EINVAL;
     launch_clear_flags(c->b, c->st);
-    rbsog_status rs = rbsog_run_async(c, nsteps);
+    rbsog_status rs = run_steps(c, nsteps, true);
     if (rs != RBSOG_OK) return rs;
     rbsog_status fs = check_flags(c);
     if (fs != RBSOG_OK) return fs;
@@ -929,6 +998,47 @@ rbsog_status rbsog_get_timing(rbsog_ctx *c, int max, char *names, double *ms, in
             std::strncpy(names + 32 * k, c->t_names[k + 1].c_str(), 31);
             names[32 * k + 31] = 0;
         }
+    }
+    *count = n;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_trace_pair(rbsog_ctx *c, int nsteps)
+{
+    if (!c || nsteps < 0) return RBSOG_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "trace");
+    // point every graph node back at the placeholders before the ring's events go
+    for (int en = 0; en < 2; ++en) {
+        if (!c->pair_node_live[en]) continue;
+        cudaGraphExecEventRecordNodeSetEvent(c->graph[en], c->pair_node[en][0], c->ev_pair_ph[0]);
+        cudaGraphExecEventRecordNodeSetEvent(c->graph[en], c->pair_node[en][1], c->ev_pair_ph[1]);
+        c->pair_node_live[en] = false;
+    }
+    for (auto ev : c->ring_s) cudaEventDestroy(ev);
+    for (auto ev : c->ring_e) cudaEventDestroy(ev);
+    c->ring_s.assign(nsteps, nullptr);
+    c->ring_e.assign(nsteps, nullptr);
+    for (int k = 0; k < nsteps; ++k) {
+        e = cudaEventCreate(&c->ring_s[k]);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ring_e[k]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "trace events");
+    }
+    c->ring_pos = 0;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_trace_pair_times(rbsog_ctx *c, int max, double *ms, int *count)
+{
+    if (!c || !count) return RBSOG_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "trace");
+    const int n = std::min(max, c->ring_pos);
+    for (int k = 0; k < n; ++k) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, c->ring_s[k], c->ring_e[k]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "trace times");
+        if (ms) ms[k] = t;
     }
     *count = n;
     return RBSOG_OK;

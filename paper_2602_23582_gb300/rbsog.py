@@ -31,7 +31,8 @@ EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_
            "rbsog_get_velocities", "rbsog_step", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
            "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_set_timing", "rbsog_get_timing",
            "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
-           "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc")
+           "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc", "rbsog_trace_pair",
+           "rbsog_trace_pair_times", "rbsog_set_thermo_every")
 
 
 class RbsogError(RuntimeError):
@@ -115,6 +116,9 @@ def lib():
     L.rbsog_structure_factor_workspace.restype = C.c_size_t
     L.rbsog_structure_factor.argtypes = [P, P, C.c_int, _D, P, C.c_int, P, P, C.c_int, P]
     L.rbsog_structure_factor_noalloc.argtypes = [P, P, C.c_int, _D, P, C.c_int, P, C.c_int, P]
+    L.rbsog_trace_pair.argtypes = [P, C.c_int]
+    L.rbsog_set_thermo_every.argtypes = [P, C.c_int]
+    L.rbsog_trace_pair_times.argtypes = [P, C.c_int, _D, _I]
     _lib = L
     return L
 
@@ -298,6 +302,21 @@ def rbsog_structure_factor(r, q, box, m, rho, work, precision=RBSOG_FP32, stream
                                           precision, st)
     if status != RBSOG_OK:
         raise RbsogError(status, "rbsog_structure_factor")
+
+
+def rbsog_set_thermo_every(ctx, every):
+    _check(lib().rbsog_set_thermo_every(ctx, int(every)), ctx)
+
+
+def rbsog_trace_pair(ctx, nsteps):
+    _check(lib().rbsog_trace_pair(ctx, int(nsteps)), ctx)
+
+
+def rbsog_trace_pair_times(ctx, max_steps):
+    ms = np.zeros(max(int(max_steps), 1))
+    n = C.c_int(0)
+    _check(lib().rbsog_trace_pair_times(ctx, int(max_steps), ms.ctypes.data_as(_D), C.byref(n)), ctx)
+    return ms[:n.value]
 
 
 def rbsog_structure_factor_noalloc(r, q, box, m, rho, precision=RBSOG_FP32, stream=None):
