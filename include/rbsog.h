@@ -243,6 +243,63 @@ rbsog_status rbsog_debug_modes(rbsog_ctx *ctx, int s, int *mr, int *mnr, int *D,
 rbsog_status rbsog_set_timing(rbsog_ctx *ctx, int enable);
 rbsog_status rbsog_get_timing(rbsog_ctx *ctx, int max, char *names, double *ms, int *count);
 
+/* ---- Pool of slots (the served path: many systems stepping in the same
+ * kernel launches, entering and leaving at run time).
+ *
+ * A pool context has n_slots slots, each sized by its rbsog_slot_caps (the
+ * cell grid takes boxes up to 1.15 max_box); all device memory is allocated
+ * by rbsog_pool_create.  Slots start empty.  rbsog_run / rbsog_run_async
+ * step every running slot together; a slot loaded with nsteps > 0 stops after
+ * that many NPT steps (its state frozen, its last results kept) until it is
+ * unloaded.  Each system keeps its own Philox counter (0 at its first
+ * evaluation), so its trajectory does not depend on the other slots. */
+typedef struct {
+    int max_atoms, max_molecules, max_bonds, max_angles, max_excl, max_types;
+    double max_box[3];
+} rbsog_slot_caps;
+
+rbsog_status rbsog_pool_create(const rbsog_params *params, int n_slots, const rbsog_slot_caps *caps,
+                               void *stream, rbsog_ctx **out);
+/* Copy a system into an empty slot (host arrays as for rbsog_create; nsteps
+ * > 0 or -1 for no limit).  Waits for the context stream.  Errors:
+ * RBSOG_EINVAL (slot busy, system larger than the slot, bad system). */
+rbsog_status rbsog_pool_load(rbsog_ctx *ctx, int slot, const rbsog_system_desc *sys, int nsteps);
+/* Evaluate forces, energies and virial of every running slot at its current
+ * counter: required after loading, before stepping (slots already running
+ * recompute identical values).  Waits and checks the flags. */
+rbsog_status rbsog_pool_prime(rbsog_ctx *ctx);
+/* Per slot: 0 empty, 1 running, 2 finished; step: its Philox counter (may be NULL). */
+rbsog_status rbsog_pool_state(rbsog_ctx *ctx, int *state, unsigned long long *step);
+/* Copy out positions (r), velocities (v) -- n x 3 host buffers of the slot's
+ * system, either may be NULL -- and the results of its last step, then empty
+ * the slot. */
+rbsog_status rbsog_pool_unload(rbsog_ctx *ctx, int slot, double *r, double *v, rbsog_result *res);
+
+/* ---- Request loop of the served path (rbsog_server.cpp, on the pool API).
+ * rbsog_server_create sizes a pool to hbm_fraction of the free device memory
+ * (at most n_slots slots, classes caps[0..n) in order).  Requests wait in
+ * arrival order; each rbsog_server_pump call retires finished requests,
+ * admits queued ones into free slots that fit them (first fit), primes them,
+ * then advances every running slot up to max_steps NPT steps in the same
+ * launches.  Step latencies (CUDA events per step) and aggregate atom-steps/s
+ * over the pumped steps are kept for rbsog_server_stats. */
+typedef struct rbsog_server rbsog_server;
+rbsog_status rbsog_server_create(const rbsog_params *params, int n_slots, const rbsog_slot_caps *caps,
+                                 double hbm_fraction, void *stream, rbsog_server **out);
+void rbsog_server_destroy(rbsog_server *srv);
+int rbsog_server_slots(const rbsog_server *srv);
+rbsog_ctx *rbsog_server_context(rbsog_server *srv);
+/* Queue a copy of `sys` for nsteps NPT steps; RBSOG_EUNSUPPORTED if it fits no slot. */
+rbsog_status rbsog_server_submit(rbsog_server *srv, const rbsog_system_desc *sys, int nsteps,
+                                 long long *ticket);
+rbsog_status rbsog_server_pump(rbsog_server *srv, int max_steps, int *n_running, int *n_queued);
+/* done = 1 once the request finished; then r, v (n x 3, may be NULL) and the
+ * results of its last step. */
+rbsog_status rbsog_server_result(rbsog_server *srv, long long ticket, int *done, double *r, double *v,
+                                 rbsog_result *res);
+rbsog_status rbsog_server_stats(const rbsog_server *srv, double *p50_ms, double *p99_ms,
+                                double *atom_steps_per_s, long long *steps);
+
 /* Pair-kernel trace for profiling inside a run: the next nsteps graph steps of
  * rbsog_run / rbsog_run_async record CUDA events immediately before and after
  * their pair kernel, on the context stream; rbsog_trace_pair_times waits for

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librbsog.so")
 SOURCES = ["k_bin.cu", "k_pair.cu", "k_sampler.cu", "k_kspace.cu", "k_mol.cu", "k_integrate.cu",
-           "k_sk_static.cu", "rbsog_api.cu"]
+           "k_sk_static.cu", "rbsog_api.cu", "rbsog_server.cpp"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Wno-deprecated-declarations",
@@ -40,7 +40,7 @@ def _stale() -> bool:
 
 
 def _compile(src: str, extra=()) -> str:
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [_nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -55,8 +55,16 @@ struct DevSys {
     int item0, item_cap;  // pair-kernel work items: [item0, item0 + item_cap)
     int nitems;           // items of the current cell list
     int ntypes, lj0;      // LJ types of the system and its first entry in the context's LJ table
+    int nmol, mol0;       // molecules of the system and its first global molecule index
+    int act;              // 1: the slot holds a system that steps; 0: empty or finished
+    int steps_left;       // NPT steps before the system stops (-1: no limit)
     unsigned long long rng_id;   // second word of the Philox key
+    unsigned long long step;     // Philox counter of the system's last force evaluation
 };
+
+// Atoms of a system that take part in the current step (0 for an empty or
+// finished slot).
+__host__ __device__ inline int live_n(const DevSys &d) { return d.act ? d.n : 0; }
 
 // Per-distinct-mode data handed from the estimator to the force kernel.
 struct ModeCoef {

@@ -108,12 +108,12 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
 struct SamplerArgs {
     int P, M, kind;
     uint64_t seed;
-    const unsigned long long *step;   // the evaluation uses *step + 1
     double wt[kMaxGauss], st[kMaxGauss];
     double cr[kMaxGauss], cn[kMaxGauss], st2q[kMaxGauss];
     double sig_u;
 };
-void launch_sampler(const Batch &b, const SamplerArgs &sa, int *mr, int *mnr, int *D, int *cr,
+// adv = 1: the evaluation of an NPT step (counter DevSys::step + 1); 0: re-evaluate at DevSys::step
+void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int *mnr, int *D, int *cr,
                     int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, int Dcap,
                     cudaStream_t st);
 
@@ -154,8 +154,7 @@ struct IntegArgs {
     double c_atom;                    // exp(-gamma dt)
     const double *inv_m, *sdv;        // per atom: 1 / m, sqrt((1 - c^2) m kB T ftm2v)
     int noise_f32;                    // 1: Gaussian noise drawn in FP32 (FP32 build)
-    uint64_t seed;
-    const unsigned long long *step;   // device counter of the last evaluation; a step uses *step + 1
+    uint64_t seed;                    // a step uses the Philox counter DevSys::step + 1
 };
 void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st);
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st);
@@ -167,8 +166,10 @@ constexpr int kRed = 64;
 void launch_finalize(const Batch &b, const double *pair_part, const double *lr_out,
                      const double *mol_part, const int *mchunk_first, const int *mchunk_count,
                      const double *kin_part, const int *chunk_first, const int *chunk_count,
-                     const double *self_energy, const IntegArgs &ia, int do_box_kick,
-                     double *sysred, unsigned long long *step, cudaStream_t st);
+                     const double *self_energy, const IntegArgs &ia, int do_box_kick, int adv,
+                     double *sysred, cudaStream_t st);
+// DevSys::step = step for every system
+void launch_set_step(const Batch &b, unsigned long long step, cudaStream_t st);
 cudaError_t prepare_sampler(int P);
 cudaError_t prepare_pair();
 

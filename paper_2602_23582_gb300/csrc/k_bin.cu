@@ -18,6 +18,10 @@ __global__ void k_box_prep(DevSys *sys, int S, int sub, double rc)
     if (s >= S) return;
     DevSys &d = sys[s];
     const int minc = 2 * sub + 1;
+    if (live_n(d) == 0) {                     // empty slot: a valid grid, no checks
+        for (int a = 0; a < 3; ++a) { d.ncell[a] = minc; d.w[a] = 1.0; }
+        return;
+    }
     for (int a = 0; a < 3; ++a) {
         double L = d.L[a];
         double x = floor(__ddiv_rn(__dmul_rn(L, (double)sub), rc));
@@ -56,8 +60,14 @@ __global__ void k_bin(const DevSys *__restrict__ sys, const int *__restrict__ at
                       double4 *__restrict__ locd, uint4 *__restrict__ su, int precision)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned act = __ballot_sync(0xffffffffu, i < N);
-    if (i >= N) return;
+    bool live = false;
+    if (i < N) {
+        const DevSys &ds = sys[atom_sys[i]];
+        live = i - ds.atom0 < live_n(ds);     // slots hold up to their capacity
+        if (!live) cell[i] = -1;
+    }
+    const unsigned act = __ballot_sync(0xffffffffu, live);
+    if (!live) return;
     const DevSys &d = sys[atom_sys[i]];
     int c[3];
     double sf[3], xl[3];
@@ -155,7 +165,7 @@ __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ 
                           const int *__restrict__ start, int *__restrict__ sidx, int N)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= N || cell[i] < 0) return;
     sidx[start[cell[i]] + rank[i]] = i;
 }
 

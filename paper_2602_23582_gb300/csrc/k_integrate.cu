@@ -53,6 +53,7 @@ __global__ void k_box_half(DevSys *sys, int S, const IntegArgs ia, const double 
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     DevSys &d = sys[s];
+    if (live_n(d) == 0) return;               // empty or finished slot
     const double *red = sysred + (size_t)s * kRed;
     double G[3];
     box_force(d, red, ia, G);
@@ -67,7 +68,7 @@ __global__ void k_box_half(DevSys *sys, int S, const IntegArgs ia, const double 
         d.Lh[a] = d.L[a] + v * tau;
     }
     uint64_t wds[4];
-    draw4(ia.seed, d.rng_id, *ia.step + 1, PUR_BOX, 0, wds);
+    draw4(ia.seed, d.rng_id, d.step + 1, PUR_BOX, 0, wds);
     double z[4];
     box_muller2(wds[0], wds[1], z[0], z[1]);
     box_muller2(wds[2], wds[3], z[2], z[3]);
@@ -107,6 +108,7 @@ __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restr
     if (i >= N) return;
     const int s = atom_sys[i];
     const DevSys &d = sys[s];
+    if (i - d.atom0 >= live_n(d)) return;     // beyond the system in its slot
     const double im = ia.inv_m[i], tau = 0.5 * ia.dt, kick = 0.5 * ia.dt * ia.ftm2v;
     double x[3], v[3];
     for (int a = 0; a < 3; ++a) {
@@ -118,7 +120,7 @@ __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restr
         v[a] = v[a] * d.isc1[a];
     }
     uint64_t wds[4];
-    draw4(ia.seed, d.rng_id, *ia.step + 1, PUR_ATOM, (uint64_t)(i - d.atom0), wds);
+    draw4(ia.seed, d.rng_id, d.step + 1, PUR_ATOM, (uint64_t)(i - d.atom0), wds);
     double z[4];
     if (NF32) {
 #pragma unroll
@@ -160,12 +162,14 @@ void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia
 // Second half kick (optional) and the kinetic tensor per quarter of an atom
 // chunk: kin_part[chunk][kKinSplit][6] = sum p (x) p / m (kcal/mol).
 __global__ void __launch_bounds__(kChunk / kKinSplit)
-k_kick_kinetic(const int *__restrict__ chunk_a0, const int *__restrict__ chunk_n, double *__restrict__ p,
-               const double *__restrict__ F, const double *__restrict__ inv_m, double kick, double mvv2e,
-               double *__restrict__ kin_part)
+k_kick_kinetic(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
+               double *__restrict__ p, const double *__restrict__ F, const double *__restrict__ inv_m, double kick,
+               double mvv2e, double *__restrict__ kin_part)
 {
     __shared__ double red[6 * (kChunk / kKinSplit + 1) + 24];
-    const int c = blockIdx.x, a0 = chunk_a0[c], na = chunk_n[c];
+    const int c = blockIdx.x, a0 = chunk_a0[c];
+    const DevSys &d = sys[chunk_sys[c]];
+    const int na = min(kChunk, live_n(d) - (a0 - d.atom0));   // <= 0: beyond the system in its slot
     double k6[6] = {0, 0, 0, 0, 0, 0};
     constexpr int per = kChunk / kKinSplit;
     const int k_end = min(na, (int)(blockIdx.y + 1) * per);
@@ -191,8 +195,8 @@ void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &i
                          double *kin_part, cudaStream_t st)
 {
     const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0;
-    k_kick_kinetic<<<dim3(b.nchunks, kKinSplit), kChunk / kKinSplit, 0, st>>>(b.chunk_a0, b.chunk_n, a.p, a.F, ia.inv_m, kick, 1.0 / ia.ftm2v,
-                                              kin_part);
+    k_kick_kinetic<<<dim3(b.nchunks, kKinSplit), kChunk / kKinSplit, 0, st>>>(
+        b.sys, b.chunk_sys, b.chunk_a0, a.p, a.F, ia.inv_m, kick, 1.0 / ia.ftm2v, kin_part);
 }
 
 // Per-system reduction of all partials (fixed order) into sysred[s][kRed]:
@@ -239,14 +243,15 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
            const double *__restrict__ mol_part, const int *__restrict__ mchunk_first,
            const int *__restrict__ mchunk_count, const double *__restrict__ kin_part,
            const int *__restrict__ chunk_first, const int *__restrict__ chunk_count,
-           const double *__restrict__ self_energy, const IntegArgs ia, int do_box_kick,
-           double *__restrict__ sysred, unsigned long long *step, int span)
+           const double *__restrict__ self_energy, const IntegArgs ia, int do_box_kick, int adv,
+           double *__restrict__ sysred, int span)
 {
     constexpr int NV = kPairRec + 21;   // pair records + 15 molecule + 6 kinetic partial sums
     __shared__ double buf[NV * (kFinThreads + 1) + 4 * NV];
     __shared__ double acc[NV];
     const int s = blockIdx.x, tid = threadIdx.x;
     DevSys &d = sys[s];
+    if (!d.act) return;                       // empty or finished: keep the last results
     double *o = sysred + (size_t)s * kRed;
     double v[NV];
 #pragma unroll
@@ -305,7 +310,7 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
         finite = finite && isfinite(W[a]);
     }
     if (!finite) d.flags |= FLAG_NONFINITE;
-    if (do_box_kick) {
+    if (do_box_kick && d.n > 0) {
         double G[3];
         box_force(d, o, ia, G);
         const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
@@ -316,20 +321,32 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
     o[52] = d.L[0]; o[53] = d.L[1]; o[54] = d.L[2];
     o[55] = d.nD; o[56] = d.nacc_r; o[57] = d.nacc_nr; o[58] = d.flags;
     o[59] = d.ph[0]; o[60] = d.ph[1]; o[61] = d.ph[2];
+    if (adv) {
+        d.step += 1ull;
+        if (d.steps_left > 0 && --d.steps_left == 0) d.act = 0;   // the last requested step
+    }
+    o[62] = (double)d.step;
 }
 
-__global__ void k_step_advance(unsigned long long *step) { *step += 1ull; }
+__global__ void k_set_step(DevSys *sys, int S, unsigned long long step)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) sys[s].step = step;
+}
+
+void launch_set_step(const Batch &b, unsigned long long step, cudaStream_t st)
+{
+    k_set_step<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, step);
+}
 
 void launch_finalize(const Batch &b, const double *pair_part, const double *lr_out, const double *mol_part,
                      const int *mchunk_first, const int *mchunk_count, const double *kin_part,
                      const int *chunk_first, const int *chunk_count, const double *self_energy,
-                     const IntegArgs &ia, int do_box_kick, double *sysred, unsigned long long *step,
-                     cudaStream_t st)
+                     const IntegArgs &ia, int do_box_kick, int adv, double *sysred, cudaStream_t st)
 {
     k_finalize<<<b.S, kFinThreads, 0, st>>>(b.sys, pair_part, lr_out, mol_part, mchunk_first, mchunk_count,
                                             kin_part, chunk_first, chunk_count, self_energy, ia, do_box_kick,
-                                            sysred, step, 2 * b.sub + 1);
-    k_step_advance<<<1, 1, 0, st>>>(step);
+                                            adv, sysred, 2 * b.sub + 1);
 }
 
 }  // namespace rbsog

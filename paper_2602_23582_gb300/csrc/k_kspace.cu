@@ -115,10 +115,11 @@ k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const in
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int d0 = blockIdx.y * kModeGroup;
-    if (d0 >= d.nD) return;
+    const int na = min(kChunk, live_n(d) - (chunk_a0[c] - d.atom0));   // <= 0: beyond the system in its slot
+    if (d0 >= d.nD || na <= 0) return;
     const int nd_here = min(kModeGroup, d.nD - d0);
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
-    sk_chunk<F32>(su, r, q, L, chunk_a0[c], chunk_n[c], D + (size_t)s * Dcap * 3, d0, nd_here,
+    sk_chunk<F32>(su, r, q, L, chunk_a0[c], na, D + (size_t)s * Dcap * 3, d0, nd_here,
                   part + ((size_t)c * Dcap + d0) * 2);
 }
 
@@ -149,7 +150,8 @@ k_estimate(DevSys *sys, const int *__restrict__ first_chunk, const int *__restri
     __shared__ double sums[7];
     const int s = blockIdx.x;
     DevSys &d = sys[s];
-    const int nD = d.nD, c0 = first_chunk[s], nc = nchunk_sys[s];
+    // chunks holding atoms of the system (its slot may have more)
+    const int nD = d.nD, c0 = first_chunk[s], nc = min(nchunk_sys[s], (live_n(d) + kChunk - 1) / kChunk);
     const int *D = D_all + (size_t)s * Dcap * 3, *cr = cr_all + (size_t)s * Dcap, *cnr = cnr_all + (size_t)s * Dcap;
     double *rho = rho_all + (size_t)s * Dcap * 2;
     ModeCoef *coef = coef_all + (size_t)s * Dcap;
@@ -228,10 +230,10 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
     __shared__ double td[F32 ? 1 : kModeTile][5];
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
-    const int nD = d.nD, a0 = chunk_a0[c], na = chunk_n[c];
+    const int nD = d.nD, a0 = chunk_a0[c], na = min(kChunk, live_n(d) - (a0 - d.atom0));
     const ModeCoef *coef = coef_all + (size_t)s * Dcap;
     const int k = blockIdx.y * kLrAtoms + threadIdx.x;
-    if (blockIdx.y * kLrAtoms >= na) return;          // whole block beyond the chunk
+    if ((int)(blockIdx.y * kLrAtoms) >= na) return;   // whole block beyond the chunk
     const bool act = k < na;
     const int i = a0 + (act ? k : 0);
     float fx = 0.f, fy = 0.f, fz = 0.f;

@@ -50,7 +50,8 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     R ue_rem = 0;      // sum ke q_i q_j (F_E(0) - F_E(r)) (the constant part is added on the host)
     double ue = 0.0;   // FP64 build: the full exclusion energy
     const int k = threadIdx.x;
-    if (k < mchunk_n[c]) {
+    // molecules of the system present (its slot may hold more)
+    if (k < min(mchunk_n[c], (d.act ? d.nmol : 0) - (mchunk_m0[c] - d.mol0))) {
         const int mi = mchunk_m0[c] + k;
         // bonds and angles in FP64 in both builds: near equilibrium r - r0 and
         // theta - theta0 are small differences of O(1) numbers, and FP32

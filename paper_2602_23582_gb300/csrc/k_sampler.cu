@@ -180,7 +180,7 @@ __device__ inline void key_mode(uint64_t k, int m[3])
 
 // scratch per system: [P] proposal modes (int4) + w, g, u_r, u_nr (double)
 __global__ void __launch_bounds__(256)
-k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__restrict__ mnr_out,
+k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, int *__restrict__ mnr_out,
           int *__restrict__ D_out, int *__restrict__ cr_out, int *__restrict__ cnr_out,
           int4 *__restrict__ pm, double *__restrict__ pw, double *__restrict__ pg,
           double *__restrict__ pu, double *__restrict__ pun, int Dcap)
@@ -194,7 +194,7 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__re
     __shared__ int scan_w[8];
     const int s = blockIdx.x;
     DevSys &d = sys[s];
-    const uint64_t step = *sa.step + 1;
+    const uint64_t step = d.step + (uint64_t)adv;
     const int P = sa.P, tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
     int *mr = mr_out + (size_t)s * P * 3, *mnr = mnr_out + (size_t)s * P * 3;
     int *D = D_out + (size_t)s * Dcap * 3, *cr = cr_out + (size_t)s * Dcap, *cnr = cnr_out + (size_t)s * Dcap;
@@ -203,7 +203,7 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int *__restrict__ mr_out, int *__re
     double *pu_s = pu + (size_t)s * P, *pun_s = pun + (size_t)s * P;
     if (tid < 3) sh.L[tid] = d.L[tid];
     __syncthreads();
-    if (d.flags & FLAG_BOX) {                 // invalid box: no modes; the step is reported as failed
+    if ((d.flags & FLAG_BOX) || live_n(d) == 0) {   // empty slot, or invalid box (the step is reported as failed)
         if (tid == 0) { d.nD = 0; d.nacc_r = 0; d.nacc_nr = 0; }
         return;
     }
@@ -451,11 +451,11 @@ cudaError_t prepare_sampler(int P)
     return cudaFuncSetAttribute(k_sampler, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sampler_smem(P));
 }
 
-void launch_sampler(const Batch &b, const SamplerArgs &sa, int *mr, int *mnr, int *D, int *cr,
+void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int *mnr, int *D, int *cr,
                     int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, int Dcap,
                     cudaStream_t st)
 {
-    k_sampler<<<b.S, 256, sampler_smem(sa.P), st>>>(b.sys, sa, mr, mnr, D, cr, cnr, pm, pw, pg, pu, pun, Dcap);
+    k_sampler<<<b.S, 256, sampler_smem(sa.P), st>>>(b.sys, sa, adv, mr, mnr, D, cr, cnr, pm, pw, pg, pu, pun, Dcap);
 }
 
 }  // namespace rbsog

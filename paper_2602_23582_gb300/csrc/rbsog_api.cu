@@ -27,16 +27,38 @@ constexpr double kKB = 0.0019872067;                         // kcal/(mol K)
 constexpr double kFtm2v = 1.0 / 48.88821291 / 48.88821291;   // (kcal/mol/A)/(g/mol) -> A/fs^2
 constexpr double kNktv2p = 68568.415;                        // atm per kcal/(mol A^3)
 
-template <typename T>
-struct DevBuf {
-    T *p = nullptr;
-    size_t n = 0;
+// Capacities of one slot of a context: a fixed batch sizes them by its
+// systems, a pool by the caller's slot classes.
+struct SlotCaps {
+    int atoms = 0, mols = 0, bonds = 0, angles = 0, excl = 0, types = 1;
+    double box[3] = {0.0, 0.0, 0.0};   // largest box the slot's cell grid is sized for
+};
+
+// Where a slot's data lives in the context's arrays.
+struct SlotLayout {
+    SlotCaps caps;
+    int atom0 = 0, mol0 = 0, bond0 = 0, angle0 = 0, excl0 = 0, lj0 = 0;
+};
+
+// Host image of one system in its slot (global indices already applied).
+struct SlotImage {
+    std::vector<double> r, p, q, mass, inv_m, sdv;
+    std::vector<int> type, mol;
+    std::vector<int> b_start, a_start, e_start;   // nmol + 1
+    std::vector<int> bonds, angles, excl;
+    std::vector<double> bk, br0, ak, at0;
+    std::vector<double2> ljd;
+    std::vector<float2> ljf, ljf_lo;
+    double self_e[2] = {0.0, 0.0};
 };
 
 }  // namespace
 
 struct rbsog_ctx {
     rbsog_params prm{};
+    std::vector<SlotLayout> lay;        // per slot
+    std::vector<double> sog_w;          // w_l (energy split), for per-system constants
+    bool pool = false;                  // slots are loaded and emptied at run time
     int S = 0, N = 0, C = 0, Dcap = 0, nchunks = 0, nmol = 0, nmchunks = 0, item_cap = 0;
     cudaStream_t st = nullptr, st2 = nullptr;
     bool own_st = false, own_st2 = false;
@@ -70,7 +92,6 @@ struct rbsog_ctx {
     double *pw = nullptr, *pg = nullptr, *pu = nullptr, *pun = nullptr;
     double *sk_part = nullptr, *rho = nullptr;
     ModeCoef *coef = nullptr;
-    unsigned long long *d_step = nullptr;
     // launch descriptions
     Batch b{};
     AtomArrays a{};
@@ -164,7 +185,9 @@ void record(rbsog_ctx *c, const char *name)
 }
 
 // One force evaluation of every system (Algorithm 1 steps 2-7).
-void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy)
+// adv = 1: the evaluation of an NPT step (Philox counter DevSys::step + 1,
+// advanced at the end); 0: evaluate at DevSys::step.
+void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
 {
     const int prec = c->prm.precision;
     record(c, "start");
@@ -172,7 +195,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy)
     record(c, "box_prep");
     cudaEventRecord(c->ev_fork, c->st);
     cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
-    launch_sampler(c->b, c->sa, c->mr, c->mnr, c->D, c->cr, c->cnr, c->pm, c->pw, c->pg, c->pu, c->pun,
+    launch_sampler(c->b, c->sa, adv, c->mr, c->mnr, c->D, c->cr, c->cnr, c->pm, c->pw, c->pg, c->pu, c->pun,
                    c->Dcap, c->st2);
     cudaEventRecord(c->ev_join, c->st2);
     launch_bin(c->b, c->a, prec, c->st);
@@ -205,7 +228,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy)
     record(c, "kick_kinetic");
     launch_reduce_pair(c->b, c->pair_part, c->pair_red, c->st);
     launch_finalize(c->b, c->pair_red, c->lr_out, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
-                    c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, c->sysred, c->d_step, c->st);
+                    c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
     record(c, "finalize");
 }
 
@@ -213,7 +236,7 @@ void enqueue_npt_step(rbsog_ctx *c, int energy)
 {
     launch_box_half(c->b, c->ia, c->sysred, c->st);
     launch_atom_update(c->b, c->a, c->ia, c->st);
-    enqueue_eval(c, 1, 1, energy);
+    enqueue_eval(c, 1, 1, energy, 1);
 }
 
 rbsog_status check_flags(rbsog_ctx *c)
@@ -239,8 +262,6 @@ rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
 {
     std::vector<double> h((size_t)c->S * kRed);
     cudaError_t e = cudaMemcpyAsync(h.data(), c->sysred, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
-    unsigned long long step = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&step, c->d_step, sizeof(step), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "results");
     static const int sym[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};   // 3x3 row-major from xx yy zz xy xz yz
@@ -263,7 +284,7 @@ rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
         r.n_distinct_modes = (int)o[55];
         r.n_accept_r = (int)o[56];
         r.n_accept_nr = (int)o[57];
-        r.step = step;
+        r.step = (uint64_t)o[62];
     }
     return RBSOG_OK;
 }
@@ -288,24 +309,166 @@ void free_ctx(rbsog_ctx *c)
     delete c;
 }
 
-rbsog_status validate(const rbsog_params *p, int S, const rbsog_system_desc *sy)
+SlotCaps caps_of(const rbsog_system_desc &d)
 {
-    if (!p || S <= 0 || !sy) return RBSOG_EINVAL;
+    SlotCaps cp;
+    cp.atoms = d.n_atoms;
+    int nm = 0;
+    for (int i = 0; i < d.n_atoms; ++i)
+        if (i == 0 || d.mol[i] != d.mol[i - 1]) ++nm;
+    cp.mols = nm;
+    cp.bonds = d.n_bonds;
+    cp.angles = d.n_angles;
+    cp.excl = d.n_excl;
+    cp.types = d.ntypes;
+    for (int a = 0; a < 3; ++a) cp.box[a] = d.box[a];
+    return cp;
+}
+
+// Image of system d for the slot `ly`; fills the per-system fields of ds
+// (box, box masses, counts, Philox key word, step 0).  false + why on a
+// system that does not fit the slot or is inconsistent.
+bool build_image(const rbsog_params &P, const SlotLayout &ly, DevSys &ds, const rbsog_system_desc &d,
+                 const std::vector<double> &w, SlotImage &im, std::string &why)
+{
+    const SlotCaps &cp = ly.caps;
+    const int n = d.n_atoms;
+    if (n > cp.atoms || d.ntypes > cp.types || d.n_bonds > cp.bonds || d.n_angles > cp.angles ||
+        d.n_excl > cp.excl) {
+        why = "system larger than its slot";
+        return false;
+    }
+    for (int a = 0; a < 3; ++a) {
+        const double x = std::floor(d.box[a] * P.cell_sub / P.rc);
+        if (!(x >= 2 * P.cell_sub + 1)) { why = "box edge too small for the cell stencil"; return false; }
+        if (!(x <= ds.ncap[a])) { why = "box larger than its slot's cell grid"; return false; }
+    }
+    const double c_atom = std::exp(-P.gamma * P.dt);
+    im.r.assign(d.r0, d.r0 + 3 * (size_t)n);
+    im.p.resize(3 * (size_t)n);
+    im.q.assign(d.q, d.q + n);
+    im.mass.assign(d.mass, d.mass + n);
+    im.inv_m.resize(n);
+    im.sdv.resize(n);
+    im.type.assign(d.type, d.type + n);
+    im.mol.assign(d.mol, d.mol + n);
+    double sq = 0.0;
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) im.p[3 * i + a] = d.v0 ? d.v0[3 * i + a] * d.mass[i] : 0.0;
+        im.inv_m[i] = 1.0 / d.mass[i];
+        im.sdv[i] = std::sqrt((1.0 - c_atom * c_atom) * d.mass[i] * kKB * P.T * kFtm2v);
+        if (d.type[i] < 0 || d.type[i] >= d.ntypes) { why = "atom type out of range"; return false; }
+        sq += d.q[i] * d.q[i];
+    }
+    // App. A: U_self = ln b / (sqrt(2 pi) sigma) (omega + (1 - b^{-(M-1)})/(b - 1)) sum q^2
+    im.self_e[0] = P.ke * std::log(P.b) / (std::sqrt(2.0 * kPi) * P.sigma) *
+                   (P.omega + (1.0 - std::pow(P.b, -(P.M_energy - 1.0))) / (P.b - 1.0)) * sq;
+    // FP32 build: the constant part sum_excl ke q_i q_j F_E(0) of the exclusion energy
+    if (P.precision == RBSOG_FP32) {
+        double fe0 = 0.0, sx = 0.0;
+        for (int l = 0; l < P.M_energy; ++l) fe0 += w[l];
+        for (int e2 = 0; e2 < d.n_excl; ++e2) sx += d.q[d.excl[2 * e2]] * d.q[d.excl[2 * e2 + 1]];
+        im.self_e[1] = P.ke * fe0 * sx;
+    }
+    // molecules: maximal runs of equal mol id; their term lists in molecule order
+    std::vector<int> mol_of(n);
+    int nm = 0;
+    for (int i = 0; i < n; ++i) {
+        if (i == 0 || d.mol[i] != d.mol[i - 1]) ++nm;
+        mol_of[i] = nm - 1;
+    }
+    if (nm > cp.mols) { why = "more molecules than the slot holds"; return false; }
+    std::vector<std::vector<int>> mb(nm), ma(nm), me(nm);
+    auto same = [&](int i, int j) { return i >= 0 && j >= 0 && i < n && j < n && mol_of[i] == mol_of[j]; };
+    for (int e2 = 0; e2 < d.n_bonds; ++e2) {
+        const int i = d.bonds[2 * e2], j = d.bonds[2 * e2 + 1];
+        if (!same(i, j)) { why = "a bond spans two molecules"; return false; }
+        mb[mol_of[i]].push_back(e2);
+    }
+    for (int e2 = 0; e2 < d.n_angles; ++e2) {
+        const int i = d.angles[3 * e2], j = d.angles[3 * e2 + 1], kk = d.angles[3 * e2 + 2];
+        if (!same(i, j) || !same(j, kk)) { why = "an angle spans two molecules"; return false; }
+        ma[mol_of[i]].push_back(e2);
+    }
+    for (int e2 = 0; e2 < d.n_excl; ++e2) {
+        const int i = d.excl[2 * e2], j = d.excl[2 * e2 + 1];
+        if (!same(i, j)) { why = "an exclusion spans two molecules"; return false; }
+        me[mol_of[i]].push_back(e2);
+    }
+    const int A0 = ly.atom0;
+    im.b_start.assign(1, ly.bond0);
+    im.a_start.assign(1, ly.angle0);
+    im.e_start.assign(1, ly.excl0);
+    for (int mm = 0; mm < nm; ++mm) {
+        for (int e2 : mb[mm]) {
+            im.bonds.push_back(A0 + d.bonds[2 * e2]); im.bonds.push_back(A0 + d.bonds[2 * e2 + 1]);
+            im.bk.push_back(d.bond_k[e2]); im.br0.push_back(d.bond_r0[e2]);
+        }
+        for (int e2 : ma[mm]) {
+            for (int t = 0; t < 3; ++t) im.angles.push_back(A0 + d.angles[3 * e2 + t]);
+            im.ak.push_back(d.angle_k[e2]); im.at0.push_back(d.angle_t0[e2]);
+        }
+        for (int e2 : me[mm]) { im.excl.push_back(A0 + d.excl[2 * e2]); im.excl.push_back(A0 + d.excl[2 * e2 + 1]); }
+        im.b_start.push_back(ly.bond0 + (int)im.bk.size());
+        im.a_start.push_back(ly.angle0 + (int)im.ak.size());
+        im.e_start.push_back(ly.excl0 + (int)im.excl.size() / 2);
+    }
+    // LJ block: (4 eps sig^12, 4 eps sig^6) per type pair, FP32 hi + lo copies
+    for (int t = 0; t < d.ntypes * d.ntypes; ++t) {
+        const double eps = d.lj_eps[t], sg = d.lj_sig[t];
+        const double s6 = sg * sg * sg * sg * sg * sg;
+        im.ljd.push_back(make_double2(4.0 * eps * s6 * s6, 4.0 * eps * s6));
+        im.ljf.push_back(make_float2((float)im.ljd.back().x, (float)im.ljd.back().y));
+        im.ljf_lo.push_back(make_float2((float)(im.ljd.back().x - (double)im.ljf.back().x),
+                                        (float)(im.ljd.back().y - (double)im.ljf.back().y)));
+    }
+    // per-system fields
+    for (int a = 0; a < 3; ++a) { ds.L[a] = d.box[a]; ds.ph[a] = 0.0; ds.Mbox[a] = 0.0; }
+    ds.V = d.box[0] * d.box[1] * d.box[2];
+    ds.n = n;
+    ds.nmol = nm;
+    ds.ntypes = d.ntypes;
+    ds.rng_id = d.rng_id;
+    ds.step = 0;                      // the system's first evaluation uses counter 0
+    ds.flags = 0;
+    ds.steps_left = -1;
+    // box masses: M_g = n_g^2 V ftm2v / (kappa L_g^2 omega^2), kappa in (kcal/mol/A^3)^-1
+    if (P.coupling != RBSOG_COUPLE_FIXED && P.tau_box > 0 && P.compressibility > 0) {
+        const double kap = P.compressibility * kNktv2p, om = 2.0 * kPi / P.tau_box;
+        if (ds.coupling == 0) {
+            ds.Mbox[0] = 9.0 * ds.V * kFtm2v / (kap * d.box[0] * d.box[0] * om * om);
+        } else {
+            ds.Mbox[0] = 4.0 * ds.V * kFtm2v / (kap * d.box[0] * d.box[0] * om * om);
+            ds.Mbox[1] = 1.0 * ds.V * kFtm2v / (kap * d.box[2] * d.box[2] * om * om);
+        }
+    }
+    return true;
+}
+
+rbsog_status validate_params(const rbsog_params *p)
+{
+    if (!p) return RBSOG_EINVAL;
     if (!(p->rc > 0) || !(p->b > 1) || !(p->sigma > 0) || p->M < 1 || p->M > kMaxGauss ||
         p->M_energy < p->M || p->M_energy > kMaxGauss || p->P < 1 || p->P > kMaxP ||
         p->sampler < 0 || p->sampler > 2 || (p->precision != 0 && p->precision != 1) ||
         (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2 || p->thermo_every < 0)
         return RBSOG_EINVAL;
-    for (int s = 0; s < S; ++s) {
-        const rbsog_system_desc &d = sy[s];
-        if (d.n_atoms < 1 || !d.q || !d.mass || !d.type || !d.mol || !d.r0 || d.ntypes < 1 ||
-            d.ntypes > kMaxTypes || !d.lj_eps || !d.lj_sig)
-            return RBSOG_EINVAL;
-        for (int a = 0; a < 3; ++a)
-            if (!(d.box[a] > 0)) return RBSOG_EBOX;
-        for (int i = 0; i < d.n_atoms; ++i)
-            if (!(d.mass[i] > 0) || !std::isfinite(d.mass[i])) return RBSOG_EINVAL;
-    }
+    return RBSOG_OK;
+}
+
+rbsog_status validate_system(const rbsog_system_desc &d)
+{
+    if (d.n_atoms < 1 || !d.q || !d.mass || !d.type || !d.mol || !d.r0 || d.ntypes < 1 ||
+        d.ntypes > kMaxTypes || !d.lj_eps || !d.lj_sig)
+        return RBSOG_EINVAL;
+    if ((d.n_bonds > 0 && (!d.bonds || !d.bond_k || !d.bond_r0)) ||
+        (d.n_angles > 0 && (!d.angles || !d.angle_k || !d.angle_t0)) || (d.n_excl > 0 && !d.excl) ||
+        d.n_bonds < 0 || d.n_angles < 0 || d.n_excl < 0)
+        return RBSOG_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(d.box[a] > 0)) return RBSOG_EBOX;
+    for (int i = 0; i < d.n_atoms; ++i)
+        if (!(d.mass[i] > 0) || !std::isfinite(d.mass[i])) return RBSOG_EINVAL;
     return RBSOG_OK;
 }
 
@@ -353,22 +516,34 @@ rbsog_status rbsog_system_range(const rbsog_ctx *ctx, int s, int *atom0, int *n)
 
 void rbsog_destroy(rbsog_ctx *ctx) { free_ctx(ctx); }
 
-rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog_system_desc *systems,
-                          void *stream, rbsog_ctx **out)
+}  // extern "C"
+
+namespace {
+
+// A context of n slots: `systems` (one per slot, sizes exact) or, for a pool,
+// `pool_caps` (empty slots of the given capacities).
+rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_system_desc *systems,
+                         const SlotCaps *pool_caps, void *stream, rbsog_ctx **out)
 {
     if (!out) return RBSOG_EINVAL;
     *out = nullptr;
-    rbsog_status vs = validate(params, n_systems, systems);
+    rbsog_status vs = validate_params(params);
     if (vs != RBSOG_OK) return vs;
+    if (n_systems <= 0 || (!systems && !pool_caps)) return RBSOG_EINVAL;
+    for (int k = 0; systems && k < n_systems; ++k) {
+        vs = validate_system(systems[k]);
+        if (vs != RBSOG_OK) return vs;
+    }
     rbsog_ctx *c = new (std::nothrow) rbsog_ctx();
     if (!c) return RBSOG_ENOMEM;
     try {
         c->prm = *params;
+        c->pool = systems == nullptr;
         if (c->prm.cell_sub == 0) {
             // cells of r_c/2 when a box edge leaves little room above 3 r_c (the
-            // box fluctuates in NPT), else cells of r_c
-            c->prm.cell_sub = 1;
-            for (int k = 0; k < n_systems; ++k)
+            // box fluctuates in NPT), else cells of r_c; pools take r_c/2
+            c->prm.cell_sub = c->pool ? 2 : 1;
+            for (int k = 0; systems && k < n_systems; ++k)
                 for (int a2 = 0; a2 < 3; ++a2)
                     if (systems[k].box[a2] < 3.3 * c->prm.rc) c->prm.cell_sub = 2;
         }
@@ -392,167 +567,78 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         cudaEventCreate(&c->ev_pair_ph[1]);
         c->Dcap = (P.sampler == RBSOG_SAMPLER_IID) ? 2 * P.P : P.P + 1;
 
-        // ---- host layout
+        // ---- host layout: one slot per system, sized by its capacities
         const int S = c->S;
-        std::vector<DevSys> hsys(S);
-        std::vector<int> atom_sys, cell_sys, chunk_sys, chunk_a0, chunk_n, first_chunk(S), nchunk(S);
-        std::vector<int> mchunk_sys, mchunk_m0, mchunk_n, mchunk_first(S), mchunk_count(S);
-        std::vector<double> r, p, q, mass, self_e(2 * S);
-        std::vector<int> type, mol;
-        std::vector<int> b_start{0}, a_start{0}, e_start{0}, bonds, angles, excl;
-        std::vector<double> bk, br0, ak, at0;
-        std::vector<double2> ljd;
-        std::vector<double> inv_m, sdv;
-        const double c_atom = std::exp(-P.gamma * P.dt);
-        std::vector<float2> ljf, ljf_lo;
-        int N = 0, C = 0, nmol = 0, item_cap = 0;
+        std::vector<SlotCaps> caps(S);
+        for (int k = 0; k < S; ++k) {
+            if (systems) caps[k] = caps_of(systems[k]);
+            else caps[k] = pool_caps[k];
+        }
         std::vector<double> w, s, wt, st;
         const int MM = std::max(P.M, P.M_energy);
         sog_terms(P, MM, w, s, wt, st);
+        c->sog_w = w;
+        std::vector<DevSys> hsys(S);
+        c->lay.resize(S);
+        int N = 0, C = 0, nmolx = 0, item_cap = 0, nbond = 0, nang = 0, nexc = 0, nlj = 0;
+        std::vector<int> atom_sys, cell_sys, chunk_sys, chunk_a0, chunk_n, first_chunk(S), nchunk(S);
+        std::vector<int> mchunk_sys, mchunk_m0, mchunk_n, mchunk_first(S), mchunk_count(S);
         c->h_atom0.resize(S); c->h_n.resize(S); c->h_cell0.resize(S); c->h_ncap_total.resize(S);
         for (int k = 0; k < S; ++k) {
-            const rbsog_system_desc &d = systems[k];
+            const SlotCaps &cp = caps[k];
             DevSys &ds = hsys[k];
             std::memset(&ds, 0, sizeof(ds));
             int ncap_t = 1;
             for (int a = 0; a < 3; ++a) {
-                ds.L[a] = d.box[a];
-                int n = (int)std::floor(d.box[a] * P.cell_sub / P.rc);
+                const int n = (int)std::floor(cp.box[a] * P.cell_sub / P.rc);
                 if (n < 2 * P.cell_sub + 1) {
                     rbsog_status rr = fail(c, RBSOG_EBOX, "system " + std::to_string(k) + ": box edge " +
-                                                              std::to_string(d.box[a]) + " too small for the cell stencil");
+                                                              std::to_string(cp.box[a]) + " too small for the cell stencil");
                     free_ctx(c);
                     return rr;
                 }
-                int cap = (int)std::floor(d.box[a] * 1.15 * P.cell_sub / P.rc);
+                // room for the box to grow by 15% under pressure
+                const int cap = (int)std::floor(cp.box[a] * 1.15 * P.cell_sub / P.rc);
                 ds.ncap[a] = std::max(cap, n);
                 ncap_t *= ds.ncap[a];
+                ds.L[a] = cp.box[a];
             }
-            ds.V = d.box[0] * d.box[1] * d.box[2];
+            SlotLayout &ly = c->lay[k];
+            ly.caps = cp;
+            ly.atom0 = N; ly.mol0 = nmolx; ly.bond0 = nbond; ly.angle0 = nang; ly.excl0 = nexc; ly.lj0 = nlj;
             ds.cell0 = C;
             ds.ncell_cap_total = ncap_t;
             // pair work items: at most one partial 32-atom group per cell; a
             // multiple of kPairWarps so that no pair-kernel block spans two systems
             ds.item0 = item_cap;
-            ds.item_cap = ((d.n_atoms + 31) / 32 + ncap_t + kPairWarps - 1) / kPairWarps * kPairWarps;
+            ds.item_cap = ((cp.atoms + 31) / 32 + ncap_t + kPairWarps - 1) / kPairWarps * kPairWarps;
             item_cap += ds.item_cap;
             ds.atom0 = N;
-            ds.n = d.n_atoms;
+            ds.lj0 = nlj;
+            ds.mol0 = nmolx;
             ds.coupling = P.coupling == RBSOG_COUPLE_SEMI_ISO ? 1 : 0;
-            ds.rng_id = d.rng_id;
-            // LJ block of this system: (4 eps sig^12, 4 eps sig^6) per type pair
-            ds.ntypes = d.ntypes;
-            ds.lj0 = (int)ljd.size();
-            for (int t = 0; t < d.ntypes * d.ntypes; ++t) {
-                const double eps = d.lj_eps[t], sg = d.lj_sig[t];
-                const double s6 = sg * sg * sg * sg * sg * sg;
-                ljd.push_back(make_double2(4.0 * eps * s6 * s6, 4.0 * eps * s6));
-                ljf.push_back(make_float2((float)ljd.back().x, (float)ljd.back().y));
-                ljf_lo.push_back(make_float2((float)(ljd.back().x - (double)ljf.back().x),
-                                             (float)(ljd.back().y - (double)ljf.back().y)));
-            }
-            // box masses: M_g = n_g^2 V ftm2v / (kappa L_g^2 omega^2), kappa in (kcal/mol/A^3)^-1
-            if (P.coupling != RBSOG_COUPLE_FIXED && P.tau_box > 0 && P.compressibility > 0) {
-                const double kap = P.compressibility * kNktv2p, om = 2.0 * kPi / P.tau_box;
-                if (ds.coupling == 0) {
-                    ds.Mbox[0] = 9.0 * ds.V * kFtm2v / (kap * d.box[0] * d.box[0] * om * om);
-                } else {
-                    ds.Mbox[0] = 4.0 * ds.V * kFtm2v / (kap * d.box[0] * d.box[0] * om * om);
-                    ds.Mbox[1] = 1.0 * ds.V * kFtm2v / (kap * d.box[2] * d.box[2] * om * om);
-                }
-            }
-            c->h_atom0[k] = N; c->h_n[k] = d.n_atoms; c->h_cell0[k] = C; c->h_ncap_total[k] = ncap_t;
+            ds.steps_left = -1;
+            c->h_atom0[k] = N; c->h_n[k] = 0; c->h_cell0[k] = C; c->h_ncap_total[k] = ncap_t;
             for (int i = 0; i < ncap_t; ++i) cell_sys.push_back(k);
             C += ncap_t;
-            // atoms
-            double sq = 0.0;
-            for (int i = 0; i < d.n_atoms; ++i) {
-                atom_sys.push_back(k);
-                for (int a = 0; a < 3; ++a) {
-                    r.push_back(d.r0[3 * i + a]);
-                    p.push_back(d.v0 ? d.v0[3 * i + a] * d.mass[i] : 0.0);
-                }
-                q.push_back(d.q[i]);
-                mass.push_back(d.mass[i]);
-                inv_m.push_back(1.0 / d.mass[i]);
-                sdv.push_back(std::sqrt((1.0 - c_atom * c_atom) * d.mass[i] * kKB * P.T * kFtm2v));
-                if (d.type[i] < 0 || d.type[i] >= d.ntypes) {
-                    rbsog_status rr = fail(c, RBSOG_EINVAL, "atom type out of range");
-                    free_ctx(c);
-                    return rr;
-                }
-                type.push_back(d.type[i]);
-                mol.push_back(d.mol[i]);
-                sq += d.q[i] * d.q[i];
-            }
-            // App. A: U_self = ln b / (sqrt(2 pi) sigma) (omega + (1 - b^{-(M-1)})/(b - 1)) sum q^2
-            self_e[2 * k] = P.ke * std::log(P.b) / (std::sqrt(2.0 * kPi) * P.sigma) *
-                            (P.omega + (1.0 - std::pow(P.b, -(P.M_energy - 1.0))) / (P.b - 1.0)) * sq;
-            // FP32 build: the constant part sum_excl ke q_i q_j F_E(0) of the exclusion energy
-            if (P.precision == RBSOG_FP32) {
-                double fe0 = 0.0, sx = 0.0;
-                for (int l = 0; l < P.M_energy; ++l) fe0 += w[l];
-                for (int e2 = 0; e2 < d.n_excl; ++e2) sx += d.q[d.excl[2 * e2]] * d.q[d.excl[2 * e2 + 1]];
-                self_e[2 * k + 1] = P.ke * fe0 * sx;
-            }
-            // chunks
+            for (int i = 0; i < cp.atoms; ++i) atom_sys.push_back(k);
             first_chunk[k] = (int)chunk_sys.size();
-            for (int a0 = 0; a0 < d.n_atoms; a0 += kChunk) {
+            for (int a0 = 0; a0 < cp.atoms; a0 += kChunk) {
                 chunk_sys.push_back(k);
                 chunk_a0.push_back(N + a0);
-                chunk_n.push_back(std::min(kChunk, d.n_atoms - a0));
+                chunk_n.push_back(std::min(kChunk, cp.atoms - a0));
             }
             nchunk[k] = (int)chunk_sys.size() - first_chunk[k];
-            // molecules: maximal runs of equal mol id
-            std::vector<int> mol_of(d.n_atoms);
-            std::vector<int> mstart;
-            for (int i = 0; i < d.n_atoms; ++i) {
-                if (i == 0 || d.mol[i] != d.mol[i - 1]) mstart.push_back(i);
-                mol_of[i] = (int)mstart.size() - 1;
-            }
-            const int nm = (int)mstart.size();
-            std::vector<std::vector<int>> mb(nm), ma(nm), me(nm);
-            auto same = [&](int i, int j) { return i >= 0 && j >= 0 && i < d.n_atoms && j < d.n_atoms && mol_of[i] == mol_of[j]; };
-            for (int e2 = 0; e2 < d.n_bonds; ++e2) {
-                int i = d.bonds[2 * e2], j = d.bonds[2 * e2 + 1];
-                if (!same(i, j)) { rbsog_status rr = fail(c, RBSOG_EINVAL, "a bond spans two molecules"); free_ctx(c); return rr; }
-                mb[mol_of[i]].push_back(e2);
-            }
-            for (int e2 = 0; e2 < d.n_angles; ++e2) {
-                int i = d.angles[3 * e2], j = d.angles[3 * e2 + 1], kk = d.angles[3 * e2 + 2];
-                if (!same(i, j) || !same(j, kk)) { rbsog_status rr = fail(c, RBSOG_EINVAL, "an angle spans two molecules"); free_ctx(c); return rr; }
-                ma[mol_of[i]].push_back(e2);
-            }
-            for (int e2 = 0; e2 < d.n_excl; ++e2) {
-                int i = d.excl[2 * e2], j = d.excl[2 * e2 + 1];
-                if (!same(i, j)) { rbsog_status rr = fail(c, RBSOG_EINVAL, "an exclusion spans two molecules"); free_ctx(c); return rr; }
-                me[mol_of[i]].push_back(e2);
-            }
             mchunk_first[k] = (int)mchunk_sys.size();
-            for (int m0 = 0; m0 < nm; m0 += kMolChunk) {
+            for (int m0 = 0; m0 < cp.mols; m0 += kMolChunk) {
                 mchunk_sys.push_back(k);
-                mchunk_m0.push_back(nmol + m0);
-                mchunk_n.push_back(std::min(kMolChunk, nm - m0));
+                mchunk_m0.push_back(nmolx + m0);
+                mchunk_n.push_back(std::min(kMolChunk, cp.mols - m0));
             }
             mchunk_count[k] = (int)mchunk_sys.size() - mchunk_first[k];
-            for (int mm = 0; mm < nm; ++mm) {
-                for (int e2 : mb[mm]) {
-                    bonds.push_back(N + d.bonds[2 * e2]); bonds.push_back(N + d.bonds[2 * e2 + 1]);
-                    bk.push_back(d.bond_k[e2]); br0.push_back(d.bond_r0[e2]);
-                }
-                for (int e2 : ma[mm]) {
-                    for (int t = 0; t < 3; ++t) angles.push_back(N + d.angles[3 * e2 + t]);
-                    ak.push_back(d.angle_k[e2]); at0.push_back(d.angle_t0[e2]);
-                }
-                for (int e2 : me[mm]) {
-                    excl.push_back(N + d.excl[2 * e2]); excl.push_back(N + d.excl[2 * e2 + 1]);
-                }
-                b_start.push_back((int)bk.size());
-                a_start.push_back((int)ak.size());
-                e_start.push_back((int)excl.size() / 2);
-            }
-            nmol += nm;
-            N += d.n_atoms;
+            N += cp.atoms;
+            nmolx += cp.mols + 1;             // + the end of the last molecule's term lists
+            nbond += cp.bonds; nang += cp.angles; nexc += cp.excl; nlj += cp.types * cp.types;
         }
         if (N >= (1 << 25)) {
             // the pair kernel's queue packs a neighbour index into 25 bits
@@ -560,7 +646,61 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             free_ctx(c);
             return rr;
         }
-        c->N = N; c->C = C; c->nmol = nmol; c->item_cap = item_cap;
+        // global host arrays; empty slots keep harmless defaults
+        std::vector<double> r(3 * (size_t)N, 0.0), p(3 * (size_t)N, 0.0), q(N, 0.0), mass(N, 1.0);
+        std::vector<double> inv_m(N, 1.0), sdv(N, 0.0), self_e(2 * S, 0.0);
+        std::vector<int> type(N, 0), mol(N, 0);
+        std::vector<int> b_start(nmolx, 0), a_start(nmolx, 0), e_start(nmolx, 0);
+        std::vector<int> bonds(2 * (size_t)nbond, 0), angles(3 * (size_t)nang, 0), excl(2 * (size_t)nexc, 0);
+        std::vector<double> bk(nbond, 0.0), br0(nbond, 0.0), ak(nang, 0.0), at0(nang, 0.0);
+        std::vector<double2> ljd(nlj, make_double2(0.0, 0.0));
+        std::vector<float2> ljf(nlj, make_float2(0.f, 0.f)), ljf_lo(nlj, make_float2(0.f, 0.f));
+        for (int k = 0; k < S; ++k) {
+            const SlotLayout &ly = c->lay[k];
+            for (int m = 0; m <= ly.caps.mols; ++m) {   // empty term lists
+                b_start[ly.mol0 + m] = ly.bond0;
+                a_start[ly.mol0 + m] = ly.angle0;
+                e_start[ly.mol0 + m] = ly.excl0;
+            }
+        }
+        if (systems) {
+            for (int k = 0; k < S; ++k) {
+                SlotImage im;
+                std::string why;
+                if (!build_image(P, c->lay[k], hsys[k], systems[k], w, im, why)) {
+                    rbsog_status rr = fail(c, RBSOG_EINVAL, "system " + std::to_string(k) + ": " + why);
+                    free_ctx(c);
+                    return rr;
+                }
+                const SlotLayout &ly = c->lay[k];
+                std::copy(im.r.begin(), im.r.end(), r.begin() + 3 * (size_t)ly.atom0);
+                std::copy(im.p.begin(), im.p.end(), p.begin() + 3 * (size_t)ly.atom0);
+                std::copy(im.q.begin(), im.q.end(), q.begin() + ly.atom0);
+                std::copy(im.mass.begin(), im.mass.end(), mass.begin() + ly.atom0);
+                std::copy(im.inv_m.begin(), im.inv_m.end(), inv_m.begin() + ly.atom0);
+                std::copy(im.sdv.begin(), im.sdv.end(), sdv.begin() + ly.atom0);
+                std::copy(im.type.begin(), im.type.end(), type.begin() + ly.atom0);
+                std::copy(im.mol.begin(), im.mol.end(), mol.begin() + ly.atom0);
+                std::copy(im.b_start.begin(), im.b_start.end(), b_start.begin() + ly.mol0);
+                std::copy(im.a_start.begin(), im.a_start.end(), a_start.begin() + ly.mol0);
+                std::copy(im.e_start.begin(), im.e_start.end(), e_start.begin() + ly.mol0);
+                std::copy(im.bonds.begin(), im.bonds.end(), bonds.begin() + 2 * (size_t)ly.bond0);
+                std::copy(im.bk.begin(), im.bk.end(), bk.begin() + ly.bond0);
+                std::copy(im.br0.begin(), im.br0.end(), br0.begin() + ly.bond0);
+                std::copy(im.angles.begin(), im.angles.end(), angles.begin() + 3 * (size_t)ly.angle0);
+                std::copy(im.ak.begin(), im.ak.end(), ak.begin() + ly.angle0);
+                std::copy(im.at0.begin(), im.at0.end(), at0.begin() + ly.angle0);
+                std::copy(im.excl.begin(), im.excl.end(), excl.begin() + 2 * (size_t)ly.excl0);
+                std::copy(im.ljd.begin(), im.ljd.end(), ljd.begin() + ly.lj0);
+                std::copy(im.ljf.begin(), im.ljf.end(), ljf.begin() + ly.lj0);
+                std::copy(im.ljf_lo.begin(), im.ljf_lo.end(), ljf_lo.begin() + ly.lj0);
+                self_e[2 * k] = im.self_e[0];
+                self_e[2 * k + 1] = im.self_e[1];
+                hsys[k].act = 1;
+                c->h_n[k] = systems[k].n_atoms;
+            }
+        }
+        c->N = N; c->C = C; c->nmol = nmolx; c->item_cap = item_cap;
         c->nchunks = (int)chunk_sys.size();
         c->nmchunks = (int)mchunk_sys.size();
 
@@ -591,7 +731,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
                   dalloc(c, c->pu, (size_t)S * P.P) && dalloc(c, c->pun, (size_t)S * P.P) &&
                   dalloc(c, c->sk_part, (size_t)c->nchunks * c->Dcap * 2) &&
                   dalloc(c, c->rho, (size_t)S * c->Dcap * 2) && dalloc(c, c->coef, (size_t)S * c->Dcap) &&
-                  dalloc(c, c->d_step, 1) && upload(c, c->ljd, ljd) && upload(c, c->ljf, ljf) && upload(c, c->ljf_lo, ljf_lo) &&
+                  upload(c, c->ljd, ljd) && upload(c, c->ljf, ljf) && upload(c, c->ljf_lo, ljf_lo) &&
                   upload(c, c->inv_m, inv_m) && upload(c, c->sdv, sdv);
         if (ok) {
             if (P.precision == 1)
@@ -599,6 +739,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
             else
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N);
         }
+        if (ok) ok = cudaMemset(c->sysred, 0, sizeof(double) * (size_t)S * kRed) == cudaSuccess;
         if (!ok) {
             free_ctx(c);
             return RBSOG_ENOMEM;
@@ -650,7 +791,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         }
         // LJ: one ntypes x ntypes block per system (uploaded with the buffers above)
         // sampler (the same expressions as the paper's formulas, FP64 on the host)
-        c->sa.P = P.P; c->sa.M = P.M; c->sa.kind = P.sampler; c->sa.seed = P.seed; c->sa.step = c->d_step;
+        c->sa.P = P.P; c->sa.M = P.M; c->sa.kind = P.sampler; c->sa.seed = P.seed; 
         const double pi15 = std::pow(kPi, 1.5);
         for (int l = 0; l < P.M; ++l) {
             double s5 = st[l] * st[l] * st[l] * st[l] * st[l];
@@ -661,7 +802,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         }
         c->sa.sig_u = 1.0 / (std::sqrt(2.0) * kPi * st[0]);
         c->ia.dt = P.dt; c->ia.T = P.T; c->ia.Pext = P.P_ext; c->ia.gamma = P.gamma; c->ia.gamma_box = P.gamma_box;
-        c->ia.kB = kKB; c->ia.ftm2v = kFtm2v; c->ia.nktv2p = kNktv2p; c->ia.seed = P.seed; c->ia.step = c->d_step;
+        c->ia.kB = kKB; c->ia.ftm2v = kFtm2v; c->ia.nktv2p = kNktv2p; c->ia.seed = P.seed; 
         c->ia.c_atom = std::exp(-P.gamma * P.dt);
         c->ia.inv_m = c->inv_m; c->ia.sdv = c->sdv;
         c->ia.noise_f32 = P.precision == RBSOG_FP32 ? 1 : 0;
@@ -676,7 +817,7 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
         c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
-        c->m.nmol = nmol; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
+        c->m.nmol = nmolx; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
         c->m.mchunk_n = c->mchunk_n; c->m.nmchunks = c->nmchunks;
@@ -686,10 +827,8 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { rbsog_status rr = cuda_fail(c, e, "create"); free_ctx(c); return rr; }
         // the first evaluation (counter 0) primes forces, virial and kinetic tensor
-        unsigned long long minus1 = ~0ull;
-        cudaMemcpyAsync(c->d_step, &minus1, sizeof(minus1), cudaMemcpyHostToDevice, c->st);
         launch_clear_flags(c->b, c->st);
-        enqueue_eval(c, 0, 0, 1);
+        enqueue_eval(c, 0, 0, 1, 0);
         c->h_step = 0;
         e = cudaStreamSynchronize(c->st);
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -701,6 +840,128 @@ rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog
         return RBSOG_ENOMEM;
     }
     *out = c;
+    return RBSOG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rbsog_status rbsog_create(const rbsog_params *params, int n_systems, const rbsog_system_desc *systems,
+                          void *stream, rbsog_ctx **out)
+{
+    if (!systems) return RBSOG_EINVAL;
+    return create_impl(params, n_systems, systems, nullptr, stream, out);
+}
+
+rbsog_status rbsog_pool_create(const rbsog_params *params, int n_slots, const rbsog_slot_caps *caps, void *stream,
+                               rbsog_ctx **out)
+{
+    if (!caps || n_slots <= 0) return RBSOG_EINVAL;
+    std::vector<SlotCaps> sc(n_slots);
+    for (int k = 0; k < n_slots; ++k) {
+        const rbsog_slot_caps &c = caps[k];
+        if (c.max_atoms < 1 || c.max_molecules < 1 || c.max_molecules > c.max_atoms || c.max_bonds < 0 ||
+            c.max_angles < 0 || c.max_excl < 0 || c.max_types < 1 || c.max_types > kMaxTypes)
+            return RBSOG_EINVAL;
+        sc[k].atoms = c.max_atoms; sc[k].mols = c.max_molecules; sc[k].bonds = c.max_bonds;
+        sc[k].angles = c.max_angles; sc[k].excl = c.max_excl; sc[k].types = c.max_types;
+        for (int a = 0; a < 3; ++a) {
+            if (!(c.max_box[a] > 0)) return RBSOG_EBOX;
+            sc[k].box[a] = c.max_box[a];
+        }
+    }
+    return create_impl(params, n_slots, nullptr, sc.data(), stream, out);
+}
+
+rbsog_status rbsog_pool_load(rbsog_ctx *c, int slot, const rbsog_system_desc *sys, int nsteps)
+{
+    if (!c || !c->pool || slot < 0 || slot >= c->S || !sys || nsteps == 0 || nsteps < -1) return RBSOG_EINVAL;
+    rbsog_status vs = validate_system(*sys);
+    if (vs != RBSOG_OK) return fail(c, vs, "rbsog_pool_load: invalid system");
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool load");
+    DevSys ds;
+    e = cudaMemcpy(&ds, c->sys + slot, sizeof(DevSys), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool load");
+    if (ds.n != 0) return fail(c, RBSOG_EINVAL, "rbsog_pool_load: slot " + std::to_string(slot) + " is not empty");
+    const SlotLayout &ly = c->lay[slot];
+    SlotImage im;
+    std::string why;
+    if (!build_image(c->prm, ly, ds, *sys, c->sog_w, im, why))
+        return fail(c, RBSOG_EINVAL, "rbsog_pool_load: slot " + std::to_string(slot) + ": " + why);
+    ds.act = 1;
+    ds.steps_left = nsteps;
+    auto put = [&](auto *dst, const auto &v) {
+        if (e == cudaSuccess && !v.empty())
+            e = cudaMemcpy(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
+    };
+    const size_t A0 = ly.atom0;
+    put(c->r + 3 * A0, im.r); put(c->p + 3 * A0, im.p); put(c->q + A0, im.q); put(c->mass + A0, im.mass);
+    put(c->inv_m + A0, im.inv_m); put(c->sdv + A0, im.sdv); put(c->type + A0, im.type); put(c->mol + A0, im.mol);
+    put(c->b_start + ly.mol0, im.b_start); put(c->a_start + ly.mol0, im.a_start); put(c->e_start + ly.mol0, im.e_start);
+    put(c->bonds + 2 * (size_t)ly.bond0, im.bonds); put(c->bk + ly.bond0, im.bk); put(c->br0 + ly.bond0, im.br0);
+    put(c->angles + 3 * (size_t)ly.angle0, im.angles); put(c->ak + ly.angle0, im.ak); put(c->at0 + ly.angle0, im.at0);
+    put(c->excl + 2 * (size_t)ly.excl0, im.excl);
+    put(c->ljd + ly.lj0, im.ljd); put(c->ljf + ly.lj0, im.ljf); put(c->ljf_lo + ly.lj0, im.ljf_lo);
+    if (e == cudaSuccess) e = cudaMemcpy(c->self_e + 2 * slot, im.self_e, 2 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->sys + slot, &ds, sizeof(DevSys), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool load");
+    c->h_n[slot] = sys->n_atoms;
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_pool_prime(rbsog_ctx *c)
+{
+    if (!c) return RBSOG_EINVAL;
+    launch_clear_flags(c->b, c->st);
+    enqueue_eval(c, 0, 0, 1, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool prime");
+    return check_flags(c);
+}
+
+rbsog_status rbsog_pool_state(rbsog_ctx *c, int *state, unsigned long long *step)
+{
+    if (!c || !state) return RBSOG_EINVAL;
+    std::vector<DevSys> h(c->S);
+    cudaError_t e = cudaMemcpyAsync(h.data(), c->sys, sizeof(DevSys) * c->S, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool state");
+    for (int s = 0; s < c->S; ++s) {
+        state[s] = h[s].n == 0 ? 0 : (h[s].act ? 1 : 2);
+        if (step) step[s] = h[s].step;
+    }
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_pool_unload(rbsog_ctx *c, int slot, double *r, double *v, rbsog_result *res)
+{
+    if (!c || !c->pool || slot < 0 || slot >= c->S) return RBSOG_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    DevSys ds;
+    if (e == cudaSuccess) e = cudaMemcpy(&ds, c->sys + slot, sizeof(DevSys), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool unload");
+    if (ds.n == 0) return fail(c, RBSOG_EINVAL, "rbsog_pool_unload: slot " + std::to_string(slot) + " is empty");
+    const size_t A0 = c->lay[slot].atom0, n = ds.n;
+    if (r) e = cudaMemcpy(r, c->r + 3 * A0, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (v && e == cudaSuccess) {
+        std::vector<double> p(3 * n), m(n);
+        e = cudaMemcpy(p.data(), c->p + 3 * A0, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(m.data(), c->mass + A0, n * sizeof(double), cudaMemcpyDeviceToHost);
+        for (size_t i = 0; e == cudaSuccess && i < 3 * n; ++i) v[i] = p[i] / m[i / 3];
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool unload");
+    if (res) {
+        std::vector<rbsog_result> all(c->S);
+        rbsog_status fs = fill_results(c, all.data());
+        if (fs != RBSOG_OK) return fs;
+        *res = all[slot];
+    }
+    ds.n = 0; ds.nmol = 0; ds.act = 0; ds.steps_left = 0; ds.flags = 0; ds.nD = 0;
+    e = cudaMemcpy(c->sys + slot, &ds, sizeof(DevSys), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pool unload");
+    c->h_n[slot] = 0;
     return RBSOG_OK;
 }
 
@@ -763,14 +1024,13 @@ rbsog_status rbsog_get_velocities(rbsog_ctx *c, double *v, int on_device)
 rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_device, rbsog_result *res)
 {
     if (!c) return RBSOG_EINVAL;
-    unsigned long long prev = (unsigned long long)step - 1ull;
-    cudaError_t e = cudaMemcpyAsync(c->d_step, &prev, sizeof(prev), cudaMemcpyHostToDevice, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "step");
+    launch_set_step(c->b, (unsigned long long)step, c->st);
+    cudaError_t e = cudaSuccess;
     for (auto ev : c->t_events) cudaEventDestroy(ev);
     c->t_events.clear();
     c->t_names.clear();
     launch_clear_flags(c->b, c->st);
-    enqueue_eval(c, 0, 0, 1);
+    enqueue_eval(c, 0, 0, 1, 0);
     c->h_step = (unsigned long long)step;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
@@ -901,10 +1161,9 @@ rbsog_status rbsog_get_state(rbsog_ctx *c, void *buf, size_t *len)
                         3 * sizeof(double) * (size_t)c->N + sizeof(double) * (size_t)c->S * kRed;
     if (!buf) { *len = need; return RBSOG_OK; }
     if (*len < need) return RBSOG_EINVAL;
-    unsigned long long step = 0;
-    cudaError_t e = cudaMemcpyAsync(&step, c->d_step, sizeof(step), cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-    uint64_t hdr[2] = {(uint64_t)step, (uint64_t)c->N};
+    // header: the host step counter (the per-system Philox counters are in DevSys)
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    uint64_t hdr[2] = {(uint64_t)c->h_step, (uint64_t)c->N};
     char *o = static_cast<char *>(buf);
     std::memcpy(o, hdr, sizeof(hdr));
     o += sizeof(hdr);
@@ -941,7 +1200,6 @@ rbsog_status rbsog_set_state(rbsog_ctx *c, const void *buf, size_t len)
     if (e == cudaSuccess) e = cudaMemcpy(c->sys, o, sizeof(DevSys) * c->S, cudaMemcpyHostToDevice);
     o += sizeof(DevSys) * c->S;
     if (e == cudaSuccess) e = cudaMemcpy(c->sysred, o, sizeof(double) * c->S * kRed, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_step, &step, sizeof(step), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
     c->h_step = step;
     return RBSOG_OK;

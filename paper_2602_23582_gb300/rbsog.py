@@ -32,13 +32,22 @@ EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_
            "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_set_timing", "rbsog_get_timing",
            "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
            "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc", "rbsog_trace_pair",
-           "rbsog_trace_pair_times", "rbsog_set_thermo_every")
+           "rbsog_trace_pair_times", "rbsog_set_thermo_every", "rbsog_pool_create", "rbsog_pool_load",
+           "rbsog_pool_prime", "rbsog_pool_state", "rbsog_pool_unload", "rbsog_server_create",
+           "rbsog_server_destroy", "rbsog_server_slots", "rbsog_server_context", "rbsog_server_submit",
+           "rbsog_server_pump", "rbsog_server_result", "rbsog_server_stats")
 
 
 class RbsogError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__(f"rbsog status {status} ({STATUS.get(status, '?')}): {msg}")
         self.status = status
+
+
+class rbsog_slot_caps(C.Structure):
+    _fields_ = [("max_atoms", C.c_int), ("max_molecules", C.c_int), ("max_bonds", C.c_int),
+                ("max_angles", C.c_int), ("max_excl", C.c_int), ("max_types", C.c_int),
+                ("max_box", C.c_double * 3)]
 
 
 class rbsog_params(C.Structure):
@@ -118,6 +127,22 @@ def lib():
     L.rbsog_structure_factor_noalloc.argtypes = [P, P, C.c_int, _D, P, C.c_int, P, C.c_int, P]
     L.rbsog_trace_pair.argtypes = [P, C.c_int]
     L.rbsog_set_thermo_every.argtypes = [P, C.c_int]
+    L.rbsog_pool_create.argtypes = [C.POINTER(rbsog_params), C.c_int, C.POINTER(rbsog_slot_caps), P, C.POINTER(P)]
+    L.rbsog_pool_load.argtypes = [P, C.c_int, C.POINTER(rbsog_system_desc), C.c_int]
+    L.rbsog_pool_prime.argtypes = [P]
+    L.rbsog_pool_state.argtypes = [P, _I, C.POINTER(C.c_ulonglong)]
+    L.rbsog_pool_unload.argtypes = [P, C.c_int, _D, _D, C.POINTER(rbsog_result)]
+    L.rbsog_server_create.argtypes = [C.POINTER(rbsog_params), C.c_int, C.POINTER(rbsog_slot_caps), C.c_double,
+                                      P, C.POINTER(P)]
+    L.rbsog_server_destroy.argtypes = [P]
+    L.rbsog_server_destroy.restype = None
+    L.rbsog_server_slots.argtypes = [P]
+    L.rbsog_server_context.argtypes = [P]
+    L.rbsog_server_context.restype = P
+    L.rbsog_server_submit.argtypes = [P, C.POINTER(rbsog_system_desc), C.c_int, C.POINTER(C.c_longlong)]
+    L.rbsog_server_pump.argtypes = [P, C.c_int, _I, _I]
+    L.rbsog_server_result.argtypes = [P, C.c_longlong, _I, _D, _D, C.POINTER(rbsog_result)]
+    L.rbsog_server_stats.argtypes = [P, _D, _D, _D, C.POINTER(C.c_longlong)]
     L.rbsog_trace_pair_times.argtypes = [P, C.c_int, _D, _I]
     _lib = L
     return L
@@ -343,6 +368,141 @@ def result_dict(r: rbsog_result) -> dict:
                box=np.array(r.box[:]), volume=r.volume, n_distinct_modes=r.n_distinct_modes,
                n_accept_r=r.n_accept_r, n_accept_nr=r.n_accept_nr, step=r.step)
     return out
+
+
+def slot_caps(max_atoms, max_box, max_molecules=None, max_bonds=None, max_angles=None, max_excl=None,
+              max_types=4) -> rbsog_slot_caps:
+    """Capacities of one slot; term limits default to generous multiples of the atoms."""
+    c = rbsog_slot_caps()
+    c.max_atoms = int(max_atoms)
+    c.max_molecules = int(max_molecules if max_molecules is not None else max_atoms)
+    c.max_bonds = int(max_bonds if max_bonds is not None else max_atoms)
+    c.max_angles = int(max_angles if max_angles is not None else max_atoms)
+    c.max_excl = int(max_excl if max_excl is not None else 2 * max_atoms)
+    c.max_types = int(max_types)
+    for a in range(3):
+        c.max_box[a] = float(max_box[a] if hasattr(max_box, "__len__") else max_box)
+    return c
+
+
+class Pool:
+    """A pool context: slots loaded and emptied at run time (served path)."""
+
+    def __init__(self, caps, params: rbsog_params | None = None, stream=None, **kw):
+        self.params = params if params is not None else rbsog_default_params(**kw)
+        arr = (rbsog_slot_caps * len(caps))(*caps)
+        self.ctx = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        _check(lib().rbsog_pool_create(C.byref(self.params), len(caps), arr, st, C.byref(self.ctx)))
+        self.S = len(caps)
+        self.systems = [None] * self.S
+
+    def load(self, slot, system, nsteps=-1, index=None):
+        hold = []
+        d = _desc(system, hold, slot if index is None else index)
+        _check(lib().rbsog_pool_load(self.ctx, int(slot), C.byref(d), int(nsteps)), self.ctx)
+        self.systems[slot] = system
+
+    def prime(self):
+        _check(lib().rbsog_pool_prime(self.ctx), self.ctx)
+
+    def run(self, nsteps):
+        res = (rbsog_result * self.S)()
+        _check(lib().rbsog_run(self.ctx, int(nsteps), res), self.ctx)
+        return [result_dict(res[k]) for k in range(self.S)]
+
+    def state(self):
+        st = np.zeros(self.S, dtype=np.int32)
+        steps = (C.c_ulonglong * self.S)()
+        _check(lib().rbsog_pool_state(self.ctx, st.ctypes.data_as(_I), steps), self.ctx)
+        return st, np.array(steps[:], dtype=np.uint64)
+
+    def unload(self, slot):
+        n = self.systems[slot].n
+        r = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        res = rbsog_result()
+        _check(lib().rbsog_pool_unload(self.ctx, int(slot), r.ctypes.data_as(_D), v.ctypes.data_as(_D),
+                                       C.byref(res)), self.ctx)
+        self.systems[slot] = None
+        return r, v, result_dict(res)
+
+    def close(self):
+        if self.ctx:
+            rbsog_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop of the served path (continuous batching over a pool)."""
+
+    def __init__(self, caps, params: rbsog_params | None = None, hbm_fraction=0.5, stream=None, **kw):
+        self.params = params if params is not None else rbsog_default_params(**kw)
+        arr = (rbsog_slot_caps * len(caps))(*caps)
+        self.srv = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        status = lib().rbsog_server_create(C.byref(self.params), len(caps), arr, float(hbm_fraction), st,
+                                           C.byref(self.srv))
+        if status != RBSOG_OK:
+            raise RbsogError(status, "rbsog_server_create: " + lib().rbsog_last_error(None).decode())
+        self.sizes = {}
+
+    @property
+    def slots(self):
+        return lib().rbsog_server_slots(self.srv)
+
+    def submit(self, system, nsteps, rng_id=None):
+        hold = []
+        d = _desc(system, hold, 0)
+        if rng_id is not None:
+            d.rng_id = int(rng_id)
+        t = C.c_longlong()
+        _check(lib().rbsog_server_submit(self.srv, C.byref(d), int(nsteps), C.byref(t)))
+        self.sizes[t.value] = system.n
+        return t.value
+
+    def pump(self, max_steps):
+        run = C.c_int()
+        que = C.c_int()
+        status = lib().rbsog_server_pump(self.srv, int(max_steps), C.byref(run), C.byref(que))
+        if status != RBSOG_OK:
+            raise RbsogError(status, lib().rbsog_last_error(lib().rbsog_server_context(self.srv)).decode())
+        return run.value, que.value
+
+    def result(self, ticket):
+        n = self.sizes[ticket]
+        done = C.c_int()
+        r = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        res = rbsog_result()
+        _check(lib().rbsog_server_result(self.srv, int(ticket), C.byref(done), r.ctypes.data_as(_D),
+                                         v.ctypes.data_as(_D), C.byref(res)))
+        if not done.value:
+            return None
+        return r, v, result_dict(res)
+
+    def stats(self):
+        p50, p99, thr = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_longlong()
+        _check(lib().rbsog_server_stats(self.srv, C.byref(p50), C.byref(p99), C.byref(thr), C.byref(n)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "atom_steps_per_s": thr.value, "steps": n.value}
+
+    def close(self):
+        if self.srv:
+            lib().rbsog_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

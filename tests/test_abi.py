@@ -35,9 +35,10 @@ def test_library_exports_every_declared_function():
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rbsog.h"\n'
-                    'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(rbsog_params), sizeof(rbsog_result),'
+                    'int main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rbsog_params), sizeof(rbsog_result),'
                     ' sizeof(rbsog_system_desc), offsetof(rbsog_system_desc, rng_id),'
-                    ' offsetof(rbsog_result, step));return 0;}\n')
+                    ' offsetof(rbsog_result, step), sizeof(rbsog_slot_caps), offsetof(rbsog_slot_caps, max_box),'
+                    ' offsetof(rbsog_params, thermo_every));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
@@ -46,6 +47,9 @@ def test_struct_layout_matches_header(tmp_path):
     assert out[2] == ctypes.sizeof(R.rbsog_system_desc)
     assert out[3] == R.rbsog_system_desc.rng_id.offset
     assert out[4] == R.rbsog_result.step.offset
+    assert out[5] == ctypes.sizeof(R.rbsog_slot_caps)
+    assert out[6] == R.rbsog_slot_caps.max_box.offset
+    assert out[7] == R.rbsog_params.thermo_every.offset
 
 
 def test_default_params_are_table2_row2(table2):
