@@ -144,6 +144,81 @@ def cpu_baseline(systems, budget_s=15.0):
                       f"{dt:.1f} s"}
 
 
+def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
+    """The served stream: 256 electrolyte/water systems of 500-20,000 atoms
+    arriving as a Poisson stream (rate_per_ms requests per ms of wall time),
+    each for 100-1000 NPT steps, through the request loop over a slot pool.
+    Returns aggregate throughput (wall time from the first arrival to the last
+    completion), the pool's per-step latency percentiles, and the plain path
+    (each system alone in its own context, a sample of the same requests)."""
+    import workloads as W
+    t0 = time.perf_counter()
+    reqs = W.served_batch(rate_per_ms=rate_per_ms, workers=max(1, min(16, os.cpu_count() or 1)))
+    t_gen = time.perf_counter() - t0
+    classes = [(3000, 45.0, 24), (9000, 62.0, 16), (20000, 82.0, 16)]
+    caps = []
+    for atoms, box, count in classes:
+        caps += [R.slot_caps(max_atoms=atoms, max_box=box, max_types=2) for _ in range(count)]
+    p = R.rbsog_default_params(10.0, precision=prec, thermo_every=100)
+    srv = R.Server(caps, p, hbm_fraction=0.6)
+    order = sorted(range(len(reqs)), key=lambda k: reqs[k][0])
+    tickets = {}
+    k_next = 0
+    t_start = time.perf_counter()
+    while True:
+        now_ms = (time.perf_counter() - t_start) * 1e3
+        while k_next < len(order) and reqs[order[k_next]][0] <= now_ms:
+            k = order[k_next]
+            tickets[k] = srv.submit(reqs[k][2], reqs[k][1], rng_id=5000 + k)
+            k_next += 1
+        running, queued = srv.pump(10)
+        if running == 0 and queued == 0 and k_next == len(order):
+            srv.pump(0)
+            break
+        if running == 0 and queued == 0:
+            time.sleep(max(0.0, (reqs[order[k_next]][0] - now_ms) * 1e-3))
+    wall = time.perf_counter() - t_start
+    done = failed = 0
+    work = 0.0                                # atom-steps actually made (a failed request stops early)
+    for k, t in tickets.items():
+        out = srv.result(t)
+        if out is not None:
+            done += 1
+            failed += out[2]["status"] != 0
+            work += reqs[k][2].n * float(out[2]["step"])
+    st = srv.stats()
+    slots = srv.slots
+    srv.close()
+    # plain path: the same requests one at a time, each alone in its context
+    pick = order[::max(1, len(order) // plain_sample)][:plain_sample]
+    pw, pt = 0.0, 0.0
+    for k in pick:
+        _, ns, s = reqs[k]
+        s.rng_id = 5000 + k
+        ctx = R.Context([s], R.rbsog_default_params(10.0, precision=prec, thermo_every=100, cell_sub=2))
+        torch_sync()
+        t1 = time.perf_counter()
+        ctx.run(ns)
+        pt += time.perf_counter() - t1
+        pw += s.n * ns
+        ctx.close()
+    return {"workload": "256 electrolyte/water systems, 500-20,000 atoms (log-uniform), 100-1000 NPT steps each, "
+                        f"Poisson arrivals at {rate_per_ms * 1e3:.0f} requests/s, P=100, FP32",
+            "value": work / wall, "unit": UNIT, "requests_done": done, "requests_failed": failed,
+            "atom_steps": work, "wall_s": wall,
+            "gpu_busy_atom_steps_per_s": st["atom_steps_per_s"], "p50_step_ms": st["p50_ms"],
+            "p99_step_ms": st["p99_ms"], "pool_steps": st["steps"], "pool_slots": slots,
+            "slot_classes": [{"max_atoms": a, "max_box": bx, "slots": c} for a, bx, c in classes],
+            "plain": {"value": pw / pt, "unit": UNIT, "sample_requests": len(pick),
+                      "path": "each request alone in its own context (rbsog_run)"},
+            "served_over_plain": (work / wall) / (pw / pt), "generation_s": t_gen}
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -187,6 +262,7 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--thermo", type=int, default=100,
                     help="energies every this many steps (as MD thermo output); forces and the "
                          "virial are computed every step either way")
@@ -345,6 +421,12 @@ def main():
             cpu = cpu_baseline(systems)
         except Exception as ex:   # reported, not fatal
             cpu = {"error": str(ex)}
+    served = None
+    if rank == 0 and not args.no_served:
+        try:
+            served = served_bench(R, prec, local)
+        except Exception as ex:   # reported, not fatal
+            served = {"error": str(ex)}
     kernels_per_step = 17   # box_half .. step_advance, one graph replay
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
@@ -360,7 +442,7 @@ def main():
                        "energy_every_step": energy_every_step,
                        "kernel_ms_eager_step": kernel_ms},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": kernels_per_step * args.steps, "clocks": clocks}
+            "gpu_launches": kernels_per_step * args.steps, "clocks": clocks, "served": served}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

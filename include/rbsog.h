@@ -268,8 +268,12 @@ rbsog_status rbsog_pool_load(rbsog_ctx *ctx, int slot, const rbsog_system_desc *
  * counter: required after loading, before stepping (slots already running
  * recompute identical values).  Waits and checks the flags. */
 rbsog_status rbsog_pool_prime(rbsog_ctx *ctx);
-/* Per slot: 0 empty, 1 running, 2 finished; step: its Philox counter (may be NULL). */
-rbsog_status rbsog_pool_state(rbsog_ctx *ctx, int *state, unsigned long long *step);
+/* Per slot: 0 empty, 1 running, 2 finished, 3 stopped by a failure (its box
+ * too small for the cell stencil, a cell overflow, non-finite results: err
+ * holds the RBSOG_E* code; the other slots are not affected); step: its
+ * Philox counter.  step and err may be NULL.  In a pool, rbsog_run and
+ * rbsog_sync stop a failing system instead of returning its error. */
+rbsog_status rbsog_pool_state(rbsog_ctx *ctx, int *state, unsigned long long *step, int *err);
 /* Copy out positions (r), velocities (v) -- n x 3 host buffers of the slot's
  * system, either may be NULL -- and the results of its last step, then empty
  * the slot. */
@@ -294,11 +298,12 @@ rbsog_status rbsog_server_submit(rbsog_server *srv, const rbsog_system_desc *sys
                                  long long *ticket);
 rbsog_status rbsog_server_pump(rbsog_server *srv, int max_steps, int *n_running, int *n_queued);
 /* done = 1 once the request finished; then r, v (n x 3, may be NULL) and the
- * results of its last step. */
+ * results of its last step.  Returns the request's own status once done
+ * (RBSOG_OK, or why its system was stopped early, e.g. RBSOG_EBOX). */
 rbsog_status rbsog_server_result(rbsog_server *srv, long long ticket, int *done, double *r, double *v,
                                  rbsog_result *res);
 rbsog_status rbsog_server_stats(const rbsog_server *srv, double *p50_ms, double *p99_ms,
-                                double *atom_steps_per_s, long long *steps);
+                                double *atom_steps_per_s, long long *steps, int *failed);
 
 /* Pair-kernel trace for profiling inside a run: the next nsteps graph steps of
  * rbsog_run / rbsog_run_async record CUDA events immediately before and after

@@ -59,6 +59,7 @@ struct rbsog_ctx {
     std::vector<SlotLayout> lay;        // per slot
     std::vector<double> sog_w;          // w_l (energy split), for per-system constants
     bool pool = false;                  // slots are loaded and emptied at run time
+    std::vector<rbsog_status> slot_err; // pool: why a slot's system was stopped (RBSOG_OK: it was not)
     int S = 0, N = 0, C = 0, Dcap = 0, nchunks = 0, nmol = 0, nmchunks = 0, item_cap = 0;
     cudaStream_t st = nullptr, st2 = nullptr;
     bool own_st = false, own_st2 = false;
@@ -246,14 +247,26 @@ rbsog_status check_flags(rbsog_ctx *c)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "device");
     for (int s = 0; s < c->S; ++s) {
-        if (h[s].flags & FLAG_BOX)
-            return fail(c, RBSOG_EBOX, "system " + std::to_string(s) + ": box edge below " +
-                                           std::to_string(2 * c->prm.cell_sub + 1) + " cells of r_c/sub");
-        if (h[s].flags & FLAG_OVERFLOW)
-            return fail(c, RBSOG_EOVERFLOW, "system " + std::to_string(s) + ": a cell holds more than " +
-                                                std::to_string(kCellCap) + " atoms");
-        if (h[s].flags & FLAG_NONFINITE)
-            return fail(c, RBSOG_ENONFINITE, "system " + std::to_string(s) + ": non-finite energy or virial");
+        if (!h[s].flags) continue;
+        rbsog_status st = RBSOG_OK;
+        std::string why;
+        if (h[s].flags & FLAG_BOX) {
+            st = RBSOG_EBOX;
+            why = "box edge below " + std::to_string(2 * c->prm.cell_sub + 1) + " cells of r_c/sub";
+        } else if (h[s].flags & FLAG_OVERFLOW) {
+            st = RBSOG_EOVERFLOW;
+            why = "a cell holds more than " + std::to_string(kCellCap) + " atoms";
+        } else {
+            st = RBSOG_ENONFINITE;
+            why = "non-finite energy or virial";
+        }
+        if (!c->pool) return fail(c, st, "system " + std::to_string(s) + ": " + why);
+        // a pool stops the failing system only; the others go on
+        if (c->slot_err[s] == RBSOG_OK) c->slot_err[s] = st;
+        h[s].act = 0;
+        h[s].flags = 0;
+        e = cudaMemcpy(c->sys + s, &h[s], sizeof(DevSys), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "device");
     }
     return RBSOG_OK;
 }
@@ -539,6 +552,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
     try {
         c->prm = *params;
         c->pool = systems == nullptr;
+        c->slot_err.assign(n_systems, RBSOG_OK);
         if (c->prm.cell_sub == 0) {
             // cells of r_c/2 when a box edge leaves little room above 3 r_c (the
             // box fluctuates in NPT), else cells of r_c; pools take r_c/2
@@ -892,6 +906,7 @@ rbsog_status rbsog_pool_load(rbsog_ctx *c, int slot, const rbsog_system_desc *sy
         return fail(c, RBSOG_EINVAL, "rbsog_pool_load: slot " + std::to_string(slot) + ": " + why);
     ds.act = 1;
     ds.steps_left = nsteps;
+    c->slot_err[slot] = RBSOG_OK;
     auto put = [&](auto *dst, const auto &v) {
         if (e == cudaSuccess && !v.empty())
             e = cudaMemcpy(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
@@ -921,7 +936,7 @@ rbsog_status rbsog_pool_prime(rbsog_ctx *c)
     return check_flags(c);
 }
 
-rbsog_status rbsog_pool_state(rbsog_ctx *c, int *state, unsigned long long *step)
+rbsog_status rbsog_pool_state(rbsog_ctx *c, int *state, unsigned long long *step, int *err)
 {
     if (!c || !state) return RBSOG_EINVAL;
     std::vector<DevSys> h(c->S);
@@ -929,8 +944,10 @@ rbsog_status rbsog_pool_state(rbsog_ctx *c, int *state, unsigned long long *step
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pool state");
     for (int s = 0; s < c->S; ++s) {
-        state[s] = h[s].n == 0 ? 0 : (h[s].act ? 1 : 2);
+        const bool failed = c->pool && c->slot_err[s] != RBSOG_OK;
+        state[s] = h[s].n == 0 ? 0 : (h[s].act ? 1 : (failed ? 3 : 2));
         if (step) step[s] = h[s].step;
+        if (err) err[s] = c->pool ? (int)c->slot_err[s] : 0;
     }
     return RBSOG_OK;
 }

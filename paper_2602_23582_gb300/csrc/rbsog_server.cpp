@@ -72,6 +72,7 @@ struct SystemCopy {
 };
 
 struct Request {
+    rbsog_status status = RBSOG_OK;   // RBSOG_OK, or why the system was stopped early
     long long ticket = 0;
     SystemCopy *sys = nullptr;
     int nsteps = 0;
@@ -112,6 +113,7 @@ struct rbsog_server {
     // statistics
     std::vector<double> step_ms;
     double atom_steps = 0.0, gpu_ms = 0.0;
+    int failed = 0;
     std::vector<cudaEvent_t> ev;
     std::string err;
 };
@@ -192,13 +194,19 @@ rbsog_status rbsog_server_pump(rbsog_server *s, int max_steps, int *n_running, i
 {
     if (!s || max_steps < 0) return RBSOG_EINVAL;
     const int S = (int)s->caps.size();
-    std::vector<int> state(S);
-    rbsog_status st = rbsog_pool_state(s->ctx, state.data(), nullptr);
+    std::vector<int> state(S), err(S);
+    std::vector<unsigned long long> steps(S);
+    rbsog_status st = rbsog_pool_state(s->ctx, state.data(), steps.data(), err.data());
     if (st != RBSOG_OK) return st;
-    // 1. retire finished slots
+    // 1. retire finished or failed slots
     for (int k = 0; k < S; ++k) {
-        if (state[k] != 2) continue;
+        if (state[k] != 2 && state[k] != 3) continue;
         Request &r = s->req[s->slot_ticket[k]];
+        r.status = (rbsog_status)err[k];
+        if (state[k] == 3) {                  // count the steps it made, not the ones it was granted
+            s->atom_steps -= (double)s->slot_atoms[k] * (r.nsteps - (long long)steps[k] - s->slot_left[k]);
+            s->failed += 1;
+        }
         r.r.resize(3 * (size_t)r.sys->d.n_atoms);
         r.v.resize(3 * (size_t)r.sys->d.n_atoms);
         st = rbsog_pool_unload(s->ctx, k, r.r.data(), r.v.data(), &r.res);
@@ -288,13 +296,14 @@ rbsog_status rbsog_server_result(rbsog_server *s, long long ticket, int *done, d
     if (r) std::memcpy(r, q.r.data(), q.r.size() * sizeof(double));
     if (v) std::memcpy(v, q.v.data(), q.v.size() * sizeof(double));
     if (res) *res = q.res;
-    return RBSOG_OK;
+    return q.status;
 }
 
 rbsog_status rbsog_server_stats(const rbsog_server *s, double *p50_ms, double *p99_ms, double *atom_steps_per_s,
-                                long long *steps)
+                                long long *steps, int *failed)
 {
     if (!s) return RBSOG_EINVAL;
+    if (failed) *failed = s->failed;
     std::vector<double> v = s->step_ms;
     std::sort(v.begin(), v.end());
     auto pct = [&](double p) {

@@ -130,7 +130,7 @@ def lib():
     L.rbsog_pool_create.argtypes = [C.POINTER(rbsog_params), C.c_int, C.POINTER(rbsog_slot_caps), P, C.POINTER(P)]
     L.rbsog_pool_load.argtypes = [P, C.c_int, C.POINTER(rbsog_system_desc), C.c_int]
     L.rbsog_pool_prime.argtypes = [P]
-    L.rbsog_pool_state.argtypes = [P, _I, C.POINTER(C.c_ulonglong)]
+    L.rbsog_pool_state.argtypes = [P, _I, C.POINTER(C.c_ulonglong), _I]
     L.rbsog_pool_unload.argtypes = [P, C.c_int, _D, _D, C.POINTER(rbsog_result)]
     L.rbsog_server_create.argtypes = [C.POINTER(rbsog_params), C.c_int, C.POINTER(rbsog_slot_caps), C.c_double,
                                       P, C.POINTER(P)]
@@ -142,7 +142,7 @@ def lib():
     L.rbsog_server_submit.argtypes = [P, C.POINTER(rbsog_system_desc), C.c_int, C.POINTER(C.c_longlong)]
     L.rbsog_server_pump.argtypes = [P, C.c_int, _I, _I]
     L.rbsog_server_result.argtypes = [P, C.c_longlong, _I, _D, _D, C.POINTER(rbsog_result)]
-    L.rbsog_server_stats.argtypes = [P, _D, _D, _D, C.POINTER(C.c_longlong)]
+    L.rbsog_server_stats.argtypes = [P, _D, _D, _D, C.POINTER(C.c_longlong), _I]
     L.rbsog_trace_pair_times.argtypes = [P, C.c_int, _D, _I]
     _lib = L
     return L
@@ -412,10 +412,12 @@ class Pool:
         return [result_dict(res[k]) for k in range(self.S)]
 
     def state(self):
+        """(state per slot: 0 empty, 1 running, 2 finished, 3 failed; Philox counters; error codes)."""
         st = np.zeros(self.S, dtype=np.int32)
+        err = np.zeros(self.S, dtype=np.int32)
         steps = (C.c_ulonglong * self.S)()
-        _check(lib().rbsog_pool_state(self.ctx, st.ctypes.data_as(_I), steps), self.ctx)
-        return st, np.array(steps[:], dtype=np.uint64)
+        _check(lib().rbsog_pool_state(self.ctx, st.ctypes.data_as(_I), steps, err.ctypes.data_as(_I)), self.ctx)
+        return st, np.array(steps[:], dtype=np.uint64), err
 
     def unload(self, slot):
         n = self.systems[slot].n
@@ -481,17 +483,24 @@ class Server:
         r = np.zeros((n, 3))
         v = np.zeros((n, 3))
         res = rbsog_result()
-        _check(lib().rbsog_server_result(self.srv, int(ticket), C.byref(done), r.ctypes.data_as(_D),
-                                         v.ctypes.data_as(_D), C.byref(res)))
+        status = lib().rbsog_server_result(self.srv, int(ticket), C.byref(done), r.ctypes.data_as(_D),
+                                           v.ctypes.data_as(_D), C.byref(res))
         if not done.value:
+            if status != RBSOG_OK:
+                raise RbsogError(status, "rbsog_server_result")
             return None
-        return r, v, result_dict(res)
+        out = result_dict(res)
+        out["status"] = status                  # RBSOG_OK, or why the system was stopped early
+        return r, v, out
 
     def stats(self):
         p50, p99, thr = C.c_double(), C.c_double(), C.c_double()
         n = C.c_longlong()
-        _check(lib().rbsog_server_stats(self.srv, C.byref(p50), C.byref(p99), C.byref(thr), C.byref(n)))
-        return {"p50_ms": p50.value, "p99_ms": p99.value, "atom_steps_per_s": thr.value, "steps": n.value}
+        failed = C.c_int()
+        _check(lib().rbsog_server_stats(self.srv, C.byref(p50), C.byref(p99), C.byref(thr), C.byref(n),
+                                        C.byref(failed)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "atom_steps_per_s": thr.value, "steps": n.value,
+                "failed": failed.value}
 
     def close(self):
         if self.srv:

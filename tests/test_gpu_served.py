@@ -46,8 +46,8 @@ def test_pool_matches_plain_contexts(prec):
         pool.load(slot, s, index=s.rng_id)
     pool.prime()
     pool.run(5)
-    state, steps = pool.state()
-    assert list(state) == [1, 0, 1, 1] and list(steps[[0, 2, 3]]) == [5, 5, 5]
+    state, steps, err = pool.state()
+    assert list(state) == [1, 0, 1, 1] and list(steps[[0, 2, 3]]) == [5, 5, 5] and not err.any()
     for slot, s in zip((0, 2, 3), systems):
         r, v, res = pool.unload(slot)
         ra, va, resa = _alone(s, prec, 5)
@@ -65,7 +65,7 @@ def test_pool_step_limits_and_slot_reuse():
     pool.load(1, b, nsteps=6, index=b.rng_id)
     pool.prime()
     pool.run(6)                                       # a stops (frozen) after its 3 steps
-    state, steps = pool.state()
+    state, steps, _ = pool.state()
     assert list(state) == [2, 2] and list(steps) == [3, 6]
     ra, _, _ = pool.unload(0)
     assert np.array_equal(ra, _alone(a, R.RBSOG_FP32, 3)[0])
@@ -108,6 +108,7 @@ def test_server_continuous_batching_matches_alone():
         out = srv.result(t)
         assert out is not None, k
         r, v, res = out
+        assert res["status"] == 0, k
         ra, va, resa = _alone(systems[k], R.RBSOG_FP32, nsteps[k])
         assert np.array_equal(r, ra), k
         assert np.array_equal(v, va), k
@@ -115,4 +116,5 @@ def test_server_continuous_batching_matches_alone():
         assert res["step"] == nsteps[k]
     st = srv.stats()
     assert st["steps"] > 0 and st["p99_ms"] >= st["p50_ms"] > 0 and st["atom_steps_per_s"] > 0
+    assert st["failed"] == 0
     srv.close()

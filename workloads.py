@@ -460,14 +460,15 @@ def membrane(seed: int = 4, Lxy: float = 64.0, Lz: float = 96.0,
 
 def served_batch(n_systems: int = 256, seed: int = 5, n_min: int = 500,
                  n_max: int = 20000, min_box: float = 30.5, steps=(100, 1000),
-                 rate_per_ms: float | None = None):
+                 rate_per_ms: float | None = None, workers: int = 1):
     """Served-request stream: ``n_systems`` independent systems, sizes
     log-uniform in [n_min, n_max] sites, each an electrolyte (C1 density) or a
     water-like box (1 g/cm^3) at random; a box too small for three cutoff
     cells per axis is widened to ``min_box`` (lower density).  Each request
     asks for a uniform number of NPT steps in ``steps``; arrivals are a
     Poisson stream of ``rate_per_ms`` requests per millisecond (all at t=0
-    when None).  Returns a list of (arrival_ms, n_steps, System)."""
+    when None).  ``workers`` > 1 builds the systems in that many spawned
+    processes (same systems).  Returns a list of (arrival_ms, n_steps, System)."""
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_systems))
     kinds = rng.random(n_systems) < 0.5
@@ -476,20 +477,28 @@ def served_batch(n_systems: int = 256, seed: int = 5, n_min: int = 500,
         t = np.cumsum(rng.exponential(1.0 / rate_per_ms, n_systems))
     else:
         t = np.zeros(n_systems)
-    out = []
-    for i in range(n_systems):
-        sub = int(rng.integers(1 << 30))
-        if kinds[i]:
-            n = max(2, int(round(sizes[i] / 2)) * 2)
-            L = max((n / (1000 / 27000.0)) ** (1 / 3), min_box)
-            s = electrolyte(n, L, seed=sub, min_dist=min(2.5, 0.8 * L / n ** (1 / 3)))
-        else:
-            nm = max(1, int(round(sizes[i] / 3)))
-            L = max(66.88 * (nm / 10000.0) ** (1 / 3), min_box)
-            lat = int(math.ceil(nm ** (1 / 3)))
-            s = water(nm, L, seed=sub, lattice=lat)
-        out.append((float(t[i]), int(nsteps[i]), s))
-    return out
+    jobs = [(bool(kinds[i]), float(sizes[i]), int(rng.integers(1 << 30)), float(min_box)) for i in range(n_systems)]
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            systems = list(ex.map(_served_system, jobs, chunksize=4))
+    else:
+        systems = [_served_system(j) for j in jobs]
+    return [(float(t[i]), int(nsteps[i]), systems[i]) for i in range(n_systems)]
+
+
+def _served_system(job):
+    """One system of the served stream: (electrolyte?, size, seed, min box)."""
+    is_el, size, sub, min_box = job
+    if is_el:
+        n = max(2, int(round(size / 2)) * 2)
+        L = max((n / (1000 / 27000.0)) ** (1 / 3), min_box)
+        return electrolyte(n, L, seed=sub, min_dist=min(2.5, 0.8 * L / n ** (1 / 3)))
+    nm = max(1, int(round(size / 3)))
+    L = max(66.88 * (nm / 10000.0) ** (1 / 3), min_box)
+    lat = int(math.ceil(nm ** (1 / 3)))
+    return water(nm, L, seed=sub, lattice=lat)
 
 
 def nacl_crystal(cells: int = 4, a: float = 5.64) -> System:
