@@ -256,6 +256,7 @@ rbsog_status rbsog_get_timing(rbsog_ctx *ctx, int max, char *names, double *ms, 
 typedef struct {
     int max_atoms, max_molecules, max_bonds, max_angles, max_excl, max_types;
     double max_box[3];
+    double max_density;     /* atoms per A^3 a loaded system may reach (sizes the FP32 pair lists) */
 } rbsog_slot_caps;
 
 rbsog_status rbsog_pool_create(const rbsog_params *params, int n_slots, const rbsog_slot_caps *caps,

@@ -60,6 +60,19 @@ struct Batch {
     int item_cap;               // pair work items, all systems
 };
 
+// FP32 pair lists: per (work unit = group x dz plane, lane) a chain of
+// kListChunk-entry chunks from a pool of cap_chunks; an entry is (index of
+// the first of 32 candidates | neighbour-cell code << 25, hit mask).
+constexpr int kListChunk = 16;
+constexpr int kEvalSplit = 4;   // FP32 evaluation warps (hit segments) per 32-atom group
+struct PairList {
+    uint2 *ent;                 // [cap_chunks * kListChunk]
+    int *next;                  // [cap_chunks] next chunk of the same list
+    int *head, *nent, *nhit;    // [units * 32] first chunk, entries and hits of each list
+    int *top;                   // [1] chunks taken this step
+    int cap_chunks;
+};
+
 struct AtomArrays {
     double *r, *p, *F;          // [3N]
     const double *q, *mass;     // [N]
@@ -82,6 +95,7 @@ struct AtomArrays {
     // ti * ntypes + tj = (4 eps sig^12, 4 eps sig^6); ljf_lo: FP32 remainders
     const float2 *ljf, *ljf_lo;
     const double2 *ljd;
+    PairList plist;             // FP32 build only
 };
 
 // ---- k_bin.cu
@@ -91,7 +105,8 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
 void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st);
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 
-// ---- k_pair.cu: partial = per block of kPairWarps work units (item x dz plane):
+// ---- k_pair.cu: partial = per record (FP32: one per item; FP64: one per
+// block of kPairWarps work units = item x dz plane):
 // (Ucoul, Ulj, Wc[6], Wl[6], W[6]) as kPairRec doubles; energies and the
 // Coulomb/LJ split only when `energy` is set (W, the total, always).  Each
 // system's item range is a multiple of kPairWarps items, so a block never
@@ -100,7 +115,7 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 constexpr int kPairWarps = 1;       // one warp per block: no block-level wait on a slower warp
 constexpr int kPairRec = 20;
 constexpr int kPairRedBlocks = 8;   // second-stage reduction of the unit records, per system
-void launch_reduce_pair(const Batch &b, const double *pair_part, double *pair_red, cudaStream_t st);
+void launch_reduce_pair(const Batch &b, int rec_per_item, const double *pair_part, double *pair_red, cudaStream_t st);
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st);
 

@@ -204,20 +204,21 @@ void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &i
 //  [15..20] W short Coulomb, [21..26] W^F,r*, [27..32] W^F,nr*, [33..38] W LJ,
 //  [39..44] W bonded + exclusions, [45..50] K, [51] V, [52..54] L,
 //  [55] nD, [56] acc r, [57] acc nr, [58] flags, [59..61] box momenta.
-// Second stage of the pair records: system s's unit records (items x dz
-// planes of its active items) in kPairRedBlocks contiguous ranges, each summed
-// in a fixed order.  grid (S, kPairRedBlocks).
+// Second stage of the pair records: system s's records (rec_per_item per
+// active item: 1 in the FP32 build, one per dz plane in the FP64 build) in
+// kPairRedBlocks contiguous ranges, each summed in a fixed order.
+// grid (S, kPairRedBlocks).
 constexpr int kRedThreads = 128;
 
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_pair(const DevSys *__restrict__ sys, int span, const double *__restrict__ part,
+k_reduce_pair(const DevSys *__restrict__ sys, int rec_per_item, const double *__restrict__ part,
               double *__restrict__ red)
 {
     __shared__ double buf[kPairRec * (kRedThreads + 1) + 4 * kPairRec];
     const int s = blockIdx.x;
     const DevSys &d = sys[s];
-    const int u0 = d.item0 * span / kPairWarps;
-    const int nu = (d.nitems * span + kPairWarps - 1) / kPairWarps;
+    const int u0 = d.item0 * rec_per_item;
+    const int nu = d.nitems * rec_per_item;
     const int per = (nu + kPairRedBlocks - 1) / kPairRedBlocks;
     const int a = min(nu, (int)blockIdx.y * per), e = min(nu, a + per);
     double v[kPairRec];
@@ -231,9 +232,9 @@ k_reduce_pair(const DevSys *__restrict__ sys, int span, const double *__restrict
     block_reduce_lanes<kPairRec, kRedThreads>(v, buf, red + ((size_t)s * kPairRedBlocks + blockIdx.y) * kPairRec);
 }
 
-void launch_reduce_pair(const Batch &b, const double *pair_part, double *pair_red, cudaStream_t st)
+void launch_reduce_pair(const Batch &b, int rec_per_item, const double *pair_part, double *pair_red, cudaStream_t st)
 {
-    k_reduce_pair<<<dim3(b.S, kPairRedBlocks), kRedThreads, 0, st>>>(b.sys, 2 * b.sub + 1, pair_part, pair_red);
+    k_reduce_pair<<<dim3(b.S, kPairRedBlocks), kRedThreads, 0, st>>>(b.sys, rec_per_item, pair_part, pair_red);
 }
 
 constexpr int kFinThreads = 128;

@@ -312,7 +312,7 @@ void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const M
                      cudaStream_t st)
 {
     const dim3 grid(b.nchunks, kChunk / kLrAtoms);
-    const int nparts = 2 * b.sub + 1;
+    const int nparts = precision == 1 ? kEvalSplit : 2 * b.sub + 1;   // FP32: hit segments; FP64: dz planes
     if (precision == 1)
         k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
                                                     coef, Dcap, a.rank, a.fpart4, nparts, b.N, a.F);

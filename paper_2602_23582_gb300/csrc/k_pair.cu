@@ -33,8 +33,9 @@ namespace rbsog {
 
 namespace {
 
-constexpr int QCAP = 64;      // per-lane queue (power of two); pending <= 32 before a batch
+constexpr int QCAP = 64;      // FP64 kernel: per-lane queue (power of two); pending <= 32 before a batch
 constexpr int kMaxPlane = 32; // neighbour cells of one dz plane (25 for cells of r_c/2)
+constexpr int kMaxNb = 128;   // neighbour cells of the stencil (125 for cells of r_c/2)
 
 size_t pair_smem(int precision)
 {
@@ -204,26 +205,134 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP32 kernel.  A queued hit carries the index (< 25) of its neighbour cell
-// within the plane; the warp keeps the plane's offsets in shared memory.
+// FP32 path in two kernels.
+//
+// k_pair_build: work unit = 32-atom group x dz plane of its neighbour cells.
+// The warp walks the plane's cells with warp-broadcast candidate loads; each
+// lane tests its atom against 32 candidates at a time and, when any hit, stores
+// one list entry: (index of the first candidate | neighbour-cell code << 25,
+// 32-bit hit mask).  Entries go to the lane's own list, chunks of kListChunk
+// entries taken from a pool with one atomic per warp for all lanes that need a
+// chunk at once.  A lane's entries keep its candidate order, so the evaluation
+// order does not depend on which chunks it got.
+//
+// k_pair_eval: work unit = 32-atom group x one of kEvalSplit segments of each
+// atom's hits (all planes in order, split by hit count), one hit per lane and
+// round, so every lane carries about the same number of pairs; segment k
+// writes force partial k, summed in segment order by the force assembly.
 // ---------------------------------------------------------------------------
-template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kPairWarps, 20 / kPairWarps)
-k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
-           const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4,
-           const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
-           const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N,
-           float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
+__global__ void __launch_bounds__(32, 32)
+k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
+             const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
+             PairList L, const float rc2_hi)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double rec[kPairWarps][kPairRec];
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
-    float4 *offp = reinterpret_cast<float4 *>(smem + kPairWarps * QCAP * 32 * sizeof(unsigned)) + warp * kMaxPlane;
+    __shared__ float2 offp[kMaxPlane];
+    const int lane = lane_id();
     const int span = 2 * sub + 1;
-    const int unit = blockIdx.x * kPairWarps + warp;   // (group, dz plane)
+    const int unit = blockIdx.x;
     const int2 item = items[unit / span];
+    if (item.x < 0) return;                            // whole block
     const int part = unit % span;
+    const int gc = item.x;
+    const int s = cell_sys[gc];
+    const DevSys &d = sys[s];
+    const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
+    const int lc = gc - d.cell0;
+    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+    const int ddz = part - sub;
+    for (int nb = lane; nb < span * span; nb += 32)
+        offp[nb] = make_float2((float)((nb % span - sub) * d.w[0]), (float)((nb / span - sub) * d.w[1]));
+    const float ozh = (float)(ddz * d.w[2]);
+    __syncwarp();
+    const int i0 = start[gc] + 32 * item.y;
+    const int ni = min(32, count[gc] - 32 * item.y);
+    const bool vi = lane < ni;
+    // lanes without an atom sit far away: their cutoff test never passes
+    float4 pi = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-0x7fffffff));
+    if (vi) pi = pos4[i0 + lane];
+    const int moli = __float_as_int(pi.w);
+    int cur = -1, fill = kListChunk, first = -1, nent = 0, nhit = 0;
+    bool overflow = false;
+    const int gz = wrapi(cz + ddz, n2);
+    for (int nb = 0; nb < span * span; ++nb) {
+        const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
+        const int j0 = start[g], nj = count[g];
+        const float2 o = offp[nb];
+        const float xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - ozh;
+        const unsigned code = (unsigned)(part * span * span + nb) << 25;
+        for (int jb = 0; jb < nj; jb += 32) {
+            const float4 *pc4 = pos4 + j0 + jb;
+            unsigned hm = 0;                           // hits among these 32 candidates
+            if (nj - jb >= 32) {
+#pragma unroll
+                for (int ub = 0; ub < 32; ub += 8) {
+                    float4 q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) q[u] = __ldg(pc4 + ub + u);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float dx = xi - q[u].x, dy = yi - q[u].y, dz = zi - q[u].z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < rc2_hi && __float_as_int(q[u].w) != moli) hm |= 1u << (ub + u);
+                    }
+                }
+            } else {
+                for (int u = 0; u < nj - jb; ++u) {
+                    const float4 pj = __ldg(pc4 + u);
+                    const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2_hi && __float_as_int(pj.w) != moli) hm |= 1u << u;
+                }
+            }
+            // lanes whose chunk is full and that have an entry to store take new chunks together
+            const unsigned need = __ballot_sync(0xffffffffu, hm != 0u && fill == kListChunk);
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                int b0 = 0;
+                if (lane == leader) b0 = atomicAdd(L.top, __popc(need));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (hm != 0u && fill == kListChunk) {
+                    const int c = b0 + __popc(need & ((1u << lane) - 1u));
+                    if (c < L.cap_chunks) {
+                        if (cur >= 0) L.next[cur] = c;
+                        else first = c;
+                        cur = c;
+                        fill = 0;
+                    } else {
+                        overflow = true;
+                    }
+                }
+            }
+            if (hm != 0u && fill < kListChunk) {
+                L.ent[(size_t)cur * kListChunk + fill] = make_uint2((unsigned)(j0 + jb) | code, hm);
+                ++fill;
+                ++nent;
+                nhit += __popc(hm);
+            }
+        }
+    }
+    if (vi) {
+        const size_t k = (size_t)unit * 32 + lane;
+        L.head[k] = first;
+        L.nent[k] = nent;
+        L.nhit[k] = nhit;
+    }
+    if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(&sys[s].flags, (int)FLAG_OVERFLOW);
+}
+
+template <int NF, bool EN>
+__global__ void __launch_bounds__(32, 24)
+k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
+            const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4,
+            const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
+            const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N, const PairList L,
+            float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
+{
+    __shared__ float4 offh[kMaxNb], offl[kMaxNb];
+    const int lane = lane_id();
+    const int span = 2 * sub + 1;
+    const int it = blockIdx.x / kEvalSplit, seg = blockIdx.x % kEvalSplit;
+    const int2 item = items[it];
     double u0 = 0.0, u1 = 0.0;
     float wv[18];                                      // Wc, Wl (energy steps), W
 #pragma unroll
@@ -231,26 +340,55 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     if (item.x >= 0) {                                 // warp-uniform
         const int gc = item.x;
         const DevSys &d = sys[cell_sys[gc]];
-        const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
-        const int lc = gc - d.cell0;
-        const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-        const int ddz = part - sub;
-        const double ozd = ddz * d.w[2];
-        const float ozh = (float)ozd, ozl = (float)(ozd - (double)ozh);
-        for (int nb = lane; nb < span * span; nb += 32) {
-            const double ox = (nb % span - sub) * d.w[0], oy = (nb / span - sub) * d.w[1];
-            const float oxh = (float)ox, oyh = (float)oy;
-            offp[nb] = make_float4(oxh, oyh, (float)(ox - (double)oxh), (float)(oy - (double)oyh));
+        // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
+        // must not shift every cross-cell distance the same way)
+        for (int nb = lane; nb < span * span * span; nb += 32) {
+            const double ox = (nb % span - sub) * d.w[0], oy = ((nb / span) % span - sub) * d.w[1],
+                         oz = (nb / (span * span) - sub) * d.w[2];
+            const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
+            offh[nb] = make_float4(hx, hy, hz, 0.f);
+            offl[nb] = make_float4((float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
         }
         __syncwarp();
         const int i0 = start[gc] + 32 * item.y;
         const int ni = min(32, count[gc] - 32 * item.y);
         const bool vi = lane < ni;
-        // lanes without an atom sit far away: their cutoff test never passes
-        float4 pi = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-0x7fffffff));
+        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 pq = make_float2(0.f, 0.f);
-        if (vi) { pi = pos4[i0 + lane]; pq = qt[i0 + lane]; }
-        const int moli = __float_as_int(pi.w);
+        const size_t u0i = (size_t)it * span * 32 + lane;   // this lane's list in plane 0
+        // this warp takes hits [h0, h1) of the lane's stream (all planes in order)
+        int nh = 0, pl = 0, rem = 0, cur = 0, pos = 0;
+        unsigned base = 0u, mask = 0u;
+        if (vi) {
+            pi = pos4[i0 + lane];
+            pq = qt[i0 + lane];
+            int tot = 0;
+            for (int p2 = 0; p2 < span; ++p2) tot += L.nhit[u0i + (size_t)p2 * 32];
+            const int h0 = (int)((long long)tot * seg / kEvalSplit);
+            const int h1 = (int)((long long)tot * (seg + 1) / kEvalSplit);
+            nh = h1 - h0;
+            if (nh > 0) {
+                int skip = h0;
+                int hp = L.nhit[u0i];
+                while (skip >= hp) { skip -= hp; ++pl; hp = L.nhit[u0i + (size_t)pl * 32]; }
+                rem = L.nent[u0i + (size_t)pl * 32];
+                cur = L.head[u0i + (size_t)pl * 32];
+                while (skip > 0) {                     // walk entries up to hit h0
+                    const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
+                    ++pos;
+                    --rem;
+                    if (pos == kListChunk && rem > 0) { cur = L.next[cur]; pos = 0; }
+                    const int c = __popc(en.y);
+                    if (c <= skip) {
+                        skip -= c;
+                    } else {
+                        base = en.x;
+                        mask = en.y;
+                        for (; skip > 0; --skip) mask &= mask - 1u;
+                    }
+                }
+            }
+        }
         const int rowi = d.lj0 + __float_as_int(pq.y) * d.ntypes;
         const float2 *ljrow = lj + rowi, *ljlorow = ljlo + rowi;
         AccF acc;
@@ -258,77 +396,40 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
         acc.uc = acc.ul = acc.uq = acc.cuc = acc.cul = acc.cuq = 0.f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc.w[k] = acc.wc[k] = acc.wl[k] = 0.f;
-        int head = 0, tail = 0;
-
-        // queue entry: neighbour atom index (25 bits) | neighbour cell in the plane (7 bits)
-        // pairs within a relative 1e-5 of r_c^2 are queued and decided in FP64
-        // from the original positions (the energy kernel N is about 2e-3 / A
-        // at r_c, so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
-        auto eval_one = [&](unsigned e) {
-            const unsigned j = e & 0x1ffffffu;
-            const float4 pj = pos4[j];
-            const float2 qj = qt[j];
-            const float4 o = offp[e >> 25];
-            const float dx = ((pi.x - o.x) - pj.x) - o.z, dy = ((pi.y - o.y) - pj.y) - o.w,
-                        dz = ((pi.z - ozh) - pj.z) - ozl;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= pc.rc2_lo && !inside_cutoff_fp64(r, sidx[i0 + lane], sidx[j], d.L, pc.rc2d)) return;
-            pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qj, acc);
-        };
-        auto pop = [&]() {
-            const int slot = (head & (QCAP - 1)) * 32 + lane;
-            ++head;
-            eval_one(q[slot]);
-        };
-
-        const int gz = wrapi(cz + ddz, n2);
-        for (int nb = 0; nb < span * span; ++nb) {
-            const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
-            const int j0 = start[g], nj = count[g];
-            const float4 o = offp[nb];
-            const float xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - ozh;
-            for (int jb = 0; jb < nj; jb += 32) {
-                const float4 *pc4 = pos4 + j0 + jb;
-                unsigned hm = 0;                       // hits among these 32 candidates
-                if (nj - jb >= 32) {
-#pragma unroll
-                    for (int ub = 0; ub < 32; ub += 4) {
-                        float4 p[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) p[u] = __ldg(pc4 + ub + u);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float dx = xi - p[u].x, dy = yi - p[u].y, dz = zi - p[u].z;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < pc.rc2_hi && __float_as_int(p[u].w) != moli) hm |= 1u << (ub + u);
-                        }
+        const int tmax = __reduce_max_sync(0xffffffffu, nh);
+        for (int k = 0; k < tmax; ++k) {
+            if (k < nh) {
+                while (mask == 0u) {                   // next (base, mask) entry of this lane
+                    while (rem == 0) {                 // next plane's list
+                        ++pl;
+                        rem = L.nent[u0i + (size_t)pl * 32];
+                        cur = L.head[u0i + (size_t)pl * 32];
+                        pos = 0;
                     }
-                } else {
-                    for (int u = 0; u < nj - jb; ++u) {
-                        const float4 pj = __ldg(pc4 + u);
-                        const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < pc.rc2_hi && __float_as_int(pj.w) != moli) hm |= 1u << u;
-                    }
+                    const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
+                    base = en.x;
+                    mask = en.y;
+                    ++pos;
+                    --rem;
+                    if (pos == kListChunk && rem > 0) { cur = L.next[cur]; pos = 0; }
                 }
-                const unsigned base = (unsigned)(j0 + jb) | ((unsigned)nb << 25);
-                while (hm) {
-                    q[(tail & (QCAP - 1)) * 32 + lane] = base + (unsigned)(__ffs(hm) - 1);
-                    hm &= hm - 1u;
-                    ++tail;
-                }
-                // full-warp rounds: every lane with an atom has a hit queued
-                const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
-                for (int t = 0; t < mn; ++t)
-                    if (vi) pop();
-                // keep room for the next 32 candidates
-                while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32)
-                    if (tail > head) pop();
+                const unsigned e = base + (unsigned)(__ffs(mask) - 1);
+                mask &= mask - 1u;
+                const unsigned j = e & 0x1ffffffu;
+                const float4 pj = pos4[j];
+                const float2 qj = qt[j];
+                const float4 oh = offh[e >> 25], ol = offl[e >> 25];
+                const float dx = ((pi.x - oh.x) - pj.x) - ol.x, dy = ((pi.y - oh.y) - pj.y) - ol.y,
+                            dz = ((pi.z - oh.z) - pj.z) - ol.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                // pairs within a relative 1e-5 of r_c^2 are decided in FP64 from the
+                // original positions (the energy kernel N is about 2e-3 / A at r_c,
+                // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
+                if (r2 < pc.rc2_lo || inside_cutoff_fp64(r, sidx[i0 + lane], sidx[j], d.L, pc.rc2d))
+                    pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qj, acc);
             }
         }
-        while (__any_sync(0xffffffffu, tail > head))
-            if (tail > head) pop();
-        if (vi) Fpart[(size_t)part * N + i0 + lane] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);
+        if (vi) Fpart[(size_t)seg * N + i0 + lane] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);
         // virials: FP32 warp sums; energies: FP64 (compensated lanes), with the
         // constant of the energy tail applied to sum q_i q_j here
 #pragma unroll
@@ -343,20 +444,14 @@ k_pair_f32(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
             }
         }
     }
-    if (lane == 0) {
-        rec[warp][0] = u0;
-        rec[warp][1] = u1;
+    // one record per (item, segment): lane t writes value t (each pair was seen from both atoms)
+    double v = 0.0;
+    if (lane == 0) v = u0;
+    if (lane == 1) v = u1;
 #pragma unroll
-        for (int k = 0; k < 18; ++k) rec[warp][2 + k] = (double)wv[k];
-    }
-    __syncthreads();
-    if (threadIdx.x < kPairRec) {
-        const int t = threadIdx.x;
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kPairWarps; ++w) s += rec[w][t];
-        partial[(size_t)blockIdx.x * kPairRec + t] = 0.5 * s;   // each pair was seen from both atoms
-    }
+    for (int k = 0; k < 18; ++k)
+        if (lane == 2 + k) v = (double)wv[k];
+    if (lane < kPairRec) partial[(size_t)blockIdx.x * kPairRec + lane] = 0.5 * v;
 }
 
 // ---------------------------------------------------------------------------
@@ -472,36 +567,32 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
 // outside any stream capture).
 cudaError_t prepare_pair()
 {
-    const int sf = (int)pair_smem(1), sd = (int)pair_smem(0);
-    cudaError_t e = cudaFuncSetAttribute(k_pair_f32<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f32<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, sd);
-    return e;
+    return cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(0));
 }
 
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st)
 {
     // item_cap is a multiple of kPairWarps per system, so every block lies in one system
-    const int blocks = b.item_cap * (2 * b.sub + 1) / kPairWarps;
-    const size_t sm = pair_smem(precision);
-    const dim3 th(32 * kPairWarps);
-#define RBSOG_PAIR_F32(NF, EN)                                                                              \
-    k_pair_f32<NF, EN><<<blocks, th, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, a.qt,  \
-                                               a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, b.N, a.fpart4, partial, cf)
+    const int units = b.item_cap * (2 * b.sub + 1);
     if (precision == 1) {
+        cudaMemsetAsync(a.plist.top, 0, sizeof(int), st);
+        k_pair_build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist,
+                                           cf.rc2_hi);
+#define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
+    k_pair_eval<NF, EN><<<b.item_cap * kEvalSplit, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items,    \
+                                                                a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \
+                                                                b.N, a.plist, a.fpart4, partial, cf)
         if (cf.nff == 4) {
-            if (energy) RBSOG_PAIR_F32(4, true); else RBSOG_PAIR_F32(4, false);
+            if (energy) RBSOG_PAIR_EVAL(4, true); else RBSOG_PAIR_EVAL(4, false);
         } else {
-            if (energy) RBSOG_PAIR_F32(0, true); else RBSOG_PAIR_F32(0, false);
+            if (energy) RBSOG_PAIR_EVAL(0, true); else RBSOG_PAIR_EVAL(0, false);
         }
+#undef RBSOG_PAIR_EVAL
     } else {
-        k_pair_f64<<<blocks, th, sm, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.posd, a.aux, a.ljd,
-                                           b.sub, b.N, a.fpartd, partial, cd);
+        k_pair_f64<<<units / kPairWarps, 32 * kPairWarps, pair_smem(0), st>>>(
+            b.sys, b.cell_sys, a.start, a.count, a.items, a.posd, a.aux, a.ljd, b.sub, b.N, a.fpartd, partial, cd);
     }
-#undef RBSOG_PAIR_F32
 }
 
 }  // namespace rbsog

@@ -31,6 +31,7 @@ constexpr double kNktv2p = 68568.415;                        // atm per kcal/(mo
 // systems, a pool by the caller's slot classes.
 struct SlotCaps {
     int atoms = 0, mols = 0, bonds = 0, angles = 0, excl = 0, types = 1;
+    double rho = 0.0;                  // atoms per A^3 the slot's FP32 pair lists are sized for
     double box[3] = {0.0, 0.0, 0.0};   // largest box the slot's cell grid is sized for
 };
 
@@ -85,6 +86,9 @@ struct rbsog_ctx {
     double *self_e = nullptr;
     double4 *fpart = nullptr;   // pair forces per dz plane (FP32 build reads it as float4)
     double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
+    uint2 *pl_ent = nullptr;     // FP32 pair lists
+    int *pl_next = nullptr, *pl_head = nullptr, *pl_nent = nullptr, *pl_nhit = nullptr, *pl_top = nullptr;
+    int plist_cap = 0;
     double *inv_m = nullptr, *sdv = nullptr;   // per-atom integrator constants
     double2 *ljd = nullptr;     // LJ blocks per system
     float2 *ljf = nullptr, *ljf_lo = nullptr;
@@ -227,7 +231,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     record(c, "molecules");
     launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
     record(c, "kick_kinetic");
-    launch_reduce_pair(c->b, c->pair_part, c->pair_red, c->st);
+    launch_reduce_pair(c->b, prec == 1 ? kEvalSplit : 2 * c->prm.cell_sub + 1, c->pair_part, c->pair_red, c->st);
     launch_finalize(c->b, c->pair_red, c->lr_out, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
     record(c, "finalize");
@@ -335,6 +339,7 @@ SlotCaps caps_of(const rbsog_system_desc &d)
     cp.excl = d.n_excl;
     cp.types = d.ntypes;
     for (int a = 0; a < 3; ++a) cp.box[a] = d.box[a];
+    cp.rho = d.n_atoms / (d.box[0] * d.box[1] * d.box[2]);
     return cp;
 }
 
@@ -733,8 +738,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
-                  dalloc(c, c->pair_part, (size_t)item_cap * (2 * P.cell_sub + 1) / kPairWarps * kPairRec) &&
-                  dalloc(c, c->fpart, (size_t)N * (2 * P.cell_sub + 1)) &&
+                  dalloc(c, c->pair_part, (size_t)item_cap * std::max(2 * P.cell_sub + 1, kEvalSplit) * kPairRec) &&
+                  dalloc(c, c->fpart, (size_t)N * std::max(2 * P.cell_sub + 1, kEvalSplit)) &&
                   dalloc(c, c->pair_red, (size_t)S * kPairRedBlocks * kPairRec) &&
                   dalloc(c, c->lr_out, (size_t)S * 16) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
@@ -752,6 +757,27 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                 ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, N) && dalloc(c, c->qt, N) && dalloc(c, c->su, N);
             else
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N);
+        }
+        if (ok && P.precision == 1) {
+            // FP32 pair lists: 1.25 x the neighbours inside r_c at each slot's
+            // density (room for compression), at least 1.5 hits per entry (a
+            // batch of 32 candidates with any hit usually holds 3-6), plus one
+            // partly filled chunk per atom and dz plane
+            const int span = 2 * P.cell_sub + 1;
+            double entries = 0.0;
+            for (int k = 0; k < S; ++k)
+                entries += (double)caps[k].atoms * 1.25 * (4.0 / 3.0) * kPi * P.rc * P.rc * P.rc * caps[k].rho / 1.5;
+            const double chunks = std::ceil(entries / kListChunk) + (double)N * span + 64.0;
+            if (chunks * kListChunk >= 2147483647.0) {
+                rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "pair lists beyond 2^31 entries");
+                free_ctx(c);
+                return rr;
+            }
+            c->plist_cap = (int)chunks;
+            const size_t units = (size_t)item_cap * span;
+            ok = dalloc(c, c->pl_ent, (size_t)c->plist_cap * kListChunk) && dalloc(c, c->pl_next, (size_t)c->plist_cap) &&
+                 dalloc(c, c->pl_head, units * 32) && dalloc(c, c->pl_nent, units * 32) &&
+                 dalloc(c, c->pl_nhit, units * 32) && dalloc(c, c->pl_top, 1);
         }
         if (ok) ok = cudaMemset(c->sysred, 0, sizeof(double) * (size_t)S * kRed) == cudaSuccess;
         if (!ok) {
@@ -831,6 +857,9 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
         c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
+        c->a.plist.ent = c->pl_ent; c->a.plist.next = c->pl_next; c->a.plist.head = c->pl_head;
+        c->a.plist.nent = c->pl_nent; c->a.plist.nhit = c->pl_nhit; c->a.plist.top = c->pl_top;
+        c->a.plist.cap_chunks = c->plist_cap;
         c->m.nmol = nmolx; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
@@ -880,6 +909,8 @@ rbsog_status rbsog_pool_create(const rbsog_params *params, int n_slots, const rb
             return RBSOG_EINVAL;
         sc[k].atoms = c.max_atoms; sc[k].mols = c.max_molecules; sc[k].bonds = c.max_bonds;
         sc[k].angles = c.max_angles; sc[k].excl = c.max_excl; sc[k].types = c.max_types;
+        if (!(c.max_density > 0)) return RBSOG_EINVAL;
+        sc[k].rho = c.max_density;
         for (int a = 0; a < 3; ++a) {
             if (!(c.max_box[a] > 0)) return RBSOG_EBOX;
             sc[k].box[a] = c.max_box[a];

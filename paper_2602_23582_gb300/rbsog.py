@@ -47,7 +47,7 @@ class RbsogError(RuntimeError):
 class rbsog_slot_caps(C.Structure):
     _fields_ = [("max_atoms", C.c_int), ("max_molecules", C.c_int), ("max_bonds", C.c_int),
                 ("max_angles", C.c_int), ("max_excl", C.c_int), ("max_types", C.c_int),
-                ("max_box", C.c_double * 3)]
+                ("max_box", C.c_double * 3), ("max_density", C.c_double)]
 
 
 class rbsog_params(C.Structure):
@@ -371,7 +371,7 @@ def result_dict(r: rbsog_result) -> dict:
 
 
 def slot_caps(max_atoms, max_box, max_molecules=None, max_bonds=None, max_angles=None, max_excl=None,
-              max_types=4) -> rbsog_slot_caps:
+              max_types=4, max_density=0.12) -> rbsog_slot_caps:
     """Capacities of one slot; term limits default to generous multiples of the atoms."""
     c = rbsog_slot_caps()
     c.max_atoms = int(max_atoms)
@@ -380,6 +380,7 @@ def slot_caps(max_atoms, max_box, max_molecules=None, max_bonds=None, max_angles
     c.max_angles = int(max_angles if max_angles is not None else max_atoms)
     c.max_excl = int(max_excl if max_excl is not None else 2 * max_atoms)
     c.max_types = int(max_types)
+    c.max_density = float(max_density)
     for a in range(3):
         c.max_box[a] = float(max_box[a] if hasattr(max_box, "__len__") else max_box)
     return c

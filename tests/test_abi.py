@@ -49,6 +49,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert out[4] == R.rbsog_result.step.offset
     assert out[5] == ctypes.sizeof(R.rbsog_slot_caps)
     assert out[6] == R.rbsog_slot_caps.max_box.offset
+    assert R.rbsog_slot_caps.max_density.offset == R.rbsog_slot_caps.max_box.offset + 24
     assert out[7] == R.rbsog_params.thermo_every.offset
 
 
