@@ -137,7 +137,9 @@ void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D,
                double *part, cudaStream_t st);
 void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_sys, const int *D,
                      const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
-                     double *rho, ModeCoef *coef, double *lr_out, cudaStream_t st);
+                     double *rho, ModeCoef *coef, double *est, cudaStream_t st);
+// mode groups of k_estimate: est holds S x estimate_blocks(Dcap) x 7 partial sums
+int estimate_blocks(int Dcap);
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
                      int Dcap, cudaStream_t st);
 size_t sk_stateless_workspace(int n, int nD);
@@ -166,7 +168,8 @@ void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const S
 // ---- k_integrate.cu
 struct IntegArgs {
     double dt, T, Pext, gamma, gamma_box, kB, ftm2v, nktv2p;
-    double c_atom;                    // exp(-gamma dt)
+    double c_atom, c_box;             // exp(-gamma dt), exp(-gamma_box dt)
+    double ke;                        // Coulomb constant
     const double *inv_m, *sdv;        // per atom: 1 / m, sqrt((1 - c^2) m kB T ftm2v)
     int noise_f32;                    // 1: Gaussian noise drawn in FP32 (FP32 build)
     uint64_t seed;                    // a step uses the Philox counter DevSys::step + 1
@@ -178,7 +181,7 @@ void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &i
                          double *kin_part, cudaStream_t st);
 // per-system reduction of every partial into sysred[S x kRed]; advances *step
 constexpr int kRed = 64;
-void launch_finalize(const Batch &b, const double *pair_part, const double *lr_out,
+void launch_finalize(const Batch &b, const double *pair_part, const double *est, int est_blocks, int P,
                      const double *mol_part, const int *mchunk_first, const int *mchunk_count,
                      const double *kin_part, const int *chunk_first, const int *chunk_count,
                      const double *self_energy, const IntegArgs &ia, int do_box_kick, int adv,

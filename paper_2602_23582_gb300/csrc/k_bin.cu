@@ -171,7 +171,7 @@ __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ 
 
 // One warp per cell: bitonic sort of the cell's atom list by original index,
 // then gather the cell-sorted copies used by the pair kernel.
-constexpr int kSortWarps = 4;
+constexpr int kSortWarps = 1;
 
 __global__ void __launch_bounds__(32 * kSortWarps)
 k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C, int *__restrict__ sidx,

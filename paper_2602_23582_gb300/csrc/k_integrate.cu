@@ -72,7 +72,7 @@ __global__ void k_box_half(DevSys *sys, int S, const IntegArgs ia, const double 
     double z[4];
     box_muller2(wds[0], wds[1], z[0], z[1]);
     box_muller2(wds[2], wds[3], z[2], z[3]);
-    const double ch = exp(-ia.gamma_box * ia.dt);
+    const double ch = ia.c_box;
     for (int g = 0; g < ng; ++g) {
         if (d.Mbox[g] <= 0.0) continue;
         double sdv = sqrt((1.0 - ch * ch) * d.Mbox[g] * ia.kB * ia.T * ia.ftm2v);
@@ -240,8 +240,8 @@ void launch_reduce_pair(const Batch &b, int rec_per_item, const double *pair_par
 constexpr int kFinThreads = 128;
 
 __global__ void __launch_bounds__(kFinThreads)
-k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__restrict__ lr_out,
-           const double *__restrict__ mol_part, const int *__restrict__ mchunk_first,
+k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__restrict__ est, int est_blocks,
+           int P, const double *__restrict__ mol_part, const int *__restrict__ mchunk_first,
            const int *__restrict__ mchunk_count, const double *__restrict__ kin_part,
            const int *__restrict__ chunk_first, const int *__restrict__ chunk_count,
            const double *__restrict__ self_energy, const IntegArgs ia, int do_box_kick, int adv,
@@ -277,7 +277,17 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
     block_reduce_lanes<NV, kFinThreads>(v, buf, acc);
     __syncthreads();
     if (tid != 0) return;
-    const double *lr = lr_out + (size_t)s * 16;
+    // long range (eqs. U_F*, P_F,r*, P_F,nr*): mode-group sums in group order,
+    // then the prefactors k_e S^r / (4 V P) and -k_e S^nr / (8 V P)
+    double es[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int g = 0; g < est_blocks; ++g)
+#pragma unroll
+        for (int t = 0; t < 7; ++t) es[t] += est[((size_t)s * est_blocks + g) * 7 + t];
+    const double Vb = d.L[0] * d.L[1] * d.L[2];
+    double lr[8];
+    lr[0] = ia.ke * d.Sr / (4.0 * Vb * P) * es[0];
+    lr[1] = lr[0];
+    for (int a = 0; a < 6; ++a) lr[2 + a] = -ia.ke * d.Snr / (8.0 * Vb * P) * es[1 + a];
     const double us = self_energy[2 * s];        // U_self (App. A)
     const double uxc = self_energy[2 * s + 1];   // FP32 build: sum over exclusions of ke q_i q_j F_E(0)
     // energies and the Coulomb/LJ virial split come from the pair kernel only
@@ -340,12 +350,13 @@ void launch_set_step(const Batch &b, unsigned long long step, cudaStream_t st)
     k_set_step<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, step);
 }
 
-void launch_finalize(const Batch &b, const double *pair_part, const double *lr_out, const double *mol_part,
+void launch_finalize(const Batch &b, const double *pair_part, const double *est, int est_blocks, int P,
+                     const double *mol_part,
                      const int *mchunk_first, const int *mchunk_count, const double *kin_part,
                      const int *chunk_first, const int *chunk_count, const double *self_energy,
                      const IntegArgs &ia, int do_box_kick, int adv, double *sysred, cudaStream_t st)
 {
-    k_finalize<<<b.S, kFinThreads, 0, st>>>(b.sys, pair_part, lr_out, mol_part, mchunk_first, mchunk_count,
+    k_finalize<<<b.S, kFinThreads, 0, st>>>(b.sys, pair_part, est, est_blocks, P, mol_part, mchunk_first, mchunk_count,
                                             kin_part, chunk_first, chunk_count, self_energy, ia, do_box_kick,
                                             adv, sysred, 2 * b.sub + 1);
 }

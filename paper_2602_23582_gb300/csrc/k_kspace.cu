@@ -135,77 +135,95 @@ void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D,
                                                 D, Dcap, part);
 }
 
-// One block per system: rho = sum of chunk partials (fixed order), estimators,
-// per-mode force coefficients.  lr_out[s][16] = {U^F*, V P^F,r* (scalar),
-// V P^F,nr* xx yy zz xy xz yz, Sr, Snr}.
-constexpr int kEstThreads = 128;
+// One block per (system, group of 32 modes).  Warp w sums its share of the
+// chunk partials of rho (fixed chunk ranges, in chunk order), warp 0 adds the
+// shares in warp order and computes, per mode, the force coefficients and the
+// mode's terms of the estimators; the group's sums go to
+// est[(s * groups + g) * 7 + t] = {sum c_r |rho|^2 / k^2,
+// sum c_nr |rho|^2 k (x) k / k^4 (xx yy zz xy xz yz)}, and k_finalize adds the
+// groups in order and applies the prefactors (eqs. U_F*, P_F,r*, P_F,nr*).
+constexpr int kEstModes = 32, kEstWarps = 4;
 
-__global__ void __launch_bounds__(kEstThreads)
-k_estimate(DevSys *sys, const int *__restrict__ first_chunk, const int *__restrict__ nchunk_sys,
+int estimate_blocks(int Dcap) { return (Dcap + kEstModes - 1) / kEstModes; }
+
+__global__ void __launch_bounds__(32 * kEstWarps)
+k_estimate(const DevSys *sys, const int *__restrict__ first_chunk, const int *__restrict__ nchunk_sys,
            const int *__restrict__ D_all, const int *__restrict__ cr_all, const int *__restrict__ cnr_all,
            int Dcap, int P, double ke, const double *__restrict__ part, double *__restrict__ rho_all,
-           ModeCoef *__restrict__ coef_all, double *__restrict__ lr_out)
+           ModeCoef *__restrict__ coef_all, double *__restrict__ est)
 {
-    __shared__ double red[7 * (kEstThreads + 1) + 28];
-    __shared__ double sums[7];
-    const int s = blockIdx.x;
-    DevSys &d = sys[s];
+    __shared__ double2 sh[kEstWarps][kEstModes];
+    const int s = blockIdx.x, g = blockIdx.y, w = threadIdx.x >> 5, lane = lane_id();
+    const DevSys &d = sys[s];
+    const int nD = d.nD, k = g * kEstModes + lane;
     // chunks holding atoms of the system (its slot may have more)
-    const int nD = d.nD, c0 = first_chunk[s], nc = min(nchunk_sys[s], (live_n(d) + kChunk - 1) / kChunk);
-    const int *D = D_all + (size_t)s * Dcap * 3, *cr = cr_all + (size_t)s * Dcap, *cnr = cnr_all + (size_t)s * Dcap;
-    double *rho = rho_all + (size_t)s * Dcap * 2;
-    ModeCoef *coef = coef_all + (size_t)s * Dcap;
-    const double V = d.L[0] * d.L[1] * d.L[2];
-    double ar = 0.0, b[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = threadIdx.x; k < nD; k += blockDim.x) {
-        double re = 0.0, im = 0.0;
+    const int c0 = first_chunk[s], nc = min(nchunk_sys[s], (live_n(d) + kChunk - 1) / kChunk);
+    const int cb = (int)((long long)nc * w / kEstWarps), ce = (int)((long long)nc * (w + 1) / kEstWarps);
+    double re = 0.0, im = 0.0;
+    if (k < nD) {
         const double2 *pk = reinterpret_cast<const double2 *>(part) + (size_t)c0 * Dcap + k;
-        int c = 0;
-        for (; c + 8 <= nc; c += 8) {          // loads issued together, sums in chunk order
-            double2 t[8];
+        int c = cb;
+        for (; c + 4 <= ce; c += 4) {          // loads issued together, sums in chunk order
+            double2 t[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = pk[(size_t)(c + u) * Dcap];
+            for (int u = 0; u < 4; ++u) t[u] = pk[(size_t)(c + u) * Dcap];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) { re += t[u].x; im += t[u].y; }
+            for (int u = 0; u < 4; ++u) { re += t[u].x; im += t[u].y; }
         }
-        for (; c < nc; ++c) { const double2 t = pk[(size_t)c * Dcap]; re += t.x; im += t.y; }
+        for (; c < ce; ++c) { const double2 t = pk[(size_t)c * Dcap]; re += t.x; im += t.y; }
+    }
+    sh[w][lane] = make_double2(re, im);
+    __syncthreads();
+    if (w != 0) return;
+    double il = 0.0;                           // lane a < 3: 1 / L_a
+    if (lane < 3) il = 1.0 / d.L[lane];
+    const double ilx = __shfl_sync(0xffffffffu, il, 0), ily = __shfl_sync(0xffffffffu, il, 1),
+                 ilz = __shfl_sync(0xffffffffu, il, 2);
+    const double iV = ilx * ily * ilz;
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (k < nD) {
+        re = sh[0][lane].x;
+        im = sh[0][lane].y;
+#pragma unroll
+        for (int u = 1; u < kEstWarps; ++u) { re += sh[u][lane].x; im += sh[u][lane].y; }
+        double *rho = rho_all + (size_t)s * Dcap * 2;
         rho[2 * k] = re;
         rho[2 * k + 1] = im;
-        double kv[3];
-        for (int a = 0; a < 3; ++a) kv[a] = kTwoPi * D[3 * k + a] / d.L[a];
-        double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
-        double r2 = re * re + im * im;
-        ar += cr[k] * r2 / k2;
-        double g = cnr[k] * r2 / (k2 * k2);
-        b[0] += g * kv[0] * kv[0]; b[1] += g * kv[1] * kv[1]; b[2] += g * kv[2] * kv[2];
-        b[3] += g * kv[0] * kv[1]; b[4] += g * kv[0] * kv[2]; b[5] += g * kv[1] * kv[2];
-        double alpha = -ke * (0.5 * d.Sr) / P * cr[k] / (V * k2);
+        const int *D = D_all + ((size_t)s * Dcap + k) * 3;
+        const int m0 = D[0], m1 = D[1], m2 = D[2];
+        const double kx = kTwoPi * m0 * ilx, ky = kTwoPi * m1 * ily, kz = kTwoPi * m2 * ilz;
+        const double ik2 = 1.0 / (kx * kx + ky * ky + kz * kz);
+        const double r2 = re * re + im * im;
+        const double cr = cr_all[(size_t)s * Dcap + k], cnr = cnr_all[(size_t)s * Dcap + k];
+        v[0] = cr * r2 * ik2;
+        const double gg = cnr * r2 * ik2 * ik2;
+        v[1] = gg * kx * kx; v[2] = gg * ky * ky; v[3] = gg * kz * kz;
+        v[4] = gg * kx * ky; v[5] = gg * kx * kz; v[6] = gg * ky * kz;
+        const double alpha = -ke * (0.5 * d.Sr) / P * iV * cr * ik2;
         ModeCoef mc;
-        mc.a[0] = alpha * kv[0]; mc.a[1] = alpha * kv[1]; mc.a[2] = alpha * kv[2];
+        mc.a[0] = alpha * kx; mc.a[1] = alpha * ky; mc.a[2] = alpha * kz;
         mc.re = re; mc.im = im;
-        mc.m[0] = D[3 * k]; mc.m[1] = D[3 * k + 1]; mc.m[2] = D[3 * k + 2];
+        mc.m[0] = m0; mc.m[1] = m1; mc.m[2] = m2;
         mc.pad = 0;
-        coef[k] = mc;
+        coef_all[(size_t)s * Dcap + k] = mc;
     }
-    const double v7[7] = {ar, b[0], b[1], b[2], b[3], b[4], b[5]};
-    block_reduce_lanes<7, kEstThreads>(v7, red, sums);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double *o = lr_out + (size_t)s * 16;
-        o[0] = ke * d.Sr / (4.0 * V * P) * sums[0];
-        o[1] = o[0];
-        for (int a = 0; a < 6; ++a) o[2 + a] = -ke * d.Snr / (8.0 * V * P) * sums[1 + a];
-        o[8] = d.Sr;
-        o[9] = d.Snr;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) v[t] = warp_sum(v[t]);
+    if (lane < 7) {
+        double x = v[0];
+#pragma unroll
+        for (int t = 1; t < 7; ++t)
+            if (lane == t) x = v[t];
+        est[((size_t)s * gridDim.y + g) * 7 + lane] = x;
     }
 }
 
 void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_sys, const int *D,
                      const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
-                     double *rho, ModeCoef *coef, double *lr_out, cudaStream_t st)
+                     double *rho, ModeCoef *coef, double *est, cudaStream_t st)
 {
-    k_estimate<<<b.S, kEstThreads, 0, st>>>(b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho,
-                                    coef, lr_out);
+    k_estimate<<<dim3(b.S, estimate_blocks(Dcap)), 32 * kEstWarps, 0, st>>>(
+        b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho, coef, est);
 }
 
 // Force assembly: F_i = sum over the pair kernel's dz-plane partials (fixed

@@ -131,7 +131,7 @@ __device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float
     const float qq = pc.ke * qi * qj.x;
     const float fc = qq * (r2inv * rinv - st);
     const int tj = __float_as_int(qj.y);
-    const float2 lab = __ldg(&ljrow[tj]);
+    const float2 lab = ljrow[tj];                        // shared memory
     const float r6inv = r2inv * r2inv * r2inv;
     const float fl = (12.f * lab.x * r6inv - 6.f * lab.y) * r6inv * r2inv;
     const float f = fc + fl;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float
         }
         kahan_add(acc.uc, acc.cuc, qq * (rinv - se));
         kahan_add(acc.uq, acc.cuq, qq);
-        const float2 lo = __ldg(&ljlo[tj]);
+        const float2 lo = ljlo[tj];
         kahan_add(acc.ul, acc.cul, (fmaf(lab.x, r6inv, -lab.y) + fmaf(lo.x, r6inv, -lo.y)) * r6inv);
         const float cx = fc * dx, cy = fc * dy, lx = fl * dx, ly = fl * dy;
         acc.wc[0] = fmaf(cx, dx, acc.wc[0]); acc.wc[1] = fmaf(cy, dy, acc.wc[1]);
@@ -200,6 +200,27 @@ __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, doub
     acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
 }
 
+// Next (base, mask) entry of one lane's hit stream: plane pl, chunk cur,
+// position pos, rem entries left in plane pl; moves to the next plane's list
+// when this one is used up.  The caller asks only for entries that exist.
+__device__ __forceinline__ uint2 next_entry(const PairList &L, size_t u0i, int &pl, int &rem, int &cur, int &pos)
+{
+    while (rem == 0) {
+        ++pl;
+        rem = L.nent[u0i + (size_t)pl * 32];
+        cur = L.head[u0i + (size_t)pl * 32];
+        pos = 0;
+    }
+    const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
+    ++pos;
+    --rem;
+    if (pos == kListChunk && rem > 0) {
+        cur = L.next[cur];
+        pos = 0;
+    }
+    return en;
+}
+
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
 }  // namespace
@@ -227,6 +248,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
              PairList L, const float rc2_hi)
 {
     __shared__ float2 offp[kMaxPlane];
+    __shared__ float4 cand[32];
     const int lane = lane_id();
     const int span = 2 * sub + 1;
     const int unit = blockIdx.x;
@@ -248,67 +270,103 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     const int ni = min(32, count[gc] - 32 * item.y);
     const bool vi = lane < ni;
     // lanes without an atom sit far away: their cutoff test never passes
-    float4 pi = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-0x7fffffff));
+    float4 pi = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     if (vi) pi = pos4[i0 + lane];
-    const int moli = __float_as_int(pi.w);
     int cur = -1, fill = kListChunk, first = -1, nent = 0, nhit = 0;
     bool overflow = false;
     const int gz = wrapi(cz + ddz, n2);
-    for (int nb = 0; nb < span * span; ++nb) {
-        const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
-        const int j0 = start[g], nj = count[g];
-        const float2 o = offp[nb];
-        const float xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - ozh;
-        const unsigned code = (unsigned)(part * span * span + nb) << 25;
-        for (int jb = 0; jb < nj; jb += 32) {
-            const float4 *pc4 = pos4 + j0 + jb;
-            unsigned hm = 0;                           // hits among these 32 candidates
-            if (nj - jb >= 32) {
+    // the plane's cells, one per lane: first atom and atom count
+    const int nn = span * span;
+    int cj0 = 0, cnj = 0;
+    if (lane < nn) {
+        const int g = d.cell0 + wrapi(cx + lane % span - sub, n0) + n0 * (wrapi(cy + lane / span - sub, n1) + n1 * gz);
+        cj0 = start[g];
+        cnj = count[g];
+    }
+    // candidates in batches of 32 (one cell at a time), each batch loaded by
+    // the whole warp with one coalesced load, one batch ahead, and tested by
+    // every lane from shared memory.  The test uses the expanded form
+    // |a - b|^2 = |a|^2 + |b|^2 - 2 a.b with a, b relative to the candidate
+    // cell's centre: the loading lane stores (-2 b, |b|^2), so a candidate
+    // costs three FMAs and a compare.  Its rounding error (below 2e-4 A^2 for
+    // the coordinates that occur near r_c) is far inside the margin of rc2_hi,
+    // and the evaluation decides every pair exactly.  A short batch is padded
+    // with entries no lane can hit; pairs of one molecule pass this test and
+    // are dropped by the evaluation (a few per atom at most).
+    const float hx = 0.5f * (float)d.w[0], hy = 0.5f * (float)d.w[1], hz = 0.5f * (float)d.w[2];
+    const float4 far = make_float4(0.f, 0.f, 0.f, 1e30f);
+    auto stage = [&](float4 q) {
+        const float bx = q.x - hx, by = q.y - hy, bz = q.z - hz;
+        return make_float4(-2.f * bx, -2.f * by, -2.f * bz, fmaf(bx, bx, fmaf(by, by, bz * bz)));
+    };
+    int nb = 0, jb = 0, j0 = 0, nj = 0;
+    for (;;) {                                         // first non-empty cell (warp-uniform)
+        if (nb >= nn) break;
+        nj = __shfl_sync(0xffffffffu, cnj, nb);
+        if (nj > 0) break;
+        ++nb;
+    }
+    float4 nxt = far;
+    if (nb < nn) {
+        j0 = __shfl_sync(0xffffffffu, cj0, nb);
+        if (lane < nj) nxt = stage(__ldg(pos4 + j0 + lane));
+    }
+    // this lane's atom relative to the centre of neighbour cell nb is pc - offp[nb]
+    const float pcx = pi.x - hx, pcy = pi.y - hy, pcz = pi.z - hz;
+    while (nb < nn) {
+        const int bnb = nb, bj = j0 + jb;
+        cand[lane] = nxt;
+        // advance to the next batch and start its load
+        jb += 32;
+        if (jb >= nj) {
+            jb = 0;
+            for (;;) {
+                if (++nb >= nn) break;
+                nj = __shfl_sync(0xffffffffu, cnj, nb);
+                if (nj > 0) break;
+            }
+            if (nb < nn) j0 = __shfl_sync(0xffffffffu, cj0, nb);
+        }
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ld = nb < nn && jb + lane < nj;
+        if (ld) qn = __ldg(pos4 + j0 + jb + lane);
+        __syncwarp();
+        const float2 o = offp[bnb];
+        const float ax = pcx - o.x, ay = pcy - o.y, az = pcz - ozh;
+        const float thr = rc2_hi - fmaf(ax, ax, fmaf(ay, ay, az * az));
+        unsigned hm = 0;                               // hits among these 32 candidates
 #pragma unroll
-                for (int ub = 0; ub < 32; ub += 8) {
-                    float4 q[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) q[u] = __ldg(pc4 + ub + u);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float dx = xi - q[u].x, dy = yi - q[u].y, dz = zi - q[u].z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rc2_hi && __float_as_int(q[u].w) != moli) hm |= 1u << (ub + u);
-                    }
-                }
-            } else {
-                for (int u = 0; u < nj - jb; ++u) {
-                    const float4 pj = __ldg(pc4 + u);
-                    const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < rc2_hi && __float_as_int(pj.w) != moli) hm |= 1u << u;
+        for (int u = 0; u < 32; ++u) {
+            const float4 c = cand[u];
+            if (fmaf(ax, c.x, fmaf(ay, c.y, fmaf(az, c.z, c.w))) < thr) hm |= 1u << u;
+        }
+        nxt = ld ? stage(qn) : far;
+        __syncwarp();                                  // cand is rewritten next round
+        const unsigned code = (unsigned)(part * nn + bnb) << 25;
+        // lanes whose chunk is full and that have an entry to store take new chunks together
+        const unsigned need = __ballot_sync(0xffffffffu, hm != 0u && fill == kListChunk);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            int b0 = 0;
+            if (lane == leader) b0 = atomicAdd(L.top, __popc(need));
+            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            if (hm != 0u && fill == kListChunk) {
+                const int c = b0 + __popc(need & ((1u << lane) - 1u));
+                if (c < L.cap_chunks) {
+                    if (cur >= 0) L.next[cur] = c;
+                    else first = c;
+                    cur = c;
+                    fill = 0;
+                } else {
+                    overflow = true;
                 }
             }
-            // lanes whose chunk is full and that have an entry to store take new chunks together
-            const unsigned need = __ballot_sync(0xffffffffu, hm != 0u && fill == kListChunk);
-            if (need) {
-                const int leader = __ffs(need) - 1;
-                int b0 = 0;
-                if (lane == leader) b0 = atomicAdd(L.top, __popc(need));
-                b0 = __shfl_sync(0xffffffffu, b0, leader);
-                if (hm != 0u && fill == kListChunk) {
-                    const int c = b0 + __popc(need & ((1u << lane) - 1u));
-                    if (c < L.cap_chunks) {
-                        if (cur >= 0) L.next[cur] = c;
-                        else first = c;
-                        cur = c;
-                        fill = 0;
-                    } else {
-                        overflow = true;
-                    }
-                }
-            }
-            if (hm != 0u && fill < kListChunk) {
-                L.ent[(size_t)cur * kListChunk + fill] = make_uint2((unsigned)(j0 + jb) | code, hm);
-                ++fill;
-                ++nent;
-                nhit += __popc(hm);
-            }
+        }
+        if (hm != 0u && fill < kListChunk) {
+            L.ent[(size_t)cur * kListChunk + fill] = make_uint2((unsigned)bj | code, hm);
+            ++fill;
+            ++nent;
+            nhit += __popc(hm);
         }
     }
     if (vi) {
@@ -321,7 +379,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
 }
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32, 24)
+__global__ void __launch_bounds__(32, EN ? 20 : 28)
 k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
             const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4,
             const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
@@ -329,6 +387,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
             float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
 {
     __shared__ float4 offh[kMaxNb], offl[kMaxNb];
+    __shared__ float2 ljs[EN ? 2 : 1][kMaxTypes * kMaxTypes];   // the system's LJ table (and remainders)
     const int lane = lane_id();
     const int span = 2 * sub + 1;
     const int it = blockIdx.x / kEvalSplit, seg = blockIdx.x % kEvalSplit;
@@ -348,6 +407,10 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
             const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
             offh[nb] = make_float4(hx, hy, hz, 0.f);
             offl[nb] = make_float4((float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
+        }
+        for (int t = lane; t < d.ntypes * d.ntypes; t += 32) {
+            ljs[0][t] = lj[d.lj0 + t];
+            if (EN) ljs[EN ? 1 : 0][t] = ljlo[d.lj0 + t];
         }
         __syncwarp();
         const int i0 = start[gc] + 32 * item.y;
@@ -389,44 +452,60 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
                 }
             }
         }
-        const int rowi = d.lj0 + __float_as_int(pq.y) * d.ntypes;
-        const float2 *ljrow = lj + rowi, *ljlorow = ljlo + rowi;
+        const int rowi = __float_as_int(pq.y) * d.ntypes;
+        const float2 *ljrow = ljs[0] + rowi, *ljlorow = ljs[EN ? 1 : 0] + rowi;
         AccF acc;
         acc.fx = acc.fy = acc.fz = 0.f;
         acc.uc = acc.ul = acc.uq = acc.cuc = acc.cul = acc.cuq = 0.f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc.w[k] = acc.wc[k] = acc.wl[k] = 0.f;
+        // one hit ahead: the next hit's atom data, and the next list entry once
+        // the current one has started, are loaded while this hit is evaluated
+        int left = nh;                                 // hits of this lane still to evaluate
+        if (left > 0 && mask == 0u) {
+            const uint2 en = next_entry(L, u0i, pl, rem, cur, pos);
+            base = en.x;
+            mask = en.y;
+        }
+        uint2 nxt = make_uint2(0u, 0u);
+        if (left > __popc(mask)) nxt = next_entry(L, u0i, pl, rem, cur, pos);
+        unsigned e = 0u;
+        float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 qj = make_float2(0.f, 0.f);
+        if (left > 0) {
+            e = base + (unsigned)(__ffs(mask) - 1);
+            mask &= mask - 1u;
+            pj = pos4[e & 0x1ffffffu];
+            qj = qt[e & 0x1ffffffu];
+        }
         const int tmax = __reduce_max_sync(0xffffffffu, nh);
         for (int k = 0; k < tmax; ++k) {
             if (k < nh) {
-                while (mask == 0u) {                   // next (base, mask) entry of this lane
-                    while (rem == 0) {                 // next plane's list
-                        ++pl;
-                        rem = L.nent[u0i + (size_t)pl * 32];
-                        cur = L.head[u0i + (size_t)pl * 32];
-                        pos = 0;
+                const unsigned ec = e;
+                const float4 pjc = pj;
+                const float2 qjc = qj;
+                if (--left > 0) {
+                    if (mask == 0u) {
+                        base = nxt.x;
+                        mask = nxt.y;
+                        if (left > __popc(mask)) nxt = next_entry(L, u0i, pl, rem, cur, pos);
                     }
-                    const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
-                    base = en.x;
-                    mask = en.y;
-                    ++pos;
-                    --rem;
-                    if (pos == kListChunk && rem > 0) { cur = L.next[cur]; pos = 0; }
+                    e = base + (unsigned)(__ffs(mask) - 1);
+                    mask &= mask - 1u;
+                    pj = pos4[e & 0x1ffffffu];
+                    qj = qt[e & 0x1ffffffu];
                 }
-                const unsigned e = base + (unsigned)(__ffs(mask) - 1);
-                mask &= mask - 1u;
-                const unsigned j = e & 0x1ffffffu;
-                const float4 pj = pos4[j];
-                const float2 qj = qt[j];
-                const float4 oh = offh[e >> 25], ol = offl[e >> 25];
-                const float dx = ((pi.x - oh.x) - pj.x) - ol.x, dy = ((pi.y - oh.y) - pj.y) - ol.y,
-                            dz = ((pi.z - oh.z) - pj.z) - ol.z;
+                const float4 oh = offh[ec >> 25], ol = offl[ec >> 25];
+                const float dx = ((pi.x - oh.x) - pjc.x) - ol.x, dy = ((pi.y - oh.y) - pjc.y) - ol.y,
+                            dz = ((pi.z - oh.z) - pjc.z) - ol.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 // pairs within a relative 1e-5 of r_c^2 are decided in FP64 from the
                 // original positions (the energy kernel N is about 2e-3 / A at r_c,
                 // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
-                if (r2 < pc.rc2_lo || inside_cutoff_fp64(r, sidx[i0 + lane], sidx[j], d.L, pc.rc2d))
-                    pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qj, acc);
+                if (__float_as_int(pjc.w) != __float_as_int(pi.w) &&   // not of one molecule
+                    (r2 < pc.rc2_lo ||
+                     inside_cutoff_fp64(r, sidx[i0 + lane], sidx[ec & 0x1ffffffu], d.L, pc.rc2d)))
+                    pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qjc, acc);
             }
         }
         if (vi) Fpart[(size_t)seg * N + i0 + lane] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);

@@ -82,7 +82,7 @@ struct rbsog_ctx {
     int *mchunk_sys = nullptr, *mchunk_m0 = nullptr, *mchunk_n = nullptr, *mchunk_first = nullptr, *mchunk_count = nullptr;
     int *b_start = nullptr, *a_start = nullptr, *e_start = nullptr, *bonds = nullptr, *angles = nullptr, *excl = nullptr;
     double *bk = nullptr, *br0 = nullptr, *ak = nullptr, *at0 = nullptr;
-    double *pair_part = nullptr, *lr_out = nullptr, *mol_part = nullptr, *kin_part = nullptr, *sysred = nullptr;
+    double *pair_part = nullptr, *est = nullptr, *mol_part = nullptr, *kin_part = nullptr, *sysred = nullptr;
     double *self_e = nullptr;
     double4 *fpart = nullptr;   // pair forces per dz plane (FP32 build reads it as float4)
     double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
@@ -223,7 +223,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     launch_sk(c->b, c->a, prec, c->D, c->Dcap, c->sk_part, c->st);
     record(c, "structure_factor");
     launch_estimate(c->b, c->first_chunk, c->nchunk_sys, c->D, c->cr, c->cnr, c->Dcap, c->prm.P, c->prm.ke,
-                    c->sk_part, c->rho, c->coef, c->lr_out, c->st);
+                    c->sk_part, c->rho, c->coef, c->est, c->st);
     record(c, "estimate");
     launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, c->st);
     record(c, "lr_force");
@@ -232,7 +232,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
     record(c, "kick_kinetic");
     launch_reduce_pair(c->b, prec == 1 ? kEvalSplit : 2 * c->prm.cell_sub + 1, c->pair_part, c->pair_red, c->st);
-    launch_finalize(c->b, c->pair_red, c->lr_out, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
+    launch_finalize(c->b, c->pair_red, c->est, estimate_blocks(c->Dcap), c->prm.P, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
     record(c, "finalize");
 }
@@ -741,7 +741,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   dalloc(c, c->pair_part, (size_t)item_cap * std::max(2 * P.cell_sub + 1, kEvalSplit) * kPairRec) &&
                   dalloc(c, c->fpart, (size_t)N * std::max(2 * P.cell_sub + 1, kEvalSplit)) &&
                   dalloc(c, c->pair_red, (size_t)S * kPairRedBlocks * kPairRec) &&
-                  dalloc(c, c->lr_out, (size_t)S * 16) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
+                  dalloc(c, c->est, (size_t)S * estimate_blocks(c->Dcap) * 7) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
                   dalloc(c, c->mr, (size_t)S * P.P * 3) && dalloc(c, c->mnr, (size_t)S * P.P * 3) &&
                   dalloc(c, c->D, (size_t)S * c->Dcap * 3) && dalloc(c, c->cr, (size_t)S * c->Dcap) &&
@@ -844,6 +844,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->ia.dt = P.dt; c->ia.T = P.T; c->ia.Pext = P.P_ext; c->ia.gamma = P.gamma; c->ia.gamma_box = P.gamma_box;
         c->ia.kB = kKB; c->ia.ftm2v = kFtm2v; c->ia.nktv2p = kNktv2p; c->ia.seed = P.seed; 
         c->ia.c_atom = std::exp(-P.gamma * P.dt);
+        c->ia.c_box = std::exp(-P.gamma_box * P.dt);
+        c->ia.ke = P.ke;
         c->ia.inv_m = c->inv_m; c->ia.sdv = c->sdv;
         c->ia.noise_f32 = P.precision == RBSOG_FP32 ? 1 : 0;
 
