@@ -58,6 +58,7 @@ struct Batch {
     const int *chunk_sys, *chunk_a0, *chunk_n;   // atom chunks
     int nchunks;
     int item_cap;               // pair work items, all systems
+    const int *item_sys;        // [item_cap] system of each work item index
 };
 
 // FP32 pair lists: per (work unit = group x dz plane, lane) a chain of
@@ -89,6 +90,8 @@ struct AtomArrays {
     double4 *posd;              // [N] sorted, FP64
     int2 *aux;                  // [N] sorted (mol, type)
     int2 *items;                // [item_cap] (cell, group) pair work items
+    int *citem0;                // [C] first work item of each cell
+    int *scell;                 // [N] cell of each cell-sorted atom (FP32 build)
     float4 *fpart4;             // [(2 sub + 1) N] pair forces per dz plane, cell-sorted (FP32 build)
     double4 *fpartd;            // same storage, FP64 build
     // LJ table: system s owns entries [lj0, lj0 + ntypes^2) (DevSys), entry
@@ -127,10 +130,17 @@ struct SamplerArgs {
     double cr[kMaxGauss], cn[kMaxGauss], st2q[kMaxGauss];
     double sig_u;
 };
+// per-system sampler scratch: 1D lattice sums T0, T2, T4 per Gaussian and
+// axis, and the chain's start state (paper MH sampler)
+struct SampScratch {
+    double T[3][kMaxGauss][3];
+    double start_w, start_g;
+    int start_m[4];
+};
 // adv = 1: the evaluation of an NPT step (counter DevSys::step + 1); 0: re-evaluate at DevSys::step
 void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int *mnr, int *D, int *cr,
-                    int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, int Dcap,
-                    cudaStream_t st);
+                    int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, SampScratch *ss,
+                    int Dcap, cudaStream_t st);
 
 // ---- k_kspace.cu
 void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
@@ -140,8 +150,9 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
                      double *rho, ModeCoef *coef, double *est, cudaStream_t st);
 // mode groups of k_estimate: est holds S x estimate_blocks(Dcap) x 7 partial sums
 int estimate_blocks(int Dcap);
+// F = pair partials + long-range force + Fmol (molecule terms; null: none)
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
-                     int Dcap, cudaStream_t st);
+                     int Dcap, const double *Fmol, cudaStream_t st);
 size_t sk_stateless_workspace(int n, int nD);
 // k_sk_static.cu: a fixed scratch for the allocation-free variant
 constexpr size_t kSkStaticBytes = (size_t)4 << 20;
@@ -161,7 +172,8 @@ struct MolArrays {
     const int *mchunk_sys, *mchunk_m0, *mchunk_n;
     int nmchunks;
 };
-void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc,
+// Fmol: per-atom forces of the molecule terms, added to (zeroed by the caller)
+void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc, double *Fmol,
                 double *partial /* per mol chunk: Ue, Ub, Ua, W[6] excl, W[6] bonded */, int precision,
                 cudaStream_t st);
 

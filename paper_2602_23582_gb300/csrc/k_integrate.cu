@@ -47,52 +47,78 @@ __device__ void box_force(const DevSys &d, const double *red, const IntegArgs &i
 
 }  // namespace
 
-// Box part of B (first half), A, O, A.  One thread per system.
-__global__ void k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred)
+// Box part of B (first half), A, O, A.  One warp per system: lane a < 3
+// works on axis a and lane g < ng on box group g, so the FP64 chains of the
+// three axes (divisions, the Gaussian of each group) run side by side.  Each
+// value is formed by the same operations as in a one-thread loop over axes.
+constexpr int kBoxWarps = 4;
+
+__global__ void __launch_bounds__(32 * kBoxWarps)
+k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * kBoxWarps + (threadIdx.x >> 5), lane = lane_id();
     if (s >= S) return;
     DevSys &d = sys[s];
-    if (live_n(d) == 0) return;               // empty or finished slot
+    if (live_n(d) == 0) return;               // empty or finished slot (warp-uniform)
     const double *red = sysred + (size_t)s * kRed;
-    double G[3];
-    box_force(d, red, ia, G);
     const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
-    for (int g = 0; g < ng; ++g)
-        if (d.Mbox[g] > 0.0) d.ph[g] += 0.5 * ia.dt * G[g] * ia.ftm2v;
-    const double tau = 0.5 * ia.dt;
-    for (int a = 0; a < 3; ++a) {
-        int g = axis_group(d.coupling, a);
-        double v = d.Mbox[g] > 0.0 ? d.ph[g] / d.Mbox[g] : 0.0;
-        d.Lp[a] = d.L[a];
-        d.Lh[a] = d.L[a] + v * tau;
+    const int ax = lane < 3 ? lane : 0;
+    const int g_of = axis_group(d.coupling, ax);            // this lane's axis -> its group
+    const double La = d.L[ax];
+    // generalised box force (box_force): the axis terms added per group in axis order
+    double term = 0.0;
+    {
+        const double V = d.L[0] * d.L[1] * d.L[2];
+        const double pext = ia.Pext / ia.nktv2p;
+        term = (red[45 + ax] + red[9 + ax] - pext * V - ia.kB * ia.T) / La;
     }
+    const double t0 = __shfl_sync(0xffffffffu, term, 0), t1 = __shfl_sync(0xffffffffu, term, 1),
+                 t2 = __shfl_sync(0xffffffffu, term, 2);
+    const int gg = lane < 3 ? lane : 0;                     // this lane's group
+    double G = 0.0;
+    if (axis_group(d.coupling, 0) == gg) G += t0;
+    if (axis_group(d.coupling, 1) == gg) G += t1;
+    if (axis_group(d.coupling, 2) == gg) G += t2;
+    const double Mb = d.Mbox[gg];
+    double ph = d.ph[gg];
+    if (gg < ng && Mb > 0.0) ph += 0.5 * ia.dt * G * ia.ftm2v;
+    const double tau = 0.5 * ia.dt;
+    // A: the axis velocity from its group's momentum
+    const double phg = __shfl_sync(0xffffffffu, ph, g_of), Mg = __shfl_sync(0xffffffffu, Mb, g_of);
+    const double v1 = Mg > 0.0 ? phg / Mg : 0.0;
+    const double Lp = La, Lh = La + v1 * tau;
+    // O: the Gaussian of group g is z[g] of one Box-Muller draw pair per two groups
     uint64_t wds[4];
     draw4(ia.seed, d.rng_id, d.step + 1, PUR_BOX, 0, wds);
-    double z[4];
-    box_muller2(wds[0], wds[1], z[0], z[1]);
-    box_muller2(wds[2], wds[3], z[2], z[3]);
-    const double ch = ia.c_box;
-    for (int g = 0; g < ng; ++g) {
-        if (d.Mbox[g] <= 0.0) continue;
-        double sdv = sqrt((1.0 - ch * ch) * d.Mbox[g] * ia.kB * ia.T * ia.ftm2v);
-        d.ph[g] = ch * d.ph[g] + sdv * z[g];
+    if (gg < ng && Mb > 0.0) {
+        const uint64_t wa = gg < 2 ? wds[0] : wds[2], wb = gg < 2 ? wds[1] : wds[3];
+        const double rr = sqrt(-2.0 * log(u01(wa)));
+        const double ang = kTwoPi * u01(wb);
+        const double z = rr * (gg == 1 ? sin(ang) : cos(ang));
+        const double ch = ia.c_box;
+        const double sdv = sqrt((1.0 - ch * ch) * Mb * ia.kB * ia.T * ia.ftm2v);
+        ph = ch * ph + sdv * z;
     }
-    for (int a = 0; a < 3; ++a) {
-        int g = axis_group(d.coupling, a);
-        double v = d.Mbox[g] > 0.0 ? d.ph[g] / d.Mbox[g] : 0.0;
-        d.L[a] = d.Lh[a] + v * tau;
-        d.sc1[a] = d.Lh[a] / d.Lp[a];
-        d.sc2[a] = d.L[a] / d.Lh[a];
-        d.isc1[a] = d.Lp[a] / d.Lh[a];
-        d.isc2[a] = d.Lh[a] / d.L[a];
-        d.invL[a] = 1.0 / d.L[a];
+    // A: second half drift with the new momentum
+    const double phn = __shfl_sync(0xffffffffu, ph, g_of);
+    const double v2 = Mg > 0.0 ? phn / Mg : 0.0;
+    const double Ln = Lh + v2 * tau;
+    if (lane < ng) d.ph[lane] = ph;
+    if (lane < 3) {
+        d.Lp[lane] = Lp;
+        d.Lh[lane] = Lh;
+        d.L[lane] = Ln;
+        d.sc1[lane] = Lh / Lp;
+        d.sc2[lane] = Ln / Lh;
+        d.isc1[lane] = Lp / Lh;
+        d.isc2[lane] = Lh / Ln;
+        d.invL[lane] = 1.0 / Ln;
     }
 }
 
 void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st)
 {
-    k_box_half<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, ia, sysred);
+    k_box_half<<<(b.S + kBoxWarps - 1) / kBoxWarps, 32 * kBoxWarps, 0, st>>>(b.sys, b.S, ia, sysred);
 }
 
 // Atom part of B (first half), A, O, A and the wrap.  Per-system drift

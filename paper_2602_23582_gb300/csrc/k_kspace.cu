@@ -226,9 +226,9 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
         b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho, coef, est);
 }
 
-// Force assembly: F_i = sum over the pair kernel's dz-plane partials (fixed
-// order) + q_i sum_d alpha_d k_d Im(e^{-i k_d.r_i} rho_d) (eq. f_approx).
-// Molecule terms are added afterwards by k_mol.  Blocks of kLrAtoms atoms of
+// Force assembly: F_i = sum over the pair kernel's partials (fixed order)
+// + q_i sum_d alpha_d k_d Im(e^{-i k_d.r_i} rho_d) (eq. f_approx) + the
+// molecule terms of k_mol.  Blocks of kLrAtoms atoms of
 // one chunk (grid: chunks x kChunk / kLrAtoms); the system's mode
 // coefficients are staged in shared memory in tiles.
 constexpr int kModeTile = 256;
@@ -240,7 +240,7 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
            const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
            const double *__restrict__ q, const ModeCoef *__restrict__ coef_all, int Dcap,
            const int *__restrict__ pos_sorted, const void *__restrict__ fpart, int nparts, int N,
-           double *__restrict__ F)
+           const double *__restrict__ Fmol, double *__restrict__ F)
 {
     __shared__ float4 tf[F32 ? kModeTile : 1];      // a (FP32)
     __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
@@ -316,27 +316,35 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
         }
     }
     if (F32) {
-        F[3 * i] = f[0] + qi * (double)fx;
-        F[3 * i + 1] = f[1] + qi * (double)fy;
-        F[3 * i + 2] = f[2] + qi * (double)fz;
+        f[0] += qi * (double)fx;
+        f[1] += qi * (double)fy;
+        f[2] += qi * (double)fz;
     } else {
-        F[3 * i] = f[0] + qi * gx;
-        F[3 * i + 1] = f[1] + qi * gy;
-        F[3 * i + 2] = f[2] + qi * gz;
+        f[0] += qi * gx;
+        f[1] += qi * gy;
+        f[2] += qi * gz;
     }
+    if (Fmol) {
+        f[0] += Fmol[3 * i];
+        f[1] += Fmol[3 * i + 1];
+        f[2] += Fmol[3 * i + 2];
+    }
+    F[3 * i] = f[0];
+    F[3 * i + 1] = f[1];
+    F[3 * i + 2] = f[2];
 }
 
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
-                     cudaStream_t st)
+                     const double *Fmol, cudaStream_t st)
 {
     const dim3 grid(b.nchunks, kChunk / kLrAtoms);
     const int nparts = precision == 1 ? kEvalSplit : 2 * b.sub + 1;   // FP32: hit segments; FP64: dz planes
     if (precision == 1)
         k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                    coef, Dcap, a.rank, a.fpart4, nparts, b.N, a.F);
+                                                    coef, Dcap, a.rank, a.fpart4, nparts, b.N, Fmol, a.F);
     else
         k_lr_force<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                     coef, Dcap, a.rank, a.fpartd, nparts, b.N, a.F);
+                                                     coef, Dcap, a.rank, a.fpartd, nparts, b.N, Fmol, a.F);
 }
 
 // ---------------------------------------------------------------------------

@@ -39,7 +39,8 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
       const int *__restrict__ e_start, const int *__restrict__ bonds, const double *__restrict__ bk,
       const double *__restrict__ br0, const int *__restrict__ angles, const double *__restrict__ ak,
       const double *__restrict__ at0, const int *__restrict__ excl, const double *__restrict__ r,
-      const double *__restrict__ q, double *__restrict__ F, double *__restrict__ partial, const SogConsts sc)
+      const double *__restrict__ q, double *__restrict__ F /* molecule-term forces */, double *__restrict__ partial,
+      const SogConsts sc)
 {
     __shared__ double red[15 * (kMolChunk + 1) + 60];
     const int c = blockIdx.x;
@@ -144,18 +145,18 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     block_reduce_lanes<15, kMolChunk>(v, red, partial + (size_t)c * 15);
 }
 
-void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc,
+void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc, double *Fmol,
                 double *partial, int precision, cudaStream_t st)
 {
     if (m.nmchunks == 0) return;
     if (precision == 1)
         k_mol<float><<<m.nmchunks, kMolChunk, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
                                                m.a_start, m.e_start, m.bonds, m.bk, m.br0, m.angles, m.ak,
-                                               m.at0, m.excl, a.r, a.q, a.F, partial, sc);
+                                               m.at0, m.excl, a.r, a.q, Fmol, partial, sc);
     else
         k_mol<double><<<m.nmchunks, kMolChunk, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
                                                 m.a_start, m.e_start, m.bonds, m.bk, m.br0, m.angles, m.ak,
-                                                m.at0, m.excl, a.r, a.q, a.F, partial, sc);
+                                                m.at0, m.excl, a.r, a.q, Fmol, partial, sc);
 }
 
 }  // namespace rbsog

@@ -203,12 +203,12 @@ __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, doub
 // Next (base, mask) entry of one lane's hit stream: plane pl, chunk cur,
 // position pos, rem entries left in plane pl; moves to the next plane's list
 // when this one is used up.  The caller asks only for entries that exist.
-__device__ __forceinline__ uint2 next_entry(const PairList &L, size_t u0i, int &pl, int &rem, int &cur, int &pos)
+__device__ __forceinline__ uint2 next_entry(const PairList &L, int u0i, int &pl, int &rem, int &cur, int &pos)
 {
     while (rem == 0) {
         ++pl;
-        rem = L.nent[u0i + (size_t)pl * 32];
-        cur = L.head[u0i + (size_t)pl * 32];
+        rem = L.nent[u0i + pl * 32];
+        cur = L.head[u0i + pl * 32];
         pos = 0;
     }
     const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
@@ -237,10 +237,12 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // chunk at once.  A lane's entries keep its candidate order, so the evaluation
 // order does not depend on which chunks it got.
 //
-// k_pair_eval: work unit = 32-atom group x one of kEvalSplit segments of each
-// atom's hits (all planes in order, split by hit count), one hit per lane and
-// round, so every lane carries about the same number of pairs; segment k
-// writes force partial k, summed in segment order by the force assembly.
+// k_pair_eval: work unit = 32 consecutive cell-sorted atoms of one system
+// (whatever their cells, so the lanes are full) x one of kEvalSplit segments
+// of each atom's hits (all planes in order, split by hit count), one hit per
+// lane and round, so every lane carries about the same number of pairs;
+// segment k writes force partial k, summed in segment order by the force
+// assembly.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32, 32)
 k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
@@ -379,9 +381,9 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
 }
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32, EN ? 20 : 28)
-k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
-            const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4,
+__global__ void __launch_bounds__(32, EN ? 20 : 24)
+k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int *__restrict__ start,
+            const int *__restrict__ scell, const int *__restrict__ citem0, const float4 *__restrict__ pos4,
             const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
             const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N, const PairList L,
             float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
@@ -391,14 +393,15 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
     const int lane = lane_id();
     const int span = 2 * sub + 1;
     const int it = blockIdx.x / kEvalSplit, seg = blockIdx.x % kEvalSplit;
-    const int2 item = items[it];
+    const DevSys &d = sys[item_sys[it]];
+    // evaluation group: 32 consecutive cell-sorted atoms of one system (group
+    // g of the system uses the record slots of its work item item0 + g)
+    const int g32 = 32 * (it - d.item0), nlive = live_n(d);
     double u0 = 0.0, u1 = 0.0;
     float wv[18];                                      // Wc, Wl (energy steps), W
 #pragma unroll
     for (int k = 0; k < 18; ++k) wv[k] = 0.f;
-    if (item.x >= 0) {                                 // warp-uniform
-        const int gc = item.x;
-        const DevSys &d = sys[cell_sys[gc]];
+    if (g32 < nlive) {                                 // warp-uniform
         // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
         // must not shift every cross-cell distance the same way)
         for (int nb = lane; nb < span * span * span; nb += 32) {
@@ -413,18 +416,20 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
             if (EN) ljs[EN ? 1 : 0][t] = ljlo[d.lj0 + t];
         }
         __syncwarp();
-        const int i0 = start[gc] + 32 * item.y;
-        const int ni = min(32, count[gc] - 32 * item.y);
-        const bool vi = lane < ni;
+        const int ks = d.atom0 + g32 + lane;           // this lane's atom (cell-sorted index)
+        const bool vi = g32 + lane < nlive;
         float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 pq = make_float2(0.f, 0.f);
-        const size_t u0i = (size_t)it * span * 32 + lane;   // this lane's list in plane 0
+        int u0i = 0;                                   // this lane's list in plane 0
         // this warp takes hits [h0, h1) of the lane's stream (all planes in order)
         int nh = 0, pl = 0, rem = 0, cur = 0, pos = 0;
         unsigned base = 0u, mask = 0u;
         if (vi) {
-            pi = pos4[i0 + lane];
-            pq = qt[i0 + lane];
+            // the atom's lists belong to work item (its cell, its 32-atom group there)
+            const int c = scell[ks], o = ks - start[c];
+            u0i = (citem0[c] + (o >> 5)) * span * 32 + (o & 31);
+            pi = pos4[ks];
+            pq = qt[ks];
             int tot = 0;
             for (int p2 = 0; p2 < span; ++p2) tot += L.nhit[u0i + (size_t)p2 * 32];
             const int h0 = (int)((long long)tot * seg / kEvalSplit);
@@ -441,9 +446,9 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
                     ++pos;
                     --rem;
                     if (pos == kListChunk && rem > 0) { cur = L.next[cur]; pos = 0; }
-                    const int c = __popc(en.y);
-                    if (c <= skip) {
-                        skip -= c;
+                    const int cc = __popc(en.y);
+                    if (cc <= skip) {
+                        skip -= cc;
                     } else {
                         base = en.x;
                         mask = en.y;
@@ -504,11 +509,11 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
                 // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
                 if (__float_as_int(pjc.w) != __float_as_int(pi.w) &&   // not of one molecule
                     (r2 < pc.rc2_lo ||
-                     inside_cutoff_fp64(r, sidx[i0 + lane], sidx[ec & 0x1ffffffu], d.L, pc.rc2d)))
+                     inside_cutoff_fp64(r, sidx[ks], sidx[ec & 0x1ffffffu], d.L, pc.rc2d)))
                     pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qjc, acc);
             }
         }
-        if (vi) Fpart[(size_t)seg * N + i0 + lane] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);
+        if (vi) Fpart[(size_t)seg * N + ks] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);
         // virials: FP32 warp sums; energies: FP64 (compensated lanes), with the
         // constant of the energy tail applied to sum q_i q_j here
 #pragma unroll
@@ -659,7 +664,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
         k_pair_build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist,
                                            cf.rc2_hi);
 #define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
-    k_pair_eval<NF, EN><<<b.item_cap * kEvalSplit, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items,    \
+    k_pair_eval<NF, EN><<<b.item_cap * kEvalSplit, 32, 0, st>>>(b.sys, b.item_sys, a.start, a.scell, a.citem0,    \
                                                                 a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \
                                                                 b.N, a.plist, a.fpart4, partial, cf)
         if (cf.nff == 4) {

@@ -178,12 +178,168 @@ __device__ inline void key_mode(uint64_t k, int m[3])
 
 }  // namespace
 
+// Step 1 on its own grid: one warp per (system, Gaussian l, axis).
+__global__ void __launch_bounds__(32)
+k_samp_sums(const DevSys *sys, const SamplerArgs sa, SampScratch *ss)
+{
+    const int s = blockIdx.x, idx = blockIdx.y, lane = lane_id();
+    const DevSys &d = sys[s];
+    if ((d.flags & FLAG_BOX) || live_n(d) == 0 || idx >= 3 * sa.M) return;
+    const int l = idx / 3, ax = idx % 3;
+    const double L = d.L[ax];
+    double c = kPi * sa.st[l] / L, a = c * c;
+    int mm = axis_mmax(a);
+    double s0 = 0.0, s2 = 0.0, s4 = 0.0;
+    for (int m = -mm + lane; m <= mm; m += 32) {
+        double m2 = (double)m * (double)m;
+        double e = exp(-(a * m2));
+        s0 += e; s2 += m2 * e; s4 += m2 * m2 * e;
+    }
+    s0 = warp_sum(s0); s2 = warp_sum(s2); s4 = warp_sum(s4);
+    if (lane == 0) {
+        double g = kTwoPi / L;
+        ss[s].T[0][l][ax] = s0;
+        ss[s].T[1][l][ax] = g * g * s2;
+        ss[s].T[2][l][ax] = g * g * g * g * s4;
+    }
+}
+
+// Shared copy of the lattice sums and H^r_l, H^nr_l (each lane l forms its
+// Gaussian's terms; the sums over l run in order on every lane).
+__device__ void load_sums(const SamplerArgs &sa, const SampScratch &sc, const double L[3], Shared &sh,
+                          double &sr, double &snr)
+{
+    const int lane = lane_id();
+    for (int k = lane; k < 3 * sa.M; k += 32) {
+        const int l = k / 3, ax = k % 3;
+        sh.T0[l][ax] = sc.T[0][l][ax];
+        sh.T2[l][ax] = sc.T[1][l][ax];
+        sh.T4[l][ax] = sc.T[2][l][ax];
+    }
+    if (lane < 3) sh.L[lane] = L[lane];
+    __syncwarp();
+    for (int l = lane; l < sa.M; l += 32) {
+        const double *T0 = sh.T0[l], *T2 = sh.T2[l], *T4 = sh.T4[l];
+        sh.Hr[l] = sa.cr[l] * (T2[0] * T0[1] * T0[2] + T0[0] * T2[1] * T0[2] + T0[0] * T0[1] * T2[2]);
+        sh.Hnr[l] = sa.cn[l] * (T4[0] * T0[1] * T0[2] + T0[0] * T4[1] * T0[2] + T0[0] * T0[1] * T4[2]
+                                + 2.0 * (T2[0] * T2[1] * T0[2] + T2[0] * T0[1] * T2[2] + T0[0] * T2[1] * T2[2]));
+    }
+    __syncwarp();
+    sr = 0.0;
+    snr = 0.0;
+    for (int l = 0; l < sa.M; ++l) {
+        sr += sh.Hr[l];
+        snr += sh.Hnr[l];
+    }
+}
+
+// P^r and P^nr (targets) for one mode by one warp: lane l forms the l-th
+// exponential, the sums over l run in order as in targets().
+__device__ void targets_warp(const SamplerArgs &sa, const double L[3], const int m[3], double &pr, double &pnr)
+{
+    const int lane = lane_id();
+    double kx = (kTwoPi * (double)m[0]) / L[0];
+    double ky = (kTwoPi * (double)m[1]) / L[1];
+    double kz = (kTwoPi * (double)m[2]) / L[2];
+    double k2 = kx * kx + ky * ky + kz * kz;
+    double a = 0.0, b = 0.0;
+    for (int l0 = 0; l0 < sa.M; l0 += 32) {
+        const int l = l0 + lane;
+        const double e = l < sa.M ? exp(-(sa.st2q[l] * k2)) : 0.0;
+        const int nl = min(32, sa.M - l0);
+        for (int u = 0; u < nl; ++u) {
+            const double eu = __shfl_sync(0xffffffffu, e, u);
+            a += sa.cr[l0 + u] * eu;
+            b += sa.cn[l0 + u] * eu;
+        }
+    }
+    pr = k2 * a;
+    pnr = (k2 * k2) * b;
+}
+
+// q(m*) of eq. proposal by one warp: lane a forms the factor of axis a.
+__device__ double qprop_warp(const SamplerArgs &sa, const double L[3], const int m[3])
+{
+    const int lane = lane_id();
+    const int ax = lane < 3 ? lane : 0;
+    const double q = q1d(m[ax], L[ax], sa.st[0]);
+    const double q0 = __shfl_sync(0xffffffffu, q, 0), q1 = __shfl_sync(0xffffffffu, q, 1),
+                 q2 = __shfl_sync(0xffffffffu, q, 2);
+    return q0 * q1 * q2;
+}
+
+// Steps 2-3 of the paper MH sampler on their own grid: block (s, t) is one
+// warp; t < P evaluates proposal t (its three normals, its target and
+// proposal masses lane-parallel), t = P draws the chain's start state exactly.
+// Every value is formed by the same operations, in the same order, as the
+// one-thread code of the CPU oracle.
+__global__ void __launch_bounds__(32)
+k_samp_prop(const DevSys *sys, const SamplerArgs sa, int adv, SampScratch *ss, int4 *__restrict__ pm,
+            double *__restrict__ pw, double *__restrict__ pg, double *__restrict__ pu, double *__restrict__ pun)
+{
+    __shared__ Shared sh;
+    const int s = blockIdx.x, t = blockIdx.y, lane = lane_id();
+    const DevSys &d = sys[s];
+    if ((d.flags & FLAG_BOX) || live_n(d) == 0) return;
+    const uint64_t step = d.step + (uint64_t)adv;
+    const int P = sa.P;
+    const double L[3] = {d.L[0], d.L[1], d.L[2]};
+    uint64_t wds[4];
+    if (t == P) {
+        double sr, snr;
+        load_sums(sa, ss[s], L, sh, sr, snr);
+        draw4(sa.seed, d.rng_id, step, PUR_START, 0, wds);
+        int m[3];
+        exact_draw_warp(sa, sh, wds, false, m);
+        double pr, pnr;
+        targets_warp(sa, L, m, pr, pnr);
+        const double q = qprop_warp(sa, L, m);
+        if (lane == 0) {
+            SampScratch &sc = ss[s];
+            sc.start_m[0] = m[0]; sc.start_m[1] = m[1]; sc.start_m[2] = m[2];
+            sc.start_w = pr / q;
+            sc.start_g = pnr / pr;
+        }
+        return;
+    }
+    draw4(sa.seed, d.rng_id, step, PUR_PROPOSAL, (uint64_t)t, wds);
+    // z_0, z_1 from the first Box-Muller pair, z_2 from the second: lane a forms z_a
+    double z = 0.0;
+    if (lane < 3) {
+        const double u1 = u01(lane < 2 ? wds[0] : wds[2]), u2 = u01(lane < 2 ? wds[1] : wds[3]);
+        const double rr = sqrt(-2.0 * log(u1)), ang = kTwoPi * u2;
+        z = rr * (lane == 1 ? sin(ang) : cos(ang));
+    }
+    const int ma = lane < 3 ? (int)floor(L[lane] * (z * sa.sig_u) + 0.5) : 0;
+    int m[3];
+    m[0] = __shfl_sync(0xffffffffu, ma, 0);
+    m[1] = __shfl_sync(0xffffffffu, ma, 1);
+    m[2] = __shfl_sync(0xffffffffu, ma, 2);
+    double w = 0.0, g = 0.0;
+    if (m[0] || m[1] || m[2]) {
+        double pr, pnr;
+        targets_warp(sa, L, m, pr, pnr);
+        const double q = qprop_warp(sa, L, m);
+        w = pr / q;
+        g = pnr / pr;
+    }
+    if (lane == 0) {
+        const size_t k = (size_t)s * P + t;
+        pm[k] = make_int4(m[0], m[1], m[2], 0);
+        pw[k] = w;
+        pg[k] = g;
+        draw4(sa.seed, d.rng_id, step, PUR_ACCEPT, (uint64_t)t, wds);
+        pu[k] = u01(wds[0]);
+        pun[k] = u01(wds[1]);
+    }
+}
+
 // scratch per system: [P] proposal modes (int4) + w, g, u_r, u_nr (double)
 __global__ void __launch_bounds__(256)
 k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, int *__restrict__ mnr_out,
           int *__restrict__ D_out, int *__restrict__ cr_out, int *__restrict__ cnr_out,
           int4 *__restrict__ pm, double *__restrict__ pw, double *__restrict__ pg,
-          double *__restrict__ pu, double *__restrict__ pun, int Dcap)
+          double *__restrict__ pu, double *__restrict__ pun, const SampScratch *__restrict__ ss, int Dcap)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     uint64_t *keys = reinterpret_cast<uint64_t *>(dyn);         // [2 * P2]
@@ -208,56 +364,24 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, 
         return;
     }
 
-    // 1. 1D lattice sums
-    for (int idx = warp; idx < 3 * sa.M; idx += nw) {
-        const int l = idx / 3, ax = idx % 3;
-        double c = kPi * sa.st[l] / sh.L[ax], a = c * c;
-        int mm = axis_mmax(a);
-        double s0 = 0.0, s2 = 0.0, s4 = 0.0;
-        for (int m = -mm + lane; m <= mm; m += 32) {
-            double m2 = (double)m * (double)m;
-            double e = exp(-(a * m2));
-            s0 += e; s2 += m2 * e; s4 += m2 * m2 * e;
-        }
-        s0 = warp_sum(s0); s2 = warp_sum(s2); s4 = warp_sum(s4);
+    // 1. 1D lattice sums (k_samp_sums) and the normalizers
+    if (warp == 0) {
+        double sr, snr;
+        load_sums(sa, ss[s], sh.L, sh, sr, snr);
         if (lane == 0) {
-            double g = kTwoPi / sh.L[ax];
-            sh.T0[l][ax] = s0;
-            sh.T2[l][ax] = g * g * s2;
-            sh.T4[l][ax] = g * g * g * g * s4;
+            sh.Sr = sr; sh.Snr = snr;
+            d.Sr = sr; d.Snr = snr;
+            cnt_r = 0; cnt_nr = 0;
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double sr = 0.0, snr = 0.0;
-        for (int l = 0; l < sa.M; ++l) {
-            const double *T0 = sh.T0[l], *T2 = sh.T2[l], *T4 = sh.T4[l];
-            sh.Hr[l] = sa.cr[l] * (T2[0] * T0[1] * T0[2] + T0[0] * T2[1] * T0[2] + T0[0] * T0[1] * T2[2]);
-            sh.Hnr[l] = sa.cn[l] * (T4[0] * T0[1] * T0[2] + T0[0] * T4[1] * T0[2] + T0[0] * T0[1] * T4[2]
-                                    + 2.0 * (T2[0] * T2[1] * T0[2] + T2[0] * T0[1] * T2[2] + T0[0] * T2[1] * T2[2]));
-            sr += sh.Hr[l];
-            snr += sh.Hnr[l];
-        }
-        sh.Sr = sr; sh.Snr = snr;
-        d.Sr = sr; d.Snr = snr;
-        cnt_r = 0; cnt_nr = 0;
     }
     __syncthreads();
 
     // 2. exact draws
     if (sa.kind == 0) {
-        if (warp == 0) {
-            uint64_t wds[4];
-            draw4(sa.seed, d.rng_id, step, PUR_START, 0, wds);
-            int m[3];
-            exact_draw_warp(sa, sh, wds, false, m);
-            if (lane == 0) {
-                double pr, pnr;
-                targets(sa, sh.L, m, pr, pnr);
-                start_m[0] = m[0]; start_m[1] = m[1]; start_m[2] = m[2];
-                start_w = pr / qprop(sa, sh.L, m);
-                start_g = pnr / pr;
-            }
+        if (tid == 0) {                       // drawn by k_samp_prop
+            start_m[0] = ss[s].start_m[0]; start_m[1] = ss[s].start_m[1]; start_m[2] = ss[s].start_m[2];
+            start_w = ss[s].start_w;
+            start_g = ss[s].start_g;
         }
     } else {
         for (int t = warp; t < P; t += nw) {
@@ -287,8 +411,9 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, 
     }
     __syncthreads();
 
-    // 3. proposal weights (parallel) and uniforms
-    for (int t = tid; t < P; t += blockDim.x) {
+    // 3. proposal weights (parallel) and uniforms; the paper sampler's are
+    // formed by k_samp_prop
+    for (int t = tid; t < P && sa.kind != 0; t += blockDim.x) {
         uint64_t wds[4];
         int m[3];
         if (sa.kind == 0) {
@@ -452,10 +577,14 @@ cudaError_t prepare_sampler(int P)
 }
 
 void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int *mnr, int *D, int *cr,
-                    int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, int Dcap,
-                    cudaStream_t st)
+                    int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, SampScratch *ss,
+                    int Dcap, cudaStream_t st)
 {
-    k_sampler<<<b.S, 256, sampler_smem(sa.P), st>>>(b.sys, sa, adv, mr, mnr, D, cr, cnr, pm, pw, pg, pu, pun, Dcap);
+    k_samp_sums<<<dim3(b.S, 3 * sa.M), 32, 0, st>>>(b.sys, sa, ss);
+    if (sa.kind == 0)
+        k_samp_prop<<<dim3(b.S, sa.P + 1), 32, 0, st>>>(b.sys, sa, adv, ss, pm, pw, pg, pu, pun);
+    k_sampler<<<b.S, 256, sampler_smem(sa.P), st>>>(b.sys, sa, adv, mr, mnr, D, cr, cnr, pm, pw, pg, pu, pun, ss,
+                                                    Dcap);
 }
 
 }  // namespace rbsog

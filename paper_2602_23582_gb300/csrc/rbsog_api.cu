@@ -62,20 +62,22 @@ struct rbsog_ctx {
     bool pool = false;                  // slots are loaded and emptied at run time
     std::vector<rbsog_status> slot_err; // pool: why a slot's system was stopped (RBSOG_OK: it was not)
     int S = 0, N = 0, C = 0, Dcap = 0, nchunks = 0, nmol = 0, nmchunks = 0, item_cap = 0;
-    cudaStream_t st = nullptr, st2 = nullptr;
+    cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr;   // st2: mode sampling, st3: molecule terms
     bool own_st = false, own_st2 = false;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
     std::string err;
     std::vector<int> h_atom0, h_n, h_cell0, h_ncap_total, h_coupling;
     std::vector<void *> allocs;
     // device
     DevSys *sys = nullptr;
     double *r = nullptr, *p = nullptr, *F = nullptr, *q = nullptr, *mass = nullptr;
+    double *Fmol = nullptr;     // molecule-term forces, added by the force assembly
     int *type = nullptr, *mol = nullptr, *atom_sys = nullptr, *cell = nullptr, *rank = nullptr;
     float4 *locf = nullptr, *pos4 = nullptr;
     double4 *locd = nullptr, *posd = nullptr;
     uint4 *su = nullptr;
     int *count = nullptr, *start = nullptr, *sidx = nullptr, *cell_sys = nullptr;
+    int *item_sys = nullptr, *citem0 = nullptr, *scell = nullptr;
     float2 *qt = nullptr;
     int2 *aux = nullptr, *items = nullptr;
     int *chunk_sys = nullptr, *chunk_a0 = nullptr, *chunk_n = nullptr, *first_chunk = nullptr, *nchunk_sys = nullptr;
@@ -94,6 +96,7 @@ struct rbsog_ctx {
     float2 *ljf = nullptr, *ljf_lo = nullptr;
     int *mr = nullptr, *mnr = nullptr, *D = nullptr, *cr = nullptr, *cnr = nullptr;
     int4 *pm = nullptr;
+    SampScratch *samp = nullptr;
     double *pw = nullptr, *pg = nullptr, *pu = nullptr, *pun = nullptr;
     double *sk_part = nullptr, *rho = nullptr;
     ModeCoef *coef = nullptr;
@@ -196,12 +199,22 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
 {
     const int prec = c->prm.precision;
     record(c, "start");
+    // molecule terms need only the positions and the box: they run beside
+    // the binning, into their own force buffer, and end before the pair kernels
+    const bool mol = c->m.nmchunks > 0;
+    if (mol) {
+        cudaEventRecord(c->ev_fork3, c->st);
+        cudaStreamWaitEvent(c->st3, c->ev_fork3, 0);
+        cudaMemsetAsync(c->Fmol, 0, 3 * sizeof(double) * (size_t)c->N, c->st3);
+        launch_mol(c->b, c->a, c->m, c->sc, c->Fmol, c->mol_part, prec, c->st3);
+        cudaEventRecord(c->ev_join3, c->st3);
+    }
     launch_box_prep(c->b, c->st);
     record(c, "box_prep");
     cudaEventRecord(c->ev_fork, c->st);
     cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
     launch_sampler(c->b, c->sa, adv, c->mr, c->mnr, c->D, c->cr, c->cnr, c->pm, c->pw, c->pg, c->pu, c->pun,
-                   c->Dcap, c->st2);
+                   c->samp, c->Dcap, c->st2);
     cudaEventRecord(c->ev_join, c->st2);
     launch_bin(c->b, c->a, prec, c->st);
     record(c, "bin");
@@ -209,6 +222,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
+    if (mol) cudaStreamWaitEvent(c->st, c->ev_join3, 0);
     // in a graph capture: event-record nodes around the pair kernel (external
     // records, not dependencies), retargeted per launch by arm_pair_trace
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -225,10 +239,8 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     launch_estimate(c->b, c->first_chunk, c->nchunk_sys, c->D, c->cr, c->cnr, c->Dcap, c->prm.P, c->prm.ke,
                     c->sk_part, c->rho, c->coef, c->est, c->st);
     record(c, "estimate");
-    launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, c->st);
+    launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, mol ? c->Fmol : nullptr, c->st);
     record(c, "lr_force");
-    launch_mol(c->b, c->a, c->m, c->sc, c->mol_part, prec, c->st);
-    record(c, "molecules");
     launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
     record(c, "kick_kinetic");
     launch_reduce_pair(c->b, prec == 1 ? kEvalSplit : 2 * c->prm.cell_sub + 1, c->pair_part, c->pair_red, c->st);
@@ -321,7 +333,10 @@ void free_ctx(rbsog_ctx *c)
     for (void *v : c->allocs) cudaFree(v);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_fork3) cudaEventDestroy(c->ev_fork3);
+    if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     if (c->own_st2 && c->st2) cudaStreamDestroy(c->st2);
+    if (c->st3) cudaStreamDestroy(c->st3);
     if (c->own_st && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -580,8 +595,12 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         e = cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rbsog_status r = cuda_fail(c, e, "stream"); free_ctx(c); return r; }
         c->own_st2 = true;
+        e = cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { rbsog_status r = cuda_fail(c, e, "stream"); free_ctx(c); return r; }
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
         cudaEventCreate(&c->ev_pair_ph[0]);
         cudaEventCreate(&c->ev_pair_ph[1]);
         c->Dcap = (P.sampler == RBSOG_SAMPLER_IID) ? 2 * P.P : P.P + 1;
@@ -600,7 +619,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         std::vector<DevSys> hsys(S);
         c->lay.resize(S);
         int N = 0, C = 0, nmolx = 0, item_cap = 0, nbond = 0, nang = 0, nexc = 0, nlj = 0;
-        std::vector<int> atom_sys, cell_sys, chunk_sys, chunk_a0, chunk_n, first_chunk(S), nchunk(S);
+        std::vector<int> atom_sys, cell_sys, item_sys, chunk_sys, chunk_a0, chunk_n, first_chunk(S), nchunk(S);
         std::vector<int> mchunk_sys, mchunk_m0, mchunk_n, mchunk_first(S), mchunk_count(S);
         c->h_atom0.resize(S); c->h_n.resize(S); c->h_cell0.resize(S); c->h_ncap_total.resize(S);
         for (int k = 0; k < S; ++k) {
@@ -632,6 +651,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             ds.item0 = item_cap;
             ds.item_cap = ((cp.atoms + 31) / 32 + ncap_t + kPairWarps - 1) / kPairWarps * kPairWarps;
             item_cap += ds.item_cap;
+            item_sys.insert(item_sys.end(), (size_t)ds.item_cap, k);
             ds.atom0 = N;
             ds.lj0 = nlj;
             ds.mol0 = nmolx;
@@ -727,6 +747,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         bool ok = upload(c, c->sys, hsys) && upload(c, c->r, r) && upload(c, c->p, p) && upload(c, c->q, q) &&
                   upload(c, c->mass, mass) && upload(c, c->type, type) && upload(c, c->mol, mol) &&
                   upload(c, c->atom_sys, atom_sys) && upload(c, c->cell_sys, cell_sys) &&
+                  upload(c, c->item_sys, item_sys) && dalloc(c, c->citem0, C) && dalloc(c, c->scell, N) &&
                   upload(c, c->chunk_sys, chunk_sys) && upload(c, c->chunk_a0, chunk_a0) &&
                   upload(c, c->chunk_n, chunk_n) && upload(c, c->first_chunk, first_chunk) &&
                   upload(c, c->nchunk_sys, nchunk) && upload(c, c->mchunk_sys, mchunk_sys) &&
@@ -735,7 +756,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->b_start, b_start) && upload(c, c->a_start, a_start) && upload(c, c->e_start, e_start) &&
                   upload(c, c->bonds, bonds) && upload(c, c->angles, angles) && upload(c, c->excl, excl) &&
                   upload(c, c->bk, bk) && upload(c, c->br0, br0) && upload(c, c->ak, ak) && upload(c, c->at0, at0) &&
-                  upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
+                  upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
                   dalloc(c, c->pair_part, (size_t)item_cap * std::max(2 * P.cell_sub + 1, kEvalSplit) * kPairRec) &&
@@ -745,7 +766,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
                   dalloc(c, c->mr, (size_t)S * P.P * 3) && dalloc(c, c->mnr, (size_t)S * P.P * 3) &&
                   dalloc(c, c->D, (size_t)S * c->Dcap * 3) && dalloc(c, c->cr, (size_t)S * c->Dcap) &&
-                  dalloc(c, c->cnr, (size_t)S * c->Dcap) && dalloc(c, c->pm, (size_t)S * P.P) &&
+                  dalloc(c, c->cnr, (size_t)S * c->Dcap) && dalloc(c, c->pm, (size_t)S * P.P) && dalloc(c, c->samp, (size_t)S) &&
                   dalloc(c, c->pw, (size_t)S * P.P) && dalloc(c, c->pg, (size_t)S * P.P) &&
                   dalloc(c, c->pu, (size_t)S * P.P) && dalloc(c, c->pun, (size_t)S * P.P) &&
                   dalloc(c, c->sk_part, (size_t)c->nchunks * c->Dcap * 2) &&
@@ -850,13 +871,13 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->ia.noise_f32 = P.precision == RBSOG_FP32 ? 1 : 0;
 
         c->b.S = S; c->b.N = N; c->b.C = C; c->b.sub = P.cell_sub; c->b.rc = P.rc; c->b.sys = c->sys;
-        c->b.atom_sys = c->atom_sys; c->b.cell_sys = c->cell_sys; c->b.chunk_sys = c->chunk_sys;
+        c->b.atom_sys = c->atom_sys; c->b.cell_sys = c->cell_sys; c->b.item_sys = c->item_sys; c->b.chunk_sys = c->chunk_sys;
         c->b.chunk_a0 = c->chunk_a0; c->b.chunk_n = c->chunk_n; c->b.nchunks = c->nchunks;
         c->b.item_cap = item_cap;
         c->a.r = c->r; c->a.p = c->p; c->a.F = c->F; c->a.q = c->q; c->a.mass = c->mass; c->a.type = c->type;
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
         c->a.su = c->su; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
-        c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
+        c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items; c->a.citem0 = c->citem0; c->a.scell = c->scell;
         c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
         c->a.plist.ent = c->pl_ent; c->a.plist.next = c->pl_next; c->a.plist.head = c->pl_head;
