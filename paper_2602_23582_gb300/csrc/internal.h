@@ -65,7 +65,7 @@ struct Batch {
 // kListChunk-entry chunks from a pool of cap_chunks; an entry is (index of
 // the first of 32 candidates | neighbour-cell code << 25, hit mask).
 constexpr int kListChunk = 16;
-constexpr int kEvalSplit = 4;   // FP32 evaluation warps (hit segments) per 32-atom group
+constexpr int kEvalSplit = 3;   // FP32 evaluation warps (hit segments) per 32-atom group
 struct PairList {
     uint2 *ent;                 // [cap_chunks * kListChunk]
     int *next;                  // [cap_chunks] next chunk of the same list

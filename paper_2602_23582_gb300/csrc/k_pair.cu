@@ -237,11 +237,12 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // chunk at once.  A lane's entries keep its candidate order, so the evaluation
 // order does not depend on which chunks it got.
 //
-// k_pair_eval: work unit = 32 consecutive cell-sorted atoms of one system
-// (whatever their cells, so the lanes are full) x one of kEvalSplit segments
-// of each atom's hits (all planes in order, split by hit count), one hit per
-// lane and round, so every lane carries about the same number of pairs;
-// segment k writes force partial k, summed in segment order by the force
+// k_pair_eval: one block per 32 consecutive cell-sorted atoms of one system
+// (whatever their cells, so the lanes are full); warp k takes segment k of
+// kEvalSplit of each atom's hits (all planes in order, split by hit count),
+// one hit per lane and round, so every lane carries about the same number of
+// pairs, and the block's warps share the same neighbour atoms in L1.
+// Segment k writes force partial k, summed in segment order by the force
 // assembly.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32, 32)
@@ -381,7 +382,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
 }
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32, EN ? 20 : 24)
+__global__ void __launch_bounds__(32 * kEvalSplit, EN ? 4 : 8)
 k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int *__restrict__ start,
             const int *__restrict__ scell, const int *__restrict__ citem0, const float4 *__restrict__ pos4,
             const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
@@ -392,7 +393,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
     __shared__ float2 ljs[EN ? 2 : 1][kMaxTypes * kMaxTypes];   // the system's LJ table (and remainders)
     const int lane = lane_id();
     const int span = 2 * sub + 1;
-    const int it = blockIdx.x / kEvalSplit, seg = blockIdx.x % kEvalSplit;
+    const int it = blockIdx.x, seg = threadIdx.x >> 5;   // one warp per segment, one block per group
     const DevSys &d = sys[item_sys[it]];
     // evaluation group: 32 consecutive cell-sorted atoms of one system (group
     // g of the system uses the record slots of its work item item0 + g)
@@ -404,18 +405,18 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
     if (g32 < nlive) {                                 // warp-uniform
         // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
         // must not shift every cross-cell distance the same way)
-        for (int nb = lane; nb < span * span * span; nb += 32) {
+        for (int nb = threadIdx.x; nb < span * span * span; nb += blockDim.x) {
             const double ox = (nb % span - sub) * d.w[0], oy = ((nb / span) % span - sub) * d.w[1],
                          oz = (nb / (span * span) - sub) * d.w[2];
             const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
             offh[nb] = make_float4(hx, hy, hz, 0.f);
             offl[nb] = make_float4((float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
         }
-        for (int t = lane; t < d.ntypes * d.ntypes; t += 32) {
+        for (int t = threadIdx.x; t < d.ntypes * d.ntypes; t += blockDim.x) {
             ljs[0][t] = lj[d.lj0 + t];
             if (EN) ljs[EN ? 1 : 0][t] = ljlo[d.lj0 + t];
         }
-        __syncwarp();
+        __syncthreads();                               // block-uniform branch
         const int ks = d.atom0 + g32 + lane;           // this lane's atom (cell-sorted index)
         const bool vi = g32 + lane < nlive;
         float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -535,7 +536,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
 #pragma unroll
     for (int k = 0; k < 18; ++k)
         if (lane == 2 + k) v = (double)wv[k];
-    if (lane < kPairRec) partial[(size_t)blockIdx.x * kPairRec + lane] = 0.5 * v;
+    if (lane < kPairRec) partial[((size_t)it * kEvalSplit + seg) * kPairRec + lane] = 0.5 * v;
 }
 
 // ---------------------------------------------------------------------------
@@ -664,7 +665,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
         k_pair_build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist,
                                            cf.rc2_hi);
 #define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
-    k_pair_eval<NF, EN><<<b.item_cap * kEvalSplit, 32, 0, st>>>(b.sys, b.item_sys, a.start, a.scell, a.citem0,    \
+    k_pair_eval<NF, EN><<<b.item_cap, 32 * kEvalSplit, 0, st>>>(b.sys, b.item_sys, a.start, a.scell, a.citem0,    \
                                                                 a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \
                                                                 b.N, a.plist, a.fpart4, partial, cf)
         if (cf.nff == 4) {
