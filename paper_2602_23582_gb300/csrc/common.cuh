@@ -171,4 +171,61 @@ __device__ inline void block_reduce_lanes(const double (&v)[V], double *smem, do
     for (int k = t; k < V; k += NT) out[k] = (s2[k * G] + s2[k * G + 1]) + (s2[k * G + 2] + s2[k * G + 3]);
 }
 
+// Cell grid of one axis for box edge L (cells of r_c / sub, at least
+// 2 sub + 1 and at most the slot's capacity ncap): sets *bad when the box is
+// too small, not finite or beyond the allocated grid.
+__device__ __forceinline__ int axis_cells(double L, int sub, double rc, int ncap, bool *bad)
+{
+    const int minc = 2 * sub + 1;
+    const double x = floor(__ddiv_rn(__dmul_rn(L, (double)sub), rc));
+    if (!(L > 0.0) || !(x < 1e9) || x < (double)minc) *bad = true;
+    int n = (x < 1e9 && x >= (double)minc) ? (int)x : minc;
+    if (n > ncap) n = ncap;
+    return n;
+}
+
+// Bin atom i of system d at position x (wrapped into [0, L)): its cell, its
+// rank there by a warp-aggregated atomic on count (act: the lanes of the warp
+// that bin an atom), cell-local coordinates and fixed-point fractional
+// coordinates.
+__device__ __forceinline__ void bin_atom(const DevSys &d, int i, const double x[3], double qi, int moli,
+                                         unsigned act, int *__restrict__ cell, int *__restrict__ rank,
+                                         int *__restrict__ count, float4 *__restrict__ locf,
+                                         double4 *__restrict__ locd, uint4 *__restrict__ su, int precision)
+{
+    int c[3];
+    double sf[3], xl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double L = d.L[a];
+        double s = __ddiv_rn(x[a], L);
+        s = __dsub_rn(s, floor(s));
+        if (s >= 1.0) s = 0.0;
+        int n = d.ncell[a];
+        int k = (int)floor(__dmul_rn(s, (double)n));
+        if (k > n - 1) k = n - 1;
+        if (!(k >= 0)) k = 0;        // non-finite coordinates (flagged by the step checks)
+        c[a] = k;
+        sf[a] = s;
+        xl[a] = s * L - k * d.w[a];
+    }
+    const int gc = d.cell0 + c[0] + d.ncell[0] * (c[1] + d.ncell[1] * c[2]);
+    cell[i] = gc;
+    // warp-aggregated atomic: one atomicAdd per distinct cell in the warp
+    const unsigned peers = __match_any_sync(act, gc);
+    const int leader = __ffs(peers) - 1;
+    const unsigned lane = threadIdx.x & 31u;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(&count[gc], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    rank[i] = base + __popc(peers & ((1u << lane) - 1u));
+    if (precision == 1) {
+        locf[i] = make_float4((float)xl[0], (float)xl[1], (float)xl[2], __int_as_float(moli));
+        su[i] = make_uint4(__double2uint_rz(sf[0] * 4294967296.0), __double2uint_rz(sf[1] * 4294967296.0),
+                           __double2uint_rz(sf[2] * 4294967296.0), __float_as_uint((float)qi));
+    } else {
+        locd[i] = make_double4(xl[0], xl[1], xl[2], qi);
+    }
+}
+
 }  // namespace rbsog

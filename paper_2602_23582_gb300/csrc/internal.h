@@ -186,8 +186,11 @@ struct IntegArgs {
     int noise_f32;                    // 1: Gaussian noise drawn in FP32 (FP32 build)
     uint64_t seed;                    // a step uses the Philox counter DevSys::step + 1
 };
-void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st);
-void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st);
+// prep = 1: also the cell grid of the new box (k_box_prep's work)
+void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st);
+// bin = 1: also k_bin's work for the updated atoms (counts zeroed by the caller)
+void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
+                        cudaStream_t st);
 constexpr int kKinSplit = 4;   // kinetic partials per atom chunk
 void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int kick,
                          double *kin_part, cudaStream_t st);

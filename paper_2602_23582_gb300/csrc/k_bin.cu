@@ -22,18 +22,16 @@ __global__ void k_box_prep(DevSys *sys, int S, int sub, double rc)
         for (int a = 0; a < 3; ++a) { d.ncell[a] = minc; d.w[a] = 1.0; }
         return;
     }
+    bool bad = false;
     for (int a = 0; a < 3; ++a) {
-        double L = d.L[a];
-        double x = floor(__ddiv_rn(__dmul_rn(L, (double)sub), rc));
         // a box that is too small, not finite or beyond the allocated grid is
         // flagged; the grid stays within [2 sub + 1, ncap] so that every
         // neighbour-cell index remains valid while the step is discarded
-        if (!(L > 0.0) || !(x < 1e9) || x < (double)minc) d.flags |= FLAG_BOX;
-        int n = (x < 1e9 && x >= (double)minc) ? (int)x : minc;
-        if (n > d.ncap[a]) n = d.ncap[a];
+        const int n = axis_cells(d.L[a], sub, rc, d.ncap[a], &bad);
         d.ncell[a] = n;
-        d.w[a] = L / n;
+        d.w[a] = d.L[a] / n;
     }
+    if (bad) d.flags |= FLAG_BOX;
     d.V = d.L[0] * d.L[1] * d.L[2];
 }
 
@@ -69,40 +67,8 @@ __global__ void k_bin(const DevSys *__restrict__ sys, const int *__restrict__ at
     const unsigned act = __ballot_sync(0xffffffffu, live);
     if (!live) return;
     const DevSys &d = sys[atom_sys[i]];
-    int c[3];
-    double sf[3], xl[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double L = d.L[a];
-        double s = __ddiv_rn(r[3 * i + a], L);
-        s = __dsub_rn(s, floor(s));
-        if (s >= 1.0) s = 0.0;
-        int n = d.ncell[a];
-        int k = (int)floor(__dmul_rn(s, (double)n));
-        if (k > n - 1) k = n - 1;
-        if (!(k >= 0)) k = 0;        // non-finite coordinates (flagged by the step checks)
-        c[a] = k;
-        sf[a] = s;
-        xl[a] = s * L - k * d.w[a];
-    }
-    const int gc = d.cell0 + c[0] + d.ncell[0] * (c[1] + d.ncell[1] * c[2]);
-    cell[i] = gc;
-    // warp-aggregated atomic: one atomicAdd per distinct cell in the warp
-    const unsigned peers = __match_any_sync(act, gc);
-    const int leader = __ffs(peers) - 1;
-    const unsigned lane = lane_id();
-    int base = 0;
-    if ((int)lane == leader) base = atomicAdd(&count[gc], __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    rank[i] = base + __popc(peers & ((1u << lane) - 1u));
-    const double qi = q[i];
-    if (precision == 1) {
-        locf[i] = make_float4((float)xl[0], (float)xl[1], (float)xl[2], __int_as_float(mol[i]));
-        su[i] = make_uint4(__double2uint_rz(sf[0] * 4294967296.0), __double2uint_rz(sf[1] * 4294967296.0),
-                           __double2uint_rz(sf[2] * 4294967296.0), __float_as_uint((float)qi));
-    } else {
-        locd[i] = make_double4(xl[0], xl[1], xl[2], qi);
-    }
+    const double x[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+    bin_atom(d, i, x, q[i], mol[i], act, cell, rank, count, locf, locd, su, precision);
 }
 
 void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)

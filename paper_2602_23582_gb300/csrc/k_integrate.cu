@@ -54,12 +54,15 @@ __device__ void box_force(const DevSys &d, const double *red, const IntegArgs &i
 constexpr int kBoxWarps = 4;
 
 __global__ void __launch_bounds__(32 * kBoxWarps)
-k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred)
+k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred, int prep_sub, double rc)
 {
     const int s = blockIdx.x * kBoxWarps + (threadIdx.x >> 5), lane = lane_id();
     if (s >= S) return;
     DevSys &d = sys[s];
-    if (live_n(d) == 0) return;               // empty or finished slot (warp-uniform)
+    if (live_n(d) == 0) {                     // empty or finished slot (warp-uniform)
+        if (prep_sub > 0 && lane < 3) { d.ncell[lane] = 2 * prep_sub + 1; d.w[lane] = 1.0; }
+        return;
+    }
     const double *red = sysred + (size_t)s * kRed;
     const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
     const int ax = lane < 3 ? lane : 0;
@@ -114,27 +117,53 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
         d.isc2[lane] = Lh / Ln;
         d.invL[lane] = 1.0 / Ln;
     }
+    if (prep_sub > 0) {
+        // the cell grid of the new box (as k_box_prep), so that the atom
+        // update can bin its atoms
+        bool bad = false;
+        if (lane < 3) {
+            const int n = axis_cells(Ln, prep_sub, rc, d.ncap[lane], &bad);
+            d.ncell[lane] = n;
+            d.w[lane] = Ln / n;
+        }
+        const bool anybad = __any_sync(0xffffffffu, bad);
+        const double L0 = __shfl_sync(0xffffffffu, Ln, 0), L1 = __shfl_sync(0xffffffffu, Ln, 1),
+                     L2 = __shfl_sync(0xffffffffu, Ln, 2);
+        if (lane == 0) {
+            if (anybad) d.flags |= FLAG_BOX;
+            d.V = L0 * L1 * L2;
+        }
+    }
 }
 
-void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, cudaStream_t st)
+void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st)
 {
-    k_box_half<<<(b.S + kBoxWarps - 1) / kBoxWarps, 32 * kBoxWarps, 0, st>>>(b.sys, b.S, ia, sysred);
+    k_box_half<<<(b.S + kBoxWarps - 1) / kBoxWarps, 32 * kBoxWarps, 0, st>>>(b.sys, b.S, ia, sysred,
+                                                                            prep ? b.sub : 0, b.rc);
 }
 
 // Atom part of B (first half), A, O, A and the wrap.  Per-system drift
 // scalings come from k_box_half; 1/m and the noise amplitude are per-atom
 // constants.  NF32: the Gaussian noise is drawn in FP32 (FP32 build), else in
 // FP64 (Box-Muller on the same Philox words as the CPU reference).
-template <bool NF32>
+// BIN: the updated atom is binned right away (as k_bin; the caller zeroed the
+// cell counts and set the new cell grid in k_box_half).
+template <bool NF32, bool BIN>
 __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys, int N,
                               double *__restrict__ r, double *__restrict__ p, const double *__restrict__ F,
-                              const IntegArgs ia)
+                              const IntegArgs ia, const AtomArrays aa, int precision)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    bool live = false;
+    if (i < N) {
+        const DevSys &ds = sys[atom_sys[i]];
+        live = i - ds.atom0 < live_n(ds);     // slots hold up to their capacity
+        if (BIN && !live) aa.cell[i] = -1;
+    }
+    const unsigned act = BIN ? __ballot_sync(0xffffffffu, live) : 0u;
+    if (!live) return;
     const int s = atom_sys[i];
     const DevSys &d = sys[s];
-    if (i - d.atom0 >= live_n(d)) return;     // beyond the system in its slot
     const double im = ia.inv_m[i], tau = 0.5 * ia.dt, kick = 0.5 * ia.dt * ia.ftm2v;
     double x[3], v[3];
     for (int a = 0; a < 3; ++a) {
@@ -175,14 +204,20 @@ __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restr
         r[3 * i + a] = x[a];
         p[3 * i + a] = v[a];
     }
+    if (BIN) bin_atom(d, i, x, aa.q[i], aa.mol[i], act, aa.cell, aa.rank, aa.count, aa.locf, aa.locd, aa.su, precision);
 }
 
-void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, cudaStream_t st)
+void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
+                        cudaStream_t st)
 {
-    if (ia.noise_f32)
-        k_atom_update<true><<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia);
-    else
-        k_atom_update<false><<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia);
+    const int g = (b.N + 255) / 256;
+    if (ia.noise_f32) {
+        if (bin) k_atom_update<true, true><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
+        else k_atom_update<true, false><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
+    } else {
+        if (bin) k_atom_update<false, true><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
+        else k_atom_update<false, false><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
+    }
 }
 
 // Second half kick (optional) and the kinetic tensor per quarter of an atom

@@ -425,10 +425,17 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
         // this warp takes hits [h0, h1) of the lane's stream (all planes in order)
         int nh = 0, pl = 0, rem = 0, cur = 0, pos = 0;
         unsigned base = 0u, mask = 0u;
+        // the atom's lists belong to work item (its cell, its 32-atom group
+        // there); an atom beyond the sorted part of an overflowing cell (the
+        // step is flagged and discarded) is left out
+        int unit = -1, o = 0;
         if (vi) {
-            // the atom's lists belong to work item (its cell, its 32-atom group there)
-            const int c = scell[ks], o = ks - start[c];
-            u0i = (citem0[c] + (o >> 5)) * span * 32 + (o & 31);
+            const int c = scell[ks];
+            o = ks - start[c];
+            unit = citem0[c] + (o >> 5);
+        }
+        if (vi && o >= 0 && (unsigned)(unit - d.item0) < (unsigned)d.item_cap) {
+            u0i = unit * span * 32 + (o & 31);
             pi = pos4[ks];
             pq = qt[ks];
             int tot = 0;

@@ -65,6 +65,7 @@ struct rbsog_ctx {
     cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr;   // st2: mode sampling, st3: molecule terms
     bool own_st = false, own_st2 = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
+    cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr;
     std::string err;
     std::vector<int> h_atom0, h_n, h_cell0, h_ncap_total, h_coupling;
     std::vector<void *> allocs;
@@ -195,29 +196,45 @@ void record(rbsog_ctx *c, const char *name)
 // One force evaluation of every system (Algorithm 1 steps 2-7).
 // adv = 1: the evaluation of an NPT step (Philox counter DevSys::step + 1,
 // advanced at the end); 0: evaluate at DevSys::step.
-void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
+// Mode sampling on the second stream: needs the box and its cell grid only.
+void fork_sampler(rbsog_ctx *c, int adv)
 {
-    const int prec = c->prm.precision;
-    record(c, "start");
-    // molecule terms need only the positions and the box: they run beside
-    // the binning, into their own force buffer, and end before the pair kernels
-    const bool mol = c->m.nmchunks > 0;
-    if (mol) {
-        cudaEventRecord(c->ev_fork3, c->st);
-        cudaStreamWaitEvent(c->st3, c->ev_fork3, 0);
-        cudaMemsetAsync(c->Fmol, 0, 3 * sizeof(double) * (size_t)c->N, c->st3);
-        launch_mol(c->b, c->a, c->m, c->sc, c->Fmol, c->mol_part, prec, c->st3);
-        cudaEventRecord(c->ev_join3, c->st3);
-    }
-    launch_box_prep(c->b, c->st);
-    record(c, "box_prep");
     cudaEventRecord(c->ev_fork, c->st);
     cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
     launch_sampler(c->b, c->sa, adv, c->mr, c->mnr, c->D, c->cr, c->cnr, c->pm, c->pw, c->pg, c->pu, c->pun,
                    c->samp, c->Dcap, c->st2);
     cudaEventRecord(c->ev_join, c->st2);
-    launch_bin(c->b, c->a, prec, c->st);
-    record(c, "bin");
+}
+
+// Molecule terms on the third stream: they need only the positions and the
+// box, run beside the binning into their own force buffer, and end before
+// the pair kernels.
+void fork_mol(rbsog_ctx *c)
+{
+    if (c->m.nmchunks == 0) return;
+    cudaEventRecord(c->ev_fork3, c->st);
+    cudaStreamWaitEvent(c->st3, c->ev_fork3, 0);
+    cudaMemsetAsync(c->Fmol, 0, 3 * sizeof(double) * (size_t)c->N, c->st3);
+    launch_mol(c->b, c->a, c->m, c->sc, c->Fmol, c->mol_part, c->prm.precision, c->st3);
+    cudaEventRecord(c->ev_join3, c->st3);
+}
+
+// prepared = 1: the caller has set the cell grid, binned the atoms and
+// forked the sampler and the molecule terms (the NPT step does this in its
+// box and atom updates).
+void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int prepared = 0)
+{
+    const int prec = c->prm.precision;
+    const bool mol = c->m.nmchunks > 0;
+    if (!prepared) {
+        record(c, "start");
+        fork_mol(c);
+        launch_box_prep(c->b, c->st);
+        record(c, "box_prep");
+        fork_sampler(c, adv);
+        launch_bin(c->b, c->a, prec, c->st);
+        record(c, "bin");
+    }
     launch_scan(c->b, c->a, c->st);
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
@@ -232,6 +249,11 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     launch_pair(c->b, c->a, prec, c->pcf, c->pcd, energy, c->pair_part, c->st);
     if (trace) cudaEventRecordWithFlags(c->ev_pair_ph[1], c->st, cudaEventRecordExternal);
     record(c, "pair");
+    // the pair records are reduced beside the long-range part
+    cudaEventRecord(c->ev_fork4, c->st);
+    cudaStreamWaitEvent(c->st3, c->ev_fork4, 0);
+    launch_reduce_pair(c->b, prec == 1 ? kEvalSplit : 2 * c->prm.cell_sub + 1, c->pair_part, c->pair_red, c->st3);
+    cudaEventRecord(c->ev_join4, c->st3);
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
     launch_sk(c->b, c->a, prec, c->D, c->Dcap, c->sk_part, c->st);
@@ -243,7 +265,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
     record(c, "lr_force");
     launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
     record(c, "kick_kinetic");
-    launch_reduce_pair(c->b, prec == 1 ? kEvalSplit : 2 * c->prm.cell_sub + 1, c->pair_part, c->pair_red, c->st);
+    cudaStreamWaitEvent(c->st, c->ev_join4, 0);
     launch_finalize(c->b, c->pair_red, c->est, estimate_blocks(c->Dcap), c->prm.P, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
     record(c, "finalize");
@@ -251,9 +273,14 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv)
 
 void enqueue_npt_step(rbsog_ctx *c, int energy)
 {
-    launch_box_half(c->b, c->ia, c->sysred, c->st);
-    launch_atom_update(c->b, c->a, c->ia, c->st);
-    enqueue_eval(c, 1, 1, energy, 1);
+    // box half-step with the new cell grid, the sampler forked right after
+    // it, then the atom update with the binning of the moved atoms
+    cudaMemsetAsync(c->count, 0, sizeof(int) * (size_t)c->C, c->st);
+    launch_box_half(c->b, c->ia, c->sysred, 1, c->st);
+    fork_sampler(c, 1);
+    launch_atom_update(c->b, c->a, c->ia, 1, c->prm.precision, c->st);
+    fork_mol(c);
+    enqueue_eval(c, 1, 1, energy, 1, 1);
 }
 
 rbsog_status check_flags(rbsog_ctx *c)
@@ -335,6 +362,8 @@ void free_ctx(rbsog_ctx *c)
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_fork3) cudaEventDestroy(c->ev_fork3);
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
+    if (c->ev_fork4) cudaEventDestroy(c->ev_fork4);
+    if (c->ev_join4) cudaEventDestroy(c->ev_join4);
     if (c->own_st2 && c->st2) cudaStreamDestroy(c->st2);
     if (c->st3) cudaStreamDestroy(c->st3);
     if (c->own_st && c->st) cudaStreamDestroy(c->st);
@@ -601,6 +630,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_fork4, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_join4, cudaEventDisableTiming);
         cudaEventCreate(&c->ev_pair_ph[0]);
         cudaEventCreate(&c->ev_pair_ph[1]);
         c->Dcap = (P.sampler == RBSOG_SAMPLER_IID) ? 2 * P.P : P.P + 1;
