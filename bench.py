@@ -38,6 +38,11 @@ FP32_LANES = 128              # FP32 FMA lanes per SM
 # special-function unit, ~67 FP32 operations
 PAIR_MUFU_PER_UNIT = 11
 PAIR_FP32_PER_UNIT = 67
+# FP64 build: the same unit on the FP64 pipe (2 DFMA lanes per SM per clock, 1/64 of FP32): 67
+# arithmetic operations plus 10 exponentials and one reciprocal square root, each counted as 14
+# FMAs (range reduction and a degree-11 polynomial, the textbook form of a double exp)
+FP64_LANES = 2
+PAIR_FP64_PER_UNIT = 67 + 11 * 14
 
 
 def workload(name: str, rank: int = 0):
@@ -394,7 +399,19 @@ def main():
     sm_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     clocks = clock_summary(clk_path, local) if rank == 0 else None
     roof = None
-    if pair_ms:
+    if pair_ms and prec != R.RBSOG_FP32:
+        fp64_peak = SM_COUNT * FP64_LANES * sm_clk / 1e12
+        t_fp64 = half_pairs * PAIR_FP64_PER_UNIT / (fp64_peak * 1e12)
+        achieved = half_pairs * PAIR_FP64_PER_UNIT / (pair_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_pair_f64", "achieved": achieved, "peak": fp64_peak,
+                "unit": "Top/s (FP64 pipe)", "frac": achieved / fp64_peak,
+                "traffic": pair_traffic(args.workload, prec), "units_per_launch": half_pairs,
+                "per_unit": f"{PAIR_FP64_PER_UNIT} FP64 operations per half-pair inside r_c",
+                "peak_basis": f"{SM_COUNT} SMs x {FP64_LANES} FP64 lanes/clk x {sm_clk / 1e6:.0f} MHz "
+                              f"(max clock); roofline time {t_fp64 * 1e6:.1f} us",
+                "launch_ms": pair_ms, "launch_ms_p50": float(np.percentile(pair_trace, 50)),
+                "timing": "CUDA events recorded by the step graph around each timed pair launch"}
+    elif pair_ms:
         # bound: max(MUFU work / MUFU peak, FP32 work / FP32 peak); on this part the FP32 side binds
         mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clk / 1e12
         fp32_peak = SM_COUNT * FP32_LANES * sm_clk / 1e12
@@ -404,7 +421,7 @@ def main():
         per = PAIR_FP32_PER_UNIT if fp32_bound else PAIR_MUFU_PER_UNIT
         peak = fp32_peak if fp32_bound else mufu_peak
         achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_pair_f32" if prec == R.RBSOG_FP32 else "k_pair_f64",
+        roof = {"bound": "alu", "kernel": "k_pair_build + k_pair_eval",
                 "achieved": achieved, "peak": peak,
                 "unit": "Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)",
                 "frac": achieved / peak, "traffic": pair_traffic(args.workload, prec),

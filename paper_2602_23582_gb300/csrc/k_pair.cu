@@ -516,8 +516,8 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
                 // original positions (the energy kernel N is about 2e-3 / A at r_c,
                 // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
                 if (__float_as_int(pjc.w) != __float_as_int(pi.w) &&   // not of one molecule
-                    (r2 < pc.rc2_lo ||
-                     inside_cutoff_fp64(r, sidx[ks], sidx[ec & 0x1ffffffu], d.L, pc.rc2d)))
+                    (r2 < pc.rc2_lo || (r2 < pc.rc2_hi &&
+                     inside_cutoff_fp64(r, sidx[ks], sidx[ec & 0x1ffffffu], d.L, pc.rc2d))))
                     pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qjc, acc);
             }
         }

@@ -820,8 +820,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             for (int k = 0; k < S; ++k)
                 entries += (double)caps[k].atoms * 1.25 * (4.0 / 3.0) * kPi * P.rc * P.rc * P.rc * caps[k].rho / 1.5;
             const double chunks = std::ceil(entries / kListChunk) + (double)N * span + 64.0;
-            if (chunks * kListChunk >= 2147483647.0) {
-                rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "pair lists beyond 2^31 entries");
+            if (chunks >= 2147483647.0) {
+                rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "pair lists beyond 2^31 chunks");
                 free_ctx(c);
                 return rr;
             }
