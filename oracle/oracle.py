@@ -66,6 +66,7 @@ class _Integ(C.Structure):
 
 def _declare(L):
     L.orc_sog_terms.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _D, _D, _D, _D]
+    L.orc_nr_shared.argtypes = [_D, C.c_int, C.c_int, _I, _I, _D, C.c_int, _D, _D, C.c_double, C.c_double, _D]
     L.orc_sog_solve.argtypes = [C.c_double, C.c_double, _D, _D, _D]
     L.orc_sog_solve.restype = C.c_int
     L.orc_bsa.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]
@@ -315,6 +316,20 @@ def rb_longrange(pos, q, L, P, D, cr, cnr, Sr, Snr, ke=KE):
     lib().orc_rb_longrange(n, _pd(pos), _pd(q), _pd(_d(L)), P, len(D), _pi(D), _pi(_i(cr)),
                            _pi(_i(cnr)), Sr, Snr, ke, _pd(F), _pd(U), _pd(Wr), _pd(Wnr), _pd(rh))
     return F, U[0], Wr.reshape(3, 3), Wnr.reshape(3, 3), rh[0::2] + 1j * rh[1::2]
+
+
+def nr_shared(L, params: Params, D, cr, rh, Sr):
+    """V P^{F,nr} by the shared-proposal estimator (sec. 3.2): the radial
+    samples (multiplicities cr over the distinct modes D, structure factors rh)
+    reused for the non-radial part with weights f_nr / P^r."""
+    w, s, wt, st = sog_terms(params.b, params.sigma, params.omega, params.M)
+    D = _i(D)
+    rr = np.zeros(2 * len(D))
+    rr[0::2], rr[1::2] = np.real(rh), np.imag(rh)
+    out = np.zeros(9)
+    lib().orc_nr_shared(_pd(_d(L)), params.P, len(D), _pi(D), _pi(_i(cr)), _pd(rr), params.M, _pd(wt), _pd(st),
+                        Sr, params.ke, _pd(out))
+    return out.reshape(3, 3)
 
 
 def self_energy(params: Params, q):

@@ -25,6 +25,8 @@
  *   orc_rho              eq. rho_k
  *   orc_rb_longrange     eqs. P_approx_r, P_approx_nr, f_approx (App. B),
  *                        U_long estimated with the same radial samples
+ *   orc_nr_shared        sec. 3.2: the shared-proposal (non-recalibrated)
+ *                        estimator of eq. PcoulFnr from the radial samples
  *   orc_self_energy      App. A (U_self)
  *   orc_exclusions       intramolecular pairs removed from the Fourier part
  *   orc_bonded           harmonic bonds and angles
@@ -940,6 +942,38 @@ void orc_rb_longrange(int N, const double *r, const double *q, const double L[3]
         double c = -ke * (0.5 * Sr) / P * q[i] / V;
         for (int a = 0; a < 3; ++a) F[3 * i + a] += c * f[a];
     }
+}
+
+/* Shared-proposal estimator of the non-radial virial (sec. 3.2, the
+ * alternative the measure recalibration replaces): the P radial samples of
+ * P^r (eq. samplingP) are reused for eq. PcoulFnr with importance weight
+ * f_nr(k) / P^r(k) = S^r k^2 R(k), where f_nr is the unnormalised P^nr of
+ * eq. samplingPnr and R(k) = sum_l w~_l s~_l^7 e^{-s~_l^2 k^2/4} /
+ * sum_l w~_l s~_l^5 e^{-s~_l^2 k^2/4}:
+ *   V P^F,nr,sh = -ke S^r /(8 V P) sum_d c_r R(k_d) |rho_d|^2 k (x) k / k^2.
+ * rho as returned by orc_rb_longrange (or orc_rho).  W: 9 values, kcal/mol. */
+void orc_nr_shared(const double L[3], int P, int nD, const int *D, const int *cr, const double *rho,
+                   int M, const double *wt, const double *st, double Sr, double ke, double *W)
+{
+    const double V = L[0] * L[1] * L[2];
+    double B[9] = {0};
+    for (int d = 0; d < nD; ++d) {
+        if (!cr[d]) continue;
+        double k[3];
+        for (int a = 0; a < 3; ++a) k[a] = 2.0 * ORC_PI * D[3 * d + a] / L[a];
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double num = 0, den = 0;
+        for (int l = 0; l < M; ++l) {
+            double e = exp(-st[l] * st[l] * k2 / 4.0);
+            double s5 = pow(st[l], 5);
+            den += wt[l] * s5 * e;
+            num += wt[l] * s5 * st[l] * st[l] * e;
+        }
+        double r2 = rho[2 * d] * rho[2 * d] + rho[2 * d + 1] * rho[2 * d + 1];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) B[3 * a + b] += cr[d] * (num / den) * r2 * k[a] * k[b] / k2;
+    }
+    for (int a = 0; a < 9; ++a) W[a] = -ke * Sr / (8.0 * V * P) * B[a];
 }
 
 /* App. A: U_self = ln b /(sqrt(2 pi) sigma) (omega + (1 - b^{-(M-1)})/(b - 1)) sum q^2, times ke. */

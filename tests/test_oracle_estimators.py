@@ -158,3 +158,44 @@ def test_bonded_forces_are_minus_gradient():
     E[0, 1] -= 2e-6
     um = O.bonded(s, pos=pos @ E.T, h=E @ np.diag(s.box))[1].sum()
     assert abs(-(up - um) / 2e-6 - Wb[0, 1]) < 1e-5 * (1 + np.abs(Wb).max())
+
+
+def _shared_stats(sys, kind, P, nseed):
+    p = O.Params.row2(P=P, kind=kind)
+    w, s, wt, st = O.sog_terms(p.b, p.sigma, p.omega, p.M)
+    Hr, Hnr, *_ = O.normalizers(sys.box, wt, st)
+    out = []
+    for step in range(nseed):
+        mr, mn, _ = O.sample_modes(sys.box, p, step)
+        D, cr, cnr = O.distinct(mr, mn)
+        rh = O.rho(sys.pos, sys.q, sys.box, D)
+        out.append(O.nr_shared(sys.box, p, D, cr, rh, Hr.sum()).reshape(-1))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kind", [1, 0])
+def test_shared_proposal_nonradial_unbiased(tiny, exact, kind):
+    # sec. 3.2: the radial samples reused for P^F,nr with weights f_nr / P^r
+    # estimate the same tensor (every radial state is P^r-distributed)
+    Fall, Uall, Wall, Wrad = exact
+    Wsh = _shared_stats(tiny, kind, 100, NSEED)
+    Wnr_ref = (Wall - Wrad * np.eye(3)).reshape(-1)
+    z, ok = _within(Wsh[:, [0, 1, 2, 4, 5, 8]], Wnr_ref[[0, 1, 2, 4, 5, 8]], k=4.0)
+    assert ok, z
+
+
+def test_shared_proposal_weight_is_the_target_ratio(tiny):
+    # one mode, multiplicity 1: the estimator equals -ke S^r/(8 V P) (f_nr/f_r) |rho|^2 k k / k^4,
+    # with f_r, f_nr the unnormalised targets of eqs. samplingP, samplingPnr (oracle targets())
+    p = O.Params.row2(P=7)
+    w, s, wt, st = O.sog_terms(p.b, p.sigma, p.omega, p.M)
+    Hr, Hnr, *_ = O.normalizers(tiny.box, wt, st)
+    D = np.array([[1, -2, 3]], np.int32)
+    rh = O.rho(tiny.pos, tiny.q, tiny.box, D)
+    Wsh = O.nr_shared(tiny.box, p, D, np.array([1], np.int32), rh, Hr.sum())
+    fr, fnr, _ = O.targets(tiny.box, p, D[0])
+    k = 2 * np.pi * D[0] / np.asarray(tiny.box)
+    k2 = k @ k
+    V = float(np.prod(tiny.box))
+    ref = -p.ke * Hr.sum() / (8 * V * p.P) * (fnr / fr) * abs(rh[0]) ** 2 * np.outer(k, k) / k2 ** 2
+    assert np.allclose(Wsh, ref, rtol=1e-12, atol=0)
