@@ -32,6 +32,7 @@ METRIC = "RBSOG atom-steps/s on 1 GB300 (plain vs batched); p50/p99 step latency
 UNIT = "atom-steps/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
+NKTV2P = 68568.415           # atm per kcal/(mol A^3) (LAMMPS real units)
 MUFU_PER_SM_CLK = 32          # ex2 results per SM per clock on this part (probe: 30.3 at 2070 MHz)
 FP32_LANES = 128              # FP32 FMA lanes per SM
 # algorithmic work per half-pair inside r_c (M~ = 10): 10 exp + 1 rsqrt on the
@@ -147,6 +148,46 @@ def cpu_baseline(systems, budget_s=15.0):
     return {"value": s.n * steps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": f"{steps} NPT steps of the {s.n}-site workload (all-pairs short range, FP64), "
                       f"{dt:.1f} s"}
+
+
+def variance_study(R, prec, names=("ionic_liquid", "membrane"), Ps=(100, 400), nseed=1000):
+    """Variance of the non-radial long-range pressure for three estimators on
+    fixed configurations, nseed Philox counters each (sec. 3.2):
+    (i) the measure-recalibrated estimator (the paper's sampler),
+    (ii) the shared-proposal estimator (the radial samples reweighted),
+    (iii) independent exact P^nr sampling with 2P modes.
+    Returns per workload and P the variances of the six components of
+    P^F,nr (atm^2) and the ratios (ii)/(i), (iii)/(i)."""
+    out = {}
+    comp = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for name in names:
+        systems, _ = workload(name)
+        s = systems[0]
+        V = float(np.prod(s.box))
+        for P in Ps:
+            est = {"recalibrated": [], "shared": [], "iid_2P": []}
+            ctx = R.Context([s], R.rbsog_default_params(10.0, precision=prec, P=P))
+            for k in range(nseed):
+                _, res = ctx.step(k)
+                est["recalibrated"].append(res[0]["virial_long_nr"])
+                est["shared"].append(ctx.virial_nr_shared()[0])
+            ctx.close()
+            ctx = R.Context([s], R.rbsog_default_params(10.0, precision=prec, P=2 * P,
+                                                        sampler=R.RBSOG_SAMPLER_IID))
+            for k in range(nseed):
+                _, res = ctx.step(k)
+                est["iid_2P"].append(res[0]["virial_long_nr"])
+            ctx.close()
+            rec = {}
+            for key, v in est.items():
+                a = np.array([np.asarray(x).reshape(3, 3) for x in v]) / V * NKTV2P
+                c = np.array([a[:, i, j] for i, j in comp]).T
+                rec[key] = {"mean_atm": c.mean(0).tolist(), "var_atm2": c.var(0, ddof=1).tolist()}
+            vi = np.array(rec["recalibrated"]["var_atm2"])
+            for key in ("shared", "iid_2P"):
+                rec[key]["var_over_recalibrated"] = (np.array(rec[key]["var_atm2"]) / vi).tolist()
+            out[f"{name}_P{P}"] = rec
+    return {"components": ["xx", "yy", "zz", "xy", "xz", "yz"], "seeds": nseed, "results": out}
 
 
 def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
@@ -268,6 +309,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--variance-study", action="store_true",
+                    help="only the estimator variance study (one JSON line), no timing")
     ap.add_argument("--thermo", type=int, default=100,
                     help="energies every this many steps (as MD thermo output); forces and the "
                          "virial are computed every step either way")
@@ -290,6 +333,11 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_2602_23582_gb300 import rbsog as R
+    if args.variance_study:
+        if rank == 0:
+            prec = R.RBSOG_FP32 if args.precision == "fp32" else R.RBSOG_FP64
+            print(json.dumps({"variance_study": variance_study(R, prec)}))
+        return
     systems, desc = workload(args.workload, rank)
     for k, s in enumerate(systems):
         s.rng_id = 1000 * rank + k

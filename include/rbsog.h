@@ -238,6 +238,17 @@ rbsog_status rbsog_debug_cells(rbsog_ctx *ctx, int s, int *ncell, int *cell_of_a
 rbsog_status rbsog_debug_modes(rbsog_ctx *ctx, int s, int *mr, int *mnr, int *D, int *cr,
                                int *cnr, int *nD, double *S, double *rho);
 
+/* Shared-proposal estimator of the non-radial long-range virial (sec. 3.2:
+ * the P radial samples of the last evaluation reused for eq. PcoulFnr with
+ * importance weights f_nr / P^r = S^r k^2 R(k), R(k) = sum_l w~_l s~_l^7
+ * e^{-s~_l^2 k^2/4} / sum_l w~_l s~_l^5 e^{-s~_l^2 k^2/4}; the alternative that
+ * the measure recalibration replaces).  out (host, n_systems x 9 doubles):
+ * V P^F,nr,sh of every system, kcal/mol, row-major.  For comparing
+ * estimators; the MD step does not use it.  Needs a previous evaluation
+ * (rbsog_step, rbsog_run); runs on the context stream and synchronizes it.
+ * Errors: RBSOG_EINVAL for a null argument, RBSOG_ECUDA. */
+rbsog_status rbsog_virial_nr_shared(rbsog_ctx *ctx, double *out);
+
 /* Kernel timings of the last rbsog_step / rbsog_run call with timing enabled:
  * enable != 0 records CUDA events around each kernel of one step (slower). */
 rbsog_status rbsog_set_timing(rbsog_ctx *ctx, int enable);

@@ -12,6 +12,8 @@ struct SogConsts {
     int M, ME;                  // Gaussians of force/pressure, energy
     double rc, ke;
     double w[kMaxGauss], s[kMaxGauss], wt[kMaxGauss], st[kMaxGauss];
+    // FP32 copies for the FP32 build's exclusion terms: w~_l, w_l, 1/s~_l^2, 1/s_l^2
+    float wtf[kMaxGauss], wf[kMaxGauss], ist2f[kMaxGauss], is2f[kMaxGauss];
 };
 
 constexpr int kTail = 7;        // degree (in u = r^2) of the Taylor tail of the wide Gaussians
@@ -153,6 +155,10 @@ int estimate_blocks(int Dcap);
 // F = pair partials + long-range force + Fmol (molecule terms; null: none)
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
                      int Dcap, const double *Fmol, cudaStream_t st);
+// V P^F,nr by the shared-proposal estimator (sec. 3.2) over the modes of the
+// last evaluation: out[S x 9] (row-major 3 x 3, kcal/mol)
+void launch_nr_shared(const Batch &b, const int *D, const int *cr, const double *rho, int Dcap, int P, double ke,
+                      const SamplerArgs &sa, double *out, cudaStream_t st);
 size_t sk_stateless_workspace(int n, int nD);
 // k_sk_static.cu: a fixed scratch for the allocation-free variant
 constexpr size_t kSkStaticBytes = (size_t)4 << 20;

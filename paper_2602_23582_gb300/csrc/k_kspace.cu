@@ -347,6 +347,59 @@ void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const M
                                                      coef, Dcap, a.rank, a.fpartd, nparts, b.N, Fmol, a.F);
 }
 
+// Shared-proposal estimator of the non-radial virial (sec. 3.2, the
+// alternative the measure recalibration replaces): the radial samples reused
+// for P^F,nr with weights f_nr / P^r = S^r k^2 R(k), R(k) = sum_l cn_l e_l /
+// sum_l cr_l e_l, e_l = e^{-s~_l^2 k^2 / 4} (eqs. samplingP, samplingPnr):
+//   V P^F,nr,sh = -ke S^r / (8 V P) sum_d c_r[d] R(k_d) |rho_d|^2 k (x) k / k^2
+// over the modes and structure factors of the last evaluation.  One block per
+// system; used to compare estimators, not part of the MD step.
+constexpr int kNrShThreads = 128;
+
+__global__ void __launch_bounds__(kNrShThreads)
+k_nr_shared(const DevSys *__restrict__ sys, const int *__restrict__ D_all, const int *__restrict__ cr_all,
+            const double *__restrict__ rho_all, int Dcap, int P, double ke, const SamplerArgs sa,
+            double *__restrict__ out)
+{
+    __shared__ double red[6 * (kNrShThreads + 1) + 24];
+    __shared__ double tot[6];
+    const int s = blockIdx.x;
+    const DevSys &d = sys[s];
+    const int nD = live_n(d) > 0 ? d.nD : 0;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < nD; k += blockDim.x) {
+        const int *Dk = D_all + ((size_t)s * Dcap + k) * 3;
+        const double kx = kTwoPi * Dk[0] / d.L[0], ky = kTwoPi * Dk[1] / d.L[1], kz = kTwoPi * Dk[2] / d.L[2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        double a = 0.0, b = 0.0;
+        for (int l = 0; l < sa.M; ++l) {
+            const double e = exp(-(sa.st2q[l] * k2));
+            a += sa.cr[l] * e;
+            b += sa.cn[l] * e;
+        }
+        const double *rh = rho_all + ((size_t)s * Dcap + k) * 2;
+        const double g = cr_all[(size_t)s * Dcap + k] * (b / a) * (rh[0] * rh[0] + rh[1] * rh[1]) / k2;
+        v[0] += g * kx * kx; v[1] += g * ky * ky; v[2] += g * kz * kz;
+        v[3] += g * kx * ky; v[4] += g * kx * kz; v[5] += g * ky * kz;
+    }
+    block_reduce_lanes<6, kNrShThreads>(v, red, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double c = -ke * d.Sr / (8.0 * (d.L[0] * d.L[1] * d.L[2]) * P);
+        double *o = out + (size_t)s * 9;
+        o[0] = c * tot[0]; o[4] = c * tot[1]; o[8] = c * tot[2];
+        o[1] = o[3] = c * tot[3];
+        o[2] = o[6] = c * tot[4];
+        o[5] = o[7] = c * tot[5];
+    }
+}
+
+void launch_nr_shared(const Batch &b, const int *D, const int *cr, const double *rho, int Dcap, int P, double ke,
+                      const SamplerArgs &sa, double *out, cudaStream_t st)
+{
+    k_nr_shared<<<b.S, kNrShThreads, 0, st>>>(b.sys, D, cr, rho, Dcap, P, ke, sa, out);
+}
+
 // ---------------------------------------------------------------------------
 // stateless structure factor on caller buffers
 // ---------------------------------------------------------------------------

@@ -98,6 +98,7 @@ struct rbsog_ctx {
     int *mr = nullptr, *mnr = nullptr, *D = nullptr, *cr = nullptr, *cnr = nullptr;
     int4 *pm = nullptr;
     SampScratch *samp = nullptr;
+    double *nrsh = nullptr;     // [S x 9] shared-proposal estimator output
     double *pw = nullptr, *pg = nullptr, *pu = nullptr, *pun = nullptr;
     double *sk_part = nullptr, *rho = nullptr;
     ModeCoef *coef = nullptr;
@@ -797,7 +798,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
                   dalloc(c, c->mr, (size_t)S * P.P * 3) && dalloc(c, c->mnr, (size_t)S * P.P * 3) &&
                   dalloc(c, c->D, (size_t)S * c->Dcap * 3) && dalloc(c, c->cr, (size_t)S * c->Dcap) &&
-                  dalloc(c, c->cnr, (size_t)S * c->Dcap) && dalloc(c, c->pm, (size_t)S * P.P) && dalloc(c, c->samp, (size_t)S) &&
+                  dalloc(c, c->cnr, (size_t)S * c->Dcap) && dalloc(c, c->pm, (size_t)S * P.P) && dalloc(c, c->samp, (size_t)S) && dalloc(c, c->nrsh, (size_t)S * 9) &&
                   dalloc(c, c->pw, (size_t)S * P.P) && dalloc(c, c->pg, (size_t)S * P.P) &&
                   dalloc(c, c->pu, (size_t)S * P.P) && dalloc(c, c->pun, (size_t)S * P.P) &&
                   dalloc(c, c->sk_part, (size_t)c->nchunks * c->Dcap * 2) &&
@@ -839,7 +840,11 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
 
         // ---- constants
         c->sc.M = P.M; c->sc.ME = P.M_energy; c->sc.rc = P.rc; c->sc.ke = P.ke;
-        for (int l = 0; l < MM; ++l) { c->sc.w[l] = w[l]; c->sc.s[l] = s[l]; c->sc.wt[l] = wt[l]; c->sc.st[l] = st[l]; }
+        for (int l = 0; l < MM; ++l) {
+            c->sc.w[l] = w[l]; c->sc.s[l] = s[l]; c->sc.wt[l] = wt[l]; c->sc.st[l] = st[l];
+            c->sc.wf[l] = (float)w[l]; c->sc.wtf[l] = (float)wt[l];
+            c->sc.is2f[l] = (float)(1.0 / (s[l] * s[l])); c->sc.ist2f[l] = (float)(1.0 / (st[l] * st[l]));
+        }
         c->pcf.M = c->pcd.M = P.M;
         c->pcf.ME = c->pcd.ME = P.M_energy;
         c->pcf.rc2 = (float)(P.rc * P.rc); c->pcd.rc2 = P.rc * P.rc; c->pcf.rc2d = P.rc * P.rc;
@@ -1338,6 +1343,18 @@ rbsog_status rbsog_debug_modes(rbsog_ctx *c, int s, int *mr, int *mnr, int *D, i
     if (e != cudaSuccess) return cuda_fail(c, e, "debug_modes");
     if (nD) *nD = h.nD;
     if (S2) { S2[0] = h.Sr; S2[1] = h.Snr; }
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_virial_nr_shared(rbsog_ctx *c, double *out)
+{
+    if (!c || !out) return RBSOG_EINVAL;
+    launch_nr_shared(c->b, c->D, c->cr, c->rho, c->Dcap, c->prm.P, c->prm.ke, c->sa, c->nrsh, c->st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, c->nrsh, sizeof(double) * 9 * (size_t)c->S, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "virial_nr_shared");
     return RBSOG_OK;
 }
 

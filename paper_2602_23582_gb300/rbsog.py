@@ -29,7 +29,7 @@ E_NAMES = ("coul_short", "coul_long", "coul_self", "coul_excl", "lj", "bond", "a
 EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_error", "rbsog_n_atoms",
            "rbsog_system_range", "rbsog_set_box", "rbsog_set_positions", "rbsog_get_positions",
            "rbsog_get_velocities", "rbsog_step", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
-           "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_set_timing", "rbsog_get_timing",
+           "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_virial_nr_shared", "rbsog_set_timing", "rbsog_get_timing",
            "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
            "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc", "rbsog_trace_pair",
            "rbsog_trace_pair_times", "rbsog_set_thermo_every", "rbsog_pool_create", "rbsog_pool_load",
@@ -119,6 +119,7 @@ def lib():
     L.rbsog_set_state.argtypes = [P, P, C.c_size_t]
     L.rbsog_debug_cells.argtypes = [P, C.c_int, _I, _I]
     L.rbsog_debug_modes.argtypes = [P, C.c_int, _I, _I, _I, _I, _I, _I, _D, _D]
+    L.rbsog_virial_nr_shared.argtypes = [P, _D]
     L.rbsog_set_timing.argtypes = [P, C.c_int]
     L.rbsog_get_timing.argtypes = [P, C.c_int, C.c_char_p, _D, _I]
     L.rbsog_structure_factor_workspace.argtypes = [C.c_int, C.c_int]
@@ -298,6 +299,12 @@ def rbsog_debug_modes(ctx, s, P, Dcap):
     n = nD.value
     return dict(mr=mr, mnr=mnr, D=D[:n].copy(), cr=cr[:n].copy(), cnr=cnr[:n].copy(), Sr=S2[0],
                 Snr=S2[1], rho=rho[0:2 * n:2] + 1j * rho[1:2 * n:2])
+
+
+def rbsog_virial_nr_shared(ctx, n_systems):
+    out = np.zeros((n_systems, 3, 3))
+    _check(lib().rbsog_virial_nr_shared(ctx, out.ctypes.data_as(_D)), ctx)
+    return out
 
 
 def rbsog_set_timing(ctx, enable=True):
@@ -567,3 +574,7 @@ class Context:
 
     def modes(self, s=0):
         return rbsog_debug_modes(self.ctx, s, self.params.P, self.Dcap)
+
+    def virial_nr_shared(self):
+        """V P^F,nr of the last evaluation by the shared-proposal estimator (S, 3, 3)."""
+        return rbsog_virial_nr_shared(self.ctx, self.S)

@@ -237,3 +237,23 @@ def test_run_is_deterministic():
         out.append(ctx.positions())
         ctx.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec,tol", [(R.RBSOG_FP64, 1e-10), (R.RBSOG_FP32, 2e-6)])
+@pytest.mark.parametrize("name", ["electrolyte", "ragged"])
+def test_shared_proposal_estimator_matches_oracle(name, prec, tol):
+    # sec. 3.2: the radial samples of one evaluation reweighted for P^F,nr
+    s = SYSTEMS[name]()
+    ctx, p = _ctx([s], prec)
+    ctx.step(5)
+    g = ctx.virial_nr_shared()[0]
+    ctx.close()
+    op = _oracle_params(p)
+    mr, mn, _ = O.sample_modes(s.box, op, 5)
+    D, cr, cnr = O.distinct(mr, mn)
+    rh = O.rho(s.pos, s.q, s.box, D)
+    w, sg, wt, st = O.sog_terms(p.b, p.sigma, p.omega, p.M)
+    Hr, Hnr, *_ = O.normalizers(s.box, wt, st)
+    ref = O.nr_shared(s.box, op, D, cr, rh, Hr.sum())
+    assert np.allclose(g, g.T, rtol=0, atol=0)
+    assert _rel(g, ref) < tol
