@@ -140,9 +140,9 @@ __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, c
 // kSmallTerms terms is one thread's (its terms in order: bonds, angles,
 // exclusions, each added to its atoms' forces at once).  A larger molecule is
 // one warp's: its terms are spread over the lanes in passes of kTermPass,
-// each term stores its atoms' contributions in shared memory, and the lane
-// that holds an atom's first contribution of the pass adds them all in term
-// order and adds the sum to F.  F is zeroed by the caller; a molecule's atoms
+// each term stores its atoms' contributions in shared memory (in R), and the
+// lane that holds an atom's first contribution of the pass adds them all in
+// term order and adds the sum to F.  F is zeroed by the caller; a molecule's atoms
 // are written by its thread or warp only, and every sum runs in a fixed
 // order.  R is the arithmetic type of the exclusion terms (float in the FP32
 // build): differences of positions are formed in FP64, then rounded.
@@ -162,7 +162,7 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     constexpr int NT = 32 * kMolWarps, NS = 3 * kTermPass;
     __shared__ double red[15 * (NT + 1) + 60];
     __shared__ int s_atom[kMolWarps][NS];
-    __shared__ double s_f[kMolWarps][NS][3];
+    __shared__ R s_f[kMolWarps][NS][3];         // contributions in R: FP32 adds in the FP32 build
     const int c = blockIdx.x, w = threadIdx.x >> 5, lane = lane_id();
     const DevSys &d = sys[mchunk_sys[c]];
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
@@ -192,7 +192,7 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     }
     // large molecules: one warp each, in chunk order over the warps
     int *sa = s_atom[w];
-    double (*sf)[3] = s_f[w];
+    R (*sf)[3] = s_f[w];
     int big = 0;                                       // large molecules seen so far (warp-uniform)
     for (int k = 0; k < nm; ++k) {
         const int mi = m0 + k;
@@ -215,7 +215,8 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
                 }
                 for (int v = 0; v < 3; ++v) {
                     sa[3 * u + v] = v < tf.n ? tf.atom[v] : -1;
-                    if (v < tf.n) { sf[3 * u + v][0] = tf.f[v][0]; sf[3 * u + v][1] = tf.f[v][1]; sf[3 * u + v][2] = tf.f[v][2]; }
+                    if (v < tf.n)
+                        for (int x = 0; x < 3; ++x) sf[3 * u + v][x] = (R)tf.f[v][x];
                 }
             }
             __syncwarp();
@@ -226,18 +227,20 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
                 bool first = true;
                 for (int u = 0; u < sl && first; ++u) first = sa[u] != at;
                 if (!first) continue;
-                // the next matching slot is found by an integer scan, so that the
-                // FP64 adds of all owning lanes issue together (an FP64 warp
+                // the adds run in R: in the FP32 build no FP64 instruction is
+                // issued here, where few lanes are active (an FP64 warp
                 // instruction costs the same for one lane as for 32)
-                double g[3] = {sf[sl][0], sf[sl][1], sf[sl][2]};
+                R g[3] = {sf[sl][0], sf[sl][1], sf[sl][2]};
                 for (int u = sl + 1;; ++u) {
                     while (u < 3 * np && sa[u] != at) ++u;
                     if (u >= 3 * np) break;
                     g[0] += sf[u][0]; g[1] += sf[u][1]; g[2] += sf[u][2];
                 }
-                F[3 * at] += g[0];
-                F[3 * at + 1] += g[1];
-                F[3 * at + 2] += g[2];
+                const double gd[3] = {(double)g[0], (double)g[1], (double)g[2]};
+                const double f0 = F[3 * at], f1 = F[3 * at + 1], f2 = F[3 * at + 2];
+                F[3 * at] = f0 + gd[0];
+                F[3 * at + 1] = f1 + gd[1];
+                F[3 * at + 2] = f2 + gd[2];
             }
             __syncwarp();
         }
