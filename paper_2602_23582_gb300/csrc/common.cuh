@@ -20,7 +20,7 @@ constexpr int kMaxGauss = 64;      // Gaussians of the split, M and M_energy
 constexpr int kMaxP = 4096;        // batch size
 constexpr int kCellCap = 2048;     // atoms per cell the kernels accept
 constexpr int kChunk = 1024;       // atoms per chunk of the per-atom kernels
-constexpr int kMolChunk = 32;      // molecules per block of the molecule kernel
+constexpr int kMolChunk = 16;      // molecules per block of the molecule kernel
 constexpr int kMaxTypes = 16;
 
 // status flags written by kernels (bit mask in DevSys::flags)
