@@ -269,11 +269,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     systems, desc = workload(args.workload)
+    desc = desc.replace("P=100", f"P={args.P}")
     s = systems[0]
     from oracle import oracle as O
     budget = max(5.0, 60.0 / max(args.steps + args.warmup, 1))
     times = []
-    p = O.Params.row2(P=100)
+    p = O.Params.row2(P=args.P)
     out = O.force_eval(s, p, 0)
     st = dict(r=s.pos.copy(), p=np.zeros_like(s.pos), L=s.box.copy(), ph=np.zeros(3),
               F=out["F"], W=out["W"].reshape(-1).copy())
@@ -309,6 +310,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--P", type=int, default=100, help="Fourier modes per step (batch size)")
     ap.add_argument("--variance-study", action="store_true",
                     help="only the estimator variance study (one JSON line), no timing")
     ap.add_argument("--thermo", type=int, default=100,
@@ -339,11 +341,12 @@ def main():
             print(json.dumps({"variance_study": variance_study(R, prec)}))
         return
     systems, desc = workload(args.workload, rank)
+    desc = desc.replace("P=100", f"P={args.P}")
     for k, s in enumerate(systems):
         s.rng_id = 1000 * rank + k
     prec = R.RBSOG_FP32 if args.precision == "fp32" else R.RBSOG_FP64
     stream = torch.cuda.Stream(device=dev)
-    p = R.rbsog_default_params(10.0, precision=prec, thermo_every=args.thermo)
+    p = R.rbsog_default_params(10.0, precision=prec, thermo_every=args.thermo, P=args.P)
     ctx = R.Context(systems, p, stream=stream.cuda_stream)
     n_atoms = ctx.n_atoms
 
