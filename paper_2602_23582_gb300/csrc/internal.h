@@ -63,17 +63,16 @@ struct Batch {
     const int *item_sys;        // [item_cap] system of each work item index
 };
 
-// FP32 pair lists: per (work unit = group x dz plane, lane) a chain of
-// kListChunk-entry chunks from a pool of cap_chunks; an entry is (index of
-// the first of 32 candidates | neighbour-cell code << 25, hit mask).
-constexpr int kListChunk = 16;
+// FP32 pair lists: for dz plane p of the stencil and cell-sorted atom i,
+// entries ent[(p * maxent + k) * ncap + i], k < nent[p * ncap + i], holding
+// nhit[p * ncap + i] hits; an entry is (index of the first of 32 candidates |
+// neighbour-cell code << 25, hit mask).
 constexpr int kEvalSplit = 3;   // FP32 evaluation warps (hit segments) per 32-atom group
 struct PairList {
-    uint2 *ent;                 // [cap_chunks * kListChunk]
-    int *next;                  // [cap_chunks] next chunk of the same list
-    int *head, *nent, *nhit;    // [units * 32] first chunk, entries and hits of each list
-    int *top;                   // [1] chunks taken this step
-    int cap_chunks;
+    uint2 *ent;                 // [span * maxent * ncap]
+    int *nent, *nhit;           // [span * ncap]
+    int maxent;                 // entries per (plane, atom)
+    int ncap;                   // atoms of the context
 };
 
 struct AtomArrays {
@@ -92,8 +91,6 @@ struct AtomArrays {
     double4 *posd;              // [N] sorted, FP64
     int2 *aux;                  // [N] sorted (mol, type)
     int2 *items;                // [item_cap] (cell, group) pair work items
-    int *citem0;                // [C] first work item of each cell
-    int *scell;                 // [N] cell of each cell-sorted atom (FP32 build)
     float4 *fpart4;             // [(2 sub + 1) N] pair forces per dz plane, cell-sorted (FP32 build)
     double4 *fpartd;            // same storage, FP64 build
     // LJ table: system s owns entries [lj0, lj0 + ntypes^2) (DevSys), entry

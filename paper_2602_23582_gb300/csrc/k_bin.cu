@@ -83,8 +83,7 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
 // pass lists the pair kernel's work items (cell, 32-atom group) of the system
 // in [item0, item0 + nitems) and marks the rest of its item range unused.
 __global__ void __launch_bounds__(1024)
-k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, int *__restrict__ citem0,
-       DevSys *sys)
+k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, DevSys *sys)
 {
     __shared__ int ta[1024], tg[1024];
     DevSys &d = sys[blockIdx.x];
@@ -113,7 +112,6 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
     for (int c = c0; c < c1; ++c) {
         const int v = count[C0 + c];
         start[C0 + c] = ra;
-        citem0[C0 + c] = rg;
         ra += v;
         const int ng = (v + 31) >> 5;
         for (int g = 0; g < ng; ++g) items[rg + g] = make_int2(C0 + c, g);
@@ -126,7 +124,7 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
 
 void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st)
 {
-    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, a.citem0, b.sys);
+    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys);
 }
 
 __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ rank,
@@ -146,7 +144,7 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
             int *__restrict__ rank, const float4 *__restrict__ locf, const double4 *__restrict__ locd,
             const double *__restrict__ q, const int *__restrict__ type, const int *__restrict__ mol,
             float4 *__restrict__ pos4, float2 *__restrict__ qt, double4 *__restrict__ posd,
-            int2 *__restrict__ aux, int *__restrict__ scell, int precision)
+            int2 *__restrict__ aux, int precision)
 {
     __shared__ int buf[kSortWarps][kCellCap];
     const int w = threadIdx.x >> 5, lane = lane_id();
@@ -177,7 +175,6 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
         sidx[base + k] = i;
         rank[i] = base + k;          // from here on: cell-sorted position of atom i
         if (precision == 1) {
-            scell[base + k] = c;
             pos4[base + k] = locf[i];
             qt[base + k] = make_float2((float)q[i], __int_as_float(type[i]));
         } else {
@@ -191,8 +188,7 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 {
     k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(a.cell, a.rank, a.start, a.sidx, b.N);
     k_cell_sort<<<(b.C + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, st>>>(
-        a.start, a.count, b.C, a.sidx, a.rank, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, a.scell,
-        precision);
+        a.start, a.count, b.C, a.sidx, a.rank, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
 }
 
 }  // namespace rbsog

@@ -200,25 +200,17 @@ __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, doub
     acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
 }
 
-// Next (base, mask) entry of one lane's hit stream: plane pl, chunk cur,
-// position pos, rem entries left in plane pl; moves to the next plane's list
-// when this one is used up.  The caller asks only for entries that exist.
-__device__ __forceinline__ uint2 next_entry(const PairList &L, int u0i, int &pl, int &rem, int &cur, int &pos)
+// Next (base, mask) entry of atom ks's hit stream: entry k of plane pl, kend
+// entries in plane pl; moves to the next plane with entries when this one is
+// used up.  The caller asks only for entries that exist.
+__device__ __forceinline__ uint2 next_entry(const PairList &L, int ks, int &pl, int &k, int &kend)
 {
-    while (rem == 0) {
+    while (k >= kend) {
         ++pl;
-        rem = L.nent[u0i + pl * 32];
-        cur = L.head[u0i + pl * 32];
-        pos = 0;
+        k = 0;
+        kend = L.nent[pl * L.ncap + ks];
     }
-    const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
-    ++pos;
-    --rem;
-    if (pos == kListChunk && rem > 0) {
-        cur = L.next[cur];
-        pos = 0;
-    }
-    return en;
+    return L.ent[((size_t)pl * L.maxent + k++) * L.ncap + ks];
 }
 
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
@@ -229,13 +221,13 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // FP32 path in two kernels.
 //
 // k_pair_build: work unit = 32-atom group x dz plane of its neighbour cells.
-// The warp walks the plane's cells with warp-broadcast candidate loads; each
-// lane tests its atom against 32 candidates at a time and, when any hit, stores
-// one list entry: (index of the first candidate | neighbour-cell code << 25,
-// 32-bit hit mask).  Entries go to the lane's own list, chunks of kListChunk
-// entries taken from a pool with one atomic per warp for all lanes that need a
-// chunk at once.  A lane's entries keep its candidate order, so the evaluation
-// order does not depend on which chunks it got.
+// The warp walks the plane's cells in batches of 32 candidates; each lane
+// tests its atom against a batch and, when any hit, stores one list entry
+// (index of the first candidate | neighbour-cell code << 25, 32-bit hit
+// mask) at the next place of its (plane, atom) list.  The lists are laid out
+// entry-major over the cell-sorted atoms, ent[(plane * maxent + k) * N + atom],
+// so that the 32 lanes of an evaluation warp read entry k of 32 consecutive
+// atoms together.
 //
 // k_pair_eval: one block per 32 consecutive cell-sorted atoms of one system
 // (whatever their cells, so the lanes are full); warp k takes segment k of
@@ -275,7 +267,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     // lanes without an atom sit far away: their cutoff test never passes
     float4 pi = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     if (vi) pi = pos4[i0 + lane];
-    int cur = -1, fill = kListChunk, first = -1, nent = 0, nhit = 0;
+    int nent = 0, nhit = 0;
     bool overflow = false;
     const int gz = wrapi(cz + ddz, n2);
     // the plane's cells, one per lane: first atom and atom count
@@ -346,45 +338,27 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         nxt = ld ? stage(qn) : far;
         __syncwarp();                                  // cand is rewritten next round
         const unsigned code = (unsigned)(part * nn + bnb) << 25;
-        // lanes whose chunk is full and that have an entry to store take new chunks together
-        const unsigned need = __ballot_sync(0xffffffffu, hm != 0u && fill == kListChunk);
-        if (need) {
-            const int leader = __ffs(need) - 1;
-            int b0 = 0;
-            if (lane == leader) b0 = atomicAdd(L.top, __popc(need));
-            b0 = __shfl_sync(0xffffffffu, b0, leader);
-            if (hm != 0u && fill == kListChunk) {
-                const int c = b0 + __popc(need & ((1u << lane) - 1u));
-                if (c < L.cap_chunks) {
-                    if (cur >= 0) L.next[cur] = c;
-                    else first = c;
-                    cur = c;
-                    fill = 0;
-                } else {
-                    overflow = true;
-                }
+        // an entry for every batch with a hit, at k = nent of this (plane, atom)
+        if (hm != 0u) {
+            if (nent < L.maxent) {
+                L.ent[((size_t)part * L.maxent + nent) * L.ncap + (i0 + lane)] = make_uint2((unsigned)bj | code, hm);
+                ++nent;
+                nhit += __popc(hm);
+            } else {
+                overflow = true;
             }
-        }
-        if (hm != 0u && fill < kListChunk) {
-            L.ent[(size_t)cur * kListChunk + fill] = make_uint2((unsigned)bj | code, hm);
-            ++fill;
-            ++nent;
-            nhit += __popc(hm);
         }
     }
     if (vi) {
-        const size_t k = (size_t)unit * 32 + lane;
-        L.head[k] = first;
-        L.nent[k] = nent;
-        L.nhit[k] = nhit;
+        L.nent[part * L.ncap + i0 + lane] = nent;
+        L.nhit[part * L.ncap + i0 + lane] = nhit;
     }
     if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(&sys[s].flags, (int)FLAG_OVERFLOW);
 }
 
 template <int NF, bool EN>
 __global__ void __launch_bounds__(32 * kEvalSplit, EN ? 4 : 8)
-k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int *__restrict__ start,
-            const int *__restrict__ scell, const int *__restrict__ citem0, const float4 *__restrict__ pos4,
+k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const float4 *__restrict__ pos4,
             const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
             const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N, const PairList L,
             float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
@@ -421,39 +395,24 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
         const bool vi = g32 + lane < nlive;
         float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 pq = make_float2(0.f, 0.f);
-        int u0i = 0;                                   // this lane's list in plane 0
         // this warp takes hits [h0, h1) of the lane's stream (all planes in order)
-        int nh = 0, pl = 0, rem = 0, cur = 0, pos = 0;
+        int nh = 0, pl = 0, k = 0, kend = 0;
         unsigned base = 0u, mask = 0u;
-        // the atom's lists belong to work item (its cell, its 32-atom group
-        // there); an atom beyond the sorted part of an overflowing cell (the
-        // step is flagged and discarded) is left out
-        int unit = -1, o = 0;
         if (vi) {
-            const int c = scell[ks];
-            o = ks - start[c];
-            unit = citem0[c] + (o >> 5);
-        }
-        if (vi && o >= 0 && (unsigned)(unit - d.item0) < (unsigned)d.item_cap) {
-            u0i = unit * span * 32 + (o & 31);
             pi = pos4[ks];
             pq = qt[ks];
             int tot = 0;
-            for (int p2 = 0; p2 < span; ++p2) tot += L.nhit[u0i + (size_t)p2 * 32];
+            for (int p2 = 0; p2 < span; ++p2) tot += L.nhit[p2 * L.ncap + ks];
             const int h0 = (int)((long long)tot * seg / kEvalSplit);
             const int h1 = (int)((long long)tot * (seg + 1) / kEvalSplit);
             nh = h1 - h0;
             if (nh > 0) {
                 int skip = h0;
-                int hp = L.nhit[u0i];
-                while (skip >= hp) { skip -= hp; ++pl; hp = L.nhit[u0i + (size_t)pl * 32]; }
-                rem = L.nent[u0i + (size_t)pl * 32];
-                cur = L.head[u0i + (size_t)pl * 32];
+                int hp = L.nhit[ks];
+                while (skip >= hp) { skip -= hp; ++pl; hp = L.nhit[pl * L.ncap + ks]; }
+                kend = L.nent[pl * L.ncap + ks];
                 while (skip > 0) {                     // walk entries up to hit h0
-                    const uint2 en = L.ent[(size_t)cur * kListChunk + pos];
-                    ++pos;
-                    --rem;
-                    if (pos == kListChunk && rem > 0) { cur = L.next[cur]; pos = 0; }
+                    const uint2 en = L.ent[((size_t)pl * L.maxent + k++) * L.ncap + ks];
                     const int cc = __popc(en.y);
                     if (cc <= skip) {
                         skip -= cc;
@@ -476,12 +435,12 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
         // the current one has started, are loaded while this hit is evaluated
         int left = nh;                                 // hits of this lane still to evaluate
         if (left > 0 && mask == 0u) {
-            const uint2 en = next_entry(L, u0i, pl, rem, cur, pos);
+            const uint2 en = next_entry(L, ks, pl, k, kend);
             base = en.x;
             mask = en.y;
         }
         uint2 nxt = make_uint2(0u, 0u);
-        if (left > __popc(mask)) nxt = next_entry(L, u0i, pl, rem, cur, pos);
+        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, k, kend);
         unsigned e = 0u;
         float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 qj = make_float2(0.f, 0.f);
@@ -492,8 +451,8 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
             qj = qt[e & 0x1ffffffu];
         }
         const int tmax = __reduce_max_sync(0xffffffffu, nh);
-        for (int k = 0; k < tmax; ++k) {
-            if (k < nh) {
+        for (int kk = 0; kk < tmax; ++kk) {
+            if (kk < nh) {
                 const unsigned ec = e;
                 const float4 pjc = pj;
                 const float2 qjc = qj;
@@ -501,7 +460,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
                     if (mask == 0u) {
                         base = nxt.x;
                         mask = nxt.y;
-                        if (left > __popc(mask)) nxt = next_entry(L, u0i, pl, rem, cur, pos);
+                        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, k, kend);
                     }
                     e = base + (unsigned)(__ffs(mask) - 1);
                     mask &= mask - 1u;
@@ -668,11 +627,10 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
     // item_cap is a multiple of kPairWarps per system, so every block lies in one system
     const int units = b.item_cap * (2 * b.sub + 1);
     if (precision == 1) {
-        cudaMemsetAsync(a.plist.top, 0, sizeof(int), st);
         k_pair_build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist,
                                            cf.rc2_hi);
 #define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
-    k_pair_eval<NF, EN><<<b.item_cap, 32 * kEvalSplit, 0, st>>>(b.sys, b.item_sys, a.start, a.scell, a.citem0,    \
+    k_pair_eval<NF, EN><<<b.item_cap, 32 * kEvalSplit, 0, st>>>(b.sys, b.item_sys,                             \
                                                                 a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \
                                                                 b.N, a.plist, a.fpart4, partial, cf)
         if (cf.nff == 4) {

@@ -78,7 +78,7 @@ struct rbsog_ctx {
     double4 *locd = nullptr, *posd = nullptr;
     uint4 *su = nullptr;
     int *count = nullptr, *start = nullptr, *sidx = nullptr, *cell_sys = nullptr;
-    int *item_sys = nullptr, *citem0 = nullptr, *scell = nullptr;
+    int *item_sys = nullptr;
     float2 *qt = nullptr;
     int2 *aux = nullptr, *items = nullptr;
     int *chunk_sys = nullptr, *chunk_a0 = nullptr, *chunk_n = nullptr, *first_chunk = nullptr, *nchunk_sys = nullptr;
@@ -90,7 +90,7 @@ struct rbsog_ctx {
     double4 *fpart = nullptr;   // pair forces per dz plane (FP32 build reads it as float4)
     double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
     uint2 *pl_ent = nullptr;     // FP32 pair lists
-    int *pl_next = nullptr, *pl_head = nullptr, *pl_nent = nullptr, *pl_nhit = nullptr, *pl_top = nullptr;
+    int *pl_nent = nullptr, *pl_nhit = nullptr;
     int plist_cap = 0;
     double *inv_m = nullptr, *sdv = nullptr;   // per-atom integrator constants
     double2 *ljd = nullptr;     // LJ blocks per system
@@ -779,7 +779,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         bool ok = upload(c, c->sys, hsys) && upload(c, c->r, r) && upload(c, c->p, p) && upload(c, c->q, q) &&
                   upload(c, c->mass, mass) && upload(c, c->type, type) && upload(c, c->mol, mol) &&
                   upload(c, c->atom_sys, atom_sys) && upload(c, c->cell_sys, cell_sys) &&
-                  upload(c, c->item_sys, item_sys) && dalloc(c, c->citem0, C) && dalloc(c, c->scell, N) &&
+                  upload(c, c->item_sys, item_sys) &&
                   upload(c, c->chunk_sys, chunk_sys) && upload(c, c->chunk_a0, chunk_a0) &&
                   upload(c, c->chunk_n, chunk_n) && upload(c, c->first_chunk, first_chunk) &&
                   upload(c, c->nchunk_sys, nchunk) && upload(c, c->mchunk_sys, mchunk_sys) &&
@@ -812,25 +812,26 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N);
         }
         if (ok && P.precision == 1) {
-            // FP32 pair lists: 1.25 x the neighbours inside r_c at each slot's
-            // density (room for compression), at least 1.5 hits per entry (a
-            // batch of 32 candidates with any hit usually holds 3-6), plus one
-            // partly filled chunk per atom and dz plane
+            // FP32 pair lists: per (dz plane, atom) one entry per batch of 32
+            // candidates with a hit, at most the batches of the plane's cells:
+            // span^2 cells of at most 1.3 x rho (4/3 r_c / sub)^3 atoms (cells
+            // are between r_c / sub and 4/3 r_c / sub wide) at the slot's
+            // largest density
             const int span = 2 * P.cell_sub + 1;
-            double entries = 0.0;
-            for (int k = 0; k < S; ++k)
-                entries += (double)caps[k].atoms * 1.25 * (4.0 / 3.0) * kPi * P.rc * P.rc * P.rc * caps[k].rho / 1.5;
-            const double chunks = std::ceil(entries / kListChunk) + (double)N * span + 64.0;
-            if (chunks >= 2147483647.0) {
-                rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "pair lists beyond 2^31 chunks");
+            double rho = 0.0;
+            for (int k = 0; k < S; ++k) rho = std::max(rho, caps[k].rho);
+            const double wc = 4.0 / 3.0 * P.rc / P.cell_sub;
+            const double per_cell = std::min((double)kCellCap, 1.3 * rho * wc * wc * wc);
+            const int maxent = span * span * ((int)std::ceil(per_cell / 32.0) + 1);
+            const double total = (double)span * maxent * N;
+            if (total >= 9.0e18) {
+                rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "pair lists too large");
                 free_ctx(c);
                 return rr;
             }
-            c->plist_cap = (int)chunks;
-            const size_t units = (size_t)item_cap * span;
-            ok = dalloc(c, c->pl_ent, (size_t)c->plist_cap * kListChunk) && dalloc(c, c->pl_next, (size_t)c->plist_cap) &&
-                 dalloc(c, c->pl_head, units * 32) && dalloc(c, c->pl_nent, units * 32) &&
-                 dalloc(c, c->pl_nhit, units * 32) && dalloc(c, c->pl_top, 1);
+            c->plist_cap = maxent;
+            ok = dalloc(c, c->pl_ent, (size_t)span * maxent * N) && dalloc(c, c->pl_nent, (size_t)span * N) &&
+                 dalloc(c, c->pl_nhit, (size_t)span * N);
         }
         if (ok) ok = cudaMemset(c->sysred, 0, sizeof(double) * (size_t)S * kRed) == cudaSuccess;
         if (!ok) {
@@ -913,12 +914,11 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->a.r = c->r; c->a.p = c->p; c->a.F = c->F; c->a.q = c->q; c->a.mass = c->mass; c->a.type = c->type;
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
         c->a.su = c->su; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
-        c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items; c->a.citem0 = c->citem0; c->a.scell = c->scell;
+        c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
         c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
-        c->a.plist.ent = c->pl_ent; c->a.plist.next = c->pl_next; c->a.plist.head = c->pl_head;
-        c->a.plist.nent = c->pl_nent; c->a.plist.nhit = c->pl_nhit; c->a.plist.top = c->pl_top;
-        c->a.plist.cap_chunks = c->plist_cap;
+        c->a.plist.ent = c->pl_ent; c->a.plist.nent = c->pl_nent; c->a.plist.nhit = c->pl_nhit;
+        c->a.plist.maxent = c->plist_cap; c->a.plist.ncap = N;
         c->m.nmol = nmolx; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
