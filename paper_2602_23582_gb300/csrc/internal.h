@@ -176,9 +176,11 @@ struct MolArrays {
     int nmchunks;
 };
 // Fmol: per-atom forces of the molecule terms, added to (zeroed by the caller)
+// energy = 0: the FP32 build leaves out the exclusion energy (forces and
+// virials are computed either way)
 void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc, double *Fmol,
                 double *partial /* per mol chunk: Ue, Ub, Ua, W[6] excl, W[6] bonded */, int precision,
-                cudaStream_t st);
+                int energy, cudaStream_t st);
 
 // ---- k_integrate.cu
 struct IntegArgs {

@@ -94,7 +94,7 @@ __device__ __forceinline__ void angle_term(int e, const int *__restrict__ angles
 template <typename R>
 __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, const double *__restrict__ r,
                                           const double *__restrict__ q, const double L[3], const SogConsts &sc,
-                                          R &ue_rem, double &ue, R wx[6], TermF &t)
+                                          int en, R &ue_rem, double &ue, R wx[6], TermF &t)
 {
     const int i = excl[2 * e], j = excl[2 * e + 1];
     double dd[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
@@ -105,16 +105,14 @@ __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, c
     const R qq = (R)(sc.ke * q[i] * q[j]);
     if constexpr (sizeof(R) == 4) {
         // F_E(0) - F_E(r) = sum_l w_l (1 - e^{-r^2/s_l^2}): small, formed without cancellation
-        // FP32 constants only: no FP64 operation or conversion per term
-        float rem = 0.f;
-        for (int l = 0; l < sc.M; ++l) {
-            const float x = (float)r2 * sc.ist2f[l];
-            const float ex = expf(-x);
-            ft = fmaf(sc.wtf[l], ex, (float)ft);
-            rem = fmaf(sc.wf[l], -expm1f(-x), rem);
+        // FP32 constants only: no FP64 operation or conversion per term; the
+        // energy remainder only on energy steps (en)
+        for (int l = 0; l < sc.M; ++l) ft = fmaf(sc.wtf[l], expf(-(float)r2 * sc.ist2f[l]), (float)ft);
+        if (en) {
+            float rem = 0.f;
+            for (int l = 0; l < sc.ME; ++l) rem = fmaf(sc.wf[l], -expm1f(-(float)r2 * sc.is2f[l]), rem);
+            ue_rem += qq * (R)rem;
         }
-        for (int l = sc.M; l < sc.ME; ++l) rem = fmaf(sc.wf[l], -expm1f(-(float)r2 * sc.is2f[l]), rem);
-        ue_rem += qq * (R)rem;
     } else {
         double fe = 0.0, ftd = 0.0;
         for (int l = 0; l < sc.M; ++l) {
@@ -156,7 +154,7 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
       const double *__restrict__ br0, const int *__restrict__ angles, const double *__restrict__ ak,
       const double *__restrict__ at0, const int *__restrict__ excl, const double *__restrict__ r,
       const double *__restrict__ q, double *__restrict__ F /* molecule-term forces */, double *__restrict__ partial,
-      const SogConsts sc)
+      const SogConsts sc, int en)
 {
     static_assert(32 * kMolWarps >= kMolChunk, "one thread per molecule of a chunk");
     constexpr int NT = 32 * kMolWarps, NS = 3 * kTermPass;
@@ -184,7 +182,7 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
                 TermF tf;
                 if (t < nb) bond_term(b0 + t, bonds, bk, br0, r, L, ub, wb, tf);
                 else if (t < nb + na) angle_term(a0 + t - nb, angles, ak, at0, r, L, ua, wb, tf);
-                else excl_term<R>(e0 + t - nb - na, excl, r, q, L, sc, ue_rem, ue, wx, tf);
+                else excl_term<R>(e0 + t - nb - na, excl, r, q, L, sc, en, ue_rem, ue, wx, tf);
                 for (int v = 0; v < tf.n; ++v)
                     for (int x = 0; x < 3; ++x) F[3 * tf.atom[v] + x] += tf.f[v][x];
             }
@@ -211,7 +209,7 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
                 if (u < np) {
                     if (t < nb) bond_term(b0 + t, bonds, bk, br0, r, L, ub, wb, tf);
                     else if (t < nb + na) angle_term(a0 + t - nb, angles, ak, at0, r, L, ua, wb, tf);
-                    else excl_term<R>(e0 + t - nb - na, excl, r, q, L, sc, ue_rem, ue, wx, tf);
+                    else excl_term<R>(e0 + t - nb - na, excl, r, q, L, sc, en, ue_rem, ue, wx, tf);
                 }
                 for (int v = 0; v < 3; ++v) {
                     sa[3 * u + v] = v < tf.n ? tf.atom[v] : -1;
@@ -254,17 +252,17 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
 }
 
 void launch_mol(const Batch &b, const AtomArrays &a, const MolArrays &m, const SogConsts &sc, double *Fmol,
-                double *partial, int precision, cudaStream_t st)
+                double *partial, int precision, int energy, cudaStream_t st)
 {
     if (m.nmchunks == 0) return;
     if (precision == 1)
         k_mol<float><<<m.nmchunks, 32 * kMolWarps, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
                                                m.a_start, m.e_start, m.bonds, m.bk, m.br0, m.angles, m.ak,
-                                               m.at0, m.excl, a.r, a.q, Fmol, partial, sc);
+                                               m.at0, m.excl, a.r, a.q, Fmol, partial, sc, energy);
     else
         k_mol<double><<<m.nmchunks, 32 * kMolWarps, 0, st>>>(b.sys, m.mchunk_sys, m.mchunk_m0, m.mchunk_n, m.b_start,
                                                 m.a_start, m.e_start, m.bonds, m.bk, m.br0, m.angles, m.ak,
-                                                m.at0, m.excl, a.r, a.q, Fmol, partial, sc);
+                                                m.at0, m.excl, a.r, a.q, Fmol, partial, sc, energy);
 }
 
 }  // namespace rbsog

@@ -210,13 +210,13 @@ void fork_sampler(rbsog_ctx *c, int adv)
 // Molecule terms on the third stream: they need only the positions and the
 // box, run beside the binning into their own force buffer, and end before
 // the pair kernels.
-void fork_mol(rbsog_ctx *c)
+void fork_mol(rbsog_ctx *c, int energy)
 {
     if (c->m.nmchunks == 0) return;
     cudaEventRecord(c->ev_fork3, c->st);
     cudaStreamWaitEvent(c->st3, c->ev_fork3, 0);
     cudaMemsetAsync(c->Fmol, 0, 3 * sizeof(double) * (size_t)c->N, c->st3);
-    launch_mol(c->b, c->a, c->m, c->sc, c->Fmol, c->mol_part, c->prm.precision, c->st3);
+    launch_mol(c->b, c->a, c->m, c->sc, c->Fmol, c->mol_part, c->prm.precision, energy, c->st3);
     cudaEventRecord(c->ev_join3, c->st3);
 }
 
@@ -229,7 +229,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     const bool mol = c->m.nmchunks > 0;
     if (!prepared) {
         record(c, "start");
-        fork_mol(c);
+        fork_mol(c, energy);
         launch_box_prep(c->b, c->st);
         record(c, "box_prep");
         fork_sampler(c, adv);
@@ -280,7 +280,7 @@ void enqueue_npt_step(rbsog_ctx *c, int energy)
     launch_box_half(c->b, c->ia, c->sysred, 1, c->st);
     fork_sampler(c, 1);
     launch_atom_update(c->b, c->a, c->ia, 1, c->prm.precision, c->st);
-    fork_mol(c);
+    fork_mol(c, energy);
     enqueue_eval(c, 1, 1, energy, 1, 1);
 }
 
