@@ -68,6 +68,9 @@ struct Batch {
 // nhit[p * ncap + i] hits; an entry is (index of the first of 32 candidates |
 // neighbour-cell code << 25, hit mask).
 constexpr int kEvalSplit = 3;   // FP32 evaluation warps (hit segments) per 32-atom group
+constexpr int kF64Split = 4;    // FP64 pair kernel: warps per (work item, dz plane), each over every 4th cell
+// force partials per atom (and pair records per work item) of the pair kernels
+inline int pair_parts(int precision, int sub) { return precision == 1 ? kEvalSplit : (2 * sub + 1) * kF64Split; }
 struct PairList {
     uint2 *ent;                 // [span * maxent * ncap]
     int *nent, *nhit;           // [span * ncap]

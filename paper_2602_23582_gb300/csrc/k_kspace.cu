@@ -338,7 +338,7 @@ void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const M
                      const double *Fmol, cudaStream_t st)
 {
     const dim3 grid(b.nchunks, kChunk / kLrAtoms);
-    const int nparts = precision == 1 ? kEvalSplit : 2 * b.sub + 1;   // FP32: hit segments; FP64: dz planes
+    const int nparts = pair_parts(precision, b.sub);   // FP32: hit segments; FP64: dz planes x cell quarters
     if (precision == 1)
         k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
                                                     coef, Dcap, a.rank, a.fpart4, nparts, b.N, Fmol, a.F);

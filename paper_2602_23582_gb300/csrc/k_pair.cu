@@ -520,9 +520,11 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
     double2 *offp = reinterpret_cast<double2 *>(smem + kPairWarps * QCAP * 32 * sizeof(unsigned)) + warp * kMaxPlane;
     const int span = 2 * sub + 1;
+    // unit = (work item, dz plane, quarter): the quarter takes every kF64Split-th
+    // cell of the plane, so that small systems still fill the SMs' FP64 pipes
     const int unit = blockIdx.x * kPairWarps + warp;
-    const int2 item = items[unit / span];
-    const int part = unit % span;
+    const int2 item = items[unit / (span * kF64Split)];
+    const int part = (unit / kF64Split) % span, quarter = unit % kF64Split;
     double red[kPairRec];
 #pragma unroll
     for (int k = 0; k < kPairRec; ++k) red[k] = 0.0;
@@ -566,7 +568,7 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
         };
 
         const int gz = wrapi(cz + ddz, n2);
-        for (int nb = 0; nb < span * span; ++nb) {
+        for (int nb = quarter; nb < span * span; nb += kF64Split) {
             const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
             const int j0 = start[g], nj = count[g];
             const double2 o = offp[nb];
@@ -592,7 +594,7 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
         }
         while (__any_sync(0xffffffffu, tail > head))
             if (tail > head) pop();
-        if (vi) Fpart[(size_t)part * N + i0 + lane] = make_double4(acc.fx, acc.fy, acc.fz, 0.0);
+        if (vi) Fpart[(size_t)(part * kF64Split + quarter) * N + i0 + lane] = make_double4(acc.fx, acc.fy, acc.fz, 0.0);
         const double v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
                               acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
 #pragma unroll
@@ -640,7 +642,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
         }
 #undef RBSOG_PAIR_EVAL
     } else {
-        k_pair_f64<<<units / kPairWarps, 32 * kPairWarps, pair_smem(0), st>>>(
+        k_pair_f64<<<units * kF64Split / kPairWarps, 32 * kPairWarps, pair_smem(0), st>>>(
             b.sys, b.cell_sys, a.start, a.count, a.items, a.posd, a.aux, a.ljd, b.sub, b.N, a.fpartd, partial, cd);
     }
 }

@@ -253,7 +253,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     // the pair records are reduced beside the long-range part
     cudaEventRecord(c->ev_fork4, c->st);
     cudaStreamWaitEvent(c->st3, c->ev_fork4, 0);
-    launch_reduce_pair(c->b, prec == 1 ? kEvalSplit : 2 * c->prm.cell_sub + 1, c->pair_part, c->pair_red, c->st3);
+    launch_reduce_pair(c->b, pair_parts(prec, c->prm.cell_sub), c->pair_part, c->pair_red, c->st3);
     cudaEventRecord(c->ev_join4, c->st3);
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
@@ -791,8 +791,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
-                  dalloc(c, c->pair_part, (size_t)item_cap * std::max(2 * P.cell_sub + 1, kEvalSplit) * kPairRec) &&
-                  dalloc(c, c->fpart, (size_t)N * std::max(2 * P.cell_sub + 1, kEvalSplit)) &&
+                  dalloc(c, c->pair_part, (size_t)item_cap * pair_parts(P.precision, P.cell_sub) * kPairRec) &&
+                  dalloc(c, c->fpart, (size_t)N * pair_parts(P.precision, P.cell_sub)) &&
                   dalloc(c, c->pair_red, (size_t)S * kPairRedBlocks * kPairRec) &&
                   dalloc(c, c->est, (size_t)S * estimate_blocks(c->Dcap) * 7) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
