@@ -134,7 +134,8 @@ __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, c
 
 }  // namespace
 
-// A block takes the kMolChunk molecules of a chunk.  A molecule with at most
+// A block takes the molecules of a chunk (kMolChunk of them for systems of
+// small molecules, kMolChunkLarge otherwise).  A molecule with at most
 // kSmallTerms terms is one thread's (its terms in order: bonds, angles,
 // exclusions, each added to its atoms' forces at once).  A larger molecule is
 // one warp's: its terms are spread over the lanes in passes of kTermPass,
@@ -144,7 +145,7 @@ __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, c
 // are written by its thread or warp only, and every sum runs in a fixed
 // order.  R is the arithmetic type of the exclusion terms (float in the FP32
 // build): differences of positions are formed in FP64, then rounded.
-constexpr int kMolWarps = 4, kTermPass = 64, kSmallTerms = 24;
+constexpr int kMolWarps = 4, kTermPass = 64;
 
 template <typename R>
 __global__ void __launch_bounds__(32 * kMolWarps)

@@ -27,6 +27,8 @@
 // subtracts both, so that the rounding of w_a does not shift every
 // cross-cell distance the same way (a systematic error that the r^-12 and
 // 1/r - F(r) terms would amplify).
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace rbsog {
@@ -213,6 +215,12 @@ __device__ __forceinline__ uint2 next_entry(const PairList &L, int ks, int &pl, 
     return L.ent[((size_t)pl * L.maxent + k++) * L.ncap + ks];
 }
 
+// Two staged candidates of the list build: (-2 b_x, -2 b_y, -2 b_z, |b|^2) in
+// half precision, candidate 2p in the low halves and 2p + 1 in the high ones.
+struct __align__(16) HPair {
+    __half2 x, y, z, w;
+};
+
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
 }  // namespace
@@ -243,7 +251,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
              PairList L, const float rc2_hi)
 {
     __shared__ float2 offp[kMaxPlane];
-    __shared__ float4 cand[32];
+    __shared__ HPair cand2[16];
     const int lane = lane_id();
     const int span = 2 * sub + 1;
     const int unit = blockIdx.x;
@@ -282,9 +290,11 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     // the whole warp with one coalesced load, one batch ahead, and tested by
     // every lane from shared memory.  The test uses the expanded form
     // |a - b|^2 = |a|^2 + |b|^2 - 2 a.b with a, b relative to the candidate
-    // cell's centre: the loading lane stores (-2 b, |b|^2), so a candidate
-    // costs three FMAs and a compare.  Its rounding error (below 2e-4 A^2 for
-    // the coordinates that occur near r_c) is far inside the margin of rc2_hi,
+    // cell's centre: the loading lane stores (-2 b, |b|^2) in half precision,
+    // two candidates per half2, so that a pair of candidates costs three
+    // packed FMAs and one packed compare.  The test accepts r^2 below
+    // 1.025 r_c^2: for the coordinates that occur near r_c (|a| < 20 A,
+    // |b| < 10 A) its rounding error stays below 1.2 A^2, inside that margin,
     // and the evaluation decides every pair exactly.  A short batch is padded
     // with entries no lane can hit; pairs of one molecule pass this test and
     // are dropped by the evaluation (a few per atom at most).
@@ -294,6 +304,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         const float bx = q.x - hx, by = q.y - hy, bz = q.z - hz;
         return make_float4(-2.f * bx, -2.f * by, -2.f * bz, fmaf(bx, bx, fmaf(by, by, bz * bz)));
     };
+    const float rc2_test = 1.025f * rc2_hi;
     int nb = 0, jb = 0, j0 = 0, nj = 0;
     for (;;) {                                         // first non-empty cell (warp-uniform)
         if (nb >= nn) break;
@@ -308,9 +319,16 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     }
     // this lane's atom relative to the centre of neighbour cell nb is pc - offp[nb]
     const float pcx = pi.x - hx, pcy = pi.y - hy, pcz = pi.z - hz;
+    __half *ch = reinterpret_cast<__half *>(cand2);    // candidate 2p + h: halves h of pair p
     while (nb < nn) {
         const int bnb = nb, bj = j0 + jb;
-        cand[lane] = nxt;
+        {
+            const int pp = lane >> 1, h = lane & 1;
+            ch[8 * pp + h] = __float2half_rn(nxt.x);
+            ch[8 * pp + 2 + h] = __float2half_rn(nxt.y);
+            ch[8 * pp + 4 + h] = __float2half_rn(nxt.z);
+            ch[8 * pp + 6 + h] = __float2half_rn(nxt.w);
+        }
         // advance to the next batch and start its load
         jb += 32;
         if (jb >= nj) {
@@ -328,15 +346,24 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         __syncwarp();
         const float2 o = offp[bnb];
         const float ax = pcx - o.x, ay = pcy - o.y, az = pcz - ozh;
-        const float thr = rc2_hi - fmaf(ax, ax, fmaf(ay, ay, az * az));
-        unsigned hm = 0;                               // hits among these 32 candidates
+        const __half2 ax2 = __float2half2_rn(ax), ay2 = __float2half2_rn(ay), az2 = __float2half2_rn(az);
+        const __half2 thr2 = __float2half2_rn(rc2_test - fmaf(ax, ax, fmaf(ay, ay, az * az)));
+        unsigned bits = 0;                             // bit p: candidate 2p, bit 16 + p: candidate 2p + 1
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-            const float4 c = cand[u];
-            if (fmaf(ax, c.x, fmaf(ay, c.y, fmaf(az, c.z, c.w))) < thr) hm |= 1u << u;
+        for (int pp = 0; pp < 16; ++pp) {
+            const HPair c = cand2[pp];
+            const __half2 t = __hfma2(ax2, c.x, __hfma2(ay2, c.y, __hfma2(az2, c.z, c.w)));
+            bits |= (__hlt2_mask(t, thr2) & 0x00010001u) << pp;
         }
+        // interleave: hit mask bit 2p from bit p, bit 2p + 1 from bit 16 + p
+        unsigned lo = bits & 0xffffu, hi = bits >> 16;
+        lo = (lo | (lo << 8)) & 0x00ff00ffu; hi = (hi | (hi << 8)) & 0x00ff00ffu;
+        lo = (lo | (lo << 4)) & 0x0f0f0f0fu; hi = (hi | (hi << 4)) & 0x0f0f0f0fu;
+        lo = (lo | (lo << 2)) & 0x33333333u; hi = (hi | (hi << 2)) & 0x33333333u;
+        lo = (lo | (lo << 1)) & 0x55555555u; hi = (hi | (hi << 1)) & 0x55555555u;
+        const unsigned hm = lo | (hi << 1);            // hits among these 32 candidates
         nxt = ld ? stage(qn) : far;
-        __syncwarp();                                  // cand is rewritten next round
+        __syncwarp();                                  // cand2 is rewritten next round
         const unsigned code = (unsigned)(part * nn + bnb) << 25;
         // an entry for every batch with a hit, at k = nent of this (plane, atom)
         if (hm != 0u) {

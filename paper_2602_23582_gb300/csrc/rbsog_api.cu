@@ -701,10 +701,14 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             }
             nchunk[k] = (int)chunk_sys.size() - first_chunk[k];
             mchunk_first[k] = (int)mchunk_sys.size();
-            for (int m0 = 0; m0 < cp.mols; m0 += kMolChunk) {
+            // one thread per molecule when the slot's molecules are small on
+            // average, else chunks of a few large molecules (one warp each)
+            const int mch = (double)cp.bonds + cp.angles + cp.excl <= (double)kSmallTerms * cp.mols
+                                ? kMolChunk : kMolChunkLarge;
+            for (int m0 = 0; m0 < cp.mols; m0 += mch) {
                 mchunk_sys.push_back(k);
                 mchunk_m0.push_back(nmolx + m0);
-                mchunk_n.push_back(std::min(kMolChunk, cp.mols - m0));
+                mchunk_n.push_back(std::min(mch, cp.mols - m0));
             }
             mchunk_count[k] = (int)mchunk_sys.size() - mchunk_first[k];
             N += cp.atoms;
