@@ -20,7 +20,7 @@ constexpr int kMaxGauss = 64;      // Gaussians of the split, M and M_energy
 constexpr int kMaxP = 4096;        // batch size
 constexpr int kCellCap = 2048;     // atoms per cell the kernels accept
 constexpr int kChunk = 1024;       // atoms per chunk of the per-atom kernels
-constexpr int kMolChunk = 128;     // molecules per block of the molecule kernel (at most)
+constexpr int kMolChunk = 32;      // molecules per block of the molecule kernel (small molecules)
 constexpr int kMolChunkLarge = 16; // ... for systems of large molecules (a warp each)
 constexpr int kSmallTerms = 24;    // terms of a molecule that one thread takes
 constexpr int kMaxTypes = 16;

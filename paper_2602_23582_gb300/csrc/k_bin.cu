@@ -135,42 +135,41 @@ __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ 
     sidx[start[cell[i]] + rank[i]] = i;
 }
 
-// One warp per cell: bitonic sort of the cell's atom list by original index,
-// then gather the cell-sorted copies used by the pair kernel.
-constexpr int kSortWarps = 1;
+// One block per cell: bitonic sort of the cell's atom list by original index
+// (kSortThreads threads, each stage one compare-exchange per thread for a
+// cell of up to 2 kSortThreads atoms), then gather the cell-sorted copies used
+// by the pair kernel.
+constexpr int kSortThreads = 128;
 
-__global__ void __launch_bounds__(32 * kSortWarps)
+__global__ void __launch_bounds__(kSortThreads)
 k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C, int *__restrict__ sidx,
             int *__restrict__ rank, const float4 *__restrict__ locf, const double4 *__restrict__ locd,
             const double *__restrict__ q, const int *__restrict__ type, const int *__restrict__ mol,
             float4 *__restrict__ pos4, float2 *__restrict__ qt, double4 *__restrict__ posd,
             int2 *__restrict__ aux, int precision)
 {
-    __shared__ int buf[kSortWarps][kCellCap];
-    const int w = threadIdx.x >> 5, lane = lane_id();
-    const int c = blockIdx.x * kSortWarps + w;
-    if (c >= C) return;
+    __shared__ int s[kCellCap];
+    const int c = blockIdx.x, t0 = threadIdx.x;
     const int base = start[c];
     const int n = min(count[c], kCellCap);
-    if (n == 0) return;
-    int *s = buf[w];
+    if (n == 0) return;                                // block-uniform
     int p2 = 1;
     while (p2 < n) p2 <<= 1;
-    for (int k = lane; k < p2; k += 32) s[k] = (k < n) ? sidx[base + k] : 0x7fffffff;
-    __syncwarp();
+    for (int k = t0; k < p2; k += kSortThreads) s[k] = (k < n) ? sidx[base + k] : 0x7fffffff;
+    __syncthreads();
     for (int k = 2; k <= p2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = lane; t < p2 / 2; t += 32) {
+            for (int t = t0; t < p2 / 2; t += kSortThreads) {
                 int lo = 2 * j * (t / j) + (t % j);
                 int hi = lo + j;
                 bool up = (lo & k) == 0;
                 int x = s[lo], y = s[hi];
                 if ((x > y) == up) { s[lo] = y; s[hi] = x; }
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
-    for (int k = lane; k < n; k += 32) {
+    for (int k = t0; k < n; k += kSortThreads) {
         int i = s[k];
         sidx[base + k] = i;
         rank[i] = base + k;          // from here on: cell-sorted position of atom i
@@ -187,7 +186,7 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
 {
     k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(a.cell, a.rank, a.start, a.sidx, b.N);
-    k_cell_sort<<<(b.C + kSortWarps - 1) / kSortWarps, 32 * kSortWarps, 0, st>>>(
+    k_cell_sort<<<b.C, kSortThreads, 0, st>>>(
         a.start, a.count, b.C, a.sidx, a.rank, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
 }
 

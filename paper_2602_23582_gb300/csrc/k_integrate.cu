@@ -337,62 +337,76 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
     }
     block_reduce_lanes<NV, kFinThreads>(v, buf, acc);
     __syncthreads();
-    if (tid != 0) return;
-    // long range (eqs. U_F*, P_F,r*, P_F,nr*): mode-group sums in group order,
-    // then the prefactors k_e S^r / (4 V P) and -k_e S^nr / (8 V P)
-    double es[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int g = 0; g < est_blocks; ++g)
-#pragma unroll
-        for (int t = 0; t < 7; ++t) es[t] += est[((size_t)s * est_blocks + g) * 7 + t];
+    if (tid >= 32) return;
+    // the outputs on the lanes of warp 0 (short FP64 chains side by side);
+    // every value is formed by the same operations as in a one-thread loop
+    const int lane = tid;
+    // long range (eqs. U_F*, P_F,r*, P_F,nr*): mode-group sums in group order
+    // (lane t < 7), then the prefactors k_e S^r / (4 V P) and -k_e S^nr / (8 V P)
+    double es = 0.0;
+    if (lane < 7)
+        for (int g = 0; g < est_blocks; ++g) es += est[((size_t)s * est_blocks + g) * 7 + lane];
     const double Vb = d.L[0] * d.L[1] * d.L[2];
-    double lr[8];
-    lr[0] = ia.ke * d.Sr / (4.0 * Vb * P) * es[0];
-    lr[1] = lr[0];
-    for (int a = 0; a < 6; ++a) lr[2 + a] = -ia.ke * d.Snr / (8.0 * Vb * P) * es[1 + a];
+    const double lrl = lane == 0 ? ia.ke * d.Sr / (4.0 * Vb * P) * es : -ia.ke * d.Snr / (8.0 * Vb * P) * es;
+    const double lr0 = __shfl_sync(0xffffffffu, lrl, 0);
+    const int a = lane < 6 ? lane : 0;
+    const double Wnr = __shfl_sync(0xffffffffu, lrl, 1 + a);
     const double us = self_energy[2 * s];        // U_self (App. A)
     const double uxc = self_energy[2 * s + 1];   // FP32 build: sum over exclusions of ke q_i q_j F_E(0)
     // energies and the Coulomb/LJ virial split come from the pair kernel only
     // on energy steps (zero otherwise); the total short-range virial always
     double e[9];
     e[0] = acc[0];                 // U^N Coulomb
-    e[1] = lr[0];                  // U^F*
+    e[1] = lr0;                    // U^F*
     e[2] = us;
     e[3] = acc[M0] - uxc;          // exclusions
     e[4] = acc[1];                 // LJ
     e[5] = acc[M0 + 1];            // bonds
     e[6] = acc[M0 + 2];            // angles
     e[7] = e[0] + e[1] - e[2] + e[3];
-    double K[6];
-    for (int a = 0; a < 6; ++a) K[a] = acc[K0 + a];
-    e[8] = 0.5 * (K[0] + K[1] + K[2]);
-    double Wc[6], Wr[6], Wnr[6], Wl[6], Wb[6], W[6];
-    for (int a = 0; a < 6; ++a) {
-        Wc[a] = acc[2 + a];
-        Wl[a] = acc[8 + a];
-        Wr[a] = a < 3 ? lr[1] : 0.0;
-        Wnr[a] = lr[2 + a];
-        Wb[a] = acc[M0 + 3 + a] + acc[M0 + 9 + a];
-        W[a] = acc[14 + a] + Wr[a] + Wnr[a] + Wb[a];
-    }
+    e[8] = 0.5 * (acc[K0] + acc[K0 + 1] + acc[K0 + 2]);
+    // tensor component a on lane a < 6
+    const double K = acc[K0 + a];
+    const double Wc = acc[2 + a], Wl = acc[8 + a];
+    const double Wr = a < 3 ? lr0 : 0.0;
+    const double Wb = acc[M0 + 3 + a] + acc[M0 + 9 + a];
+    const double W = acc[14 + a] + Wr + Wnr + Wb;
     bool finite = true;
-    for (int a = 0; a < 9; ++a) { o[a] = e[a]; finite = finite && isfinite(e[a]); }
-    for (int a = 0; a < 6; ++a) {
-        o[9 + a] = W[a]; o[15 + a] = Wc[a]; o[21 + a] = Wr[a]; o[27 + a] = Wnr[a];
-        o[33 + a] = Wl[a]; o[39 + a] = Wb[a]; o[45 + a] = K[a];
-        finite = finite && isfinite(W[a]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        if (lane == k) o[k] = e[k];
+        finite = finite && isfinite(e[k]);
     }
+    if (lane < 6) {
+        o[9 + a] = W; o[15 + a] = Wc; o[21 + a] = Wr; o[27 + a] = Wnr;
+        o[33 + a] = Wl; o[39 + a] = Wb; o[45 + a] = K;
+    }
+    finite = __all_sync(0xffffffffu, finite && (lane >= 6 || isfinite(W)));
+    // second half of the box kick: generalised box force (box_force) on lanes
+    // a < 3, added per group in axis order
+    const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
+    const double pext = ia.Pext / ia.nktv2p;
+    const double term = (K + W - pext * Vb - ia.kB * ia.T) / d.L[a];
+    const double t0 = __shfl_sync(0xffffffffu, term, 0), t1 = __shfl_sync(0xffffffffu, term, 1),
+                 t2 = __shfl_sync(0xffffffffu, term, 2);
+    const int gg = lane < 3 ? lane : 0;
+    double ph = d.ph[gg];
+    if (do_box_kick && d.n > 0 && lane < ng && d.Mbox[gg] > 0.0) {
+        double G = 0.0;
+        if (axis_group(d.coupling, 0) == gg) G += t0;
+        if (axis_group(d.coupling, 1) == gg) G += t1;
+        if (axis_group(d.coupling, 2) == gg) G += t2;
+        ph += 0.5 * ia.dt * G * ia.ftm2v;
+        d.ph[gg] = ph;
+    }
+    const double ph0 = __shfl_sync(0xffffffffu, ph, 0), ph1 = __shfl_sync(0xffffffffu, ph, 1),
+                 ph2 = __shfl_sync(0xffffffffu, ph, 2);
+    if (lane != 0) return;
     if (!finite) d.flags |= FLAG_NONFINITE;
-    if (do_box_kick && d.n > 0) {
-        double G[3];
-        box_force(d, o, ia, G);
-        const int ng = d.coupling == 0 ? 1 : (d.coupling == 1 ? 2 : 3);
-        for (int g = 0; g < ng; ++g)
-            if (d.Mbox[g] > 0.0) d.ph[g] += 0.5 * ia.dt * G[g] * ia.ftm2v;
-    }
-    o[51] = d.L[0] * d.L[1] * d.L[2];
+    o[51] = Vb;
     o[52] = d.L[0]; o[53] = d.L[1]; o[54] = d.L[2];
     o[55] = d.nD; o[56] = d.nacc_r; o[57] = d.nacc_nr; o[58] = d.flags;
-    o[59] = d.ph[0]; o[60] = d.ph[1]; o[61] = d.ph[2];
+    o[59] = ph0; o[60] = ph1; o[61] = ph2;
     if (adv) {
         d.step += 1ull;
         if (d.steps_left > 0 && --d.steps_left == 0) d.act = 0;   // the last requested step

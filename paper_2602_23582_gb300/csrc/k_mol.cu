@@ -135,7 +135,7 @@ __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, c
 }  // namespace
 
 // A block takes the molecules of a chunk (kMolChunk of them for systems of
-// small molecules, kMolChunkLarge otherwise).  A molecule with at most
+// small molecules, kMolChunkLarge otherwise; at most one per thread).  A molecule with at most
 // kSmallTerms terms is one thread's (its terms in order: bonds, angles,
 // exclusions, each added to its atoms' forces at once).  A larger molecule is
 // one warp's: its terms are spread over the lanes in passes of kTermPass,
