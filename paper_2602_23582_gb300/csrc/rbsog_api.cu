@@ -114,6 +114,8 @@ struct rbsog_ctx {
     // graphs of one NPT step: [0] forces and virial, [1] also energies
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraph_t graph_src[2] = {nullptr, nullptr};
+    cudaGraphExec_t eval_graph = nullptr;   // one evaluation with energies (rbsog_step)
+    cudaGraph_t eval_graph_src = nullptr;
     // pair-kernel trace: event-record nodes around the pair kernel in each
     // graph; their events are swapped per launch to a ring of caller-visible
     // timings (placeholders when no trace is armed)
@@ -353,6 +355,8 @@ void free_ctx(rbsog_ctx *c)
         if (g) cudaGraphExecDestroy(g);
     for (auto g : c->graph_src)
         if (g) cudaGraphDestroy(g);
+    if (c->eval_graph) cudaGraphExecDestroy(c->eval_graph);
+    if (c->eval_graph_src) cudaGraphDestroy(c->eval_graph_src);
     for (auto e : c->ring_s) cudaEventDestroy(e);
     for (auto e : c->ring_e) cudaEventDestroy(e);
     for (auto e : c->ev_pair_ph)
@@ -1132,6 +1136,24 @@ rbsog_status rbsog_get_velocities(rbsog_ctx *c, double *v, int on_device)
     return RBSOG_OK;
 }
 
+// The evaluation of rbsog_step as a CUDA graph (captured on first use; the
+// step counter is set by a kernel launched before it).
+static rbsog_status ensure_eval_graph(rbsog_ctx *c)
+{
+    if (c->eval_graph) return RBSOG_OK;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capture");
+    launch_clear_flags(c->b, c->st);
+    enqueue_eval(c, 0, 0, 1, 0);
+    e = cudaStreamEndCapture(c->st, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capture end");
+    e = cudaGraphInstantiate(&c->eval_graph, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "graph instantiate"); }
+    c->eval_graph_src = g;
+    return RBSOG_OK;
+}
+
 rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_device, rbsog_result *res)
 {
     if (!c) return RBSOG_EINVAL;
@@ -1140,8 +1162,15 @@ rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_devi
     for (auto ev : c->t_events) cudaEventDestroy(ev);
     c->t_events.clear();
     c->t_names.clear();
-    launch_clear_flags(c->b, c->st);
-    enqueue_eval(c, 0, 0, 1, 0);
+    if (c->timing) {                          // eager, with events around each kernel
+        launch_clear_flags(c->b, c->st);
+        enqueue_eval(c, 0, 0, 1, 0);
+    } else {
+        rbsog_status gs = ensure_eval_graph(c);
+        if (gs != RBSOG_OK) return gs;
+        e = cudaGraphLaunch(c->eval_graph, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    }
     c->h_step = (unsigned long long)step;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
