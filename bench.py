@@ -225,12 +225,16 @@ def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
             time.sleep(max(0.0, (reqs[order[k_next]][0] - now_ms) * 1e-3))
     wall = time.perf_counter() - t_start
     done = failed = 0
+    why = {}                                  # failed requests: status name -> [(atoms, box edge, steps made)]
     work = 0.0                                # atom-steps actually made (a failed request stops early)
     for k, t in tickets.items():
         out = srv.result(t)
         if out is not None:
             done += 1
-            failed += out[2]["status"] != 0
+            if out[2]["status"] != 0:
+                failed += 1
+                why.setdefault(R.STATUS.get(out[2]["status"], str(out[2]["status"])), []).append(
+                    (reqs[k][2].n, round(float(np.min(reqs[k][2].box)), 2), int(out[2]["step"])))
             work += reqs[k][2].n * float(out[2]["step"])
     st = srv.stats()
     slots = srv.slots
@@ -250,7 +254,7 @@ def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
         ctx.close()
     return {"workload": "256 electrolyte/water systems, 500-20,000 atoms (log-uniform), 100-1000 NPT steps each, "
                         f"Poisson arrivals at {rate_per_ms * 1e3:.0f} requests/s, P=100, FP32",
-            "value": work / wall, "unit": UNIT, "requests_done": done, "requests_failed": failed,
+            "value": work / wall, "unit": UNIT, "requests_done": done, "requests_failed": failed, "failed_why": why,
             "atom_steps": work, "wall_s": wall,
             "gpu_busy_atom_steps_per_s": st["atom_steps_per_s"], "p50_step_ms": st["p50_ms"],
             "p99_step_ms": st["p99_ms"], "pool_steps": st["steps"], "pool_slots": slots,

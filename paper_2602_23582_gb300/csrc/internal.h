@@ -107,7 +107,7 @@ struct AtomArrays {
 void launch_box_prep(const Batch &b, cudaStream_t st);
 void launch_clear_flags(const Batch &b, cudaStream_t st);
 void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
-void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st);
+void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 
 // ---- k_pair.cu: partial = per record (FP32: one per item; FP64: one per

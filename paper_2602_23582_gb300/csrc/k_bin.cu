@@ -80,24 +80,66 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
 
 // Per-system exclusive scan of the cell counts (one block per system): the
 // atoms of system s occupy [atom0, atom0 + n) of the sorted arrays.  The same
-// pass lists the pair kernel's work items (cell, 32-atom group) of the system
-// in [item0, item0 + nitems) and marks the rest of its item range unused.
+// pass lists the pair kernel's work items of the system in [item0, item0 +
+// nitems) and marks the rest of its item range unused.  An item is (cell g,
+// k >= 0): the k-th group of 32 atoms of cell g, or (cell g, -m): the m >= 2
+// consecutive cells g .. g + m - 1 of one x-row, holding 32 atoms or fewer
+// together (maxrun > 1 allows such runs; the FP32 list build takes them).
+// Each thread groups the cells of its own range, in order.
+__device__ __forceinline__ int scan_items(const int *__restrict__ count, int C0, int c0, int c1, int n0,
+                                          int maxrun, int2 *__restrict__ items, int rg, bool write)
+{
+    int ni = 0, run0 = -1, runn = 0, runa = 0;
+    auto flush = [&]() {
+        if (runn > 0) {
+            if (write) items[rg + ni] = make_int2(C0 + run0, runn > 1 ? -runn : 0);
+            ++ni;
+        }
+        runn = 0;
+        runa = 0;
+    };
+    for (int c = c0; c < c1; ++c) {
+        const int v = count[C0 + c];
+        if (v == 0 || v > 32 || maxrun < 2) {
+            flush();
+            const int ng = (v + 31) >> 5;
+            for (int g = 0; g < ng; ++g) {
+                if (write) items[rg + ni] = make_int2(C0 + c, g);
+                ++ni;
+            }
+            continue;
+        }
+        // a run continues with the next cell of the same x-row while it fits
+        if (runn > 0 && (c % n0) != 0 && runn < maxrun && runa + v <= 32) {
+            ++runn;
+            runa += v;
+        } else {
+            flush();
+            run0 = c;
+            runn = 1;
+            runa = v;
+        }
+    }
+    flush();
+    return ni;
+}
+
 __global__ void __launch_bounds__(1024)
-k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, DevSys *sys)
+k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, DevSys *sys, int maxrun)
 {
     __shared__ int ta[1024], tg[1024];
     DevSys &d = sys[blockIdx.x];
     const int t = threadIdx.x, T = blockDim.x;
-    const int C0 = d.cell0, nc = d.ncell_cap_total;
+    const int C0 = d.cell0, nc = d.ncell_cap_total, n0 = d.ncell[0];
     const int per = (nc + T - 1) / T;
     const int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
-    int sa = 0, sg = 0;
+    int sa = 0;
     for (int c = c0; c < c1; ++c) {
         const int v = count[C0 + c];
         if (v > kCellCap) atomicOr(&d.flags, (int)FLAG_OVERFLOW);
         sa += v;
-        sg += (v + 31) >> 5;
     }
+    const int sg = scan_items(count, C0, c0, c1, n0, maxrun, items, 0, false);
     ta[t] = sa;
     tg[t] = sg;
     __syncthreads();
@@ -108,23 +150,24 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
         tg[t] += vg;
         __syncthreads();
     }
-    int ra = d.atom0 + ta[t] - sa, rg = d.item0 + tg[t] - sg;
+    int ra = d.atom0 + ta[t] - sa;
+    const int rg = d.item0 + tg[t] - sg;
     for (int c = c0; c < c1; ++c) {
-        const int v = count[C0 + c];
         start[C0 + c] = ra;
-        ra += v;
-        const int ng = (v + 31) >> 5;
-        for (int g = 0; g < ng; ++g) items[rg + g] = make_int2(C0 + c, g);
-        rg += ng;
+        ra += count[C0 + c];
     }
+    scan_items(count, C0, c0, c1, n0, maxrun, items, rg, true);
     const int total = tg[T - 1];
     if (t == T - 1) d.nitems = total;
     for (int k = total + t; k < d.item_cap; k += T) items[d.item0 + k] = make_int2(-1, -1);
 }
 
-void launch_scan(const Batch &b, const AtomArrays &a, cudaStream_t st)
+void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
 {
-    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys);
+    // runs of cells whose stencil rows fit one warp's cell table: (span + m - 1) span <= 32
+    const int span = 2 * b.sub + 1;
+    const int maxrun = precision == 1 ? 32 / span - span + 1 : 1;
+    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys, maxrun);
 }
 
 __global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ rank,

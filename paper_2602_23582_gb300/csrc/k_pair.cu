@@ -250,7 +250,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
              const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
              PairList L, const float rc2_hi)
 {
-    __shared__ float2 offp[kMaxPlane];
+    __shared__ float4 offp[kMaxPlane];                 // x, y offset; column; code of row
     __shared__ HPair cand2[16];
     const int lane = lane_id();
     const int span = 2 * sub + 1;
@@ -265,13 +265,27 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     const int lc = gc - d.cell0;
     const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
     const int ddz = part - sub;
-    for (int nb = lane; nb < span * span; nb += 32)
-        offp[nb] = make_float2((float)((nb % span - sub) * d.w[0]), (float)((nb / span - sub) * d.w[1]));
+    // the item's cells: one cell (group item.y), or a run of rc = -item.y cells
+    // of one x-row; a lane's atom lies in cell gc + ldx of the run
+    const int rc_n = item.y < 0 ? -item.y : 1;
+    const int ncol = span + rc_n - 1;                  // x columns of the plane's cells
+    const int nn = ncol * span;
+    for (int nb = lane; nb < nn; nb += 32)
+        offp[nb] = make_float4((float)((nb % ncol - sub) * d.w[0]), (float)((nb / ncol - sub) * d.w[1]),
+                               __int_as_float(nb % ncol), __int_as_float(part * span * span + (nb / ncol) * span));
     const float ozh = (float)(ddz * d.w[2]);
     __syncwarp();
-    const int i0 = start[gc] + 32 * item.y;
-    const int ni = min(32, count[gc] - 32 * item.y);
+    int i0, ni;
+    if (item.y >= 0) {
+        i0 = start[gc] + 32 * item.y;
+        ni = min(32, count[gc] - 32 * item.y);
+    } else {
+        i0 = start[gc];
+        ni = start[gc + rc_n - 1] + count[gc + rc_n - 1] - i0;
+    }
     const bool vi = lane < ni;
+    int ldx = 0;                                       // this lane's cell within the run
+    for (int k = 1; k < rc_n; ++k) ldx += (i0 + lane >= start[gc + k]) ? 1 : 0;
     // lanes without an atom sit far away: their cutoff test never passes
     float4 pi = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     if (vi) pi = pos4[i0 + lane];
@@ -279,10 +293,9 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     bool overflow = false;
     const int gz = wrapi(cz + ddz, n2);
     // the plane's cells, one per lane: first atom and atom count
-    const int nn = span * span;
     int cj0 = 0, cnj = 0;
     if (lane < nn) {
-        const int g = d.cell0 + wrapi(cx + lane % span - sub, n0) + n0 * (wrapi(cy + lane / span - sub, n1) + n1 * gz);
+        const int g = d.cell0 + wrapi(cx + lane % ncol - sub, n0) + n0 * (wrapi(cy + lane / ncol - sub, n1) + n1 * gz);
         cj0 = start[g];
         cnj = count[g];
     }
@@ -318,7 +331,8 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         if (lane < nj) nxt = stage(__ldg(pos4 + j0 + lane));
     }
     // this lane's atom relative to the centre of neighbour cell nb is pc - offp[nb]
-    const float pcx = pi.x - hx, pcy = pi.y - hy, pcz = pi.z - hz;
+    // (and its cell lies ldx columns right of the run's first cell)
+    const float pcx = pi.x - hx + (float)ldx * (float)d.w[0], pcy = pi.y - hy, pcz = pi.z - hz;
     __half *ch = reinterpret_cast<__half *>(cand2);    // candidate 2p + h: halves h of pair p
     while (nb < nn) {
         const int bnb = nb, bj = j0 + jb;
@@ -344,8 +358,12 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         const bool ld = nb < nn && jb + lane < nj;
         if (ld) qn = __ldg(pos4 + j0 + jb + lane);
         __syncwarp();
-        const float2 o = offp[bnb];
+        const float4 o = offp[bnb];
         const float ax = pcx - o.x, ay = pcy - o.y, az = pcz - ozh;
+        // the candidate cell relative to this lane's cell: outside the lane's
+        // stencil (a run's far end) it holds no pair within r_c
+        const int dxl = __float_as_int(o.z) - ldx;     // sub + x offset of the candidate cell
+        const bool incol = (unsigned)dxl < (unsigned)span;
         const __half2 ax2 = __float2half2_rn(ax), ay2 = __float2half2_rn(ay), az2 = __float2half2_rn(az);
         const __half2 thr2 = __float2half2_rn(rc2_test - fmaf(ax, ax, fmaf(ay, ay, az * az)));
         unsigned bits = 0;                             // bit p: candidate 2p, bit 16 + p: candidate 2p + 1
@@ -361,10 +379,10 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         lo = (lo | (lo << 4)) & 0x0f0f0f0fu; hi = (hi | (hi << 4)) & 0x0f0f0f0fu;
         lo = (lo | (lo << 2)) & 0x33333333u; hi = (hi | (hi << 2)) & 0x33333333u;
         lo = (lo | (lo << 1)) & 0x55555555u; hi = (hi | (hi << 1)) & 0x55555555u;
-        const unsigned hm = lo | (hi << 1);            // hits among these 32 candidates
+        const unsigned hm = incol ? (lo | (hi << 1)) : 0u;   // hits among these 32 candidates
         nxt = ld ? stage(qn) : far;
         __syncwarp();                                  // cand2 is rewritten next round
-        const unsigned code = (unsigned)(part * nn + bnb) << 25;
+        const unsigned code = (unsigned)(__float_as_int(o.w) + dxl) << 25;
         // an entry for every batch with a hit, at k = nent of this (plane, atom)
         if (hm != 0u) {
             if (nent < L.maxent) {

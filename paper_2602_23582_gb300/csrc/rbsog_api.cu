@@ -238,7 +238,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
         launch_bin(c->b, c->a, prec, c->st);
         record(c, "bin");
     }
-    launch_scan(c->b, c->a, c->st);
+    launch_scan(c->b, c->a, prec, c->st);
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
