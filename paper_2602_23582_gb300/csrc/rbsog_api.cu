@@ -65,7 +65,7 @@ struct rbsog_ctx {
     cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr;   // st2: mode sampling, st3: molecule terms
     bool own_st = false, own_st2 = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
-    cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr;
+    cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr, ev_bin = nullptr;
     std::string err;
     std::vector<int> h_atom0, h_n, h_cell0, h_ncap_total, h_coupling;
     std::vector<void *> allocs;
@@ -200,12 +200,36 @@ void record(rbsog_ctx *c, const char *name)
 // adv = 1: the evaluation of an NPT step (Philox counter DevSys::step + 1,
 // advanced at the end); 0: evaluate at DevSys::step.
 // Mode sampling on the second stream: needs the box and its cell grid only.
+// Unless kernels are timed one by one, the structure factor and the estimator
+// follow on the same stream (fork_kspace) and the join comes after them.
 void fork_sampler(rbsog_ctx *c, int adv)
 {
     cudaEventRecord(c->ev_fork, c->st);
     cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
     launch_sampler(c->b, c->sa, adv, c->mr, c->mnr, c->D, c->cr, c->cnr, c->pm, c->pw, c->pg, c->pu, c->pun,
                    c->samp, c->Dcap, c->st2);
+    if (c->timing) cudaEventRecord(c->ev_join, c->st2);
+}
+
+// Structure factor and estimator on the second stream, after the sampler and
+// the binning (which writes the fixed-point coordinates they read): they need
+// neither the cell lists nor the pair forces, so they run beside the list
+// build and the pair evaluation.
+void enqueue_kspace(rbsog_ctx *c, cudaStream_t st)
+{
+    launch_sk(c->b, c->a, c->prm.precision, c->D, c->Dcap, c->sk_part, st);
+    record(c, "structure_factor");
+    launch_estimate(c->b, c->first_chunk, c->nchunk_sys, c->D, c->cr, c->cnr, c->Dcap, c->prm.P, c->prm.ke,
+                    c->sk_part, c->rho, c->coef, c->est, st);
+    record(c, "estimate");
+}
+
+void fork_kspace(rbsog_ctx *c)
+{
+    if (c->timing) return;
+    cudaEventRecord(c->ev_bin, c->st);
+    cudaStreamWaitEvent(c->st2, c->ev_bin, 0);
+    enqueue_kspace(c, c->st2);
     cudaEventRecord(c->ev_join, c->st2);
 }
 
@@ -238,6 +262,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
         launch_bin(c->b, c->a, prec, c->st);
         record(c, "bin");
     }
+    fork_kspace(c);
     launch_scan(c->b, c->a, prec, c->st);
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
@@ -259,11 +284,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     cudaEventRecord(c->ev_join4, c->st3);
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
-    launch_sk(c->b, c->a, prec, c->D, c->Dcap, c->sk_part, c->st);
-    record(c, "structure_factor");
-    launch_estimate(c->b, c->first_chunk, c->nchunk_sys, c->D, c->cr, c->cnr, c->Dcap, c->prm.P, c->prm.ke,
-                    c->sk_part, c->rho, c->coef, c->est, c->st);
-    record(c, "estimate");
+    if (c->timing) enqueue_kspace(c, c->st);
     launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, mol ? c->Fmol : nullptr, c->st);
     record(c, "lr_force");
     launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
@@ -364,6 +385,7 @@ void free_ctx(rbsog_ctx *c)
     for (auto e : c->t_events) cudaEventDestroy(e);
     for (void *v : c->allocs) cudaFree(v);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_bin) cudaEventDestroy(c->ev_bin);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_fork3) cudaEventDestroy(c->ev_fork3);
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
@@ -632,6 +654,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         e = cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rbsog_status r = cuda_fail(c, e, "stream"); free_ctx(c); return r; }
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming);

@@ -42,6 +42,9 @@ SYSTEMS = {
     "electrolyte": lambda: W.electrolyte(n_ions=1000, L=30.0, seed=1),
     "water_small": lambda: W.water(n_mol=1200, L=33.0, lattice=11, seed=2),
     "ragged": lambda: W.random_charges(n=1333, box=(31.0, 34.5, 40.25), seed=5, min_dist=1.6, lj=True),
+    # a few atoms per cell: whole x-rows of cells become one list-build item,
+    # and the row wraps around the periodic boundary within the item's stencil
+    "sparse_rows": lambda: W.random_charges(n=400, box=(80.0, 30.0, 31.0), seed=7, min_dist=2.0, lj=True),
 }
 
 
@@ -88,9 +91,10 @@ def _compare_eval(s, prec, step=5, **kw):
 
 
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_eval_fp64_matches_oracle(name):
+@pytest.mark.parametrize("sub", [1, 2])
+def test_eval_fp64_matches_oracle(name, sub):
     s = SYSTEMS[name]()
-    F, r, ref = _compare_eval(s, R.RBSOG_FP64)
+    F, r, ref = _compare_eval(s, R.RBSOG_FP64, cell_sub=sub)
     assert _rel(F, ref["F"]) < 1e-10
     assert _rel(r["virial"], ref["W"]) < 1e-10
     assert _rel(r["virial_coul_short"], ref["W_parts"][0]) < 1e-10
@@ -103,9 +107,12 @@ def test_eval_fp64_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_eval_fp32_matches_oracle(name):
+@pytest.mark.parametrize("sub", [1, 2])
+def test_eval_fp32_matches_oracle(name, sub):
+    # cell_sub 2 (cells of r_c/2, a dozen atoms each) makes the list build
+    # take runs of several cells of one x-row per work item
     s = SYSTEMS[name]()
-    F, r, ref = _compare_eval(s, R.RBSOG_FP32)
+    F, r, ref = _compare_eval(s, R.RBSOG_FP32, cell_sub=sub)
     V = float(np.prod(s.box))
     assert _rel(F, ref["F"]) < 1e-5
     P_gpu = r["virial"] / V
