@@ -499,7 +499,7 @@ def main():
             served = served_bench(R, prec, local)
         except Exception as ex:   # reported, not fatal
             served = {"error": str(ex)}
-    kernels_per_step = 17   # box_half .. finalize, one graph replay (three streams)
+    kernels_per_step = 16   # box_half .. finalize, one graph replay (three streams)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == R.RBSOG_FP32 else "f64",

@@ -152,9 +152,6 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
                      double *rho, ModeCoef *coef, double *est, cudaStream_t st);
 // mode groups of k_estimate: est holds S x estimate_blocks(Dcap) x 7 partial sums
 int estimate_blocks(int Dcap);
-// F = pair partials + long-range force + Fmol (molecule terms; null: none)
-void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
-                     int Dcap, const double *Fmol, cudaStream_t st);
 // V P^F,nr by the shared-proposal estimator (sec. 3.2) over the modes of the
 // last evaluation: out[S x 9] (row-major 3 x 3, kcal/mol)
 void launch_nr_shared(const Batch &b, const int *D, const int *cr, const double *rho, int Dcap, int P, double ke,
@@ -199,9 +196,13 @@ void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, 
 // bin = 1: also k_bin's work for the updated atoms (counts zeroed by the caller)
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
                         cudaStream_t st);
-constexpr int kKinSplit = 4;   // kinetic partials per atom chunk
-void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int kick,
-                         double *kin_part, cudaStream_t st);
+constexpr int kKinSplit = 8;   // kinetic partials per atom chunk (one per force-assembly block)
+// F = pair partials + long-range force + Fmol (molecule terms; null: none),
+// then (kick != 0) the second half kick p += dt/2 F, and the kinetic tensor
+// per kChunk / kKinSplit atoms: kin_part[chunk][kKinSplit][6] = sum p (x) p / m
+void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
+                     int Dcap, const double *Fmol, const IntegArgs &ia, int kick, double *kin_part,
+                     cudaStream_t st);
 // per-system reduction of every partial into sysred[S x kRed]; advances *step
 constexpr int kRed = 64;
 void launch_finalize(const Batch &b, const double *pair_part, const double *est, int est_blocks, int P,

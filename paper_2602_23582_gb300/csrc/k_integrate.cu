@@ -220,46 +220,6 @@ void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia
     }
 }
 
-// Second half kick (optional) and the kinetic tensor per quarter of an atom
-// chunk: kin_part[chunk][kKinSplit][6] = sum p (x) p / m (kcal/mol).
-__global__ void __launch_bounds__(kChunk / kKinSplit)
-k_kick_kinetic(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
-               double *__restrict__ p, const double *__restrict__ F, const double *__restrict__ inv_m, double kick,
-               double mvv2e, double *__restrict__ kin_part)
-{
-    __shared__ double red[6 * (kChunk / kKinSplit + 1) + 24];
-    const int c = blockIdx.x, a0 = chunk_a0[c];
-    const DevSys &d = sys[chunk_sys[c]];
-    const int na = min(kChunk, live_n(d) - (a0 - d.atom0));   // <= 0: beyond the system in its slot
-    double k6[6] = {0, 0, 0, 0, 0, 0};
-    constexpr int per = kChunk / kKinSplit;
-    const int k_end = min(na, (int)(blockIdx.y + 1) * per);
-    for (int k = blockIdx.y * per + threadIdx.x; k < k_end; k += blockDim.x) {
-        const int i = a0 + k;
-        double v[3];
-        for (int a = 0; a < 3; ++a) {
-            v[a] = p[3 * i + a];
-            if (kick != 0.0) {
-                v[a] += kick * F[3 * i + a];
-                p[3 * i + a] = v[a];
-            }
-        }
-        const double im = inv_m[i];
-        k6[0] += v[0] * v[0] * im; k6[1] += v[1] * v[1] * im; k6[2] += v[2] * v[2] * im;
-        k6[3] += v[0] * v[1] * im; k6[4] += v[0] * v[2] * im; k6[5] += v[1] * v[2] * im;
-    }
-    for (int a = 0; a < 6; ++a) k6[a] *= mvv2e;
-    block_reduce_lanes<6, kChunk / kKinSplit>(k6, red, kin_part + ((size_t)c * kKinSplit + blockIdx.y) * 6);
-}
-
-void launch_kick_kinetic(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int do_kick,
-                         double *kin_part, cudaStream_t st)
-{
-    const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0;
-    k_kick_kinetic<<<dim3(b.nchunks, kKinSplit), kChunk / kKinSplit, 0, st>>>(
-        b.sys, b.chunk_sys, b.chunk_a0, a.p, a.F, ia.inv_m, kick, 1.0 / ia.ftm2v, kin_part);
-}
-
 // Per-system reduction of all partials (fixed order) into sysred[s][kRed]:
 //  [0..8] energies (RBSOG_E_*), [9..14] W total (xx yy zz xy xz yz),
 //  [15..20] W short Coulomb, [21..26] W^F,r*, [27..32] W^F,nr*, [33..38] W LJ,

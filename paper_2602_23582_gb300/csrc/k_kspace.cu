@@ -230,9 +230,11 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
 // + q_i sum_d alpha_d k_d Im(e^{-i k_d.r_i} rho_d) (eq. f_approx) + the
 // molecule terms of k_mol.  Blocks of kLrAtoms atoms of
 // one chunk (grid: chunks x kChunk / kLrAtoms); the system's mode
-// coefficients are staged in shared memory in tiles.
+// coefficients are staged in shared memory in tiles.  The same blocks then
+// give the atoms their second half kick (velocity Verlet B step) and sum the
+// kinetic tensor p (x) p / m of their atoms, one partial per block.
 constexpr int kModeTile = 256;
-constexpr int kLrAtoms = 128;
+constexpr int kLrAtoms = kChunk / kKinSplit;
 
 template <bool F32>
 __global__ void __launch_bounds__(kLrAtoms)
@@ -240,18 +242,24 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
            const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
            const double *__restrict__ q, const ModeCoef *__restrict__ coef_all, int Dcap,
            const int *__restrict__ pos_sorted, const void *__restrict__ fpart, int nparts, int N,
-           const double *__restrict__ Fmol, double *__restrict__ F)
+           const double *__restrict__ Fmol, double *__restrict__ F, double *__restrict__ mom,
+           const double *__restrict__ inv_m, double kick, double mvv2e, double *__restrict__ kin_part)
 {
     __shared__ float4 tf[F32 ? kModeTile : 1];      // a (FP32)
     __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
     __shared__ int4 tm[kModeTile];
     __shared__ double td[F32 ? 1 : kModeTile][5];
+    __shared__ double red[6 * (kLrAtoms + 1) + 24];
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int nD = d.nD, a0 = chunk_a0[c], na = min(kChunk, live_n(d) - (a0 - d.atom0));
     const ModeCoef *coef = coef_all + (size_t)s * Dcap;
     const int k = blockIdx.y * kLrAtoms + threadIdx.x;
-    if ((int)(blockIdx.y * kLrAtoms) >= na) return;   // whole block beyond the chunk
+    double *kin = kin_part + ((size_t)c * kKinSplit + blockIdx.y) * 6;
+    if ((int)(blockIdx.y * kLrAtoms) >= na) {         // whole block beyond the chunk
+        if (threadIdx.x < 6) kin[threadIdx.x] = 0.0;
+        return;
+    }
     const bool act = k < na;
     const int i = a0 + (act ? k : 0);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -302,49 +310,66 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
             }
         }
     }
-    if (!act) return;
-    const double qi = q[i];
-    const int ks = pos_sorted[i];
-    double f[3] = {0.0, 0.0, 0.0};
-    for (int p = 0; p < nparts; ++p) {
-        if (F32) {
-            const float4 e = reinterpret_cast<const float4 *>(fpart)[(size_t)p * N + ks];
-            f[0] += (double)e.x; f[1] += (double)e.y; f[2] += (double)e.z;
-        } else {
-            const double4 e = reinterpret_cast<const double4 *>(fpart)[(size_t)p * N + ks];
-            f[0] += e.x; f[1] += e.y; f[2] += e.z;
+    double k6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (act) {
+        const double qi = q[i];
+        const int ks = pos_sorted[i];
+        double f[3] = {0.0, 0.0, 0.0};
+        for (int p = 0; p < nparts; ++p) {
+            if (F32) {
+                const float4 e = reinterpret_cast<const float4 *>(fpart)[(size_t)p * N + ks];
+                f[0] += (double)e.x; f[1] += (double)e.y; f[2] += (double)e.z;
+            } else {
+                const double4 e = reinterpret_cast<const double4 *>(fpart)[(size_t)p * N + ks];
+                f[0] += e.x; f[1] += e.y; f[2] += e.z;
+            }
         }
+        if (F32) {
+            f[0] += qi * (double)fx;
+            f[1] += qi * (double)fy;
+            f[2] += qi * (double)fz;
+        } else {
+            f[0] += qi * gx;
+            f[1] += qi * gy;
+            f[2] += qi * gz;
+        }
+        if (Fmol) {
+            f[0] += Fmol[3 * i];
+            f[1] += Fmol[3 * i + 1];
+            f[2] += Fmol[3 * i + 2];
+        }
+        F[3 * i] = f[0];
+        F[3 * i + 1] = f[1];
+        F[3 * i + 2] = f[2];
+        double v[3];
+        for (int a = 0; a < 3; ++a) {
+            v[a] = mom[3 * i + a];
+            if (kick != 0.0) {
+                v[a] += kick * f[a];
+                mom[3 * i + a] = v[a];
+            }
+        }
+        const double im = inv_m[i];
+        k6[0] = v[0] * v[0] * im * mvv2e; k6[1] = v[1] * v[1] * im * mvv2e; k6[2] = v[2] * v[2] * im * mvv2e;
+        k6[3] = v[0] * v[1] * im * mvv2e; k6[4] = v[0] * v[2] * im * mvv2e; k6[5] = v[1] * v[2] * im * mvv2e;
     }
-    if (F32) {
-        f[0] += qi * (double)fx;
-        f[1] += qi * (double)fy;
-        f[2] += qi * (double)fz;
-    } else {
-        f[0] += qi * gx;
-        f[1] += qi * gy;
-        f[2] += qi * gz;
-    }
-    if (Fmol) {
-        f[0] += Fmol[3 * i];
-        f[1] += Fmol[3 * i + 1];
-        f[2] += Fmol[3 * i + 2];
-    }
-    F[3 * i] = f[0];
-    F[3 * i + 1] = f[1];
-    F[3 * i + 2] = f[2];
+    block_reduce_lanes<6, kLrAtoms>(k6, red, kin);
 }
 
 void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
-                     const double *Fmol, cudaStream_t st)
+                     const double *Fmol, const IntegArgs &ia, int do_kick, double *kin_part, cudaStream_t st)
 {
+    const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0, mvv2e = 1.0 / ia.ftm2v;
     const dim3 grid(b.nchunks, kChunk / kLrAtoms);
     const int nparts = pair_parts(precision, b.sub);   // FP32: hit segments; FP64: dz planes x cell quarters
     if (precision == 1)
         k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                    coef, Dcap, a.rank, a.fpart4, nparts, b.N, Fmol, a.F);
+                                                    coef, Dcap, a.rank, a.fpart4, nparts, b.N, Fmol, a.F,
+                                                    a.p, ia.inv_m, kick, mvv2e, kin_part);
     else
         k_lr_force<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                     coef, Dcap, a.rank, a.fpartd, nparts, b.N, Fmol, a.F);
+                                                     coef, Dcap, a.rank, a.fpartd, nparts, b.N, Fmol, a.F,
+                                                     a.p, ia.inv_m, kick, mvv2e, kin_part);
 }
 
 // Shared-proposal estimator of the non-radial virial (sec. 3.2, the

@@ -285,10 +285,8 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
     if (c->timing) enqueue_kspace(c, c->st);
-    launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, mol ? c->Fmol : nullptr, c->st);
-    record(c, "lr_force");
-    launch_kick_kinetic(c->b, c->a, c->ia, kick, c->kin_part, c->st);
-    record(c, "kick_kinetic");
+    launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, mol ? c->Fmol : nullptr, c->ia, kick, c->kin_part, c->st);
+    record(c, "lr_force_kick");
     cudaStreamWaitEvent(c->st, c->ev_join4, 0);
     launch_finalize(c->b, c->pair_red, c->est, estimate_blocks(c->Dcap), c->prm.P, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
