@@ -51,6 +51,13 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {
     float y = x - c;
@@ -117,7 +124,7 @@ __device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float
                                           const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlo,
                                           float2 qj, AccF &acc)
 {
-    float rinv = rsqrtf(r2);
+    float rinv = rsqrt_approx(r2);                       // r^2 of a pair is far above the subnormals
     rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);   // one Newton step: the approximate
     const float r2inv = rinv * rinv;                     // rsqrt error would bias r^-12 terms
     // force kernel: F~(r) = tail polynomial in r^2 + narrow Gaussians
@@ -202,18 +209,22 @@ __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, doub
     acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
 }
 
-// Next (base, mask) entry of atom ks's hit stream: entry k of plane pl, kend
-// entries in plane pl; moves to the next plane with entries when this one is
-// used up.  The caller asks only for entries that exist.
-__device__ __forceinline__ uint2 next_entry(const PairList &L, int ks, int &pl, int &k, int &kend)
+// Next (base, mask) entry of atom ks's hit stream: ep points at it, krem
+// entries of plane pl are left; moves to the next plane with entries when
+// this one is used up.  The caller asks only for entries that exist.
+__device__ __forceinline__ uint2 next_entry(const PairList &L, int ks, int &pl, const uint2 *&ep, int &krem)
 {
-    while (k >= kend) {
+    while (krem <= 0) {
         ++pl;
-        k = 0;
-        kend = L.nent[pl * L.ncap + ks];
+        ep = L.ent + (size_t)pl * L.maxent * L.ncap + ks;
+        krem = L.nent[pl * L.ncap + ks];
     }
-    return L.ent[((size_t)pl * L.maxent + k++) * L.ncap + ks];
+    --krem;
+    const uint2 v = *ep;
+    ep += L.ncap;
+    return v;
 }
+
 
 // Two staged candidates of the list build: (-2 b_x, -2 b_y, -2 b_z, |b|^2) in
 // half precision, candidate 2p in the low halves and 2p + 1 in the high ones.
@@ -441,7 +452,8 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
         float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 pq = make_float2(0.f, 0.f);
         // this warp takes hits [h0, h1) of the lane's stream (all planes in order)
-        int nh = 0, pl = 0, k = 0, kend = 0;
+        int nh = 0, pl = 0, krem = 0;
+        const uint2 *ep = L.ent + ks;
         unsigned base = 0u, mask = 0u;
         if (vi) {
             pi = pos4[ks];
@@ -455,9 +467,12 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
                 int skip = h0;
                 int hp = L.nhit[ks];
                 while (skip >= hp) { skip -= hp; ++pl; hp = L.nhit[pl * L.ncap + ks]; }
-                kend = L.nent[pl * L.ncap + ks];
+                ep = L.ent + (size_t)pl * L.maxent * L.ncap + ks;
+                krem = L.nent[pl * L.ncap + ks];
                 while (skip > 0) {                     // walk entries up to hit h0
-                    const uint2 en = L.ent[((size_t)pl * L.maxent + k++) * L.ncap + ks];
+                    const uint2 en = *ep;
+                    ep += L.ncap;
+                    --krem;
                     const int cc = __popc(en.y);
                     if (cc <= skip) {
                         skip -= cc;
@@ -480,12 +495,12 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
         // the current one has started, are loaded while this hit is evaluated
         int left = nh;                                 // hits of this lane still to evaluate
         if (left > 0 && mask == 0u) {
-            const uint2 en = next_entry(L, ks, pl, k, kend);
+            const uint2 en = next_entry(L, ks, pl, ep, krem);
             base = en.x;
             mask = en.y;
         }
         uint2 nxt = make_uint2(0u, 0u);
-        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, k, kend);
+        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, ep, krem);
         unsigned e = 0u;
         float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
         float2 qj = make_float2(0.f, 0.f);
@@ -505,7 +520,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
                     if (mask == 0u) {
                         base = nxt.x;
                         mask = nxt.y;
-                        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, k, kend);
+                        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, ep, krem);
                     }
                     e = base + (unsigned)(__ffs(mask) - 1);
                     mask &= mask - 1u;
