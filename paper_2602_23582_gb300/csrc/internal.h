@@ -68,6 +68,7 @@ struct Batch {
 // nhit[p * ncap + i] hits; an entry is (index of the first of 32 candidates |
 // neighbour-cell code << 25, hit mask).
 constexpr int kEvalSplit = 3;   // FP32 evaluation warps (hit segments) per 32-atom group
+constexpr int kEvalGroups = 2;   // evaluation groups of 32 atoms per block (item_cap per system: a multiple)
 constexpr int kF64Split = 4;    // FP64 pair kernel: warps per (work item, dz plane), each over every 4th cell
 // force partials per atom (and pair records per work item) of the pair kernels
 inline int pair_parts(int precision, int sub) { return precision == 1 ? kEvalSplit : (2 * sub + 1) * kF64Split; }
@@ -114,10 +115,12 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 // block of kPairWarps work units = item x dz plane):
 // (Ucoul, Ulj, Wc[6], Wl[6], W[6]) as kPairRec doubles; energies and the
 // Coulomb/LJ split only when `energy` is set (W, the total, always).  Each
-// system's item range is a multiple of kPairWarps items, so a block never
+// system's item range is a multiple of kItemAlign items, so a block never
 // mixes systems.  launch_reduce_pair (k_integrate.cu) sums each system's
 // records into kPairRedBlocks records in a fixed order.
 constexpr int kPairWarps = 1;       // one warp per block: no block-level wait on a slower warp
+constexpr int kItemAlign = kEvalGroups > kPairWarps ? kEvalGroups : kPairWarps;
+static_assert(kItemAlign % kPairWarps == 0 && kItemAlign % kEvalGroups == 0, "item alignment");
 constexpr int kPairRec = 20;
 constexpr int kPairRedBlocks = 8;   // second-stage reduction of the unit records, per system
 void launch_reduce_pair(const Batch &b, int rec_per_item, const double *pair_part, double *pair_red, cudaStream_t st);

@@ -413,7 +413,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
 }
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kEvalSplit, EN ? 4 : 8)
+__global__ void __launch_bounds__(32 * kEvalSplit * kEvalGroups, (EN ? 4 : 8) / kEvalGroups)
 k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const float4 *__restrict__ pos4,
             const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
             const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N, const PairList L,
@@ -423,7 +423,11 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
     __shared__ float2 ljs[EN ? 2 : 1][kMaxTypes * kMaxTypes];   // the system's LJ table (and remainders)
     const int lane = lane_id();
     const int span = 2 * sub + 1;
-    const int it = blockIdx.x, seg = threadIdx.x >> 5;   // one warp per segment, one block per group
+    // kEvalGroups consecutive groups per block (they share most neighbour
+    // atoms in L1), one warp per (group, segment)
+    const int warp = threadIdx.x >> 5;
+    const int it = blockIdx.x * kEvalGroups + warp / kEvalSplit, seg = warp % kEvalSplit;
+    // the block's groups lie in one system (item_cap per system is a multiple of kEvalGroups)
     const DevSys &d = sys[item_sys[it]];
     // evaluation group: 32 consecutive cell-sorted atoms of one system (group
     // g of the system uses the record slots of its work item item0 + g)
@@ -432,7 +436,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
     float wv[18];                                      // Wc, Wl (energy steps), W
 #pragma unroll
     for (int k = 0; k < 18; ++k) wv[k] = 0.f;
-    if (g32 < nlive) {                                 // warp-uniform
+    if (32 * (blockIdx.x * kEvalGroups - d.item0) < nlive) {   // block-uniform: some group is live
         // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
         // must not shift every cross-cell distance the same way)
         for (int nb = threadIdx.x; nb < span * span * span; nb += blockDim.x) {
@@ -446,7 +450,9 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
             ljs[0][t] = lj[d.lj0 + t];
             if (EN) ljs[EN ? 1 : 0][t] = ljlo[d.lj0 + t];
         }
-        __syncthreads();                               // block-uniform branch
+        __syncthreads();
+    }
+    if (g32 < nlive) {                                 // warp-uniform
         const int ks = d.atom0 + g32 + lane;           // this lane's atom (cell-sorted index)
         const bool vi = g32 + lane < nlive;
         float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -692,7 +698,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
         k_pair_build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist,
                                            cf.rc2_hi);
 #define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
-    k_pair_eval<NF, EN><<<b.item_cap, 32 * kEvalSplit, 0, st>>>(b.sys, b.item_sys,                             \
+    k_pair_eval<NF, EN><<<b.item_cap / kEvalGroups, 32 * kEvalSplit * kEvalGroups, 0, st>>>(b.sys, b.item_sys, \
                                                                 a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \
                                                                 b.N, a.plist, a.fpart4, partial, cf)
         if (cf.nff == 4) {

@@ -706,7 +706,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             // pair work items: at most one partial 32-atom group per cell; a
             // multiple of kPairWarps so that no pair-kernel block spans two systems
             ds.item0 = item_cap;
-            ds.item_cap = ((cp.atoms + 31) / 32 + ncap_t + kPairWarps - 1) / kPairWarps * kPairWarps;
+            ds.item_cap = ((cp.atoms + 31) / 32 + ncap_t + kItemAlign - 1) / kItemAlign * kItemAlign;
             item_cap += ds.item_cap;
             item_sys.insert(item_sys.end(), (size_t)ds.item_cap, k);
             ds.atom0 = N;
