@@ -366,7 +366,14 @@ def main():
 
     # ---- NPT steps: warm-up, then K steps timed one by one with an L2 flush between
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    R.rbsog_run(ctx.ctx, args.warmup)
+    # warm-up: W steps, continued until the GPU has run steps for at least
+    # 0.3 s (clock ramp-up from idle takes tens of ms; the early steps of a
+    # run otherwise time the ramp, not the step)
+    warm_steps = 0
+    t_warm = time.perf_counter()
+    while warm_steps < args.warmup or time.perf_counter() - t_warm < 0.3:
+        R.rbsog_run(ctx.ctx, args.warmup if warm_steps == 0 else 10)
+        warm_steps += args.warmup if warm_steps == 0 else 10
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
@@ -508,6 +515,7 @@ def main():
                        "precision": "FP32 math, FP64 accumulation" if prec == R.RBSOG_FP32 else "FP64",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between timed steps (256 MiB write)",
+                       "warmup_steps_run": warm_steps,
                        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                        "ns_per_day": (p.dt * 1e-6) / (float(step_ms.mean()) / 1e3 / 86400.0),
                        "energies": f"every {args.thermo} steps (thermo output); forces and virial every step",
