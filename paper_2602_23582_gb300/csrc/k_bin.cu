@@ -164,9 +164,11 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
 
 void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
 {
-    // runs of cells whose stencil rows fit one warp's cell table: (span + m - 1) span <= 32
+    // runs of cells whose stencil rows fit one warp's cell table, (span + m - 1) span <= 32,
+    // for the FP32 list build with cells of r_c / 2 (the only size where cells of
+    // a few atoms are the rule)
     const int span = 2 * b.sub + 1;
-    const int maxrun = precision == 1 ? 32 / span - span + 1 : 1;
+    const int maxrun = precision == 1 && b.sub >= 2 ? 32 / span - span + 1 : 1;
     k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys, maxrun);
 }
 

@@ -256,6 +256,7 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // Segment k writes force partial k, summed in segment order by the force
 // assembly.
 // ---------------------------------------------------------------------------
+template <bool RUNS>
 __global__ void __launch_bounds__(32, 32)
 k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
              const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
@@ -278,8 +279,8 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     const int ddz = part - sub;
     // the item's cells: one cell (group item.y), or a run of rc = -item.y cells
     // of one x-row; a lane's atom lies in cell gc + ldx of the run
-    const int rc_n = item.y < 0 ? -item.y : 1;
-    const int ncol = span + rc_n - 1;                  // x columns of the plane's cells
+    const int rc_n = RUNS && item.y < 0 ? -item.y : 1;
+    const int ncol = RUNS ? span + rc_n - 1 : span;    // x columns of the plane's cells
     const int nn = ncol * span;
     for (int nb = lane; nb < nn; nb += 32)
         offp[nb] = make_float4((float)((nb % ncol - sub) * d.w[0]), (float)((nb / ncol - sub) * d.w[1]),
@@ -287,7 +288,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     const float ozh = (float)(ddz * d.w[2]);
     __syncwarp();
     int i0, ni;
-    if (item.y >= 0) {
+    if (!RUNS || item.y >= 0) {
         i0 = start[gc] + 32 * item.y;
         ni = min(32, count[gc] - 32 * item.y);
     } else {
@@ -296,7 +297,8 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     }
     const bool vi = lane < ni;
     int ldx = 0;                                       // this lane's cell within the run
-    for (int k = 1; k < rc_n; ++k) ldx += (i0 + lane >= start[gc + k]) ? 1 : 0;
+    if (RUNS)
+        for (int k = 1; k < rc_n; ++k) ldx += (i0 + lane >= start[gc + k]) ? 1 : 0;
     // lanes without an atom sit far away: their cutoff test never passes
     float4 pi = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     if (vi) pi = pos4[i0 + lane];
@@ -374,7 +376,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         // the candidate cell relative to this lane's cell: outside the lane's
         // stencil (a run's far end) it holds no pair within r_c
         const int dxl = __float_as_int(o.z) - ldx;     // sub + x offset of the candidate cell
-        const bool incol = (unsigned)dxl < (unsigned)span;
+        const bool incol = !RUNS || (unsigned)dxl < (unsigned)span;
         const __half2 ax2 = __float2half2_rn(ax), ay2 = __float2half2_rn(ay), az2 = __float2half2_rn(az);
         const __half2 thr2 = __float2half2_rn(rc2_test - fmaf(ax, ax, fmaf(ay, ay, az * az)));
         unsigned bits = 0;                             // bit p: candidate 2p, bit 16 + p: candidate 2p + 1
@@ -692,11 +694,12 @@ cudaError_t prepare_pair()
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st)
 {
-    // item_cap is a multiple of kPairWarps per system, so every block lies in one system
+    // item_cap is a multiple of kItemAlign per system, so every block lies in one system
     const int units = b.item_cap * (2 * b.sub + 1);
     if (precision == 1) {
-        k_pair_build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist,
-                                           cf.rc2_hi);
+        // runs of several cells per item occur with cells of r_c / 2 (a dozen atoms)
+        auto build = b.sub >= 2 ? k_pair_build<true> : k_pair_build<false>;
+        build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist, cf.rc2_hi);
 #define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
     k_pair_eval<NF, EN><<<b.item_cap / kEvalGroups, 32 * kEvalSplit * kEvalGroups, 0, st>>>(b.sys, b.item_sys, \
                                                                 a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \

@@ -42,8 +42,8 @@ SYSTEMS = {
     "electrolyte": lambda: W.electrolyte(n_ions=1000, L=30.0, seed=1),
     "water_small": lambda: W.water(n_mol=1200, L=33.0, lattice=11, seed=2),
     "ragged": lambda: W.random_charges(n=1333, box=(31.0, 34.5, 40.25), seed=5, min_dist=1.6, lj=True),
-    # a few atoms per cell: whole x-rows of cells become one list-build item,
-    # and the row wraps around the periodic boundary within the item's stencil
+    # a few atoms per cell: with cells of r_c/2, pairs of cells of one x-row
+    # become one list-build item
     "sparse_rows": lambda: W.random_charges(n=400, box=(80.0, 30.0, 31.0), seed=7, min_dist=2.0, lj=True),
 }
 
@@ -120,6 +120,17 @@ def test_eval_fp32_matches_oracle(name, sub):
     assert _rel(P_gpu, P_ref) < 1e-6
     assert abs(r["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
     assert abs(r["lj"] - ref["lj"]) <= 1e-6 * max(abs(ref["lj"]), 1.0)
+
+
+def test_eval_fp32_run_items_wrapping_stencil():
+    # cells of r_c/2 with five cells along x: a list-build item of two cells
+    # spans six stencil columns, so its first and last column are one cell;
+    # every atom must still see each neighbour cell once
+    s = W.random_charges(n=300, box=(27.0, 40.0, 33.0), seed=17, min_dist=2.0, lj=True)
+    F, r, ref = _compare_eval(s, R.RBSOG_FP32, cell_sub=2)
+    assert _rel(F, ref["F"]) < 1e-5
+    assert _rel(r["virial"], ref["W"]) < 1e-6
+    assert abs(r["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
 
 
 def test_eval_fp32_full_water_box():
