@@ -315,6 +315,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--P", type=int, default=100, help="Fourier modes per step (batch size)")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="pair-list skin in A (FP32 build; default: the library's)")
     ap.add_argument("--variance-study", action="store_true",
                     help="only the estimator variance study (one JSON line), no timing")
     ap.add_argument("--thermo", type=int, default=100,
@@ -351,6 +353,8 @@ def main():
     prec = R.RBSOG_FP32 if args.precision == "fp32" else R.RBSOG_FP64
     stream = torch.cuda.Stream(device=dev)
     p = R.rbsog_default_params(10.0, precision=prec, thermo_every=args.thermo, P=args.P)
+    if args.skin is not None:
+        p.skin = args.skin
     ctx = R.Context(systems, p, stream=stream.cuda_stream)
     n_atoms = ctx.n_atoms
 
@@ -375,6 +379,7 @@ def main():
         R.rbsog_run(ctx.ctx, args.warmup if warm_steps == 0 else 10)
         warm_steps += args.warmup if warm_steps == 0 else 10
     torch.cuda.synchronize()
+    builds0 = sum(r["list_builds"] for r in ctx.run(0))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
@@ -401,6 +406,7 @@ def main():
         proc.terminate()
         fh.close()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    res_builds = sum(r["list_builds"] for r in ctx.run(0)) - builds0
     total_s = float(step_ms.sum()) / 1e3
     if world > 1:
         t = torch.tensor([total_s], device=dev)
@@ -516,6 +522,9 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "warmup_steps_run": warm_steps,
+                       "pair_lists": (f"kept while displacements allow (skin {p.skin:g} A), "
+                                      f"{res_builds} builds in {args.steps} timed steps") if p.skin > 0 and
+                                     prec == R.RBSOG_FP32 else "rebuilt every step",
                        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                        "ns_per_day": (p.dt * 1e-6) / (float(step_ms.mean()) / 1e3 / 86400.0),
                        "energies": f"every {args.thermo} steps (thermo output); forces and virial every step",

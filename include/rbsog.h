@@ -105,6 +105,16 @@ typedef struct {
                                steps compute forces and the total virial only, which is
                                all the dynamics uses.  Forces and the total virial do
                                not depend on this setting.  Default 1 (every step). */
+    double skin;            /* A, FP32 build only (ignored in FP64): NPT steps keep the
+                               pair lists of the last build, made with cells and a
+                               candidate test at r_c + skin, while every atom's
+                               displacement since that build (after the affine rescaling
+                               of the box) stays below (min_a lambda_a (r_c + skin) - r_c)/2,
+                               lambda_a = L_a / L_a at the build; then no pair within r_c
+                               can be missing from them.  Otherwise, and on every
+                               rbsog_step, the lists are rebuilt.  0: rebuilt every step.
+                               The box must hold 2 cell_sub + 1 cells of (r_c + skin) /
+                               cell_sub. */
 } rbsog_params;
 
 typedef struct {
@@ -162,6 +172,7 @@ typedef struct {
     int n_distinct_modes;
     int n_accept_r, n_accept_nr;
     uint64_t step;
+    int list_builds;         /* pair-list builds of this system so far (FP32 build) */
 } rbsog_result;
 
 typedef struct rbsog_ctx rbsog_ctx;

@@ -60,6 +60,11 @@ struct DevSys {
     int nmol, mol0;       // molecules of the system and its first global molecule index
     int act;              // 1: the slot holds a system that steps; 0: empty or finished
     int steps_left;       // NPT steps before the system stops (-1: no limit)
+    int rebuild;          // 1: this evaluation bins the atoms and rebuilds the pair lists
+    int list_valid;       // 0: positions or box were set from the host since the last build
+    int list_builds;      // pair-list builds so far
+    double Lref[3];       // box at the last list build
+    double thr2;          // squared displacement bound of the current step (lists with a skin)
     unsigned long long rng_id;   // second word of the Philox key
     unsigned long long step;     // Philox counter of the system's last force evaluation
 };

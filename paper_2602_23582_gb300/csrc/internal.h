@@ -29,6 +29,7 @@ struct PairConstsF {
     int nff, nfe;               // exponentials for the force (l < nff) and the energy (l < nfe)
     float rc2, ke;
     float rc2_hi, rc2_lo;       // r_c^2 (1 +- 1e-5): pairs in between are decided in FP64
+    float rl2_hi;               // (r_c + skin)^2 (1 + 1e-5): the list build's radius
     double rc2d;                // r_c^2 in FP64
     float beta[kMaxGauss];      // log2(e) / s~_l^2 (force)
     float wt[kMaxGauss];        // w~_l
@@ -54,6 +55,8 @@ struct Batch {
     int C;                      // total cells (capacity)
     int sub;                    // cells per cutoff
     double rc;
+    double rlist;               // list radius r_c + skin (cells of rlist / sub)
+    int skin;                   // 1: NPT steps keep the lists while displacements allow
     DevSys *sys;                // [S]
     const int *atom_sys;        // [N]
     const int *cell_sys;        // [C]
@@ -88,6 +91,7 @@ struct AtomArrays {
     float4 *locf;               // [N] cell-local coords + mol bits (FP32)
     double4 *locd;              // [N] cell-local coords + q (FP64)
     uint4 *su;                  // [N] fixed-point fractional coords + q bits
+    double *xref;               // [3N] positions at the last list build
     int *count, *start;         // [C], [C + 1]
     int *sidx;                  // [N] cell-sorted original index
     float4 *pos4;               // [N] sorted, FP32
@@ -107,7 +111,14 @@ struct AtomArrays {
 // ---- k_bin.cu
 void launch_box_prep(const Batch &b, cudaStream_t st);
 void launch_clear_flags(const Batch &b, cudaStream_t st);
-void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
+// bins the atoms of the systems whose lists are rebuilt (all, outside NPT
+// steps with a skin); zero_counts: clear the cell counts first
+void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st, bool zero_counts = true);
+// cell-local coordinates (pos4) and fixed-point coordinates (su) of the atoms
+// of systems that keep their lists, in the cells of the last build
+void launch_refresh(const Batch &b, const AtomArrays &a, cudaStream_t st);
+// marks every system's lists stale (positions or box set from the host)
+void launch_invalidate_lists(const Batch &b, cudaStream_t st);
 void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
 
@@ -197,8 +208,10 @@ struct IntegArgs {
 // prep = 1: also the cell grid of the new box (k_box_prep's work)
 void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st);
 // bin = 1: also k_bin's work for the updated atoms (counts zeroed by the caller)
+// skin (with bin = 0): flag the system for a list rebuild when an atom has
+// moved beyond the step's displacement bound
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
-                        cudaStream_t st);
+                        cudaStream_t st, int skin = 0);
 constexpr int kKinSplit = 8;   // kinetic partials per atom chunk (one per force-assembly block)
 // F = pair partials + long-range force + Fmol (molecule terms; null: none),
 // then (kick != 0) the second half kick p += dt/2 F, and the kinetic tensor

@@ -8,6 +8,12 @@
 // exclusive scan gives the cell starts; atoms are scattered to their cell and
 // each cell's list is then sorted by original index, so the cell-sorted order
 // (and every sum over it) is deterministic.
+//
+// Lists with a skin (FP32 build, NPT steps): cells are r_list / sub wide,
+// r_list = r_c + skin, and the binning, scan, scatter, cell sort and list
+// build run only for systems flagged for a rebuild (DevSys::rebuild); the
+// others keep their cell-sorted order and lists, and k_refresh writes their
+// atoms' current coordinates relative to the cells of the last build.
 #include "internal.h"
 
 namespace rbsog {
@@ -17,6 +23,7 @@ __global__ void k_box_prep(DevSys *sys, int S, int sub, double rc)
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     DevSys &d = sys[s];
+    d.rebuild = 1;                            // an evaluation outside the NPT step: fresh lists
     const int minc = 2 * sub + 1;
     if (live_n(d) == 0) {                     // empty slot: a valid grid, no checks
         for (int a = 0; a < 3; ++a) { d.ncell[a] = minc; d.w[a] = 1.0; }
@@ -48,34 +55,90 @@ void launch_clear_flags(const Batch &b, cudaStream_t st)
 
 void launch_box_prep(const Batch &b, cudaStream_t st)
 {
-    k_box_prep<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, b.sub, b.rc);
+    k_box_prep<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S, b.sub, b.rlist);
+}
+
+__global__ void k_invalidate_lists(DevSys *sys, int S)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) sys[s].list_valid = 0;
+}
+
+void launch_invalidate_lists(const Batch &b, cudaStream_t st)
+{
+    k_invalidate_lists<<<(b.S + 127) / 128, 128, 0, st>>>(b.sys, b.S);
 }
 
 __global__ void k_bin(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys,
                       const double *__restrict__ r, const double *__restrict__ q,
                       const int *__restrict__ mol, int N, int *__restrict__ cell,
                       int *__restrict__ rank, int *__restrict__ count, float4 *__restrict__ locf,
-                      double4 *__restrict__ locd, uint4 *__restrict__ su, int precision)
+                      double4 *__restrict__ locd, uint4 *__restrict__ su, double *__restrict__ xref,
+                      int precision)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool live = false;
     if (i < N) {
         const DevSys &ds = sys[atom_sys[i]];
-        live = i - ds.atom0 < live_n(ds);     // slots hold up to their capacity
-        if (!live) cell[i] = -1;
+        if (ds.rebuild) {                     // else the atom keeps the cell of the last build
+            live = i - ds.atom0 < live_n(ds); // slots hold up to their capacity
+            if (!live) cell[i] = -1;
+        }
     }
     const unsigned act = __ballot_sync(0xffffffffu, live);
     if (!live) return;
     const DevSys &d = sys[atom_sys[i]];
     const double x[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
     bin_atom(d, i, x, q[i], mol[i], act, cell, rank, count, locf, locd, su, precision);
+    xref[3 * i] = x[0];
+    xref[3 * i + 1] = x[1];
+    xref[3 * i + 2] = x[2];
 }
 
-void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
+void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st, bool zero_counts)
 {
-    cudaMemsetAsync(a.count, 0, sizeof(int) * b.C, st);
+    if (zero_counts) cudaMemsetAsync(a.count, 0, sizeof(int) * b.C, st);
     k_bin<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.r, a.q, a.mol, b.N, a.cell, a.rank,
-                                             a.count, a.locf, a.locd, a.su, precision);
+                                             a.count, a.locf, a.locd, a.su, a.xref, precision);
+}
+
+// Atoms of systems that keep their lists: cell-local coordinates relative to
+// the cell of the last build (the image nearest that cell; the cell widths
+// follow the box) and fixed-point fractional coordinates, as bin_atom forms
+// them.  One thread per cell-sorted slot.
+__global__ void k_refresh(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys,
+                          const double *__restrict__ r, const double *__restrict__ q, const int *__restrict__ mol,
+                          const int *__restrict__ sidx, const int *__restrict__ cell, int N,
+                          float4 *__restrict__ pos4, uint4 *__restrict__ su)
+{
+    const int ks = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ks >= N) return;
+    const DevSys &d = sys[atom_sys[ks]];      // sorted slots keep their system's range
+    if (d.rebuild || ks - d.atom0 >= live_n(d)) return;
+    const int i = sidx[ks];
+    const int lc = cell[i] - d.cell0;
+    const int k[3] = {lc % d.ncell[0], (lc / d.ncell[0]) % d.ncell[1], lc / (d.ncell[0] * d.ncell[1])};
+    double sf[3], xl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double L = d.L[a];
+        double s = __ddiv_rn(r[3 * i + a], L);
+        s = __dsub_rn(s, floor(s));
+        if (s >= 1.0) s = 0.0;
+        sf[a] = s;
+        double x = s * L - k[a] * d.w[a];
+        x -= L * rint(x / L);
+        xl[a] = x;
+    }
+    pos4[ks] = make_float4((float)xl[0], (float)xl[1], (float)xl[2], __int_as_float(mol[i]));
+    su[i] = make_uint4(__double2uint_rz(sf[0] * 4294967296.0), __double2uint_rz(sf[1] * 4294967296.0),
+                       __double2uint_rz(sf[2] * 4294967296.0), __float_as_uint((float)q[i]));
+}
+
+void launch_refresh(const Batch &b, const AtomArrays &a, cudaStream_t st)
+{
+    k_refresh<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.r, a.q, a.mol, a.sidx, a.cell, b.N,
+                                                 a.pos4, a.su);
 }
 
 // Per-system exclusive scan of the cell counts (one block per system): the
@@ -129,6 +192,7 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
 {
     __shared__ int ta[1024], tg[1024];
     DevSys &d = sys[blockIdx.x];
+    if (!d.rebuild) return;                  // block-uniform: the system keeps its lists
     const int t = threadIdx.x, T = blockDim.x;
     const int C0 = d.cell0, nc = d.ncell_cap_total, n0 = d.ncell[0];
     const int per = (nc + T - 1) / T;
@@ -158,7 +222,12 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
     }
     scan_items(count, C0, c0, c1, n0, maxrun, items, rg, true);
     const int total = tg[T - 1];
-    if (t == T - 1) d.nitems = total;
+    if (t == T - 1) {
+        d.nitems = total;
+        d.Lref[0] = d.L[0]; d.Lref[1] = d.L[1]; d.Lref[2] = d.L[2];
+        d.list_valid = 1;
+        ++d.list_builds;
+    }
     for (int k = total + t; k < d.item_cap; k += T) items[d.item0 + k] = make_int2(-1, -1);
 }
 
@@ -172,11 +241,12 @@ void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_
     k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys, maxrun);
 }
 
-__global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ rank,
+__global__ void k_scatter(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys,
+                          const int *__restrict__ cell, const int *__restrict__ rank,
                           const int *__restrict__ start, int *__restrict__ sidx, int N)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || cell[i] < 0) return;
+    if (i >= N || !sys[atom_sys[i]].rebuild || cell[i] < 0) return;
     sidx[start[cell[i]] + rank[i]] = i;
 }
 
@@ -230,7 +300,7 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
 
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
 {
-    k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(a.cell, a.rank, a.start, a.sidx, b.N);
+    k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.cell, a.rank, a.start, a.sidx, b.N);
     k_cell_sort<<<b.C, kSortThreads, 0, st>>>(
         a.start, a.count, b.C, a.sidx, a.rank, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
 }

@@ -54,13 +54,15 @@ __device__ void box_force(const DevSys &d, const double *red, const IntegArgs &i
 constexpr int kBoxWarps = 4;
 
 __global__ void __launch_bounds__(32 * kBoxWarps)
-k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred, int prep_sub, double rc)
+k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred, int prep_sub, double rc,
+           double rlist, int skin)
 {
     const int s = blockIdx.x * kBoxWarps + (threadIdx.x >> 5), lane = lane_id();
     if (s >= S) return;
     DevSys &d = sys[s];
     if (live_n(d) == 0) {                     // empty or finished slot (warp-uniform)
         if (prep_sub > 0 && lane < 3) { d.ncell[lane] = 2 * prep_sub + 1; d.w[lane] = 1.0; }
+        if (prep_sub > 0 && lane == 0) d.rebuild = 1;
         return;
     }
     const double *red = sysred + (size_t)s * kRed;
@@ -118,20 +120,33 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
         d.invL[lane] = 1.0 / Ln;
     }
     if (prep_sub > 0) {
-        // the cell grid of the new box (as k_box_prep), so that the atom
-        // update can bin its atoms
+        // the cell grid of the new box (as k_box_prep, cells of rlist / sub),
+        // so that the atom update can bin its atoms
         bool bad = false;
+        int n = 0;
+        if (lane < 3) n = axis_cells(Ln, prep_sub, rlist, d.ncap[lane], &bad);
+        const bool anybad = __any_sync(0xffffffffu, bad);
+        const bool regrid = __any_sync(0xffffffffu, lane < 3 && n != d.ncell[lane]);
+        // lists with a skin stay valid while every displacement since the
+        // build, after the affine rescaling lambda_a = L_a / Lref_a, is below
+        // (min_a lambda_a rlist - r_c) / 2: a pair at least rlist apart then
+        // stays at least r_c apart
+        const double lam = lane < 3 ? Ln / d.Lref[lane] : 1e300;
+        const double lmin = fmin(__shfl_sync(0xffffffffu, lam, 0),
+                                 fmin(__shfl_sync(0xffffffffu, lam, 1), __shfl_sync(0xffffffffu, lam, 2)));
         if (lane < 3) {
-            const int n = axis_cells(Ln, prep_sub, rc, d.ncap[lane], &bad);
             d.ncell[lane] = n;
             d.w[lane] = Ln / n;
         }
-        const bool anybad = __any_sync(0xffffffffu, bad);
         const double L0 = __shfl_sync(0xffffffffu, Ln, 0), L1 = __shfl_sync(0xffffffffu, Ln, 1),
                      L2 = __shfl_sync(0xffffffffu, Ln, 2);
         if (lane == 0) {
             if (anybad) d.flags |= FLAG_BOX;
             d.V = L0 * L1 * L2;
+            const double thr = 0.5 * (lmin * rlist - rc);
+            const bool keep = skin && d.list_valid && !regrid && thr > 0.0;   // NaN lmin: rebuild
+            d.thr2 = keep ? thr * thr : 0.0;
+            d.rebuild = keep ? 0 : 1;
         }
     }
 }
@@ -139,7 +154,8 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
 void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st)
 {
     k_box_half<<<(b.S + kBoxWarps - 1) / kBoxWarps, 32 * kBoxWarps, 0, st>>>(b.sys, b.S, ia, sysred,
-                                                                            prep ? b.sub : 0, b.rc);
+                                                                            prep ? b.sub : 0, b.rc, b.rlist,
+                                                                            b.skin);
 }
 
 // Atom part of B (first half), A, O, A and the wrap.  Per-system drift
@@ -148,8 +164,11 @@ void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, 
 // FP64 (Box-Muller on the same Philox words as the CPU reference).
 // BIN: the updated atom is binned right away (as k_bin; the caller zeroed the
 // cell counts and set the new cell grid in k_box_half).
-template <bool NF32, bool BIN>
-__global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys, int N,
+// SKIN: the atom's displacement since the last list build, after the affine
+// rescaling of the box, is checked against the step's bound (k_box_half); a
+// larger one flags the system for a list rebuild.
+template <bool NF32, bool BIN, bool SKIN>
+__global__ void k_atom_update(DevSys *__restrict__ sys, const int *__restrict__ atom_sys, int N,
                               double *__restrict__ r, double *__restrict__ p, const double *__restrict__ F,
                               const IntegArgs ia, const AtomArrays aa, int precision)
 {
@@ -204,20 +223,34 @@ __global__ void k_atom_update(const DevSys *__restrict__ sys, const int *__restr
         r[3 * i + a] = x[a];
         p[3 * i + a] = v[a];
     }
+    if (SKIN && !d.rebuild) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double u = x[a] - aa.xref[3 * i + a] * (d.L[a] / d.Lref[a]);
+            u -= d.L[a] * rint(u * d.invL[a]);
+            d2 += u * u;
+        }
+        if (!(d2 <= d.thr2)) sys[s].rebuild = 1;   // every far atom writes the same value
+    }
     if (BIN) bin_atom(d, i, x, aa.q[i], aa.mol[i], act, aa.cell, aa.rank, aa.count, aa.locf, aa.locd, aa.su, precision);
 }
 
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
-                        cudaStream_t st)
+                        cudaStream_t st, int skin)
 {
     const int g = (b.N + 255) / 256;
+#define RBSOG_ATOM_UPDATE(NF, BN, SK) \
+    k_atom_update<NF, BN, SK><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision)
     if (ia.noise_f32) {
-        if (bin) k_atom_update<true, true><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
-        else k_atom_update<true, false><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
+        if (bin) RBSOG_ATOM_UPDATE(true, true, false);
+        else if (skin) RBSOG_ATOM_UPDATE(true, false, true);
+        else RBSOG_ATOM_UPDATE(true, false, false);
     } else {
-        if (bin) k_atom_update<false, true><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
-        else k_atom_update<false, false><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision);
+        if (bin) RBSOG_ATOM_UPDATE(false, true, false);
+        else if (skin) RBSOG_ATOM_UPDATE(false, false, true);
+        else RBSOG_ATOM_UPDATE(false, false, false);
     }
+#undef RBSOG_ATOM_UPDATE
 }
 
 // Per-system reduction of all partials (fixed order) into sysred[s][kRed]:
@@ -372,6 +405,7 @@ k_finalize(DevSys *sys, const double *__restrict__ pair_part, const double *__re
         if (d.steps_left > 0 && --d.steps_left == 0) d.act = 0;   // the last requested step
     }
     o[62] = (double)d.step;
+    o[63] = (double)d.list_builds;
 }
 
 __global__ void k_set_step(DevSys *sys, int S, unsigned long long step)

@@ -260,7 +260,7 @@ template <bool RUNS>
 __global__ void __launch_bounds__(32, 32)
 k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
              const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
-             PairList L, const float rc2_hi)
+             PairList L, const float rl2_hi)
 {
     __shared__ float4 offp[kMaxPlane];                 // x, y offset; column; code of row
     __shared__ HPair cand2[16];
@@ -273,6 +273,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     const int gc = item.x;
     const int s = cell_sys[gc];
     const DevSys &d = sys[s];
+    if (!d.rebuild) return;                            // the system keeps its lists
     const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
     const int lc = gc - d.cell0;
     const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
@@ -319,9 +320,10 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     // cell's centre: the loading lane stores (-2 b, |b|^2) in half precision,
     // two candidates per half2, so that a pair of candidates costs three
     // packed FMAs and one packed compare.  The test accepts r^2 below
-    // 1.025 r_c^2: for the coordinates that occur near r_c (|a| < 20 A,
-    // |b| < 10 A) its rounding error stays below 1.2 A^2, inside that margin,
-    // and the evaluation decides every pair exactly.  A short batch is padded
+    // 1.025 r_l^2, r_l = r_c + skin the list radius: for the coordinates that
+    // occur near r_l (|a| < 2 r_l, |b| < r_l) its rounding error stays below
+    // 0.012 r_l^2, inside that margin, and the evaluation decides every pair
+    // exactly.  A short batch is padded
     // with entries no lane can hit; pairs of one molecule pass this test and
     // are dropped by the evaluation (a few per atom at most).
     const float hx = 0.5f * (float)d.w[0], hy = 0.5f * (float)d.w[1], hz = 0.5f * (float)d.w[2];
@@ -330,7 +332,7 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
         const float bx = q.x - hx, by = q.y - hy, bz = q.z - hz;
         return make_float4(-2.f * bx, -2.f * by, -2.f * bz, fmaf(bx, bx, fmaf(by, by, bz * bz)));
     };
-    const float rc2_test = 1.025f * rc2_hi;
+    const float rc2_test = 1.025f * rl2_hi;
     int nb = 0, jb = 0, j0 = 0, nj = 0;
     for (;;) {                                         // first non-empty cell (warp-uniform)
         if (nb >= nn) break;
@@ -699,7 +701,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
     if (precision == 1) {
         // runs of several cells per item occur with cells of r_c / 2 (a dozen atoms)
         auto build = b.sub >= 2 ? k_pair_build<true> : k_pair_build<false>;
-        build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist, cf.rc2_hi);
+        build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist, cf.rl2_hi);
 #define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
     k_pair_eval<NF, EN><<<b.item_cap / kEvalGroups, 32 * kEvalSplit * kEvalGroups, 0, st>>>(b.sys, b.item_sys, \
                                                                 a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \

@@ -77,6 +77,7 @@ struct rbsog_ctx {
     float4 *locf = nullptr, *pos4 = nullptr;
     double4 *locd = nullptr, *posd = nullptr;
     uint4 *su = nullptr;
+    double *xref = nullptr;   // positions at the last list build
     int *count = nullptr, *start = nullptr, *sidx = nullptr, *cell_sys = nullptr;
     int *item_sys = nullptr;
     float2 *qt = nullptr;
@@ -135,6 +136,13 @@ struct rbsog_ctx {
 namespace {
 
 thread_local std::string g_create_err;   // error text of a failed rbsog_create
+
+// Radius of the pair lists and of the cells (r_c + skin; the skin applies to
+// the FP32 build only).
+double list_radius(const rbsog_params &P)
+{
+    return P.rc + (P.precision == RBSOG_FP32 ? P.skin : 0.0);
+}
 
 rbsog_status fail(rbsog_ctx *c, rbsog_status s, const std::string &msg)
 {
@@ -300,7 +308,16 @@ void enqueue_npt_step(rbsog_ctx *c, int energy)
     cudaMemsetAsync(c->count, 0, sizeof(int) * (size_t)c->C, c->st);
     launch_box_half(c->b, c->ia, c->sysred, 1, c->st);
     fork_sampler(c, 1);
-    launch_atom_update(c->b, c->a, c->ia, 1, c->prm.precision, c->st);
+    if (c->b.skin) {
+        // lists with a skin: the atom update flags the systems that rebuild,
+        // which are then binned; the others get their coordinates in the
+        // cells of their last build
+        launch_atom_update(c->b, c->a, c->ia, 0, c->prm.precision, c->st, 1);
+        launch_bin(c->b, c->a, c->prm.precision, c->st, false);
+        launch_refresh(c->b, c->a, c->st);
+    } else {
+        launch_atom_update(c->b, c->a, c->ia, 1, c->prm.precision, c->st);
+    }
     fork_mol(c, energy);
     enqueue_eval(c, 1, 1, energy, 1, 1);
 }
@@ -363,6 +380,7 @@ rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
         r.n_accept_r = (int)o[56];
         r.n_accept_nr = (int)o[57];
         r.step = (uint64_t)o[62];
+        r.list_builds = (int)o[63];
     }
     return RBSOG_OK;
 }
@@ -426,7 +444,7 @@ bool build_image(const rbsog_params &P, const SlotLayout &ly, DevSys &ds, const 
         return false;
     }
     for (int a = 0; a < 3; ++a) {
-        const double x = std::floor(d.box[a] * P.cell_sub / P.rc);
+        const double x = std::floor(d.box[a] * P.cell_sub / list_radius(P));
         if (!(x >= 2 * P.cell_sub + 1)) { why = "box edge too small for the cell stencil"; return false; }
         if (!(x <= ds.ncap[a])) { why = "box larger than its slot's cell grid"; return false; }
     }
@@ -538,7 +556,8 @@ rbsog_status validate_params(const rbsog_params *p)
     if (!(p->rc > 0) || !(p->b > 1) || !(p->sigma > 0) || p->M < 1 || p->M > kMaxGauss ||
         p->M_energy < p->M || p->M_energy > kMaxGauss || p->P < 1 || p->P > kMaxP ||
         p->sampler < 0 || p->sampler > 2 || (p->precision != 0 && p->precision != 1) ||
-        (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2 || p->thermo_every < 0)
+        (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2 || p->thermo_every < 0 ||
+        !(p->skin >= 0.0 && p->skin <= p->rc))
         return RBSOG_EINVAL;
     return RBSOG_OK;
 }
@@ -633,7 +652,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             c->prm.cell_sub = c->pool ? 2 : 1;
             for (int k = 0; systems && k < n_systems; ++k)
                 for (int a2 = 0; a2 < 3; ++a2)
-                    if (systems[k].box[a2] < 3.3 * c->prm.rc) c->prm.cell_sub = 2;
+                    if (systems[k].box[a2] < 3.3 * list_radius(c->prm)) c->prm.cell_sub = 2;
         }
         const rbsog_params &P = c->prm;
         c->S = n_systems;
@@ -685,7 +704,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             std::memset(&ds, 0, sizeof(ds));
             int ncap_t = 1;
             for (int a = 0; a < 3; ++a) {
-                const int n = (int)std::floor(cp.box[a] * P.cell_sub / P.rc);
+                const int n = (int)std::floor(cp.box[a] * P.cell_sub / list_radius(P));
                 if (n < 2 * P.cell_sub + 1) {
                     rbsog_status rr = fail(c, RBSOG_EBOX, "system " + std::to_string(k) + ": box edge " +
                                                               std::to_string(cp.box[a]) + " too small for the cell stencil");
@@ -693,7 +712,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                     return rr;
                 }
                 // room for the box to grow by 15% under pressure
-                const int cap = (int)std::floor(cp.box[a] * 1.15 * P.cell_sub / P.rc);
+                const int cap = (int)std::floor(cp.box[a] * 1.15 * P.cell_sub / list_radius(P));
                 ds.ncap[a] = std::max(cap, n);
                 ncap_t *= ds.ncap[a];
                 ds.L[a] = cp.box[a];
@@ -839,6 +858,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                 ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, N) && dalloc(c, c->qt, N) && dalloc(c, c->su, N);
             else
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N);
+            ok = ok && dalloc(c, c->xref, 3 * (size_t)N);
         }
         if (ok && P.precision == 1) {
             // FP32 pair lists: per (dz plane, atom) one entry per batch of 32
@@ -849,7 +869,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             const int span = 2 * P.cell_sub + 1;
             double rho = 0.0;
             for (int k = 0; k < S; ++k) rho = std::max(rho, caps[k].rho);
-            const double wc = 4.0 / 3.0 * P.rc / P.cell_sub;
+            const double wc = 4.0 / 3.0 * list_radius(P) / P.cell_sub;
             const double per_cell = std::min((double)kCellCap, 1.3 * rho * wc * wc * wc);
             const int maxent = span * span * ((int)std::ceil(per_cell / 32.0) + 1);
             const double total = (double)span * maxent * N;
@@ -880,6 +900,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->pcf.rc2 = (float)(P.rc * P.rc); c->pcd.rc2 = P.rc * P.rc; c->pcf.rc2d = P.rc * P.rc;
         c->pcf.rc2_hi = (float)(P.rc * P.rc * (1.0 + 1e-5));
         c->pcf.rc2_lo = (float)(P.rc * P.rc * (1.0 - 1e-5));
+        c->pcf.rl2_hi = (float)(list_radius(P) * list_radius(P) * (1.0 + 1e-5));
         c->pcf.ke = (float)P.ke; c->pcd.ke = P.ke;
         for (int l = 0; l < MM; ++l) {
             c->pcd.inv_s2[l] = 1.0 / (s[l] * s[l]);
@@ -937,12 +958,14 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->ia.noise_f32 = P.precision == RBSOG_FP32 ? 1 : 0;
 
         c->b.S = S; c->b.N = N; c->b.C = C; c->b.sub = P.cell_sub; c->b.rc = P.rc; c->b.sys = c->sys;
+        c->b.rlist = list_radius(P);
+        c->b.skin = c->b.rlist > P.rc ? 1 : 0;
         c->b.atom_sys = c->atom_sys; c->b.cell_sys = c->cell_sys; c->b.item_sys = c->item_sys; c->b.chunk_sys = c->chunk_sys;
         c->b.chunk_a0 = c->chunk_a0; c->b.chunk_n = c->chunk_n; c->b.nchunks = c->nchunks;
         c->b.item_cap = item_cap;
         c->a.r = c->r; c->a.p = c->p; c->a.F = c->F; c->a.q = c->q; c->a.mass = c->mass; c->a.type = c->type;
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
-        c->a.su = c->su; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
+        c->a.su = c->su; c->a.xref = c->xref; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
         c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
@@ -1025,6 +1048,8 @@ rbsog_status rbsog_pool_load(rbsog_ctx *c, int slot, const rbsog_system_desc *sy
         return fail(c, RBSOG_EINVAL, "rbsog_pool_load: slot " + std::to_string(slot) + ": " + why);
     ds.act = 1;
     ds.steps_left = nsteps;
+    ds.list_valid = 0;
+    ds.list_builds = 0;
     c->slot_err[slot] = RBSOG_OK;
     auto put = [&](auto *dst, const auto &v) {
         if (e == cudaSuccess && !v.empty())
@@ -1105,7 +1130,7 @@ rbsog_status rbsog_set_box(rbsog_ctx *c, int s, const double box[3], int rescale
 {
     if (!c || s < 0 || s >= c->S || !box) return RBSOG_EINVAL;
     for (int a = 0; a < 3; ++a)
-        if (!(box[a] > 0) || (int)std::floor(box[a] * c->prm.cell_sub / c->prm.rc) < 2 * c->prm.cell_sub + 1)
+        if (!(box[a] > 0) || (int)std::floor(box[a] * c->prm.cell_sub / list_radius(c->prm)) < 2 * c->prm.cell_sub + 1)
             return fail(c, RBSOG_EBOX, "box edge below 3 cells");
     DevSys h;
     cudaError_t e = cudaMemcpyAsync(&h, c->sys + s, sizeof(DevSys), cudaMemcpyDeviceToHost, c->st);
@@ -1121,6 +1146,7 @@ rbsog_status rbsog_set_box(rbsog_ctx *c, int s, const double box[3], int rescale
     }
     for (int a = 0; a < 3; ++a) h.L[a] = box[a];
     h.V = box[0] * box[1] * box[2];
+    h.list_valid = 0;
     e = cudaMemcpy(c->sys + s, &h, sizeof(DevSys), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_box");
     return RBSOG_OK;
@@ -1132,6 +1158,7 @@ rbsog_status rbsog_set_positions(rbsog_ctx *c, const double *r, int on_device)
     cudaError_t e = cudaMemcpyAsync(c->r, r, 3 * sizeof(double) * c->N,
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_positions");
+    launch_invalidate_lists(c->b, c->st);
     return RBSOG_OK;
 }
 
@@ -1362,6 +1389,7 @@ rbsog_status rbsog_set_state(rbsog_ctx *c, const void *buf, size_t len)
     o += sizeof(DevSys) * c->S;
     if (e == cudaSuccess) e = cudaMemcpy(c->sysred, o, sizeof(double) * c->S * kRed, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    launch_invalidate_lists(c->b, c->st);     // the lists are not part of the state
     c->h_step = step;
     return RBSOG_OK;
 }

@@ -56,7 +56,7 @@ class rbsog_params(C.Structure):
                 ("seed", C.c_uint64), ("precision", C.c_int), ("ke", C.c_double),
                 ("dt", C.c_double), ("T", C.c_double), ("P_ext", C.c_double), ("gamma", C.c_double),
                 ("gamma_box", C.c_double), ("tau_box", C.c_double), ("compressibility", C.c_double),
-                ("coupling", C.c_int), ("cell_sub", C.c_int), ("thermo_every", C.c_int)]
+                ("coupling", C.c_int), ("cell_sub", C.c_int), ("thermo_every", C.c_int), ("skin", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -78,7 +78,8 @@ class rbsog_result(C.Structure):
                 ("virial_long_nr", C.c_double * 9), ("virial_lj", C.c_double * 9),
                 ("virial_bonded", C.c_double * 9), ("pressure", C.c_double * 9),
                 ("box", C.c_double * 3), ("volume", C.c_double), ("n_distinct_modes", C.c_int),
-                ("n_accept_r", C.c_int), ("n_accept_nr", C.c_int), ("step", C.c_uint64)]
+                ("n_accept_r", C.c_int), ("n_accept_nr", C.c_int), ("step", C.c_uint64),
+                ("list_builds", C.c_int)]
 
 
 _lib = None
@@ -373,7 +374,7 @@ def result_dict(r: rbsog_result) -> dict:
                virial_long_r=t(r.virial_long_r), virial_long_nr=t(r.virial_long_nr),
                virial_lj=t(r.virial_lj), virial_bonded=t(r.virial_bonded), pressure=t(r.pressure),
                box=np.array(r.box[:]), volume=r.volume, n_distinct_modes=r.n_distinct_modes,
-               n_accept_r=r.n_accept_r, n_accept_nr=r.n_accept_nr, step=r.step)
+               n_accept_r=r.n_accept_r, n_accept_nr=r.n_accept_nr, step=r.step, list_builds=r.list_builds)
     return out
 
 

@@ -78,7 +78,8 @@ def test_without_gpu_create_fails_loudly():
 def test_invalid_arguments_are_rejected_before_any_device_call():
     import workloads as W
     s = W.electrolyte(n_ions=100, L=30.0, seed=1)
-    for bad in (dict(P=0), dict(M=0), dict(M=70), dict(sampler=7), dict(precision=3), dict(cell_sub=3)):
+    for bad in (dict(P=0), dict(M=0), dict(M=70), dict(sampler=7), dict(precision=3), dict(cell_sub=3),
+                dict(skin=-1.0), dict(skin=float("nan")), dict(skin=11.0)):
         p = R.rbsog_default_params(10.0, **bad)
         with pytest.raises(R.RbsogError) as e:
             R.rbsog_create(p, [s])

@@ -133,6 +133,52 @@ def test_eval_fp32_run_items_wrapping_stencil():
     assert abs(r["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
 
 
+def _last_forces(ctx, n):
+    # forces of the last evaluation, from the state record (header, r, p, F, ...)
+    state = R.rbsog_get_state(ctx.ctx)
+    return np.frombuffer(state, np.float64, 3 * n, 16 + 48 * n).reshape(n, 3)
+
+
+@pytest.mark.parametrize("name", ["electrolyte", "water_small"])
+def test_skin_lists_match_oracle_after_npt_steps(name):
+    # lists kept over NPT steps while the displacement bound holds: the last
+    # step's forces and virial equal the oracle's at its positions and box
+    import copy
+    s = SYSTEMS[name]()
+    ctx, p = _ctx([s], R.RBSOG_FP32, skin=1.0, thermo_every=0)
+    res = ctx.run(40)[0]
+    F = _last_forces(ctx, s.n)
+    s2 = copy.copy(s)
+    s2.pos = ctx.positions()
+    s2.box = np.array(res["box"])
+    ctx.close()
+    # the context's first evaluation builds, then NPT steps rebuild only now and then
+    assert 2 <= res["list_builds"] <= 30, res["list_builds"]
+    ref = O.force_eval(s2, _oracle_params(p), int(res["step"]))
+    assert _rel(F, ref["F"]) < 1e-5
+    assert _rel(res["virial"], ref["W"]) < 1e-6
+    assert abs(res["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
+
+
+def test_skin_lists_alone_equals_mixed():
+    systems = [W.electrolyte(n_ions=600, L=31.0, seed=11), W.water(n_mol=1500, L=36.0, lattice=12, seed=12)]
+    for k, s in enumerate(systems):
+        s.rng_id = 300 + k
+    mix, _ = _ctx(systems, R.RBSOG_FP32, cell_sub=2, skin=1.5)
+    rm = mix.run(25)
+    pos_m = mix.positions()
+    mix.close()
+    off = 0
+    for k, s in enumerate(systems):
+        alone, _ = _ctx([s], R.RBSOG_FP32, cell_sub=2, skin=1.5)
+        ra = alone.run(25)
+        assert np.array_equal(alone.positions(), pos_m[off:off + s.n]), k
+        assert np.array_equal(ra[0]["pressure"], rm[k]["pressure"]), k
+        assert ra[0]["list_builds"] == rm[k]["list_builds"] < 26, k
+        alone.close()
+        off += s.n
+
+
 def test_eval_fp32_full_water_box():
     # the benchmark workload (10,000 molecules, 30,000 sites) at full size
     s = W.water()
