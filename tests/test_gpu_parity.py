@@ -160,6 +160,21 @@ def test_skin_lists_match_oracle_after_npt_steps(name):
     assert abs(res["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
 
 
+def test_skin_lists_rebuilt_after_host_changes():
+    s = SYSTEMS["water_small"]()
+    ctx, p = _ctx([s], R.RBSOG_FP32, skin=1.5, thermo_every=0)
+    b0 = ctx.run(1)[0]["list_builds"]
+    b1 = ctx.run(1)[0]["list_builds"]
+    assert b1 == b0                                  # a small step keeps the lists
+    ctx.set_positions(ctx.positions())               # positions from the host: rebuilt
+    b2 = ctx.run(1)[0]["list_builds"]
+    assert b2 == b1 + 1
+    R.rbsog_set_box(ctx.ctx, 0, ctx.run(0)[0]["box"])   # box from the host: rebuilt
+    b3 = ctx.run(1)[0]["list_builds"]
+    assert b3 == b2 + 1
+    ctx.close()
+
+
 def test_skin_lists_alone_equals_mixed():
     systems = [W.electrolyte(n_ions=600, L=31.0, seed=11), W.water(n_mol=1500, L=36.0, lattice=12, seed=12)]
     for k, s in enumerate(systems):
