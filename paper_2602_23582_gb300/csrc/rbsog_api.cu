@@ -128,6 +128,7 @@ struct rbsog_ctx {
     unsigned long long h_step = 0;   // host copy of the device step counter
     // timing
     bool timing = false;
+    bool mol_late = false;    // molecule terms joined before the force assembly (large molecules)
     std::vector<std::string> t_names;
     std::vector<cudaEvent_t> t_events;
     std::vector<double> t_ms;
@@ -242,8 +243,11 @@ void fork_kspace(rbsog_ctx *c)
 }
 
 // Molecule terms on the third stream: they need only the positions and the
-// box, run beside the binning into their own force buffer, and end before
-// the pair kernels.
+// box and run beside the binning into their own force buffer.  Small
+// molecules (a thread each, a few tens of microseconds) join before the pair
+// kernels, so that they do not take SMs from them; large ones (a warp each,
+// e.g. 15-site ions with 137 terms: several times longer) join before the
+// force assembly and overlap the pair kernels.
 void fork_mol(rbsog_ctx *c, int energy)
 {
     if (c->m.nmchunks == 0) return;
@@ -275,7 +279,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     record(c, "scan");
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
-    if (mol) cudaStreamWaitEvent(c->st, c->ev_join3, 0);
+    if (mol && !c->mol_late) cudaStreamWaitEvent(c->st, c->ev_join3, 0);
     // in a graph capture: event-record nodes around the pair kernel (external
     // records, not dependencies), retargeted per launch by arm_pair_trace
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -293,6 +297,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
     if (c->timing) enqueue_kspace(c, c->st);
+    if (mol && c->mol_late) cudaStreamWaitEvent(c->st, c->ev_join3, 0);
     launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, mol ? c->Fmol : nullptr, c->ia, kick, c->kin_part, c->st);
     record(c, "lr_force_kick");
     cudaStreamWaitEvent(c->st, c->ev_join4, 0);
@@ -749,6 +754,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             // average, else chunks of a few large molecules (one warp each)
             const int mch = (double)cp.bonds + cp.angles + cp.excl <= (double)kSmallTerms * cp.mols
                                 ? kMolChunk : kMolChunkLarge;
+            if (mch == kMolChunkLarge && cp.mols > 0) c->mol_late = true;
             for (int m0 = 0; m0 < cp.mols; m0 += mch) {
                 mchunk_sys.push_back(k);
                 mchunk_m0.push_back(nmolx + m0);
