@@ -64,16 +64,19 @@ def workload(name: str, rank: int = 0):
         return [s], "membrane-like slab 64x64x96 A, 120,000 sites, semi-isotropic, rc=10 A, P=100"
     if name == "big_water":
         s = W.big_water()
-        return [s], "water-like box, 10,000,002 sites (3,333,334 molecules), L=463.7 A, rc=10 A, P=100"
+        return [s], "water-like box, 10,290,000 sites (7^3 copies of the 10,000-molecule box), L=468.16 A, rc=10 A, P=100"
     raise ValueError(name)
 
 
 def relax(R, systems, prec, stages=((0.01, 300), (0.1, 300), (0.5, 300))):
     """Damped fixed-box Langevin steps (friction 1/fs, 300 K) at growing time
     steps, from a synthetic start whose sites overlap (LJ contacts well inside
-    sigma): the overlaps push atoms apart with forces up to ~1e5 kcal/mol/A,
-    which at the production time step would heat the system to a gas.  The
-    systems' positions and velocities are replaced by the relaxed ones."""
+    sigma in the ionic-liquid and membrane starts; in a 10^7-site lattice of
+    randomly oriented water molecules, a few sites of neighbours almost on
+    top of each other): the overlaps push atoms apart with forces up to
+    ~1e5 kcal/mol/A, which at the production time step would heat the system
+    to a gas or make it diverge.  The systems' positions and velocities are
+    replaced by the relaxed ones."""
     for dt, n in stages:
         p = R.rbsog_default_params(10.0, precision=prec, thermo_every=0, dt=dt, gamma=1.0,
                                    coupling=R.RBSOG_COUPLE_FIXED)

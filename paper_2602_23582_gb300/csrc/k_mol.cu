@@ -139,9 +139,9 @@ __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, c
 // kSmallTerms terms is one thread's (its terms in order: bonds, angles,
 // exclusions, each added to its atoms' forces at once).  A larger molecule is
 // one warp's: its terms are spread over the lanes in passes of kTermPass,
-// each term stores its atoms' contributions in shared memory (in R), and the
-// lane that holds an atom's first contribution of the pass adds them all in
-// term order and adds the sum to F.  F is zeroed by the caller; a molecule's atoms
+// each term stores its atoms' contributions in shared memory (in R), and
+// lane k sums the contributions to the pass's k-th atom in term order and
+// adds the sum to F.  F is zeroed by the caller; a molecule's atoms
 // are written by its thread or warp only, and every sum runs in a fixed
 // order.  R is the arithmetic type of the exclusion terms (float in the FP32
 // build): differences of positions are formed in FP64, then rounded.
@@ -219,22 +219,33 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
                 }
             }
             __syncwarp();
-            // per atom: the lane owning its first slot of the pass sums its slots in order
+            // per atom (a molecule's atoms are contiguous): lane k takes atom
+            // lo + k of the pass and sums its slots in slot order; every lane
+            // reads the same slot at a time (a shared-memory broadcast), so
+            // the scans run side by side
+            int lo = 0x7fffffff, hi = -1;
             for (int sl = lane; sl < 3 * np; sl += 32) {
                 const int at = sa[sl];
-                if (at < 0) continue;
-                bool first = true;
-                for (int u = 0; u < sl && first; ++u) first = sa[u] != at;
-                if (!first) continue;
+                if (at >= 0) { lo = min(lo, at); hi = max(hi, at); }
+            }
+            lo = __reduce_min_sync(0xffffffffu, lo);
+            hi = __reduce_max_sync(0xffffffffu, hi);
+            for (int at = lo + lane; at <= hi; at += 32) {
                 // the adds run in R: in the FP32 build no FP64 instruction is
                 // issued here, where few lanes are active (an FP64 warp
                 // instruction costs the same for one lane as for 32)
-                R g[3] = {sf[sl][0], sf[sl][1], sf[sl][2]};
-                for (int u = sl + 1;; ++u) {
-                    while (u < 3 * np && sa[u] != at) ++u;
-                    if (u >= 3 * np) break;
-                    g[0] += sf[u][0]; g[1] += sf[u][1]; g[2] += sf[u][2];
+                R g[3] = {0, 0, 0};
+                bool any = false;
+                for (int u = 0; u < 3 * np; ++u) {
+                    if (sa[u] != at) continue;
+                    if (any) {
+                        g[0] += sf[u][0]; g[1] += sf[u][1]; g[2] += sf[u][2];
+                    } else {
+                        g[0] = sf[u][0]; g[1] = sf[u][1]; g[2] = sf[u][2];
+                        any = true;
+                    }
                 }
+                if (!any) continue;
                 const double gd[3] = {(double)g[0], (double)g[1], (double)g[2]};
                 const double f0 = F[3 * at], f1 = F[3 * at + 1], f2 = F[3 * at + 2];
                 F[3 * at] = f0 + gd[0];

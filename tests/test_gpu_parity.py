@@ -194,6 +194,19 @@ def test_skin_lists_alone_equals_mixed():
         off += s.n
 
 
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32])
+def test_eval_large_molecules_match_oracle(prec):
+    # 15-site anions (32 springs and 105 excluded pairs each): the molecule
+    # terms run one warp per molecule, its per-atom sums in shared memory
+    s = W.ionic_liquid(n_pairs=100, seed=5)
+    F, r, ref = _compare_eval(s, prec)
+    tol_f, tol_w = (1e-10, 1e-10) if prec == R.RBSOG_FP64 else (1e-5, 1e-6)
+    assert _rel(F, ref["F"]) < tol_f
+    assert _rel(r["virial"], ref["W"]) < tol_w
+    assert abs(r["bond"] - ref["bond"]) <= tol_w * max(abs(ref["bond"]), 1.0)
+    assert abs(r["coul"] - ref["coul"]) <= tol_w * abs(ref["coul"])
+
+
 def test_eval_fp32_full_water_box():
     # the benchmark workload (10,000 molecules, 30,000 sites) at full size
     s = W.water()
