@@ -64,7 +64,7 @@ def workload(name: str, rank: int = 0):
         return [s], "membrane-like slab 64x64x96 A, 120,000 sites, semi-isotropic, rc=10 A, P=100"
     if name == "big_water":
         s = W.big_water()
-        return [s], "water-like box, 10,290,000 sites (7^3 copies of the 10,000-molecule box), L=468.16 A, rc=10 A, P=100"
+        return [s], "water-like box, 10,000,002 sites (3,333,334 molecules, no two molecules' sites within 0.8 A), L=463.7 A, rc=10 A, P=100"
     raise ValueError(name)
 
 

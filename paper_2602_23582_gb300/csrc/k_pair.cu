@@ -274,6 +274,10 @@ k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const i
     const int s = cell_sys[gc];
     const DevSys &d = sys[s];
     if (!d.rebuild) return;                            // the system keeps its lists
+    // a cell beyond kCellCap atoms (flagged by the scan; e.g. non-finite
+    // coordinates all binned into one cell) would make this unit walk
+    // millions of candidates: the step is reported failed, skip its pairs
+    if (d.flags & FLAG_OVERFLOW) return;
     const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
     const int lc = gc - d.cell0;
     const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
@@ -440,7 +444,8 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
     float wv[18];                                      // Wc, Wl (energy steps), W
 #pragma unroll
     for (int k = 0; k < 18; ++k) wv[k] = 0.f;
-    if (32 * (blockIdx.x * kEvalGroups - d.item0) < nlive) {   // block-uniform: some group is live
+    const bool ok = !(d.flags & FLAG_OVERFLOW);       // lists of a failed step are not walked
+    if (ok && 32 * (blockIdx.x * kEvalGroups - d.item0) < nlive) {   // block-uniform: some group is live
         // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
         // must not shift every cross-cell distance the same way)
         for (int nb = threadIdx.x; nb < span * span * span; nb += blockDim.x) {
@@ -456,7 +461,7 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
         }
         __syncthreads();
     }
-    if (g32 < nlive) {                                 // warp-uniform
+    if (ok && g32 < nlive) {                           // warp-uniform
         const int ks = d.atom0 + g32 + lane;           // this lane's atom (cell-sorted index)
         const bool vi = g32 + lane < nlive;
         float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -598,7 +603,8 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
     double red[kPairRec];
 #pragma unroll
     for (int k = 0; k < kPairRec; ++k) red[k] = 0.0;
-    if (item.x >= 0) {
+    // (a system with a cell beyond kCellCap atoms has failed its step: skipped)
+    if (item.x >= 0 && !(sys[cell_sys[item.x]].flags & FLAG_OVERFLOW)) {
         const int gc = item.x;
         const DevSys &d = sys[cell_sys[gc]];
         const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];

@@ -261,27 +261,45 @@ def water(n_mol: int = 10000, L: float = 66.88, seed: int = 2, lattice: int = 22
                    angles, np.full(na, _WATER_KA), np.full(na, _WATER_T0))
 
 
-def big_water(n_rep: int = 7, seed: int = 6) -> System:
-    """The ~10^7-site water-like scale point: n_rep^3 copies of a
-    10,000-molecule box (``water`` with this seed) on a cubic grid, 7^3 =
-    343 copies = 3,430,000 molecules, 10,290,000 sites, L = 468.16 A at
-    1 g/cm^3.  Copies of a box known to run stably: a single lattice of 3.4e6
-    randomly oriented molecules holds, somewhere, O-H contacts far inside the
-    hydrogen-bond distance that collapse under the first steps (H has no LJ
-    core).  The copies decorrelate through their Langevin noise."""
-    base = water(seed=seed)
-    n1, nm1 = base.n, 10000
-    k = np.arange(n_rep ** 3)
-    off = np.stack(np.unravel_index(k, (n_rep,) * 3), -1) * base.box
-    pos = (base.pos[None, :, :] + off[:, None, :]).reshape(-1, 3)
-    mol = (base.mol[None, :] + nm1 * k[:, None]).reshape(-1)
-    bonds = (base.bonds[None] + n1 * k[:, None, None]).reshape(-1, 2)
-    angles = (base.angles[None] + n1 * k[:, None, None]).reshape(-1, 3)
-    rep = n_rep ** 3
-    return _finish("water", pos, np.tile(base.q, rep), np.tile(base.mass, rep), np.tile(base.type, rep), mol,
-                   base.box * n_rep, [_SPCE_EPS_O, 0.0], [_SPCE_SIG_O, 1.0],
-                   bonds, np.tile(base.bond_k, rep), np.tile(base.bond_r0, rep),
-                   angles, np.tile(base.angle_k, rep), np.tile(base.angle_t0, rep))
+def big_water(n_sites: int = 10_000_000, seed: int = 6, min_contact: float = 0.8) -> System:
+    """The 10^7-site water-like scale point: ceil(n_sites/3) molecules at
+    1 g/cm^3 (L = 463.7 A for 3,333,334 molecules), jittered lattice, random
+    orientations redrawn (all at once per round) for every molecule with a
+    site closer than ``min_contact`` to another molecule's site: among 3.3e6
+    random orientations some O-H contacts come out far closer than any in the
+    10,000-molecule box (0.80 A there, which runs stably), and H carries no LJ
+    core to stop them collapsing."""
+    from scipy.spatial import cKDTree
+    n_mol = -(-n_sites // 3)
+    L = 66.88 * (n_mol / 10000.0) ** (1.0 / 3.0)
+    lattice = int(math.ceil(n_mol ** (1.0 / 3.0)))
+    rng = np.random.default_rng(seed)
+    a = L / lattice
+    g = np.arange(lattice)
+    grid = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:n_mol]
+    centres = (grid + 0.5) * a + rng.uniform(-0.2, 0.2, (n_mol, 3))
+    R = _random_rotations(rng, n_mol)
+    frame = _water_frame()
+    sites = centres[:, None, :] + np.einsum("nij,sj->nsi", R, frame)
+    box = np.array([L, L, L])
+    for _ in range(100):
+        p = np.mod(sites.reshape(-1, 3), box)
+        p[p >= box] = 0.0
+        pairs = cKDTree(p, boxsize=box).query_pairs(min_contact, output_type="ndarray") // 3
+        bad = np.unique(pairs[pairs[:, 0] != pairs[:, 1]])
+        if bad.size == 0:
+            break
+        R[bad] = _random_rotations(rng, bad.size)
+        sites[bad] = centres[bad][:, None, :] + np.einsum("nij,sj->nsi", R[bad], frame)
+    else:
+        raise RuntimeError("could not remove close contacts")
+    pos, q, mass, mol, bonds, angles = _water_block(centres, R, 0, 0)
+    typ = np.tile(np.array([0, 1, 1], np.int32), n_mol)
+    nb, na = len(bonds), len(angles)
+    return _finish("water", pos, q, mass, typ, mol, box,
+                   [_SPCE_EPS_O, 0.0], [_SPCE_SIG_O, 1.0],
+                   bonds, np.full(nb, _WATER_KB), np.full(nb, _WATER_R0),
+                   angles, np.full(na, _WATER_KA), np.full(na, _WATER_T0))
 
 
 def _anion_template(rng, n_sites=15, radius=3.5, dmin=1.2):
