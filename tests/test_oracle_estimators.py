@@ -199,3 +199,23 @@ def test_shared_proposal_weight_is_the_target_ratio(tiny):
     V = float(np.prod(tiny.box))
     ref = -p.ke * Hr.sum() / (8 * V * p.P) * (fnr / fr) * abs(rh[0]) ** 2 * np.outer(k, k) / k2 ** 2
     assert np.allclose(Wsh, ref, rtol=1e-12, atol=0)
+
+
+def test_pressure_variance_does_not_grow_with_N():
+    # Theorem 3.7 (Debye-Hueckel regime): the variance of the random-batch
+    # pressure is bounded independently of N.  At fixed density, 8,000 and
+    # 27,000 ions give the same spread of P^F,r* and P^F,nr* over counters
+    # (the per-atom force noise, by contrast, grows with the box)
+    sds = []
+    for n, L in ((8000, 60.0), (27000, 90.0)):
+        s = W.electrolyte(n_ions=n, L=L, seed=1)
+        p = O.Params.row2(P=100)
+        V = float(np.prod(s.box))
+        r, nr = [], []
+        for step in range(40):
+            _, _, wr, wnr, _ = _rb(s, p, step)
+            r.append(wr[0, 0] / V)
+            nr.append(wnr[0, 0] / V)
+        sds.append((np.std(r, ddof=1), np.std(nr, ddof=1)))
+    for k in range(2):
+        assert 0.6 < sds[1][k] / sds[0][k] < 1.7, sds
