@@ -349,3 +349,17 @@ def test_shared_proposal_estimator_matches_oracle(name, prec, tol):
     ref = O.nr_shared(s.box, op, D, cr, rh, Hr.sum())
     assert np.allclose(g, g.T, rtol=0, atol=0)
     assert _rel(g, ref) < tol
+
+
+@pytest.mark.parametrize("prec", [R.RBSOG_FP32, R.RBSOG_FP64])
+def test_overfull_cell_is_reported_without_pair_work(prec):
+    # 2,500 atoms inside one 10 A cell (beyond the 2,048 a cell takes): the
+    # scan flags the system, the pair kernels skip it (instead of walking the
+    # cell's atoms from every work item) and the first evaluation reports
+    # RBSOG_EOVERFLOW
+    s = W.random_charges(n=3000, box=(30.0, 30.0, 30.0), seed=3, min_dist=0.3)
+    rng = np.random.default_rng(3)
+    s.pos[:2500] = rng.uniform(0.5, 4.5, (2500, 3))
+    with pytest.raises(R.RbsogError) as e:
+        R.Context([s], R.rbsog_default_params(10.0, precision=prec, cell_sub=1))
+    assert e.value.status == -8
