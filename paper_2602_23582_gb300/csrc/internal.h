@@ -206,7 +206,9 @@ struct IntegArgs {
     uint64_t seed;                    // a step uses the Philox counter DevSys::step + 1
 };
 // prep = 1: also the cell grid of the new box (k_box_prep's work)
-void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st);
+// count (optional): zeroes the C cell counts in the same launch
+void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st,
+                     int *count = nullptr);
 // bin = 1: also k_bin's work for the updated atoms (counts zeroed by the caller)
 // skin (with bin = 0): flag the system for a list rebuild when an atom has
 // moved beyond the step's displacement bound

@@ -11,6 +11,8 @@
 //   force evaluation (counter n)
 //   B  p += dt/2 F ftm2v;  K = sum p (x) p / m;  p^h += dt/2 G(K, W) ftm2v
 // with the generalised box force G_g = sum_{a in g} (K_aa + W_aa - P_ext V - kB T) / L_a.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace rbsog {
@@ -55,8 +57,11 @@ constexpr int kBoxWarps = 4;
 
 __global__ void __launch_bounds__(32 * kBoxWarps)
 k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sysred, int prep_sub, double rc,
-           double rlist, int skin)
+           double rlist, int skin, int *__restrict__ count, int C)
 {
+    // the cell counts of the step's binning start at zero (count: null to keep them)
+    if (count)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < C; k += gridDim.x * blockDim.x) count[k] = 0;
     const int s = blockIdx.x * kBoxWarps + (threadIdx.x >> 5), lane = lane_id();
     if (s >= S) return;
     DevSys &d = sys[s];
@@ -151,11 +156,11 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
     }
 }
 
-void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st)
+void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, int prep, cudaStream_t st,
+                     int *count)
 {
-    k_box_half<<<(b.S + kBoxWarps - 1) / kBoxWarps, 32 * kBoxWarps, 0, st>>>(b.sys, b.S, ia, sysred,
-                                                                            prep ? b.sub : 0, b.rc, b.rlist,
-                                                                            b.skin);
+    const int g = std::max((b.S + kBoxWarps - 1) / kBoxWarps, count ? (b.C + 32 * kBoxWarps * 8 - 1) / (32 * kBoxWarps * 8) : 1);
+    k_box_half<<<g, 32 * kBoxWarps, 0, st>>>(b.sys, b.S, ia, sysred, prep ? b.sub : 0, b.rc, b.rlist, b.skin, count, b.C);
 }
 
 // Atom part of B (first half), A, O, A and the wrap.  Per-system drift

@@ -310,8 +310,7 @@ void enqueue_npt_step(rbsog_ctx *c, int energy)
 {
     // box half-step with the new cell grid, the sampler forked right after
     // it, then the atom update with the binning of the moved atoms
-    cudaMemsetAsync(c->count, 0, sizeof(int) * (size_t)c->C, c->st);
-    launch_box_half(c->b, c->ia, c->sysred, 1, c->st);
+    launch_box_half(c->b, c->ia, c->sysred, 1, c->st, c->count);
     fork_sampler(c, 1);
     if (c->b.skin) {
         // lists with a skin: the atom update flags the systems that rebuild,
