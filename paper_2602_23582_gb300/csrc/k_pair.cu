@@ -257,7 +257,7 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // assembly.
 // ---------------------------------------------------------------------------
 template <bool RUNS>
-__global__ void __launch_bounds__(32, 32)
+__global__ void __launch_bounds__(32, 20)
 k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
              const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
              PairList L, const float rl2_hi)
