@@ -256,8 +256,11 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // Segment k writes force partial k, summed in segment order by the force
 // assembly.
 // ---------------------------------------------------------------------------
+// Resident blocks per SM: 20 for one-cell items (80 registers, no spills;
+// 32 blocks measured slower), 32 for runs of small cells, whose short units
+// need more warps to hide their latency.
 template <bool RUNS>
-__global__ void __launch_bounds__(32, 20)
+__global__ void __launch_bounds__(32, RUNS ? 32 : 20)
 k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
              const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
              PairList L, const float rl2_hi)
