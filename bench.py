@@ -20,6 +20,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -418,8 +419,8 @@ def main():
     torch.cuda.synchronize()
     builds0 = sum(r["list_builds"] for r in ctx.run(0))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk_dir = tempfile.mkdtemp(prefix="rbsog_clocks_")
+    clk_path = os.path.join(clk_dir, f"clocks_rank{rank}.csv")
     proc, fh = clock_sampler(clk_path) if rank == 0 else (None, None)
     time.sleep(0.3)
     if world > 1:

@@ -325,12 +325,75 @@ def rbsog_structure_factor_workspace(n_atoms, nD):
     return lib().rbsog_structure_factor_workspace(n_atoms, nD)
 
 
+def _check_tensor(name, t, dtype, numel_min=None, numel_eq=None):
+    """Refuse a device buffer the kernels would read or write out of bounds
+    (or misread): not a torch tensor, wrong dtype, not contiguous, a wrong
+    number of elements.  The device is checked apart (_check_devices), after
+    every buffer has passed these checks."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if numel_eq is not None and t.numel() != numel_eq:
+        raise ValueError(f"{name}: expected {numel_eq} elements, got {t.numel()}")
+    if numel_min is not None and t.numel() < numel_min:
+        raise ValueError(f"{name}: needs at least {numel_min} elements, got {t.numel()}")
+
+
+def _check_devices(**tensors):
+    """Every buffer must be CUDA device memory, all on one device."""
+    for name, t in tensors.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name}: must be a CUDA tensor (device memory), got device {t.device}")
+    devs = {t.device for t in tensors.values()}
+    if len(devs) != 1:
+        raise ValueError(f"{', '.join(tensors)} must be on one device, got {sorted(str(d) for d in devs)}")
+
+
+def _check_sf_args(r, q, box, m, rho, precision):
+    """Arguments of the stateless structure factor: r float64 (n, 3), q
+    float64 (n,), m int32 (nD, 3), rho float64 (>= 2 nD), box three positive
+    finite edges, precision RBSOG_FP64 or RBSOG_FP32.  Returns (n, nD); the
+    caller checks the devices."""
+    import torch
+    if precision not in (RBSOG_FP64, RBSOG_FP32):
+        raise ValueError(f"precision: expected RBSOG_FP64 or RBSOG_FP32, got {precision!r}")
+    b = np.asarray(box, dtype=np.float64).reshape(-1)
+    if b.size != 3 or not np.all(np.isfinite(b)) or not np.all(b > 0):
+        raise ValueError(f"box: expected three positive finite edge lengths, got {box!r}")
+    if not isinstance(q, torch.Tensor) or q.numel() < 1:
+        raise ValueError("q: expected a non-empty torch tensor of charges")
+    n = int(q.numel())
+    if not isinstance(m, torch.Tensor) or m.numel() < 3 or m.numel() % 3:
+        raise ValueError("m: expected a torch tensor of shape (nD, 3), nD >= 1")
+    nD = int(m.numel()) // 3
+    _check_tensor("r", r, torch.float64, numel_eq=3 * n)
+    _check_tensor("q", q, torch.float64, numel_eq=n)
+    _check_tensor("m", m, torch.int32, numel_eq=3 * nD)
+    _check_tensor("rho", rho, torch.float64, numel_min=2 * nD)
+    return n, nD
+
+
 def rbsog_structure_factor(r, q, box, m, rho, work, precision=RBSOG_FP32, stream=None):
-    """r, q, m, rho, work: torch CUDA tensors (device buffers)."""
+    """r (n, 3) float64, q (n,) float64, m (nD, 3) int32, rho (2 nD,) float64
+    and work (>= rbsog_structure_factor_workspace(n, nD) bytes, any dtype):
+    contiguous torch CUDA tensors of one device.  Bad arguments raise
+    ValueError before the library is called."""
+    import torch
+    n, nD = _check_sf_args(r, q, box, m, rho, precision)
+    if not isinstance(work, torch.Tensor) or not work.is_contiguous():
+        raise ValueError("work: expected a contiguous torch tensor")
+    need = rbsog_structure_factor_workspace(n, nD)
+    if work.numel() * work.element_size() < need:
+        raise ValueError(f"work: needs {need} bytes, got {work.numel() * work.element_size()}")
+    _check_devices(r=r, q=q, m=m, rho=rho, work=work)
     b = (C.c_double * 3)(*[float(x) for x in box])
     st = C.c_void_p(stream) if stream else None
-    status = lib().rbsog_structure_factor(C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()), int(q.numel()),
-                                          b, C.c_void_p(m.data_ptr()), int(m.shape[0]),
+    status = lib().rbsog_structure_factor(C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()), n,
+                                          b, C.c_void_p(m.data_ptr()), nD,
                                           C.c_void_p(rho.data_ptr()), C.c_void_p(work.data_ptr()),
                                           precision, st)
     if status != RBSOG_OK:
@@ -355,11 +418,14 @@ def rbsog_trace_pair_times(ctx, max_steps):
 def rbsog_structure_factor_noalloc(r, q, box, m, rho, precision=RBSOG_FP32, stream=None):
     """As rbsog_structure_factor, with the library's fixed scratch instead of a
     caller workspace (no device allocation; calls on one device must not
-    overlap in time)."""
+    overlap in time).  Bad arguments raise ValueError before the library is
+    called."""
+    n, nD = _check_sf_args(r, q, box, m, rho, precision)
+    _check_devices(r=r, q=q, m=m, rho=rho)
     b = (C.c_double * 3)(*[float(x) for x in box])
     st = C.c_void_p(stream) if stream else None
     status = lib().rbsog_structure_factor_noalloc(C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()),
-                                                  int(q.numel()), b, C.c_void_p(m.data_ptr()), int(m.shape[0]),
+                                                  n, b, C.c_void_p(m.data_ptr()), nD,
                                                   C.c_void_p(rho.data_ptr()), precision, st)
     if status != RBSOG_OK:
         raise RbsogError(status, lib().rbsog_last_error(None).decode())

@@ -3,7 +3,8 @@ identical seeded inputs and identical Philox counters.
 
 Bars (from the contract of this build):
 * cell membership and sampled mode indices: bit-exact;
-* FP64 build: forces, virial/pressure and energies within 1e-10 relative;
+* FP64 build: forces, virial/pressure (and each of its parts) and energies
+  within 1e-12 relative;
 * FP32 build (FP32 math, FP64 accumulation): forces within 1e-5 relative RMS,
   pressure tensor (Frobenius) and energies within 1e-6 relative;
 * batched path: each system bit-identical alone and in a mix.
@@ -32,6 +33,10 @@ def _oracle_params(p, sysid=0):
     # the binding keys system k with rng_id = k unless the system sets one
     return O.Params(rc=p.rc, b=p.b, sigma=p.sigma, omega=p.omega, ke=p.ke, M=p.M, ME=p.M_energy,
                     P=p.P, kind=p.sampler, seed=int(p.seed), sysid=sysid)
+
+
+# FP64 build bar (forces, pressure tensor and its parts, energies), relative
+TOL64 = 1e-12
 
 
 def _rel(a, b):
@@ -95,14 +100,16 @@ def _compare_eval(s, prec, step=5, **kw):
 def test_eval_fp64_matches_oracle(name, sub):
     s = SYSTEMS[name]()
     F, r, ref = _compare_eval(s, R.RBSOG_FP64, cell_sub=sub)
-    assert _rel(F, ref["F"]) < 1e-10
-    assert _rel(r["virial"], ref["W"]) < 1e-10
-    assert _rel(r["virial_coul_short"], ref["W_parts"][0]) < 1e-10
-    assert _rel(r["virial_long_r"], ref["W_parts"][1]) < 1e-10
-    assert _rel(r["virial_long_nr"], ref["W_parts"][2]) < 1e-10
+    assert _rel(F, ref["F"]) < TOL64
+    assert _rel(r["virial"], ref["W"]) < TOL64
+    assert _rel(r["virial_coul_short"], ref["W_parts"][0]) < TOL64
+    assert _rel(r["virial_long_r"], ref["W_parts"][1]) < TOL64
+    assert _rel(r["virial_long_nr"], ref["W_parts"][2]) < TOL64
+    assert _rel(r["virial_lj"], ref["W_parts"][3]) < TOL64
+    assert _rel(r["virial_bonded"], ref["W_parts"][4]) < TOL64 or np.abs(ref["W_parts"][4]).max() == 0
     for k in ("coul_short", "coul_long", "coul_self", "lj", "bond", "angle"):
-        assert abs(r[k] - ref[k]) <= 1e-10 * max(abs(ref[k]), 1.0), k
-    assert abs(r["coul"] - ref["coul"]) <= 1e-10 * abs(ref["coul"])
+        assert abs(r[k] - ref[k]) <= TOL64 * max(abs(ref[k]), 1.0), k
+    assert abs(r["coul"] - ref["coul"]) <= TOL64 * abs(ref["coul"])
     assert r["n_distinct_modes"] == int(ref["n_distinct"])
 
 
@@ -200,7 +207,7 @@ def test_eval_large_molecules_match_oracle(prec):
     # terms run one warp per molecule, its per-atom sums in shared memory
     s = W.ionic_liquid(n_pairs=100, seed=5)
     F, r, ref = _compare_eval(s, prec)
-    tol_f, tol_w = (1e-10, 1e-10) if prec == R.RBSOG_FP64 else (1e-5, 1e-6)
+    tol_f, tol_w = (TOL64, TOL64) if prec == R.RBSOG_FP64 else (1e-5, 1e-6)
     assert _rel(F, ref["F"]) < tol_f
     assert _rel(r["virial"], ref["W"]) < tol_w
     assert abs(r["bond"] - ref["bond"]) <= tol_w * max(abs(ref["bond"]), 1.0)
@@ -219,32 +226,60 @@ def test_eval_fp32_full_water_box():
     assert abs(res[0]["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
 
 
-def test_npt_fp64_trajectory_matches_oracle():
-    s = W.electrolyte(n_ions=300, L=30.0, seed=9)
+def _npt_fp64_vs_oracle(s, coupling, nsteps=5):
+    # FP64 NPT steps through the C ABI against the oracle's integrator from
+    # the same start, with the box masses the library sets for the coupling
     rng = np.random.default_rng(0)
     s.vel = rng.normal(size=s.pos.shape) * np.sqrt(O.KB * 300.0 * O.FTM2V / s.mass[:, None])
-    ctx, p = _ctx([s], R.RBSOG_FP64, P=50, dt=1.0)
+    ctx, p = _ctx([s], R.RBSOG_FP64, P=50, dt=1.0, coupling=coupling)
     op = _oracle_params(p)
     # oracle state after the priming evaluation at counter 0
     out0 = O.force_eval(s, op, 0)
     st = dict(r=s.pos.copy(), p=s.vel * s.mass[:, None], L=s.box.copy(), ph=np.zeros(3),
               F=out0["F"], W=out0["W"].reshape(-1).copy())
-    # box mass as the library sets it (isotropic group)
+    # box mass per group: M_g = n_g^2 V ftm2v / (kappa L_g^2 omega^2)
     kap = p.compressibility * O.NKTV2P
     om = 2 * np.pi / p.tau_box
-    Mb = 9.0 * np.prod(s.box) * O.FTM2V / (kap * s.box[0] ** 2 * om ** 2)
+    V = np.prod(s.box)
+    if coupling == R.RBSOG_COUPLE_ISO:
+        Mbox = (9.0 * V * O.FTM2V / (kap * s.box[0] ** 2 * om ** 2), 0.0, 0.0)
+    else:
+        Mbox = (4.0 * V * O.FTM2V / (kap * s.box[0] ** 2 * om ** 2),
+                1.0 * V * O.FTM2V / (kap * s.box[2] ** 2 * om ** 2), 0.0)
     ig = O.Integ(dt=p.dt, T=p.T, Pext_atm=p.P_ext, gamma=p.gamma, gamma_box=p.gamma_box,
-                 coupling=0, Mbox=(Mb, 0.0, 0.0))
-    res = ctx.run(5)
-    O.npt_run(s, op, ig, st, 0, 5)
+                 coupling=coupling, Mbox=Mbox)
+    res = ctx.run(nsteps)
+    O.npt_run(s, op, ig, st, 0, nsteps)
     r_gpu = ctx.positions()
     v_gpu = ctx.velocities()
-    assert np.allclose(res[0]["box"], st["L"], rtol=1e-11, atol=0)
+    ctx.close()
+    return res[0], r_gpu, v_gpu * s.mass[:, None], st
+
+
+def test_npt_fp64_trajectory_matches_oracle():
+    s = W.electrolyte(n_ions=300, L=30.0, seed=9)
+    res, r_gpu, p_gpu, st = _npt_fp64_vs_oracle(s, R.RBSOG_COUPLE_ISO)
+    assert np.allclose(res["box"], st["L"], rtol=1e-13, atol=0)
     d = r_gpu - st["r"]
     d -= st["L"] * np.rint(d / st["L"])
-    assert np.abs(d).max() < 1e-8
-    assert _rel(v_gpu * s.mass[:, None], st["p"]) < 1e-8
-    ctx.close()
+    assert np.abs(d).max() < 1e-10
+    assert _rel(p_gpu, st["p"]) < 1e-10
+
+
+def test_npt_fp64_semi_isotropic_trajectory_matches_oracle():
+    # coupling 1: x = y share one box momentum, z its own (sec. 4.3, the
+    # membrane's setting); an anisotropic box so that the groups differ
+    s = W.random_charges(n=400, box=(31.0, 31.0, 37.0), seed=19, min_dist=2.2, lj=True)
+    res, r_gpu, p_gpu, st = _npt_fp64_vs_oracle(s, R.RBSOG_COUPLE_SEMI_ISO)
+    L = np.asarray(res["box"])
+    assert L[0] == L[1]
+    assert np.allclose(L, st["L"], rtol=1e-13, atol=0)
+    # the z edge moved differently from x and y
+    assert abs(L[2] / L[0] - 37.0 / 31.0) > 1e-9
+    d = r_gpu - st["r"]
+    d -= st["L"] * np.rint(d / st["L"])
+    assert np.abs(d).max() < 1e-10
+    assert _rel(p_gpu, st["p"]) < 1e-10
 
 
 def test_batched_alone_equals_mixed():
@@ -285,7 +320,7 @@ def test_structure_factor_stateless():
     r = torch.tensor(s.pos, device=dev)
     q = torch.tensor(s.q, device=dev)
     mt = torch.tensor(m, device=dev)
-    for prec, tol in ((R.RBSOG_FP64, 1e-11), (R.RBSOG_FP32, 2e-6)):
+    for prec, tol in ((R.RBSOG_FP64, TOL64), (R.RBSOG_FP32, 2e-6)):
         rho = torch.zeros(2 * len(m), dtype=torch.float64, device=dev)
         nb = R.rbsog_structure_factor_workspace(s.n, len(m))
         work = torch.zeros(nb, dtype=torch.uint8, device=dev)
@@ -331,7 +366,7 @@ def test_run_is_deterministic():
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("prec,tol", [(R.RBSOG_FP64, 1e-10), (R.RBSOG_FP32, 2e-6)])
+@pytest.mark.parametrize("prec,tol", [(R.RBSOG_FP64, TOL64), (R.RBSOG_FP32, 2e-6)])
 @pytest.mark.parametrize("name", ["electrolyte", "ragged"])
 def test_shared_proposal_estimator_matches_oracle(name, prec, tol):
     # sec. 3.2: the radial samples of one evaluation reweighted for P^F,nr
