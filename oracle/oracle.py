@@ -46,7 +46,7 @@ class _Params(C.Structure):
     _fields_ = [("rc", C.c_double), ("b", C.c_double), ("sigma", C.c_double),
                 ("omega", C.c_double), ("ke", C.c_double), ("M", C.c_int),
                 ("ME", C.c_int), ("P", C.c_int), ("kind", C.c_int),
-                ("seed", C.c_uint64), ("sysid", C.c_uint64)]
+                ("seed", C.c_uint64), ("sysid", C.c_uint64), ("short_cells", C.c_int)]
 
 
 class _System(C.Structure):
@@ -77,6 +77,10 @@ def _declare(L):
     L.orc_cell_bin.argtypes = [C.c_int, _D, _D, C.c_double, C.c_int, _I, _I]
     L.orc_short_range.argtypes = [C.c_int, _D, _D, _I, _I, _D, C.c_double, C.c_int, _D, _D,
                                   C.c_int, _D, _D, C.c_int, _D, _D, C.c_double, _D, _D, _D, _D]
+    L.orc_short_range_cells.argtypes = L.orc_short_range.argtypes
+    L.orc_short_range_cells.restype = C.c_int
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_set_threads.restype = None
     L.orc_kspace_all.argtypes = [C.c_int, _D, _D, _D, C.c_int, _D, _D, C.c_int, _D, _D, _I,
                                  C.c_double, _D, _D, _D, _D]
     L.orc_pf_realspace.argtypes = [C.c_int, _D, _D, _D, C.c_double, C.c_double, _I, C.c_double, _D]
@@ -142,6 +146,7 @@ class Params:
                            # 2: exact i.i.d. radial draws + recalibration chain
     seed: int = 1
     sysid: int = 0
+    short_cells: int = 0   # 1: short range over cell lists (bit-identical; for the timed baseline)
 
     @classmethod
     def row2(cls, rc=10.0, **kw):
@@ -149,7 +154,7 @@ class Params:
 
     def c(self):
         return _Params(self.rc, self.b, self.sigma, self.omega, self.ke, self.M, self.ME,
-                       self.P, self.kind, self.seed, self.sysid)
+                       self.P, self.kind, self.seed, self.sysid, self.short_cells)
 
 
 def sog_terms(b, sigma, omega, M):
@@ -208,6 +213,29 @@ def short_range(sys, params: Params, h=None, pos=None):
                           sys.ntypes, _pd(_d(sys.lj_eps)), _pd(_d(sys.lj_sig)), params.ke,
                           _pd(F), _pd(en), _pd(Wc), _pd(Wl))
     return F, en[0], en[1], Wc.reshape(3, 3), Wl.reshape(3, 3)
+
+
+def short_range_cells(sys, params: Params, h=None, pos=None):
+    """As short_range, over cell lists (bit-identical; None if the box holds
+    fewer than 3 cells of r_c per axis or h is not diagonal)."""
+    pos = _d(sys.pos if pos is None else pos)
+    h = _d(box_matrix(sys.box) if h is None else h)
+    MM = max(params.M, params.ME)
+    w, s, wt, st = sog_terms(params.b, params.sigma, params.omega, MM)
+    F = np.zeros((sys.n, 3))
+    en, Wc, Wl = np.zeros(2), np.zeros(9), np.zeros(9)
+    rc = lib().orc_short_range_cells(sys.n, _pd(pos), _pd(_d(sys.q)), _pi(_i(sys.type)), _pi(_i(sys.mol)),
+                                     _pd(h), params.rc, params.M, _pd(wt), _pd(st), params.ME, _pd(w), _pd(s),
+                                     sys.ntypes, _pd(_d(sys.lj_eps)), _pd(_d(sys.lj_sig)), params.ke,
+                                     _pd(F), _pd(en), _pd(Wc), _pd(Wl))
+    if rc != 0:
+        return None
+    return F, en[0], en[1], Wc.reshape(3, 3), Wl.reshape(3, 3)
+
+
+def set_threads(n: int):
+    """OpenMP threads of the oracle's parallel sums (the timed baseline)."""
+    lib().orc_set_threads(int(n))
 
 
 def kspace_mmax(h, st0, eps=1e-17):

@@ -370,6 +370,146 @@ void orc_short_range(int N, const double *r, const double *q, const int *type,
     for (int a = 0; a < 9; ++a) { Wc[a] = wc[a]; Wl[a] = wl[a]; }
 }
 
+/* The same sums over cell lists (used by the timed CPU baseline only): for
+ * an orthorhombic h with at least 3 cells of >= r_c per axis, every pair
+ * within r_c lies in the 27 cells around i's cell.  The hits of atom i are
+ * gathered from those cells with the same minimum-image arithmetic as above,
+ * sorted by j, and then evaluated and added in ascending j exactly as the
+ * all-pairs loop adds them (same expressions, same order, same static split
+ * of i over the threads), so the results are bit for bit those of
+ * orc_short_range.  Returns -1 (nothing computed) when h is not diagonal or
+ * a box edge holds fewer than 3 cells. */
+typedef struct { int j; double d[3]; double r2; } orc_hit;
+
+static int cmp_hit(const void *a, const void *b)
+{
+    const int x = ((const orc_hit *)a)->j, y = ((const orc_hit *)b)->j;
+    return (x > y) - (x < y);
+}
+
+int orc_short_range_cells(int N, const double *r, const double *q, const int *type,
+                          const int *mol, const double *h, double rc,
+                          int M, const double *wt, const double *st,
+                          int ME, const double *w, const double *s,
+                          int ntypes, const double *lj_eps, const double *lj_sig,
+                          double ke, double *F, double *en, double *Wc, double *Wl)
+{
+    if (h[1] != 0 || h[2] != 0 || h[3] != 0 || h[5] != 0 || h[6] != 0 || h[7] != 0) return -1;
+    const double L[3] = {h[0], h[4], h[8]};
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)floor(L[a] / rc);
+        if (nc[a] < 3) return -1;
+    }
+    const int C = nc[0] * nc[1] * nc[2];
+    int *cell = (int *)malloc(sizeof(int) * (size_t)N);
+    int *start = (int *)calloc((size_t)C + 1, sizeof(int));
+    int *list = (int *)malloc(sizeof(int) * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            double u = r[3 * i + a] / L[a];
+            u = u - floor(u);
+            if (u >= 1.0) u = 0.0;
+            int k = (int)floor(u * nc[a]);
+            if (k > nc[a] - 1) k = nc[a] - 1;
+            if (k < 0) k = 0;
+            c[a] = k;
+        }
+        cell[i] = c[0] + nc[0] * (c[1] + nc[1] * c[2]);
+        ++start[cell[i] + 1];
+    }
+    for (int c = 0; c < C; ++c) start[c + 1] += start[c];
+    {
+        int *fill = (int *)malloc(sizeof(int) * (size_t)C);
+        memcpy(fill, start, sizeof(int) * (size_t)C);
+        for (int i = 0; i < N; ++i) list[fill[cell[i]]++] = i;   /* ascending index within a cell */
+        free(fill);
+    }
+    double hi[9];
+    inv3(h, hi);
+    const double rc2 = rc * rc;
+    double Uc = 0, Ul = 0, wc[9] = {0}, wl[9] = {0};
+#pragma omp parallel
+    {
+        double uc = 0, ul = 0, tc[9] = {0}, tl[9] = {0};
+        int cap = 1024;
+        orc_hit *hits = (orc_hit *)malloc(sizeof(orc_hit) * (size_t)cap);
+#pragma omp for schedule(static)
+        for (int i = 0; i < N; ++i) {
+            const int ci = cell[i];
+            const int cx = ci % nc[0], cy = (ci / nc[0]) % nc[1], cz = ci / (nc[0] * nc[1]);
+            int nh = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int g = (cx + dx + nc[0]) % nc[0] +
+                                      nc[0] * ((cy + dy + nc[1]) % nc[1] + nc[1] * ((cz + dz + nc[2]) % nc[2]));
+                        for (int k = start[g]; k < start[g + 1]; ++k) {
+                            const int j = list[k];
+                            if (j == i || mol[i] == mol[j]) continue;
+                            double d[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1],
+                                           r[3 * i + 2] - r[3 * j + 2]};
+                            min_image(h, hi, d);
+                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (r2 >= rc2) continue;
+                            if (nh == cap) {
+                                cap *= 2;
+                                hits = (orc_hit *)realloc(hits, sizeof(orc_hit) * (size_t)cap);
+                            }
+                            hits[nh].j = j;
+                            hits[nh].d[0] = d[0]; hits[nh].d[1] = d[1]; hits[nh].d[2] = d[2];
+                            hits[nh].r2 = r2;
+                            ++nh;
+                        }
+                    }
+            qsort(hits, (size_t)nh, sizeof(orc_hit), cmp_hit);
+            double fi[3] = {0, 0, 0};
+            for (int e = 0; e < nh; ++e) {
+                const int j = hits[e].j;
+                const double *d = hits[e].d;
+                const double r2 = hits[e].r2;
+                double rr = sqrt(r2);
+                double fs = 1.0 / (r2 * rr), es = 1.0 / rr;
+                for (int l = 0; l < M; ++l) fs -= wt[l] * exp(-r2 / (st[l] * st[l]));
+                for (int l = 0; l < ME; ++l) es -= w[l] * exp(-r2 / (s[l] * s[l]));
+                double qq = ke * q[i] * q[j];
+                double f = qq * fs;
+                uc += 0.5 * qq * es;
+                double eps = lj_eps[type[i] * ntypes + type[j]];
+                double fl = 0.0;
+                if (eps != 0.0) {
+                    double sg = lj_sig[type[i] * ntypes + type[j]];
+                    double sr2 = sg * sg / r2, sr6 = sr2 * sr2 * sr2;
+                    ul += 0.5 * 4.0 * eps * (sr6 * sr6 - sr6);
+                    fl = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
+                }
+                for (int a = 0; a < 3; ++a) {
+                    fi[a] += (f + fl) * d[a];
+                    for (int b = 0; b < 3; ++b) {
+                        tc[3 * a + b] += 0.5 * f * d[a] * d[b];
+                        tl[3 * a + b] += 0.5 * fl * d[a] * d[b];
+                    }
+                }
+            }
+            for (int a = 0; a < 3; ++a) F[3 * i + a] += fi[a];
+        }
+        free(hits);
+#pragma omp for ordered schedule(static, 1)
+        for (int t = 0; t < orc_team_size(); ++t) {
+#pragma omp ordered
+            {
+                Uc += uc; Ul += ul;
+                for (int a = 0; a < 9; ++a) { wc[a] += tc[a]; wl[a] += tl[a]; }
+            }
+        }
+    }
+    en[0] = Uc; en[1] = Ul;
+    for (int a = 0; a < 9; ++a) { Wc[a] = wc[a]; Wl[a] = wl[a]; }
+    free(cell); free(start); free(list);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* deterministic Fourier part over all modes                                */
 /* ------------------------------------------------------------------------ */
@@ -1077,6 +1217,7 @@ typedef struct {
     double rc, b, sigma, omega, ke;
     int M, ME, P, kind;
     uint64_t seed, sysid;
+    int short_cells;              /* 1: short range over cell lists (same results; timed baseline) */
 } orc_params;
 
 typedef struct {
@@ -1108,8 +1249,11 @@ void orc_force_eval(const orc_params *pp, const orc_system *sy, const double *r,
     diag_box(L, h);
     memset(F, 0, sizeof(double) * 3 * N);
     double esr[2], Wc[9], Wl[9];
-    orc_short_range(N, r, sy->q, sy->type, sy->mol, h, pp->rc, M, wt, st, ME, w, s,
-                    sy->ntypes, sy->lj_eps, sy->lj_sig, pp->ke, F, esr, Wc, Wl);
+    if (!pp->short_cells ||
+        orc_short_range_cells(N, r, sy->q, sy->type, sy->mol, h, pp->rc, M, wt, st, ME, w, s,
+                              sy->ntypes, sy->lj_eps, sy->lj_sig, pp->ke, F, esr, Wc, Wl) != 0)
+        orc_short_range(N, r, sy->q, sy->type, sy->mol, h, pp->rc, M, wt, st, ME, w, s,
+                        sy->ntypes, sy->lj_eps, sy->lj_sig, pp->ke, F, esr, Wc, Wl);
     int *mr = (int *)malloc(sizeof(int) * 6 * P);
     int *mnr = mr + 3 * P;
     double stats[2];
@@ -1261,6 +1405,15 @@ void orc_npt_run(const orc_params *pp, const orc_system *sy, const orc_integ *ig
             if (ig->Mbox[g] > 0.0) ph[g] += 0.5 * ig->dt * G[g] * ig->ftm2v;
     }
     for (int a = 0; a < 9; ++a) K_out[a] = K[a];
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 int orc_num_threads(void)

@@ -200,3 +200,33 @@ def test_cell_binning_geometry():
         lo = c / nc
         hi = (c + 1) / nc
         assert np.all(frac >= lo - 1e-12) and np.all(frac < hi + 1e-12)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.water(n_mol=700, L=31.0, lattice=9, seed=3),
+    lambda: W.electrolyte(n_ions=500, L=33.0, seed=2),
+    lambda: W.random_charges(n=300, box=(30.5, 36.0, 41.0), seed=8, min_dist=2.0, lj=True),
+])
+def test_cell_list_short_range_is_bit_identical(make):
+    # the timed CPU baseline's short range over cell lists: the same hits,
+    # evaluated and added in the same order as the all-pairs definition
+    s = make()
+    p = O.Params.row2()
+    a = O.short_range(s, p)
+    b = O.short_range_cells(s, p)
+    assert b is not None
+    assert np.array_equal(a[0], b[0])
+    for k in (1, 2):
+        assert a[k] == b[k]
+    for k in (3, 4):
+        assert np.array_equal(a[k], b[k])
+    # a full evaluation with it is bit-identical too
+    pc = O.Params.row2(P=20, short_cells=1)
+    e1 = O.force_eval(s, O.Params.row2(P=20), 3)
+    e2 = O.force_eval(s, pc, 3)
+    assert np.array_equal(e1["F"], e2["F"]) and np.array_equal(e1["W"], e2["W"])
+
+
+def test_cell_list_short_range_needs_three_cells():
+    s = W.random_charges(n=50, box=(25.0, 40.0, 40.0), seed=1, min_dist=2.0)
+    assert O.short_range_cells(s, O.Params.row2()) is None
