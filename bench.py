@@ -529,7 +529,7 @@ def main():
         per = PAIR_FP32_PER_UNIT if fp32_bound else PAIR_MUFU_PER_UNIT
         peak = fp32_peak if fp32_bound else mufu_peak
         achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_pair_build + k_pair_eval",
+        roof = {"bound": "alu", "kernel": "k_pair_cluster",
                 "achieved": achieved, "peak": peak,
                 "unit": "Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)",
                 "frac": achieved / peak, "traffic": pair_traffic(args.workload, prec),

@@ -24,6 +24,8 @@ constexpr int kMolChunk = 32;      // molecules per block of the molecule kernel
 constexpr int kMolChunkLarge = 16; // ... for systems of large molecules (a warp each)
 constexpr int kSmallTerms = 24;    // terms of a molecule that one thread takes
 constexpr int kMaxTypes = 16;
+constexpr int kClus = 4;          // atoms per cluster of the FP32 pair kernel
+constexpr double kFixScale = 4294967296.0;   // FP32 pair forces: 64-bit fixed point, units of 2^-32
 
 // status flags written by kernels (bit mask in DevSys::flags)
 enum : int {
@@ -59,6 +61,7 @@ struct DevSys {
     int ntypes, lj0;      // LJ types of the system and its first entry in the context's LJ table
     int nmol, mol0;       // molecules of the system and its first global molecule index
     int act;              // 1: the slot holds a system that steps; 0: empty or finished
+    int kc;               // FP32 build: sub-columns per cell axis of the in-cell atom order
     int steps_left;       // NPT steps before the system stops (-1: no limit)
     int rebuild;          // 1: this evaluation bins the atoms and rebuilds the pair lists
     int list_valid;       // 0: positions or box were set from the host since the last build

@@ -66,21 +66,19 @@ struct Batch {
     const int *item_sys;        // [item_cap] system of each work item index
 };
 
-// FP32 pair lists: for dz plane p of the stencil and cell-sorted atom i,
-// entries ent[(p * maxent + k) * ncap + i], k < nent[p * ncap + i], holding
-// nhit[p * ncap + i] hits; an entry is (index of the first of 32 candidates |
-// neighbour-cell code << 25, hit mask).
-constexpr int kEvalSplit = 3;   // FP32 evaluation warps (hit segments) per 32-atom group
-constexpr int kEvalGroups = 2;   // evaluation groups of 32 atoms per block (item_cap per system: a multiple)
+// FP32 pair kernel: work items are clusters of kClus consecutive cell-sorted
+// atoms of one cell; one warp per (cluster, dz plane of the half stencil),
+// kCpWarps warps per block, one pair record per block.
+constexpr int kCpWarps = 4;
 constexpr int kF64Split = 4;    // FP64 pair kernel: warps per (work item, dz plane), each over every 4th cell
-// force partials per atom (and pair records per work item) of the pair kernels
-inline int pair_parts(int precision, int sub) { return precision == 1 ? kEvalSplit : (2 * sub + 1) * kF64Split; }
-struct PairList {
-    uint2 *ent;                 // [span * maxent * ncap]
-    int *nent, *nhit;           // [span * ncap]
-    int maxent;                 // entries per (plane, atom)
-    int ncap;                   // atoms of the context
-};
+// warps per work item of the pair kernels: FP32, the dz planes 0..sub of the
+// half stencil; FP64, the 2 sub + 1 dz planes x kF64Split cell quarters (each
+// writes a force partial per atom of its item)
+inline int pair_parts(int precision, int sub) { return precision == 1 ? sub + 1 : (2 * sub + 1) * kF64Split; }
+// pair records per work item, as a fraction num / den (FP32: one record per
+// block of kCpWarps warps; FP64: one per warp)
+inline int pair_rec_num(int precision, int sub) { return pair_parts(precision, sub); }
+inline int pair_rec_den(int precision) { return precision == 1 ? kCpWarps : 1; }
 
 struct AtomArrays {
     double *r, *p, *F;          // [3N]
@@ -98,14 +96,15 @@ struct AtomArrays {
     float2 *qt;                 // [N] sorted (q, type bits)
     double4 *posd;              // [N] sorted, FP64
     int2 *aux;                  // [N] sorted (mol, type)
-    int2 *items;                // [item_cap] (cell, group) pair work items
-    float4 *fpart4;             // [(2 sub + 1) N] pair forces per dz plane, cell-sorted (FP32 build)
-    double4 *fpartd;            // same storage, FP64 build
+    int2 *items;                // [item_cap] (cell, group) pair work items; FP32: (cell, k) = cluster k of the cell
+    int2 *ccl;                  // [C] FP32: (item of the first cluster, clusters) of each cell
+    float4 *cbox;               // [2 item_cap] FP32: cluster bounding box (centre | first atom, half extent | atoms)
+    unsigned long long *ffix;   // [3 N] FP32: pair forces, x | y | z blocks, cell-sorted, fixed point (kFixScale)
+    double4 *fpartd;            // [(2 sub + 1) kF64Split N] FP64 build: pair forces per (dz plane, quarter)
     // LJ table: system s owns entries [lj0, lj0 + ntypes^2) (DevSys), entry
     // ti * ntypes + tj = (4 eps sig^12, 4 eps sig^6); ljf_lo: FP32 remainders
     const float2 *ljf, *ljf_lo;
     const double2 *ljd;
-    PairList plist;             // FP32 build only
 };
 
 // ---- k_bin.cu
@@ -120,21 +119,28 @@ void launch_refresh(const Batch &b, const AtomArrays &a, cudaStream_t st);
 // marks every system's lists stale (positions or box set from the host)
 void launch_invalidate_lists(const Batch &b, cudaStream_t st);
 void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
+// scatter + per-cell sort (FP32: along the snake path of sub-columns, and
+// the cluster bounding boxes of the rebuilt systems)
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st);
+// FP32, lists with a skin: cluster bounding boxes of the systems that keep
+// their lists (after launch_refresh)
+void launch_cluster_box(const Batch &b, const AtomArrays &a, cudaStream_t st);
 
-// ---- k_pair.cu: partial = per record (FP32: one per item; FP64: one per
-// block of kPairWarps work units = item x dz plane):
+// ---- k_pair.cu: partial = per record (FP32: one per block of kCpWarps
+// warps; FP64: one per block of kPairWarps work units = item x dz plane):
 // (Ucoul, Ulj, Wc[6], Wl[6], W[6]) as kPairRec doubles; energies and the
 // Coulomb/LJ split only when `energy` is set (W, the total, always).  Each
 // system's item range is a multiple of kItemAlign items, so a block never
 // mixes systems.  launch_reduce_pair (k_integrate.cu) sums each system's
 // records into kPairRedBlocks records in a fixed order.
-constexpr int kPairWarps = 1;       // one warp per block: no block-level wait on a slower warp
-constexpr int kItemAlign = kEvalGroups > kPairWarps ? kEvalGroups : kPairWarps;
-static_assert(kItemAlign % kPairWarps == 0 && kItemAlign % kEvalGroups == 0, "item alignment");
+constexpr int kPairWarps = 1;       // FP64: one warp per block, no block-level wait on a slower warp
+constexpr int kItemAlign = kCpWarps;
+static_assert(kItemAlign % kPairWarps == 0, "item alignment");
 constexpr int kPairRec = 20;
 constexpr int kPairRedBlocks = 8;   // second-stage reduction of the unit records, per system
-void launch_reduce_pair(const Batch &b, int rec_per_item, const double *pair_part, double *pair_red, cudaStream_t st);
+// records of system s: [item0 * num / den, ceil((item0 + nitems) * num / den))
+void launch_reduce_pair(const Batch &b, int rec_num, int rec_den, const double *pair_part, double *pair_red,
+                        cudaStream_t st);
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st);
 

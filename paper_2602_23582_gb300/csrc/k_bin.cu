@@ -6,8 +6,12 @@
 // x fastest.  A warp-aggregated counting sort (match_any + one atomicAdd per
 // distinct cell in the warp) gives every atom a rank in its cell; an
 // exclusive scan gives the cell starts; atoms are scattered to their cell and
-// each cell's list is then sorted by original index, so the cell-sorted order
-// (and every sum over it) is deterministic.
+// each cell's list is then sorted, so the cell-sorted order (and every sum
+// over it) is deterministic.  FP64 build: by original index.  FP32 build:
+// along a snake path through the cell -- kc x kc sub-columns in boustrophedon
+// order, z up and down in alternate columns, ties by original index -- so
+// that every kClus consecutive atoms (a cluster of the pair kernel) lie close
+// together; the same pass writes each cluster's bounding box.
 //
 // Lists with a skin (FP32 build, NPT steps): cells are r_list / sub wide,
 // r_list = r_c + skin, and the binning, scan, scatter, cell sort and list
@@ -145,56 +149,34 @@ void launch_refresh(const Batch &b, const AtomArrays &a, cudaStream_t st)
 // atoms of system s occupy [atom0, atom0 + n) of the sorted arrays.  The same
 // pass lists the pair kernel's work items of the system in [item0, item0 +
 // nitems) and marks the rest of its item range unused.  An item is (cell g,
-// k >= 0): the k-th group of 32 atoms of cell g, or (cell g, -m): the m >= 2
-// consecutive cells g .. g + m - 1 of one x-row, holding 32 atoms or fewer
-// together (maxrun > 1 allows such runs; the FP32 list build takes them).
-// Each thread groups the cells of its own range, in order.
-__device__ __forceinline__ int scan_items(const int *__restrict__ count, int C0, int c0, int c1, int n0,
-                                          int maxrun, int2 *__restrict__ items, int rg, bool write)
+// k): the k-th group of gsize atoms of cell g (FP64: 32-atom groups; FP32:
+// clusters of kClus atoms, and ccl[g] = (first item of cell g, its items)).
+// Each thread lists the cells of its own range, in order.
+__device__ __forceinline__ int scan_items(const int *__restrict__ count, int C0, int c0, int c1, int gsize,
+                                          int2 *__restrict__ items, int2 *__restrict__ ccl, int rg, bool write)
 {
-    int ni = 0, run0 = -1, runn = 0, runa = 0;
-    auto flush = [&]() {
-        if (runn > 0) {
-            if (write) items[rg + ni] = make_int2(C0 + run0, runn > 1 ? -runn : 0);
-            ++ni;
-        }
-        runn = 0;
-        runa = 0;
-    };
+    int ni = 0;
     for (int c = c0; c < c1; ++c) {
-        const int v = count[C0 + c];
-        if (v == 0 || v > 32 || maxrun < 2) {
-            flush();
-            const int ng = (v + 31) >> 5;
-            for (int g = 0; g < ng; ++g) {
-                if (write) items[rg + ni] = make_int2(C0 + c, g);
-                ++ni;
-            }
-            continue;
+        const int v = min(count[C0 + c], kCellCap);
+        const int ng = (v + gsize - 1) / gsize;
+        if (write) {
+            if (ccl) ccl[C0 + c] = make_int2(rg + ni, ng);
+            for (int g = 0; g < ng; ++g) items[rg + ni + g] = make_int2(C0 + c, g);
         }
-        // a run continues with the next cell of the same x-row while it fits
-        if (runn > 0 && (c % n0) != 0 && runn < maxrun && runa + v <= 32) {
-            ++runn;
-            runa += v;
-        } else {
-            flush();
-            run0 = c;
-            runn = 1;
-            runa = v;
-        }
+        ni += ng;
     }
-    flush();
     return ni;
 }
 
 __global__ void __launch_bounds__(1024)
-k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, DevSys *sys, int maxrun)
+k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, int2 *__restrict__ ccl,
+       DevSys *sys, int gsize)
 {
     __shared__ int ta[1024], tg[1024];
     DevSys &d = sys[blockIdx.x];
     if (!d.rebuild) return;                  // block-uniform: the system keeps its lists
     const int t = threadIdx.x, T = blockDim.x;
-    const int C0 = d.cell0, nc = d.ncell_cap_total, n0 = d.ncell[0];
+    const int C0 = d.cell0, nc = d.ncell_cap_total;
     const int per = (nc + T - 1) / T;
     const int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
     int sa = 0;
@@ -203,7 +185,7 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
         if (v > kCellCap) atomicOr(&d.flags, (int)FLAG_OVERFLOW);
         sa += v;
     }
-    const int sg = scan_items(count, C0, c0, c1, n0, maxrun, items, 0, false);
+    const int sg = scan_items(count, C0, c0, c1, gsize, items, ccl, 0, false);
     ta[t] = sa;
     tg[t] = sg;
     __syncthreads();
@@ -220,7 +202,7 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
         start[C0 + c] = ra;
         ra += count[C0 + c];
     }
-    scan_items(count, C0, c0, c1, n0, maxrun, items, rg, true);
+    scan_items(count, C0, c0, c1, gsize, items, ccl, rg, true);
     const int total = tg[T - 1];
     if (t == T - 1) {
         d.nitems = total;
@@ -233,12 +215,8 @@ k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict_
 
 void launch_scan(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
 {
-    // runs of cells whose stencil rows fit one warp's cell table, (span + m - 1) span <= 32,
-    // for the FP32 list build with cells of r_c / 2 (the only size where cells of
-    // a few atoms are the rule)
-    const int span = 2 * b.sub + 1;
-    const int maxrun = precision == 1 && b.sub >= 2 ? 32 / span - span + 1 : 1;
-    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, b.sys, maxrun);
+    k_scan<<<b.S, 1024, 0, st>>>(a.count, a.start, a.items, precision == 1 ? a.ccl : nullptr, b.sys,
+                                 precision == 1 ? kClus : 32);
 }
 
 __global__ void k_scatter(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys,
@@ -250,27 +228,51 @@ __global__ void k_scatter(const DevSys *__restrict__ sys, const int *__restrict_
     sidx[start[cell[i]] + rank[i]] = i;
 }
 
-// One block per cell: bitonic sort of the cell's atom list by original index
+// One block per cell: bitonic sort of the cell's atom list by a 64-bit key
 // (kSortThreads threads, each stage one compare-exchange per thread for a
 // cell of up to 2 kSortThreads atoms), then gather the cell-sorted copies used
-// by the pair kernel.
+// by the pair kernel.  FP64: key = original index.  FP32: key = (sub-column
+// along the snake path) << 48 | (z position along the column's direction,
+// 16 bits) << 32 | original index; then the bounding box of each cluster of
+// kClus consecutive atoms (centre, half extent; cell-local coordinates).
 constexpr int kSortThreads = 128;
 
-__global__ void __launch_bounds__(kSortThreads)
-k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C, int *__restrict__ sidx,
-            int *__restrict__ rank, const float4 *__restrict__ locf, const double4 *__restrict__ locd,
-            const double *__restrict__ q, const int *__restrict__ type, const int *__restrict__ mol,
-            float4 *__restrict__ pos4, float2 *__restrict__ qt, double4 *__restrict__ posd,
-            int2 *__restrict__ aux, int precision)
+__device__ __forceinline__ unsigned long long snake_key(float4 l, const DevSys &d, int i)
 {
-    __shared__ int s[kCellCap];
+    const int kc = d.kc;
+    const float fx = l.x / (float)d.w[0], fy = l.y / (float)d.w[1], fz = l.z / (float)d.w[2];
+    const int sx = min(kc - 1, max(0, (int)(fx * (float)kc)));
+    const int sy = min(kc - 1, max(0, (int)(fy * (float)kc)));
+    const int col = sy * kc + ((sy & 1) ? kc - 1 - sx : sx);
+    unsigned zq = (unsigned)(fminf(fmaxf(fz, 0.f), 1.f) * 65535.f);
+    if (col & 1) zq = 65535u - zq;
+    return ((unsigned long long)col << 48) | ((unsigned long long)zq << 32) | (unsigned)i;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_cell_sort(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
+            const int *__restrict__ count, int C, int *__restrict__ sidx, int *__restrict__ rank,
+            const float4 *__restrict__ locf, const double4 *__restrict__ locd, const double *__restrict__ q,
+            const int *__restrict__ type, const int *__restrict__ mol, float4 *__restrict__ pos4,
+            float2 *__restrict__ qt, double4 *__restrict__ posd, int2 *__restrict__ aux,
+            const int2 *__restrict__ ccl, float4 *__restrict__ cbox, int precision)
+{
+    __shared__ unsigned long long s[kCellCap];
     const int c = blockIdx.x, t0 = threadIdx.x;
     const int base = start[c];
     const int n = min(count[c], kCellCap);
-    if (n == 0) return;                                // block-uniform
+    if (n == 0) return;                                // block-uniform (and systems that keep their lists)
+    const DevSys &d = sys[cell_sys[c]];
     int p2 = 1;
     while (p2 < n) p2 <<= 1;
-    for (int k = t0; k < p2; k += kSortThreads) s[k] = (k < n) ? sidx[base + k] : 0x7fffffff;
+    for (int k = t0; k < p2; k += kSortThreads) {
+        unsigned long long key = ~0ull;
+        if (k < n) {
+            const int i = sidx[base + k];
+            key = precision == 1 ? snake_key(locf[i], d, i) : (unsigned long long)(unsigned)i;
+        }
+        s[k] = key;
+    }
     __syncthreads();
     for (int k = 2; k <= p2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -278,14 +280,14 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
                 int lo = 2 * j * (t / j) + (t % j);
                 int hi = lo + j;
                 bool up = (lo & k) == 0;
-                int x = s[lo], y = s[hi];
+                const unsigned long long x = s[lo], y = s[hi];
                 if ((x > y) == up) { s[lo] = y; s[hi] = x; }
             }
             __syncthreads();
         }
     }
     for (int k = t0; k < n; k += kSortThreads) {
-        int i = s[k];
+        const int i = (int)(unsigned)(s[k] & 0xffffffffull);
         sidx[base + k] = i;
         rank[i] = base + k;          // from here on: cell-sorted position of atom i
         if (precision == 1) {
@@ -296,13 +298,57 @@ k_cell_sort(const int *__restrict__ start, const int *__restrict__ count, int C,
             aux[base + k] = make_int2(mol[i], type[i]);
         }
     }
+    if (precision != 1) return;
+    const int2 cc = ccl[c];
+    for (int k = t0; k < cc.y; k += kSortThreads) {
+        const int a0 = kClus * k, na = min(kClus, n - a0);
+        float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+        for (int j = 0; j < na; ++j) {
+            const float4 v = locf[(int)(unsigned)(s[a0 + j] & 0xffffffffull)];
+            lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
+            hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+        }
+        cbox[2 * (cc.x + k)] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]),
+                                           __int_as_float(base + a0));
+        cbox[2 * (cc.x + k) + 1] = make_float4(0.5f * (hi[0] - lo[0]), 0.5f * (hi[1] - lo[1]),
+                                               0.5f * (hi[2] - lo[2]), __int_as_float(na));
+    }
+}
+
+// Bounding boxes of the clusters of systems that keep their lists (their
+// atoms' coordinates were refreshed in the cells of the last build); one
+// thread per work item.
+__global__ void k_cluster_box(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, int item_cap,
+                              const int2 *__restrict__ items, const float4 *__restrict__ pos4,
+                              float4 *__restrict__ cbox)
+{
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= item_cap) return;
+    const DevSys &d = sys[item_sys[it]];
+    if (d.rebuild || live_n(d) == 0 || it - d.item0 >= d.nitems || items[it].x < 0) return;
+    const float4 b0 = cbox[2 * it], b1 = cbox[2 * it + 1];
+    const int a0 = __float_as_int(b0.w), na = __float_as_int(b1.w);
+    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+    for (int j = 0; j < na; ++j) {
+        const float4 v = pos4[a0 + j];
+        lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
+        hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+    }
+    cbox[2 * it] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]), b0.w);
+    cbox[2 * it + 1] = make_float4(0.5f * (hi[0] - lo[0]), 0.5f * (hi[1] - lo[1]), 0.5f * (hi[2] - lo[2]), b1.w);
+}
+
+void launch_cluster_box(const Batch &b, const AtomArrays &a, cudaStream_t st)
+{
+    k_cluster_box<<<(b.item_cap + 255) / 256, 256, 0, st>>>(b.sys, b.item_sys, b.item_cap, a.items, a.pos4, a.cbox);
 }
 
 void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cudaStream_t st)
 {
     k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.cell, a.rank, a.start, a.sidx, b.N);
-    k_cell_sort<<<b.C, kSortThreads, 0, st>>>(
-        a.start, a.count, b.C, a.sidx, a.rank, a.locf, a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, precision);
+    k_cell_sort<<<b.C, kSortThreads, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, b.C, a.sidx, a.rank, a.locf,
+                                              a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, a.ccl,
+                                              a.cbox, precision);
 }
 
 }  // namespace rbsog

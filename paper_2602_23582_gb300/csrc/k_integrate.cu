@@ -263,21 +263,22 @@ void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia
 //  [15..20] W short Coulomb, [21..26] W^F,r*, [27..32] W^F,nr*, [33..38] W LJ,
 //  [39..44] W bonded + exclusions, [45..50] K, [51] V, [52..54] L,
 //  [55] nD, [56] acc r, [57] acc nr, [58] flags, [59..61] box momenta.
-// Second stage of the pair records: system s's records (rec_per_item per
-// active item: 1 in the FP32 build, one per dz plane in the FP64 build) in
-// kPairRedBlocks contiguous ranges, each summed in a fixed order.
+// Second stage of the pair records: system s's records (rec_num / rec_den per
+// active item: FP32, one per block of kCpWarps (item, plane) warps; FP64, one
+// per (dz plane, cell quarter)) in kPairRedBlocks contiguous ranges, each
+// summed in a fixed order.
 // grid (S, kPairRedBlocks).
 constexpr int kRedThreads = 128;
 
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_pair(const DevSys *__restrict__ sys, int rec_per_item, const double *__restrict__ part,
+k_reduce_pair(const DevSys *__restrict__ sys, int rec_num, int rec_den, const double *__restrict__ part,
               double *__restrict__ red)
 {
     __shared__ double buf[kPairRec * (kRedThreads + 1) + 4 * kPairRec];
     const int s = blockIdx.x;
     const DevSys &d = sys[s];
-    const int u0 = d.item0 * rec_per_item;
-    const int nu = d.nitems * rec_per_item;
+    const long long u0 = (long long)d.item0 * rec_num / rec_den;   // item0 is a multiple of rec_den
+    const int nu = (int)(((long long)d.nitems * rec_num + rec_den - 1) / rec_den);
     const int per = (nu + kPairRedBlocks - 1) / kPairRedBlocks;
     const int a = min(nu, (int)blockIdx.y * per), e = min(nu, a + per);
     double v[kPairRec];
@@ -291,9 +292,10 @@ k_reduce_pair(const DevSys *__restrict__ sys, int rec_per_item, const double *__
     block_reduce_lanes<kPairRec, kRedThreads>(v, buf, red + ((size_t)s * kPairRedBlocks + blockIdx.y) * kPairRec);
 }
 
-void launch_reduce_pair(const Batch &b, int rec_per_item, const double *pair_part, double *pair_red, cudaStream_t st)
+void launch_reduce_pair(const Batch &b, int rec_num, int rec_den, const double *pair_part, double *pair_red,
+                        cudaStream_t st)
 {
-    k_reduce_pair<<<dim3(b.S, kPairRedBlocks), kRedThreads, 0, st>>>(b.sys, rec_per_item, pair_part, pair_red);
+    k_reduce_pair<<<dim3(b.S, kPairRedBlocks), kRedThreads, 0, st>>>(b.sys, rec_num, rec_den, pair_part, pair_red);
 }
 
 constexpr int kFinThreads = 128;

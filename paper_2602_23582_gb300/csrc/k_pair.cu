@@ -6,29 +6,17 @@
 //   f   = ke q_i q_j (1/r^3 - sum_{l<M} w~_l e^{-r^2/s~_l^2}) r_vec   (kernel N~)
 //   U  += ke q_i q_j (1/r   - sum_{l<ME} w_l e^{-r^2/s_l^2})          (kernel N)
 //   W  += f (x) r_vec  (eq. P_short: P^N = W / V)
-// Full pairs: each atom sums all its neighbours itself (no atomics, so results
-// do not depend on scheduling); energies and virials take half.
 //
-// Work unit = one warp = a group of up to 32 atoms of one cell (lane = atom,
-// in registers) and one dz plane of its neighbour cells (the (2 sub + 1)
-// planes of a group run as separate warps, which keeps enough warps in flight;
-// their partial forces are summed in a fixed order by the force assembly
-// kernel).  The warp walks the (2 sub + 1)^2 neighbour cells of its plane;
-// candidate neighbours are read with warp-broadcast loads (every lane the same
-// address, served by L1), 32 at a time, and each lane records its hits
-// (r^2 < r_c^2, different molecule) in a bit mask, then pushes them, with the
-// index of their neighbour cell, into its queue in shared memory.  The warp
-// evaluates the SOG kernel in rounds in which every lane with an atom has a
-// queued hit, so the expensive part runs with full lanes.  Each block writes
-// one record of energy and virial sums (its warps belong to one system).
+// FP32 build: one fused kernel over clusters of 4 atoms (k_pair_cluster),
+// every pair evaluated once (Newton's third law), forces accumulated in 64-bit
+// fixed point.  FP64 build: one warp per (32-atom group, dz plane, cell
+// quarter), full pairs (each atom sums all its neighbours itself), hits
+// queued per lane and evaluated with full lanes (k_pair_f64).
 //
 // Coordinates are cell-local.  A neighbour cell's periodic offset d_a w_a is
-// split into FP32 hi + lo parts: the cutoff test uses hi, the evaluation
-// subtracts both, so that the rounding of w_a does not shift every
-// cross-cell distance the same way (a systematic error that the r^-12 and
-// 1/r - F(r) terms would amplify).
-#include <cuda_fp16.h>
-
+// split into FP32 hi + lo parts: the evaluation subtracts both, so that the
+// rounding of w_a does not shift every cross-cell distance the same way (a
+// systematic error that the r^-12 and 1/r - F(r) terms would amplify).
 #include "internal.h"
 
 namespace rbsog {
@@ -65,13 +53,6 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     c = (t - s) - y;
     s = t;
 }
-
-struct AccF {
-    float fx, fy, fz;
-    float w[6];               // total virial (every step)
-    float uc, ul, uq, cuc, cul, cuq;   // energies and sum q_i q_j, with compensation terms
-    float wc[6], wl[6];       // Coulomb / LJ split of the virial (energy steps)
-};
 
 struct AccD {
     double fx, fy, fz;
@@ -116,66 +97,6 @@ __device__ __forceinline__ float exp2_poly(float x)
     return __int_as_float(__float_as_int(p) + ((int)n << 23));
 }
 
-// One pair from the i side.  NF: exponentials of the force kernel (0: pc.nff
-// at run time); EN: energies and the Coulomb/LJ virial split.  The force and
-// the total virial are computed the same way in both modes.
-template <int NF, bool EN>
-__device__ __forceinline__ void pair_eval(const PairConstsF &pc, float dx, float dy, float dz, float r2, float qi,
-                                          const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlo,
-                                          float2 qj, AccF &acc)
-{
-    float rinv = rsqrt_approx(r2);                       // r^2 of a pair is far above the subnormals
-    rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);   // one Newton step: the approximate
-    const float r2inv = rinv * rinv;                     // rsqrt error would bias r^-12 terms
-    // force kernel: F~(r) = tail polynomial in r^2 + narrow Gaussians
-    float st = pc.tt[kTail];
-#pragma unroll
-    for (int k = kTail - 1; k >= 0; --k) st = fmaf(st, r2, pc.tt[k]);
-    if (NF > 0) {
-#pragma unroll
-        for (int l = 0; l < NF; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
-    } else {
-        for (int l = 0; l < pc.nff; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
-    }
-    const float qq = pc.ke * qi * qj.x;
-    const float fc = qq * (r2inv * rinv - st);
-    const int tj = __float_as_int(qj.y);
-    const float2 lab = ljrow[tj];                        // shared memory
-    const float r6inv = r2inv * r2inv * r2inv;
-    const float fl = (12.f * lab.x * r6inv - 6.f * lab.y) * r6inv * r2inv;
-    const float f = fc + fl;
-    acc.fx = fmaf(f, dx, acc.fx);
-    acc.fy = fmaf(f, dy, acc.fy);
-    acc.fz = fmaf(f, dz, acc.fz);
-    const float gx = f * dx, gy = f * dy;
-    acc.w[0] = fmaf(gx, dx, acc.w[0]); acc.w[1] = fmaf(gy, dy, acc.w[1]);
-    acc.w[2] = fmaf(f * dz, dz, acc.w[2]); acc.w[3] = fmaf(gx, dy, acc.w[3]);
-    acc.w[4] = fmaf(gx, dz, acc.w[4]); acc.w[5] = fmaf(gy, dz, acc.w[5]);
-    if (EN) {
-        // energy kernel N(r) = 1/r - F(r); the constant of the tail is applied
-        // to sum q_i q_j in FP64 by the caller
-        float se = pc.te[kTail];
-#pragma unroll
-        for (int k = kTail - 1; k >= 1; --k) se = fmaf(se, r2, pc.te[k]);
-        se *= r2;
-        for (int l = 0; l < pc.nfe; ++l) {
-            const float e = exp2_poly(fmaf(-r2, pc.be_hi[l], -r2 * pc.be_lo[l]));
-            se = fmaf(pc.w_hi[l], e, fmaf(pc.w_lo[l], e, se));
-        }
-        kahan_add(acc.uc, acc.cuc, qq * (rinv - se));
-        kahan_add(acc.uq, acc.cuq, qq);
-        const float2 lo = ljlo[tj];
-        kahan_add(acc.ul, acc.cul, (fmaf(lab.x, r6inv, -lab.y) + fmaf(lo.x, r6inv, -lo.y)) * r6inv);
-        const float cx = fc * dx, cy = fc * dy, lx = fl * dx, ly = fl * dy;
-        acc.wc[0] = fmaf(cx, dx, acc.wc[0]); acc.wc[1] = fmaf(cy, dy, acc.wc[1]);
-        acc.wc[2] = fmaf(fc * dz, dz, acc.wc[2]); acc.wc[3] = fmaf(cx, dy, acc.wc[3]);
-        acc.wc[4] = fmaf(cx, dz, acc.wc[4]); acc.wc[5] = fmaf(cy, dz, acc.wc[5]);
-        acc.wl[0] = fmaf(lx, dx, acc.wl[0]); acc.wl[1] = fmaf(ly, dy, acc.wl[1]);
-        acc.wl[2] = fmaf(fl * dz, dz, acc.wl[2]); acc.wl[3] = fmaf(lx, dy, acc.wl[3]);
-        acc.wl[4] = fmaf(lx, dz, acc.wl[4]); acc.wl[5] = fmaf(ly, dz, acc.wl[5]);
-    }
-}
-
 __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, double dy, double dz, double qi,
                                           const double2 *__restrict__ ljrow, double qj, int tj, AccD &acc)
 {
@@ -209,246 +130,174 @@ __device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, doub
     acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
 }
 
-// Next (base, mask) entry of atom ks's hit stream: ep points at it, krem
-// entries of plane pl are left; moves to the next plane with entries when
-// this one is used up.  The caller asks only for entries that exist.
-__device__ __forceinline__ uint2 next_entry(const PairList &L, int ks, int &pl, const uint2 *&ep, int &krem)
-{
-    while (krem <= 0) {
-        ++pl;
-        ep = L.ent + (size_t)pl * L.maxent * L.ncap + ks;
-        krem = L.nent[pl * L.ncap + ks];
-    }
-    --krem;
-    const uint2 v = *ep;
-    ep += L.ncap;
-    return v;
-}
-
-
-// Two staged candidates of the list build: (-2 b_x, -2 b_y, -2 b_z, |b|^2) in
-// half precision, candidate 2p in the low halves and 2p + 1 in the high ones.
-struct __align__(16) HPair {
-    __half2 x, y, z, w;
-};
-
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP32 path in two kernels.
+// FP32 path: one fused kernel over clusters, each pair evaluated once.
 //
-// k_pair_build: work unit = 32-atom group x dz plane of its neighbour cells.
-// The warp walks the plane's cells in batches of 32 candidates; each lane
-// tests its atom against a batch and, when any hit, stores one list entry
-// (index of the first candidate | neighbour-cell code << 25, 32-bit hit
-// mask) at the next place of its (plane, atom) list.  The lists are laid out
-// entry-major over the cell-sorted atoms, ent[(plane * maxent + k) * N + atom],
-// so that the 32 lanes of an evaluation warp read entry k of 32 consecutive
-// atoms together.
+// Work unit = one warp = i-cluster I (kClus = 4 consecutive cell-sorted atoms
+// of one cell) x dz plane p = 0..sub of the half stencil: the neighbour cells
+// (dx, dy, p) with p > 0, or p = 0 and (dy > 0 or dy = 0 and dx > 0), and on
+// plane 0 the clusters J > I of I's own cell plus the pairs inside I.  Every
+// unordered pair of atoms within r_c is seen exactly once.
 //
-// k_pair_eval: one block per 32 consecutive cell-sorted atoms of one system
-// (whatever their cells, so the lanes are full); warp k takes segment k of
-// kEvalSplit of each atom's hits (all planes in order, split by hit count),
-// one hit per lane and round, so every lane carries about the same number of
-// pairs, and the block's warps share the same neighbour atoms in L1.
-// Segment k writes force partial k, summed in segment order by the force
-// assembly.
+// The warp tests the candidate clusters of its cells 32 at a time against I
+// by their bounding boxes (ballot; the passing ones are appended to a small
+// queue in shared memory) and evaluates them in rounds of 8 tiles: lane
+// (g, k) of the 8 four-lane groups holds atom k of I and, in step t = 0..3,
+// pairs it with atom (k + t) mod 4 of the group's cluster J, so each group
+// evaluates its 4 x 4 tile with full lanes.  The force on I accumulates in
+// registers over the whole unit; the force on J's atoms travels with them
+// (after each step the running sum moves one lane down, to the lane that meets
+// that atom next), so after the fourth step each lane holds one J atom's total
+// over the tile and adds it to the force buffer.  Forces are accumulated as
+// 64-bit fixed point (units of 2^-32 kcal/mol/A): integer additions are
+// exact and commute, so the sum does not depend on the order in which the
+// warps reach an atom, and results are deterministic.  Energies and the
+// virial are summed per lane in the warp's fixed pair order and reduced to
+// one record per block.
 // ---------------------------------------------------------------------------
-// Resident blocks per SM: 20 for one-cell items (80 registers, no spills;
-// 32 blocks measured slower), 32 for runs of small cells, whose short units
-// need more warps to hide their latency.
-template <bool RUNS>
-__global__ void __launch_bounds__(32, RUNS ? 32 : 20)
-k_pair_build(DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
-             const int *__restrict__ count, const int2 *__restrict__ items, const float4 *__restrict__ pos4, int sub,
-             PairList L, const float rl2_hi)
+namespace {
+
+constexpr int kQueue = 64;           // tile queue per warp (entries in flight <= 7 + 32)
+
+struct TileAcc {
+    float fx, fy, fz;                // force on this lane's i atom
+    float w[6];                      // total virial
+    float uc, ul, uq, cuc, cul, cuq; // energies, sum q_i q_j (EN), with compensation terms
+    float wc[6], wl[6];              // Coulomb / LJ split of the virial (EN)
+};
+
+__device__ __forceinline__ long long to_fix(float f)
 {
-    __shared__ float4 offp[kMaxPlane];                 // x, y offset; column; code of row
-    __shared__ HPair cand2[16];
-    const int lane = lane_id();
-    const int span = 2 * sub + 1;
-    const int unit = blockIdx.x;
-    const int2 item = items[unit / span];
-    if (item.x < 0) return;                            // whole block
-    const int part = unit % span;
-    const int gc = item.x;
-    const int s = cell_sys[gc];
-    const DevSys &d = sys[s];
-    if (!d.rebuild) return;                            // the system keeps its lists
-    // a cell beyond kCellCap atoms (flagged by the scan; e.g. non-finite
-    // coordinates all binned into one cell) would make this unit walk
-    // millions of candidates: the step is reported failed, skip its pairs
-    if (d.flags & FLAG_OVERFLOW) return;
-    const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
-    const int lc = gc - d.cell0;
-    const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-    const int ddz = part - sub;
-    // the item's cells: one cell (group item.y), or a run of rc = -item.y cells
-    // of one x-row; a lane's atom lies in cell gc + ldx of the run
-    const int rc_n = RUNS && item.y < 0 ? -item.y : 1;
-    const int ncol = RUNS ? span + rc_n - 1 : span;    // x columns of the plane's cells
-    const int nn = ncol * span;
-    for (int nb = lane; nb < nn; nb += 32)
-        offp[nb] = make_float4((float)((nb % ncol - sub) * d.w[0]), (float)((nb / ncol - sub) * d.w[1]),
-                               __int_as_float(nb % ncol), __int_as_float(part * span * span + (nb / ncol) * span));
-    const float ozh = (float)(ddz * d.w[2]);
-    __syncwarp();
-    int i0, ni;
-    if (!RUNS || item.y >= 0) {
-        i0 = start[gc] + 32 * item.y;
-        ni = min(32, count[gc] - 32 * item.y);
-    } else {
-        i0 = start[gc];
-        ni = start[gc + rc_n - 1] + count[gc + rc_n - 1] - i0;
-    }
-    const bool vi = lane < ni;
-    int ldx = 0;                                       // this lane's cell within the run
-    if (RUNS)
-        for (int k = 1; k < rc_n; ++k) ldx += (i0 + lane >= start[gc + k]) ? 1 : 0;
-    // lanes without an atom sit far away: their cutoff test never passes
-    float4 pi = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-    if (vi) pi = pos4[i0 + lane];
-    int nent = 0, nhit = 0;
-    bool overflow = false;
-    const int gz = wrapi(cz + ddz, n2);
-    // the plane's cells, one per lane: first atom and atom count
-    int cj0 = 0, cnj = 0;
-    if (lane < nn) {
-        const int g = d.cell0 + wrapi(cx + lane % ncol - sub, n0) + n0 * (wrapi(cy + lane / ncol - sub, n1) + n1 * gz);
-        cj0 = start[g];
-        cnj = count[g];
-    }
-    // candidates in batches of 32 (one cell at a time), each batch loaded by
-    // the whole warp with one coalesced load, one batch ahead, and tested by
-    // every lane from shared memory.  The test uses the expanded form
-    // |a - b|^2 = |a|^2 + |b|^2 - 2 a.b with a, b relative to the candidate
-    // cell's centre: the loading lane stores (-2 b, |b|^2) in half precision,
-    // two candidates per half2, so that a pair of candidates costs three
-    // packed FMAs and one packed compare.  The test accepts r^2 below
-    // 1.025 r_l^2, r_l = r_c + skin the list radius: for the coordinates that
-    // occur near r_l (|a| < 2 r_l, |b| < r_l) its rounding error stays below
-    // 0.012 r_l^2, inside that margin, and the evaluation decides every pair
-    // exactly.  A short batch is padded
-    // with entries no lane can hit; pairs of one molecule pass this test and
-    // are dropped by the evaluation (a few per atom at most).
-    const float hx = 0.5f * (float)d.w[0], hy = 0.5f * (float)d.w[1], hz = 0.5f * (float)d.w[2];
-    const float4 far = make_float4(0.f, 0.f, 0.f, 1e30f);
-    auto stage = [&](float4 q) {
-        const float bx = q.x - hx, by = q.y - hy, bz = q.z - hz;
-        return make_float4(-2.f * bx, -2.f * by, -2.f * bz, fmaf(bx, bx, fmaf(by, by, bz * bz)));
-    };
-    const float rc2_test = 1.025f * rl2_hi;
-    int nb = 0, jb = 0, j0 = 0, nj = 0;
-    for (;;) {                                         // first non-empty cell (warp-uniform)
-        if (nb >= nn) break;
-        nj = __shfl_sync(0xffffffffu, cnj, nb);
-        if (nj > 0) break;
-        ++nb;
-    }
-    float4 nxt = far;
-    if (nb < nn) {
-        j0 = __shfl_sync(0xffffffffu, cj0, nb);
-        if (lane < nj) nxt = stage(__ldg(pos4 + j0 + lane));
-    }
-    // this lane's atom relative to the centre of neighbour cell nb is pc - offp[nb]
-    // (and its cell lies ldx columns right of the run's first cell)
-    const float pcx = pi.x - hx + (float)ldx * (float)d.w[0], pcy = pi.y - hy, pcz = pi.z - hz;
-    __half *ch = reinterpret_cast<__half *>(cand2);    // candidate 2p + h: halves h of pair p
-    while (nb < nn) {
-        const int bnb = nb, bj = j0 + jb;
-        {
-            const int pp = lane >> 1, h = lane & 1;
-            ch[8 * pp + h] = __float2half_rn(nxt.x);
-            ch[8 * pp + 2 + h] = __float2half_rn(nxt.y);
-            ch[8 * pp + 4 + h] = __float2half_rn(nxt.z);
-            ch[8 * pp + 6 + h] = __float2half_rn(nxt.w);
-        }
-        // advance to the next batch and start its load
-        jb += 32;
-        if (jb >= nj) {
-            jb = 0;
-            for (;;) {
-                if (++nb >= nn) break;
-                nj = __shfl_sync(0xffffffffu, cnj, nb);
-                if (nj > 0) break;
-            }
-            if (nb < nn) j0 = __shfl_sync(0xffffffffu, cj0, nb);
-        }
-        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool ld = nb < nn && jb + lane < nj;
-        if (ld) qn = __ldg(pos4 + j0 + jb + lane);
-        __syncwarp();
-        const float4 o = offp[bnb];
-        const float ax = pcx - o.x, ay = pcy - o.y, az = pcz - ozh;
-        // the candidate cell relative to this lane's cell: outside the lane's
-        // stencil (a run's far end) it holds no pair within r_c
-        const int dxl = __float_as_int(o.z) - ldx;     // sub + x offset of the candidate cell
-        const bool incol = !RUNS || (unsigned)dxl < (unsigned)span;
-        const __half2 ax2 = __float2half2_rn(ax), ay2 = __float2half2_rn(ay), az2 = __float2half2_rn(az);
-        const __half2 thr2 = __float2half2_rn(rc2_test - fmaf(ax, ax, fmaf(ay, ay, az * az)));
-        unsigned bits = 0;                             // bit p: candidate 2p, bit 16 + p: candidate 2p + 1
-#pragma unroll
-        for (int pp = 0; pp < 16; ++pp) {
-            const HPair c = cand2[pp];
-            const __half2 t = __hfma2(ax2, c.x, __hfma2(ay2, c.y, __hfma2(az2, c.z, c.w)));
-            bits |= (__hlt2_mask(t, thr2) & 0x00010001u) << pp;
-        }
-        // interleave: hit mask bit 2p from bit p, bit 2p + 1 from bit 16 + p
-        unsigned lo = bits & 0xffffu, hi = bits >> 16;
-        lo = (lo | (lo << 8)) & 0x00ff00ffu; hi = (hi | (hi << 8)) & 0x00ff00ffu;
-        lo = (lo | (lo << 4)) & 0x0f0f0f0fu; hi = (hi | (hi << 4)) & 0x0f0f0f0fu;
-        lo = (lo | (lo << 2)) & 0x33333333u; hi = (hi | (hi << 2)) & 0x33333333u;
-        lo = (lo | (lo << 1)) & 0x55555555u; hi = (hi | (hi << 1)) & 0x55555555u;
-        const unsigned hm = incol ? (lo | (hi << 1)) : 0u;   // hits among these 32 candidates
-        nxt = ld ? stage(qn) : far;
-        __syncwarp();                                  // cand2 is rewritten next round
-        const unsigned code = (unsigned)(__float_as_int(o.w) + dxl) << 25;
-        // an entry for every batch with a hit, at k = nent of this (plane, atom)
-        if (hm != 0u) {
-            if (nent < L.maxent) {
-                L.ent[((size_t)part * L.maxent + nent) * L.ncap + (i0 + lane)] = make_uint2((unsigned)bj | code, hm);
-                ++nent;
-                nhit += __popc(hm);
-            } else {
-                overflow = true;
-            }
-        }
-    }
-    if (vi) {
-        L.nent[part * L.ncap + i0 + lane] = nent;
-        L.nhit[part * L.ncap + i0 + lane] = nhit;
-    }
-    if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(&sys[s].flags, (int)FLAG_OVERFLOW);
+    return __float2ll_rn(f * (float)kFixScale);
 }
 
+// One 4 x 4 tile: this lane's atom i (cell-local xi, already shifted by the
+// high part of J's cell offset) against atom (k + t) mod 4 of J in step t.
+// DIAG: J = I (steps 1..3 only; every unordered pair is met twice, from each
+// side, so it adds to the force on i only and counts half in energy and
+// virial).  Returns with fj = the force on J atom (k + 3) mod 4 over the tile.
+template <int NF, bool EN, bool DIAG>
+__device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, float zs, float4 ol, int moli,
+                                     float qi, int ai, int jfirst, int nj, int kk, int gbase,
+                                     const float4 *__restrict__ pos4, const float2 *__restrict__ qt,
+                                     const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlorow,
+                                     const int *__restrict__ sidx, const double *__restrict__ r, const double *L,
+                                     TileAcc &acc, float &fjx, float &fjy, float &fjz)
+{
+    fjx = fjy = fjz = 0.f;
+#pragma unroll
+    for (int t = DIAG ? 1 : 0; t < 4; ++t) {
+        const int jj = (kk + t) & 3;
+        const bool vj = jj < nj;
+        const int aj = jfirst + jj;
+        float4 pj = make_float4(1e15f, 1e15f, 1e15f, __int_as_float(-2));
+        float2 qj = make_float2(0.f, 0.f);
+        if (vj) {
+            pj = pos4[aj];
+            qj = qt[aj];
+        }
+        const float dx = (xs - pj.x) - ol.x, dy = (ys - pj.y) - ol.y, dz = (zs - pj.z) - ol.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // pairs within a relative 1e-5 of r_c^2 are decided in FP64 from the
+        // original positions (the energy kernel N is about 2e-3 / A at r_c,
+        // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
+        bool in = r2 < pc.rc2_lo;
+        if (!in && r2 < pc.rc2_hi && vj) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
+        in = in && __float_as_int(pj.w) != moli;       // pairs of one molecule are excluded
+        float rinv = rsqrt_approx(in ? r2 : 1.f);
+        rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);
+        const float r2inv = rinv * rinv;
+        float st = pc.tt[kTail];
+#pragma unroll
+        for (int k = kTail - 1; k >= 0; --k) st = fmaf(st, r2, pc.tt[k]);
+        if (NF > 0) {
+#pragma unroll
+            for (int l = 0; l < NF; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
+        } else {
+            for (int l = 0; l < pc.nff; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
+        }
+        const float qq = qi * qj.x;                    // qi holds ke q_i
+        const float fc = qq * (r2inv * rinv - st);
+        const int tj = __float_as_int(qj.y);
+        const float2 lab = ljrow[tj];
+        const float r6inv = r2inv * r2inv * r2inv;
+        const float fl = (12.f * lab.x * r6inv - 6.f * lab.y) * r6inv * r2inv;
+        const float f = in ? fc + fl : 0.f;
+        acc.fx = fmaf(f, dx, acc.fx);
+        acc.fy = fmaf(f, dy, acc.fy);
+        acc.fz = fmaf(f, dz, acc.fz);
+        const float fw = DIAG ? 0.5f * f : f;
+        const float gx = fw * dx, gy = fw * dy;
+        acc.w[0] = fmaf(gx, dx, acc.w[0]); acc.w[1] = fmaf(gy, dy, acc.w[1]);
+        acc.w[2] = fmaf(fw * dz, dz, acc.w[2]); acc.w[3] = fmaf(gx, dy, acc.w[3]);
+        acc.w[4] = fmaf(gx, dz, acc.w[4]); acc.w[5] = fmaf(gy, dz, acc.w[5]);
+        if (EN && in) {
+            // energy kernel N(r) = 1/r - F(r); the constant of the tail is
+            // applied to sum q_i q_j in FP64 by the caller
+            const float h = DIAG ? 0.5f : 1.f;
+            float se = pc.te[kTail];
+#pragma unroll
+            for (int k = kTail - 1; k >= 1; --k) se = fmaf(se, r2, pc.te[k]);
+            se *= r2;
+            for (int l = 0; l < pc.nfe; ++l) {
+                const float e = exp2_poly(fmaf(-r2, pc.be_hi[l], -r2 * pc.be_lo[l]));
+                se = fmaf(pc.w_hi[l], e, fmaf(pc.w_lo[l], e, se));
+            }
+            kahan_add(acc.uc, acc.cuc, h * (qq * (rinv - se)));
+            kahan_add(acc.uq, acc.cuq, h * qq);
+            const float2 lo = ljlorow[tj];
+            kahan_add(acc.ul, acc.cul, h * ((fmaf(lab.x, r6inv, -lab.y) + fmaf(lo.x, r6inv, -lo.y)) * r6inv));
+            const float fcw = h * fc, flw = h * fl;
+            const float cx = fcw * dx, cy = fcw * dy, lx = flw * dx, ly = flw * dy;
+            acc.wc[0] = fmaf(cx, dx, acc.wc[0]); acc.wc[1] = fmaf(cy, dy, acc.wc[1]);
+            acc.wc[2] = fmaf(fcw * dz, dz, acc.wc[2]); acc.wc[3] = fmaf(cx, dy, acc.wc[3]);
+            acc.wc[4] = fmaf(cx, dz, acc.wc[4]); acc.wc[5] = fmaf(cy, dz, acc.wc[5]);
+            acc.wl[0] = fmaf(lx, dx, acc.wl[0]); acc.wl[1] = fmaf(ly, dy, acc.wl[1]);
+            acc.wl[2] = fmaf(flw * dz, dz, acc.wl[2]); acc.wl[3] = fmaf(lx, dy, acc.wl[3]);
+            acc.wl[4] = fmaf(lx, dz, acc.wl[4]); acc.wl[5] = fmaf(ly, dz, acc.wl[5]);
+        }
+        if (!DIAG) {
+            fjx = fmaf(-f, dx, fjx);
+            fjy = fmaf(-f, dy, fjy);
+            fjz = fmaf(-f, dz, fjz);
+            if (t < 3) {                               // hand the sums to the lane that meets these atoms next
+                const int src = gbase + ((kk + 1) & 3);
+                fjx = __shfl_sync(0xffffffffu, fjx, src);
+                fjy = __shfl_sync(0xffffffffu, fjy, src);
+                fjz = __shfl_sync(0xffffffffu, fjz, src);
+            }
+        }
+    }
+}
+
+}  // namespace
+
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kEvalSplit * kEvalGroups, (EN ? 4 : 8) / kEvalGroups)
-k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const float4 *__restrict__ pos4,
-            const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
-            const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N, const PairList L,
-            float4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsF pc)
+__global__ void __launch_bounds__(32 * kCpWarps)
+k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int2 *__restrict__ items,
+               const int2 *__restrict__ ccl, const float4 *__restrict__ cbox, const float4 *__restrict__ pos4,
+               const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
+               const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N,
+               unsigned long long *__restrict__ ffix, double *__restrict__ partial, const PairConstsF pc)
 {
     __shared__ float4 offh[kMaxNb], offl[kMaxNb];
     __shared__ float2 ljs[EN ? 2 : 1][kMaxTypes * kMaxTypes];   // the system's LJ table (and remainders)
-    const int lane = lane_id();
-    const int span = 2 * sub + 1;
-    // kEvalGroups consecutive groups per block (they share most neighbour
-    // atoms in L1), one warp per (group, segment)
-    const int warp = threadIdx.x >> 5;
-    const int it = blockIdx.x * kEvalGroups + warp / kEvalSplit, seg = warp % kEvalSplit;
-    // the block's groups lie in one system (item_cap per system is a multiple of kEvalGroups)
-    const DevSys &d = sys[item_sys[it]];
-    // evaluation group: 32 consecutive cell-sorted atoms of one system (group
-    // g of the system uses the record slots of its work item item0 + g)
-    const int g32 = 32 * (it - d.item0), nlive = live_n(d);
-    double u0 = 0.0, u1 = 0.0;
-    float wv[18];                                      // Wc, Wl (energy steps), W
-#pragma unroll
-    for (int k = 0; k < 18; ++k) wv[k] = 0.f;
-    const bool ok = !(d.flags & FLAG_OVERFLOW);       // lists of a failed step are not walked
-    if (ok && 32 * (blockIdx.x * kEvalGroups - d.item0) < nlive) {   // block-uniform: some group is live
+    __shared__ int2 queue[kCpWarps][kQueue];
+    __shared__ double rec[kCpWarps][kPairRec];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int kk = lane & 3, gbase = lane & ~3, grp = lane >> 2;
+    const int span = 2 * sub + 1, nparts = sub + 1;
+    // units: item-major, kCpWarps per block; a system's item range is a
+    // multiple of kCpWarps items, so a block never mixes systems
+    const int unit = blockIdx.x * kCpWarps + warp;
+    const int it = unit / nparts, part = unit % nparts;
+    const DevSys &d = sys[item_sys[(blockIdx.x * kCpWarps) / nparts]];
+    const bool ok = !(d.flags & FLAG_OVERFLOW) && live_n(d) > 0;   // block-uniform
+    if (ok) {
         // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
         // must not shift every cross-cell distance the same way)
         for (int nb = threadIdx.x; nb < span * span * span; nb += blockDim.x) {
@@ -462,107 +311,136 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
             ljs[0][t] = lj[d.lj0 + t];
             if (EN) ljs[EN ? 1 : 0][t] = ljlo[d.lj0 + t];
         }
-        __syncthreads();
     }
-    if (ok && g32 < nlive) {                           // warp-uniform
-        const int ks = d.atom0 + g32 + lane;           // this lane's atom (cell-sorted index)
-        const bool vi = g32 + lane < nlive;
-        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 pq = make_float2(0.f, 0.f);
-        // this warp takes hits [h0, h1) of the lane's stream (all planes in order)
-        int nh = 0, pl = 0, krem = 0;
-        const uint2 *ep = L.ent + ks;
-        unsigned base = 0u, mask = 0u;
-        if (vi) {
-            pi = pos4[ks];
-            pq = qt[ks];
-            int tot = 0;
-            for (int p2 = 0; p2 < span; ++p2) tot += L.nhit[p2 * L.ncap + ks];
-            const int h0 = (int)((long long)tot * seg / kEvalSplit);
-            const int h1 = (int)((long long)tot * (seg + 1) / kEvalSplit);
-            nh = h1 - h0;
-            if (nh > 0) {
-                int skip = h0;
-                int hp = L.nhit[ks];
-                while (skip >= hp) { skip -= hp; ++pl; hp = L.nhit[pl * L.ncap + ks]; }
-                ep = L.ent + (size_t)pl * L.maxent * L.ncap + ks;
-                krem = L.nent[pl * L.ncap + ks];
-                while (skip > 0) {                     // walk entries up to hit h0
-                    const uint2 en = *ep;
-                    ep += L.ncap;
-                    --krem;
-                    const int cc = __popc(en.y);
-                    if (cc <= skip) {
-                        skip -= cc;
-                    } else {
-                        base = en.x;
-                        mask = en.y;
-                        for (; skip > 0; --skip) mask &= mask - 1u;
-                    }
-                }
-            }
-        }
-        const int rowi = __float_as_int(pq.y) * d.ntypes;
-        const float2 *ljrow = ljs[0] + rowi, *ljlorow = ljs[EN ? 1 : 0] + rowi;
-        AccF acc;
-        acc.fx = acc.fy = acc.fz = 0.f;
-        acc.uc = acc.ul = acc.uq = acc.cuc = acc.cul = acc.cuq = 0.f;
+    __syncthreads();
+    TileAcc acc;
+    acc.fx = acc.fy = acc.fz = 0.f;
+    acc.uc = acc.ul = acc.uq = acc.cuc = acc.cul = acc.cuq = 0.f;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc.w[k] = acc.wc[k] = acc.wl[k] = 0.f;
-        // one hit ahead: the next hit's atom data, and the next list entry once
-        // the current one has started, are loaded while this hit is evaluated
-        int left = nh;                                 // hits of this lane still to evaluate
-        if (left > 0 && mask == 0u) {
-            const uint2 en = next_entry(L, ks, pl, ep, krem);
-            base = en.x;
-            mask = en.y;
+    for (int k = 0; k < 6; ++k) acc.w[k] = acc.wc[k] = acc.wl[k] = 0.f;
+    const int2 item = items[it];
+    if (ok && item.x >= 0 && it - d.item0 < d.nitems) {     // warp-uniform
+        const int gc = item.x;
+        const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
+        const int lc = gc - d.cell0;
+        const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
+        const float4 bi0 = cbox[2 * it], bi1 = cbox[2 * it + 1];
+        const int ifirst = __float_as_int(bi0.w), ni = __float_as_int(bi1.w);
+        const bool vi = kk < ni;
+        const int ai = ifirst + (vi ? kk : 0);
+        float4 pi = make_float4(-1e15f, -1e15f, -1e15f, __int_as_float(-1));
+        float2 qi2 = make_float2(0.f, 0.f);
+        if (vi) {
+            pi = pos4[ai];
+            qi2 = qt[ai];
         }
-        uint2 nxt = make_uint2(0u, 0u);
-        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, ep, krem);
-        unsigned e = 0u;
-        float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 qj = make_float2(0.f, 0.f);
-        if (left > 0) {
-            e = base + (unsigned)(__ffs(mask) - 1);
-            mask &= mask - 1u;
-            pj = pos4[e & 0x1ffffffu];
-            qj = qt[e & 0x1ffffffu];
-        }
-        const int tmax = __reduce_max_sync(0xffffffffu, nh);
-        for (int kk = 0; kk < tmax; ++kk) {
-            if (kk < nh) {
-                const unsigned ec = e;
-                const float4 pjc = pj;
-                const float2 qjc = qj;
-                if (--left > 0) {
-                    if (mask == 0u) {
-                        base = nxt.x;
-                        mask = nxt.y;
-                        if (left > __popc(mask)) nxt = next_entry(L, ks, pl, ep, krem);
-                    }
-                    e = base + (unsigned)(__ffs(mask) - 1);
-                    mask &= mask - 1u;
-                    pj = pos4[e & 0x1ffffffu];
-                    qj = qt[e & 0x1ffffffu];
+        const int moli = __float_as_int(pi.w);
+        const float qi = pc.ke * qi2.x;
+        const int rowi = __float_as_int(qi2.y) * d.ntypes;
+        const float2 *ljrow = ljs[0] + rowi, *ljlorow = ljs[EN ? 1 : 0] + rowi;
+        unsigned long long *const fxs = ffix, *const fys = ffix + N, *const fzs = ffix + 2 * (size_t)N;
+        const float4 ozero = make_float4(0.f, 0.f, 0.f, 0.f);
+        float fjx, fjy, fjz;
+        // the pairs inside I (plane 0), by the first group
+        if (part == 0 && grp == 0)
+            tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, ozero, moli, qi, ai, ifirst, ni, kk, gbase, pos4, qt, ljrow,
+                               ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
+        // candidate cells of this plane: index ci over the (dx, dy) pairs of
+        // the plane (plane 0 starts with I's own cell, then the upper half)
+        // box test at r_c (tiles are formed anew every evaluation), with a
+        // margin far above the rounding of centres and extents
+        const float rl = sqrtf(pc.rc2_hi) + 1e-3f;
+        const float rl2 = rl * rl;
+        int2 *q = queue[warp];
+        int qhead = 0, qtail = 0;
+        int ci = -1, j = 0, jend = 0, nb = 0;
+        float cix = 0.f, ciy = 0.f, ciz = 0.f;         // I's centre relative to the candidate cell
+        const int ncand = part == 0 ? sub * (span + 1) + 1 : span * span;
+        for (;;) {
+            if (qtail - qhead >= 8 || (ci >= ncand && qtail > qhead)) {
+                // a round: group g takes queue entry qhead + g (if any)
+                const int qe = qhead + grp;
+                int2 e = make_int2(0, 0);
+                if (qe < qtail) e = q[qe & (kQueue - 1)];
+                qhead = min(qhead + 8, qtail);
+                const int jfirst = e.x & 0x1ffffff, nj = e.y;
+                const int code = (unsigned)e.x >> 25;
+                const float4 oh = offh[code], ol = offl[code];
+                tile<NF, EN, false>(pc, pi.x - oh.x, pi.y - oh.y, pi.z - oh.z, ol, moli, qi, ai, jfirst, nj, kk,
+                                    gbase, pos4, qt, ljrow, ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
+                const int jl = (kk + 3) & 3;            // the J atom whose sum this lane holds
+                if (jl < nj) {
+                    const int aj = jfirst + jl;
+                    atomicAdd(fxs + aj, (unsigned long long)to_fix(fjx));
+                    atomicAdd(fys + aj, (unsigned long long)to_fix(fjy));
+                    atomicAdd(fzs + aj, (unsigned long long)to_fix(fjz));
                 }
-                const float4 oh = offh[ec >> 25], ol = offl[ec >> 25];
-                const float dx = ((pi.x - oh.x) - pjc.x) - ol.x, dy = ((pi.y - oh.y) - pjc.y) - ol.y,
-                            dz = ((pi.z - oh.z) - pjc.z) - ol.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                // pairs within a relative 1e-5 of r_c^2 are decided in FP64 from the
-                // original positions (the energy kernel N is about 2e-3 / A at r_c,
-                // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
-                if (__float_as_int(pjc.w) != __float_as_int(pi.w) &&   // not of one molecule
-                    (r2 < pc.rc2_lo || (r2 < pc.rc2_hi &&
-                     inside_cutoff_fp64(r, sidx[ks], sidx[ec & 0x1ffffffu], d.L, pc.rc2d))))
-                    pair_eval<NF, EN>(pc, dx, dy, dz, r2, pq.x, ljrow, ljlorow, qjc, acc);
+                __syncwarp();
+                continue;
             }
+            if (ci >= ncand) break;
+            if (j >= jend) {                           // next candidate cell (warp-uniform)
+                ++ci;
+                if (ci >= ncand) continue;
+                int ddx, ddy;
+                if (part == 0) {
+                    if (ci == 0) { ddx = 0; ddy = 0; }
+                    else if (ci <= sub) { ddx = ci; ddy = 0; }
+                    else { const int u = ci - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
+                } else {
+                    ddx = ci % span - sub; ddy = ci / span - sub;
+                }
+                const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + part, n2));
+                const int2 cc = ccl[g];
+                j = cc.x;
+                jend = cc.x + cc.y;
+                if (part == 0 && ci == 0) j = it + 1;  // own cell: the clusters after I
+                nb = (part + sub) * span * span + (ddy + sub) * span + (ddx + sub);
+                const float4 oh = offh[nb];
+                cix = bi0.x - oh.x; ciy = bi0.y - oh.y; ciz = bi0.z - oh.z;
+                continue;
+            }
+            // a batch of up to 32 candidates, one per lane: box-to-box distance
+            const int jc = j + lane;
+            bool pass = false;
+            int2 ent = make_int2(0, 0);
+            if (jc < jend) {
+                const float4 b0 = cbox[2 * jc], b1 = cbox[2 * jc + 1];
+                const float gx = fmaxf(fabsf(cix - b0.x) - (bi1.x + b1.x), 0.f);
+                const float gy = fmaxf(fabsf(ciy - b0.y) - (bi1.y + b1.y), 0.f);
+                const float gz = fmaxf(fabsf(ciz - b0.z) - (bi1.z + b1.z), 0.f);
+                pass = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rl2;
+                ent = make_int2(__float_as_int(b0.w) | (nb << 25), __float_as_int(b1.w));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) q[(qtail + __popc(m & ((1u << lane) - 1u))) & (kQueue - 1)] = ent;
+            qtail += __popc(m);
+            j += 32;
+            __syncwarp();
         }
-        if (vi) Fpart[(size_t)seg * N + ks] = make_float4(acc.fx, acc.fy, acc.fz, 0.f);
-        // virials: FP32 warp sums; energies: FP64 (compensated lanes), with the
-        // constant of the energy tail applied to sum q_i q_j here
+        // the force on I's atoms: sum over the 8 groups, one add per atom
+        float fx = acc.fx, fy = acc.fy, fz = acc.fz;
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane < 4 && vi) {
+            atomicAdd(fxs + ai, (unsigned long long)to_fix(fx));
+            atomicAdd(fys + ai, (unsigned long long)to_fix(fy));
+            atomicAdd(fzs + ai, (unsigned long long)to_fix(fz));
+        }
+    }
+    // the warp's record: virials as FP32 warp sums, energies in FP64
+    // (compensated lanes) with the constant of the energy tail applied to
+    // sum q_i q_j here; then the block's record, warps in order
+    double v = 0.0;
+    {
+        float wv[18];
 #pragma unroll
         for (int k = 0; k < 6; ++k) wv[12 + k] = warp_sumf(acc.w[k]);
+        double u0 = 0.0, u1 = 0.0;
         if (EN) {
             u0 = warp_sum((double)acc.uc - (double)acc.cuc - pc.te0 * ((double)acc.uq - (double)acc.cuq));
             u1 = warp_sum((double)acc.ul - (double)acc.cul);
@@ -571,16 +449,24 @@ k_pair_eval(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, co
                 wv[k] = warp_sumf(acc.wc[k]);
                 wv[6 + k] = warp_sumf(acc.wl[k]);
             }
-        }
-    }
-    // one record per (item, segment): lane t writes value t (each pair was seen from both atoms)
-    double v = 0.0;
-    if (lane == 0) v = u0;
-    if (lane == 1) v = u1;
+        } else {
 #pragma unroll
-    for (int k = 0; k < 18; ++k)
-        if (lane == 2 + k) v = (double)wv[k];
-    if (lane < kPairRec) partial[((size_t)it * kEvalSplit + seg) * kPairRec + lane] = 0.5 * v;
+            for (int k = 0; k < 12; ++k) wv[k] = 0.f;
+        }
+        if (lane == 0) v = u0;
+        if (lane == 1) v = u1;
+#pragma unroll
+        for (int k = 0; k < 18; ++k)
+            if (lane == 2 + k) v = (double)wv[k];
+    }
+    if (lane < kPairRec) rec[warp][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < kPairRec) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kCpWarps; ++w) t += rec[w][threadIdx.x];
+        partial[(size_t)blockIdx.x * kPairRec + threadIdx.x] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -705,23 +591,21 @@ cudaError_t prepare_pair()
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st)
 {
-    // item_cap is a multiple of kItemAlign per system, so every block lies in one system
-    const int units = b.item_cap * (2 * b.sub + 1);
     if (precision == 1) {
-        // runs of several cells per item occur with cells of r_c / 2 (a dozen atoms)
-        auto build = b.sub >= 2 ? k_pair_build<true> : k_pair_build<false>;
-        build<<<units, 32, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, a.items, a.pos4, b.sub, a.plist, cf.rl2_hi);
-#define RBSOG_PAIR_EVAL(NF, EN)                                                                                  \
-    k_pair_eval<NF, EN><<<b.item_cap / kEvalGroups, 32 * kEvalSplit * kEvalGroups, 0, st>>>(b.sys, b.item_sys, \
-                                                                a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, b.sub, \
-                                                                b.N, a.plist, a.fpart4, partial, cf)
+        // (item, dz plane) units, kCpWarps per block (item_cap is a multiple of kCpWarps per system)
+        const int blocks = b.item_cap * (b.sub + 1) / kCpWarps;
+#define RBSOG_PAIR_CLUSTER(NF, EN)                                                                          \
+    k_pair_cluster<NF, EN><<<blocks, 32 * kCpWarps, 0, st>>>(b.sys, b.item_sys, a.items, a.ccl, a.cbox,  \
+                                                             a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, \
+                                                             b.sub, b.N, a.ffix, partial, cf)
         if (cf.nff == 4) {
-            if (energy) RBSOG_PAIR_EVAL(4, true); else RBSOG_PAIR_EVAL(4, false);
+            if (energy) RBSOG_PAIR_CLUSTER(4, true); else RBSOG_PAIR_CLUSTER(4, false);
         } else {
-            if (energy) RBSOG_PAIR_EVAL(0, true); else RBSOG_PAIR_EVAL(0, false);
+            if (energy) RBSOG_PAIR_CLUSTER(0, true); else RBSOG_PAIR_CLUSTER(0, false);
         }
-#undef RBSOG_PAIR_EVAL
+#undef RBSOG_PAIR_CLUSTER
     } else {
+        const int units = b.item_cap * (2 * b.sub + 1);
         k_pair_f64<<<units * kF64Split / kPairWarps, 32 * kPairWarps, pair_smem(0), st>>>(
             b.sys, b.cell_sys, a.start, a.count, a.items, a.posd, a.aux, a.ljd, b.sub, b.N, a.fpartd, partial, cd);
     }

@@ -88,11 +88,11 @@ struct rbsog_ctx {
     double *bk = nullptr, *br0 = nullptr, *ak = nullptr, *at0 = nullptr;
     double *pair_part = nullptr, *est = nullptr, *mol_part = nullptr, *kin_part = nullptr, *sysred = nullptr;
     double *self_e = nullptr;
-    double4 *fpart = nullptr;   // pair forces per dz plane (FP32 build reads it as float4)
+    double4 *fpart = nullptr;   // FP64 build: pair forces per (dz plane, cell quarter)
+    unsigned long long *ffix = nullptr;   // FP32 build: pair forces in fixed point, x | y | z blocks
+    int2 *ccl = nullptr;        // FP32 build: per cell (first cluster item, clusters)
+    float4 *cbox = nullptr;     // FP32 build: cluster bounding boxes
     double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
-    uint2 *pl_ent = nullptr;     // FP32 pair lists
-    int *pl_nent = nullptr, *pl_nhit = nullptr;
-    int plist_cap = 0;
     double *inv_m = nullptr, *sdv = nullptr;   // per-atom integrator constants
     double2 *ljd = nullptr;     // LJ blocks per system
     float2 *ljf = nullptr, *ljf_lo = nullptr;
@@ -292,7 +292,8 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     // the pair records are reduced beside the long-range part
     cudaEventRecord(c->ev_fork4, c->st);
     cudaStreamWaitEvent(c->st3, c->ev_fork4, 0);
-    launch_reduce_pair(c->b, pair_parts(prec, c->prm.cell_sub), c->pair_part, c->pair_red, c->st3);
+    launch_reduce_pair(c->b, pair_rec_num(prec, c->prm.cell_sub), pair_rec_den(prec), c->pair_part, c->pair_red,
+                       c->st3);
     cudaEventRecord(c->ev_join4, c->st3);
     cudaStreamWaitEvent(c->st, c->ev_join, 0);
     record(c, "sampler_join");
@@ -319,6 +320,7 @@ void enqueue_npt_step(rbsog_ctx *c, int energy)
         launch_atom_update(c->b, c->a, c->ia, 0, c->prm.precision, c->st, 1);
         launch_bin(c->b, c->a, c->prm.precision, c->st, false);
         launch_refresh(c->b, c->a, c->st);
+        launch_cluster_box(c->b, c->a, c->st);
     } else {
         launch_atom_update(c->b, c->a, c->ia, 1, c->prm.precision, c->st);
     }
@@ -538,6 +540,14 @@ bool build_image(const rbsog_params &P, const SlotLayout &ly, DevSys &ds, const 
     ds.nmol = nm;
     ds.ntypes = d.ntypes;
     ds.rng_id = d.rng_id;
+    // FP32 in-cell order: sub-columns about one cluster (kClus atoms at the
+    // system's density) wide
+    {
+        const double rho = n / (d.box[0] * d.box[1] * d.box[2]);
+        const double a = std::cbrt(kClus / std::max(rho, 1e-12));
+        const double wcell = list_radius(P) / P.cell_sub;
+        ds.kc = std::min(4, std::max(1, (int)std::lround(wcell / a)));
+    }
     ds.step = 0;                      // the system's first evaluation uses counter 0
     ds.flags = 0;
     ds.steps_left = -1;
@@ -726,10 +736,12 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             ly.atom0 = N; ly.mol0 = nmolx; ly.bond0 = nbond; ly.angle0 = nang; ly.excl0 = nexc; ly.lj0 = nlj;
             ds.cell0 = C;
             ds.ncell_cap_total = ncap_t;
-            // pair work items: at most one partial 32-atom group per cell; a
-            // multiple of kPairWarps so that no pair-kernel block spans two systems
+            // pair work items (FP32: clusters of kClus atoms; FP64: groups of
+            // 32): at most one partial group per cell; a multiple of
+            // kItemAlign so that no pair-kernel block spans two systems
+            const int gsize = P.precision == RBSOG_FP32 ? kClus : 32;
             ds.item0 = item_cap;
-            ds.item_cap = ((cp.atoms + 31) / 32 + ncap_t + kItemAlign - 1) / kItemAlign * kItemAlign;
+            ds.item_cap = ((cp.atoms + gsize - 1) / gsize + ncap_t + kItemAlign - 1) / kItemAlign * kItemAlign;
             item_cap += ds.item_cap;
             item_sys.insert(item_sys.end(), (size_t)ds.item_cap, k);
             ds.atom0 = N;
@@ -844,8 +856,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
-                  dalloc(c, c->pair_part, (size_t)item_cap * pair_parts(P.precision, P.cell_sub) * kPairRec) &&
-                  dalloc(c, c->fpart, (size_t)N * pair_parts(P.precision, P.cell_sub)) &&
+                  dalloc(c, c->pair_part, (size_t)item_cap * pair_rec_num(P.precision, P.cell_sub) /
+                                              pair_rec_den(P.precision) * kPairRec) &&
                   dalloc(c, c->pair_red, (size_t)S * kPairRedBlocks * kPairRec) &&
                   dalloc(c, c->est, (size_t)S * estimate_blocks(c->Dcap) * 7) && dalloc(c, c->mol_part, (size_t)c->nmchunks * 15) &&
                   dalloc(c, c->kin_part, (size_t)c->nchunks * kKinSplit * 6) && dalloc(c, c->sysred, (size_t)S * kRed) &&
@@ -860,32 +872,12 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->inv_m, inv_m) && upload(c, c->sdv, sdv);
         if (ok) {
             if (P.precision == 1)
-                ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, N) && dalloc(c, c->qt, N) && dalloc(c, c->su, N);
+                ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, N) && dalloc(c, c->qt, N) && dalloc(c, c->su, N) &&
+                     dalloc(c, c->ffix, 3 * (size_t)N) && dalloc(c, c->ccl, C) && dalloc(c, c->cbox, 2 * (size_t)item_cap);
             else
-                ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N);
+                ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N) &&
+                     dalloc(c, c->fpart, (size_t)N * pair_parts(P.precision, P.cell_sub));
             ok = ok && dalloc(c, c->xref, 3 * (size_t)N);
-        }
-        if (ok && P.precision == 1) {
-            // FP32 pair lists: per (dz plane, atom) one entry per batch of 32
-            // candidates with a hit, at most the batches of the plane's cells:
-            // span^2 cells of at most 1.3 x rho (4/3 r_c / sub)^3 atoms (cells
-            // are between r_c / sub and 4/3 r_c / sub wide) at the slot's
-            // largest density
-            const int span = 2 * P.cell_sub + 1;
-            double rho = 0.0;
-            for (int k = 0; k < S; ++k) rho = std::max(rho, caps[k].rho);
-            const double wc = 4.0 / 3.0 * list_radius(P) / P.cell_sub;
-            const double per_cell = std::min((double)kCellCap, 1.3 * rho * wc * wc * wc);
-            const int maxent = span * span * ((int)std::ceil(per_cell / 32.0) + 1);
-            const double total = (double)span * maxent * N;
-            if (total >= 9.0e18) {
-                rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED, "pair lists too large");
-                free_ctx(c);
-                return rr;
-            }
-            c->plist_cap = maxent;
-            ok = dalloc(c, c->pl_ent, (size_t)span * maxent * N) && dalloc(c, c->pl_nent, (size_t)span * N) &&
-                 dalloc(c, c->pl_nhit, (size_t)span * N);
         }
         if (ok) ok = cudaMemset(c->sysred, 0, sizeof(double) * (size_t)S * kRed) == cudaSuccess;
         if (!ok) {
@@ -972,10 +964,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
         c->a.su = c->su; c->a.xref = c->xref; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
-        c->a.fpartd = c->fpart; c->a.fpart4 = reinterpret_cast<float4 *>(c->fpart);
+        c->a.fpartd = c->fpart; c->a.ffix = c->ffix; c->a.ccl = c->ccl; c->a.cbox = c->cbox;
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
-        c->a.plist.ent = c->pl_ent; c->a.plist.nent = c->pl_nent; c->a.plist.nhit = c->pl_nhit;
-        c->a.plist.maxent = c->plist_cap; c->a.plist.ncap = N;
         c->m.nmol = nmolx; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
