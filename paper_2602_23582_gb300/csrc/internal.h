@@ -68,17 +68,17 @@ struct Batch {
 
 // FP32 pair kernel: work items are clusters of kClus consecutive cell-sorted
 // atoms of one cell; one warp per (cluster, dz plane of the half stencil),
-// kCpWarps warps per block, one pair record per block.
+// kCpWarps warps per block, one pair record per warp.
 constexpr int kCpWarps = 4;
 constexpr int kF64Split = 4;    // FP64 pair kernel: warps per (work item, dz plane), each over every 4th cell
 // warps per work item of the pair kernels: FP32, the dz planes 0..sub of the
 // half stencil; FP64, the 2 sub + 1 dz planes x kF64Split cell quarters (each
 // writes a force partial per atom of its item)
 inline int pair_parts(int precision, int sub) { return precision == 1 ? sub + 1 : (2 * sub + 1) * kF64Split; }
-// pair records per work item, as a fraction num / den (FP32: one record per
-// block of kCpWarps warps; FP64: one per warp)
+// pair records per work item, as a fraction num / den (one per warp in both
+// builds; the fraction leaves room for records per block)
 inline int pair_rec_num(int precision, int sub) { return pair_parts(precision, sub); }
-inline int pair_rec_den(int precision) { return precision == 1 ? kCpWarps : 1; }
+inline int pair_rec_den(int) { return 1; }
 
 struct AtomArrays {
     double *r, *p, *F;          // [3N]
@@ -92,8 +92,8 @@ struct AtomArrays {
     double *xref;               // [3N] positions at the last list build
     int *count, *start;         // [C], [C + 1]
     int *sidx;                  // [N] cell-sorted original index
-    float4 *pos4;               // [N] sorted, FP32
-    float2 *qt;                 // [N] sorted (q, type bits)
+    float4 *pos4;               // [kClus item_cap] FP32: cluster slots (x, y, z, molecule id), padded
+    float2 *qt;                 // [kClus item_cap] FP32: cluster slots (q, type bits), padded
     double4 *posd;              // [N] sorted, FP64
     int2 *aux;                  // [N] sorted (mol, type)
     int2 *items;                // [item_cap] (cell, group) pair work items; FP32: (cell, k) = cluster k of the cell

@@ -112,8 +112,8 @@ void launch_bin(const Batch &b, const AtomArrays &a, int precision, cudaStream_t
 // them.  One thread per cell-sorted slot.
 __global__ void k_refresh(const DevSys *__restrict__ sys, const int *__restrict__ atom_sys,
                           const double *__restrict__ r, const double *__restrict__ q, const int *__restrict__ mol,
-                          const int *__restrict__ sidx, const int *__restrict__ cell, int N,
-                          float4 *__restrict__ pos4, uint4 *__restrict__ su)
+                          const int *__restrict__ sidx, const int *__restrict__ cell, const int *__restrict__ start,
+                          const int2 *__restrict__ ccl, int N, float4 *__restrict__ pos4, uint4 *__restrict__ su)
 {
     const int ks = blockIdx.x * blockDim.x + threadIdx.x;
     if (ks >= N) return;
@@ -134,15 +134,18 @@ __global__ void k_refresh(const DevSys *__restrict__ sys, const int *__restrict_
         x -= L * rint(x / L);
         xl[a] = x;
     }
-    pos4[ks] = make_float4((float)xl[0], (float)xl[1], (float)xl[2], __int_as_float(mol[i]));
+    // cluster slot of the atom: the cell's clusters start at item ccl.x
+    const int g = cell[i], kc = ks - start[g];
+    pos4[kClus * (ccl[g].x + kc / kClus) + kc % kClus] =
+        make_float4((float)xl[0], (float)xl[1], (float)xl[2], __int_as_float(mol[i]));
     su[i] = make_uint4(__double2uint_rz(sf[0] * 4294967296.0), __double2uint_rz(sf[1] * 4294967296.0),
                        __double2uint_rz(sf[2] * 4294967296.0), __float_as_uint((float)q[i]));
 }
 
 void launch_refresh(const Batch &b, const AtomArrays &a, cudaStream_t st)
 {
-    k_refresh<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.r, a.q, a.mol, a.sidx, a.cell, b.N,
-                                                 a.pos4, a.su);
+    k_refresh<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.r, a.q, a.mol, a.sidx, a.cell, a.start,
+                                                 a.ccl, b.N, a.pos4, a.su);
 }
 
 // Per-system exclusive scan of the cell counts (one block per system): the
@@ -286,20 +289,29 @@ k_cell_sort(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
             __syncthreads();
         }
     }
+    int2 cc = make_int2(0, 0);
+    if (precision == 1) cc = ccl[c];
     for (int k = t0; k < n; k += kSortThreads) {
         const int i = (int)(unsigned)(s[k] & 0xffffffffull);
         sidx[base + k] = i;
         rank[i] = base + k;          // from here on: cell-sorted position of atom i
         if (precision == 1) {
-            pos4[base + k] = locf[i];
-            qt[base + k] = make_float2((float)q[i], __int_as_float(type[i]));
+            // cluster slot k % kClus of the cell's cluster k / kClus
+            const int slot = kClus * (cc.x + k / kClus) + k % kClus;
+            pos4[slot] = locf[i];
+            qt[slot] = make_float2((float)q[i], __int_as_float(type[i]));
         } else {
             posd[base + k] = locd[i];
             aux[base + k] = make_int2(mol[i], type[i]);
         }
     }
     if (precision != 1) return;
-    const int2 cc = ccl[c];
+    // the unused slots of the last cluster: a far-away atom of no molecule
+    for (int k = n + t0; k < kClus * cc.y; k += kSortThreads) {
+        const int slot = kClus * (cc.x + k / kClus) + k % kClus;
+        pos4[slot] = make_float4(1e15f, 1e15f, 1e15f, __int_as_float(-2));
+        qt[slot] = make_float2(0.f, __int_as_float(0));
+    }
     for (int k = t0; k < cc.y; k += kSortThreads) {
         const int a0 = kClus * k, na = min(kClus, n - a0);
         float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
@@ -327,10 +339,10 @@ __global__ void k_cluster_box(const DevSys *__restrict__ sys, const int *__restr
     const DevSys &d = sys[item_sys[it]];
     if (d.rebuild || live_n(d) == 0 || it - d.item0 >= d.nitems || items[it].x < 0) return;
     const float4 b0 = cbox[2 * it], b1 = cbox[2 * it + 1];
-    const int a0 = __float_as_int(b0.w), na = __float_as_int(b1.w);
+    const int na = __float_as_int(b1.w);
     float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
     for (int j = 0; j < na; ++j) {
-        const float4 v = pos4[a0 + j];
+        const float4 v = pos4[kClus * it + j];
         lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
         hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
     }

@@ -143,9 +143,11 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // plane 0 the clusters J > I of I's own cell plus the pairs inside I.  Every
 // unordered pair of atoms within r_c is seen exactly once.
 //
-// The warp tests the candidate clusters of its cells 32 at a time against I
-// by their bounding boxes (ballot; the passing ones are appended to a small
-// queue in shared memory) and evaluates them in rounds of 8 tiles: lane
+// The clusters of the unit's cells are numbered consecutively; the warp
+// tests them 32 at a time against I by their bounding boxes (each lane finds
+// its candidate's cell by bisection over the cells' first numbers, held one
+// per lane; the passing clusters are appended to a small queue in shared
+// memory) and evaluates them in rounds of 8 tiles: lane
 // (g, k) of the 8 four-lane groups holds atom k of I and, in step t = 0..3,
 // pairs it with atom (k + t) mod 4 of the group's cluster J, so each group
 // evaluates its 4 x 4 tile with full lanes.  The force on I accumulates in
@@ -157,7 +159,7 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // exact and commute, so the sum does not depend on the order in which the
 // warps reach an atom, and results are deterministic.  Energies and the
 // virial are summed per lane in the warp's fixed pair order and reduced to
-// one record per block.
+// one record per warp.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -182,7 +184,7 @@ __device__ __forceinline__ long long to_fix(float f)
 // virial).  Returns with fj = the force on J atom (k + 3) mod 4 over the tile.
 template <int NF, bool EN, bool DIAG>
 __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, float zs, float4 ol, int moli,
-                                     float qi, int ai, int jfirst, int nj, int kk, int gbase,
+                                     float qi, int ai, int jslot, int jfirst, int kk, int gbase,
                                      const float4 *__restrict__ pos4, const float2 *__restrict__ qt,
                                      const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlorow,
                                      const int *__restrict__ sidx, const double *__restrict__ r, const double *L,
@@ -191,22 +193,19 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
     fjx = fjy = fjz = 0.f;
 #pragma unroll
     for (int t = DIAG ? 1 : 0; t < 4; ++t) {
+        // atom (k + t) mod 4 of J; slots past a cluster's atoms hold a far-away
+        // atom of no molecule, which no cutoff test passes
         const int jj = (kk + t) & 3;
-        const bool vj = jj < nj;
+        const float4 pj = pos4[jslot + jj];
+        const float2 qj = qt[jslot + jj];
         const int aj = jfirst + jj;
-        float4 pj = make_float4(1e15f, 1e15f, 1e15f, __int_as_float(-2));
-        float2 qj = make_float2(0.f, 0.f);
-        if (vj) {
-            pj = pos4[aj];
-            qj = qt[aj];
-        }
         const float dx = (xs - pj.x) - ol.x, dy = (ys - pj.y) - ol.y, dz = (zs - pj.z) - ol.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         // pairs within a relative 1e-5 of r_c^2 are decided in FP64 from the
         // original positions (the energy kernel N is about 2e-3 / A at r_c,
         // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
         bool in = r2 < pc.rc2_lo;
-        if (!in && r2 < pc.rc2_hi && vj) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
+        if (!in && r2 < pc.rc2_hi) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
         in = in && __float_as_int(pj.w) != moli;       // pairs of one molecule are excluded
         float rinv = rsqrt_approx(in ? r2 : 1.f);
         rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);
@@ -277,17 +276,16 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
 }  // namespace
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kCpWarps)
+__global__ void __launch_bounds__(32 * kCpWarps, 6)
 k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int2 *__restrict__ items,
                const int2 *__restrict__ ccl, const float4 *__restrict__ cbox, const float4 *__restrict__ pos4,
                const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
-               const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N,
+               const int *__restrict__ sidx, const double *__restrict__ r, int sub, int N, int item_cap,
                unsigned long long *__restrict__ ffix, double *__restrict__ partial, const PairConstsF pc)
 {
     __shared__ float4 offh[kMaxNb], offl[kMaxNb];
     __shared__ float2 ljs[EN ? 2 : 1][kMaxTypes * kMaxTypes];   // the system's LJ table (and remainders)
     __shared__ int2 queue[kCpWarps][kQueue];
-    __shared__ double rec[kCpWarps][kPairRec];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     const int kk = lane & 3, gbase = lane & ~3, grp = lane >> 2;
     const int span = 2 * sub + 1, nparts = sub + 1;
@@ -328,46 +326,67 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
         const int ifirst = __float_as_int(bi0.w), ni = __float_as_int(bi1.w);
         const bool vi = kk < ni;
         const int ai = ifirst + (vi ? kk : 0);
-        float4 pi = make_float4(-1e15f, -1e15f, -1e15f, __int_as_float(-1));
-        float2 qi2 = make_float2(0.f, 0.f);
-        if (vi) {
-            pi = pos4[ai];
-            qi2 = qt[ai];
-        }
+        const float4 pi = pos4[kClus * it + kk];
+        const float2 qi2 = qt[kClus * it + kk];
         const int moli = __float_as_int(pi.w);
         const float qi = pc.ke * qi2.x;
         const int rowi = __float_as_int(qi2.y) * d.ntypes;
         const float2 *ljrow = ljs[0] + rowi, *ljlorow = ljs[EN ? 1 : 0] + rowi;
         unsigned long long *const fxs = ffix, *const fys = ffix + N, *const fzs = ffix + 2 * (size_t)N;
-        const float4 ozero = make_float4(0.f, 0.f, 0.f, 0.f);
         float fjx, fjy, fjz;
         // the pairs inside I (plane 0), by the first group
         if (part == 0 && grp == 0)
-            tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, ozero, moli, qi, ai, ifirst, ni, kk, gbase, pos4, qt, ljrow,
-                               ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
-        // candidate cells of this plane: index ci over the (dx, dy) pairs of
-        // the plane (plane 0 starts with I's own cell, then the upper half)
+            tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, make_float4(0.f, 0.f, 0.f, 0.f), moli, qi, ai, kClus * it,
+                               ifirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
+        // candidate cells of this plane, one per lane: the (dx, dy) pairs of
+        // the plane (plane 0: I's own cell -- its clusters after I -- then
+        // the upper half), their clusters numbered consecutively
+        const int ncand = part == 0 ? sub * (span + 1) + 1 : span * span;
+        int cj = 0, cn = 0, cnb = 0;
+        if (lane < ncand) {
+            int ddx, ddy;
+            if (part == 0) {
+                if (lane == 0) { ddx = 0; ddy = 0; }
+                else if (lane <= sub) { ddx = lane; ddy = 0; }
+                else { const int u = lane - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
+            } else {
+                ddx = lane % span - sub; ddy = lane / span - sub;
+            }
+            const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + part, n2));
+            const int2 cc = ccl[g];
+            cj = cc.x;
+            cn = cc.y;
+            if (part == 0 && lane == 0) { cj = it + 1; cn = cc.x + cc.y - (it + 1); }
+            cnb = (part + sub) * span * span + (ddy + sub) * span + (ddx + sub);
+        }
+        int incl = cn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int cbase = lane < ncand ? incl - cn : 0x7fffffff;   // first candidate of this lane's cell
         // box test at r_c (tiles are formed anew every evaluation), with a
         // margin far above the rounding of centres and extents
         const float rl = sqrtf(pc.rc2_hi) + 1e-3f;
         const float rl2 = rl * rl;
         int2 *q = queue[warp];
-        int qhead = 0, qtail = 0;
-        int ci = -1, j = 0, jend = 0, nb = 0;
-        float cix = 0.f, ciy = 0.f, ciz = 0.f;         // I's centre relative to the candidate cell
-        const int ncand = part == 0 ? sub * (span + 1) + 1 : span * span;
+        int qhead = 0, qtail = 0, k0 = 0;
         for (;;) {
-            if (qtail - qhead >= 8 || (ci >= ncand && qtail > qhead)) {
-                // a round: group g takes queue entry qhead + g (if any)
+            if (qtail - qhead >= 8 || (k0 >= total && qtail > qhead)) {
+                // a round: group g takes queue entry qhead + g (a group
+                // without one takes the dummy cluster past the last item,
+                // whose slots hold far-away atoms of no molecule)
                 const int qe = qhead + grp;
-                int2 e = make_int2(0, 0);
+                int2 e = make_int2(item_cap, 0);
                 if (qe < qtail) e = q[qe & (kQueue - 1)];
                 qhead = min(qhead + 8, qtail);
-                const int jfirst = e.x & 0x1ffffff, nj = e.y;
-                const int code = (unsigned)e.x >> 25;
+                const int jc = e.x, code = e.y & 0x7f, nj = (unsigned)e.y >> 7;
                 const float4 oh = offh[code], ol = offl[code];
-                tile<NF, EN, false>(pc, pi.x - oh.x, pi.y - oh.y, pi.z - oh.z, ol, moli, qi, ai, jfirst, nj, kk,
-                                    gbase, pos4, qt, ljrow, ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
+                const int jfirst = nj ? __float_as_int(cbox[2 * jc].w) : 0;
+                tile<NF, EN, false>(pc, pi.x - oh.x, pi.y - oh.y, pi.z - oh.z, ol, moli, qi, ai, kClus * jc,
+                                    jfirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
                 const int jl = (kk + 3) & 3;            // the J atom whose sum this lane holds
                 if (jl < nj) {
                     const int aj = jfirst + jl;
@@ -378,44 +397,34 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
                 __syncwarp();
                 continue;
             }
-            if (ci >= ncand) break;
-            if (j >= jend) {                           // next candidate cell (warp-uniform)
-                ++ci;
-                if (ci >= ncand) continue;
-                int ddx, ddy;
-                if (part == 0) {
-                    if (ci == 0) { ddx = 0; ddy = 0; }
-                    else if (ci <= sub) { ddx = ci; ddy = 0; }
-                    else { const int u = ci - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
-                } else {
-                    ddx = ci % span - sub; ddy = ci / span - sub;
-                }
-                const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + part, n2));
-                const int2 cc = ccl[g];
-                j = cc.x;
-                jend = cc.x + cc.y;
-                if (part == 0 && ci == 0) j = it + 1;  // own cell: the clusters after I
-                nb = (part + sub) * span * span + (ddy + sub) * span + (ddx + sub);
-                const float4 oh = offh[nb];
-                cix = bi0.x - oh.x; ciy = bi0.y - oh.y; ciz = bi0.z - oh.z;
-                continue;
+            if (k0 >= total) break;
+            // a batch of 32 candidates, one per lane: find the lane's cell (the
+            // last cell whose first candidate is not past it), then the
+            // box-to-box distance
+            const int k = k0 + lane;
+            int c = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int b = __shfl_sync(0xffffffffu, cbase, c + st);
+                if (b <= k) c += st;
             }
-            // a batch of up to 32 candidates, one per lane: box-to-box distance
-            const int jc = j + lane;
+            const int jc = __shfl_sync(0xffffffffu, cj, c) + (k - __shfl_sync(0xffffffffu, cbase, c));
+            const int nb = __shfl_sync(0xffffffffu, cnb, c);
             bool pass = false;
             int2 ent = make_int2(0, 0);
-            if (jc < jend) {
+            if (k < total) {
                 const float4 b0 = cbox[2 * jc], b1 = cbox[2 * jc + 1];
-                const float gx = fmaxf(fabsf(cix - b0.x) - (bi1.x + b1.x), 0.f);
-                const float gy = fmaxf(fabsf(ciy - b0.y) - (bi1.y + b1.y), 0.f);
-                const float gz = fmaxf(fabsf(ciz - b0.z) - (bi1.z + b1.z), 0.f);
+                const float4 oh = offh[nb];
+                const float gx = fmaxf(fabsf((bi0.x - oh.x) - b0.x) - (bi1.x + b1.x), 0.f);
+                const float gy = fmaxf(fabsf((bi0.y - oh.y) - b0.y) - (bi1.y + b1.y), 0.f);
+                const float gz = fmaxf(fabsf((bi0.z - oh.z) - b0.z) - (bi1.z + b1.z), 0.f);
                 pass = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rl2;
-                ent = make_int2(__float_as_int(b0.w) | (nb << 25), __float_as_int(b1.w));
+                ent = make_int2(jc, nb | (__float_as_int(b1.w) << 7));
             }
             const unsigned m = __ballot_sync(0xffffffffu, pass);
             if (pass) q[(qtail + __popc(m & ((1u << lane) - 1u))) & (kQueue - 1)] = ent;
             qtail += __popc(m);
-            j += 32;
+            k0 += 32;
             __syncwarp();
         }
         // the force on I's atoms: sum over the 8 groups, one add per atom
@@ -434,7 +443,7 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
     }
     // the warp's record: virials as FP32 warp sums, energies in FP64
     // (compensated lanes) with the constant of the energy tail applied to
-    // sum q_i q_j here; then the block's record, warps in order
+    // sum q_i q_j here
     double v = 0.0;
     {
         float wv[18];
@@ -459,14 +468,7 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
         for (int k = 0; k < 18; ++k)
             if (lane == 2 + k) v = (double)wv[k];
     }
-    if (lane < kPairRec) rec[warp][lane] = v;
-    __syncthreads();
-    if (threadIdx.x < kPairRec) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kCpWarps; ++w) t += rec[w][threadIdx.x];
-        partial[(size_t)blockIdx.x * kPairRec + threadIdx.x] = t;
-    }
+    if (lane < kPairRec) partial[(size_t)unit * kPairRec + lane] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -597,7 +599,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
 #define RBSOG_PAIR_CLUSTER(NF, EN)                                                                          \
     k_pair_cluster<NF, EN><<<blocks, 32 * kCpWarps, 0, st>>>(b.sys, b.item_sys, a.items, a.ccl, a.cbox,  \
                                                              a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, \
-                                                             b.sub, b.N, a.ffix, partial, cf)
+                                                             b.sub, b.N, b.item_cap, a.ffix, partial, cf)
         if (cf.nff == 4) {
             if (energy) RBSOG_PAIR_CLUSTER(4, true); else RBSOG_PAIR_CLUSTER(4, false);
         } else {

@@ -872,12 +872,22 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->inv_m, inv_m) && upload(c, c->sdv, sdv);
         if (ok) {
             if (P.precision == 1)
-                ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, N) && dalloc(c, c->qt, N) && dalloc(c, c->su, N) &&
+                ok = dalloc(c, c->locf, N) && dalloc(c, c->pos4, (size_t)kClus * (item_cap + 1)) &&
+                     dalloc(c, c->qt, (size_t)kClus * (item_cap + 1)) && dalloc(c, c->su, N) &&
                      dalloc(c, c->ffix, 3 * (size_t)N) && dalloc(c, c->ccl, C) && dalloc(c, c->cbox, 2 * (size_t)item_cap);
             else
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N) &&
                      dalloc(c, c->fpart, (size_t)N * pair_parts(P.precision, P.cell_sub));
             ok = ok && dalloc(c, c->xref, 3 * (size_t)N);
+        }
+        if (ok && P.precision == 1) {
+            // the dummy cluster past the last item (the FP32 pair kernel's
+            // empty tiles): far-away atoms of no molecule
+            std::vector<float4> far(kClus, make_float4(1e15f, 1e15f, 1e15f, 0.f));
+            int m2 = -2;
+            for (auto &f : far) std::memcpy(&f.w, &m2, sizeof(int));
+            ok = cudaMemcpy(c->pos4 + (size_t)kClus * item_cap, far.data(), sizeof(float4) * kClus,
+                            cudaMemcpyHostToDevice) == cudaSuccess;
         }
         if (ok) ok = cudaMemset(c->sysred, 0, sizeof(double) * (size_t)S * kRed) == cudaSuccess;
         if (!ok) {
