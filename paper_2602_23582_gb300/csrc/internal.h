@@ -40,13 +40,23 @@ struct PairConstsF {
     double te0;                 // sum_{nfe <= l < ME} w_l, applied in FP64 to the per-atom sum of q_i q_j
 };
 
-struct PairConstsD {           // FP64 pair kernel constants
-    int M, ME;
+constexpr int kTailD = 12;      // FP64: degree (in u = r^2) of the Taylor tail of the wide Gaussians
+
+// FP64 pair kernel constants.  Gaussians with s_l >= 2.5 r_c are summed as a
+// Taylor polynomial in u = r^2 (u / s_l^2 <= 0.16 for r <= r_c: the
+// remainder is below 0.16^13 / 13! ~ 1e-20 of w_l); the nf narrower ones, of
+// the force and the energy split alike (s = s~ for l < M), as exponentials.
+struct PairConstsD {
+    int M, ME, nf;
     double rc2, ke;
+    float rc2f;                 // r_c^2 (1 + 1e-5): the FP32 candidate test
     double inv_s2[kMaxGauss];   // 1 / s_l^2
     double wt[kMaxGauss];
     double w[kMaxGauss];
+    double tt[kTailD + 1];      // sum_{nf <= l < M} w~_l e^{-u/s~_l^2} = sum_k tt[k] u^k
+    double te[kTailD + 1];      // sum_{nf <= l < ME} w_l e^{-u/s_l^2} = sum_k te[k] u^k
 };
+constexpr double kFix2Scale = 1099511627776.0;   // FP64 pair forces: two words, units 2^-40 and 2^-80
 
 // Everything a kernel needs about the batch of systems.
 struct Batch {
@@ -71,10 +81,9 @@ struct Batch {
 // kCpWarps warps per block, one pair record per warp.
 constexpr int kCpWarps = 4;
 constexpr int kF64Split = 4;    // FP64 pair kernel: warps per (work item, dz plane), each over every 4th cell
-// warps per work item of the pair kernels: FP32, the dz planes 0..sub of the
-// half stencil; FP64, the 2 sub + 1 dz planes x kF64Split cell quarters (each
-// writes a force partial per atom of its item)
-inline int pair_parts(int precision, int sub) { return precision == 1 ? sub + 1 : (2 * sub + 1) * kF64Split; }
+// warps per work item of the pair kernels: the dz planes 0..sub of the half
+// stencil (FP64: x kF64Split cell quarters)
+inline int pair_parts(int precision, int sub) { return precision == 1 ? sub + 1 : (sub + 1) * kF64Split; }
 // pair records per work item, as a fraction num / den (one per warp in both
 // builds; the fraction leaves room for records per block)
 inline int pair_rec_num(int precision, int sub) { return pair_parts(precision, sub); }
@@ -99,8 +108,10 @@ struct AtomArrays {
     int2 *items;                // [item_cap] (cell, group) pair work items; FP32: (cell, k) = cluster k of the cell
     int2 *ccl;                  // [C] FP32: (item of the first cluster, clusters) of each cell
     float4 *cbox;               // [2 item_cap] FP32: cluster bounding box (centre | first atom, half extent | atoms)
-    unsigned long long *ffix;   // [3 N] FP32: pair forces, x | y | z blocks, cell-sorted, fixed point (kFixScale)
-    double4 *fpartd;            // [(2 sub + 1) kF64Split N] FP64 build: pair forces per (dz plane, quarter)
+    unsigned long long *ffix;   // pair forces, cell-sorted, fixed point: FP32 [3 N] x | y | z in units of
+                                // 2^-32 (kFixScale); FP64 [6 N] x | y | z in units of 2^-40, then the
+                                // remainders x | y | z in units of 2^-80 (kFix2Scale)
+    float4 *posf;               // [N] FP64 build: cell-sorted cell-local coordinates in FP32 + molecule id
     // LJ table: system s owns entries [lj0, lj0 + ntypes^2) (DevSys), entry
     // ti * ntypes + tj = (4 eps sig^12, 4 eps sig^6); ljf_lo: FP32 remainders
     const float2 *ljf, *ljf_lo;

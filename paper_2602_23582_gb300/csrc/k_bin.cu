@@ -257,8 +257,8 @@ k_cell_sort(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
             const int *__restrict__ count, int C, int *__restrict__ sidx, int *__restrict__ rank,
             const float4 *__restrict__ locf, const double4 *__restrict__ locd, const double *__restrict__ q,
             const int *__restrict__ type, const int *__restrict__ mol, float4 *__restrict__ pos4,
-            float2 *__restrict__ qt, double4 *__restrict__ posd, int2 *__restrict__ aux,
-            const int2 *__restrict__ ccl, float4 *__restrict__ cbox, int precision)
+            float2 *__restrict__ qt, double4 *__restrict__ posd, float4 *__restrict__ posf,
+            int2 *__restrict__ aux, const int2 *__restrict__ ccl, float4 *__restrict__ cbox, int precision)
 {
     __shared__ unsigned long long s[kCellCap];
     const int c = blockIdx.x, t0 = threadIdx.x;
@@ -301,7 +301,9 @@ k_cell_sort(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, co
             pos4[slot] = locf[i];
             qt[slot] = make_float2((float)q[i], __int_as_float(type[i]));
         } else {
-            posd[base + k] = locd[i];
+            const double4 l = locd[i];
+            posd[base + k] = l;
+            posf[base + k] = make_float4((float)l.x, (float)l.y, (float)l.z, __int_as_float(mol[i]));
             aux[base + k] = make_int2(mol[i], type[i]);
         }
     }
@@ -359,7 +361,8 @@ void launch_scatter_sort(const Batch &b, const AtomArrays &a, int precision, cud
 {
     k_scatter<<<(b.N + 255) / 256, 256, 0, st>>>(b.sys, b.atom_sys, a.cell, a.rank, a.start, a.sidx, b.N);
     k_cell_sort<<<b.C, kSortThreads, 0, st>>>(b.sys, b.cell_sys, a.start, a.count, b.C, a.sidx, a.rank, a.locf,
-                                              a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.aux, a.ccl,
+                                              a.locd, a.q, a.type, a.mol, a.pos4, a.qt, a.posd, a.posf, a.aux,
+                                              a.ccl,
                                               a.cbox, precision);
 }
 

@@ -241,8 +241,7 @@ __global__ void __launch_bounds__(kLrAtoms)
 k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
            const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
            const double *__restrict__ q, const ModeCoef *__restrict__ coef_all, int Dcap,
-           const int *__restrict__ pos_sorted, const double4 *__restrict__ fpart, int nparts,
-           unsigned long long *__restrict__ ffix, int N,
+           const int *__restrict__ pos_sorted, unsigned long long *__restrict__ ffix, int N,
            const double *__restrict__ Fmol, double *__restrict__ F, double *__restrict__ mom,
            const double *__restrict__ inv_m, double kick, double mvv2e, double *__restrict__ kin_part)
 {
@@ -316,16 +315,18 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
         const double qi = q[i];
         const int ks = pos_sorted[i];
         double f[3] = {0.0, 0.0, 0.0};
+        // fixed-point pair forces (FP64: two words), cleared for the next evaluation
         if (F32) {
-            // fixed-point pair forces, cleared for the next evaluation
             for (int a = 0; a < 3; ++a) {
                 f[a] = (double)(long long)ffix[(size_t)a * N + ks] * (1.0 / kFixScale);
                 ffix[(size_t)a * N + ks] = 0ull;
             }
         } else {
-            for (int p = 0; p < nparts; ++p) {
-                const double4 e = fpart[(size_t)p * N + ks];
-                f[0] += e.x; f[1] += e.y; f[2] += e.z;
+            for (int a = 0; a < 3; ++a) {
+                const long long h = (long long)ffix[(size_t)a * N + ks], l = (long long)ffix[(size_t)(3 + a) * N + ks];
+                f[a] = (double)h * (1.0 / kFix2Scale) + (double)l * (1.0 / (kFix2Scale * kFix2Scale));
+                ffix[(size_t)a * N + ks] = 0ull;
+                ffix[(size_t)(3 + a) * N + ks] = 0ull;
             }
         }
         if (F32) {
@@ -365,14 +366,13 @@ void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const M
 {
     const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0, mvv2e = 1.0 / ia.ftm2v;
     const dim3 grid(b.nchunks, kChunk / kLrAtoms);
-    const int nparts = pair_parts(0, b.sub);   // FP64: dz planes x cell quarters
     if (precision == 1)
         k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                    coef, Dcap, a.rank, nullptr, 0, a.ffix, b.N, Fmol, a.F,
+                                                    coef, Dcap, a.rank, a.ffix, b.N, Fmol, a.F,
                                                     a.p, ia.inv_m, kick, mvv2e, kin_part);
     else
         k_lr_force<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                     coef, Dcap, a.rank, a.fpartd, nparts, nullptr, b.N, Fmol,
+                                                     coef, Dcap, a.rank, a.ffix, b.N, Fmol,
                                                      a.F, a.p, ia.inv_m, kick, mvv2e, kin_part);
 }
 

@@ -7,10 +7,10 @@
 //   U  += ke q_i q_j (1/r   - sum_{l<ME} w_l e^{-r^2/s_l^2})          (kernel N)
 //   W  += f (x) r_vec  (eq. P_short: P^N = W / V)
 //
-// FP32 build: one fused kernel over clusters of 4 atoms (k_pair_cluster),
-// every pair evaluated once (Newton's third law), forces accumulated in 64-bit
-// fixed point.  FP64 build: one warp per (32-atom group, dz plane, cell
-// quarter), full pairs (each atom sums all its neighbours itself), hits
+// Both builds evaluate every pair once (Newton's third law) and add forces
+// as 64-bit fixed point, so sums do not depend on the order of the adds.
+// FP32 build: one fused kernel over clusters of 4 atoms (k_pair_cluster).
+// FP64 build: one warp per (32-atom group, dz plane, cell quarter), hits
 // queued per lane and evaluated with full lanes (k_pair_f64).
 //
 // Coordinates are cell-local.  A neighbour cell's periodic offset d_a w_a is
@@ -55,9 +55,8 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 }
 
 struct AccD {
-    double fx, fy, fz;
     double uc, ul;
-    double wc[6], wl[6];
+    double w[6], wc[6], wl[6];
 };
 
 // Cutoff decision for a pair close to r_c, in FP64 from the original
@@ -97,40 +96,56 @@ __device__ __forceinline__ float exp2_poly(float x)
     return __int_as_float(__float_as_int(p) + ((int)n << 23));
 }
 
-__device__ __forceinline__ void pair_eval(const PairConstsD &pc, double dx, double dy, double dz, double qi,
-                                          const double2 *__restrict__ ljrow, double qj, int tj, AccD &acc)
+// One FP64 pair (i, j) with d = r_i - r_j: returns f (force on i = f d)
+// and adds energies and virials (EN: also the Coulomb / LJ split and the
+// energies; the total virial W always).
+template <bool EN>
+__device__ __forceinline__ double pair_eval_d(const PairConstsD &pc, double dx, double dy, double dz, double r2,
+                                              double qq, double2 lab, AccD &acc)
 {
-    const double r2 = dx * dx + dy * dy + dz * dz;
     const double rinv = rsqrt(r2);
     const double r2inv = rinv * rinv;
-    double st = 0.0, se = 0.0;
-    for (int l = 0; l < pc.M; ++l) {
-        double e = exp(-r2 * pc.inv_s2[l]);
-        st = fma(pc.wt[l], e, st);
-        se = fma(pc.w[l], e, se);
+    double st = pc.tt[kTailD], se = pc.te[kTailD];
+#pragma unroll
+    for (int k = kTailD - 1; k >= 0; --k) {
+        st = fma(st, r2, pc.tt[k]);
+        if (EN) se = fma(se, r2, pc.te[k]);
     }
-    for (int l = pc.M; l < pc.ME; ++l) se = fma(pc.w[l], exp(-r2 * pc.inv_s2[l]), se);
-    const double qq = pc.ke * qi * qj;
+    for (int l = 0; l < pc.nf; ++l) {
+        const double e = exp(-r2 * pc.inv_s2[l]);
+        st = fma(pc.wt[l], e, st);
+        if (EN) se = fma(pc.w[l], e, se);
+    }
     const double fc = qq * (r2inv * rinv - st);
-    const double ec = qq * (rinv - se);
-    const double2 lab = __ldg(&ljrow[tj]);
-    const double la = lab.x, lb = lab.y;
     const double r6inv = r2inv * r2inv * r2inv;
-    const double fl = (12.0 * la * r6inv - 6.0 * lb) * r6inv * r2inv;
-    const double el = (la * r6inv - lb) * r6inv;
+    const double fl = (12.0 * lab.x * r6inv - 6.0 * lab.y) * r6inv * r2inv;
     const double f = fc + fl;
-    acc.fx = fma(f, dx, acc.fx);
-    acc.fy = fma(f, dy, acc.fy);
-    acc.fz = fma(f, dz, acc.fz);
-    acc.uc += ec;
-    acc.ul += el;
-    acc.wc[0] += fc * dx * dx; acc.wc[1] += fc * dy * dy; acc.wc[2] += fc * dz * dz;
-    acc.wc[3] += fc * dx * dy; acc.wc[4] += fc * dx * dz; acc.wc[5] += fc * dy * dz;
-    acc.wl[0] += fl * dx * dx; acc.wl[1] += fl * dy * dy; acc.wl[2] += fl * dz * dz;
-    acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
+    acc.w[0] = fma(f * dx, dx, acc.w[0]); acc.w[1] = fma(f * dy, dy, acc.w[1]); acc.w[2] = fma(f * dz, dz, acc.w[2]);
+    acc.w[3] = fma(f * dx, dy, acc.w[3]); acc.w[4] = fma(f * dx, dz, acc.w[4]); acc.w[5] = fma(f * dy, dz, acc.w[5]);
+    if (EN) {
+        acc.uc += qq * (rinv - se);
+        acc.ul += (lab.x * r6inv - lab.y) * r6inv;
+        acc.wc[0] += fc * dx * dx; acc.wc[1] += fc * dy * dy; acc.wc[2] += fc * dz * dz;
+        acc.wc[3] += fc * dx * dy; acc.wc[4] += fc * dx * dz; acc.wc[5] += fc * dy * dz;
+        acc.wl[0] += fl * dx * dx; acc.wl[1] += fl * dy * dy; acc.wl[2] += fl * dz * dz;
+        acc.wl[3] += fl * dx * dy; acc.wl[4] += fl * dx * dz; acc.wl[5] += fl * dy * dz;
+    }
+    return f;
 }
 
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// f added to a force of the FP64 build: two 64-bit fixed-point words, the
+// value in units of 2^-40 rounded to an integer and the rest in units of
+// 2^-80 (integer sums are exact and order-independent).
+__device__ __forceinline__ void add_fix2(unsigned long long *hi, unsigned long long *lo, double f)
+{
+    const double v = f * kFix2Scale;
+    const long long h = __double2ll_rn(v);
+    const long long l = __double2ll_rn((v - (double)h) * kFix2Scale);
+    atomicAdd(hi, (unsigned long long)h);
+    atomicAdd(lo, (unsigned long long)l);
+}
 
 }  // namespace
 
@@ -276,7 +291,7 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
 }  // namespace
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kCpWarps, 6)
+__global__ void __launch_bounds__(32 * kCpWarps, 8)
 k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int2 *__restrict__ items,
                const int2 *__restrict__ ccl, const float4 *__restrict__ cbox, const float4 *__restrict__ pos4,
                const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,
@@ -472,28 +487,38 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 kernel (same structure; plane offsets in FP64 need no lo part)
+// FP64 kernel: one warp per (32-atom group of a cell, dz plane 0..sub of the
+// half stencil, quarter of the plane's cells); every pair evaluated once.
+// Lane = atom i of the group.  The candidate atoms of the plane's cells are
+// read with warp-broadcast loads and tested in FP32 (cell-local coordinates,
+// r^2 < 1.00001 r_c^2, different molecules); the hits are queued per lane and
+// evaluated in FP64 in rounds where every lane with an atom has one, with the
+// exact cutoff test r^2 < r_c^2 in FP64.  On plane 0 the home cell
+// contributes its atoms after i (cell-sorted order), and of the other cells
+// those with dy > 0, or dy = 0 and dx > 0.  The force on i is summed in
+// registers, the force on j added per hit; both as two-word fixed point.
 // ---------------------------------------------------------------------------
+template <bool EN>
 __global__ void __launch_bounds__(32 * kPairWarps)
 k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, const int *__restrict__ start,
            const int *__restrict__ count, const int2 *__restrict__ items, const double4 *__restrict__ posd,
-           const int2 *__restrict__ aux, const double2 *__restrict__ lj, int sub, int N,
-           double4 *__restrict__ Fpart, double *__restrict__ partial, const PairConstsD pc)
+           const float4 *__restrict__ posf, const int2 *__restrict__ aux, const double2 *__restrict__ lj, int sub,
+           int N, unsigned long long *__restrict__ ffix, double *__restrict__ partial, const PairConstsD pc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double rec[kPairWarps][kPairRec];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
     double2 *offp = reinterpret_cast<double2 *>(smem + kPairWarps * QCAP * 32 * sizeof(unsigned)) + warp * kMaxPlane;
-    const int span = 2 * sub + 1;
+    const int span = 2 * sub + 1, nparts = sub + 1;
     // unit = (work item, dz plane, quarter): the quarter takes every kF64Split-th
     // cell of the plane, so that small systems still fill the SMs' FP64 pipes
     const int unit = blockIdx.x * kPairWarps + warp;
-    const int2 item = items[unit / (span * kF64Split)];
-    const int part = (unit / kF64Split) % span, quarter = unit % kF64Split;
-    double red[kPairRec];
+    const int2 item = items[unit / (nparts * kF64Split)];
+    const int part = (unit / kF64Split) % nparts, quarter = unit % kF64Split;
+    AccD acc;
+    acc.uc = acc.ul = 0.0;
 #pragma unroll
-    for (int k = 0; k < kPairRec; ++k) red[k] = 0.0;
+    for (int k = 0; k < 6; ++k) acc.w[k] = acc.wc[k] = acc.wl[k] = 0.0;
     // (a system with a cell beyond kCellCap atoms has failed its step: skipped)
     if (item.x >= 0 && !(sys[cell_sys[item.x]].flags & FLAG_OVERFLOW)) {
         const int gc = item.x;
@@ -501,32 +526,58 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
         const int n0 = d.ncell[0], n1 = d.ncell[1], n2 = d.ncell[2];
         const int lc = gc - d.cell0;
         const int cx = lc % n0, cy = (lc / n0) % n1, cz = lc / (n0 * n1);
-        const int ddz = part - sub;
-        const double oz = ddz * d.w[2];
-        for (int nb = lane; nb < span * span; nb += 32)
-            offp[nb] = make_double2((nb % span - sub) * d.w[0], (nb / span - sub) * d.w[1]);
+        const double oz = part * d.w[2];
+        const int ncand = part == 0 ? sub * (span + 1) + 1 : span * span;
+        // the plane's candidate cells: (dx, dy) and their offsets
+        for (int c = lane; c < ncand; c += 32) {
+            int ddx, ddy;
+            if (part == 0) {
+                if (c == 0) { ddx = 0; ddy = 0; }
+                else if (c <= sub) { ddx = c; ddy = 0; }
+                else { const int u = c - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
+            } else {
+                ddx = c % span - sub; ddy = c / span - sub;
+            }
+            offp[c] = make_double2(ddx * d.w[0], ddy * d.w[1]);
+        }
         __syncwarp();
         const int i0 = start[gc] + 32 * item.y;
         const int ni = min(32, count[gc] - 32 * item.y);
         const bool vi = lane < ni;
         double4 pi = make_double4(0, 0, 0, 0);
-        int2 ai = make_int2(-0x7fffffff, 0);
-        if (vi) { pi = posd[i0 + lane]; ai = aux[i0 + lane]; }
-        const double2 *ljrow = lj + d.lj0 + ai.y * d.ntypes;
-        const double rc2 = pc.rc2;
-        AccD acc;
-        acc.fx = acc.fy = acc.fz = 0.0;
-        acc.uc = acc.ul = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc.wc[k] = acc.wl[k] = 0.0;
+        float4 pif = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+        int moli = -0x7fffffff, ti = 0;
+        if (vi) {
+            pi = posd[i0 + lane];
+            pif = posf[i0 + lane];
+            const int2 ai = aux[i0 + lane];
+            moli = ai.x;
+            ti = ai.y;
+        }
+        const double2 *ljrow = lj + d.lj0 + ti * d.ntypes;
+        const double qike = pc.ke * pi.w;
+        const float rc2f = pc.rc2f;
+        double fix = 0.0, fiy = 0.0, fiz = 0.0;
+        unsigned long long *const hx = ffix, *const hy = ffix + N, *const hz = ffix + 2 * (size_t)N;
+        unsigned long long *const lx = ffix + 3 * (size_t)N, *const ly = ffix + 4 * (size_t)N,
+                           *const lz = ffix + 5 * (size_t)N;
         int head = 0, tail = 0;
 
         auto eval_one = [&](unsigned e) {
-            const unsigned j = e & 0x1ffffffu;
-            const double4 pj = posd[j];
-            const int tj = aux[j].y;
+            const int j = (int)(e & 0x1ffffffu);
             const double2 o = offp[e >> 25];
-            pair_eval(pc, (pi.x - o.x) - pj.x, (pi.y - o.y) - pj.y, (pi.z - oz) - pj.z, pi.w, ljrow, pj.w, tj, acc);
+            const double4 pj = posd[j];
+            const double dx = (pi.x - o.x) - pj.x, dy = (pi.y - o.y) - pj.y, dz = (pi.z - oz) - pj.z;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < pc.rc2)) return;                // the exact cutoff, in FP64
+            const double2 lab = __ldg(&ljrow[aux[j].y]);
+            const double f = pair_eval_d<EN>(pc, dx, dy, dz, r2, qike * pj.w, lab, acc);
+            fix = fma(f, dx, fix);
+            fiy = fma(f, dy, fiy);
+            fiz = fma(f, dz, fiz);
+            add_fix2(hx + j, lx + j, -f * dx);
+            add_fix2(hy + j, ly + j, -f * dy);
+            add_fix2(hz + j, lz + j, -f * dz);
         };
         auto pop = [&]() {
             const int slot = (head & (QCAP - 1)) * 32 + lane;
@@ -534,20 +585,31 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
             eval_one(q[slot]);
         };
 
-        const int gz = wrapi(cz + ddz, n2);
-        for (int nb = quarter; nb < span * span; nb += kF64Split) {
-            const int g = d.cell0 + wrapi(cx + nb % span - sub, n0) + n0 * (wrapi(cy + nb / span - sub, n1) + n1 * gz);
-            const int j0 = start[g], nj = count[g];
-            const double2 o = offp[nb];
-            const double xi = pi.x - o.x, yi = pi.y - o.y, zi = pi.z - oz;
-            const unsigned code = (unsigned)nb << 25;
+        const int gz = wrapi(cz + part, n2);
+        for (int c = quarter; c < ncand; c += kF64Split) {
+            int ddx, ddy;
+            if (part == 0) {
+                if (c == 0) { ddx = 0; ddy = 0; }
+                else if (c <= sub) { ddx = c; ddy = 0; }
+                else { const int u = c - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
+            } else {
+                ddx = c % span - sub; ddy = c / span - sub;
+            }
+            const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * gz);
+            int j0 = start[g];
+            const int nj = count[g];
+            const double2 o = offp[c];
+            const float xi = pif.x - (float)o.x, yi = pif.y - (float)o.y, zi = pif.z - (float)oz;
+            const unsigned code = (unsigned)c << 25;
+            // home cell: the atoms after i in cell-sorted order
+            const int jmin = (part == 0 && c == 0) ? i0 + lane + 1 : 0;
             for (int jb = 0; jb < nj; jb += 32) {
                 const int je = min(jb + 32, nj);
                 for (int j = jb; j < je; ++j) {
-                    const double4 pj = posd[j0 + j];
-                    const double dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                    const double r2 = dx * dx + dy * dy + dz * dz;
-                    if (vi && r2 < rc2 && aux[j0 + j].x != ai.x) {
+                    const float4 pj = posf[j0 + j];
+                    const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (vi && r2 < rc2f && __float_as_int(pj.w) != moli && j0 + j >= jmin) {
                         q[(tail & (QCAP - 1)) * 32 + lane] = (unsigned)(j0 + j) | code;
                         ++tail;
                     }
@@ -561,33 +623,38 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
         }
         while (__any_sync(0xffffffffu, tail > head))
             if (tail > head) pop();
-        if (vi) Fpart[(size_t)(part * kF64Split + quarter) * N + i0 + lane] = make_double4(acc.fx, acc.fy, acc.fz, 0.0);
-        const double v[14] = {acc.uc, acc.ul, acc.wc[0], acc.wc[1], acc.wc[2], acc.wc[3], acc.wc[4],
-                              acc.wc[5], acc.wl[0], acc.wl[1], acc.wl[2], acc.wl[3], acc.wl[4], acc.wl[5]};
-#pragma unroll
-        for (int k = 0; k < 14; ++k) red[k] = warp_sum(v[k]);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[14 + k] = red[2 + k] + red[8 + k];
+        if (vi) {
+            add_fix2(hx + i0 + lane, lx + i0 + lane, fix);
+            add_fix2(hy + i0 + lane, ly + i0 + lane, fiy);
+            add_fix2(hz + i0 + lane, lz + i0 + lane, fiz);
+        }
     }
-    if (lane == 0) {
+    // the warp's record (Ucoul, Ulj, Wc, Wl, W): FP64 warp sums
+    double v = 0.0;
+    {
+        const double uc = warp_sum(acc.uc), ul = warp_sum(acc.ul);
+        if (lane == 0) v = uc;
+        if (lane == 1) v = ul;
 #pragma unroll
-        for (int k = 0; k < kPairRec; ++k) rec[warp][k] = red[k];
+        for (int k = 0; k < 6; ++k) {
+            const double a = warp_sum(acc.wc[k]), b = warp_sum(acc.wl[k]), t = warp_sum(acc.w[k]);
+            if (lane == 2 + k) v = a;
+            if (lane == 8 + k) v = b;
+            if (lane == 14 + k) v = t;
+        }
     }
-    __syncthreads();
-    if (threadIdx.x < kPairRec) {
-        const int t = threadIdx.x;
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kPairWarps; ++w) s += rec[w][t];
-        partial[(size_t)blockIdx.x * kPairRec + t] = 0.5 * s;
-    }
+    if (lane < kPairRec) partial[(size_t)unit * kPairRec + lane] = v;
 }
 
 // Opt the pair kernels into their dynamic shared memory (once per context,
 // outside any stream capture).
 cudaError_t prepare_pair()
 {
-    return cudaFuncSetAttribute(k_pair_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(0));
+    cudaError_t e = cudaFuncSetAttribute(k_pair_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pair_smem(0));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pair_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem(0));
+    return e;
 }
 
 void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairConstsF &cf,
@@ -607,9 +674,11 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
         }
 #undef RBSOG_PAIR_CLUSTER
     } else {
-        const int units = b.item_cap * (2 * b.sub + 1);
-        k_pair_f64<<<units * kF64Split / kPairWarps, 32 * kPairWarps, pair_smem(0), st>>>(
-            b.sys, b.cell_sys, a.start, a.count, a.items, a.posd, a.aux, a.ljd, b.sub, b.N, a.fpartd, partial, cd);
+        const int units = b.item_cap * (b.sub + 1) * kF64Split;
+        auto k = energy ? k_pair_f64<true> : k_pair_f64<false>;
+        k<<<units / kPairWarps, 32 * kPairWarps, pair_smem(0), st>>>(b.sys, b.cell_sys, a.start, a.count, a.items,
+                                                                      a.posd, a.posf, a.aux, a.ljd, b.sub, b.N,
+                                                                      a.ffix, partial, cd);
     }
 }
 

@@ -88,8 +88,8 @@ struct rbsog_ctx {
     double *bk = nullptr, *br0 = nullptr, *ak = nullptr, *at0 = nullptr;
     double *pair_part = nullptr, *est = nullptr, *mol_part = nullptr, *kin_part = nullptr, *sysred = nullptr;
     double *self_e = nullptr;
-    double4 *fpart = nullptr;   // FP64 build: pair forces per (dz plane, cell quarter)
-    unsigned long long *ffix = nullptr;   // FP32 build: pair forces in fixed point, x | y | z blocks
+    float4 *posf = nullptr;     // FP64 build: cell-sorted coordinates in FP32 (candidate tests)
+    unsigned long long *ffix = nullptr;   // pair forces in fixed point (FP32: 3 N words, FP64: 6 N)
     int2 *ccl = nullptr;        // FP32 build: per cell (first cluster item, clusters)
     float4 *cbox = nullptr;     // FP32 build: cluster bounding boxes
     double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
@@ -877,7 +877,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                      dalloc(c, c->ffix, 3 * (size_t)N) && dalloc(c, c->ccl, C) && dalloc(c, c->cbox, 2 * (size_t)item_cap);
             else
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N) &&
-                     dalloc(c, c->fpart, (size_t)N * pair_parts(P.precision, P.cell_sub));
+                     dalloc(c, c->posf, N) && dalloc(c, c->ffix, 6 * (size_t)N);
             ok = ok && dalloc(c, c->xref, 3 * (size_t)N);
         }
         if (ok && P.precision == 1) {
@@ -913,6 +913,22 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             c->pcd.inv_s2[l] = 1.0 / (s[l] * s[l]);
             c->pcd.w[l] = w[l];
             c->pcd.wt[l] = l < P.M ? wt[l] : 0.0;
+        }
+        {
+            // FP64 split: Gaussians with s_l >= 2.5 r_c go into a Taylor tail in u = r^2
+            const double swide = 2.5 * P.rc;
+            int nf = 0;
+            while (nf < MM && s[nf] < swide && st[nf] < swide) ++nf;
+            c->pcd.nf = nf;
+            c->pcd.rc2f = (float)(P.rc * P.rc * (1.0 + 1e-5));
+            for (int k = 0; k <= kTailD; ++k) {
+                double tk = 0.0, ek = 0.0, fact = 1.0;
+                for (int i = 2; i <= k; ++i) fact *= i;
+                for (int l = nf; l < P.M; ++l) tk += wt[l] * std::pow(-1.0 / (st[l] * st[l]), k) / fact;
+                for (int l = nf; l < P.M_energy; ++l) ek += w[l] * std::pow(-1.0 / (s[l] * s[l]), k) / fact;
+                c->pcd.tt[k] = tk;
+                c->pcd.te[k] = ek;
+            }
         }
         {
             // FP32 split: Gaussians with s_l >= 2.5 r_c go into a Taylor tail in u = r^2
@@ -974,7 +990,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->a.mol = c->mol; c->a.cell = c->cell; c->a.rank = c->rank; c->a.locf = c->locf; c->a.locd = c->locd;
         c->a.su = c->su; c->a.xref = c->xref; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
-        c->a.fpartd = c->fpart; c->a.ffix = c->ffix; c->a.ccl = c->ccl; c->a.cbox = c->cbox;
+        c->a.posf = c->posf; c->a.ffix = c->ffix; c->a.ccl = c->ccl; c->a.cbox = c->cbox;
         c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
         c->m.nmol = nmolx; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;

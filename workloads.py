@@ -491,12 +491,16 @@ def membrane(seed: int = 4, Lxy: float = 64.0, Lz: float = 96.0,
 
 
 def served_batch(n_systems: int = 256, seed: int = 5, n_min: int = 500,
-                 n_max: int = 20000, min_box: float = 30.5, steps=(100, 1000),
+                 n_max: int = 20000, min_box: float = 28.0, steps=(100, 1000),
                  rate_per_ms: float | None = None, workers: int = 1):
     """Served-request stream: ``n_systems`` independent systems, sizes
     log-uniform in [n_min, n_max] sites, each an electrolyte (C1 density) or a
-    water-like box (1 g/cm^3) at random; a box too small for three cutoff
-    cells per axis is widened to ``min_box`` (lower density).  Each request
+    water-like box (1 g/cm^3) at random.  A system whose box at that density
+    would be shorter than ``min_box`` (28 A: the 5 x 5 x 5 stencil of cells of
+    r_c / 2 at r_c = 10 A needs 25 A, and the box breathes under NPT) is given
+    more atoms, at the same density, to fill a box of ``min_box`` (a box
+    widened at a fixed atom count would be dilute, and collapse under 1 atm
+    below the stencil's size).  Each request
     asks for a uniform number of NPT steps in ``steps``; arrivals are a
     Poisson stream of ``rate_per_ms`` requests per millisecond (all at t=0
     when None).  ``workers`` > 1 builds the systems in that many spawned
@@ -524,11 +528,14 @@ def _served_system(job):
     """One system of the served stream: (electrolyte?, size, seed, min box)."""
     is_el, size, sub, min_box = job
     if is_el:
+        rho = 1000 / 27000.0                            # the C1 electrolyte's ions per A^3
         n = max(2, int(round(size / 2)) * 2)
-        L = max((n / (1000 / 27000.0)) ** (1 / 3), min_box)
+        n = max(n, 2 * int(math.ceil(rho * min_box ** 3 / 2)))
+        L = (n / rho) ** (1 / 3)
         return electrolyte(n, L, seed=sub, min_dist=min(2.5, 0.8 * L / n ** (1 / 3)))
     nm = max(1, int(round(size / 3)))
-    L = max(66.88 * (nm / 10000.0) ** (1 / 3), min_box)
+    nm = max(nm, int(math.ceil(10000.0 * (min_box / 66.88) ** 3)))
+    L = 66.88 * (nm / 10000.0) ** (1 / 3)
     lat = int(math.ceil(nm ** (1 / 3)))
     return water(nm, L, seed=sub, lattice=lat)
 
