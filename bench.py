@@ -306,6 +306,7 @@ def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
     done = failed = 0
     why = {}                                  # failed requests: status name -> [(atoms, box edge, steps made)]
     work = 0.0                                # atom-steps actually made (a failed request stops early)
+    pair_work = 0.0                           # algorithmic half-pair evaluations made
     for k, t in tickets.items():
         out = srv.result(t)
         if out is not None:
@@ -315,6 +316,8 @@ def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
                 why.setdefault(R.STATUS.get(out[2]["status"], str(out[2]["status"])), []).append(
                     (reqs[k][2].n, round(float(np.min(reqs[k][2].box)), 2), int(out[2]["step"])))
             work += reqs[k][2].n * float(out[2]["step"])
+            sy = reqs[k][2]
+            pair_work += float(out[2]["step"]) * 0.5 * sy.n * (4.0 / 3.0 * math.pi * 1000.0 * sy.n / float(np.prod(sy.box)))
     st = srv.stats()
     slots = srv.slots
     srv.close()
@@ -340,7 +343,14 @@ def served_bench(R, prec, dev_index, rate_per_ms=0.05, plain_sample=12):
             "slot_classes": [{"max_atoms": a, "max_box": bx, "slots": c} for a, bx, c in classes],
             "plain": {"value": pw / pt, "unit": UNIT, "sample_requests": len(pick),
                       "path": "each request alone in its own context (rbsog_run)"},
-            "served_over_plain": (work / wall) / (pw / pt), "generation_s": t_gen}
+            "served_over_plain": (work / wall) / (pw / pt), "generation_s": t_gen,
+            "roofline": {"bound": "alu", "kernel": "whole served stream (pair work)",
+                         "achieved": pair_work * PAIR_FP32_PER_UNIT / wall / 1e12,
+                         "peak": SM_COUNT * FP32_LANES * 2070e6 / 1e12, "unit": "Top/s (FP32 pipe)",
+                         "frac": pair_work * PAIR_FP32_PER_UNIT / wall / (SM_COUNT * FP32_LANES * 2070e6),
+                         "per_unit": f"{PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c, summed over every "
+                                     "request's steps (density of its starting box), over the stream's wall time",
+                         "traffic": None}}
 
 
 def torch_sync():
@@ -388,6 +398,111 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def pair_roofline(half_pairs, pair_ms, prec, sm_clk, pair_trace=None, traffic=None):
+    """Roofline of the pair kernel for one launch: algorithmic half-pairs
+    inside r_c x the work per half-pair, over the launch time, against the
+    bounding pipe (FP32 build: max of FP32 and MUFU work; FP64 build: the
+    FP64 pipe), peaks from the unit counts at the maximum SM clock."""
+    if not pair_ms:
+        return None
+    rec = {"bound": "alu", "units_per_launch": half_pairs, "launch_ms": pair_ms, "traffic": traffic,
+           "timing": "CUDA events recorded by the step graph around each timed pair launch"}
+    if pair_trace is not None and len(pair_trace):
+        rec["launch_ms_p50"] = float(np.percentile(pair_trace, 50))
+    if prec == 0:
+        peak = SM_COUNT * FP64_LANES * sm_clk / 1e12
+        achieved = half_pairs * PAIR_FP64_PER_UNIT / (pair_ms * 1e-3) / 1e12
+        rec.update(kernel="k_pair_f64", achieved=achieved, peak=peak, unit="Top/s (FP64 pipe)",
+                   frac=achieved / peak, per_unit=f"{PAIR_FP64_PER_UNIT} FP64 operations per half-pair inside r_c",
+                   peak_basis=f"{SM_COUNT} SMs x {FP64_LANES} FP64 lanes/clk x {sm_clk / 1e6:.0f} MHz (max clock); "
+                              f"roofline time {half_pairs * PAIR_FP64_PER_UNIT / (peak * 1e12) * 1e6:.1f} us")
+        return rec
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clk / 1e12
+    fp32_peak = SM_COUNT * FP32_LANES * sm_clk / 1e12
+    t_mufu = half_pairs * PAIR_MUFU_PER_UNIT / (mufu_peak * 1e12)
+    t_fp32 = half_pairs * PAIR_FP32_PER_UNIT / (fp32_peak * 1e12)
+    fp32_bound = t_fp32 >= t_mufu
+    per = PAIR_FP32_PER_UNIT if fp32_bound else PAIR_MUFU_PER_UNIT
+    peak = fp32_peak if fp32_bound else mufu_peak
+    achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
+    rec.update(kernel="k_pair_cluster", achieved=achieved, peak=peak,
+               unit="Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)", frac=achieved / peak,
+               per_unit=f"{PAIR_MUFU_PER_UNIT} MUFU + {PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c",
+               peak_basis=f"{SM_COUNT} SMs x ({FP32_LANES} FP32 lanes, {MUFU_PER_SM_CLK} MUFU)/clk x "
+                          f"{sm_clk / 1e6:.0f} MHz (max clock); roofline time MUFU {t_mufu * 1e6:.1f} us, "
+                          f"FP32 {t_fp32 * 1e6:.1f} us")
+    return rec
+
+
+def half_pairs_of(systems, results, rc=10.0):
+    """Algorithmic half-pairs inside r_c per evaluation: N (2 pi / 3) r_c^3
+    rho per system, at the density of the last evaluation's box."""
+    hp = 0.0
+    for s, r in zip(systems, results):
+        rho = s.n / float(np.prod(r["box"]))
+        hp += 0.5 * s.n * (4.0 / 3.0 * math.pi * rc ** 3 * rho)
+    return hp
+
+
+def time_steps(R, ctx, stream, flush, steps, trace=True):
+    """steps NPT steps, each bracketed by CUDA events on the context stream
+    after an L2 flush; returns (per-step ms, per-step pair-kernel ms)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    if trace:
+        R.rbsog_trace_pair(ctx.ctx, steps)
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            R.rbsog_run_async(ctx.ctx, 1)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    R.rbsog_sync(ctx.ctx)
+    tr = np.array([])
+    if trace:
+        tr = R.rbsog_trace_pair_times(ctx.ctx, steps)
+        R.rbsog_trace_pair(ctx.ctx, 0)
+    return np.array([a.elapsed_time(b) for a, b in ev]), tr
+
+
+def sub_record(R, stream, flush, sm_clk, name, prec, P=100, steps=50, warmup=10, systems=None, desc=None,
+               relaxed=False, coupling=None):
+    """One workload at one precision and batch size: NPT steps (as the main
+    line: graph replays, L2 flushed between steps, energies every 100 steps)
+    with the pair kernel's roofline."""
+    if systems is None:
+        systems, desc = workload(name)
+        if relaxed:
+            nrel = relax(R, systems, prec)
+            desc += f"; synthetic start relaxed by {nrel} damped fixed-box steps"
+    desc = desc.replace("P=100", f"P={P}")
+    p = R.rbsog_default_params(10.0, precision=prec, thermo_every=100, P=P)
+    if coupling is not None:
+        p.coupling = coupling
+    t0 = time.perf_counter()
+    ctx = R.Context(systems, p, stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    box0 = ctx.run(0)[0]["box"]
+    R.rbsog_run(ctx.ctx, warmup)
+    step_ms, tr = time_steps(R, ctx, stream, flush, steps)
+    res = ctx.run(0)
+    ctx.close()
+    n = sum(s.n for s in systems)
+    total = float(step_ms.sum()) / 1e3
+    hp = half_pairs_of(systems, res)
+    rec = {"workload": desc, "precision": "FP64" if prec == 0 else "FP32 math, FP64 accumulation",
+           "value": n * steps / total, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": float(step_ms.mean()), "p50_ms": float(np.percentile(step_ms, 50)),
+           "p99_ms": float(np.percentile(step_ms, 99)),
+           "ns_per_day": (p.dt * 1e-6) / (float(step_ms.mean()) / 1e3 / 86400.0),
+           "box_start": [float(x) for x in box0], "box_end": [float(x) for x in res[0]["box"]],
+           "context_create_s": t_create,
+           "roofline": pair_roofline(hp, float(np.mean(tr)) if len(tr) else None, prec, sm_clk, tr)}
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +514,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-more", action="store_true", help="skip the sub-records of the other workloads")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 10^7-site scale point")
     ap.add_argument("--P", type=int, default=100, help="Fourier modes per step (batch size)")
     ap.add_argument("--skin", type=float, default=None,
                     help="pair-list skin in A (FP32 build; default: the library's)")
@@ -563,40 +680,37 @@ def main():
     peaks = load_peaks()
     sm_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     clocks = clock_summary(clk_path, local) if rank == 0 else None
-    roof = None
-    if pair_ms and prec != R.RBSOG_FP32:
-        fp64_peak = SM_COUNT * FP64_LANES * sm_clk / 1e12
-        t_fp64 = half_pairs * PAIR_FP64_PER_UNIT / (fp64_peak * 1e12)
-        achieved = half_pairs * PAIR_FP64_PER_UNIT / (pair_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_pair_f64", "achieved": achieved, "peak": fp64_peak,
-                "unit": "Top/s (FP64 pipe)", "frac": achieved / fp64_peak,
-                "traffic": pair_traffic(args.workload, prec), "units_per_launch": half_pairs,
-                "per_unit": f"{PAIR_FP64_PER_UNIT} FP64 operations per half-pair inside r_c",
-                "peak_basis": f"{SM_COUNT} SMs x {FP64_LANES} FP64 lanes/clk x {sm_clk / 1e6:.0f} MHz "
-                              f"(max clock); roofline time {t_fp64 * 1e6:.1f} us",
-                "launch_ms": pair_ms, "launch_ms_p50": float(np.percentile(pair_trace, 50)),
-                "timing": "CUDA events recorded by the step graph around each timed pair launch"}
-    elif pair_ms:
-        # bound: max(MUFU work / MUFU peak, FP32 work / FP32 peak); on this part the FP32 side binds
-        mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * sm_clk / 1e12
-        fp32_peak = SM_COUNT * FP32_LANES * sm_clk / 1e12
-        t_mufu = half_pairs * PAIR_MUFU_PER_UNIT / (mufu_peak * 1e12)
-        t_fp32 = half_pairs * PAIR_FP32_PER_UNIT / (fp32_peak * 1e12)
-        fp32_bound = t_fp32 >= t_mufu
-        per = PAIR_FP32_PER_UNIT if fp32_bound else PAIR_MUFU_PER_UNIT
-        peak = fp32_peak if fp32_bound else mufu_peak
-        achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_pair_cluster",
-                "achieved": achieved, "peak": peak,
-                "unit": "Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)",
-                "frac": achieved / peak, "traffic": pair_traffic(args.workload, prec),
-                "units_per_launch": half_pairs, "per_unit": f"{PAIR_MUFU_PER_UNIT} MUFU + "
-                f"{PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c",
-                "peak_basis": f"{SM_COUNT} SMs x ({FP32_LANES} FP32 lanes, {MUFU_PER_SM_CLK} MUFU)/clk x "
-                              f"{sm_clk / 1e6:.0f} MHz (max clock); roofline time MUFU {t_mufu * 1e6:.1f} us, "
-                              f"FP32 {t_fp32 * 1e6:.1f} us",
-                "launch_ms": pair_ms, "launch_ms_p50": float(np.percentile(pair_trace, 50)),
-                "timing": "CUDA events recorded by the step graph around each timed pair launch"}
+    roof = pair_roofline(half_pairs, pair_ms, 1 if prec == R.RBSOG_FP32 else 0, sm_clk, pair_trace,
+                         pair_traffic(args.workload, prec))
+    # ---- more workloads (sub-records; rank 0 of a single-GPU run): the plain
+    # FP64 path on the 1000-ion electrolyte and the water box, the
+    # ionic-liquid-like mix at P = 100 and 400, the membrane-like slab in
+    # semi-isotropic NPT, and the 10^7-site water box at P = 100 and 1000
+    more = {}
+    if rank == 0 and world == 1 and not args.no_more:
+        plan = [("fp64_electrolyte", "electrolyte", R.RBSOG_FP64, 100, 100, dict()),
+                ("fp64_water", "water", R.RBSOG_FP64, 100, 30, dict()),
+                ("ionic_liquid_P100", "ionic_liquid", R.RBSOG_FP32, 100, 100, dict(relaxed=True)),
+                ("ionic_liquid_P400", "ionic_liquid", R.RBSOG_FP32, 400, 100, dict(relaxed=True)),
+                # the slab holds 3x water's site density (as configured): at 1 atm
+                # it expands without bound under NPT (semi-isotropic: 64 -> 144 A
+                # in x and y within 110 steps), so its box is held fixed here
+                ("membrane_fixed_box", "membrane", R.RBSOG_FP32, 100, 100,
+                 dict(relaxed=True, coupling=R.RBSOG_COUPLE_FIXED))]
+        for key, name, pr, P, ns, kw in plan:
+            try:
+                more[key] = sub_record(R, stream, flush, sm_clk, name, pr, P=P, steps=ns, **kw)
+            except Exception as ex:   # reported, not fatal
+                more[key] = {"error": str(ex)}
+        if not args.no_scale:
+            try:
+                big, bdesc = workload("big_water")
+                for P in (100, 1000):
+                    more[f"water_1e7_P{P}"] = sub_record(R, stream, flush, sm_clk, "big_water", R.RBSOG_FP32, P=P,
+                                                         steps=20, warmup=5, systems=big, desc=bdesc)
+                del big
+            except Exception as ex:
+                more["water_1e7"] = {"error": str(ex)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -610,8 +724,9 @@ def main():
         except Exception as ex:   # reported, not fatal
             served = {"error": str(ex)}
     # box_half .. finalize, one graph replay (three streams); lists with a skin
-    # add the binning of rebuilt systems and the refresh of the others
-    kernels_per_step = 16 + (2 if p.skin > 0 and prec == R.RBSOG_FP32 else 0)
+    # add the binning of rebuilt systems, the refresh of the others and their
+    # cluster boxes
+    kernels_per_step = 15 + (3 if p.skin > 0 and prec == R.RBSOG_FP32 else 0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == R.RBSOG_FP32 else "f64",
@@ -630,7 +745,8 @@ def main():
                        "energy_every_step": energy_every_step,
                        "kernel_ms_eager_step": kernel_ms},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": kernels_per_step * args.steps, "clocks": clocks, "served": served}
+            "gpu_launches": kernels_per_step * args.steps, "clocks": clocks, "served": served,
+            "more_workloads": more}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -115,6 +115,11 @@ typedef struct {
                                rbsog_step, the lists are rebuilt.  0: rebuilt every step.
                                The box must hold 2 cell_sub + 1 cells of (r_c + skin) /
                                cell_sub. */
+    int cluster_cols;       /* FP32 build: sub-columns per cell axis of the in-cell atom
+                               order that forms the pair kernel's 4-atom clusters, 1..4;
+                               0 = from each system's density (about one cluster wide).
+                               A launch-shape choice: results change only by FP32
+                               rounding (each choice is deterministic). */
 } rbsog_params;
 
 typedef struct {
@@ -228,6 +233,12 @@ rbsog_status rbsog_run(rbsog_ctx *ctx, int nsteps, rbsog_result *last);
  * cell overflow, non-finite results) raised since the last check. */
 rbsog_status rbsog_run_async(rbsog_ctx *ctx, int nsteps);
 rbsog_status rbsog_sync(rbsog_ctx *ctx);
+/* Bounded wait for the steps enqueued on the context (a request loop that
+ * must not block on the GPU): returns RBSOG_ETIMEOUT when they are still
+ * running after timeout_ms (they keep running; call again, or rbsog_sync),
+ * else what rbsog_sync returns.  The wait polls the stream (no device-side
+ * wait is involved).  Errors: RBSOG_EINVAL (timeout_ms < 0 or not finite). */
+rbsog_status rbsog_sync_timeout(rbsog_ctx *ctx, double timeout_ms);
 
 /* Change thermo_every (rbsog_params) of a live context; every >= 0. */
 rbsog_status rbsog_set_thermo_every(rbsog_ctx *ctx, int every);
@@ -373,6 +384,75 @@ rbsog_status rbsog_structure_factor(const double *r, const double *q, int n_atom
 rbsog_status rbsog_structure_factor_noalloc(const double *r, const double *q, int n_atoms,
                                             const double box[3], const int *m, int nD,
                                             double *rho, int precision, void *stream);
+
+/* ---- Autotuner (launch shapes per size class).  Times one NPT step of the
+ * given systems for each candidate shape -- cell_sub in {1, 2} (where the
+ * boxes hold the stencil of cells of r_c) x cluster_cols in {1, 2, 3, 4} in
+ * the FP32 build; cell_sub alone in the FP64 build -- as the median of
+ * `nsteps` graph steps after a warm-up, each candidate in a context of its
+ * own on `stream`, and writes the fastest into *best (a copy of *params with
+ * cell_sub and cluster_cols set).  times (may be NULL): ms per step of each
+ * candidate, in the order cell_sub 1..2, then cluster_cols 1..4 (FP32: 8
+ * entries, FP64: 2), negative for a candidate the boxes cannot take.  The
+ * systems are not changed (each candidate steps its own copy).  Errors: as
+ * rbsog_create; RBSOG_EINVAL when no candidate runs. */
+rbsog_status rbsog_autotune(const rbsog_params *params, int n_systems, const rbsog_system_desc *systems,
+                            int nsteps, void *stream, rbsog_params *best, double *times);
+
+/* ---- Single-system decomposition over several GPUs (sec. 3.2; Algorithm 1,
+ * steps 4-6): every rank draws the same modes from the same Philox key
+ * (rbsog_modes), forms the partial structure factors of its own atoms
+ * (rbsog_structure_factor on its slab), the partials are summed across
+ * ranks by the caller (one all-reduce of 2 nD doubles), and every rank then
+ * computes the long-range forces on its own atoms and the estimators from
+ * the summed rho (rbsog_longrange_force) with no further exchange. */
+
+/* Capacity the mode arrays of rbsog_modes need: P + 1 (paper and
+ * recalibrated samplers) or 2 P (independent draws); 0 for a bad argument. */
+int rbsog_modes_capacity(const rbsog_params *params);
+
+/* The random batch of one evaluation, as a context with this box draws it
+ * for a system keyed (params->seed, rng_id) at Philox counter `step`: the
+ * App. D radial chain and the recalibration chain of sec. 3.2 (or the
+ * sampler params->sampler names), reduced to the distinct modes.
+ *   box  host, 3 edge lengths (orthorhombic h)
+ *   D    host, >= 3 rbsog_modes_capacity(params) ints: the distinct modes m
+ *        (k = 2 pi m / box) in lexicographic order, row-major nD x 3
+ *   cr, cnr host, >= rbsog_modes_capacity(params) ints: multiplicities of
+ *        each mode among the P radial and the P recalibrated samples
+ *   nD   host, out: the number of distinct modes
+ *   S    host, 2 doubles or NULL: the normalizers S^r, S^nr (eqs. Sr, Snr)
+ * Runs on `stream` (cudaStream_t; NULL: the legacy stream), synchronizes it,
+ * and allocates and frees a small device buffer.  Errors: RBSOG_EINVAL (null
+ * argument, bad parameters), RBSOG_EBOX (box edge <= 0), RBSOG_ENOMEM,
+ * RBSOG_ECUDA; the text is in rbsog_last_error(NULL). */
+rbsog_status rbsog_modes(const rbsog_params *params, const double box[3], uint64_t rng_id, uint64_t step, int *D,
+                         int *cr, int *cnr, int *nD, double *S, void *stream);
+
+/* Random-batch long-range forces on n_atoms atoms from the structure factors
+ * of the whole system (eq. f_approx: F_i = q_i sum_d alpha_d k_d
+ * Im(e^{-i k_d . r_i} rho_d), alpha_d = -ke S^r c_r[d] / (2 P V k_d^2)), and
+ * optionally the estimators of eqs. P_approx_r, P_approx_nr:
+ *   r, q     device, n_atoms x 3 positions and n_atoms charges (FP64); the
+ *            caller's atoms (a rank's slab), any image
+ *   m, cr    device, nD x 3 modes and nD radial multiplicities (rbsog_modes)
+ *   cnr      device, nD recalibrated multiplicities, or NULL (no P^F,nr*)
+ *   rho      device, 2 nD FP64 (re, im): rho(k_d) summed over ALL atoms of
+ *            the system (every rank's partial rbsog_structure_factor, summed)
+ *   P, Sr, Snr, ke: batch size, normalizers (rbsog_modes) and Coulomb constant
+ *   F        device, n_atoms x 3 FP64, overwritten (kcal/(mol A))
+ *   est      host, 7 doubles or NULL: U^F* (= V tr P^F,r* / 3; kcal/mol) and
+ *            V P^F,nr* (xx yy zz xy xz yz; kcal/mol).  With est the call
+ *            synchronizes the stream; without, it only enqueues.
+ *   work     device scratch of rbsog_longrange_force_workspace(nD) bytes
+ * precision: RBSOG_FP64, or RBSOG_FP32 (FP32 phases from 32-bit fixed-point
+ * fractional coordinates, FP64 sums).  Errors: RBSOG_EINVAL, RBSOG_EBOX,
+ * RBSOG_ECUDA. */
+size_t rbsog_longrange_force_workspace(int nD);
+rbsog_status rbsog_longrange_force(const double *r, const double *q, int n_atoms, const double box[3], const int *m,
+                                   const int *cr, const int *cnr, int nD, const double *rho, int P, double Sr,
+                                   double Snr, double ke, double *F, double *est, void *work, int precision,
+                                   void *stream);
 
 #ifdef __cplusplus
 }

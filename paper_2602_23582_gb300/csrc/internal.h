@@ -40,12 +40,14 @@ struct PairConstsF {
     double te0;                 // sum_{nfe <= l < ME} w_l, applied in FP64 to the per-atom sum of q_i q_j
 };
 
-constexpr int kTailD = 12;      // FP64: degree (in u = r^2) of the Taylor tail of the wide Gaussians
+constexpr int kTailD = 20;      // FP64: degree (in u = r^2) of the Taylor tail of the wider Gaussians
 
-// FP64 pair kernel constants.  Gaussians with s_l >= 2.5 r_c are summed as a
-// Taylor polynomial in u = r^2 (u / s_l^2 <= 0.16 for r <= r_c: the
-// remainder is below 0.16^13 / 13! ~ 1e-20 of w_l); the nf narrower ones, of
-// the force and the energy split alike (s = s~ for l < M), as exponentials.
+// FP64 pair kernel constants.  Gaussians with s_l >= 0.8 r_c are summed as
+// one Taylor polynomial in u = r^2 of degree kTailD (u / s_l^2 <= 1.6 for
+// r <= r_c; over r <= r_c the polynomial differs from the exponentials by
+// less than 2e-15 of their sum, rounding included, for Table 2 row 2 at r_c =
+// 10 A: measured against direct evaluation); the nf narrower ones, of the
+// force and the energy split alike (s = s~ for l < M), as exponentials.
 struct PairConstsD {
     int M, ME, nf;
     double rc2, ke;
@@ -148,7 +150,7 @@ constexpr int kPairWarps = 1;       // FP64: one warp per block, no block-level 
 constexpr int kItemAlign = kCpWarps;
 static_assert(kItemAlign % kPairWarps == 0, "item alignment");
 constexpr int kPairRec = 20;
-constexpr int kPairRedBlocks = 8;   // second-stage reduction of the unit records, per system
+constexpr int kPairRedBlocks = 64;  // second-stage reduction of the unit records, per system
 // records of system s: [item0 * num / den, ceil((item0 + nitems) * num / den))
 void launch_reduce_pair(const Batch &b, int rec_num, int rec_den, const double *pair_part, double *pair_red,
                         cudaStream_t st);
@@ -193,6 +195,13 @@ constexpr size_t kSkStaticBytes = (size_t)4 << 20;
 cudaError_t sk_static_scratch(void **ptr);
 cudaError_t sk_stateless(const double *r, const double *q, int n, const double box[3], const int *m,
                          int nD, double *rho, void *work, int precision, cudaStream_t st);
+// long-range force on n atoms from given structure factors (eq. f_approx),
+// and (est != null, host) U^F* and V P^F,nr* (xx yy zz xy xz yz)
+size_t lrs_workspace(int nD);
+cudaError_t lr_force_stateless(const double *r, const double *q, int n, const double box[3], const int *m,
+                               const int *cr, const int *cnr, int nD, const double *rho, int P, double Sr,
+                               double Snr, double ke, double *F, double *est, void *work, int precision,
+                               cudaStream_t st);
 
 // ---- k_mol.cu
 struct MolArrays {

@@ -496,4 +496,135 @@ cudaError_t sk_stateless(const double *r, const double *q, int n, const double b
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// stateless long-range force and estimators from given structure factors
+// (the per-rank step of the single-system decomposition: rho summed over
+// every rank's atoms, then each rank's own atoms)
+// ---------------------------------------------------------------------------
+constexpr int kLrsThreads = 128;
+
+// per mode: alpha_d k_d (force coefficient, eq. f_approx) and the estimator
+// terms; one thread per mode
+__global__ void k_lrs_coef(const int *__restrict__ m, const int *__restrict__ cr, const int *__restrict__ cnr,
+                           const double *__restrict__ rho, int nD, double L0, double L1, double L2, int P,
+                           double Sr, double Snr, double ke, double4 *__restrict__ coef, double *__restrict__ terms)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nD) return;
+    const double V = L0 * L1 * L2;
+    const double k[3] = {kTwoPi * m[3 * d] / L0, kTwoPi * m[3 * d + 1] / L1, kTwoPi * m[3 * d + 2] / L2};
+    const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const double a = -ke * 0.5 * Sr * (double)cr[d] / ((double)P * V * k2);
+    coef[d] = make_double4(a * k[0], a * k[1], a * k[2], 0.0);
+    const double r2 = rho[2 * d] * rho[2 * d] + rho[2 * d + 1] * rho[2 * d + 1];
+    // U^F* (= tr V P^F,r* / 3) and V P^F,nr* (xx yy zz xy xz yz), summed over
+    // the modes in order by k_lrs_sum
+    const double ur = ke * Sr / (4.0 * V * P) * (double)cr[d] * r2 / k2;
+    const double cn = cnr ? -ke * Snr / (8.0 * V * P) * (double)cnr[d] * r2 / (k2 * k2) : 0.0;
+    double *t = terms + 7 * (size_t)d;
+    t[0] = ur;
+    t[1] = cn * k[0] * k[0]; t[2] = cn * k[1] * k[1]; t[3] = cn * k[2] * k[2];
+    t[4] = cn * k[0] * k[1]; t[5] = cn * k[0] * k[2]; t[6] = cn * k[1] * k[2];
+}
+
+__global__ void k_lrs_sum(const double *__restrict__ terms, int nD, double *__restrict__ out)
+{
+    const int c = threadIdx.x;
+    if (c >= 7) return;
+    double s = 0.0;
+    for (int d = 0; d < nD; ++d) s += terms[7 * (size_t)d + c];
+    out[c] = s;
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kLrsThreads)
+k_lrs_force(const double *__restrict__ r, const double *__restrict__ q, int n, double L0, double L1, double L2,
+            const int *__restrict__ m, const double *__restrict__ rho, const double4 *__restrict__ coef, int nD,
+            double *__restrict__ F)
+{
+    __shared__ int4 tm[kModeTile];
+    __shared__ double tc[kModeTile][5];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < n;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (act) {
+        const double L[3] = {L0, L1, L2};
+        double s3[3];
+        unsigned f[3];
+        for (int a = 0; a < 3; ++a) {
+            double s = r[3 * i + a] / L[a];
+            s -= floor(s);
+            if (s >= 1.0) s = 0.0;
+            s3[a] = s;
+            f[a] = __double2uint_rz(s * 4294967296.0);
+        }
+        sx = s3[0]; sy = s3[1]; sz = s3[2];
+        v = make_uint4(f[0], f[1], f[2], 0u);
+    }
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int t0 = 0; t0 < nD; t0 += kModeTile) {
+        const int nt = min(kModeTile, nD - t0);
+        __syncthreads();
+        for (int u = threadIdx.x; u < nt; u += blockDim.x) {
+            const int d = t0 + u;
+            tm[u] = make_int4(m[3 * d], m[3 * d + 1], m[3 * d + 2], 0);
+            const double4 c = coef[d];
+            tc[u][0] = c.x; tc[u][1] = c.y; tc[u][2] = c.z;
+            tc[u][3] = rho[2 * d]; tc[u][4] = rho[2 * d + 1];
+        }
+        __syncthreads();
+        for (int u = 0; u < nt; ++u) {
+            const int mm[3] = {tm[u].x, tm[u].y, tm[u].z};
+            double sn, cs;
+            if (F32) {
+                float s32, c32;
+                phase_sincos_f(mm, v, s32, c32);
+                sn = s32; cs = c32;
+            } else {
+                phase_sincos_d(mm, sx, sy, sz, sn, cs);
+            }
+            const double g = tc[u][4] * cs - tc[u][3] * sn;   // Im(e^{-i k.r} rho)
+            gx += tc[u][0] * g;
+            gy += tc[u][1] * g;
+            gz += tc[u][2] * g;
+        }
+    }
+    if (act) {
+        F[3 * i] = q[i] * gx;
+        F[3 * i + 1] = q[i] * gy;
+        F[3 * i + 2] = q[i] * gz;
+    }
+}
+
+size_t lrs_workspace(int nD)
+{
+    return (((size_t)nD * sizeof(double4) + 255) / 256) * 256 + (size_t)nD * 7 * sizeof(double) + 8 * sizeof(double);
+}
+
+cudaError_t lr_force_stateless(const double *r, const double *q, int n, const double box[3], const int *m,
+                               const int *cr, const int *cnr, int nD, const double *rho, int P, double Sr,
+                               double Snr, double ke, double *F, double *est, void *work, int precision,
+                               cudaStream_t st)
+{
+    double4 *coef = static_cast<double4 *>(work);
+    double *terms = reinterpret_cast<double *>(static_cast<char *>(work) + (((size_t)nD * sizeof(double4) + 255) / 256) * 256);
+    double *sums = terms + (size_t)nD * 7;
+    k_lrs_coef<<<(nD + 127) / 128, 128, 0, st>>>(m, cr, cnr, rho, nD, box[0], box[1], box[2], P, Sr, Snr, ke,
+                                                 coef, terms);
+    if (n > 0) {
+        if (precision == 1)
+            k_lrs_force<true><<<(n + kLrsThreads - 1) / kLrsThreads, kLrsThreads, 0, st>>>(
+                r, q, n, box[0], box[1], box[2], m, rho, coef, nD, F);
+        else
+            k_lrs_force<false><<<(n + kLrsThreads - 1) / kLrsThreads, kLrsThreads, 0, st>>>(
+                r, q, n, box[0], box[1], box[2], m, rho, coef, nD, F);
+    }
+    if (est) {
+        k_lrs_sum<<<1, 32, 0, st>>>(terms, nD, sums);
+        cudaMemcpyAsync(est, sums, 7 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace rbsog

@@ -138,11 +138,38 @@ __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >
 // f added to a force of the FP64 build: two 64-bit fixed-point words, the
 // value in units of 2^-40 rounded to an integer and the rest in units of
 // 2^-80 (integer sums are exact and order-independent).
+// The words are formed from the bits of f with integer instructions only
+// (the FP64 pipe, which bounds this kernel, is left to the arithmetic):
+// |f| = m 2^(e - 52), so |f| 2^80 = m 2^(e + 28) as a 128-bit integer U
+// (rounded to an integer, ties away from zero, when e + 28 < 0); the words
+// are U >> 40 and U mod 2^40, negated as one 128-bit number for f < 0 (the
+// second word then stays in [0, 2^40)).  |f| >= 2^23 saturates.
 __device__ __forceinline__ void add_fix2(unsigned long long *hi, unsigned long long *lo, double f)
 {
-    const double v = f * kFix2Scale;
-    const long long h = __double2ll_rn(v);
-    const long long l = __double2ll_rn((v - (double)h) * kFix2Scale);
+    const long long b = __double_as_longlong(f);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | 0x10000000000000ull;
+    const int sh = e + 28;
+    unsigned long long uh, ul;                         // U = uh 2^64 + ul
+    if (sh >= 0) {
+        if (sh < 51) {
+            uh = sh == 0 ? 0ull : m >> (64 - sh);
+            ul = m << sh;
+        } else {
+            uh = 0x7fffffull;                          // saturate: 2^(63 + 40 - 64) - 1
+            ul = ~0ull;
+        }
+    } else {
+        uh = 0ull;
+        ul = sh > -54 ? (m + (1ull << (-sh - 1))) >> -sh : 0ull;
+    }
+    const unsigned long long mask = (1ull << 40) - 1ull;
+    long long h = (long long)((uh << 24) | (ul >> 40));
+    long long l = (long long)(ul & mask);
+    if (b < 0) {                                       // -U: borrow from the high word when l != 0
+        h = l ? -h - 1 : -h;
+        l = l ? (long long)(mask + 1ull) - l : 0;
+    }
     atomicAdd(hi, (unsigned long long)h);
     atomicAdd(lo, (unsigned long long)l);
 }
@@ -187,6 +214,9 @@ struct TileAcc {
     float wc[6], wl[6];              // Coulomb / LJ split of the virial (EN)
 };
 
+// round(f 2^32) as a 64-bit integer: one conversion instruction (it issues to
+// the FP64 pipe, which overlaps the FP32 work here; an integer-only version
+// from the float's bits measured slower: 9.5M more instructions per launch)
 __device__ __forceinline__ long long to_fix(float f)
 {
     return __float2ll_rn(f * (float)kFixScale);
@@ -220,7 +250,10 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
         // original positions (the energy kernel N is about 2e-3 / A at r_c,
         // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
         bool in = r2 < pc.rc2_lo;
-        if (!in && r2 < pc.rc2_hi) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
+        const bool near = !in && r2 < pc.rc2_hi;
+        if (__any_sync(0xffffffffu, near)) {             // rare: out of the common path
+            if (near) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
+        }
         in = in && __float_as_int(pj.w) != moli;       // pairs of one molecule are excluded
         float rinv = rsqrt_approx(in ? r2 : 1.f);
         rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);
@@ -349,10 +382,13 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
         const float2 *ljrow = ljs[0] + rowi, *ljlorow = ljs[EN ? 1 : 0] + rowi;
         unsigned long long *const fxs = ffix, *const fys = ffix + N, *const fzs = ffix + 2 * (size_t)N;
         float fjx, fjy, fjz;
-        // the pairs inside I (plane 0), by the first group
-        if (part == 0 && grp == 0)
-            tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, make_float4(0.f, 0.f, 0.f, 0.f), moli, qi, ai, kClus * it,
-                               ifirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
+        // the pairs inside I (plane 0), by the first group; the whole warp
+        // runs the tile (its votes need every lane), the other groups against
+        // the dummy cluster, which adds nothing
+        if (part == 0)
+            tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, make_float4(0.f, 0.f, 0.f, 0.f), moli, qi, ai,
+                               kClus * (grp == 0 ? it : item_cap), ifirst, kk, gbase, pos4, qt, ljrow, ljlorow,
+                               sidx, r, d.L, acc, fjx, fjy, fjz);
         // candidate cells of this plane, one per lane: the (dx, dy) pairs of
         // the plane (plane 0: I's own cell -- its clusters after I -- then
         // the upper half), their clusters numbered consecutively
@@ -477,11 +513,11 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
 #pragma unroll
             for (int k = 0; k < 12; ++k) wv[k] = 0.f;
         }
-        if (lane == 0) v = u0;
-        if (lane == 1) v = u1;
+        float fv = 0.f;                                // this lane's value: one conversion per lane
 #pragma unroll
         for (int k = 0; k < 18; ++k)
-            if (lane == 2 + k) v = (double)wv[k];
+            if (lane == 2 + k) fv = wv[k];
+        v = lane == 0 ? u0 : (lane == 1 ? u1 : (double)fv);
     }
     if (lane < kPairRec) partial[(size_t)unit * kPairRec + lane] = v;
 }

@@ -9,11 +9,13 @@
 //   kick/kinetic -> finalize (+ step counter advance)
 // An NPT step prepends box_half and atom_update.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/rbsog.h"
@@ -193,6 +195,24 @@ void sog_terms(const rbsog_params &p, int M, std::vector<double> &w, std::vector
     }
     w[0] *= p.omega;
     wt[0] *= p.omega;
+}
+
+// Sampler constants (the same expressions as the paper's formulas, FP64 on
+// the host): pi^1.5 w~ s~^5 and pi^1.5 w~ s~^7 (eqs. samplingP,
+// samplingPnr), s~^2 / 4, and the proposal's standard deviation (App. D).
+void fill_sampler_args(const rbsog_params &P, const std::vector<double> &wt, const std::vector<double> &st,
+                       SamplerArgs &sa)
+{
+    sa.P = P.P; sa.M = P.M; sa.kind = P.sampler; sa.seed = P.seed;
+    const double pi15 = std::pow(kPi, 1.5);
+    for (int l = 0; l < P.M; ++l) {
+        double s5 = st[l] * st[l] * st[l] * st[l] * st[l];
+        sa.wt[l] = wt[l]; sa.st[l] = st[l];
+        sa.cr[l] = pi15 * wt[l] * s5;
+        sa.cn[l] = pi15 * wt[l] * s5 * st[l] * st[l];
+        sa.st2q[l] = st[l] * st[l] * 0.25;
+    }
+    sa.sig_u = 1.0 / (std::sqrt(2.0) * kPi * st[0]);
 }
 
 void record(rbsog_ctx *c, const char *name)
@@ -547,6 +567,7 @@ bool build_image(const rbsog_params &P, const SlotLayout &ly, DevSys &ds, const 
         const double a = std::cbrt(kClus / std::max(rho, 1e-12));
         const double wcell = list_radius(P) / P.cell_sub;
         ds.kc = std::min(4, std::max(1, (int)std::lround(wcell / a)));
+        if (P.cluster_cols > 0) ds.kc = P.cluster_cols;
     }
     ds.step = 0;                      // the system's first evaluation uses counter 0
     ds.flags = 0;
@@ -571,7 +592,7 @@ rbsog_status validate_params(const rbsog_params *p)
         p->M_energy < p->M || p->M_energy > kMaxGauss || p->P < 1 || p->P > kMaxP ||
         p->sampler < 0 || p->sampler > 2 || (p->precision != 0 && p->precision != 1) ||
         (p->cell_sub < 0 || p->cell_sub > 2) || p->coupling < 0 || p->coupling > 2 || p->thermo_every < 0 ||
-        !(p->skin >= 0.0 && p->skin <= p->rc))
+        !(p->skin >= 0.0 && p->skin <= p->rc) || p->cluster_cols < 0 || p->cluster_cols > 4)
         return RBSOG_EINVAL;
     return RBSOG_OK;
 }
@@ -915,8 +936,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             c->pcd.wt[l] = l < P.M ? wt[l] : 0.0;
         }
         {
-            // FP64 split: Gaussians with s_l >= 2.5 r_c go into a Taylor tail in u = r^2
-            const double swide = 2.5 * P.rc;
+            // FP64 split: Gaussians with s_l >= 0.8 r_c go into a Taylor tail in u = r^2
+            const double swide = 0.8 * P.rc;
             int nf = 0;
             while (nf < MM && s[nf] < swide && st[nf] < swide) ++nf;
             c->pcd.nf = nf;
@@ -961,17 +982,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             c->pcf.te0 = te0;
         }
         // LJ: one ntypes x ntypes block per system (uploaded with the buffers above)
-        // sampler (the same expressions as the paper's formulas, FP64 on the host)
-        c->sa.P = P.P; c->sa.M = P.M; c->sa.kind = P.sampler; c->sa.seed = P.seed; 
-        const double pi15 = std::pow(kPi, 1.5);
-        for (int l = 0; l < P.M; ++l) {
-            double s5 = st[l] * st[l] * st[l] * st[l] * st[l];
-            c->sa.wt[l] = wt[l]; c->sa.st[l] = st[l];
-            c->sa.cr[l] = pi15 * wt[l] * s5;
-            c->sa.cn[l] = pi15 * wt[l] * s5 * st[l] * st[l];
-            c->sa.st2q[l] = st[l] * st[l] * 0.25;
-        }
-        c->sa.sig_u = 1.0 / (std::sqrt(2.0) * kPi * st[0]);
+        fill_sampler_args(P, wt, st, c->sa);
         c->ia.dt = P.dt; c->ia.T = P.T; c->ia.Pext = P.P_ext; c->ia.gamma = P.gamma; c->ia.gamma_box = P.gamma_box;
         c->ia.kB = kKB; c->ia.ftm2v = kFtm2v; c->ia.nktv2p = kNktv2p; c->ia.seed = P.seed; 
         c->ia.c_atom = std::exp(-P.gamma * P.dt);
@@ -1349,6 +1360,22 @@ rbsog_status rbsog_sync(rbsog_ctx *c)
     return fs;
 }
 
+rbsog_status rbsog_sync_timeout(rbsog_ctx *c, double timeout_ms)
+{
+    if (!c || !(timeout_ms >= 0.0) || !std::isfinite(timeout_ms)) return RBSOG_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(c->st);
+        if (e == cudaSuccess) return rbsog_sync(c);
+        if (e != cudaErrorNotReady) return cuda_fail(c, e, "sync");
+        const double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (el >= timeout_ms)
+            return fail(c, RBSOG_ETIMEOUT, "rbsog_sync_timeout: the enqueued steps still run after " +
+                                               std::to_string(timeout_ms) + " ms");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
 void *rbsog_stream(rbsog_ctx *c) { return c ? (void *)c->st : nullptr; }
 
 rbsog_status rbsog_run(rbsog_ctx *c, int nsteps, rbsog_result *last)
@@ -1563,6 +1590,147 @@ rbsog_status rbsog_structure_factor_noalloc(const double *r, const double *q, in
     }
     e = sk_stateless(r, q, n_atoms, box, m, nD, rho, work, precision, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? RBSOG_OK : RBSOG_ECUDA;
+}
+
+rbsog_status rbsog_autotune(const rbsog_params *params, int n_systems, const rbsog_system_desc *systems,
+                            int nsteps, void *stream, rbsog_params *best, double *times)
+{
+    if (!params || !systems || n_systems < 1 || !best || nsteps < 1) return RBSOG_EINVAL;
+    rbsog_status vs = validate_params(params);
+    if (vs != RBSOG_OK) return vs;
+    const bool f32 = params->precision == RBSOG_FP32;
+    const int ncols = f32 ? 4 : 1;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e300;
+    int k = 0;
+    for (int sub = 1; sub <= 2; ++sub) {
+        for (int col = 1; col <= ncols; ++col, ++k) {
+            rbsog_params p = *params;
+            p.cell_sub = sub;
+            p.cluster_cols = f32 ? col : 0;
+            if (times) times[k] = -1.0;
+            rbsog_ctx *c = nullptr;
+            if (rbsog_create(&p, n_systems, systems, stream, &c) != RBSOG_OK) continue;   // box too small for the cells
+            std::vector<double> ms;
+            bool ok = rbsog_run(c, 3, nullptr) == RBSOG_OK;   // warm-up (and the step graphs)
+            for (int t = 0; ok && t < nsteps; ++t) {
+                cudaEventRecord(e0, c->st);
+                ok = rbsog_run_async(c, 1) == RBSOG_OK;
+                cudaEventRecord(e1, c->st);
+                float m = 0.f;
+                if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess;
+                ms.push_back(m);
+            }
+            if (ok) ok = rbsog_sync(c) == RBSOG_OK;
+            rbsog_destroy(c);
+            if (!ok || ms.empty()) continue;
+            std::sort(ms.begin(), ms.end());
+            const double med = ms[ms.size() / 2];
+            if (times) times[k] = med;
+            if (med < best_ms) {
+                best_ms = med;
+                *best = p;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cs;
+    if (!(best_ms < 1e300)) return fail(nullptr, RBSOG_EINVAL, "rbsog_autotune: no candidate shape runs");
+    return RBSOG_OK;
+}
+
+int rbsog_modes_capacity(const rbsog_params *p)
+{
+    if (!p || p->P < 1) return 0;
+    return p->sampler == RBSOG_SAMPLER_IID ? 2 * p->P : p->P + 1;
+}
+
+rbsog_status rbsog_modes(const rbsog_params *params, const double box[3], uint64_t rng_id, uint64_t step, int *D,
+                         int *cr, int *cnr, int *nD, double *S, void *stream)
+{
+    if (!params || !box || !D || !cr || !cnr || !nD) return fail(nullptr, RBSOG_EINVAL, "rbsog_modes: null argument");
+    rbsog_status vs = validate_params(params);
+    if (vs != RBSOG_OK) return fail(nullptr, vs, "rbsog_modes: bad parameters");
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0) || !std::isfinite(box[a])) return fail(nullptr, RBSOG_EBOX, "rbsog_modes: box edge <= 0");
+    const rbsog_params &P = *params;
+    std::vector<double> w, s, wt, st;
+    sog_terms(P, P.M, w, s, wt, st);
+    SamplerArgs sa{};
+    fill_sampler_args(P, wt, st, sa);
+    const int Pn = P.P, Dcap = rbsog_modes_capacity(params);
+    // one system of one atom (the sampler reads only its box, key and counter)
+    DevSys h;
+    std::memset(&h, 0, sizeof(h));
+    for (int a = 0; a < 3; ++a) h.L[a] = box[a];
+    h.V = box[0] * box[1] * box[2];
+    h.act = 1;
+    h.n = 1;
+    h.rng_id = rng_id;
+    h.step = step;
+    const size_t nb_sys = ((sizeof(DevSys) + 255) / 256) * 256, nb_ss = ((sizeof(SampScratch) + 255) / 256) * 256;
+    const size_t nb_i = (size_t)(2 * 3 * Pn + 3 * Dcap + 2 * Dcap) * sizeof(int);
+    const size_t nb_pm = (size_t)Pn * sizeof(int4), nb_d = (size_t)4 * Pn * sizeof(double);
+    const size_t total = nb_sys + nb_ss + ((nb_i + 255) / 256) * 256 + ((nb_pm + 255) / 256) * 256 + nb_d;
+    char *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, total);
+    if (e != cudaSuccess) return fail(nullptr, RBSOG_ENOMEM, "rbsog_modes: device memory");
+    DevSys *dsys = reinterpret_cast<DevSys *>(buf);
+    SampScratch *ss = reinterpret_cast<SampScratch *>(buf + nb_sys);
+    int *ib = reinterpret_cast<int *>(buf + nb_sys + nb_ss);
+    int *mr = ib, *mnr = ib + 3 * Pn, *dD = ib + 6 * Pn, *dcr = dD + 3 * Dcap, *dcnr = dcr + Dcap;
+    int4 *pm = reinterpret_cast<int4 *>(buf + nb_sys + nb_ss + ((nb_i + 255) / 256) * 256);
+    double *pd = reinterpret_cast<double *>(reinterpret_cast<char *>(pm) + ((nb_pm + 255) / 256) * 256);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    e = prepare_sampler(Pn);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsys, &h, sizeof(h), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) {
+        Batch b{};
+        b.S = 1;
+        b.sys = dsys;
+        launch_sampler(b, sa, 0, mr, mnr, dD, dcr, dcnr, pm, pd, pd + Pn, pd + 2 * Pn, pd + 3 * Pn, ss, Dcap, cs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dsys, sizeof(h), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess && h.nD > 0) {
+        e = cudaMemcpy(D, dD, sizeof(int) * 3 * h.nD, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(cr, dcr, sizeof(int) * h.nD, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(cnr, dcnr, sizeof(int) * h.nD, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(nullptr, RBSOG_ECUDA, std::string("rbsog_modes: ") + cudaGetErrorString(e));
+    *nD = h.nD;
+    if (S) { S[0] = h.Sr; S[1] = h.Snr; }
+    return RBSOG_OK;
+}
+
+size_t rbsog_longrange_force_workspace(int nD)
+{
+    return nD < 1 ? 0 : lrs_workspace(nD);
+}
+
+rbsog_status rbsog_longrange_force(const double *r, const double *q, int n_atoms, const double box[3], const int *m,
+                                   const int *cr, const int *cnr, int nD, const double *rho, int P, double Sr,
+                                   double Snr, double ke, double *F, double *est, void *work, int precision,
+                                   void *stream)
+{
+    if (!box || !m || !cr || !rho || !work || n_atoms < 0 || nD < 1 || P < 1 || (n_atoms > 0 && (!r || !q || !F)) ||
+        (precision != 0 && precision != 1) || !(Sr > 0) || (cnr && !(Snr > 0)))
+        return fail(nullptr, RBSOG_EINVAL, "rbsog_longrange_force: bad argument");
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0)) return fail(nullptr, RBSOG_EBOX, "rbsog_longrange_force: box edge <= 0");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = lr_force_stateless(r, q, n_atoms, box, m, cr, cnr, nD, rho, P, Sr, Snr, ke, F, est, work,
+                                       precision, cs);
+    if (e == cudaSuccess && est) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess)
+        return fail(nullptr, RBSOG_ECUDA, std::string("rbsog_longrange_force: ") + cudaGetErrorString(e));
+    return RBSOG_OK;
 }
 
 }  // extern "C"

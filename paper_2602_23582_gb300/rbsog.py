@@ -35,7 +35,9 @@ EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_
            "rbsog_trace_pair_times", "rbsog_set_thermo_every", "rbsog_pool_create", "rbsog_pool_load",
            "rbsog_pool_prime", "rbsog_pool_state", "rbsog_pool_unload", "rbsog_server_create",
            "rbsog_server_destroy", "rbsog_server_slots", "rbsog_server_context", "rbsog_server_submit",
-           "rbsog_server_pump", "rbsog_server_result", "rbsog_server_stats")
+           "rbsog_server_pump", "rbsog_server_result", "rbsog_server_stats", "rbsog_modes_capacity",
+           "rbsog_modes", "rbsog_longrange_force_workspace", "rbsog_longrange_force", "rbsog_autotune",
+           "rbsog_sync_timeout")
 
 
 class RbsogError(RuntimeError):
@@ -56,7 +58,8 @@ class rbsog_params(C.Structure):
                 ("seed", C.c_uint64), ("precision", C.c_int), ("ke", C.c_double),
                 ("dt", C.c_double), ("T", C.c_double), ("P_ext", C.c_double), ("gamma", C.c_double),
                 ("gamma_box", C.c_double), ("tau_box", C.c_double), ("compressibility", C.c_double),
-                ("coupling", C.c_int), ("cell_sub", C.c_int), ("thermo_every", C.c_int), ("skin", C.c_double)]
+                ("coupling", C.c_int), ("cell_sub", C.c_int), ("thermo_every", C.c_int), ("skin", C.c_double),
+                ("cluster_cols", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -146,6 +149,15 @@ def lib():
     L.rbsog_server_result.argtypes = [P, C.c_longlong, _I, _D, _D, C.POINTER(rbsog_result)]
     L.rbsog_server_stats.argtypes = [P, _D, _D, _D, C.POINTER(C.c_longlong), _I]
     L.rbsog_trace_pair_times.argtypes = [P, C.c_int, _D, _I]
+    L.rbsog_sync_timeout.argtypes = [P, C.c_double]
+    L.rbsog_autotune.argtypes = [C.POINTER(rbsog_params), C.c_int, C.POINTER(rbsog_system_desc), C.c_int, P,
+                                 C.POINTER(rbsog_params), _D]
+    L.rbsog_modes_capacity.argtypes = [C.POINTER(rbsog_params)]
+    L.rbsog_modes.argtypes = [C.POINTER(rbsog_params), _D, C.c_uint64, C.c_uint64, _I, _I, _I, _I, _D, P]
+    L.rbsog_longrange_force_workspace.argtypes = [C.c_int]
+    L.rbsog_longrange_force_workspace.restype = C.c_size_t
+    L.rbsog_longrange_force.argtypes = [P, P, C.c_int, _D, P, P, P, C.c_int, P, C.c_int, C.c_double, C.c_double,
+                                        C.c_double, P, _D, P, C.c_int, P]
     _lib = L
     return L
 
@@ -429,6 +441,95 @@ def rbsog_structure_factor_noalloc(r, q, box, m, rho, precision=RBSOG_FP32, stre
                                                   C.c_void_p(rho.data_ptr()), precision, st)
     if status != RBSOG_OK:
         raise RbsogError(status, lib().rbsog_last_error(None).decode())
+
+
+def rbsog_sync_timeout(ctx, timeout_ms):
+    """RBSOG_OK once the enqueued steps have finished (flags checked as by
+    rbsog_sync), RBSOG_ETIMEOUT (returned, not raised) while they still run
+    after timeout_ms; other errors raise."""
+    st = lib().rbsog_sync_timeout(ctx, float(timeout_ms))
+    if st not in (RBSOG_OK, -6):
+        _check(st, ctx)
+    return st
+
+
+def rbsog_autotune(params: rbsog_params, systems, nsteps=10, stream=None):
+    """Launch-shape search (cell_sub x cluster_cols): returns (best params,
+    list of (cell_sub, cluster_cols, ms per step or None))."""
+    hold = []
+    descs = (rbsog_system_desc * len(systems))(*[_desc(s, hold, k) for k, s in enumerate(systems)])
+    best = rbsog_params()
+    f32 = params.precision == RBSOG_FP32
+    cands = [(sub, col if f32 else 0) for sub in (1, 2) for col in ((1, 2, 3, 4) if f32 else (0,))]
+    times = np.zeros(len(cands))
+    st = C.c_void_p(stream) if stream else None
+    _check(lib().rbsog_autotune(C.byref(params), len(systems), descs, int(nsteps), st, C.byref(best),
+                                times.ctypes.data_as(_D)))
+    return best, [(a, b, float(t) if t >= 0 else None) for (a, b), t in zip(cands, times)]
+
+
+def rbsog_modes(params: rbsog_params, box, rng_id, step, stream=None):
+    """The distinct modes of one evaluation (host arrays): dict with D (nD, 3),
+    cr, cnr (nD,) and S = (S^r, S^nr)."""
+    cap = lib().rbsog_modes_capacity(C.byref(params))
+    D = np.zeros((cap, 3), np.int32)
+    cr, cnr = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    nD, S = C.c_int(0), np.zeros(2)
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    st = C.c_void_p(stream) if stream else None
+    status = lib().rbsog_modes(C.byref(params), b, int(rng_id), int(step), D.ctypes.data_as(_I),
+                               cr.ctypes.data_as(_I), cnr.ctypes.data_as(_I), C.byref(nD),
+                               S.ctypes.data_as(_D), st)
+    if status != RBSOG_OK:
+        raise RbsogError(status, lib().rbsog_last_error(None).decode())
+    n = nD.value
+    return dict(D=D[:n].copy(), cr=cr[:n].copy(), cnr=cnr[:n].copy(), S=(float(S[0]), float(S[1])))
+
+
+def rbsog_longrange_force_workspace(nD):
+    return lib().rbsog_longrange_force_workspace(int(nD))
+
+
+def rbsog_longrange_force(r, q, box, m, cr, cnr, rho, P, Sr, Snr, ke, F, work, precision=RBSOG_FP64,
+                          estimators=True, stream=None):
+    """Long-range forces on the atoms (r, q) from the whole system's rho
+    (device tensors: r (n, 3) / q (n,) / rho (2 nD,) / F (n, 3) float64, m
+    (nD, 3) / cr / cnr (nD,) int32, work uint8 of the workspace size); returns
+    (U^F*, V P^F,nr* as a 3x3 array) when estimators is set."""
+    import torch
+    n, nD = int(q.numel()), int(m.numel()) // 3
+    if n > 0:
+        _check_tensor("r", r, torch.float64, numel_eq=3 * n)
+        _check_tensor("q", q, torch.float64, numel_eq=n)
+        _check_tensor("F", F, torch.float64, numel_eq=3 * n)
+    _check_tensor("m", m, torch.int32, numel_eq=3 * nD)
+    _check_tensor("cr", cr, torch.int32, numel_eq=nD)
+    if cnr is not None:
+        _check_tensor("cnr", cnr, torch.int32, numel_eq=nD)
+    _check_tensor("rho", rho, torch.float64, numel_min=2 * nD)
+    need = lib().rbsog_longrange_force_workspace(nD)
+    if not isinstance(work, torch.Tensor) or work.numel() * work.element_size() < need:
+        raise ValueError(f"work: needs {need} bytes")
+    devs = dict(m=m, cr=cr, rho=rho, work=work)
+    if n > 0:
+        devs.update(r=r, q=q, F=F)
+    if cnr is not None:
+        devs["cnr"] = cnr
+    _check_devices(**devs)
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    est = np.zeros(7)
+    vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    st = C.c_void_p(stream) if stream else None
+    status = lib().rbsog_longrange_force(vp(r) if n else None, vp(q) if n else None, n, b, vp(m), vp(cr), vp(cnr),
+                                         nD, vp(rho), int(P), float(Sr), float(Snr), float(ke),
+                                         vp(F) if n else None, est.ctypes.data_as(_D) if estimators else None,
+                                         vp(work), precision, st)
+    if status != RBSOG_OK:
+        raise RbsogError(status, lib().rbsog_last_error(None).decode())
+    if estimators:
+        W = np.array([[est[1], est[4], est[5]], [est[4], est[2], est[6]], [est[5], est[6], est[3]]])
+        return float(est[0]), W
+    return None
 
 
 def result_dict(r: rbsog_result) -> dict:
