@@ -16,14 +16,18 @@ struct SogConsts {
     float wtf[kMaxGauss], wf[kMaxGauss], ist2f[kMaxGauss], is2f[kMaxGauss];
 };
 
-constexpr int kTail = 7;        // degree (in u = r^2) of the Taylor tail of the wide Gaussians
+constexpr int kTail = 7;        // energy: degree (in u = r^2) of the Taylor tail of the wide Gaussians
+constexpr int kTailF = 8;       // force: degree of its Taylor tail
 
-// FP32 pair kernel constants.  Gaussians with s_l >= 2.5 r_c vary little over
-// r <= r_c: their sum is a Taylor polynomial in u = r^2 (remainder below
-// 0.16^8 / 8! of w_l); the narrower ones are exponentials.  The energy path
-// keeps its coefficients as FP32 hi + lo pairs: a rounding shared by every
-// pair would otherwise be multiplied by sum q_i q_j / r, which is far larger
-// than the short-range energy itself.
+// FP32 pair kernel constants.  The wider Gaussians vary little over r <= r_c
+// and are summed as a Taylor polynomial in u = r^2: for the force, those with
+// s~_l >= 1.3 r_c (u / s~^2 <= 0.6; degree 8, within 1.8e-7 of their sum in
+// FP32, about one FP32 exponential's own error; measured), for the energy
+// those with s_l >= 2.5 r_c (remainder below 0.16^8 / 8! of w_l); the
+// narrower ones are exponentials.  The energy path keeps its coefficients
+// as FP32 hi + lo pairs: a rounding shared by every pair would otherwise be
+// multiplied by sum q_i q_j / r, which is far larger than the short-range
+// energy itself.
 struct PairConstsF {
     int M, ME;
     int nff, nfe;               // exponentials for the force (l < nff) and the energy (l < nfe)
@@ -33,7 +37,7 @@ struct PairConstsF {
     double rc2d;                // r_c^2 in FP64
     float beta[kMaxGauss];      // log2(e) / s~_l^2 (force)
     float wt[kMaxGauss];        // w~_l
-    float tt[kTail + 1];        // sum_{nff <= l < M} w~_l e^{-u / s~_l^2} = sum_k tt[k] u^k
+    float tt[kTailF + 1];       // sum_{nff <= l < M} w~_l e^{-u / s~_l^2} = sum_k tt[k] u^k
     float be_hi[kMaxGauss], be_lo[kMaxGauss];   // log2(e) / s_l^2 (energy)
     float w_hi[kMaxGauss], w_lo[kMaxGauss];     // w_l
     float te[kTail + 1];        // energy tail without its constant (te[0] = 0)

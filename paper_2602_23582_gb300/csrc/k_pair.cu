@@ -255,12 +255,14 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
             if (near) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
         }
         in = in && __float_as_int(pj.w) != moli;       // pairs of one molecule are excluded
-        float rinv = rsqrt_approx(in ? r2 : 1.f);
+        // (a pair that is not inside may give non-finite values here, e.g. two
+        // padding atoms at one place: its force is selected away below)
+        float rinv = rsqrt_approx(r2);
         rinv = rinv * fmaf(-0.5f * r2 * rinv, rinv, 1.5f);
         const float r2inv = rinv * rinv;
-        float st = pc.tt[kTail];
+        float st = pc.tt[kTailF];
 #pragma unroll
-        for (int k = kTail - 1; k >= 0; --k) st = fmaf(st, r2, pc.tt[k]);
+        for (int k = kTailF - 1; k >= 0; --k) st = fmaf(st, r2, pc.tt[k]);
         if (NF > 0) {
 #pragma unroll
             for (int l = 0; l < NF; ++l) st = fmaf(pc.wt[l], ex2f(-r2 * pc.beta[l]), st);
@@ -703,8 +705,9 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
     k_pair_cluster<NF, EN><<<blocks, 32 * kCpWarps, 0, st>>>(b.sys, b.item_sys, a.items, a.ccl, a.cbox,  \
                                                              a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, \
                                                              b.sub, b.N, b.item_cap, a.ffix, partial, cf)
-        if (cf.nff == 4) {
-            if (energy) RBSOG_PAIR_CLUSTER(4, true); else RBSOG_PAIR_CLUSTER(4, false);
+        // two narrow force Gaussians for Table 2 row 2 (any r_c): unrolled
+        if (cf.nff == 2) {
+            if (energy) RBSOG_PAIR_CLUSTER(2, true); else RBSOG_PAIR_CLUSTER(2, false);
         } else {
             if (energy) RBSOG_PAIR_CLUSTER(0, true); else RBSOG_PAIR_CLUSTER(0, false);
         }

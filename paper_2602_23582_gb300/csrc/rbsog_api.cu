@@ -952,10 +952,11 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             }
         }
         {
-            // FP32 split: Gaussians with s_l >= 2.5 r_c go into a Taylor tail in u = r^2
-            const double swide = 2.5 * P.rc, log2e = 1.4426950408889634;
+            // FP32 split: Taylor tails in u = r^2 for the force Gaussians with
+            // s~_l >= 1.3 r_c and the energy Gaussians with s_l >= 2.5 r_c
+            const double swide = 2.5 * P.rc, swide_f = 1.3 * P.rc, log2e = 1.4426950408889634;
             int nff = 0, nfe = 0;
-            while (nff < P.M && st[nff] < swide) ++nff;
+            while (nff < P.M && st[nff] < swide_f) ++nff;
             while (nfe < P.M_energy && s[nfe] < swide) ++nfe;
             c->pcf.nff = nff;
             c->pcf.nfe = nfe;
@@ -970,12 +971,16 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             }
             // sum_l w_l e^{-u/s_l^2} = sum_k u^k sum_l w_l (-1/s_l^2)^k / k!
             double te0 = 0.0;
-            for (int k = 0; k <= kTail; ++k) {
-                double tk = 0.0, ek = 0.0, fact = 1.0;
+            for (int k = 0; k <= kTailF; ++k) {
+                double tk = 0.0, fact = 1.0;
                 for (int i = 2; i <= k; ++i) fact *= i;
                 for (int l = nff; l < P.M; ++l) tk += wt[l] * std::pow(-1.0 / (st[l] * st[l]), k) / fact;
-                for (int l = nfe; l < P.M_energy; ++l) ek += w[l] * std::pow(-1.0 / (s[l] * s[l]), k) / fact;
                 c->pcf.tt[k] = (float)tk;
+            }
+            for (int k = 0; k <= kTail; ++k) {
+                double ek = 0.0, fact = 1.0;
+                for (int i = 2; i <= k; ++i) fact *= i;
+                for (int l = nfe; l < P.M_energy; ++l) ek += w[l] * std::pow(-1.0 / (s[l] * s[l]), k) / fact;
                 c->pcf.te[k] = k == 0 ? 0.f : (float)ek;
                 if (k == 0) te0 = ek;
             }
