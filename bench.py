@@ -413,6 +413,7 @@ def pair_roofline(half_pairs, pair_ms, prec, sm_clk, pair_trace=None, traffic=No
         peak = SM_COUNT * FP64_LANES * sm_clk / 1e12
         achieved = half_pairs * PAIR_FP64_PER_UNIT / (pair_ms * 1e-3) / 1e12
         rec.update(kernel="k_pair_f64", achieved=achieved, peak=peak, unit="Top/s (FP64 pipe)",
+                   limit="FP64 pipe: busy 83 % of the cycles in a full ncu capture (profiles/pair_kernel_f64_water.md)",
                    frac=achieved / peak, per_unit=f"{PAIR_FP64_PER_UNIT} FP64 operations per half-pair inside r_c",
                    peak_basis=f"{SM_COUNT} SMs x {FP64_LANES} FP64 lanes/clk x {sm_clk / 1e6:.0f} MHz (max clock); "
                               f"roofline time {half_pairs * PAIR_FP64_PER_UNIT / (peak * 1e12) * 1e6:.1f} us")
@@ -426,6 +427,9 @@ def pair_roofline(half_pairs, pair_ms, prec, sm_clk, pair_trace=None, traffic=No
     peak = fp32_peak if fp32_bound else mufu_peak
     achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
     rec.update(kernel="k_pair_cluster", achieved=achieved, peak=peak,
+               limit=("instruction issue: 11 warp instructions per pair inside r_c (78 operations of "
+                      "algorithmic work at 44 % tile fill, plus candidate tests, queue and fixed-point adds), "
+                      "issue slots 68 % busy at 36 % warp occupancy (profiles/pair_kernel_cluster_water.md)"),
                unit="Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)", frac=achieved / peak,
                per_unit=f"{PAIR_MUFU_PER_UNIT} MUFU + {PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c",
                peak_basis=f"{SM_COUNT} SMs x ({FP32_LANES} FP32 lanes, {MUFU_PER_SM_CLK} MUFU)/clk x "
@@ -516,6 +520,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-more", action="store_true", help="skip the sub-records of the other workloads")
     ap.add_argument("--no-scale", action="store_true", help="skip the 10^7-site scale point")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (no autotuner)")
     ap.add_argument("--P", type=int, default=100, help="Fourier modes per step (batch size)")
     ap.add_argument("--skin", type=float, default=None,
                     help="pair-list skin in A (FP32 build; default: the library's)")
@@ -567,6 +572,16 @@ def main():
         # configured size (Langevin NVT)
         p.coupling = R.RBSOG_COUPLE_FIXED
         desc = desc.replace("semi-isotropic", "box held fixed")
+    # launch shapes for this size class from the project's autotuner (cell size
+    # x cluster sub-columns; a few timed graph steps per candidate)
+    tuning = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        best, cands = R.rbsog_autotune(p, systems, nsteps=10, stream=stream.cuda_stream)
+        tuning = {"candidates": [{"cell_sub": a, "cluster_cols": b, "ms_per_step": t} for a, b, t in cands],
+                  "chosen": {"cell_sub": best.cell_sub, "cluster_cols": best.cluster_cols}, "search_s": time.perf_counter() - t0,
+                  "method": "rbsog_autotune: median of 10 graph steps per candidate after 3 warm-up steps"}
+        p = best
     ctx = R.Context(systems, p, stream=stream.cuda_stream)
     n_atoms = ctx.n_atoms
 
@@ -743,7 +758,7 @@ def main():
                        "ns_per_day": (p.dt * 1e-6) / (float(step_ms.mean()) / 1e3 / 86400.0),
                        "energies": f"every {args.thermo} steps (thermo output); forces and virial every step",
                        "energy_every_step": energy_every_step,
-                       "kernel_ms_eager_step": kernel_ms},
+                       "kernel_ms_eager_step": kernel_ms, "launch_shapes": tuning},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": kernels_per_step * args.steps, "clocks": clocks, "served": served,
             "more_workloads": more}

@@ -87,9 +87,11 @@ struct Batch {
 // kCpWarps warps per block, one pair record per warp.
 constexpr int kCpWarps = 4;
 constexpr int kF64Split = 4;    // FP64 pair kernel: warps per (work item, dz plane), each over every 4th cell
-// warps per work item of the pair kernels: the dz planes 0..sub of the half
-// stencil (FP64: x kF64Split cell quarters)
-inline int pair_parts(int precision, int sub) { return precision == 1 ? sub + 1 : (sub + 1) * kF64Split; }
+// warps per work item of the pair kernels: FP32, one (cells of r_c: the two
+// dz planes of the half stencil together, 14 cells) or sub + 1 (cells of
+// r_c / sub: one dz plane each); FP64, the sub + 1 planes x kF64Split cell
+// quarters
+__host__ __device__ inline int pair_parts(int precision, int sub) { return precision == 1 ? (sub == 1 ? 1 : sub + 1) : (sub + 1) * kF64Split; }
 // pair records per work item, as a fraction num / den (one per warp in both
 // builds; the fraction leaves room for records per block)
 inline int pair_rec_num(int precision, int sub) { return pair_parts(precision, sub); }

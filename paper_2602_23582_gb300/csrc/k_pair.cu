@@ -61,7 +61,9 @@ struct AccD {
 
 // Cutoff decision for a pair close to r_c, in FP64 from the original
 // positions with the minimum image, as the CPU reference decides it.
-__device__ __forceinline__ bool inside_cutoff_fp64(const double *__restrict__ r, int i, int j, const double L[3],
+// (out of line: the call sits in a branch taken a few times per launch, and an
+// inlined body costs the common path registers and instructions)
+__device__ __noinline__ bool inside_cutoff_fp64(const double *__restrict__ r, int i, int j, const double L[3],
                                                 double rc2)
 {
     double r2 = 0.0;
@@ -338,7 +340,7 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
     __shared__ int2 queue[kCpWarps][kQueue];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     const int kk = lane & 3, gbase = lane & ~3, grp = lane >> 2;
-    const int span = 2 * sub + 1, nparts = sub + 1;
+    const int span = 2 * sub + 1, nparts = pair_parts(1, sub);
     // units: item-major, kCpWarps per block; a system's item range is a
     // multiple of kCpWarps items, so a block never mixes systems
     const int unit = blockIdx.x * kCpWarps + warp;
@@ -391,26 +393,32 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
             tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, make_float4(0.f, 0.f, 0.f, 0.f), moli, qi, ai,
                                kClus * (grp == 0 ? it : item_cap), ifirst, kk, gbase, pos4, qt, ljrow, ljlorow,
                                sidx, r, d.L, acc, fjx, fjy, fjz);
-        // candidate cells of this plane, one per lane: the (dx, dy) pairs of
-        // the plane (plane 0: I's own cell -- its clusters after I -- then
-        // the upper half), their clusters numbered consecutively
-        const int ncand = part == 0 ? sub * (span + 1) + 1 : span * span;
+        // candidate cells, one per lane: plane 0 (I's own cell -- its clusters
+        // after I -- then the upper half), then with one unit per cluster
+        // (cells of r_c) the planes above
+        const int nc0 = sub * (span + 1) + 1;
+        const int ncand = nparts == 1 ? nc0 + span * span : (part == 0 ? nc0 : span * span);
         int cj = 0, cn = 0, cnb = 0;
         if (lane < ncand) {
-            int ddx, ddy;
-            if (part == 0) {
-                if (lane == 0) { ddx = 0; ddy = 0; }
-                else if (lane <= sub) { ddx = lane; ddy = 0; }
-                else { const int u = lane - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
+            int ddx, ddy, pz;
+            const int c0 = nparts == 1 ? lane : (part == 0 ? lane : nc0 + lane);
+            if (c0 < nc0) {
+                pz = 0;
+                if (c0 == 0) { ddx = 0; ddy = 0; }
+                else if (c0 <= sub) { ddx = c0; ddy = 0; }
+                else { const int u = c0 - sub - 1; ddx = u % span - sub; ddy = u / span + 1; }
             } else {
-                ddx = lane % span - sub; ddy = lane / span - sub;
+                const int u = c0 - nc0;
+                pz = nparts == 1 ? 1 + u / (span * span) : part;
+                const int v = u % (span * span);
+                ddx = v % span - sub; ddy = v / span - sub;
             }
-            const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + part, n2));
+            const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * wrapi(cz + pz, n2));
             const int2 cc = ccl[g];
             cj = cc.x;
             cn = cc.y;
-            if (part == 0 && lane == 0) { cj = it + 1; cn = cc.x + cc.y - (it + 1); }
-            cnb = (part + sub) * span * span + (ddy + sub) * span + (ddx + sub);
+            if (c0 == 0) { cj = it + 1; cn = cc.x + cc.y - (it + 1); }
+            cnb = (pz + sub) * span * span + (ddy + sub) * span + (ddx + sub);
         }
         int incl = cn;
 #pragma unroll
@@ -700,7 +708,7 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
 {
     if (precision == 1) {
         // (item, dz plane) units, kCpWarps per block (item_cap is a multiple of kCpWarps per system)
-        const int blocks = b.item_cap * (b.sub + 1) / kCpWarps;
+        const int blocks = b.item_cap * pair_parts(1, b.sub) / kCpWarps;
 #define RBSOG_PAIR_CLUSTER(NF, EN)                                                                          \
     k_pair_cluster<NF, EN><<<blocks, 32 * kCpWarps, 0, st>>>(b.sys, b.item_sys, a.items, a.ccl, a.cbox,  \
                                                              a.pos4, a.qt, a.ljf, a.ljf_lo, a.sidx, a.r, \
