@@ -105,6 +105,26 @@ def _declare(L):
     L.orc_npt_run.argtypes = [C.POINTER(_Params), C.POINTER(_System), C.POINTER(_Integ),
                               _D, _D, _D, _D, _D, _D, C.c_uint64, C.c_int, _D, _D]
     L.orc_num_threads.restype = C.c_int
+    L.orc_tri_q.argtypes = [_D, C.c_double, _I, C.c_int]
+    L.orc_tri_q.restype = C.c_double
+    L.orc_tri_create.argtypes = [_D, C.c_int, _D, _D]
+    L.orc_tri_create.restype = C.c_void_p
+    L.orc_tri_free.argtypes = [C.c_void_p]
+    L.orc_tri_free.restype = None
+    L.orc_tri_normalizers.argtypes = [C.c_void_p, _D, _D, _I]
+    L.orc_tri_normalizers.restype = None
+    L.orc_tri_targets.argtypes = [C.c_void_p, _I, _D]
+    L.orc_tri_targets.restype = None
+    L.orc_tri_sample_modes.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _I, _I, _D]
+    L.orc_tri_sample_modes.restype = None
+    L.orc_tri_draw_r.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, _I]
+    L.orc_tri_draw_r.restype = None
+    L.orc_rho_h.argtypes = [C.c_int, _D, _D, _D, C.c_int, _I, _D]
+    L.orc_rb_longrange_h.argtypes = L.orc_rb_longrange.argtypes
+    L.orc_force_eval_h.argtypes = [C.POINTER(_Params), C.POINTER(_System), _D, _D, C.c_void_p, C.c_uint64,
+                                   _D, _D, _D, _D, _I]
+    L.orc_nvt_run_h.argtypes = [C.POINTER(_Params), C.POINTER(_System), C.POINTER(_Integ), C.c_void_p,
+                                _D, _D, _D, _D, C.c_uint64, C.c_int, _D, _D]
 
 
 def _d(a):
@@ -460,3 +480,109 @@ def npt_run(sys, params: Params, integ: Integ, state: dict, step0: int, nsteps: 
     state["en"] = {k: en[i] for i, k in enumerate(EN_KEYS)}
     state["K"] = K.reshape(3, 3)
     return state
+
+
+# ---------------------------------------------------------------------------
+# a general (triclinic) cell h: upper triangular, cell vectors as columns
+# ---------------------------------------------------------------------------
+
+def tilted_box(L, tilt):
+    """h for edge lengths L = (Lx, Ly, Lz) and LAMMPS tilts (xy, xz, yz)."""
+    Lx, Ly, Lz = L
+    xy, xz, yz = tilt
+    return np.array([[Lx, xy, xz], [0.0, Ly, yz], [0.0, 0.0, Lz]])
+
+
+def tri_q(h, st0, m, nq=20):
+    """q(m*) of eq. proposal for a general h (nq Gauss-Legendre nodes per axis)."""
+    return lib().orc_tri_q(_pd(_d(h)), float(st0), _pi(_i(m)), int(nq))
+
+
+class TriCell:
+    """Sums of the sampler for one cell h and SOG split (orc_tri_create)."""
+
+    def __init__(self, h, params: Params):
+        w, s, wt, st = sog_terms(params.b, params.sigma, params.omega, params.M)
+        self.h = _d(h)
+        self.params = params
+        self.st = st
+        self._p = lib().orc_tri_create(_pd(self.h), params.M, _pd(wt), _pd(st))
+        if not self._p:
+            raise ValueError("h must be upper triangular with 1 <= M <= the oracle's maximum")
+
+    def __del__(self):
+        if getattr(self, "_p", None):
+            lib().orc_tri_free(self._p)
+            self._p = None
+
+    def normalizers(self):
+        M = self.params.M
+        Hr, Hnr, mm = np.zeros(M), np.zeros(M), np.zeros(3, np.int32)
+        lib().orc_tri_normalizers(self._p, _pd(Hr), _pd(Hnr), _pi(mm))
+        return Hr, Hnr, mm
+
+    def targets(self, m):
+        out = np.zeros(3)
+        lib().orc_tri_targets(self._p, _pi(_i(m)), _pd(out))
+        return out
+
+    def draw_r(self, step, index, sysid=None):
+        m = np.zeros(3, np.int32)
+        lib().orc_tri_draw_r(self._p, self.params.seed, self.params.sysid if sysid is None else sysid,
+                             step, index, _pi(m))
+        return m
+
+    def sample_modes(self, step, sysid=None):
+        P = self.params.P
+        mr, mnr, stats = np.zeros((P, 3), np.int32), np.zeros((P, 3), np.int32), np.zeros(2)
+        lib().orc_tri_sample_modes(self._p, P, self.params.seed,
+                                   self.params.sysid if sysid is None else sysid, step,
+                                   _pi(mr), _pi(mnr), _pd(stats))
+        return mr, mnr, stats
+
+
+def rho_h(pos, q, h, D):
+    pos, q, D = _d(pos), _d(q), _i(D)
+    out = np.zeros(2 * len(D))
+    lib().orc_rho_h(len(q), _pd(pos), _pd(q), _pd(_d(h)), len(D), _pi(D), _pd(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def rb_longrange_h(pos, q, h, P, D, cr, cnr, Sr, Snr, ke=KE):
+    """rb_longrange for a general h: (F, U^F*, W^{F,r*}, W^{F,nr*}, rho)."""
+    pos, q, D = _d(pos), _d(q), _i(D)
+    F, out, Wr, Wnr = np.zeros((len(q), 3)), np.zeros(1), np.zeros(9), np.zeros(9)
+    rho_ = np.zeros(2 * len(D))
+    lib().orc_rb_longrange_h(len(q), _pd(pos), _pd(q), _pd(_d(h)), P, len(D), _pi(D), _pi(_i(cr)),
+                             _pi(_i(cnr)), Sr, Snr, ke, _pd(F), _pd(out), _pd(Wr), _pd(Wnr), _pd(rho_))
+    return F, out[0], Wr.reshape(3, 3), Wnr.reshape(3, 3), rho_[0::2] + 1j * rho_[1::2]
+
+
+def force_eval_h(sys, params: Params, step, cell: TriCell, pos=None):
+    """force_eval for the general cell of `cell` (the paper's sampler)."""
+    pos = _d(sys.pos if pos is None else pos)
+    hold = _SysHold(sys)
+    pc = params.c()
+    F, en, W, Wp = np.zeros((sys.n, 3)), np.zeros(9), np.zeros(9), np.zeros(45)
+    modes = np.zeros(6 * params.P, np.int32)
+    lib().orc_force_eval_h(C.byref(pc), C.byref(hold.c), _pd(pos), _pd(cell.h), cell._p, step, _pd(F),
+                           _pd(en), _pd(W), _pd(Wp), _pi(modes))
+    V = float(abs(np.linalg.det(cell.h)))
+    out = {k: en[i] for i, k in enumerate(EN_KEYS)}
+    out.update(F=F, W=W.reshape(3, 3), W_parts=Wp.reshape(5, 3, 3),
+               P=W.reshape(3, 3) / V * NKTV2P,
+               mr=modes[:3 * params.P].reshape(-1, 3), mnr=modes[3 * params.P:].reshape(-1, 3))
+    return out
+
+
+def nvt_run_h(sys, params: Params, integ: "Integ", cell: TriCell, state: dict, step0: int, nsteps: int):
+    """Langevin steps step0+1 .. step0+nsteps in the fixed cell of `cell`.
+    state: r, p, F, W (updated in place); returns (energies, K)."""
+    hold = _SysHold(sys)
+    pc, ic = params.c(), integ.c()
+    en, K = np.zeros(9), np.zeros(9)
+    for k in ("r", "p", "F", "W"):
+        state[k] = np.ascontiguousarray(state[k], dtype=np.float64)
+    lib().orc_nvt_run_h(C.byref(pc), C.byref(hold.c), C.byref(ic), cell._p, _pd(state["r"]), _pd(state["p"]),
+                        _pd(state["F"]), _pd(state["W"]), step0, nsteps, _pd(en), _pd(K))
+    return {k: en[i] for i, k in enumerate(EN_KEYS)}, K.reshape(3, 3)

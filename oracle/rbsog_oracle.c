@@ -32,6 +32,11 @@
  *   orc_bonded           harmonic bonds and angles
  *   orc_force_eval       Algorithm 1 steps 2-7 for one configuration
  *   orc_npt_run          Algorithm 1 step 8 with eq. Langevin_NPT
+ *   orc_tri_*, orc_rho_h, orc_rb_longrange_h, orc_force_eval_h, orc_nvt_run_h
+ *                        the same steps for a general (triclinic) cell h:
+ *                        k = 2 pi h^{-T} m (eq. Sr), eq. proposal as a
+ *                        Gaussian integral over the cube around m*, lattice
+ *                        sums over Z^3 (eqs. Sr, Snr)
  *
  * Conventions shared with the inputs (not with the CUDA code): LAMMPS "real"
  * units; h is row-major with the cell vectors as its columns (r = h s);
@@ -1423,4 +1428,477 @@ int orc_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* a general (triclinic) cell h                                              */
+/* ------------------------------------------------------------------------ */
+/*
+ * h is upper triangular (the cell vectors a = (h00, 0, 0), b = (h01, h11, 0),
+ * c = (h02, h12, h22) are its columns, the LAMMPS convention; any cell can be
+ * rotated into this form).  The reciprocal vectors of eq. Sr are
+ * k = 2 pi h^{-T} m, i.e. h^T k = 2 pi m, solved by forward substitution.
+ *
+ * Sampling (App. D with a general h):
+ *   - proposal m* = round(h^T u), u_a ~ N(0, sigma_u^2), sigma_u^2 = 1/(2 pi^2 s~0^2);
+ *   - its mass q(m*) (eq. proposal) is the probability that h^T u lies in the
+ *     unit cube around m*.  With h^T lower triangular, (h^T u)_0 depends on
+ *     u_0 only, (h^T u)_1 on u_0, u_1: the cube condition is an interval for
+ *     u_0, an interval for u_1 given u_0 and one for u_2 given (u_0, u_1).  The
+ *     u_2 integral is an erf difference; the (u_0, u_1) integral is taken by
+ *     Gauss-Legendre quadrature with nq nodes per axis (nq = 20: converged to
+ *     about 1e-15 relative for the boxes used, pinned in the tests);
+ *   - the radial chain starts from an exact draw of P^r: component (l, a)
+ *     with weight c_l sum_m k_a^2 e_l(m) (c_l = pi^1.5 w~ s~^5, e_l = e^{-s~_l^2
+ *     k^2/4}; the weights over a add up to H^r_l), then m_0 from its marginal,
+ *     m_1 given m_0 and m_2 given (m_0, m_1), each by inverse CDF over
+ *     m = 0, 1, -1, 2, -2, ...  The sums run over |m_a| <= mm_a, the box that
+ *     holds the ellipsoid |k| <= 2 sqrt(46)/s~0 (terms beyond it are below
+ *     e^-46 of the largest).  For a diagonal h each step reduces to the
+ *     orthorhombic draw (orc_sample_modes), which a test checks;
+ *   - acceptance tests and the recalibration chain are those of
+ *     orc_sample_modes with the general k.
+ * Only the paper's construction (kind 0) is provided for a general h.
+ */
+
+static void kvec_h(const double *h, const int *m, double *k)
+{
+    k[0] = (2.0 * ORC_PI * (double)m[0]) / h[0];
+    k[1] = (2.0 * ORC_PI * (double)m[1] - h[1] * k[0]) / h[4];
+    k[2] = (2.0 * ORC_PI * (double)m[2] - h[2] * k[0] - h[5] * k[1]) / h[8];
+}
+
+/* Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on P_n from
+ * the Chebyshev-like first guess cos(pi (i + 3/4) / (n + 1/2)). */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = cos(ORC_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* P(lo <= u <= hi) for u ~ N(0, sig^2), without cancellation in the tails */
+static double normal_interval(double lo, double hi, double sig)
+{
+    double x = lo / (sqrt(2.0) * sig), y = hi / (sqrt(2.0) * sig);
+    if (x >= 0.0) return 0.5 * (erfc(x) - erfc(y));
+    if (y <= 0.0) return 0.5 * (erfc(-y) - erfc(-x));
+    return 0.5 * (erf(y) - erf(x));
+}
+
+/* eq. proposal for a general (upper-triangular) h: see the section comment. */
+double orc_tri_q(const double *h, double st0, const int *m, int nq)
+{
+    double x[64], wq[64];
+    if (nq < 1) nq = 1;
+    if (nq > 64) nq = 64;
+    gauss_legendre(nq, x, wq);
+    const double sig = 1.0 / (sqrt(2.0) * ORC_PI * st0);
+    const double nrm = 1.0 / (sqrt(2.0 * ORC_PI) * sig);
+    const double A0 = ((double)m[0] - 0.5) / h[0], B0 = ((double)m[0] + 0.5) / h[0];
+    double tot = 0.0;
+    for (int i = 0; i < nq; ++i) {
+        double u0 = 0.5 * (A0 + B0) + 0.5 * (B0 - A0) * x[i];
+        double A1 = ((double)m[1] - 0.5 - h[1] * u0) / h[4], B1 = ((double)m[1] + 0.5 - h[1] * u0) / h[4];
+        double inner = 0.0;
+        for (int j = 0; j < nq; ++j) {
+            double u1 = 0.5 * (A1 + B1) + 0.5 * (B1 - A1) * x[j];
+            double c = h[2] * u0 + h[5] * u1;
+            double pz = normal_interval(((double)m[2] - 0.5 - c) / h[8], ((double)m[2] + 0.5 - c) / h[8], sig);
+            inner += wq[j] * nrm * exp(-u1 * u1 / (2.0 * sig * sig)) * pz;
+        }
+        tot += wq[i] * nrm * exp(-u0 * u0 / (2.0 * sig * sig)) * 0.5 * (B1 - A1) * inner;
+    }
+    return tot * 0.5 * (B0 - A0);
+}
+
+typedef struct {
+    double h[9];
+    int M, mm[3], nx, ny, nz;
+    double wt[ORC_MAXM], st[ORC_MAXM], cr[ORC_MAXM], cn[ORC_MAXM], st2q[ORC_MAXM];
+    double Hr[ORC_MAXM], Hnr[ORC_MAXM];
+    double S[ORC_MAXM][3];     /* sum_m k_a^2 e_l(m) */
+    double *Gx;                /* [M][3][nx]: sum over (m_1, m_2) of k_a^2 e_l */
+    double *Gy;                /* [M][3][nx][ny]: sum over m_2 of k_a^2 e_l */
+} tri_ctx;
+
+static int walk_index(int k) { return (k == 0) ? 0 : ((k & 1) ? (k + 1) / 2 : -(k / 2)); }
+
+/* Set up the sums of a cell h (upper triangular) and SOG split (w~, s~). */
+tri_ctx *orc_tri_create(const double *h, int M, const double *wt, const double *st)
+{
+    if (M < 1 || M > ORC_MAXM || h[3] != 0.0 || h[6] != 0.0 || h[7] != 0.0) return NULL;
+    tri_ctx *c = (tri_ctx *)calloc(1, sizeof(tri_ctx));
+    memcpy(c->h, h, 9 * sizeof(double));
+    c->M = M;
+    const double pi15 = pow(ORC_PI, 1.5);
+    for (int l = 0; l < M; ++l) {
+        double s5 = st[l] * st[l] * st[l] * st[l] * st[l];
+        c->wt[l] = wt[l]; c->st[l] = st[l];
+        c->cr[l] = pi15 * wt[l] * s5;
+        c->cn[l] = pi15 * wt[l] * s5 * st[l] * st[l];
+        c->st2q[l] = st[l] * st[l] * 0.25;
+    }
+    /* |m_a| <= R |column a of h| holds the ellipsoid |h^{-T} m| <= R */
+    const double R = 2.0 * sqrt(46.0) / st[0] / (2.0 * ORC_PI);
+    const double len[3] = {fabs(h[0]), sqrt(h[1] * h[1] + h[4] * h[4]),
+                           sqrt(h[2] * h[2] + h[5] * h[5] + h[8] * h[8])};
+    for (int a = 0; a < 3; ++a) c->mm[a] = (int)ceil(R * len[a]) + 2;
+    c->nx = 2 * c->mm[0] + 1; c->ny = 2 * c->mm[1] + 1; c->nz = 2 * c->mm[2] + 1;
+    c->Gx = (double *)calloc((size_t)M * 3 * c->nx, sizeof(double));
+    c->Gy = (double *)calloc((size_t)M * 3 * c->nx * c->ny, sizeof(double));
+    for (int l = 0; l < M; ++l) {
+        double s4 = 0.0;
+        for (int i = 0; i < c->nx; ++i) {
+            double gx[3] = {0, 0, 0};
+            for (int j = 0; j < c->ny; ++j) {
+                double g[3] = {0, 0, 0};
+                for (int kz = 0; kz < c->nz; ++kz) {
+                    int m[3] = {i - c->mm[0], j - c->mm[1], kz - c->mm[2]};
+                    double k[3];
+                    kvec_h(h, m, k);
+                    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                    double e = exp(-(c->st2q[l] * k2));
+                    for (int a = 0; a < 3; ++a) g[a] += k[a] * k[a] * e;
+                    s4 += (k2 * k2) * e;
+                }
+                for (int a = 0; a < 3; ++a) {
+                    c->Gy[(((size_t)l * 3 + a) * c->nx + i) * c->ny + j] = g[a];
+                    gx[a] += g[a];
+                }
+            }
+            for (int a = 0; a < 3; ++a) c->Gx[((size_t)l * 3 + a) * c->nx + i] = gx[a];
+        }
+        for (int a = 0; a < 3; ++a) {
+            double sa = 0.0;
+            for (int i = 0; i < c->nx; ++i) sa += c->Gx[((size_t)l * 3 + a) * c->nx + i];
+            c->S[l][a] = sa;
+        }
+        c->Hr[l] = c->cr[l] * (c->S[l][0] + c->S[l][1] + c->S[l][2]);
+        c->Hnr[l] = c->cn[l] * s4;
+    }
+    return c;
+}
+
+void orc_tri_free(tri_ctx *c)
+{
+    if (!c) return;
+    free(c->Gx);
+    free(c->Gy);
+    free(c);
+}
+
+void orc_tri_normalizers(const tri_ctx *c, double *Hr, double *Hnr, int *mm)
+{
+    for (int l = 0; l < c->M; ++l) { Hr[l] = c->Hr[l]; Hnr[l] = c->Hnr[l]; }
+    if (mm) for (int a = 0; a < 3; ++a) mm[a] = c->mm[a];
+}
+
+static void tri_targets(const tri_ctx *c, const int *m, double *pr, double *pnr)
+{
+    double k[3];
+    kvec_h(c->h, m, k);
+    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    double a = 0, b = 0;
+    for (int l = 0; l < c->M; ++l) {
+        double e = exp(-(c->st2q[l] * k2));
+        a += c->cr[l] * e;
+        b += c->cn[l] * e;
+    }
+    *pr = k2 * a;
+    *pnr = (k2 * k2) * b;
+}
+
+#define ORC_TRI_NQ 20
+
+/* inverse CDF over m = 0, 1, -1, ... of a table indexed by m + mm */
+static int walk_table(double target, const double *tab, int mm)
+{
+    double cum = 0.0;
+    int last = 0;
+    for (int k = 0; k <= 2 * mm; ++k) {
+        int m = walk_index(k);
+        cum += tab[m + mm];
+        last = m;
+        if (cum > target) return m;
+    }
+    return last;
+}
+
+static void tri_exact_draw_r(const tri_ctx *c, const uint64_t wds[4], int *m)
+{
+    double tot = 0;
+    for (int l = 0; l < c->M; ++l) tot += c->Hr[l];
+    double target = orc_u01(wds[0]) * tot, cum = 0;
+    int lsel = c->M - 1, asel = 2, done = 0;
+    for (int l = 0; l < c->M && !done; ++l)
+        for (int a = 0; a < 3; ++a) {
+            cum += c->cr[l] * c->S[l][a];
+            if (cum > target) { lsel = l; asel = a; done = 1; break; }
+        }
+    const double *gx = c->Gx + ((size_t)lsel * 3 + asel) * c->nx;
+    double tx = 0.0;
+    for (int i = 0; i < c->nx; ++i) tx += gx[i];
+    m[0] = walk_table(orc_u01(wds[1]) * tx, gx, c->mm[0]);
+    const double *gy = c->Gy + (((size_t)lsel * 3 + asel) * c->nx + (m[0] + c->mm[0])) * c->ny;
+    double ty = 0.0;
+    for (int j = 0; j < c->ny; ++j) ty += gy[j];
+    m[1] = walk_table(orc_u01(wds[2]) * ty, gy, c->mm[1]);
+    /* m_2 given (m_0, m_1): weights k_a^2 e_l formed in walk order */
+    double tz = 0.0;
+    for (int kz = 0; kz < c->nz; ++kz) {
+        int mm3[3] = {m[0], m[1], kz - c->mm[2]};
+        double k[3];
+        kvec_h(c->h, mm3, k);
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        tz += k[asel] * k[asel] * exp(-(c->st2q[lsel] * k2));
+    }
+    double target2 = orc_u01(wds[3]) * tz, cz = 0.0;
+    int last = 0;
+    m[2] = 0;
+    for (int k = 0; k <= 2 * c->mm[2]; ++k) {
+        int mm3[3] = {m[0], m[1], walk_index(k)};
+        double kk[3];
+        kvec_h(c->h, mm3, kk);
+        double k2 = kk[0] * kk[0] + kk[1] * kk[1] + kk[2] * kk[2];
+        cz += kk[asel] * kk[asel] * exp(-(c->st2q[lsel] * k2));
+        last = mm3[2];
+        if (cz > target2) break;
+    }
+    m[2] = last;
+}
+
+/* one exact draw from P^r (the chain's start state at index 0), for tests */
+void orc_tri_draw_r(const tri_ctx *c, uint64_t seed, uint64_t sysid, uint64_t step, uint64_t index, int *m)
+{
+    uint64_t wds[4];
+    draw4(seed, sysid, step, PUR_START, index, wds);
+    tri_exact_draw_r(c, wds, m);
+}
+
+/* pr, pnr (unnormalised targets) and q (eq. proposal) of one mode */
+void orc_tri_targets(const tri_ctx *c, const int *m, double *out)
+{
+    tri_targets(c, m, &out[0], &out[1]);
+    out[2] = orc_tri_q(c->h, c->st[0], m, ORC_TRI_NQ);
+}
+
+/* the paper's construction (kind 0 of orc_sample_modes) for a general h */
+void orc_tri_sample_modes(const tri_ctx *c, int P, uint64_t seed, uint64_t sysid, uint64_t step,
+                          int *mr, int *mnr, double *stats)
+{
+    const double *h = c->h;
+    const double sig_u = 1.0 / (sqrt(2.0) * ORC_PI * c->st[0]);
+    uint64_t wds[4];
+    int x[3];
+    double pr, pnr;
+    stats[0] = stats[1] = 0;
+    draw4(seed, sysid, step, PUR_START, 0, wds);
+    tri_exact_draw_r(c, wds, x);
+    tri_targets(c, x, &pr, &pnr);
+    double wcur = pr / orc_tri_q(h, c->st[0], x, ORC_TRI_NQ);
+    for (int t = 1; t <= P; ++t) {
+        double z[3], zz;
+        draw4(seed, sysid, step, PUR_PROPOSAL, (uint64_t)(t - 1), wds);
+        box_muller(wds[0], wds[1], &z[0], &z[1]);
+        box_muller(wds[2], wds[3], &z[2], &zz);
+        /* gamma = h^T (sigma_u z) */
+        double g0 = h[0] * (z[0] * sig_u);
+        double g1 = h[4] * (z[1] * sig_u) + h[1] * (z[0] * sig_u);
+        double g2 = h[8] * (z[2] * sig_u) + (h[2] * (z[0] * sig_u) + h[5] * (z[1] * sig_u));
+        int ms[3] = {(int)floor(g0 + 0.5), (int)floor(g1 + 0.5), (int)floor(g2 + 0.5)};
+        double ws = 0.0;
+        if (ms[0] || ms[1] || ms[2]) {
+            tri_targets(c, ms, &pr, &pnr);
+            ws = pr / orc_tri_q(h, c->st[0], ms, ORC_TRI_NQ);
+        }
+        draw4(seed, sysid, step, PUR_ACCEPT, (uint64_t)(t - 1), wds);
+        if (orc_u01(wds[0]) * wcur < ws) {
+            x[0] = ms[0]; x[1] = ms[1]; x[2] = ms[2];
+            wcur = ws;
+            stats[0] += 1;
+        }
+        mr[3 * (t - 1)] = x[0]; mr[3 * (t - 1) + 1] = x[1]; mr[3 * (t - 1) + 2] = x[2];
+    }
+    int y[3] = {mr[0], mr[1], mr[2]};
+    tri_targets(c, y, &pr, &pnr);
+    double gcur = pnr / pr;
+    for (int t = 1; t <= P; ++t) {
+        const int *xt = mr + 3 * (t - 1);
+        tri_targets(c, xt, &pr, &pnr);
+        double gt = pnr / pr;
+        draw4(seed, sysid, step, PUR_ACCEPT, (uint64_t)(t - 1), wds);
+        if (orc_u01(wds[1]) * gcur < gt) {
+            y[0] = xt[0]; y[1] = xt[1]; y[2] = xt[2];
+            gcur = gt;
+            stats[1] += 1;
+        }
+        mnr[3 * (t - 1)] = y[0]; mnr[3 * (t - 1) + 1] = y[1]; mnr[3 * (t - 1) + 2] = y[2];
+    }
+}
+
+/* eq. rho_k with k = 2 pi h^{-T} m */
+void orc_rho_h(int N, const double *r, const double *q, const double *h, int nD, const int *D, double *rho)
+{
+#pragma omp parallel for schedule(static)
+    for (int d = 0; d < nD; ++d) {
+        double k[3];
+        kvec_h(h, D + 3 * d, k);
+        double re = 0, im = 0;
+        for (int j = 0; j < N; ++j) {
+            double th = k[0] * r[3 * j] + k[1] * r[3 * j + 1] + k[2] * r[3 * j + 2];
+            re += q[j] * cos(th);
+            im += q[j] * sin(th);
+        }
+        rho[2 * d] = re;
+        rho[2 * d + 1] = im;
+    }
+}
+
+/* orc_rb_longrange with k = 2 pi h^{-T} m and V = det h */
+void orc_rb_longrange_h(int N, const double *r, const double *q, const double *h,
+                        int P, int nD, const int *D, const int *cr, const int *cnr,
+                        double Sr, double Snr, double ke, double *F, double *out,
+                        double *Wr, double *Wnr, double *rho)
+{
+    const double V = fabs(det3(h));
+    orc_rho_h(N, r, q, h, nD, D, rho);
+    double Ar = 0, B[9] = {0};
+    for (int d = 0; d < nD; ++d) {
+        double k[3];
+        kvec_h(h, D + 3 * d, k);
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double r2 = rho[2 * d] * rho[2 * d] + rho[2 * d + 1] * rho[2 * d + 1];
+        Ar += cr[d] * r2 / k2;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) B[3 * a + b] += cnr[d] * r2 * k[a] * k[b] / (k2 * k2);
+    }
+    out[0] = ke * Sr / (4.0 * V * P) * Ar;
+    for (int a = 0; a < 9; ++a) {
+        Wr[a] = (a % 4 == 0) ? ke * Sr / (4.0 * V * P) * Ar : 0.0;
+        Wnr[a] = -ke * Snr / (8.0 * V * P) * B[a];
+    }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; ++i) {
+        double f[3] = {0, 0, 0};
+        for (int d = 0; d < nD; ++d) {
+            if (!cr[d]) continue;
+            double k[3];
+            kvec_h(h, D + 3 * d, k);
+            double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+            double th = k[0] * r[3 * i] + k[1] * r[3 * i + 1] + k[2] * r[3 * i + 2];
+            double g = rho[2 * d + 1] * cos(th) - rho[2 * d] * sin(th);
+            for (int a = 0; a < 3; ++a) f[a] += cr[d] * k[a] * g / k2;
+        }
+        double cc = -ke * (0.5 * Sr) / P * q[i] / V;
+        for (int a = 0; a < 3; ++a) F[3 * i + a] += cc * f[a];
+    }
+}
+
+/* orc_force_eval for a general (upper-triangular) cell h, the paper's
+ * sampler (kind 0) with the sums of tc (made for the same h and split);
+ * outputs as orc_force_eval. */
+void orc_force_eval_h(const orc_params *pp, const orc_system *sy, const double *r, const double *h,
+                      const tri_ctx *tc, uint64_t step, double *F, double *en, double *W,
+                      double *Wparts, int *modes_out)
+{
+    int N = sy->N, M = pp->M, ME = pp->ME, P = pp->P;
+    int MM = M > ME ? M : ME;
+    double *w = (double *)malloc(sizeof(double) * 4 * MM);
+    double *s = w + MM, *wt = w + 2 * MM, *st = w + 3 * MM;
+    orc_sog_terms(pp->b, pp->sigma, pp->omega, MM, w, s, wt, st);
+    memset(F, 0, sizeof(double) * 3 * N);
+    double esr[2], Wc[9], Wl[9];
+    orc_short_range(N, r, sy->q, sy->type, sy->mol, h, pp->rc, M, wt, st, ME, w, s,
+                    sy->ntypes, sy->lj_eps, sy->lj_sig, pp->ke, F, esr, Wc, Wl);
+    int *mr = (int *)malloc(sizeof(int) * 6 * P);
+    int *mnr = mr + 3 * P;
+    double stats[2];
+    orc_tri_sample_modes(tc, P, pp->seed, pp->sysid, step, mr, mnr, stats);
+    if (modes_out) memcpy(modes_out, mr, sizeof(int) * 6 * P);
+    int *D = (int *)malloc(sizeof(int) * 3 * 2 * P);
+    int *cr = (int *)malloc(sizeof(int) * 2 * P), *cnr = (int *)malloc(sizeof(int) * 2 * P);
+    int nD = orc_distinct(P, mr, P, mnr, D, cr, cnr);
+    double Sr = 0, Snr = 0;
+    for (int l = 0; l < M; ++l) { Sr += tc->Hr[l]; Snr += tc->Hnr[l]; }
+    double *rho = (double *)malloc(sizeof(double) * 2 * nD);
+    double uf, Wr[9], Wnr[9];
+    orc_rb_longrange_h(N, r, sy->q, h, P, nD, D, cr, cnr, Sr, Snr, pp->ke, F, &uf, Wr, Wnr, rho);
+    double ux, Wx[9], eb[2], Wb[9];
+    orc_exclusions(sy->ne, sy->excl, r, sy->q, h, M, wt, st, ME, w, s, pp->ke, F, &ux, Wx);
+    orc_bonded(sy->nb, sy->bonds, sy->bk, sy->br0, sy->na, sy->angles, sy->ak, sy->at0, r, h, F, eb, Wb);
+    double us = orc_self_energy(pp->b, pp->sigma, pp->omega, ME, N, sy->q, pp->ke);
+    en[0] = esr[0]; en[1] = uf; en[2] = us; en[3] = ux; en[4] = esr[1]; en[5] = eb[0]; en[6] = eb[1];
+    en[7] = esr[0] + uf - us + ux;
+    en[8] = nD;
+    for (int a = 0; a < 9; ++a) {
+        W[a] = Wc[a] + Wr[a] + Wnr[a] + Wl[a] + Wx[a] + Wb[a];
+        if (Wparts) {
+            Wparts[a] = Wc[a]; Wparts[9 + a] = Wr[a]; Wparts[18 + a] = Wnr[a];
+            Wparts[27 + a] = Wl[a]; Wparts[36 + a] = Wx[a] + Wb[a];
+        }
+    }
+    free(rho); free(D); free(cr); free(cnr); free(mr); free(w);
+}
+
+/* Algorithm 1 step 8 with the cell held fixed (Langevin NVT in a general
+ * cell): the BAOAB splitting of orc_npt_run without the box terms; atoms are
+ * wrapped into the cell by whole cell vectors, r <- r - h floor(h^{-1} r). */
+void orc_nvt_run_h(const orc_params *pp, const orc_system *sy, const orc_integ *ig, const tri_ctx *tc,
+                   double *r, double *p, double *F, double *W, uint64_t step0, int nsteps,
+                   double *en_out, double *K_out)
+{
+    int N = sy->N;
+    const double *h = tc->h;
+    double hi[9], mvv2e = 1.0 / ig->ftm2v, K[9];
+    inv3(h, hi);
+    double c = exp(-ig->gamma * ig->dt);
+    for (int n = 1; n <= nsteps; ++n) {
+        uint64_t step = step0 + (uint64_t)n;
+        for (int i = 0; i < 3 * N; ++i) p[i] += 0.5 * ig->dt * F[i] * ig->ftm2v;
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < 3; ++a) r[3 * i + a] = r[3 * i + a] + p[3 * i + a] / sy->mass[i] * (0.5 * ig->dt);
+        uint64_t wds[4];
+        for (int i = 0; i < N; ++i) {
+            double z[4];
+            draw4(pp->seed, pp->sysid, step, PUR_ATOM, (uint64_t)i, wds);
+            box_muller(wds[0], wds[1], &z[0], &z[1]);
+            box_muller(wds[2], wds[3], &z[2], &z[3]);
+            double sdv = sqrt((1.0 - c * c) * sy->mass[i] * ig->kB * ig->T * ig->ftm2v);
+            for (int a = 0; a < 3; ++a) p[3 * i + a] = c * p[3 * i + a] + sdv * z[a];
+        }
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < 3; ++a) r[3 * i + a] = r[3 * i + a] + p[3 * i + a] / sy->mass[i] * (0.5 * ig->dt);
+        for (int i = 0; i < N; ++i) {
+            double *x = r + 3 * i, f[3];
+            for (int a = 0; a < 3; ++a) f[a] = floor(hi[3 * a] * x[0] + hi[3 * a + 1] * x[1] + hi[3 * a + 2] * x[2]);
+            for (int a = 0; a < 3; ++a) x[a] -= h[3 * a] * f[0] + h[3 * a + 1] * f[1] + h[3 * a + 2] * f[2];
+        }
+        orc_force_eval_h(pp, sy, r, h, tc, step, F, en_out, W, NULL, NULL);
+        for (int i = 0; i < 3 * N; ++i) p[i] += 0.5 * ig->dt * F[i] * ig->ftm2v;
+    }
+    kinetic(N, p, sy->mass, mvv2e, K);
+    for (int a = 0; a < 9; ++a) K_out[a] = K[a];
 }

@@ -58,6 +58,7 @@ class System:
     angle_t0: np.ndarray     # (na,) float64
     excl: np.ndarray         # (ne, 2) int32
     coupling: int = 0        # 0 isotropic, 1 semi-isotropic (x=y coupled, z free)
+    tilt: tuple = (0.0, 0.0, 0.0)   # (xy, xz, yz): h = [[Lx, xy, xz], [0, Ly, yz], [0, 0, Lz]]
 
     @property
     def n(self) -> int:
@@ -554,6 +555,29 @@ def nacl_crystal(cells: int = 4, a: float = 5.64) -> System:
     L = cells * a
     return _finish("nacl", pos, q, np.where(typ == 0, 22.99, 35.45), typ,
                    np.arange(n, dtype=np.int32), [L, L, L], [0.0, 0.0], [1.0, 1.0])
+
+
+def sheared(sys: System, tilt) -> System:
+    """The same system in a triclinic cell: edge lengths kept, tilts (xy, xz,
+    yz) added.  Each molecule moves rigidly so that its first atom keeps its
+    fractional coordinates (s = r / L of the orthorhombic box, r' = h s), then
+    every atom is wrapped into the cell by whole cell vectors; intramolecular
+    geometry is unchanged."""
+    L = np.asarray(sys.box, dtype=np.float64)
+    xy, xz, yz = (float(t) for t in tilt)
+    h = np.array([[L[0], xy, xz], [0.0, L[1], yz], [0.0, 0.0, L[2]]])
+    pos = np.array(sys.pos, dtype=np.float64)
+    change = np.flatnonzero(np.diff(sys.mol)) + 1
+    starts = np.concatenate([[0], change]).astype(np.int64)
+    ends = np.concatenate([change, [sys.n]]).astype(np.int64)
+    for a, b in zip(starts, ends):
+        d = pos[a:b] - pos[a]
+        d -= L * np.rint(d / L)                  # the molecule whole (minimum image in the old box)
+        pos[a:b] = h @ (pos[a] / L) + d
+    sfrac = np.linalg.solve(h, pos.T).T
+    pos -= np.floor(sfrac) @ h.T
+    out = dataclasses.replace(sys, pos=pos, tilt=(xy, xz, yz), coupling=2)
+    return out
 
 
 def random_charges(n: int = 64, box=(20.0, 20.0, 20.0), seed: int = 0,
