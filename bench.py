@@ -64,6 +64,10 @@ def workload(name: str, rank: int = 0):
     if name == "membrane":
         s = W.membrane()
         return [s], "membrane-like slab 64x64x96 A, 120,000 sites, semi-isotropic, rc=10 A, P=100"
+    if name == "water_sheared":
+        s = W.sheared(W.water(), (6.688, -4.0, 5.0))
+        return [s], ("water-like box of 30,000 sites in a triclinic cell (edges 66.88 A, tilts xy=6.688, "
+                     "xz=-4.0, yz=5.0 A), rc=10 A, P=100, Langevin with the cell held fixed")
     if name == "big_water":
         s = W.big_water()
         return [s], "water-like box, 10,000,002 sites (3,333,334 molecules, no two molecules' sites within 0.8 A), L=463.7 A, rc=10 A, P=100"
@@ -699,8 +703,9 @@ def main():
                          pair_traffic(args.workload, prec))
     # ---- more workloads (sub-records; rank 0 of a single-GPU run): the plain
     # FP64 path on the 1000-ion electrolyte and the water box, the
-    # ionic-liquid-like mix at P = 100 and 400, the membrane-like slab in
-    # semi-isotropic NPT, and the 10^7-site water box at P = 100 and 1000
+    # ionic-liquid-like mix at P = 100 and 400, the membrane-like slab, the
+    # water box in a triclinic cell (FP32 and FP64), and the 10^7-site water
+    # box at P = 100 and 1000
     more = {}
     if rank == 0 and world == 1 and not args.no_more:
         plan = [("fp64_electrolyte", "electrolyte", R.RBSOG_FP64, 100, 100, dict()),
@@ -711,7 +716,12 @@ def main():
                 # it expands without bound under NPT (semi-isotropic: 64 -> 144 A
                 # in x and y within 110 steps), so its box is held fixed here
                 ("membrane_fixed_box", "membrane", R.RBSOG_FP32, 100, 100,
-                 dict(relaxed=True, coupling=R.RBSOG_COUPLE_FIXED))]
+                 dict(relaxed=True, coupling=R.RBSOG_COUPLE_FIXED)),
+                # a tilted cell is held fixed (its flexible-cell dynamics is not built)
+                ("triclinic_water", "water_sheared", R.RBSOG_FP32, 100, 100,
+                 dict(coupling=R.RBSOG_COUPLE_FIXED)),
+                ("triclinic_water_fp64", "water_sheared", R.RBSOG_FP64, 100, 30,
+                 dict(coupling=R.RBSOG_COUPLE_FIXED))]
         for key, name, pr, P, ns, kw in plan:
             try:
                 more[key] = sub_record(R, stream, flush, sm_clk, name, pr, P=P, steps=ns, **kw)

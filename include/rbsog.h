@@ -26,8 +26,16 @@
  *     them.  The context owns every other device allocation.
  *   - Arrays of atoms are row-major N x 3 FP64 unless stated; atoms of all
  *     systems of a context are concatenated in system order.
- *   - The cell h is orthorhombic: box[3] are its edge lengths.  A box edge
- *     shorter than (2 cell_sub + 1) r_c / cell_sub is rejected (RBSOG_EBOX).
+ *   - The cell h is upper triangular, h = [[Lx, xy, xz], [0, Ly, yz], [0, 0, Lz]]
+ *     (cell vectors as columns): box[3] are its edge lengths (Lx, Ly, Lz) and
+ *     tilt[3] = (xy, xz, yz) its tilts, zero for an orthorhombic box.  A box
+ *     whose perpendicular width along an axis (the edge itself when
+ *     orthorhombic) is below (2 cell_sub + 1) r_c / cell_sub is rejected
+ *     (RBSOG_EBOX).  A tilted (triclinic) cell is held fixed: it needs
+ *     coupling RBSOG_COUPLE_FIXED, skin 0 and the paper sampler, in a context
+ *     made by rbsog_create (RBSOG_EUNSUPPORTED otherwise); the Fourier modes
+ *     are k = 2 pi h^{-T} m (eq. Sr) and the proposal of App. D is
+ *     m* = round(h^T u) with the mass of eq. proposal.
  *   - Results depend only on (inputs, seed, rng_id, step): Philox4x64-10
  *     counters (step, purpose, index) under the key (seed, rng_id).
  */
@@ -148,6 +156,8 @@ typedef struct {
     double box[3];          /* edge lengths, A */
     uint64_t rng_id;        /* second word of this system's Philox key (seed, rng_id):
                                results do not depend on the system's place in a batch */
+    double tilt[3];         /* (xy, xz, yz), A: tilts of a triclinic cell (all zero:
+                               orthorhombic); see the conventions above */
 } rbsog_system_desc;
 
 /* Energies, kcal/mol: indices into rbsog_result.energy */
@@ -178,6 +188,7 @@ typedef struct {
     int n_accept_r, n_accept_nr;
     uint64_t step;
     int list_builds;         /* pair-list builds of this system so far (FP32 build) */
+    double tilt[3];          /* (xy, xz, yz) of the cell */
 } rbsog_result;
 
 typedef struct rbsog_ctx rbsog_ctx;
@@ -207,7 +218,7 @@ int rbsog_n_atoms(const rbsog_ctx *ctx);
 rbsog_status rbsog_system_range(const rbsog_ctx *ctx, int s, int *atom0, int *n);
 
 /* Replace the box of system s; rescale_positions != 0 scales its positions
- * affinely (r -> r L'/L). */
+ * affinely (r -> r L'/L).  A tilted cell is held fixed: RBSOG_EUNSUPPORTED. */
 rbsog_status rbsog_set_box(rbsog_ctx *ctx, int s, const double box[3], int rescale_positions);
 
 /* Copy positions (all systems, N_total x 3) in or out.  on_device: r is a

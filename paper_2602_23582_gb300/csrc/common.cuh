@@ -70,6 +70,11 @@ struct DevSys {
     double thr2;          // squared displacement bound of the current step (lists with a skin)
     unsigned long long rng_id;   // second word of the Philox key
     unsigned long long step;     // Philox counter of the system's last force evaluation
+    // triclinic cell (held fixed): h = [[L0, xy, xz], [0, L1, yz], [0, 0, L2]],
+    // cell vectors as columns; all zero for an orthorhombic box
+    double tilt[3];       // (xy, xz, yz)
+    double tw[3];         // tilt per cell: xy / ncell[1], xz / ncell[2], yz / ncell[2]
+    int tri;              // 1: some tilt is non-zero
 };
 
 // Atoms of a system that take part in the current step (0 for an empty or
@@ -181,6 +186,18 @@ __device__ inline void block_reduce_lanes(const double (&v)[V], double *smem, do
     for (int k = t; k < V; k += NT) out[k] = (s2[k * G] + s2[k * G + 1]) + (s2[k * G + 2] + s2[k * G + 3]);
 }
 
+// Perpendicular width of the cell of d along axis a (the distance between
+// the two faces the a-th cell vector joins): V / |b x c| etc.; L_a when the
+// cell is orthorhombic.
+__host__ __device__ inline double perp_width(const double L[3], const double t[3], int a)
+{
+    const double xy = t[0], xz = t[1], yz = t[2];
+    if (a == 2) return L[2];
+    if (a == 1) return L[1] * L[2] / sqrt(L[2] * L[2] + yz * yz);
+    const double b0 = L[1] * L[2], b1 = xy * L[2], b2 = xy * yz - L[1] * xz;
+    return L[0] * L[1] * L[2] / sqrt(b0 * b0 + b1 * b1 + b2 * b2);
+}
+
 // Cell grid of one axis for box edge L (cells of r_c / sub, at least
 // 2 sub + 1 and at most the slot's capacity ncap): sets *bad when the box is
 // too small, not finite or beyond the allocated grid.
@@ -194,6 +211,45 @@ __device__ __forceinline__ int axis_cells(double L, int sub, double rc, int ncap
     return n;
 }
 
+// Fractional coordinates s = h^{-1} x for the upper-triangular h of d, by back
+// substitution (for a zero tilt, s_a = x_a / L_a exactly, as each product
+// with a zero tilt adds an exact zero).
+__device__ __forceinline__ void frac_of(const DevSys &d, const double x[3], double s[3])
+{
+    s[2] = __ddiv_rn(x[2], d.L[2]);
+    s[1] = __ddiv_rn(__dsub_rn(x[1], __dmul_rn(d.tilt[2], s[2])), d.L[1]);
+    s[0] = __ddiv_rn(__dsub_rn(__dsub_rn(x[0], __dmul_rn(d.tilt[0], s[1])), __dmul_rn(d.tilt[1], s[2])), d.L[0]);
+}
+
+// x - h n for an integer vector n (a lattice translation of the cell of d)
+__device__ __forceinline__ void sub_lattice(const DevSys &d, const double n[3], double x[3])
+{
+    x[0] -= d.L[0] * n[0] + d.tilt[0] * n[1] + d.tilt[1] * n[2];
+    x[1] -= d.L[1] * n[1] + d.tilt[2] * n[2];
+    x[2] -= d.L[2] * n[2];
+}
+
+// Minimum image of a difference vector in the tilted cell of d: the image
+// whose fractional components lie in [-1/2, 1/2].  For two atoms within r_c
+// that is the image within r_c (every perpendicular width of the cell is
+// above 2 r_c, as the cell grid requires).
+__device__ __forceinline__ void min_image_tri(const DevSys &d, double x[3])
+{
+    double s[3], n[3];
+    frac_of(d, x, s);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) n[a] = rint(s[a]);
+    sub_lattice(d, n, x);
+}
+
+// k = 2 pi h^{-T} m for the cell of d (h^T k = 2 pi m, forward substitution)
+__device__ __forceinline__ void kvec_of(const DevSys &d, const int m[3], double k[3])
+{
+    k[0] = (kTwoPi * (double)m[0]) / d.L[0];
+    k[1] = (kTwoPi * (double)m[1] - d.tilt[0] * k[0]) / d.L[1];
+    k[2] = (kTwoPi * (double)m[2] - d.tilt[1] * k[0] - d.tilt[2] * k[1]) / d.L[2];
+}
+
 // Bin atom i of system d at position x (wrapped into [0, L)): its cell, its
 // rank there by a warp-aggregated atomic on count (act: the lanes of the warp
 // that bin an atom), cell-local coordinates and fixed-point fractional
@@ -205,10 +261,11 @@ __device__ __forceinline__ void bin_atom(const DevSys &d, int i, const double x[
 {
     int c[3];
     double sf[3], xl[3];
+    frac_of(d, x, sf);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double L = d.L[a];
-        double s = __ddiv_rn(x[a], L);
+        double s = sf[a];
         s = __dsub_rn(s, floor(s));
         if (s >= 1.0) s = 0.0;
         int n = d.ncell[a];
@@ -218,6 +275,11 @@ __device__ __forceinline__ void bin_atom(const DevSys &d, int i, const double x[
         c[a] = k;
         sf[a] = s;
         xl[a] = s * L - k * d.w[a];
+    }
+    if (d.tri) {
+        // cell-local Cartesian coordinates h (s - c / n): the tilt terms
+        xl[0] += (d.tilt[0] * sf[1] - c[1] * d.tw[0]) + (d.tilt[1] * sf[2] - c[2] * d.tw[1]);
+        xl[1] += d.tilt[2] * sf[2] - c[2] * d.tw[2];
     }
     const int gc = d.cell0 + c[0] + d.ncell[0] * (c[1] + d.ncell[1] * c[2]);
     cell[i] = gc;

@@ -164,20 +164,40 @@ void launch_pair(const Batch &b, const AtomArrays &a, int precision, const PairC
                  const PairConstsD &cd, int energy, double *partial, cudaStream_t st);
 
 // ---- k_sampler.cu
+constexpr int kGL = 20;         // Gauss-Legendre nodes per axis of the proposal mass of a tilted cell
 struct SamplerArgs {
     int P, M, kind;
     uint64_t seed;
     double wt[kMaxGauss], st[kMaxGauss];
     double cr[kMaxGauss], cn[kMaxGauss], st2q[kMaxGauss];
     double sig_u;
+    double glx[kGL], glw[kGL];  // Gauss-Legendre nodes and weights on [-1, 1]
+    double *tri_tab;            // lattice-sum tables of the tilted systems (SampScratch::tab0)
 };
 // per-system sampler scratch: 1D lattice sums T0, T2, T4 per Gaussian and
-// axis, and the chain's start state (paper MH sampler)
+// axis, and the chain's start state (paper MH sampler).  A tilted system
+// (DevSys::tri) has instead sums over Z^3, made once for its fixed cell:
+// tS[l][a] = sum_m k_a^2 e_l(m), the normalizer terms tHr, tHnr, and tables
+// at tri_tab + tab0: Gy[l][a][i][j] = sum over m_2 of k_a^2 e_l (m_0 = i -
+// tmm[0], m_1 = j - tmm[1]), then Gx[l][a][i] = sum over j of Gy, then
+// scratch G4[l][i][j] = sum over m_2 of k^4 e_l.
 struct SampScratch {
     double T[3][kMaxGauss][3];
     double start_w, start_g;
     int start_m[4];
+    double tS[kMaxGauss][3], tHr[kMaxGauss], tHnr[kMaxGauss];
+    long long tab0;
+    int tmm[4];
 };
+// doubles of the tables of one tilted system (see SampScratch)
+inline size_t tri_tab_size(int M, const int mm[3])
+{
+    const size_t nx = 2 * mm[0] + 1, ny = 2 * mm[1] + 1;
+    return (size_t)M * nx * ny * 4 + (size_t)M * 3 * nx;
+}
+// the sums of the tilted systems (once per cell: the cell is held fixed)
+void launch_tri_tables(const Batch &b, const SamplerArgs &sa, SampScratch *ss, const int *tri_sys, int ntri,
+                       const int *mm_max, cudaStream_t st);
 // adv = 1: the evaluation of an NPT step (counter DevSys::step + 1); 0: re-evaluate at DevSys::step
 void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int *mnr, int *D, int *cr,
                     int *cnr, int4 *pm, double *pw, double *pg, double *pu, double *pun, SampScratch *ss,

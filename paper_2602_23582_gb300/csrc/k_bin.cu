@@ -3,7 +3,9 @@
 // Binning convention (matches the oracle's definition bit for bit; no FMA in
 // the decision arithmetic): s = r / L, s -= floor(s), s = 0 if s >= 1;
 // n = floor(L * sub / r_c) cells per axis; cell = min(floor(s n), n - 1),
-// x fastest.  A warp-aggregated counting sort (match_any + one atomicAdd per
+// x fastest.  A tilted cell h: s = h^{-1} r (back substitution) and n from
+// the perpendicular widths instead of the edges; cell-local coordinates are
+// h (s - c / n), and the offset of neighbour cell c + d is h (d / n).  A warp-aggregated counting sort (match_any + one atomicAdd per
 // distinct cell in the warp) gives every atom a rank in its cell; an
 // exclusive scan gives the cell starts; atoms are scattered to their cell and
 // each cell's list is then sorted, so the cell-sorted order (and every sum
@@ -37,11 +39,17 @@ __global__ void k_box_prep(DevSys *sys, int S, int sub, double rc)
     for (int a = 0; a < 3; ++a) {
         // a box that is too small, not finite or beyond the allocated grid is
         // flagged; the grid stays within [2 sub + 1, ncap] so that every
-        // neighbour-cell index remains valid while the step is discarded
-        const int n = axis_cells(d.L[a], sub, rc, d.ncap[a], &bad);
+        // neighbour-cell index remains valid while the step is discarded.
+        // A tilted cell is cut along its perpendicular widths, so that the
+        // neighbour cells within sub steps hold every pair within r_c.
+        const double span = d.tri ? perp_width(d.L, d.tilt, a) : d.L[a];
+        const int n = axis_cells(span, sub, rc, d.ncap[a], &bad);
         d.ncell[a] = n;
         d.w[a] = d.L[a] / n;
     }
+    d.tw[0] = d.tilt[0] / d.ncell[1];
+    d.tw[1] = d.tilt[1] / d.ncell[2];
+    d.tw[2] = d.tilt[2] / d.ncell[2];
     if (bad) d.flags |= FLAG_BOX;
     d.V = d.L[0] * d.L[1] * d.L[2];
 }

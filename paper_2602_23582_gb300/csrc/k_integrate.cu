@@ -129,7 +129,7 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
         // so that the atom update can bin its atoms
         bool bad = false;
         int n = 0;
-        if (lane < 3) n = axis_cells(Ln, prep_sub, rlist, d.ncap[lane], &bad);
+        if (lane < 3) n = axis_cells(d.tri ? perp_width(d.L, d.tilt, lane) : Ln, prep_sub, rlist, d.ncap[lane], &bad);
         const bool anybad = __any_sync(0xffffffffu, bad);
         const bool regrid = __any_sync(0xffffffffu, lane < 3 && n != d.ncell[lane]);
         // lists with a skin stay valid while every displacement since the
@@ -142,6 +142,9 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
         if (lane < 3) {
             d.ncell[lane] = n;
             d.w[lane] = Ln / n;
+            // tilt per cell (a tilted cell is held fixed: Ln = L)
+            const int nn = __shfl_sync(0x7u, n, lane == 0 ? 1 : 2);
+            d.tw[lane] = d.tilt[lane] / nn;
         }
         const double L0 = __shfl_sync(0xffffffffu, Ln, 0), L1 = __shfl_sync(0xffffffffu, Ln, 1),
                      L2 = __shfl_sync(0xffffffffu, Ln, 2);
@@ -221,13 +224,22 @@ __global__ void k_atom_update(DevSys *__restrict__ sys, const int *__restrict__ 
     for (int a = 0; a < 3; ++a) {
         x[a] = d.sc2[a] * x[a] + v[a] * im * tau;
         v[a] = v[a] * d.isc2[a];
-        const double L = d.L[a];
-        x[a] -= L * floor(x[a] * d.invL[a]);
-        if (x[a] >= L) x[a] -= L;
-        if (x[a] < 0.0) x[a] += L;
-        r[3 * i + a] = x[a];
+        if (!d.tri) {
+            const double L = d.L[a];
+            x[a] -= L * floor(x[a] * d.invL[a]);
+            if (x[a] >= L) x[a] -= L;
+            if (x[a] < 0.0) x[a] += L;
+        }
         p[3 * i + a] = v[a];
     }
+    if (d.tri) {
+        // into the tilted cell by whole cell vectors: x - h floor(h^{-1} x)
+        double sf[3], n[3];
+        frac_of(d, x, sf);
+        for (int a = 0; a < 3; ++a) n[a] = floor(sf[a]);
+        sub_lattice(d, n, x);
+    }
+    for (int a = 0; a < 3; ++a) r[3 * i + a] = x[a];
     if (SKIN && !d.rebuild) {
         double d2 = 0.0;
         for (int a = 0; a < 3; ++a) {

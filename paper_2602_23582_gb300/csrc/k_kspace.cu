@@ -51,8 +51,10 @@ __device__ __forceinline__ void phase_sincos_d(const int m[3], double sx, double
 
 // rho partial sums of one chunk of atoms for a group of modes.
 // su: FP32 atom data (fixed-point s, q bits); r/q/L: FP64 atom data.
+// B: the edges L and, for a tilted cell, the tilts (xy, xz, yz) in B[3..5]
+// (null: orthorhombic); the FP64 phases use s = h^{-1} r.
 template <bool F32>
-__device__ void sk_chunk(const uint4 *su, const double *r, const double *q, const double L[3],
+__device__ void sk_chunk(const uint4 *su, const double *r, const double *q, const double L[3], const double *tilt,
                          int a0, int na, const int *D, int d0, int nd_here, double *out /* [nd_here][2] */)
 {
     __shared__ uint4 s_su[F32 ? kChunk : 1];
@@ -63,9 +65,17 @@ __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, cons
             s_su[k] = su[a0 + k];
         } else {
             const int i = a0 + k;
-            s_sd[k][0] = r[3 * i] / L[0];
-            s_sd[k][1] = r[3 * i + 1] / L[1];
-            s_sd[k][2] = r[3 * i + 2] / L[2];
+            if (tilt) {
+                const double sz = r[3 * i + 2] / L[2];
+                const double sy = (r[3 * i + 1] - tilt[2] * sz) / L[1];
+                s_sd[k][0] = (r[3 * i] - tilt[0] * sy - tilt[1] * sz) / L[0];
+                s_sd[k][1] = sy;
+                s_sd[k][2] = sz;
+            } else {
+                s_sd[k][0] = r[3 * i] / L[0];
+                s_sd[k][1] = r[3 * i + 1] / L[1];
+                s_sd[k][2] = r[3 * i + 2] / L[2];
+            }
             s_sd[k][3] = q[i];
         }
     }
@@ -119,7 +129,7 @@ k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const in
     if (d0 >= d.nD || na <= 0) return;
     const int nd_here = min(kModeGroup, d.nD - d0);
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
-    sk_chunk<F32>(su, r, q, L, chunk_a0[c], na, D + (size_t)s * Dcap * 3, d0, nd_here,
+    sk_chunk<F32>(su, r, q, L, d.tri ? d.tilt : nullptr, chunk_a0[c], na, D + (size_t)s * Dcap * 3, d0, nd_here,
                   part + ((size_t)c * Dcap + d0) * 2);
 }
 
@@ -191,7 +201,13 @@ k_estimate(const DevSys *sys, const int *__restrict__ first_chunk, const int *__
         rho[2 * k + 1] = im;
         const int *D = D_all + ((size_t)s * Dcap + k) * 3;
         const int m0 = D[0], m1 = D[1], m2 = D[2];
-        const double kx = kTwoPi * m0 * ilx, ky = kTwoPi * m1 * ily, kz = kTwoPi * m2 * ilz;
+        double kx = kTwoPi * m0 * ilx, ky = kTwoPi * m1 * ily, kz = kTwoPi * m2 * ilz;
+        if (d.tri) {                           // k = 2 pi h^{-T} m
+            const int mm[3] = {m0, m1, m2};
+            double kk[3];
+            kvec_of(d, mm, kk);
+            kx = kk[0]; ky = kk[1]; kz = kk[2];
+        }
         const double ik2 = 1.0 / (kx * kx + ky * ky + kz * kz);
         const double r2 = re * re + im * im;
         const double cr = cr_all[(size_t)s * Dcap + k], cnr = cnr_all[(size_t)s * Dcap + k];
@@ -267,7 +283,12 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
     uint4 v = make_uint4(0, 0, 0, 0);
     double sx = 0.0, sy = 0.0, sz = 0.0;
     if (F32) v = su[i];
-    else { sx = r[3 * i] / d.L[0]; sy = r[3 * i + 1] / d.L[1]; sz = r[3 * i + 2] / d.L[2]; }
+    else if (d.tri) {
+        const double x[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+        double sf[3];
+        frac_of(d, x, sf);
+        sx = sf[0]; sy = sf[1]; sz = sf[2];
+    } else { sx = r[3 * i] / d.L[0]; sy = r[3 * i + 1] / d.L[1]; sz = r[3 * i + 2] / d.L[2]; }
     for (int t0 = 0; t0 < nD; t0 += kModeTile) {
         const int nt = min(kModeTile, nD - t0);
         __syncthreads();
@@ -398,7 +419,12 @@ k_nr_shared(const DevSys *__restrict__ sys, const int *__restrict__ D_all, const
     double v[6] = {0, 0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < nD; k += blockDim.x) {
         const int *Dk = D_all + ((size_t)s * Dcap + k) * 3;
-        const double kx = kTwoPi * Dk[0] / d.L[0], ky = kTwoPi * Dk[1] / d.L[1], kz = kTwoPi * Dk[2] / d.L[2];
+        double kx = kTwoPi * Dk[0] / d.L[0], ky = kTwoPi * Dk[1] / d.L[1], kz = kTwoPi * Dk[2] / d.L[2];
+        if (d.tri) {
+            double kk[3];
+            kvec_of(d, Dk, kk);
+            kx = kk[0]; ky = kk[1]; kz = kk[2];
+        }
         const double k2 = kx * kx + ky * ky + kz * kz;
         double a = 0.0, b = 0.0;
         for (int l = 0; l < sa.M; ++l) {
@@ -458,7 +484,7 @@ k_sk_stateless(const uint4 *__restrict__ su, const double *__restrict__ r, const
     if (d0 >= nD) return;
     const int a0 = c * kChunk, na = min(kChunk, n - a0);
     const double L[3] = {L0, L1, L2};
-    sk_chunk<F32>(su, r, q, L, a0, na, m, d0, min(kModeGroup, nD - d0), part + ((size_t)c * nD + d0) * 2);
+    sk_chunk<F32>(su, r, q, L, nullptr, a0, na, m, d0, min(kModeGroup, nD - d0), part + ((size_t)c * nD + d0) * 2);
 }
 
 __global__ void k_sk_reduce(const double *__restrict__ part, int nchunks, int nD, double *__restrict__ rho)

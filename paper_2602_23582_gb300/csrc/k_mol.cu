@@ -19,12 +19,30 @@ namespace rbsog {
 
 namespace {
 
-__device__ __forceinline__ void min_image(double d[3], const double L[3])
+// the box of a system in registers: edges, tilts (xy, xz, yz), tilted or not
+struct Box {
+    double L[3], t[3];
+    bool tri;
+};
+
+__device__ __forceinline__ void min_image(double d[3], const Box &B)
 {
+    if (B.tri) {
+        // the image whose fractional components s = h^{-1} d lie in [-1/2, 1/2]
+        // (h upper triangular: back substitution), d <- d - h rint(s)
+        const double s2 = d[2] / B.L[2];
+        const double s1 = (d[1] - B.t[2] * s2) / B.L[1];
+        const double s0 = (d[0] - B.t[0] * s1 - B.t[1] * s2) / B.L[0];
+        const double n0 = rint(s0), n1 = rint(s1), n2 = rint(s2);
+        d[0] -= B.L[0] * n0 + B.t[0] * n1 + B.t[1] * n2;
+        d[1] -= B.L[1] * n1 + B.t[2] * n2;
+        d[2] -= B.L[2] * n2;
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (d[a] > 0.5 * L[a]) d[a] -= L[a] * rint(d[a] / L[a]);
-        else if (d[a] < -0.5 * L[a]) d[a] -= L[a] * rint(d[a] / L[a]);
+        if (d[a] > 0.5 * B.L[a]) d[a] -= B.L[a] * rint(d[a] / B.L[a]);
+        else if (d[a] < -0.5 * B.L[a]) d[a] -= B.L[a] * rint(d[a] / B.L[a]);
     }
 }
 
@@ -40,7 +58,7 @@ struct TermF {
 // virial).
 __device__ __forceinline__ void bond_term(int e, const int *__restrict__ bonds, const double *__restrict__ bk,
                                           const double *__restrict__ br0, const double *__restrict__ r,
-                                          const double L[3], double &ub, double wb[6], TermF &t)
+                                          const Box &L, double &ub, double wb[6], TermF &t)
 {
     const int i = bonds[2 * e], j = bonds[2 * e + 1];
     double dv[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
@@ -60,7 +78,7 @@ __device__ __forceinline__ void bond_term(int e, const int *__restrict__ bonds, 
 // Angle e (i, j at the vertex, k): U = k (theta - theta0)^2 in FP64.
 __device__ __forceinline__ void angle_term(int e, const int *__restrict__ angles, const double *__restrict__ ak,
                                            const double *__restrict__ at0, const double *__restrict__ r,
-                                           const double L[3], double &ua, double wb[6], TermF &t)
+                                           const Box &L, double &ua, double wb[6], TermF &t)
 {
     const int i = angles[3 * e], j = angles[3 * e + 1], kk = angles[3 * e + 2];
     double d1[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
@@ -93,7 +111,7 @@ __device__ __forceinline__ void angle_term(int e, const int *__restrict__ angles
 // Exclusion e: removes the pair's Fourier-part interaction (see the header).
 template <typename R>
 __device__ __forceinline__ void excl_term(int e, const int *__restrict__ excl, const double *__restrict__ r,
-                                          const double *__restrict__ q, const double L[3], const SogConsts &sc,
+                                          const double *__restrict__ q, const Box &L, const SogConsts &sc,
                                           int en, R &ue_rem, double &ue, R wx[6], TermF &t)
 {
     const int i = excl[2 * e], j = excl[2 * e + 1];
@@ -164,7 +182,7 @@ k_mol(const DevSys *__restrict__ sys, const int *__restrict__ mchunk_sys, const 
     __shared__ R s_f[kMolWarps][NS][3];         // contributions in R: FP32 adds in the FP32 build
     const int c = blockIdx.x, w = threadIdx.x >> 5, lane = lane_id();
     const DevSys &d = sys[mchunk_sys[c]];
-    const double L[3] = {d.L[0], d.L[1], d.L[2]};
+    const Box L = {{d.L[0], d.L[1], d.L[2]}, {d.tilt[0], d.tilt[1], d.tilt[2]}, d.tri != 0};
     double ub = 0, ua = 0, wb[6] = {0, 0, 0, 0, 0, 0};
     R wx[6] = {0, 0, 0, 0, 0, 0};
     R ue_rem = 0;      // sum ke q_i q_j (F_E(0) - F_E(r)) (the constant part is added on the host)

@@ -63,14 +63,20 @@ struct AccD {
 // positions with the minimum image, as the CPU reference decides it.
 // (out of line: the call sits in a branch taken a few times per launch, and an
 // inlined body costs the common path registers and instructions)
-__device__ __noinline__ bool inside_cutoff_fp64(const double *__restrict__ r, int i, int j, const double L[3],
+__device__ __noinline__ bool inside_cutoff_fp64(const double *__restrict__ r, int i, int j, const DevSys &d,
                                                 double rc2)
 {
     double r2 = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        double dd = r[3 * i + a] - r[3 * j + a];
-        dd = L[a] * (dd / L[a] - rint(dd / L[a]));
-        r2 += dd * dd;
+    if (d.tri) {
+        double dd[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+        min_image_tri(d, dd);
+        r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+    } else {
+        for (int a = 0; a < 3; ++a) {
+            double dd = r[3 * i + a] - r[3 * j + a];
+            dd = d.L[a] * (dd / d.L[a] - rint(dd / d.L[a]));
+            r2 += dd * dd;
+        }
     }
     return r2 < rc2;
 }
@@ -234,7 +240,7 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
                                      float qi, int ai, int jslot, int jfirst, int kk, int gbase,
                                      const float4 *__restrict__ pos4, const float2 *__restrict__ qt,
                                      const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlorow,
-                                     const int *__restrict__ sidx, const double *__restrict__ r, const double *L,
+                                     const int *__restrict__ sidx, const double *__restrict__ r, const DevSys &dsys,
                                      TileAcc &acc, float &fjx, float &fjy, float &fjz)
 {
     fjx = fjy = fjz = 0.f;
@@ -254,7 +260,7 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
         bool in = r2 < pc.rc2_lo;
         const bool near = !in && r2 < pc.rc2_hi;
         if (__any_sync(0xffffffffu, near)) {             // rare: out of the common path
-            if (near) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], L, pc.rc2d);
+            if (near) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], dsys, pc.rc2d);
         }
         in = in && __float_as_int(pj.w) != moli;       // pairs of one molecule are excluded
         // (a pair that is not inside may give non-finite values here, e.g. two
@@ -351,8 +357,10 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
         // neighbour-cell offsets d_a w_a as FP32 hi + lo (the rounding of w
         // must not shift every cross-cell distance the same way)
         for (int nb = threadIdx.x; nb < span * span * span; nb += blockDim.x) {
-            const double ox = (nb % span - sub) * d.w[0], oy = ((nb / span) % span - sub) * d.w[1],
-                         oz = (nb / (span * span) - sub) * d.w[2];
+            // h (delta / n): the diagonal part and the tilt terms (zero when orthorhombic)
+            const int ex = nb % span - sub, ey = (nb / span) % span - sub, ez = nb / (span * span) - sub;
+            const double ox = ex * d.w[0] + (ey * d.tw[0] + ez * d.tw[1]), oy = ey * d.w[1] + ez * d.tw[2],
+                         oz = ez * d.w[2];
             const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
             offh[nb] = make_float4(hx, hy, hz, 0.f);
             offl[nb] = make_float4((float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
@@ -392,7 +400,7 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
         if (part == 0)
             tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, make_float4(0.f, 0.f, 0.f, 0.f), moli, qi, ai,
                                kClus * (grp == 0 ? it : item_cap), ifirst, kk, gbase, pos4, qt, ljrow, ljlorow,
-                               sidx, r, d.L, acc, fjx, fjy, fjz);
+                               sidx, r, d, acc, fjx, fjy, fjz);
         // candidate cells, one per lane: plane 0 (I's own cell -- its clusters
         // after I -- then the upper half), then with one unit per cluster
         // (cells of r_c) the planes above
@@ -447,7 +455,7 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
                 const float4 oh = offh[code], ol = offl[code];
                 const int jfirst = nj ? __float_as_int(cbox[2 * jc].w) : 0;
                 tile<NF, EN, false>(pc, pi.x - oh.x, pi.y - oh.y, pi.z - oh.z, ol, moli, qi, ai, kClus * jc,
-                                    jfirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d.L, acc, fjx, fjy, fjz);
+                                    jfirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d, acc, fjx, fjy, fjz);
                 const int jl = (kk + 3) & 3;            // the J atom whose sum this lane holds
                 if (jl < nj) {
                     const int aj = jfirst + jl;
@@ -584,7 +592,7 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
             } else {
                 ddx = c % span - sub; ddy = c / span - sub;
             }
-            offp[c] = make_double2(ddx * d.w[0], ddy * d.w[1]);
+            offp[c] = make_double2(ddx * d.w[0] + (ddy * d.tw[0] + part * d.tw[1]), ddy * d.w[1] + part * d.tw[2]);
         }
         __syncwarp();
         const int i0 = start[gc] + 32 * item.y;

@@ -20,6 +20,15 @@
 //  4. recalibration chain (sec. 3.2): proposals are the radial samples;
 //     accept iff u'_t g(y) < g(x_t) with g = P^nr / P^r.
 //  5. distinct modes of the union, lexicographic order, multiplicities.
+//
+// A tilted cell (DevSys::tri, h = [[L0, xy, xz], [0, L1, yz], [0, 0, L2]],
+// held fixed): k = 2 pi h^{-T} m; the lattice sums over Z^3 are made once per
+// cell (k_tri_gy, k_tri_reduce); the proposal is m* = round(h^T u) and its
+// mass q(m*) the probability that h^T u lies in the unit cube around m*: an
+// erf difference in u_2 given (u_0, u_1), Gauss-Legendre quadrature over
+// (u_0, u_1); the chain's start is an exact draw of P^r: component (l, a)
+// with weight c_l sum_m k_a^2 e_l, then m_0, m_1 given m_0 and m_2 given
+// (m_0, m_1) by inverse CDF over m = 0, 1, -1, 2, ... (tables for m_0 and m_1).
 #include "internal.h"
 
 namespace rbsog {
@@ -184,7 +193,7 @@ k_samp_sums(const DevSys *sys, const SamplerArgs sa, SampScratch *ss)
 {
     const int s = blockIdx.x, idx = blockIdx.y, lane = lane_id();
     const DevSys &d = sys[s];
-    if ((d.flags & FLAG_BOX) || live_n(d) == 0 || idx >= 3 * sa.M) return;
+    if ((d.flags & FLAG_BOX) || live_n(d) == 0 || idx >= 3 * sa.M || d.tri) return;   // tilted: k_tri_*
     const int l = idx / 3, ax = idx % 3;
     const double L = d.L[ax];
     double c = kPi * sa.st[l] / L, a = c * c;
@@ -268,6 +277,144 @@ __device__ double qprop_warp(const SamplerArgs &sa, const double L[3], const int
     return q0 * q1 * q2;
 }
 
+// ---- tilted cell ----------------------------------------------------------
+
+__device__ inline int walk_m(int k) { return (k == 0) ? 0 : ((k & 1) ? (k + 1) / 2 : -(k / 2)); }
+
+// P^r and P^nr (targets) of one mode in the tilted cell of d, by one warp
+__device__ void targets_tri_warp(const SamplerArgs &sa, const DevSys &d, const int m[3], double &pr, double &pnr)
+{
+    const int lane = lane_id();
+    double k[3];
+    kvec_of(d, m, k);
+    const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    double a = 0.0, b = 0.0;
+    for (int l0 = 0; l0 < sa.M; l0 += 32) {
+        const int l = l0 + lane;
+        const double e = l < sa.M ? exp(-(sa.st2q[l] * k2)) : 0.0;
+        const int nl = min(32, sa.M - l0);
+        for (int u = 0; u < nl; ++u) {
+            const double eu = __shfl_sync(0xffffffffu, e, u);
+            a += sa.cr[l0 + u] * eu;
+            b += sa.cn[l0 + u] * eu;
+        }
+    }
+    pr = k2 * a;
+    pnr = (k2 * k2) * b;
+}
+
+// P(lo <= u <= hi) for u ~ N(0, sig^2), without cancellation in the tails
+__device__ double normal_interval(double lo, double hi, double sig)
+{
+    const double x = lo / (sqrt(2.0) * sig), y = hi / (sqrt(2.0) * sig);
+    if (x >= 0.0) return 0.5 * (erfc(x) - erfc(y));
+    if (y <= 0.0) return 0.5 * (erfc(-y) - erfc(-x));
+    return 0.5 * (erf(y) - erf(x));
+}
+
+// q(m*) of eq. proposal in the tilted cell of d, by one warp: (h^T u)_0 =
+// L0 u_0, (h^T u)_1 = xy u_0 + L1 u_1, (h^T u)_2 = xz u_0 + yz u_1 + L2 u_2;
+// the u_2 interval in closed form, kGL x kGL Gauss-Legendre nodes over u_0
+// and u_1 (one node pair per lane and pass)
+__device__ double qprop_tri_warp(const SamplerArgs &sa, const DevSys &d, const int m[3])
+{
+    const int lane = lane_id();
+    const double sig = sa.sig_u, nrm = 1.0 / (sqrt(2.0 * kPi) * sig), i2s2 = 1.0 / (2.0 * sig * sig);
+    const double A0 = ((double)m[0] - 0.5) / d.L[0], B0 = ((double)m[0] + 0.5) / d.L[0];
+    const double c0 = 0.5 * (A0 + B0), h0 = 0.5 * (B0 - A0);
+    double acc = 0.0;
+    for (int p = lane; p < kGL * kGL; p += 32) {
+        const int i = p / kGL, j = p % kGL;
+        const double u0 = c0 + h0 * sa.glx[i];
+        const double A1 = ((double)m[1] - 0.5 - d.tilt[0] * u0) / d.L[1];
+        const double B1 = ((double)m[1] + 0.5 - d.tilt[0] * u0) / d.L[1];
+        const double u1 = 0.5 * (A1 + B1) + 0.5 * (B1 - A1) * sa.glx[j];
+        const double c = d.tilt[1] * u0 + d.tilt[2] * u1;
+        const double pz = normal_interval(((double)m[2] - 0.5 - c) / d.L[2], ((double)m[2] + 0.5 - c) / d.L[2], sig);
+        acc += (sa.glw[i] * nrm * exp(-u0 * u0 * i2s2)) * (0.5 * (B1 - A1)) * (sa.glw[j] * nrm * exp(-u1 * u1 * i2s2)) * pz;
+    }
+    return warp_sum(acc) * h0;
+}
+
+// inverse CDF over m = 0, 1, -1, ... of tab[m + mm] (|m| <= mm), one warp
+__device__ int walk_table_warp(double target, const double *__restrict__ tab, int mm)
+{
+    const int lane = lane_id();
+    double cum = 0.0;
+    const int kmax = 2 * mm;
+    for (int k0 = 0; k0 <= kmax; k0 += 32) {
+        const int k = k0 + lane;
+        const int m = walk_m(k);
+        double incl = k <= kmax ? tab[m + mm] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, k <= kmax && cum + incl > target);
+        if (hit) return __shfl_sync(0xffffffffu, m, __ffs(hit) - 1);
+        cum += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    return walk_m(kmax);
+}
+
+// exact draw from P^r in the tilted cell of d, one warp (same on every lane)
+__device__ void exact_draw_tri_warp(const SamplerArgs &sa, const DevSys &d, const SampScratch &sc,
+                                    const uint64_t wds[4], int m[3])
+{
+    const int lane = lane_id();
+    int sel = 0;
+    if (lane == 0) {
+        double tot = 0.0;
+        for (int l = 0; l < sa.M; ++l) tot += sc.tHr[l];
+        const double target = u01(wds[0]) * tot;
+        double cum = 0.0;
+        int lsel = sa.M - 1, asel = 2;
+        bool done = false;
+        for (int l = 0; l < sa.M && !done; ++l)
+            for (int a = 0; a < 3; ++a) {
+                cum += sa.cr[l] * sc.tS[l][a];
+                if (cum > target) { lsel = l; asel = a; done = true; break; }
+            }
+        sel = 3 * lsel + asel;
+    }
+    sel = __shfl_sync(0xffffffffu, sel, 0);
+    const int l = sel / 3, a = sel % 3;
+    const int mm0 = sc.tmm[0], mm1 = sc.tmm[1], mm2 = sc.tmm[2];
+    const size_t nx = 2 * mm0 + 1, ny = 2 * mm1 + 1;
+    const double *Gy = sa.tri_tab + sc.tab0;
+    const double *Gx = Gy + (size_t)sa.M * 3 * nx * ny;
+    m[0] = walk_table_warp(u01(wds[1]) * sc.tS[l][a], Gx + (size_t)sel * nx, mm0);
+    const size_t ix = (size_t)(m[0] + mm0);
+    m[1] = walk_table_warp(u01(wds[2]) * Gx[(size_t)sel * nx + ix], Gy + ((size_t)sel * nx + ix) * ny, mm1);
+    const size_t iy = (size_t)(m[1] + mm1);
+    // m_2 given (m_0, m_1): weights k_a^2 e_l formed in walk order
+    const double target = u01(wds[3]) * Gy[((size_t)sel * nx + ix) * ny + iy];
+    double cum = 0.0;
+    const int kmax = 2 * mm2;
+    for (int k0 = 0; k0 <= kmax; k0 += 32) {
+        const int k = k0 + lane;
+        const int mz = walk_m(k);
+        double incl = 0.0;
+        if (k <= kmax) {
+            const int mk[3] = {m[0], m[1], mz};
+            double kv[3];
+            kvec_of(d, mk, kv);
+            const double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+            incl = kv[a] * kv[a] * exp(-(sa.st2q[l] * k2));
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, k <= kmax && cum + incl > target);
+        if (hit) { m[2] = __shfl_sync(0xffffffffu, mz, __ffs(hit) - 1); return; }
+        cum += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    m[2] = walk_m(kmax);
+}
+
 // Steps 2-3 of the paper MH sampler on their own grid: block (s, t) is one
 // warp; t < P evaluates proposal t (its three normals, its target and
 // proposal masses lane-parallel), t = P draws the chain's start state exactly.
@@ -285,6 +432,55 @@ k_samp_prop(const DevSys *sys, const SamplerArgs sa, int adv, SampScratch *ss, i
     const int P = sa.P;
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
     uint64_t wds[4];
+    if (d.tri) {
+        int m[3];
+        double w = 0.0, g = 0.0;
+        if (t == P) {
+            draw4(sa.seed, d.rng_id, step, PUR_START, 0, wds);
+            exact_draw_tri_warp(sa, d, ss[s], wds, m);
+        } else {
+            draw4(sa.seed, d.rng_id, step, PUR_PROPOSAL, (uint64_t)t, wds);
+            double z = 0.0;
+            if (lane < 3) {
+                const double u1 = u01(lane < 2 ? wds[0] : wds[2]), u2 = u01(lane < 2 ? wds[1] : wds[3]);
+                const double rr = sqrt(-2.0 * log(u1)), ang = kTwoPi * u2;
+                z = rr * (lane == 1 ? sin(ang) : cos(ang));
+            }
+            const double z0 = __shfl_sync(0xffffffffu, z, 0), z1 = __shfl_sync(0xffffffffu, z, 1),
+                         z2 = __shfl_sync(0xffffffffu, z, 2);
+            // gamma = h^T (sigma_u z)
+            const double g0 = d.L[0] * (z0 * sa.sig_u);
+            const double g1 = d.L[1] * (z1 * sa.sig_u) + d.tilt[0] * (z0 * sa.sig_u);
+            const double g2 = d.L[2] * (z2 * sa.sig_u) + (d.tilt[1] * (z0 * sa.sig_u) + d.tilt[2] * (z1 * sa.sig_u));
+            m[0] = (int)floor(g0 + 0.5);
+            m[1] = (int)floor(g1 + 0.5);
+            m[2] = (int)floor(g2 + 0.5);
+        }
+        if (t == P || m[0] || m[1] || m[2]) {
+            double pr, pnr;
+            targets_tri_warp(sa, d, m, pr, pnr);
+            const double q = qprop_tri_warp(sa, d, m);
+            w = pr / q;
+            g = pnr / pr;
+        }
+        if (lane == 0) {
+            if (t == P) {
+                SampScratch &sc = ss[s];
+                sc.start_m[0] = m[0]; sc.start_m[1] = m[1]; sc.start_m[2] = m[2];
+                sc.start_w = w;
+                sc.start_g = g;
+            } else {
+                const size_t k = (size_t)s * P + t;
+                pm[k] = make_int4(m[0], m[1], m[2], 0);
+                pw[k] = w;
+                pg[k] = g;
+                draw4(sa.seed, d.rng_id, step, PUR_ACCEPT, (uint64_t)t, wds);
+                pu[k] = u01(wds[0]);
+                pun[k] = u01(wds[1]);
+            }
+        }
+        return;
+    }
     if (t == P) {
         double sr, snr;
         load_sums(sa, ss[s], L, sh, sr, snr);
@@ -364,10 +560,18 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, 
         return;
     }
 
-    // 1. 1D lattice sums (k_samp_sums) and the normalizers
+    // 1. 1D lattice sums (k_samp_sums) and the normalizers (a tilted cell:
+    // the sums over Z^3 of k_tri_reduce)
     if (warp == 0) {
-        double sr, snr;
-        load_sums(sa, ss[s], sh.L, sh, sr, snr);
+        double sr = 0.0, snr = 0.0;
+        if (d.tri) {
+            for (int l = 0; l < sa.M; ++l) {
+                sr += ss[s].tHr[l];
+                snr += ss[s].tHnr[l];
+            }
+        } else {
+            load_sums(sa, ss[s], sh.L, sh, sr, snr);
+        }
         if (lane == 0) {
             sh.Sr = sr; sh.Snr = snr;
             d.Sr = sr; d.Snr = snr;
@@ -562,6 +766,79 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, 
         d.nacc_r = cnt_r;
         d.nacc_nr = cnt_nr;
     }
+}
+
+// Lattice sums of a tilted cell, once per cell.  k_tri_gy: one thread per
+// (l, m_0, m_1), the sums over m_2 (ascending) of k_a^2 e_l and k^4 e_l;
+// k_tri_reduce: one block per tilted system, Gx = sum over m_1 (ascending),
+// tS = sum over m_0, the normalizer terms H^r_l = c_l (tS_0 + tS_1 + tS_2)
+// and H^nr_l = c'_l sum_{m_0, m_1} G4.
+__global__ void k_tri_gy(const DevSys *__restrict__ sys, const SamplerArgs sa, const SampScratch *__restrict__ ss,
+                         const int *__restrict__ tri_sys)
+{
+    const int s = tri_sys[blockIdx.y];
+    const DevSys &d = sys[s];
+    const SampScratch &sc = ss[s];
+    const int mm0 = sc.tmm[0], mm1 = sc.tmm[1], mm2 = sc.tmm[2];
+    const int nx = 2 * mm0 + 1, ny = 2 * mm1 + 1, nz = 2 * mm2 + 1;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)sa.M * nx * ny) return;
+    const int l = (int)(idx / ((long long)nx * ny)), i = (int)((idx / ny) % nx), j = (int)(idx % ny);
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0, g4 = 0.0;
+    for (int kz = 0; kz < nz; ++kz) {
+        const int m[3] = {i - mm0, j - mm1, kz - mm2};
+        double k[3];
+        kvec_of(d, m, k);
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        const double e = exp(-(sa.st2q[l] * k2));
+        g0 += k[0] * k[0] * e;
+        g1 += k[1] * k[1] * e;
+        g2 += k[2] * k[2] * e;
+        g4 += (k2 * k2) * e;
+    }
+    double *Gy = sa.tri_tab + sc.tab0;
+    double *G4 = Gy + (size_t)sa.M * 3 * nx * ny + (size_t)sa.M * 3 * nx;
+    Gy[(((size_t)l * 3 + 0) * nx + i) * ny + j] = g0;
+    Gy[(((size_t)l * 3 + 1) * nx + i) * ny + j] = g1;
+    Gy[(((size_t)l * 3 + 2) * nx + i) * ny + j] = g2;
+    G4[((size_t)l * nx + i) * ny + j] = g4;
+}
+
+__global__ void k_tri_reduce(const SamplerArgs sa, SampScratch *__restrict__ ss, const int *__restrict__ tri_sys)
+{
+    SampScratch &sc = ss[tri_sys[blockIdx.x]];
+    const int nx = 2 * sc.tmm[0] + 1, ny = 2 * sc.tmm[1] + 1;
+    const double *Gy = sa.tri_tab + sc.tab0;
+    double *Gx = sa.tri_tab + sc.tab0 + (size_t)sa.M * 3 * nx * ny;
+    const double *G4 = Gx + (size_t)sa.M * 3 * nx;
+    for (int r = threadIdx.x; r < sa.M * 3 * nx; r += blockDim.x) {
+        double a = 0.0;
+        for (int j = 0; j < ny; ++j) a += Gy[(size_t)r * ny + j];
+        Gx[r] = a;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < sa.M * 3; r += blockDim.x) {
+        double a = 0.0;
+        for (int i = 0; i < nx; ++i) a += Gx[(size_t)r * nx + i];
+        sc.tS[r / 3][r % 3] = a;
+    }
+    for (int l = threadIdx.x; l < sa.M; l += blockDim.x) {
+        double a = 0.0;
+        for (size_t u = 0; u < (size_t)nx * ny; ++u) a += G4[(size_t)l * nx * ny + u];
+        sc.tHnr[l] = sa.cn[l] * a;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < sa.M; l += blockDim.x) sc.tHr[l] = sa.cr[l] * (sc.tS[l][0] + sc.tS[l][1] + sc.tS[l][2]);
+}
+
+void launch_tri_tables(const Batch &b, const SamplerArgs &sa, SampScratch *ss, const int *tri_sys, int ntri,
+                       const int *mm_max, cudaStream_t st)
+{
+    (void)b;
+    if (ntri == 0) return;
+    const long long n = (long long)sa.M * (2 * mm_max[0] + 1) * (2 * mm_max[1] + 1);
+    k_tri_gy<<<dim3((unsigned)((n + 127) / 128), ntri), 128, 0, st>>>(b.sys, sa, ss, tri_sys);
+    k_tri_reduce<<<ntri, 256, 0, st>>>(sa, ss, tri_sys);
 }
 
 static size_t sampler_smem(int P)

@@ -70,6 +70,8 @@ struct rbsog_ctx {
     cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr, ev_bin = nullptr;
     std::string err;
     std::vector<int> h_atom0, h_n, h_cell0, h_ncap_total, h_coupling;
+    std::vector<double> h_tilt;         // per system (xy, xz, yz): tilted cells are held fixed
+    double *tri_tab = nullptr;          // lattice-sum tables of the tilted systems
     std::vector<void *> allocs;
     // device
     DevSys *sys = nullptr;
@@ -213,7 +215,52 @@ void fill_sampler_args(const rbsog_params &P, const std::vector<double> &wt, con
         sa.st2q[l] = st[l] * st[l] * 0.25;
     }
     sa.sig_u = 1.0 / (std::sqrt(2.0) * kPi * st[0]);
+    // Gauss-Legendre rule of kGL nodes on [-1, 1]: the roots of P_n by Newton
+    // iteration from cos(pi (i + 3/4) / (n + 1/2)), weights 2 / ((1 - x^2) P_n'(x)^2)
+    const int n = kGL;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double x = std::cos(kPi * (i + 0.75) / (n + 0.5)), dpn = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm1 = 1.0, pn = x;                 // P_0, P_1
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2 * k - 1) * x * pn - (k - 1) * pm1) / k;
+                pm1 = pn;
+                pn = pk;
+            }
+            dpn = n * (x * pn - pm1) / (x * x - 1.0);
+            const double step = pn / dpn;
+            x -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        double pm1 = 1.0, pn = x;
+        for (int k = 2; k <= n; ++k) {
+            const double pk = ((2 * k - 1) * x * pn - (k - 1) * pm1) / k;
+            pm1 = pn;
+            pn = pk;
+        }
+        dpn = n * (x * pn - pm1) / (x * x - 1.0);
+        sa.glx[i] = -x;
+        sa.glx[n - 1 - i] = x;
+        sa.glw[i] = sa.glw[n - 1 - i] = 2.0 / ((1.0 - x * x) * dpn * dpn);
+    }
+    sa.tri_tab = nullptr;
 }
+
+// Range |m_a| <= mm[a] of the lattice sums of a tilted cell: the box around
+// the ellipsoid |k| <= 2 sqrt(46) / s~_0 (beyond it every term is below
+// e^-46 of the largest), |m_a| <= (2 sqrt(46) / (2 pi s~_0)) |a-th cell vector|.
+void tri_range(const double L[3], const double t[3], double st0, int mm[3])
+{
+    const double R = 2.0 * std::sqrt(46.0) / st0 / (2.0 * kPi);
+    const double len[3] = {L[0], std::sqrt(t[0] * t[0] + L[1] * L[1]), std::sqrt(t[1] * t[1] + t[2] * t[2] + L[2] * L[2])};
+    for (int a = 0; a < 3; ++a) mm[a] = (int)std::ceil(R * len[a]) + 2;
+}
+
+bool tilted(const rbsog_system_desc &d) { return d.tilt[0] != 0.0 || d.tilt[1] != 0.0 || d.tilt[2] != 0.0; }
+
+// the extent that sets the cell grid along axis a: the edge, or for a tilted
+// cell its perpendicular width
+double grid_span(const rbsog_system_desc &d, int a) { return perp_width(d.box, d.tilt, a); }
 
 void record(rbsog_ctx *c, const char *name)
 {
@@ -402,6 +449,7 @@ rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
         }
         r.volume = o[51];
         r.box[0] = o[52]; r.box[1] = o[53]; r.box[2] = o[54];
+        for (int a = 0; a < 3; ++a) r.tilt[a] = c->h_tilt.empty() ? 0.0 : c->h_tilt[3 * s + a];
         r.n_distinct_modes = (int)o[55];
         r.n_accept_r = (int)o[56];
         r.n_accept_nr = (int)o[57];
@@ -470,7 +518,7 @@ bool build_image(const rbsog_params &P, const SlotLayout &ly, DevSys &ds, const 
         return false;
     }
     for (int a = 0; a < 3; ++a) {
-        const double x = std::floor(d.box[a] * P.cell_sub / list_radius(P));
+        const double x = std::floor(grid_span(d, a) * P.cell_sub / list_radius(P));
         if (!(x >= 2 * P.cell_sub + 1)) { why = "box edge too small for the cell stencil"; return false; }
         if (!(x <= ds.ncap[a])) { why = "box larger than its slot's cell grid"; return false; }
     }
@@ -554,7 +602,8 @@ bool build_image(const rbsog_params &P, const SlotLayout &ly, DevSys &ds, const 
                                         (float)(im.ljd.back().y - (double)im.ljf.back().y)));
     }
     // per-system fields
-    for (int a = 0; a < 3; ++a) { ds.L[a] = d.box[a]; ds.ph[a] = 0.0; ds.Mbox[a] = 0.0; }
+    for (int a = 0; a < 3; ++a) { ds.L[a] = d.box[a]; ds.ph[a] = 0.0; ds.Mbox[a] = 0.0; ds.tilt[a] = d.tilt[a]; }
+    ds.tri = tilted(d) ? 1 : 0;
     ds.V = d.box[0] * d.box[1] * d.box[2];
     ds.n = n;
     ds.nmol = nm;
@@ -607,7 +656,7 @@ rbsog_status validate_system(const rbsog_system_desc &d)
         d.n_bonds < 0 || d.n_angles < 0 || d.n_excl < 0)
         return RBSOG_EINVAL;
     for (int a = 0; a < 3; ++a)
-        if (!(d.box[a] > 0)) return RBSOG_EBOX;
+        if (!(d.box[a] > 0) || !std::isfinite(d.tilt[a])) return RBSOG_EBOX;
     for (int i = 0; i < d.n_atoms; ++i)
         if (!(d.mass[i] > 0) || !std::isfinite(d.mass[i])) return RBSOG_EINVAL;
     return RBSOG_OK;
@@ -681,13 +730,22 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->prm = *params;
         c->pool = systems == nullptr;
         c->slot_err.assign(n_systems, RBSOG_OK);
+        bool any_tri = false;
+        for (int k = 0; systems && k < n_systems; ++k) any_tri = any_tri || tilted(systems[k]);
+        if (any_tri && (c->prm.coupling != RBSOG_COUPLE_FIXED || c->prm.skin > 0.0 ||
+                        c->prm.sampler != RBSOG_SAMPLER_PAPER)) {
+            rbsog_status rr = fail(c, RBSOG_EUNSUPPORTED,
+                                   "a tilted cell needs coupling RBSOG_COUPLE_FIXED, skin 0 and the paper sampler");
+            free_ctx(c);
+            return rr;
+        }
         if (c->prm.cell_sub == 0) {
             // cells of r_c/2 when a box edge leaves little room above 3 r_c (the
             // box fluctuates in NPT), else cells of r_c; pools take r_c/2
             c->prm.cell_sub = c->pool ? 2 : 1;
             for (int k = 0; systems && k < n_systems; ++k)
                 for (int a2 = 0; a2 < 3; ++a2)
-                    if (systems[k].box[a2] < 3.3 * list_radius(c->prm)) c->prm.cell_sub = 2;
+                    if (grid_span(systems[k], a2) < 3.3 * list_radius(c->prm)) c->prm.cell_sub = 2;
         }
         const rbsog_params &P = c->prm;
         c->S = n_systems;
@@ -739,7 +797,8 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             std::memset(&ds, 0, sizeof(ds));
             int ncap_t = 1;
             for (int a = 0; a < 3; ++a) {
-                const int n = (int)std::floor(cp.box[a] * P.cell_sub / list_radius(P));
+                const double span = systems ? grid_span(systems[k], a) : cp.box[a];
+                const int n = (int)std::floor(span * P.cell_sub / list_radius(P));
                 if (n < 2 * P.cell_sub + 1) {
                     rbsog_status rr = fail(c, RBSOG_EBOX, "system " + std::to_string(k) + ": box edge " +
                                                               std::to_string(cp.box[a]) + " too small for the cell stencil");
@@ -1017,6 +1076,35 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         if (e == cudaSuccess) e = prepare_pair();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { rbsog_status rr = cuda_fail(c, e, "create"); free_ctx(c); return rr; }
+        // tilted cells: the sampler's lattice sums, once (the cell is held fixed)
+        c->h_tilt.assign(3 * (size_t)S, 0.0);
+        if (any_tri) {
+            std::vector<SampScratch> hss(S);
+            std::memset(hss.data(), 0, sizeof(SampScratch) * S);
+            std::vector<int> tri_sys;
+            int mmx[3] = {0, 0, 0};
+            size_t tab = 0;
+            for (int k = 0; k < S; ++k) {
+                for (int a = 0; a < 3; ++a) c->h_tilt[3 * k + a] = systems[k].tilt[a];
+                if (!tilted(systems[k])) continue;
+                int mm[3];
+                tri_range(systems[k].box, systems[k].tilt, st[0], mm);
+                for (int a = 0; a < 3; ++a) { hss[k].tmm[a] = mm[a]; mmx[a] = std::max(mmx[a], mm[a]); }
+                hss[k].tab0 = (long long)tab;
+                tab += tri_tab_size(P.M, mm);
+                tri_sys.push_back(k);
+            }
+            int *d_tri = nullptr;
+            bool ok2 = dalloc(c, c->tri_tab, tab) && dalloc(c, d_tri, tri_sys.size()) &&
+                       cudaMemcpy(c->samp, hss.data(), sizeof(SampScratch) * S, cudaMemcpyHostToDevice) == cudaSuccess &&
+                       cudaMemcpy(d_tri, tri_sys.data(), sizeof(int) * tri_sys.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+            if (!ok2) { free_ctx(c); return RBSOG_ENOMEM; }
+            c->sa.tri_tab = c->tri_tab;
+            launch_tri_tables(c->b, c->sa, c->samp, d_tri, (int)tri_sys.size(), mmx, c->st);
+            e = cudaStreamSynchronize(c->st);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) { rbsog_status rr = cuda_fail(c, e, "tilted-cell tables"); free_ctx(c); return rr; }
+        }
         // the first evaluation (counter 0) primes forces, virial and kinetic tensor
         launch_clear_flags(c->b, c->st);
         enqueue_eval(c, 0, 0, 1, 0);
@@ -1072,6 +1160,7 @@ rbsog_status rbsog_pool_load(rbsog_ctx *c, int slot, const rbsog_system_desc *sy
     if (!c || !c->pool || slot < 0 || slot >= c->S || !sys || nsteps == 0 || nsteps < -1) return RBSOG_EINVAL;
     rbsog_status vs = validate_system(*sys);
     if (vs != RBSOG_OK) return fail(c, vs, "rbsog_pool_load: invalid system");
+    if (tilted(*sys)) return fail(c, RBSOG_EUNSUPPORTED, "rbsog_pool_load: tilted cells are served by rbsog_create contexts");
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pool load");
     DevSys ds;
@@ -1166,6 +1255,8 @@ rbsog_status rbsog_pool_unload(rbsog_ctx *c, int slot, double *r, double *v, rbs
 rbsog_status rbsog_set_box(rbsog_ctx *c, int s, const double box[3], int rescale)
 {
     if (!c || s < 0 || s >= c->S || !box) return RBSOG_EINVAL;
+    if (!c->h_tilt.empty() && (c->h_tilt[3 * s] != 0.0 || c->h_tilt[3 * s + 1] != 0.0 || c->h_tilt[3 * s + 2] != 0.0))
+        return fail(c, RBSOG_EUNSUPPORTED, "set_box: a tilted cell is held fixed");
     for (int a = 0; a < 3; ++a)
         if (!(box[a] > 0) || (int)std::floor(box[a] * c->prm.cell_sub / list_radius(c->prm)) < 2 * c->prm.cell_sub + 1)
             return fail(c, RBSOG_EBOX, "box edge below 3 cells");

@@ -72,7 +72,7 @@ class rbsog_system_desc(C.Structure):
                 ("n_bonds", C.c_int), ("bonds", _I), ("bond_k", _D), ("bond_r0", _D),
                 ("n_angles", C.c_int), ("angles", _I), ("angle_k", _D), ("angle_t0", _D),
                 ("n_excl", C.c_int), ("excl", _I), ("r0", _D), ("v0", _D), ("box", C.c_double * 3),
-                ("rng_id", C.c_uint64)]
+                ("rng_id", C.c_uint64), ("tilt", C.c_double * 3)]
 
 
 class rbsog_result(C.Structure):
@@ -82,7 +82,7 @@ class rbsog_result(C.Structure):
                 ("virial_bonded", C.c_double * 9), ("pressure", C.c_double * 9),
                 ("box", C.c_double * 3), ("volume", C.c_double), ("n_distinct_modes", C.c_int),
                 ("n_accept_r", C.c_int), ("n_accept_nr", C.c_int), ("step", C.c_uint64),
-                ("list_builds", C.c_int)]
+                ("list_builds", C.c_int), ("tilt", C.c_double * 3)]
 
 
 _lib = None
@@ -212,8 +212,10 @@ def _desc(sys, hold, index):
     desc.excl = i(sys.excl)
     desc.r0 = d(sys.pos)
     desc.v0 = d(v0) if v0 is not None else None
+    tilt = getattr(sys, "tilt", (0.0, 0.0, 0.0))
     for a in range(3):
         desc.box[a] = float(sys.box[a])
+        desc.tilt[a] = float(tilt[a])
     desc.rng_id = int(getattr(sys, "rng_id", index))
     return desc
 
@@ -221,8 +223,9 @@ def _desc(sys, hold, index):
 def rbsog_create(params: rbsog_params, systems, stream=None):
     """Create a context over a list of systems (duck-typed: pos, q, mass,
     type, mol, box, lj_eps, lj_sig, bonds, bond_k, bond_r0, angles, angle_k,
-    angle_t0, excl; optional vel and rng_id -- the Philox key word, default
-    the system's index).  Returns the opaque context pointer."""
+    angle_t0, excl; optional vel, rng_id -- the Philox key word, default
+    the system's index -- and tilt = (xy, xz, yz) of a triclinic cell).
+    Returns the opaque context pointer."""
     hold = []
     arr = (rbsog_system_desc * len(systems))()
     for k, s in enumerate(systems):
@@ -541,7 +544,8 @@ def result_dict(r: rbsog_result) -> dict:
                virial_long_r=t(r.virial_long_r), virial_long_nr=t(r.virial_long_nr),
                virial_lj=t(r.virial_lj), virial_bonded=t(r.virial_bonded), pressure=t(r.pressure),
                box=np.array(r.box[:]), volume=r.volume, n_distinct_modes=r.n_distinct_modes,
-               n_accept_r=r.n_accept_r, n_accept_nr=r.n_accept_nr, step=r.step, list_builds=r.list_builds)
+               n_accept_r=r.n_accept_r, n_accept_nr=r.n_accept_nr, step=r.step, list_builds=r.list_builds,
+               tilt=np.array(r.tilt[:]))
     return out
 
 
