@@ -64,6 +64,10 @@ def workload(name: str, rank: int = 0):
     if name == "membrane":
         s = W.membrane()
         return [s], "membrane-like slab 64x64x96 A, 120,000 sites, semi-isotropic, rc=10 A, P=100"
+    if name == "tiny":
+        s = W.electrolyte(n_ions=216, L=26.0, seed=3)
+        return [s], ("216-ion electrolyte, L=26 A, rc=10 A, P=100, isotropic Langevin NPT: the per-step "
+                     "floor of the step graph (launch and dependency latency of its kernels)")
     if name == "water_sheared":
         s = W.sheared(W.water(), (6.688, -4.0, 5.0))
         return [s], ("water-like box of 30,000 sites in a triclinic cell (edges 66.88 A, tilts xy=6.688, "
@@ -721,7 +725,8 @@ def main():
                 ("triclinic_water", "water_sheared", R.RBSOG_FP32, 100, 100,
                  dict(coupling=R.RBSOG_COUPLE_FIXED)),
                 ("triclinic_water_fp64", "water_sheared", R.RBSOG_FP64, 100, 30,
-                 dict(coupling=R.RBSOG_COUPLE_FIXED))]
+                 dict(coupling=R.RBSOG_COUPLE_FIXED)),
+                ("graph_floor", "tiny", R.RBSOG_FP32, 100, 300, dict())]
         for key, name, pr, P, ns, kw in plan:
             try:
                 more[key] = sub_record(R, stream, flush, sm_clk, name, pr, P=P, steps=ns, **kw)

@@ -271,6 +271,11 @@ rbsog_status rbsog_debug_cells(rbsog_ctx *ctx, int s, int *ncell, int *cell_of_a
 rbsog_status rbsog_debug_modes(rbsog_ctx *ctx, int s, int *mr, int *mnr, int *D, int *cr,
                                int *cnr, int *nD, double *S, double *rho);
 
+/* Number of cudaMalloc and cudaFree calls the library has made in this
+ * process so far (every thread, every context): a test shows with it that a
+ * call allocates and frees nothing. */
+unsigned long long rbsog_debug_device_alloc_calls(void);
+
 /* Shared-proposal estimator of the non-radial long-range virial (sec. 3.2:
  * the P radial samples of the last evaluation reused for eq. PcoulFnr with
  * importance weights f_nr / P^r = S^r k^2 R(k), R(k) = sum_l w~_l s~_l^7

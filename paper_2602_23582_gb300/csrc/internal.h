@@ -32,7 +32,7 @@ struct PairConstsF {
     int M, ME;
     int nff, nfe;               // exponentials for the force (l < nff) and the energy (l < nfe)
     float rc2, ke;
-    float rc2_hi, rc2_lo;       // r_c^2 (1 +- 1e-5): pairs in between are decided in FP64
+    float rc2_hi, rc2_lo;       // r_c^2 (1 +- 1e-5): pairs in between are decided in FP64 (with energies)
     float rl2_hi;               // (r_c + skin)^2 (1 + 1e-5): the list build's radius
     double rc2d;                // r_c^2 in FP64
     float beta[kMaxGauss];      // log2(e) / s~_l^2 (force)

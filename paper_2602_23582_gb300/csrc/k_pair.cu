@@ -254,13 +254,21 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
         const int aj = jfirst + jj;
         const float dx = (xs - pj.x) - ol.x, dy = (ys - pj.y) - ol.y, dz = (zs - pj.z) - ol.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        // pairs within a relative 1e-5 of r_c^2 are decided in FP64 from the
-        // original positions (the energy kernel N is about 2e-3 / A at r_c,
-        // so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3)
-        bool in = r2 < pc.rc2_lo;
-        const bool near = !in && r2 < pc.rc2_hi;
-        if (__any_sync(0xffffffffu, near)) {             // rare: out of the common path
-            if (near) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], dsys, pc.rc2d);
+        // with energies, pairs within a relative 1e-5 of r_c^2 are decided in
+        // FP64 from the original positions (the energy kernel N is about 2e-3 / A
+        // at r_c, so one pair on the wrong side shifts U by ~ke q_i q_j 2e-3);
+        // force-only evaluations decide in FP32: the force kernel N~ is ~5e-9 at
+        // r_c, and a pair within FP32 rounding of r_c moves a force by at most
+        // the LJ force there
+        bool in;
+        if (EN) {
+            in = r2 < pc.rc2_lo;
+            const bool near = !in && r2 < pc.rc2_hi;
+            if (__any_sync(0xffffffffu, near)) {         // rare: out of the common path
+                if (near) in = inside_cutoff_fp64(r, sidx[ai], sidx[aj], dsys, pc.rc2d);
+            }
+        } else {
+            in = r2 < pc.rc2;
         }
         in = in && __float_as_int(pj.w) != moli;       // pairs of one molecule are excluded
         // (a pair that is not inside may give non-finite values here, e.g. two
@@ -280,9 +288,10 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
         const float qq = qi * qj.x;                    // qi holds ke q_i
         const float fc = qq * (r2inv * rinv - st);
         const int tj = __float_as_int(qj.y);
-        const float2 lab = ljrow[tj];
+        const float2 lab = ljrow[tj];   // EN: (4 eps s^12, 4 eps s^6); else (48 eps s^12, 24 eps s^6)
         const float r6inv = r2inv * r2inv * r2inv;
-        const float fl = (12.f * lab.x * r6inv - 6.f * lab.y) * r6inv * r2inv;
+        const float fl = EN ? (12.f * lab.x * r6inv - 6.f * lab.y) * r6inv * r2inv
+                            : fmaf(lab.x, r6inv, -lab.y) * r6inv * r2inv;
         const float f = in ? fc + fl : 0.f;
         acc.fx = fmaf(f, dx, acc.fx);
         acc.fy = fmaf(f, dy, acc.fy);
@@ -366,7 +375,8 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
             offl[nb] = make_float4((float)(ox - (double)hx), (float)(oy - (double)hy), (float)(oz - (double)hz), 0.f);
         }
         for (int t = threadIdx.x; t < d.ntypes * d.ntypes; t += blockDim.x) {
-            ljs[0][t] = lj[d.lj0 + t];
+            const float2 v = lj[d.lj0 + t];
+            ljs[0][t] = EN ? v : make_float2(12.f * v.x, 6.f * v.y);
             if (EN) ljs[EN ? 1 : 0][t] = ljlo[d.lj0 + t];
         }
     }

@@ -9,6 +9,7 @@
 //   kick/kinetic -> finalize (+ step counter advance)
 // An NPT step prepends box_half and atom_update.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -161,11 +162,15 @@ rbsog_status cuda_fail(rbsog_ctx *c, cudaError_t e, const char *where)
     return fail(c, RBSOG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// every cudaMalloc and cudaFree the library makes (rbsog_debug_device_alloc_calls)
+std::atomic<unsigned long long> g_dev_alloc_calls{0};
+
 template <typename T>
 bool dalloc(rbsog_ctx *c, T *&ptr, size_t n)
 {
     if (n == 0) n = 1;
     void *v = nullptr;
+    ++g_dev_alloc_calls;
     if (cudaMalloc(&v, n * sizeof(T)) != cudaSuccess) return false;
     cudaMemset(v, 0, n * sizeof(T));
     c->allocs.push_back(v);
@@ -473,7 +478,10 @@ void free_ctx(rbsog_ctx *c)
     for (auto e : c->ev_pair_ph)
         if (e) cudaEventDestroy(e);
     for (auto e : c->t_events) cudaEventDestroy(e);
-    for (void *v : c->allocs) cudaFree(v);
+    for (void *v : c->allocs) {
+        ++g_dev_alloc_calls;
+        cudaFree(v);
+    }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_bin) cudaEventDestroy(c->ev_bin);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -693,6 +701,8 @@ void rbsog_default_params(rbsog_params *p, double rc)
 }
 
 const char *rbsog_last_error(const rbsog_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+unsigned long long rbsog_debug_device_alloc_calls(void) { return g_dev_alloc_calls.load(); }
 
 int rbsog_n_atoms(const rbsog_ctx *ctx) { return ctx ? ctx->N : 0; }
 
@@ -1773,6 +1783,7 @@ rbsog_status rbsog_modes(const rbsog_params *params, const double box[3], uint64
     const size_t nb_pm = (size_t)Pn * sizeof(int4), nb_d = (size_t)4 * Pn * sizeof(double);
     const size_t total = nb_sys + nb_ss + ((nb_i + 255) / 256) * 256 + ((nb_pm + 255) / 256) * 256 + nb_d;
     char *buf = nullptr;
+    ++g_dev_alloc_calls;
     cudaError_t e = cudaMalloc(&buf, total);
     if (e != cudaSuccess) return fail(nullptr, RBSOG_ENOMEM, "rbsog_modes: device memory");
     DevSys *dsys = reinterpret_cast<DevSys *>(buf);
@@ -1798,6 +1809,7 @@ rbsog_status rbsog_modes(const rbsog_params *params, const double box[3], uint64
         if (e == cudaSuccess) e = cudaMemcpy(cr, dcr, sizeof(int) * h.nD, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(cnr, dcnr, sizeof(int) * h.nD, cudaMemcpyDeviceToHost);
     }
+    ++g_dev_alloc_calls;
     cudaFree(buf);
     if (e != cudaSuccess) return fail(nullptr, RBSOG_ECUDA, std::string("rbsog_modes: ") + cudaGetErrorString(e));
     *nD = h.nD;

@@ -29,7 +29,7 @@ E_NAMES = ("coul_short", "coul_long", "coul_self", "coul_excl", "lj", "bond", "a
 EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_error", "rbsog_n_atoms",
            "rbsog_system_range", "rbsog_set_box", "rbsog_set_positions", "rbsog_get_positions",
            "rbsog_get_velocities", "rbsog_step", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
-           "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_virial_nr_shared", "rbsog_set_timing", "rbsog_get_timing",
+           "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_debug_device_alloc_calls", "rbsog_virial_nr_shared", "rbsog_set_timing", "rbsog_get_timing",
            "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
            "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc", "rbsog_trace_pair",
            "rbsog_trace_pair_times", "rbsog_set_thermo_every", "rbsog_pool_create", "rbsog_pool_load",
@@ -109,6 +109,8 @@ def lib():
     L.rbsog_last_error.restype = C.c_char_p
     L.rbsog_n_atoms.argtypes = [P]
     L.rbsog_system_range.argtypes = [P, C.c_int, _I, _I]
+    L.rbsog_debug_device_alloc_calls.argtypes = []
+    L.rbsog_debug_device_alloc_calls.restype = C.c_ulonglong
     L.rbsog_set_box.argtypes = [P, C.c_int, _D, C.c_int]
     L.rbsog_set_positions.argtypes = [P, P, C.c_int]
     L.rbsog_get_positions.argtypes = [P, P, C.c_int]

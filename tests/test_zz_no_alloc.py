@@ -40,11 +40,15 @@ def test_noalloc_matches_workspace_entry_point(prec, tol):
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     alloc0 = torch.cuda.memory_allocated()
+    calls0 = R.lib().rbsog_debug_device_alloc_calls()
     for k in (1, 2):                                   # two calls in a row
         R.rbsog_structure_factor_noalloc(r, q, s.box, mt, out[k], precision=prec)
     torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] == free0
+    # the library made no cudaMalloc or cudaFree call (its own counter), and
+    # neither torch's allocator nor the device's free memory moved
+    assert R.lib().rbsog_debug_device_alloc_calls() == calls0
     assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
     scale = float(np.abs(s.q).sum())
     g_ref = ref.cpu().numpy()
     for k in range(3):
