@@ -17,14 +17,16 @@ struct SogConsts {
 };
 
 constexpr int kTail = 7;        // energy: degree (in u = r^2) of the Taylor tail of the wide Gaussians
-constexpr int kTailF = 8;       // force: degree of its Taylor tail
+constexpr int kTailF = 5;       // force: degree of its polynomial tail (Chebyshev-node interpolant)
 
 // FP32 pair kernel constants.  The wider Gaussians vary little over r <= r_c
-// and are summed as a Taylor polynomial in u = r^2: for the force, those with
-// s~_l >= 1.3 r_c (u / s~^2 <= 0.6; degree 8, within 1.8e-7 of their sum in
-// FP32, about one FP32 exponential's own error; measured), for the energy
-// those with s_l >= 2.5 r_c (remainder below 0.16^8 / 8! of w_l); the
-// narrower ones are exponentials.  The energy path keeps its coefficients
+// and are summed as a polynomial in u = r^2: for the force, those with
+// s~_l >= 1.3 r_c (u / s~^2 <= 0.6) as the degree-5 polynomial through their
+// sum at the Chebyshev nodes of [0, r_c^2] (within 1e-8 of the sum at u = 0,
+// 1e-7 with the FP32 rounding of its evaluation, as for the degree-8 Taylor
+// polynomial it replaced; measured), for the energy those with s_l >= 2.5 r_c
+// as a Taylor polynomial (remainder below 0.16^8 / 8! of w_l); the narrower
+// ones are exponentials.  The energy path keeps its coefficients
 // as FP32 hi + lo pairs: a rounding shared by every pair would otherwise be
 // multiplied by sum q_i q_j / r, which is far larger than the short-range
 // energy itself.
@@ -37,7 +39,7 @@ struct PairConstsF {
     double rc2d;                // r_c^2 in FP64
     float beta[kMaxGauss];      // log2(e) / s~_l^2 (force)
     float wt[kMaxGauss];        // w~_l
-    float tt[kTailF + 1];       // sum_{nff <= l < M} w~_l e^{-u / s~_l^2} = sum_k tt[k] u^k
+    float tt[kTailF + 1];       // sum_{nff <= l < M} w~_l e^{-u / s~_l^2} ~= sum_k tt[k] u^k
     float be_hi[kMaxGauss], be_lo[kMaxGauss];   // log2(e) / s_l^2 (energy)
     float w_hi[kMaxGauss], w_lo[kMaxGauss];     // w_l
     float te[kTail + 1];        // energy tail without its constant (te[0] = 0)

@@ -1038,14 +1038,43 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                 c->pcf.w_hi[l] = (float)w[l];
                 c->pcf.w_lo[l] = (float)(w[l] - (double)c->pcf.w_hi[l]);
             }
-            // sum_l w_l e^{-u/s_l^2} = sum_k u^k sum_l w_l (-1/s_l^2)^k / k!
-            double te0 = 0.0;
-            for (int k = 0; k <= kTailF; ++k) {
-                double tk = 0.0, fact = 1.0;
-                for (int i = 2; i <= k; ++i) fact *= i;
-                for (int l = nff; l < P.M; ++l) tk += wt[l] * std::pow(-1.0 / (st[l] * st[l]), k) / fact;
-                c->pcf.tt[k] = (float)tk;
+            // force tail sum_{l >= nff} w~_l e^{-u/s~_l^2} on u in [0, r_c^2 (1 + 1e-5)]:
+            // the polynomial of degree kTailF through its values at the kTailF + 1
+            // Chebyshev nodes of the interval (within 1e-8 of the tail's value at
+            // u = 0 for Table 2 row 2, below the FP32 rounding of its evaluation)
+            {
+                const int D = kTailF;
+                const double U = P.rc * P.rc * (1.0 + 1e-5);
+                double A[kTailF + 1][kTailF + 2];
+                for (int k = 0; k <= D; ++k) {
+                    const double t = 0.5 * (1.0 - std::cos((2 * k + 1) * kPi / (2.0 * (D + 1))));   // node / U
+                    double tv = 0.0;
+                    for (int l = nff; l < P.M; ++l) tv += wt[l] * std::exp(-(t * U) / (st[l] * st[l]));
+                    double pw = 1.0;
+                    for (int j = 0; j <= D; ++j) { A[k][j] = pw; pw *= t; }
+                    A[k][D + 1] = tv;
+                }
+                // Gaussian elimination with partial pivoting (in t = u / U)
+                for (int col = 0; col <= D; ++col) {
+                    int piv = col;
+                    for (int r2 = col + 1; r2 <= D; ++r2)
+                        if (std::fabs(A[r2][col]) > std::fabs(A[piv][col])) piv = r2;
+                    for (int j = 0; j <= D + 1; ++j) std::swap(A[col][j], A[piv][j]);
+                    for (int r2 = col + 1; r2 <= D; ++r2) {
+                        const double f = A[r2][col] / A[col][col];
+                        for (int j = col; j <= D + 1; ++j) A[r2][j] -= f * A[col][j];
+                    }
+                }
+                double a[kTailF + 1];
+                for (int k = D; k >= 0; --k) {
+                    double v = A[k][D + 1];
+                    for (int j = k + 1; j <= D; ++j) v -= A[k][j] * a[j];
+                    a[k] = v / A[k][k];
+                }
+                double scale = 1.0;
+                for (int k = 0; k <= D; ++k) { c->pcf.tt[k] = (float)(a[k] / scale); scale *= U; }
             }
+            double te0 = 0.0;
             for (int k = 0; k <= kTail; ++k) {
                 double ek = 0.0, fact = 1.0;
                 for (int i = 2; i <= k; ++i) fact *= i;
