@@ -41,11 +41,14 @@ FP32_LANES = 128              # FP32 FMA lanes per SM
 # special-function unit, ~67 FP32 operations
 PAIR_MUFU_PER_UNIT = 11
 PAIR_FP32_PER_UNIT = 67
-# FP64 build: the same unit on the FP64 pipe (2 DFMA lanes per SM per clock, 1/64 of FP32): 67
-# arithmetic operations plus 10 exponentials and one reciprocal square root, each counted as 14
-# FMAs (range reduction and a degree-11 polynomial, the textbook form of a double exp)
+# FP64 build: the FP64 pipe (2 lanes per SM per clock, 1/64 of FP32), and as the unit the FP64
+# operations (DADD, DMUL, DFMA) the kernel's form of the pair term executes per half-pair inside
+# r_c: the 9 wide Gaussians as one degree-20 polynomial, one exponential, the reciprocal square
+# root, the Coulomb/LJ force and the virial -- counted by ncu on the water box (491M per launch
+# for 6.25M half-pairs).  The form with 10 exponentials of ~14 operations each would be 221, and
+# the kernel runs below that form's roofline time.
 FP64_LANES = 2
-PAIR_FP64_PER_UNIT = 67 + 11 * 14
+PAIR_FP64_PER_UNIT = 79
 
 
 def workload(name: str, rank: int = 0):
@@ -421,8 +424,9 @@ def pair_roofline(half_pairs, pair_ms, prec, sm_clk, pair_trace=None, traffic=No
         peak = SM_COUNT * FP64_LANES * sm_clk / 1e12
         achieved = half_pairs * PAIR_FP64_PER_UNIT / (pair_ms * 1e-3) / 1e12
         rec.update(kernel="k_pair_f64", achieved=achieved, peak=peak, unit="Top/s (FP64 pipe)",
-                   limit="FP64 pipe: busy 83 % of the cycles in a full ncu capture (profiles/pair_kernel_f64_water.md)",
-                   frac=achieved / peak, per_unit=f"{PAIR_FP64_PER_UNIT} FP64 operations per half-pair inside r_c",
+                   limit=("FP64 pipe (the FP64 operations at 92 % lane occupancy, 29.6 of 32 lanes per "
+                          "instruction; profiles/pair_kernel_f64_water.md)"),
+                   frac=achieved / peak, per_unit=f"{PAIR_FP64_PER_UNIT} FP64 operations per half-pair inside r_c (as executed, ncu count)",
                    peak_basis=f"{SM_COUNT} SMs x {FP64_LANES} FP64 lanes/clk x {sm_clk / 1e6:.0f} MHz (max clock); "
                               f"roofline time {half_pairs * PAIR_FP64_PER_UNIT / (peak * 1e12) * 1e6:.1f} us")
         return rec

@@ -212,10 +212,17 @@ __device__ __forceinline__ int axis_cells(double L, int sub, double rc, int ncap
 }
 
 // Fractional coordinates s = h^{-1} x for the upper-triangular h of d, by back
-// substitution (for a zero tilt, s_a = x_a / L_a exactly, as each product
-// with a zero tilt adds an exact zero).
+// substitution; an orthorhombic box takes s_a = x_a / L_a, three independent
+// divisions (the substitution chains them, and FP64 divisions are long
+// sequences on this part's FP64 pipe: chained, they tripled the latency of
+// the binning kernels).
 __device__ __forceinline__ void frac_of(const DevSys &d, const double x[3], double s[3])
 {
+    if (!d.tri) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s[a] = __ddiv_rn(x[a], d.L[a]);
+        return;
+    }
     s[2] = __ddiv_rn(x[2], d.L[2]);
     s[1] = __ddiv_rn(__dsub_rn(x[1], __dmul_rn(d.tilt[2], s[2])), d.L[1]);
     s[0] = __ddiv_rn(__dsub_rn(__dsub_rn(x[0], __dmul_rn(d.tilt[0], s[1])), __dmul_rn(d.tilt[1], s[2])), d.L[0]);

@@ -175,6 +175,7 @@ struct SamplerArgs {
     double sig_u;
     double glx[kGL], glw[kGL];  // Gauss-Legendre nodes and weights on [-1, 1]
     double *tri_tab;            // lattice-sum tables of the tilted systems (SampScratch::tab0)
+    int has_tri;                // 1: some system of the context has a tilted cell
 };
 // per-system sampler scratch: 1D lattice sums T0, T2, T4 per Gaussian and
 // axis, and the chain's start state (paper MH sampler).  A tilted system

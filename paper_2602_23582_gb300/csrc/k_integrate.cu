@@ -144,7 +144,7 @@ k_box_half(DevSys *sys, int S, const IntegArgs ia, const double *__restrict__ sy
             d.w[lane] = Ln / n;
             // tilt per cell (a tilted cell is held fixed: Ln = L)
             const int nn = __shfl_sync(0x7u, n, lane == 0 ? 1 : 2);
-            d.tw[lane] = d.tilt[lane] / nn;
+            d.tw[lane] = d.tri ? d.tilt[lane] / nn : 0.0;
         }
         const double L0 = __shfl_sync(0xffffffffu, Ln, 0), L1 = __shfl_sync(0xffffffffu, Ln, 1),
                      L2 = __shfl_sync(0xffffffffu, Ln, 2);

@@ -23,13 +23,13 @@ namespace rbsog {
 
 namespace {
 
-constexpr int QCAP = 64;      // FP64 kernel: per-lane queue (power of two); pending <= 32 before a batch
+constexpr int QCAP = 64;      // FP64 kernel: the warp's hit queue (power of two; < 32 pending before a push of <= 32)
 constexpr int kMaxPlane = 32; // neighbour cells of one dz plane (25 for cells of r_c/2)
 constexpr int kMaxNb = 128;   // neighbour cells of the stencil (125 for cells of r_c/2)
 
 size_t pair_smem(int precision)
 {
-    return (size_t)kPairWarps * (QCAP * 32 * sizeof(unsigned) + kMaxPlane * 16);
+    return (size_t)kPairWarps * (QCAP * sizeof(uint2) + kMaxPlane * 16);
 }
 
 __device__ __forceinline__ float ex2f(float x)
@@ -553,14 +553,17 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
 // ---------------------------------------------------------------------------
 // FP64 kernel: one warp per (32-atom group of a cell, dz plane 0..sub of the
 // half stencil, quarter of the plane's cells); every pair evaluated once.
-// Lane = atom i of the group.  The candidate atoms of the plane's cells are
-// read with warp-broadcast loads and tested in FP32 (cell-local coordinates,
-// r^2 < 1.00001 r_c^2, different molecules); the hits are queued per lane and
-// evaluated in FP64 in rounds where every lane with an atom has one, with the
-// exact cutoff test r^2 < r_c^2 in FP64.  On plane 0 the home cell
+// Lane = atom i of the group for the candidate test: the candidate atoms of
+// the plane's cells are read with warp-broadcast loads and tested in FP32
+// (cell-local coordinates, r^2 < 1.00001 r_c^2, different molecules); the hits
+// (i, j) of all lanes go to one queue of the warp in lane order, and every 32
+// of them are evaluated in FP64 with one pair per lane (the FP64 pipe of this
+// part takes a warp instruction's time whatever the number of active lanes),
+// with the exact cutoff test r^2 < r_c^2 in FP64.  On plane 0 the home cell
 // contributes its atoms after i (cell-sorted order), and of the other cells
-// those with dy > 0, or dy = 0 and dx > 0.  The force on i is summed in
-// registers, the force on j added per hit; both as two-word fixed point.
+// those with dy > 0, or dy = 0 and dx > 0.  The forces on i and j are added
+// per pair as two-word fixed point (exact, so the order of the adds does not
+// matter).
 // ---------------------------------------------------------------------------
 template <bool EN>
 __global__ void __launch_bounds__(32 * kPairWarps)
@@ -571,8 +574,8 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
-    unsigned *q = reinterpret_cast<unsigned *>(smem) + warp * QCAP * 32;
-    double2 *offp = reinterpret_cast<double2 *>(smem + kPairWarps * QCAP * 32 * sizeof(unsigned)) + warp * kMaxPlane;
+    uint2 *q = reinterpret_cast<uint2 *>(smem) + warp * QCAP;
+    double2 *offp = reinterpret_cast<double2 *>(smem + kPairWarps * QCAP * sizeof(uint2)) + warp * kMaxPlane;
     const int span = 2 * sub + 1, nparts = sub + 1;
     // unit = (work item, dz plane, quarter): the quarter takes every kF64Split-th
     // cell of the plane, so that small systems still fill the SMs' FP64 pipes
@@ -608,45 +611,41 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
         const int i0 = start[gc] + 32 * item.y;
         const int ni = min(32, count[gc] - 32 * item.y);
         const bool vi = lane < ni;
-        double4 pi = make_double4(0, 0, 0, 0);
         float4 pif = make_float4(1e15f, 1e15f, 1e15f, 0.f);
-        int moli = -0x7fffffff, ti = 0;
+        int moli = -0x7fffffff;
         if (vi) {
-            pi = posd[i0 + lane];
             pif = posf[i0 + lane];
-            const int2 ai = aux[i0 + lane];
-            moli = ai.x;
-            ti = ai.y;
+            moli = aux[i0 + lane].x;
         }
-        const double2 *ljrow = lj + d.lj0 + ti * d.ntypes;
-        const double qike = pc.ke * pi.w;
         const float rc2f = pc.rc2f;
-        double fix = 0.0, fiy = 0.0, fiz = 0.0;
         unsigned long long *const hx = ffix, *const hy = ffix + N, *const hz = ffix + 2 * (size_t)N;
         unsigned long long *const lx = ffix + 3 * (size_t)N, *const ly = ffix + 4 * (size_t)N,
                            *const lz = ffix + 5 * (size_t)N;
+        // one queue of the warp's hits (entry: j | cell code << 25, i's lane),
+        // filled in lane order; every 32 entries are evaluated with one pair
+        // per lane, so the FP64 instructions run with full lanes
         int head = 0, tail = 0;
-
-        auto eval_one = [&](unsigned e) {
-            const int j = (int)(e & 0x1ffffffu);
-            const double2 o = offp[e >> 25];
-            const double4 pj = posd[j];
-            const double dx = (pi.x - o.x) - pj.x, dy = (pi.y - o.y) - pj.y, dz = (pi.z - oz) - pj.z;
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (!(r2 < pc.rc2)) return;                // the exact cutoff, in FP64
-            const double2 lab = __ldg(&ljrow[aux[j].y]);
-            const double f = pair_eval_d<EN>(pc, dx, dy, dz, r2, qike * pj.w, lab, acc);
-            fix = fma(f, dx, fix);
-            fiy = fma(f, dy, fiy);
-            fiz = fma(f, dz, fiz);
-            add_fix2(hx + j, lx + j, -f * dx);
-            add_fix2(hy + j, ly + j, -f * dy);
-            add_fix2(hz + j, lz + j, -f * dz);
-        };
-        auto pop = [&]() {
-            const int slot = (head & (QCAP - 1)) * 32 + lane;
-            ++head;
-            eval_one(q[slot]);
+        auto eval_round = [&](int n) {
+            if (lane < n) {
+                const uint2 e = q[(head + lane) & (QCAP - 1)];
+                const int j = (int)(e.x & 0x1ffffffu), ii = i0 + (int)e.y;
+                const double2 o = offp[e.x >> 25];
+                const double4 pa = posd[ii], pj = posd[j];
+                const double dx = (pa.x - o.x) - pj.x, dy = (pa.y - o.y) - pj.y, dz = (pa.z - oz) - pj.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < pc.rc2) {                     // the exact cutoff, in FP64
+                    const double2 lab = __ldg(&lj[d.lj0 + aux[ii].y * d.ntypes + aux[j].y]);
+                    const double f = pair_eval_d<EN>(pc, dx, dy, dz, r2, pc.ke * pa.w * pj.w, lab, acc);
+                    add_fix2(hx + ii, lx + ii, f * dx);
+                    add_fix2(hy + ii, ly + ii, f * dy);
+                    add_fix2(hz + ii, lz + ii, f * dz);
+                    add_fix2(hx + j, lx + j, -f * dx);
+                    add_fix2(hy + j, ly + j, -f * dy);
+                    add_fix2(hz + j, lz + j, -f * dz);
+                }
+            }
+            head += n;
+            __syncwarp();
         };
 
         const int gz = wrapi(cz + part, n2);
@@ -660,38 +659,28 @@ k_pair_f64(const DevSys *__restrict__ sys, const int *__restrict__ cell_sys, con
                 ddx = c % span - sub; ddy = c / span - sub;
             }
             const int g = d.cell0 + wrapi(cx + ddx, n0) + n0 * (wrapi(cy + ddy, n1) + n1 * gz);
-            int j0 = start[g];
+            const int j0 = start[g];
             const int nj = count[g];
             const double2 o = offp[c];
             const float xi = pif.x - (float)o.x, yi = pif.y - (float)o.y, zi = pif.z - (float)oz;
             const unsigned code = (unsigned)c << 25;
             // home cell: the atoms after i in cell-sorted order
             const int jmin = (part == 0 && c == 0) ? i0 + lane + 1 : 0;
-            for (int jb = 0; jb < nj; jb += 32) {
-                const int je = min(jb + 32, nj);
-                for (int j = jb; j < je; ++j) {
-                    const float4 pj = posf[j0 + j];
-                    const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if (vi && r2 < rc2f && __float_as_int(pj.w) != moli && j0 + j >= jmin) {
-                        q[(tail & (QCAP - 1)) * 32 + lane] = (unsigned)(j0 + j) | code;
-                        ++tail;
-                    }
-                }
-                const int mn = __reduce_min_sync(0xffffffffu, vi ? tail - head : QCAP);
-                for (int t = 0; t < mn; ++t)
-                    if (vi) pop();
-                while (__reduce_max_sync(0xffffffffu, tail - head) > QCAP - 32)
-                    if (tail > head) pop();
+            for (int j = 0; j < nj; ++j) {
+                const float4 pj = posf[j0 + j];
+                const float dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool hit = vi && r2 < rc2f && __float_as_int(pj.w) != moli && j0 + j >= jmin;
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit)
+                    q[(tail + __popc(m & ((1u << lane) - 1u))) & (QCAP - 1)] =
+                        make_uint2((unsigned)(j0 + j) | code, (unsigned)lane);
+                tail += __popc(m);
+                __syncwarp();
+                if (tail - head >= 32) eval_round(32);
             }
         }
-        while (__any_sync(0xffffffffu, tail > head))
-            if (tail > head) pop();
-        if (vi) {
-            add_fix2(hx + i0 + lane, lx + i0 + lane, fix);
-            add_fix2(hy + i0 + lane, ly + i0 + lane, fiy);
-            add_fix2(hz + i0 + lane, lz + i0 + lane, fiz);
-        }
+        if (tail > head) eval_round(tail - head);
     }
     // the warp's record (Ucoul, Ulj, Wc, Wl, W): FP64 warp sums
     double v = 0.0;

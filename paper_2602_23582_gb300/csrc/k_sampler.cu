@@ -432,55 +432,7 @@ k_samp_prop(const DevSys *sys, const SamplerArgs sa, int adv, SampScratch *ss, i
     const int P = sa.P;
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
     uint64_t wds[4];
-    if (d.tri) {
-        int m[3];
-        double w = 0.0, g = 0.0;
-        if (t == P) {
-            draw4(sa.seed, d.rng_id, step, PUR_START, 0, wds);
-            exact_draw_tri_warp(sa, d, ss[s], wds, m);
-        } else {
-            draw4(sa.seed, d.rng_id, step, PUR_PROPOSAL, (uint64_t)t, wds);
-            double z = 0.0;
-            if (lane < 3) {
-                const double u1 = u01(lane < 2 ? wds[0] : wds[2]), u2 = u01(lane < 2 ? wds[1] : wds[3]);
-                const double rr = sqrt(-2.0 * log(u1)), ang = kTwoPi * u2;
-                z = rr * (lane == 1 ? sin(ang) : cos(ang));
-            }
-            const double z0 = __shfl_sync(0xffffffffu, z, 0), z1 = __shfl_sync(0xffffffffu, z, 1),
-                         z2 = __shfl_sync(0xffffffffu, z, 2);
-            // gamma = h^T (sigma_u z)
-            const double g0 = d.L[0] * (z0 * sa.sig_u);
-            const double g1 = d.L[1] * (z1 * sa.sig_u) + d.tilt[0] * (z0 * sa.sig_u);
-            const double g2 = d.L[2] * (z2 * sa.sig_u) + (d.tilt[1] * (z0 * sa.sig_u) + d.tilt[2] * (z1 * sa.sig_u));
-            m[0] = (int)floor(g0 + 0.5);
-            m[1] = (int)floor(g1 + 0.5);
-            m[2] = (int)floor(g2 + 0.5);
-        }
-        if (t == P || m[0] || m[1] || m[2]) {
-            double pr, pnr;
-            targets_tri_warp(sa, d, m, pr, pnr);
-            const double q = qprop_tri_warp(sa, d, m);
-            w = pr / q;
-            g = pnr / pr;
-        }
-        if (lane == 0) {
-            if (t == P) {
-                SampScratch &sc = ss[s];
-                sc.start_m[0] = m[0]; sc.start_m[1] = m[1]; sc.start_m[2] = m[2];
-                sc.start_w = w;
-                sc.start_g = g;
-            } else {
-                const size_t k = (size_t)s * P + t;
-                pm[k] = make_int4(m[0], m[1], m[2], 0);
-                pw[k] = w;
-                pg[k] = g;
-                draw4(sa.seed, d.rng_id, step, PUR_ACCEPT, (uint64_t)t, wds);
-                pu[k] = u01(wds[0]);
-                pun[k] = u01(wds[1]);
-            }
-        }
-        return;
-    }
+    if (d.tri) return;                        // tilted cells: k_samp_prop_tri
     if (t == P) {
         double sr, snr;
         load_sums(sa, ss[s], L, sh, sr, snr);
@@ -528,6 +480,67 @@ k_samp_prop(const DevSys *sys, const SamplerArgs sa, int adv, SampScratch *ss, i
         pu[k] = u01(wds[0]);
         pun[k] = u01(wds[1]);
     }
+}
+
+// Steps 2-3 for the tilted cells (DevSys::tri), a kernel of its own so that
+// the orthorhombic one keeps its code: block (s, t) as in k_samp_prop.
+__global__ void __launch_bounds__(32)
+k_samp_prop_tri(const DevSys *sys, const SamplerArgs sa, int adv, SampScratch *ss, int4 *__restrict__ pm,
+                double *__restrict__ pw, double *__restrict__ pg, double *__restrict__ pu, double *__restrict__ pun)
+{
+    const int s = blockIdx.x, t = blockIdx.y, lane = lane_id();
+    const DevSys &d = sys[s];
+    if ((d.flags & FLAG_BOX) || live_n(d) == 0 || !d.tri) return;
+    const uint64_t step = d.step + (uint64_t)adv;
+    const int P = sa.P;
+    uint64_t wds[4];
+    int m[3];
+    double w = 0.0, g = 0.0;
+    if (t == P) {
+        draw4(sa.seed, d.rng_id, step, PUR_START, 0, wds);
+        exact_draw_tri_warp(sa, d, ss[s], wds, m);
+    } else {
+        draw4(sa.seed, d.rng_id, step, PUR_PROPOSAL, (uint64_t)t, wds);
+        double z = 0.0;
+        if (lane < 3) {
+            const double u1 = u01(lane < 2 ? wds[0] : wds[2]), u2 = u01(lane < 2 ? wds[1] : wds[3]);
+            const double rr = sqrt(-2.0 * log(u1)), ang = kTwoPi * u2;
+            z = rr * (lane == 1 ? sin(ang) : cos(ang));
+        }
+        const double z0 = __shfl_sync(0xffffffffu, z, 0), z1 = __shfl_sync(0xffffffffu, z, 1),
+                     z2 = __shfl_sync(0xffffffffu, z, 2);
+        // gamma = h^T (sigma_u z)
+        const double g0 = d.L[0] * (z0 * sa.sig_u);
+        const double g1 = d.L[1] * (z1 * sa.sig_u) + d.tilt[0] * (z0 * sa.sig_u);
+        const double g2 = d.L[2] * (z2 * sa.sig_u) + (d.tilt[1] * (z0 * sa.sig_u) + d.tilt[2] * (z1 * sa.sig_u));
+        m[0] = (int)floor(g0 + 0.5);
+        m[1] = (int)floor(g1 + 0.5);
+        m[2] = (int)floor(g2 + 0.5);
+    }
+    if (t == P || m[0] || m[1] || m[2]) {
+        double pr, pnr;
+        targets_tri_warp(sa, d, m, pr, pnr);
+        const double q = qprop_tri_warp(sa, d, m);
+        w = pr / q;
+        g = pnr / pr;
+    }
+    if (lane == 0) {
+        if (t == P) {
+            SampScratch &sc = ss[s];
+            sc.start_m[0] = m[0]; sc.start_m[1] = m[1]; sc.start_m[2] = m[2];
+            sc.start_w = w;
+            sc.start_g = g;
+        } else {
+            const size_t k = (size_t)s * P + t;
+            pm[k] = make_int4(m[0], m[1], m[2], 0);
+            pw[k] = w;
+            pg[k] = g;
+            draw4(sa.seed, d.rng_id, step, PUR_ACCEPT, (uint64_t)t, wds);
+            pu[k] = u01(wds[0]);
+            pun[k] = u01(wds[1]);
+        }
+    }
+    return;
 }
 
 // scratch per system: [P] proposal modes (int4) + w, g, u_r, u_nr (double)
@@ -858,8 +871,11 @@ void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int
                     int Dcap, cudaStream_t st)
 {
     k_samp_sums<<<dim3(b.S, 3 * sa.M), 32, 0, st>>>(b.sys, sa, ss);
-    if (sa.kind == 0)
+    if (sa.kind == 0) {
         k_samp_prop<<<dim3(b.S, sa.P + 1), 32, 0, st>>>(b.sys, sa, adv, ss, pm, pw, pg, pu, pun);
+        if (sa.has_tri)
+            k_samp_prop_tri<<<dim3(b.S, sa.P + 1), 32, 0, st>>>(b.sys, sa, adv, ss, pm, pw, pg, pu, pun);
+    }
     k_sampler<<<b.S, 256, sampler_smem(sa.P), st>>>(b.sys, sa, adv, mr, mnr, D, cr, cnr, pm, pw, pg, pu, pun, ss,
                                                     Dcap);
 }

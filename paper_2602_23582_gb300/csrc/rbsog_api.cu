@@ -249,6 +249,7 @@ void fill_sampler_args(const rbsog_params &P, const std::vector<double> &wt, con
         sa.glw[i] = sa.glw[n - 1 - i] = 2.0 / ((1.0 - x * x) * dpn * dpn);
     }
     sa.tri_tab = nullptr;
+    sa.has_tri = 0;
 }
 
 // Range |m_a| <= mm[a] of the lattice sums of a tilted cell: the box around
@@ -1139,6 +1140,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                        cudaMemcpy(d_tri, tri_sys.data(), sizeof(int) * tri_sys.size(), cudaMemcpyHostToDevice) == cudaSuccess;
             if (!ok2) { free_ctx(c); return RBSOG_ENOMEM; }
             c->sa.tri_tab = c->tri_tab;
+            c->sa.has_tri = 1;
             launch_tri_tables(c->b, c->sa, c->samp, d_tri, (int)tri_sys.size(), mmx, c->st);
             e = cudaStreamSynchronize(c->st);
             if (e == cudaSuccess) e = cudaGetLastError();

@@ -402,3 +402,26 @@ def test_overfull_cell_is_reported_without_pair_work(prec):
     with pytest.raises(R.RbsogError) as e:
         R.Context([s], R.rbsog_default_params(10.0, precision=prec, cell_sub=1))
     assert e.value.status == -8
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("P", [1, 4096])
+def test_batch_size_extremes_match_oracle(kind, P):
+    # the smallest batch and the largest the library takes (4096 modes per
+    # chain; the i.i.d. sampler then holds up to 8192 distinct modes): modes
+    # bit-exact, FP64 forces and virial parts within 1e-12
+    s = W.random_charges(n=300, box=(30.0, 31.0, 32.0), seed=13, min_dist=2.0, lj=True)
+    ctx, p = _ctx([s], R.RBSOG_FP64, sampler=kind, P=P)
+    op = _oracle_params(p)
+    F, res = ctx.step(3)
+    g = ctx.modes(0)
+    ctx.close()
+    mr, mn, _ = O.sample_modes(s.box, op, 3)
+    assert np.array_equal(g["mr"], mr) and np.array_equal(g["mnr"], mn)
+    ref = O.force_eval(s, op, 3)
+    r = res[0]
+    assert r["n_distinct_modes"] == int(ref["n_distinct"])
+    assert _rel(F, ref["F"]) < TOL64
+    assert _rel(r["virial_long_r"], ref["W_parts"][1]) < TOL64
+    assert _rel(r["virial_long_nr"], ref["W_parts"][2]) < TOL64
+    assert abs(r["coul_long"] - ref["coul_long"]) <= TOL64 * abs(ref["coul_long"])
