@@ -760,7 +760,7 @@ def main():
     # box_half .. finalize, one graph replay (three streams); lists with a skin
     # add the binning of rebuilt systems, the refresh of the others and their
     # cluster boxes
-    kernels_per_step = 15 + (3 if p.skin > 0 and prec == R.RBSOG_FP32 else 0)
+    kernels_per_step = 16 + (3 if p.skin > 0 and prec == R.RBSOG_FP32 else 0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == R.RBSOG_FP32 else "f64",

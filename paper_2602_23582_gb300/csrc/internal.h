@@ -270,12 +270,14 @@ void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, 
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
                         cudaStream_t st, int skin = 0);
 constexpr int kKinSplit = 8;   // kinetic partials per atom chunk (one per force-assembly block)
-// F = pair partials + long-range force + Fmol (molecule terms; null: none),
-// then (kick != 0) the second half kick p += dt/2 F, and the kinetic tensor
-// per kChunk / kKinSplit atoms: kin_part[chunk][kKinSplit][6] = sum p (x) p / m
-void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef,
-                     int Dcap, const double *Fmol, const IntegArgs &ia, int kick, double *kin_part,
-                     cudaStream_t st);
+// long-range force per atom (eq. f_approx) into Flr [3N] (beside the pair kernel)
+void launch_lr_fourier(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
+                       double *Flr, cudaStream_t st);
+// F = pair partials + Flr + Fmol (molecule terms; null: none), then (kick != 0)
+// the second half kick p += dt/2 F, and the kinetic tensor per kChunk /
+// kKinSplit atoms: kin_part[chunk][kKinSplit][6] = sum p (x) p / m
+void launch_force_assembly(const Batch &b, const AtomArrays &a, int precision, const double *Flr,
+                           const double *Fmol, const IntegArgs &ia, int kick, double *kin_part, cudaStream_t st);
 // per-system reduction of every partial into sysred[S x kRed]; advances *step
 constexpr int kRed = 64;
 void launch_finalize(const Batch &b, const double *pair_part, const double *est, int est_blocks, int P,

@@ -242,40 +242,31 @@ void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_s
         b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho, coef, est);
 }
 
-// Force assembly: F_i = sum over the pair kernel's partials (fixed order)
-// + q_i sum_d alpha_d k_d Im(e^{-i k_d.r_i} rho_d) (eq. f_approx) + the
-// molecule terms of k_mol.  Blocks of kLrAtoms atoms of
-// one chunk (grid: chunks x kChunk / kLrAtoms); the system's mode
-// coefficients are staged in shared memory in tiles.  The same blocks then
-// give the atoms their second half kick (velocity Verlet B step) and sum the
-// kinetic tensor p (x) p / m of their atoms, one partial per block.
+// Long-range force (eq. f_approx): F^lr_i = q_i sum_d alpha_d k_d
+// Im(e^{-i k_d.r_i} rho_d), written per atom to Flr.  It needs the modes'
+// coefficients and the atoms' positions only, so it runs on the sampler's
+// stream beside the pair kernel.  Blocks of kLrAtoms atoms of one chunk
+// (grid: chunks x kChunk / kLrAtoms); the system's mode coefficients are
+// staged in shared memory in tiles.
 constexpr int kModeTile = 256;
 constexpr int kLrAtoms = kChunk / kKinSplit;
 
 template <bool F32>
 __global__ void __launch_bounds__(kLrAtoms)
-k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
-           const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
-           const double *__restrict__ q, const ModeCoef *__restrict__ coef_all, int Dcap,
-           const int *__restrict__ pos_sorted, unsigned long long *__restrict__ ffix, int N,
-           const double *__restrict__ Fmol, double *__restrict__ F, double *__restrict__ mom,
-           const double *__restrict__ inv_m, double kick, double mvv2e, double *__restrict__ kin_part)
+k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
+             const uint4 *__restrict__ su, const double *__restrict__ r, const double *__restrict__ q,
+             const ModeCoef *__restrict__ coef_all, int Dcap, double *__restrict__ Flr)
 {
     __shared__ float4 tf[F32 ? kModeTile : 1];      // a (FP32)
     __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
     __shared__ int4 tm[kModeTile];
     __shared__ double td[F32 ? 1 : kModeTile][5];
-    __shared__ double red[6 * (kLrAtoms + 1) + 24];
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int nD = d.nD, a0 = chunk_a0[c], na = min(kChunk, live_n(d) - (a0 - d.atom0));
     const ModeCoef *coef = coef_all + (size_t)s * Dcap;
     const int k = blockIdx.y * kLrAtoms + threadIdx.x;
-    double *kin = kin_part + ((size_t)c * kKinSplit + blockIdx.y) * 6;
-    if ((int)(blockIdx.y * kLrAtoms) >= na) {         // whole block beyond the chunk
-        if (threadIdx.x < 6) kin[threadIdx.x] = 0.0;
-        return;
-    }
+    if ((int)(blockIdx.y * kLrAtoms) >= na) return;   // whole block beyond the chunk
     const bool act = k < na;
     const int i = a0 + (act ? k : 0);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -309,14 +300,14 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
             for (int u = 0; u < nt; ++u) {
                 const int4 mm = tm[u];
                 const int m[3] = {mm.x, mm.y, mm.z};
-                const float4 a = tf[u];
+                const float4 av = tf[u];
                 const float2 rr = tr[u];
                 float sn, cs;
                 phase_sincos_f(m, v, sn, cs);
                 const float g = rr.y * cs - rr.x * sn;
-                fx = fmaf(a.x, g, fx);
-                fy = fmaf(a.y, g, fy);
-                fz = fmaf(a.z, g, fz);
+                fx = fmaf(av.x, g, fx);
+                fy = fmaf(av.y, g, fy);
+                fz = fmaf(av.z, g, fz);
             }
         } else {
             for (int u = 0; u < nt; ++u) {
@@ -331,9 +322,57 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
             }
         }
     }
-    double k6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (act) {
         const double qi = q[i];
+        if (F32) {
+            Flr[3 * i] = qi * (double)fx;
+            Flr[3 * i + 1] = qi * (double)fy;
+            Flr[3 * i + 2] = qi * (double)fz;
+        } else {
+            Flr[3 * i] = qi * gx;
+            Flr[3 * i + 1] = qi * gy;
+            Flr[3 * i + 2] = qi * gz;
+        }
+    }
+}
+
+void launch_lr_fourier(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
+                       double *Flr, cudaStream_t st)
+{
+    const dim3 grid(b.nchunks, kChunk / kLrAtoms);
+    if (precision == 1)
+        k_lr_fourier<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr);
+    else
+        k_lr_fourier<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr);
+}
+
+// Force assembly: F_i = the pair kernel's fixed-point sum (read and cleared)
+// + the long-range force Flr (k_lr_fourier) + the molecule terms of k_mol, in
+// that order.  The same blocks (kLrAtoms atoms of one chunk) then give the
+// atoms their second half kick (velocity Verlet B step) and sum the kinetic
+// tensor p (x) p / m of their atoms, one partial per block.
+template <bool F32>
+__global__ void __launch_bounds__(kLrAtoms)
+k_force_assembly(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
+                 const double *__restrict__ Flr, const int *__restrict__ pos_sorted,
+                 unsigned long long *__restrict__ ffix, int N, const double *__restrict__ Fmol,
+                 double *__restrict__ F, double *__restrict__ mom, const double *__restrict__ inv_m, double kick,
+                 double mvv2e, double *__restrict__ kin_part)
+{
+    __shared__ double red[6 * (kLrAtoms + 1) + 24];
+    const int c = blockIdx.x, s = chunk_sys[c];
+    const DevSys &d = sys[s];
+    const int a0 = chunk_a0[c], na = min(kChunk, live_n(d) - (a0 - d.atom0));
+    const int k = blockIdx.y * kLrAtoms + threadIdx.x;
+    double *kin = kin_part + ((size_t)c * kKinSplit + blockIdx.y) * 6;
+    if ((int)(blockIdx.y * kLrAtoms) >= na) {         // whole block beyond the chunk
+        if (threadIdx.x < 6) kin[threadIdx.x] = 0.0;
+        return;
+    }
+    const bool act = k < na;
+    const int i = a0 + (act ? k : 0);
+    double k6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (act) {
         const int ks = pos_sorted[i];
         double f[3] = {0.0, 0.0, 0.0};
         // fixed-point pair forces (FP64: two words), cleared for the next evaluation
@@ -350,15 +389,9 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
                 ffix[(size_t)(3 + a) * N + ks] = 0ull;
             }
         }
-        if (F32) {
-            f[0] += qi * (double)fx;
-            f[1] += qi * (double)fy;
-            f[2] += qi * (double)fz;
-        } else {
-            f[0] += qi * gx;
-            f[1] += qi * gy;
-            f[2] += qi * gz;
-        }
+        f[0] += Flr[3 * i];
+        f[1] += Flr[3 * i + 1];
+        f[2] += Flr[3 * i + 2];
         if (Fmol) {
             f[0] += Fmol[3 * i];
             f[1] += Fmol[3 * i + 1];
@@ -382,19 +415,17 @@ k_lr_force(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, co
     block_reduce_lanes<6, kLrAtoms>(k6, red, kin);
 }
 
-void launch_lr_force(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
-                     const double *Fmol, const IntegArgs &ia, int do_kick, double *kin_part, cudaStream_t st)
+void launch_force_assembly(const Batch &b, const AtomArrays &a, int precision, const double *Flr,
+                           const double *Fmol, const IntegArgs &ia, int do_kick, double *kin_part, cudaStream_t st)
 {
     const double kick = do_kick ? 0.5 * ia.dt * ia.ftm2v : 0.0, mvv2e = 1.0 / ia.ftm2v;
     const dim3 grid(b.nchunks, kChunk / kLrAtoms);
     if (precision == 1)
-        k_lr_force<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                    coef, Dcap, a.rank, a.ffix, b.N, Fmol, a.F,
-                                                    a.p, ia.inv_m, kick, mvv2e, kin_part);
+        k_force_assembly<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, Flr, a.rank, a.ffix, b.N,
+                                                          Fmol, a.F, a.p, ia.inv_m, kick, mvv2e, kin_part);
     else
-        k_lr_force<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                     coef, Dcap, a.rank, a.ffix, b.N, Fmol,
-                                                     a.F, a.p, ia.inv_m, kick, mvv2e, kin_part);
+        k_force_assembly<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, Flr, a.rank, a.ffix, b.N,
+                                                           Fmol, a.F, a.p, ia.inv_m, kick, mvv2e, kin_part);
 }
 
 // Shared-proposal estimator of the non-radial virial (sec. 3.2, the

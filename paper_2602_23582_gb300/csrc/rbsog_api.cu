@@ -78,6 +78,7 @@ struct rbsog_ctx {
     DevSys *sys = nullptr;
     double *r = nullptr, *p = nullptr, *F = nullptr, *q = nullptr, *mass = nullptr;
     double *Fmol = nullptr;     // molecule-term forces, added by the force assembly
+    double *Flr = nullptr;      // long-range forces (beside the pair kernel), added by the force assembly
     int *type = nullptr, *mol = nullptr, *atom_sys = nullptr, *cell = nullptr, *rank = nullptr;
     float4 *locf = nullptr, *pos4 = nullptr;
     double4 *locd = nullptr, *posd = nullptr;
@@ -293,10 +294,10 @@ void fork_sampler(rbsog_ctx *c, int adv)
     if (c->timing) cudaEventRecord(c->ev_join, c->st2);
 }
 
-// Structure factor and estimator on the second stream, after the sampler and
-// the binning (which writes the fixed-point coordinates they read): they need
-// neither the cell lists nor the pair forces, so they run beside the list
-// build and the pair evaluation.
+// Structure factor, estimator and long-range force on the second stream,
+// after the sampler and the binning (which writes the fixed-point coordinates
+// they read): they need neither the cell lists nor the pair forces, so they
+// run beside the list build and the pair evaluation.
 void enqueue_kspace(rbsog_ctx *c, cudaStream_t st)
 {
     launch_sk(c->b, c->a, c->prm.precision, c->D, c->Dcap, c->sk_part, st);
@@ -304,6 +305,8 @@ void enqueue_kspace(rbsog_ctx *c, cudaStream_t st)
     launch_estimate(c->b, c->first_chunk, c->nchunk_sys, c->D, c->cr, c->cnr, c->Dcap, c->prm.P, c->prm.ke,
                     c->sk_part, c->rho, c->coef, c->est, st);
     record(c, "estimate");
+    launch_lr_fourier(c->b, c->a, c->prm.precision, c->coef, c->Dcap, c->Flr, st);
+    record(c, "lr_force");
 }
 
 void fork_kspace(rbsog_ctx *c)
@@ -372,8 +375,8 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     record(c, "sampler_join");
     if (c->timing) enqueue_kspace(c, c->st);
     if (mol && c->mol_late) cudaStreamWaitEvent(c->st, c->ev_join3, 0);
-    launch_lr_force(c->b, c->a, prec, c->coef, c->Dcap, mol ? c->Fmol : nullptr, c->ia, kick, c->kin_part, c->st);
-    record(c, "lr_force_kick");
+    launch_force_assembly(c->b, c->a, prec, c->Flr, mol ? c->Fmol : nullptr, c->ia, kick, c->kin_part, c->st);
+    record(c, "assembly_kick");
     cudaStreamWaitEvent(c->st, c->ev_join4, 0);
     launch_finalize(c->b, c->pair_red, c->est, estimate_blocks(c->Dcap), c->prm.P, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
@@ -944,7 +947,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->b_start, b_start) && upload(c, c->a_start, a_start) && upload(c, c->e_start, e_start) &&
                   upload(c, c->bonds, bonds) && upload(c, c->angles, angles) && upload(c, c->excl, excl) &&
                   upload(c, c->bk, bk) && upload(c, c->br0, br0) && upload(c, c->ak, ak) && upload(c, c->at0, at0) &&
-                  upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
+                  upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->Flr, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
                   dalloc(c, c->pair_part, (size_t)item_cap * pair_rec_num(P.precision, P.cell_sub) /
