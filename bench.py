@@ -192,27 +192,38 @@ def oracle_npt(O, s, P=100, coupling=0):
     the short range over cell lists (bit-identical to the all-pairs
     definition), the paper's MH sampler, Langevin NPT with the library's
     defaults (dt 0.5 fs, 300 K, 1 atm, 0.1 ps / 0.5 ps, box masses from
-    4.5e-5 bar^-1).  Returns (params, integrator settings, state after the
-    priming evaluation at counter 0)."""
+    4.5e-5 bar^-1; coupling 2: the box held fixed; a triclinic cell is held
+    fixed and stepped by the oracle's fixed-cell integrator).  Returns
+    advance(step0, n): n steps after counter step0, from the state after the
+    priming evaluation at counter 0."""
     p = O.Params.row2(P=P, short_cells=1)
+    vel = getattr(s, "vel", None)
+    mom = np.zeros_like(s.pos) if vel is None else vel * s.mass[:, None]
+    tilt = tuple(getattr(s, "tilt", (0.0, 0.0, 0.0)))
+    if any(t != 0.0 for t in tilt):
+        cell = O.TriCell(O.tilted_box(s.box, tilt), p)
+        ig = O.Integ(dt=0.5, T=300.0, gamma=1.0 / 100.0, coupling=2)
+        out = O.force_eval_h(s, p, 0, cell)
+        st = dict(r=s.pos.copy(), p=mom, F=out["F"], W=out["W"].reshape(-1).copy())
+        return lambda k0, n: O.nvt_run_h(s, p, ig, cell, st, k0, n)
     kap = 4.5e-5 * 1.01325 * NKTV2P
     om = 2.0 * math.pi / 500.0
     V = float(np.prod(s.box))
     if coupling == 0:
         Mbox = (9.0 * V * O.FTM2V / (kap * s.box[0] ** 2 * om ** 2), 0.0, 0.0)
-    else:
+    elif coupling == 1:
         Mbox = (4.0 * V * O.FTM2V / (kap * s.box[0] ** 2 * om ** 2),
                 1.0 * V * O.FTM2V / (kap * s.box[2] ** 2 * om ** 2), 0.0)
+    else:
+        Mbox = (0.0, 0.0, 0.0)
     ig = O.Integ(dt=0.5, T=300.0, Pext_atm=1.0, gamma=1.0 / 100.0, gamma_box=1.0 / 500.0,
                  coupling=coupling, Mbox=Mbox)
     out = O.force_eval(s, p, 0)
-    vel = getattr(s, "vel", None)
-    mom = np.zeros_like(s.pos) if vel is None else vel * s.mass[:, None]
     st = dict(r=s.pos.copy(), p=mom, L=s.box.copy(), ph=np.zeros(3), F=out["F"], W=out["W"].reshape(-1).copy())
-    return p, ig, st
+    return lambda k0, n: O.npt_run(s, p, ig, st, k0, n)
 
 
-def cpu_baseline(systems, budget_s=12.0):
+def cpu_baseline(systems, budget_s=12.0, coupling=0):
     """The FP64 oracle (cell-list short range, random-batch long range, the
     paper's sampler, Langevin NPT as the GPU arm) on the same workload: NPT
     steps on all host cores for about budget_s, then single-threaded."""
@@ -221,22 +232,23 @@ def cpu_baseline(systems, budget_s=12.0):
     cores = os.cpu_count() or 1
     O.set_threads(cores)
     t0 = time.perf_counter()
-    p, ig, st = oracle_npt(O, s)
+    advance = oracle_npt(O, s, coupling=coupling)
     t_prime = time.perf_counter() - t0
     steps = max(1, min(50, int(budget_s / max(t_prime, 1e-3))))
     t0 = time.perf_counter()
-    O.npt_run(s, p, ig, st, 0, steps)
+    advance(0, steps)
     dt_all = time.perf_counter() - t0
     threads = O.num_threads()
     O.set_threads(1)
     t0 = time.perf_counter()
-    O.npt_run(s, p, ig, st, steps, 1)
+    advance(steps, 1)
     dt_one = time.perf_counter() - t0
     O.set_threads(cores)
+    kind = {0: "isotropic Langevin NPT", 1: "semi-isotropic Langevin NPT", 2: "Langevin, box held fixed"}[coupling]
     return {"value": s.n * steps / dt_all, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{steps} isotropic Langevin NPT steps of the {s.n}-site workload on {threads} threads "
+            "sample": f"{steps} {kind} steps of the {s.n}-site workload on {threads} threads "
                       f"({dt_all:.1f} s), FP64, cell-list short range, P=100",
-            "single_thread": {"value": s.n / dt_one, "unit": UNIT, "sample": f"1 NPT step, {dt_one:.1f} s"},
+            "single_thread": {"value": s.n / dt_one, "unit": UNIT, "sample": f"1 step, {dt_one:.1f} s"},
             "cpu_model": cpu_model(), "nproc": cores}
 
 
@@ -381,13 +393,14 @@ def run_reference(args, rank, world):
     from oracle import oracle as O
     cores = os.cpu_count() or 1
     O.set_threads(cores)
-    coupling = 1 if args.workload == "membrane" else 0
-    p, ig, st = oracle_npt(O, s, P=args.P, coupling=coupling)
+    # the GPU arm holds the membrane slab's box and a triclinic cell fixed
+    coupling = 2 if args.workload in ("membrane", "water_sheared") else 0
+    advance = oracle_npt(O, s, P=args.P, coupling=coupling)
     budget = max(5.0, 90.0 / max(args.steps + args.warmup, 1))
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        O.npt_run(s, p, ig, st, k, 1)
+        advance(k, 1)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
@@ -399,7 +412,7 @@ def run_reference(args, rank, world):
             "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": desc, "engine": "FP64 CPU oracle (cell-list short range)",
+            "config": {"workload": desc, "engine": ("FP64 CPU oracle (all-pairs short range: its cell lists take orthorhombic boxes)" if any(getattr(s, "tilt", (0, 0, 0))) else "FP64 CPU oracle (cell-list short range)"),
                        "precision": "FP64", "parallelism": f"{O.num_threads()} host threads",
                        "integrator": "Langevin NPT, dt 0.5 fs, 300 K, 1 atm (the GPU arm's settings)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
@@ -578,10 +591,10 @@ def main():
     p = R.rbsog_default_params(10.0, precision=prec, thermo_every=args.thermo, P=args.P)
     if args.skin is not None:
         p.skin = args.skin
-    if args.workload == "membrane":
+    if args.workload in ("membrane", "water_sheared"):
         # the slab is 3x water's density: at 1 atm it expands without bound
         # (a gas after a few hundred steps), so its box is held at the
-        # configured size (Langevin NVT)
+        # configured size (Langevin NVT); a triclinic cell is held fixed
         p.coupling = R.RBSOG_COUPLE_FIXED
         desc = desc.replace("semi-isotropic", "box held fixed")
     # launch shapes for this size class from the project's autotuner (cell size
@@ -748,7 +761,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(systems)
+            cpu = cpu_baseline(systems, coupling=2 if p.coupling == R.RBSOG_COUPLE_FIXED else (1 if p.coupling == R.RBSOG_COUPLE_SEMI_ISO else 0))
         except Exception as ex:   # reported, not fatal
             cpu = {"error": str(ex)}
     served = None

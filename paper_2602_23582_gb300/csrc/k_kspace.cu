@@ -10,9 +10,9 @@
 // for the consistent split (w_l = w~_l s~_l^2 / 2, App. C).
 //
 // FP32 build: the phase m.s mod 1 is formed exactly in 32-bit integer
-// arithmetic on fixed-point fractional coordinates (s 2^32), then sincospif
-// on a reduced argument in [-1, 1); per-lane sums are compensated FP32,
-// lane/chunk sums FP64.  FP64 build: phases and sums in FP64.
+// arithmetic on fixed-point fractional coordinates (s 2^32), then its sine
+// and cosine from a 256-entry table and the remainder's short Taylor forms
+// (phase_sincos_f); per-lane sums are compensated FP32, lane/chunk sums FP64.  FP64 build: phases and sums in FP64.
 #include "internal.h"
 
 namespace rbsog {
@@ -34,11 +34,38 @@ struct Kahan {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-__device__ __forceinline__ void phase_sincos_f(const int m[3], uint4 su, float &sn, float &cs)
+// Table of (cos, sin)(2 pi k / 256), k < 256, for phase_sincos_f; filled by
+// the threads of a block (sincospif of exact arguments k / 128), which must
+// synchronise before the first use.
+constexpr int kTurnTab = 256;
+__device__ __forceinline__ void fill_turn_table(float2 *tab)
 {
-    unsigned ph = (unsigned)m[0] * su.x + (unsigned)m[1] * su.y + (unsigned)m[2] * su.z;
-    float f = (float)(int)ph * 4.656612873077393e-10f;   // 2^-31: turns*2 in [-1, 1)
-    sincospif(f, &sn, &cs);
+    for (int k = threadIdx.x; k < kTurnTab; k += blockDim.x) {
+        float sn, cs;
+        sincospif((float)k * (1.0f / 128.0f), &sn, &cs);
+        tab[k] = make_float2(cs, sn);
+    }
+}
+
+// sin and cos of 2 pi (m . s) for fixed-point fractional coordinates s 2^32:
+// the phase ph = m . s 2^32 mod 2^32 is exact in 32-bit integer arithmetic;
+// ph = 2^24 k + r with k the nearest of 256 table angles and |r| <= 2^23, so
+// the remainder angle b = 2 pi r / 2^32 has |b| <= pi / 256, where sin b =
+// b - b^3/6 (next term below 2.4e-12) and cos b = 1 - b^2/2 (next term below
+// 9.4e-10) are exact to FP32 rounding; the angle-sum formulas combine them
+// with the table (about as accurate as sincospif, in a third of the
+// instructions).
+__device__ __forceinline__ void phase_sincos_f(const int m[3], uint4 su, const float2 *tab, float &sn, float &cs)
+{
+    const unsigned ph = (unsigned)m[0] * su.x + (unsigned)m[1] * su.y + (unsigned)m[2] * su.z;
+    const unsigned k = (ph + 0x800000u) >> 24;
+    const float b = (float)(int)(ph - (k << 24)) * 1.4629180792671596e-09f;   // 2 pi / 2^32
+    const float b2 = b * b;
+    const float sb = fmaf(b * b2, -0.16666667f, b);
+    const float cb = fmaf(b2, -0.5f, 1.0f);
+    const float2 t = tab[k & (kTurnTab - 1)];
+    sn = fmaf(t.y, cb, t.x * sb);
+    cs = fmaf(t.x, cb, -(t.y * sb));
 }
 
 __device__ __forceinline__ void phase_sincos_d(const int m[3], double sx, double sy, double sz,
@@ -59,6 +86,8 @@ __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, cons
 {
     __shared__ uint4 s_su[F32 ? kChunk : 1];
     __shared__ double s_sd[F32 ? 1 : kChunk][4];
+    __shared__ float2 s_tab[F32 ? kTurnTab : 1];
+    if (F32) fill_turn_table(s_tab);
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
     for (int k = tid; k < na; k += blockDim.x) {
         if (F32) {
@@ -88,7 +117,7 @@ __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, cons
             for (int k = lane; k < na; k += 32) {
                 uint4 v = s_su[k];
                 float sn, cs;
-                phase_sincos_f(m, v, sn, cs);
+                phase_sincos_f(m, v, s_tab, sn, cs);
                 float qq = __uint_as_float(v.w);
                 kr.add(qq * cs);
                 ki.add(qq * sn);
@@ -261,12 +290,14 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
     __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
     __shared__ int4 tm[kModeTile];
     __shared__ double td[F32 ? 1 : kModeTile][5];
+    __shared__ float2 tab[F32 ? kTurnTab : 1];
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int nD = d.nD, a0 = chunk_a0[c], na = min(kChunk, live_n(d) - (a0 - d.atom0));
     const ModeCoef *coef = coef_all + (size_t)s * Dcap;
     const int k = blockIdx.y * kLrAtoms + threadIdx.x;
     if ((int)(blockIdx.y * kLrAtoms) >= na) return;   // whole block beyond the chunk
+    if (F32) fill_turn_table(tab);                    // used after the tile loop's barrier
     const bool act = k < na;
     const int i = a0 + (act ? k : 0);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -303,7 +334,7 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
                 const float4 av = tf[u];
                 const float2 rr = tr[u];
                 float sn, cs;
-                phase_sincos_f(m, v, sn, cs);
+                phase_sincos_f(m, v, tab, sn, cs);
                 const float g = rr.y * cs - rr.x * sn;
                 fx = fmaf(av.x, g, fx);
                 fy = fmaf(av.y, g, fy);
@@ -601,6 +632,8 @@ k_lrs_force(const double *__restrict__ r, const double *__restrict__ q, int n, d
 {
     __shared__ int4 tm[kModeTile];
     __shared__ double tc[kModeTile][5];
+    __shared__ float2 ttab[F32 ? kTurnTab : 1];
+    if (F32) fill_turn_table(ttab);                   // used after the tile loop's barrier
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = i < n;
     double sx = 0.0, sy = 0.0, sz = 0.0;
@@ -636,7 +669,7 @@ k_lrs_force(const double *__restrict__ r, const double *__restrict__ q, int n, d
             double sn, cs;
             if (F32) {
                 float s32, c32;
-                phase_sincos_f(mm, v, s32, c32);
+                phase_sincos_f(mm, v, ttab, s32, c32);
                 sn = s32; cs = c32;
             } else {
                 phase_sincos_d(mm, sx, sy, sz, sn, cs);
