@@ -668,57 +668,73 @@ k_sampler(DevSys *sys, const SamplerArgs sa, int adv, int *__restrict__ mr_out, 
     }
     __syncthreads();
 
-    // 4. chains, warp 0: a block of 32 states is loaded at once (one lane per
-    // state); the accept tests then run in order with the uniforms and weights
+    // 4. chains: the radial chain on warp 0 and the recalibration chain on
+    // warp 1, one block of 32 steps behind it (its proposals are the radial
+    // states), so that the two run side by side.  Within a block a lane holds
+    // one step's operands and the accept tests run in order with them
     // broadcast by shuffles, so every decision sees the same operands as a
     // sequential loop.
-    if (warp == 0 && sa.kind != 1) {
-        int cur = -1;                         // kind 0: proposal index of the current radial state
-        double wcur = start_w, gcur = 0.0;
-        int nacc = 0, nn = 0;
-        int ym0 = 0, ym1 = 0, ym2 = 0;        // current recalibration state
+    __shared__ int xs[2][32][3];              // radial states of a block (double buffer)
+    __shared__ double xg[2][32];              // and their g = P^nr / P^r
+    if (sa.kind != 1) {
+        const int nb = (P + 31) / 32;
+        int cur = -1, nacc = 0;               // warp 0: proposal index of the current radial state
+        double wcur = start_w;
+        int ym0 = 0, ym1 = 0, ym2 = 0, nn = 0;    // warp 1: current recalibration state
+        double gcur = 0.0;
         if (sa.kind == 2) { ym0 = nrstart_m[0]; ym1 = nrstart_m[1]; ym2 = nrstart_m[2]; gcur = nrstart_g; }
-        for (int t0 = 0; t0 < P; t0 += 32) {
-            const int t = t0 + lane, nt = min(32, P - t0);
-            const bool valid = t < P;
-            int m0, m1, m2;
-            double gt;
-            if (sa.kind == 0) {
-                const double u = valid ? pu_s[t] : 0.0, w = valid ? pw_s[t] : 0.0;
-                int mysrc = -1;
-                for (int j = 0; j < nt; ++j) {
-                    const double uj = __shfl_sync(0xffffffffu, u, j), wj = __shfl_sync(0xffffffffu, w, j);
-                    if (uj * wcur < wj) { cur = t0 + j; wcur = wj; ++nacc; }
-                    if (lane == j) mysrc = cur;
+        for (int bk = 0; bk <= nb; ++bk) {
+            if (warp == 0 && bk < nb) {
+                const int t0 = 32 * bk, t = t0 + lane, nt = min(32, P - t0);
+                const bool valid = t < P;
+                int m0, m1, m2;
+                double gt;
+                if (sa.kind == 0) {
+                    const double u = valid ? pu_s[t] : 0.0, w = valid ? pw_s[t] : 0.0;
+                    int mysrc = -1;
+                    for (int j = 0; j < nt; ++j) {
+                        const double uj = __shfl_sync(0xffffffffu, u, j), wj = __shfl_sync(0xffffffffu, w, j);
+                        if (uj * wcur < wj) { cur = t0 + j; wcur = wj; ++nacc; }
+                        if (lane == j) mysrc = cur;
+                    }
+                    int4 mm = make_int4(start_m[0], start_m[1], start_m[2], 0);
+                    gt = start_g;
+                    if (valid && mysrc >= 0) { mm = pm_s[mysrc]; gt = pg_s[mysrc]; }
+                    m0 = mm.x; m1 = mm.y; m2 = mm.z;
+                    if (valid) { mr[3 * t] = m0; mr[3 * t + 1] = m1; mr[3 * t + 2] = m2; }
+                } else {
+                    m0 = valid ? mr[3 * t] : 0; m1 = valid ? mr[3 * t + 1] : 0; m2 = valid ? mr[3 * t + 2] : 0;
+                    gt = valid ? pg_s[t] : 0.0;
                 }
-                int4 mm = make_int4(start_m[0], start_m[1], start_m[2], 0);
-                gt = start_g;
-                if (valid && mysrc >= 0) { mm = pm_s[mysrc]; gt = pg_s[mysrc]; }
-                m0 = mm.x; m1 = mm.y; m2 = mm.z;
-                if (valid) { mr[3 * t] = m0; mr[3 * t + 1] = m1; mr[3 * t + 2] = m2; }
-                if (t0 == 0) {                // y_0 = x_1: the first radial state
+                xs[bk & 1][lane][0] = m0; xs[bk & 1][lane][1] = m1; xs[bk & 1][lane][2] = m2;
+                xg[bk & 1][lane] = gt;
+            }
+            if (warp == 1 && bk >= 1) {
+                const int b1 = bk - 1, t0 = 32 * b1, t = t0 + lane, nt = min(32, P - t0);
+                const bool valid = t < P;
+                const int m0 = xs[b1 & 1][lane][0], m1 = xs[b1 & 1][lane][1], m2 = xs[b1 & 1][lane][2];
+                const double gt = xg[b1 & 1][lane];
+                if (b1 == 0 && sa.kind == 0) {   // y_0 = x_1: the first radial state
                     gcur = __shfl_sync(0xffffffffu, gt, 0);
                     ym0 = __shfl_sync(0xffffffffu, m0, 0);
                     ym1 = __shfl_sync(0xffffffffu, m1, 0);
                     ym2 = __shfl_sync(0xffffffffu, m2, 0);
                 }
-            } else {
-                m0 = valid ? mr[3 * t] : 0; m1 = valid ? mr[3 * t + 1] : 0; m2 = valid ? mr[3 * t + 2] : 0;
-                gt = valid ? pg_s[t] : 0.0;
+                const double un = valid ? pun_s[t] : 0.0;
+                int y0 = 0, y1 = 0, y2 = 0;
+                for (int j = 0; j < nt; ++j) {
+                    const double uj = __shfl_sync(0xffffffffu, un, j), gj = __shfl_sync(0xffffffffu, gt, j);
+                    const int c0 = __shfl_sync(0xffffffffu, m0, j), c1 = __shfl_sync(0xffffffffu, m1, j),
+                              c2 = __shfl_sync(0xffffffffu, m2, j);
+                    if (uj * gcur < gj) { ym0 = c0; ym1 = c1; ym2 = c2; gcur = gj; ++nn; }
+                    if (lane == j) { y0 = ym0; y1 = ym1; y2 = ym2; }
+                }
+                if (valid) { mnr[3 * t] = y0; mnr[3 * t + 1] = y1; mnr[3 * t + 2] = y2; }
             }
-            // recalibration chain: proposals are the radial states x_t
-            const double un = valid ? pun_s[t] : 0.0;
-            int y0 = 0, y1 = 0, y2 = 0;
-            for (int j = 0; j < nt; ++j) {
-                const double uj = __shfl_sync(0xffffffffu, un, j), gj = __shfl_sync(0xffffffffu, gt, j);
-                const int c0 = __shfl_sync(0xffffffffu, m0, j), c1 = __shfl_sync(0xffffffffu, m1, j),
-                          c2 = __shfl_sync(0xffffffffu, m2, j);
-                if (uj * gcur < gj) { ym0 = c0; ym1 = c1; ym2 = c2; gcur = gj; ++nn; }
-                if (lane == j) { y0 = ym0; y1 = ym1; y2 = ym2; }
-            }
-            if (valid) { mnr[3 * t] = y0; mnr[3 * t + 1] = y1; mnr[3 * t + 2] = y2; }
+            __syncthreads();
         }
-        if (lane == 0) { cnt_r = nacc; cnt_nr = nn; }
+        if (warp == 0 && lane == 0) cnt_r = nacc;
+        if (warp == 1 && lane == 0) cnt_nr = nn;
     }
     __syncthreads();
 
