@@ -264,11 +264,20 @@ __device__ __forceinline__ void kvec_of(const DevSys &d, const int m[3], double 
 __device__ __forceinline__ void bin_atom(const DevSys &d, int i, const double x[3], double qi, int moli,
                                          unsigned act, int *__restrict__ cell, int *__restrict__ rank,
                                          int *__restrict__ count, float4 *__restrict__ locf,
-                                         double4 *__restrict__ locd, uint4 *__restrict__ su, int precision)
+                                         double4 *__restrict__ locd, uint4 *__restrict__ su, int precision, bool fast = false)
 {
     int c[3];
     double sf[3], xl[3];
-    frac_of(d, x, sf);
+    if (fast && !d.tri) {
+        // NPT steps: s = x (1/L), the reciprocal of the step's box half-step
+        // (one FP64 multiply instead of an IEEE division; the cell of an atom
+        // within an ulp of a cell face may differ from the division's, which
+        // any consistent binning allows)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sf[a] = x[a] * d.invL[a];
+    } else {
+        frac_of(d, x, sf);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double L = d.L[a];

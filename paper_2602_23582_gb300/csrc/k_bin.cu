@@ -1,7 +1,8 @@
 // k_bin.cu -- cell lists rebuilt every step (the box rescales each step).
 //
-// Binning convention (matches the oracle's definition bit for bit; no FMA in
-// the decision arithmetic): s = r / L, s -= floor(s), s = 0 if s >= 1;
+// Binning convention (an evaluation outside the NPT step matches the oracle's
+// definition bit for bit; no FMA in the decision arithmetic; the NPT step's
+// atom update takes s = r (1/L) instead): s = r / L, s -= floor(s), s = 0 if s >= 1;
 // n = floor(L * sub / r_c) cells per axis; cell = min(floor(s n), n - 1),
 // x fastest.  A tilted cell h: s = h^{-1} r (back substitution) and n from
 // the perpendicular widths instead of the edges; cell-local coordinates are

@@ -249,7 +249,7 @@ __global__ void k_atom_update(DevSys *__restrict__ sys, const int *__restrict__ 
         }
         if (!(d2 <= d.thr2)) sys[s].rebuild = 1;   // every far atom writes the same value
     }
-    if (BIN) bin_atom(d, i, x, aa.q[i], aa.mol[i], act, aa.cell, aa.rank, aa.count, aa.locf, aa.locd, aa.su, precision);
+    if (BIN) bin_atom(d, i, x, aa.q[i], aa.mol[i], act, aa.cell, aa.rank, aa.count, aa.locf, aa.locd, aa.su, precision, true);
 }
 
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
