@@ -425,3 +425,30 @@ def test_batch_size_extremes_match_oracle(kind, P):
     assert _rel(r["virial_long_r"], ref["W_parts"][1]) < TOL64
     assert _rel(r["virial_long_nr"], ref["W_parts"][2]) < TOL64
     assert abs(r["coul_long"] - ref["coul_long"]) <= TOL64 * abs(ref["coul_long"])
+
+
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32])
+def test_degenerate_systems_match_oracle(prec):
+    # the method's degenerate cases: no charge at all (rho = 0: every
+    # long-range term and the short-range Coulomb part vanish, LJ alone
+    # remains), and two atoms whose single pair lies inside r_c (most cells
+    # empty, one cluster each)
+    zero = W.random_charges(n=200, box=(30.0, 30.0, 30.0), seed=31, min_dist=2.2, lj=True)
+    zero.q = np.zeros_like(zero.q)
+    two = W.random_charges(n=2, box=(30.0, 31.0, 32.0), seed=32, min_dist=2.0, lj=True)
+    two.pos = np.array([[10.0, 11.0, 12.0], [13.5, 12.0, 14.0]])
+    two.q = np.array([0.7, -0.7])
+    for s in (zero, two):
+        ctx, p = _ctx([s], prec)
+        F, res = ctx.step(4)
+        ctx.close()
+        ref = O.force_eval(s, _oracle_params(p), 4)
+        r = res[0]
+        tol = TOL64 if prec == R.RBSOG_FP64 else 1e-5
+        assert _rel(F, ref["F"]) < tol
+        assert _rel(r["virial"], ref["W"]) < (TOL64 if prec == R.RBSOG_FP64 else 1e-6)
+        if s is zero:
+            for k in ("coul_short", "coul_long", "coul_excl"):
+                assert r[k] == 0.0, k
+            assert np.all(r["virial_long_r"] == 0.0) and np.all(r["virial_long_nr"] == 0.0)
+            assert abs(r["lj"] - ref["lj"]) <= 1e-6 * abs(ref["lj"])
