@@ -207,9 +207,14 @@ __device__ __forceinline__ void add_fix2(unsigned long long *hi, unsigned long l
 // over the tile and adds it to the force buffer.  Forces are accumulated as
 // 64-bit fixed point (units of 2^-32 kcal/mol/A): integer additions are
 // exact and commute, so the sum does not depend on the order in which the
-// warps reach an atom, and results are deterministic.  Energies and the
-// virial are summed per lane in the warp's fixed pair order and reduced to
-// one record per warp.
+// warps reach an atom, and results are deterministic.  Energies (and, with
+// energies, the virial and its Coulomb / LJ split) are summed per lane in the
+// warp's fixed pair order and reduced to one record per warp.  Force-only
+// evaluations form the virial sum_pairs r_ij (x) f_ij from the force sums the
+// kernel holds anyway: sum_i x_i (x) F_i over the unit (I's cell frame) plus,
+// per tile, sum_j (x_j + o) (x) F_j with o J's cell offset (the same sum by
+// F_i = sum_j f_ij, F_j = -sum_i f_ij; 9 operations per lane and tile instead
+// of 9 per pair).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -241,7 +246,7 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
                                      const float4 *__restrict__ pos4, const float2 *__restrict__ qt,
                                      const float2 *__restrict__ ljrow, const float2 *__restrict__ ljlorow,
                                      const int *__restrict__ sidx, const double *__restrict__ r, const DevSys &dsys,
-                                     TileAcc &acc, float &fjx, float &fjy, float &fjz)
+                                     TileAcc &acc, float &fjx, float &fjy, float &fjz, float4 &pjl)
 {
     fjx = fjy = fjz = 0.f;
 #pragma unroll
@@ -250,6 +255,7 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
         // atom of no molecule, which no cutoff test passes
         const int jj = (kk + t) & 3;
         const float4 pj = pos4[jslot + jj];
+        if (t == 3) pjl = pj;                          // the atom whose sum this lane ends with
         const float2 qj = qt[jslot + jj];
         const int aj = jfirst + jj;
         const float dx = (xs - pj.x) - ol.x, dy = (ys - pj.y) - ol.y, dz = (zs - pj.z) - ol.z;
@@ -296,11 +302,13 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
         acc.fx = fmaf(f, dx, acc.fx);
         acc.fy = fmaf(f, dy, acc.fy);
         acc.fz = fmaf(f, dz, acc.fz);
-        const float fw = DIAG ? 0.5f * f : f;
-        const float gx = fw * dx, gy = fw * dy;
-        acc.w[0] = fmaf(gx, dx, acc.w[0]); acc.w[1] = fmaf(gy, dy, acc.w[1]);
-        acc.w[2] = fmaf(fw * dz, dz, acc.w[2]); acc.w[3] = fmaf(gx, dy, acc.w[3]);
-        acc.w[4] = fmaf(gx, dz, acc.w[4]); acc.w[5] = fmaf(gy, dz, acc.w[5]);
+        if (EN) {                                      // per-pair virial (force-only: from the sums, below)
+            const float fw = DIAG ? 0.5f * f : f;
+            const float gx = fw * dx, gy = fw * dy;
+            acc.w[0] = fmaf(gx, dx, acc.w[0]); acc.w[1] = fmaf(gy, dy, acc.w[1]);
+            acc.w[2] = fmaf(fw * dz, dz, acc.w[2]); acc.w[3] = fmaf(gx, dy, acc.w[3]);
+            acc.w[4] = fmaf(gx, dz, acc.w[4]); acc.w[5] = fmaf(gy, dz, acc.w[5]);
+        }
         if (EN && in) {
             // energy kernel N(r) = 1/r - F(r); the constant of the tail is
             // applied to sum q_i q_j in FP64 by the caller
@@ -404,13 +412,14 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
         const float2 *ljrow = ljs[0] + rowi, *ljlorow = ljs[EN ? 1 : 0] + rowi;
         unsigned long long *const fxs = ffix, *const fys = ffix + N, *const fzs = ffix + 2 * (size_t)N;
         float fjx, fjy, fjz;
+        float4 pjl;
         // the pairs inside I (plane 0), by the first group; the whole warp
         // runs the tile (its votes need every lane), the other groups against
         // the dummy cluster, which adds nothing
         if (part == 0)
             tile<NF, EN, true>(pc, pi.x, pi.y, pi.z, make_float4(0.f, 0.f, 0.f, 0.f), moli, qi, ai,
                                kClus * (grp == 0 ? it : item_cap), ifirst, kk, gbase, pos4, qt, ljrow, ljlorow,
-                               sidx, r, d, acc, fjx, fjy, fjz);
+                               sidx, r, d, acc, fjx, fjy, fjz, pjl);
         // candidate cells, one per lane: plane 0 (I's own cell -- its clusters
         // after I -- then the upper half), then with one unit per cluster
         // (cells of r_c) the planes above
@@ -465,7 +474,16 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
                 const float4 oh = offh[code], ol = offl[code];
                 const int jfirst = nj ? __float_as_int(cbox[2 * jc].w) : 0;
                 tile<NF, EN, false>(pc, pi.x - oh.x, pi.y - oh.y, pi.z - oh.z, ol, moli, qi, ai, kClus * jc,
-                                    jfirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d, acc, fjx, fjy, fjz);
+                                    jfirst, kk, gbase, pos4, qt, ljrow, ljlorow, sidx, r, d, acc, fjx, fjy, fjz,
+                                    pjl);
+                if (!EN) {
+                    // force-only virial, J side: (x_j + o) (x) F_j over the tile, x_j + o the
+                    // image of J's atom in I's cell frame (high part of the offset)
+                    const float px = pjl.x + oh.x, py = pjl.y + oh.y, pz = pjl.z + oh.z;
+                    acc.w[0] = fmaf(px, fjx, acc.w[0]); acc.w[1] = fmaf(py, fjy, acc.w[1]);
+                    acc.w[2] = fmaf(pz, fjz, acc.w[2]); acc.w[3] = fmaf(px, fjy, acc.w[3]);
+                    acc.w[4] = fmaf(px, fjz, acc.w[4]); acc.w[5] = fmaf(py, fjz, acc.w[5]);
+                }
                 const int jl = (kk + 3) & 3;            // the J atom whose sum this lane holds
                 if (jl < nj) {
                     const int aj = jfirst + jl;
@@ -505,6 +523,13 @@ k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys,
             qtail += __popc(m);
             k0 += 32;
             __syncwarp();
+        }
+        if (!EN) {
+            // force-only virial, I side: x_i (x) F_i, F_i this lane's share of the force on
+            // atom i over the unit (padding slots: F_i = 0 at a finite far-away x_i)
+            acc.w[0] = fmaf(pi.x, acc.fx, acc.w[0]); acc.w[1] = fmaf(pi.y, acc.fy, acc.w[1]);
+            acc.w[2] = fmaf(pi.z, acc.fz, acc.w[2]); acc.w[3] = fmaf(pi.x, acc.fy, acc.w[3]);
+            acc.w[4] = fmaf(pi.x, acc.fz, acc.w[4]); acc.w[5] = fmaf(pi.y, acc.fz, acc.w[5]);
         }
         // the force on I's atoms: sum over the 8 groups, one add per atom
         float fx = acc.fx, fy = acc.fy, fz = acc.fz;

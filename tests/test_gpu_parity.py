@@ -170,6 +170,41 @@ def test_skin_lists_match_oracle_after_npt_steps(name):
     assert abs(res["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
 
 
+def _state_after_steps(ctx, n):
+    # step counter, positions, forces and result record of the last step,
+    # from the state record (header, r, p, F, per-system records, results)
+    st = R.rbsog_get_state(ctx.ctx)
+    step = int(np.frombuffer(st, np.uint64, 1, 0)[0])
+    r = np.frombuffer(st, np.float64, 3 * n, 16).reshape(n, 3)
+    F = np.frombuffer(st, np.float64, 3 * n, 16 + 48 * n).reshape(n, 3)
+    red = np.frombuffer(st, np.float64, 64, len(st) - 8 * 64)
+    W = red[9:15][[0, 3, 4, 3, 1, 5, 4, 5, 2]].reshape(3, 3)
+    return step, r.copy(), F.copy(), W, red[52:55].copy()
+
+
+@pytest.mark.parametrize("name", ["electrolyte", "water_small", "ragged"])
+@pytest.mark.parametrize("sub", [1, 2])
+def test_force_only_steps_match_oracle(name, sub):
+    # steps without energies (box held: these boxes are near the stencil's
+    # minimum and the compressing ones would leave it): the FP32 pair kernel forms the virial from
+    # its force sums (x_i F_i per unit, (x_j + o) F_j per tile) instead of
+    # pair by pair; the last step's forces and virial against the oracle at
+    # its positions, box and step
+    import copy
+    s = SYSTEMS[name]()
+    ctx, p = _ctx([s], R.RBSOG_FP32, cell_sub=sub, thermo_every=0, coupling=R.RBSOG_COUPLE_FIXED)
+    R.rbsog_run_async(ctx.ctx, 6)
+    R.rbsog_sync(ctx.ctx)
+    step, r, F, Wg, box = _state_after_steps(ctx, s.n)
+    ctx.close()
+    s2 = copy.copy(s)
+    s2.pos = r
+    s2.box = box
+    ref = O.force_eval(s2, _oracle_params(p), step)
+    assert _rel(F, ref["F"]) < 1e-5
+    assert _rel(Wg, ref["W"]) < 1e-6
+
+
 def test_skin_lists_rebuilt_after_host_changes():
     s = SYSTEMS["water_small"]()
     ctx, p = _ctx([s], R.RBSOG_FP32, skin=1.5, thermo_every=0)

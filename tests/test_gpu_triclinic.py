@@ -112,6 +112,30 @@ def test_tilted_eval_fp32_matches_oracle(name):
     assert abs(r["lj"] - ref["lj"]) <= 1e-6 * max(abs(ref["lj"]), 1.0)
 
 
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_tilted_force_only_steps_fp32_match_oracle(name):
+    # fixed-cell steps without energies: the FP32 virial from the force sums
+    # with tilted cell offsets, against the oracle at the last step
+    import copy
+    s = SYSTEMS[name]()
+    ctx, p = _ctx(s, R.RBSOG_FP32, thermo_every=0)
+    op, cell = _oracle(p, s)
+    R.rbsog_run_async(ctx.ctx, 5)
+    R.rbsog_sync(ctx.ctx)
+    st = R.rbsog_get_state(ctx.ctx)
+    ctx.close()
+    n = s.n
+    step = int(np.frombuffer(st, np.uint64, 1, 0)[0])
+    F = np.frombuffer(st, np.float64, 3 * n, 16 + 48 * n).reshape(n, 3)
+    red = np.frombuffer(st, np.float64, 64, len(st) - 8 * 64)
+    Wg = red[9:15][[0, 3, 4, 3, 1, 5, 4, 5, 2]].reshape(3, 3)
+    s2 = copy.copy(s)
+    s2.pos = np.frombuffer(st, np.float64, 3 * n, 16).reshape(n, 3).copy()
+    ref = O.force_eval_h(s2, op, step, cell)
+    assert _rel(F, ref["F"]) < 1e-5
+    assert _rel(Wg, ref["W"]) < 1e-6
+
+
 def test_tilted_fixed_cell_trajectory_fp64():
     s = SYSTEMS["water_shear"]()
     rng = np.random.default_rng(3)
