@@ -66,9 +66,11 @@ struct rbsog_ctx {
     std::vector<rbsog_status> slot_err; // pool: why a slot's system was stopped (RBSOG_OK: it was not)
     int S = 0, N = 0, C = 0, Dcap = 0, nchunks = 0, nmol = 0, nmchunks = 0, item_cap = 0;
     cudaStream_t st = nullptr, st2 = nullptr, st3 = nullptr;   // st2: mode sampling, st3: molecule terms
+    cudaStream_t st4 = nullptr;         // records the pair-kernel trace events beside the main stream
     bool own_st = false, own_st2 = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
     cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr, ev_bin = nullptr;
+    cudaEvent_t ev_tr[3] = {nullptr, nullptr, nullptr};   // forks to / join from st4
     std::string err;
     std::vector<int> h_atom0, h_n, h_cell0, h_ncap_total, h_coupling;
     std::vector<double> h_tilt;         // per system (xy, xz, yz): tilted cells are held fixed
@@ -134,7 +136,7 @@ struct rbsog_ctx {
     unsigned long long h_step = 0;   // host copy of the device step counter
     // timing
     bool timing = false;
-    bool mol_late = false;    // molecule terms joined before the force assembly (large molecules)
+    bool mol_late = false;    // molecule terms joined before the force assembly (FP32 build, large molecules)
     std::vector<std::string> t_names;
     std::vector<cudaEvent_t> t_events;
     std::vector<double> t_ms;
@@ -324,11 +326,13 @@ void fork_kspace(rbsog_ctx *c)
 }
 
 // Molecule terms on the third stream: they need only the positions and the
-// box and run beside the binning into their own force buffer.  Small
-// molecules (a thread each, a few tens of microseconds) join before the pair
-// kernels, so that they do not take SMs from them; large ones (a warp each,
-// e.g. 15-site ions with 137 terms: several times longer) join before the
-// force assembly and overlap the pair kernels.
+// box and run beside the binning into their own force buffer.  In the FP32
+// build, and for large molecules (a warp each, e.g. 15-site ions with 137
+// terms) in both builds, they join before the force assembly and overlap the
+// pair kernel (water, FP32: the step 0.203 -> 0.198 ms, the pair launch
+// unchanged; joined before the pair kernel they held it back).  Small
+// molecules in the FP64 build join before the pair kernel: their FP64 bonded
+// terms would share the FP64 pipe with it.
 void fork_mol(rbsog_ctx *c, int energy)
 {
     if (c->m.nmchunks == 0) return;
@@ -361,14 +365,25 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     launch_scatter_sort(c->b, c->a, prec, c->st);
     record(c, "scatter_sort");
     if (mol && !c->mol_late) cudaStreamWaitEvent(c->st, c->ev_join3, 0);
-    // in a graph capture: event-record nodes around the pair kernel (external
-    // records, not dependencies), retargeted per launch by arm_pair_trace
+    // in a graph capture: event-record nodes at the pair kernel's start and end
+    // (external records, retargeted per launch by arm_pair_trace), on st4: an
+    // event node between two kernels of the main stream would stand between
+    // them and their programmatic (early-launch) edge
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(c->st, &cap);
     const bool trace = cap == cudaStreamCaptureStatusActive && c->ev_pair_ph[0] && c->ev_pair_ph[1];
-    if (trace) cudaEventRecordWithFlags(c->ev_pair_ph[0], c->st, cudaEventRecordExternal);
+    if (trace) {
+        cudaEventRecord(c->ev_tr[0], c->st);
+        cudaStreamWaitEvent(c->st4, c->ev_tr[0], 0);
+        cudaEventRecordWithFlags(c->ev_pair_ph[0], c->st4, cudaEventRecordExternal);
+    }
     launch_pair(c->b, c->a, prec, c->pcf, c->pcd, energy, c->pair_part, c->st);
-    if (trace) cudaEventRecordWithFlags(c->ev_pair_ph[1], c->st, cudaEventRecordExternal);
+    if (trace) {
+        cudaEventRecord(c->ev_tr[1], c->st);
+        cudaStreamWaitEvent(c->st4, c->ev_tr[1], 0);
+        cudaEventRecordWithFlags(c->ev_pair_ph[1], c->st4, cudaEventRecordExternal);
+        cudaEventRecord(c->ev_tr[2], c->st4);
+    }
     record(c, "pair");
     // the pair records are reduced beside the long-range part
     cudaEventRecord(c->ev_fork4, c->st);
@@ -384,6 +399,7 @@ void enqueue_eval(rbsog_ctx *c, int kick, int box_kick, int energy, int adv, int
     launch_force_assembly(c->b, c->a, prec, c->Flr, mol ? c->Fmol : nullptr, c->ia, kick, c->kin_part, c->st);
     record(c, "assembly_kick");
     cudaStreamWaitEvent(c->st, c->ev_join4, 0);
+    if (trace) cudaStreamWaitEvent(c->st, c->ev_tr[2], 0);   // st4 joins (long done by now)
     launch_finalize(c->b, c->pair_red, c->est, estimate_blocks(c->Dcap), c->prm.P, c->mol_part, c->mchunk_first, c->mchunk_count, c->kin_part,
                     c->first_chunk, c->nchunk_sys, c->self_e, c->ia, box_kick, adv, c->sysred, c->st);
     record(c, "finalize");
@@ -500,7 +516,10 @@ void free_ctx(rbsog_ctx *c)
     if (c->ev_fork4) cudaEventDestroy(c->ev_fork4);
     if (c->ev_join4) cudaEventDestroy(c->ev_join4);
     if (c->own_st2 && c->st2) cudaStreamDestroy(c->st2);
+    for (auto ev : c->ev_tr)
+        if (ev) cudaEventDestroy(ev);
     if (c->st3) cudaStreamDestroy(c->st3);
+    if (c->st4) cudaStreamDestroy(c->st4);
     if (c->own_st && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -783,6 +802,9 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->own_st2 = true;
         e = cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rbsog_status r = cuda_fail(c, e, "stream"); free_ctx(c); return r; }
+        e = cudaStreamCreateWithFlags(&c->st4, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { rbsog_status r = cuda_fail(c, e, "stream"); free_ctx(c); return r; }
+        for (auto &ev : c->ev_tr) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
@@ -865,7 +887,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
             // average, else chunks of a few large molecules (one warp each)
             const int mch = (double)cp.bonds + cp.angles + cp.excl <= (double)kSmallTerms * cp.mols
                                 ? kMolChunk : kMolChunkLarge;
-            if (mch == kMolChunkLarge && cp.mols > 0) c->mol_late = true;
+            if (cp.mols > 0 && (mch == kMolChunkLarge || P.precision == RBSOG_FP32)) c->mol_late = true;
             for (int m0 = 0; m0 < cp.mols; m0 += mch) {
                 mchunk_sys.push_back(k);
                 mchunk_m0.push_back(nmolx + m0);
@@ -1746,7 +1768,6 @@ rbsog_status rbsog_autotune(const rbsog_params *params, int n_systems, const rbs
     if (vs != RBSOG_OK) return vs;
     const bool f32 = params->precision == RBSOG_FP32;
     const int ncols = f32 ? 4 : 1;
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1784,7 +1805,6 @@ rbsog_status rbsog_autotune(const rbsog_params *params, int n_systems, const rbs
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    (void)cs;
     if (!(best_ms < 1e300)) return fail(nullptr, RBSOG_EINVAL, "rbsog_autotune: no candidate shape runs");
     return RBSOG_OK;
 }
