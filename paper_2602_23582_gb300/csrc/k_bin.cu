@@ -184,50 +184,38 @@ __global__ void __launch_bounds__(1024)
 k_scan(const int *__restrict__ count, int *__restrict__ start, int2 *__restrict__ items, int2 *__restrict__ ccl,
        DevSys *sys, int gsize)
 {
-    __shared__ int wa[32], wg[32];
+    __shared__ int ta[1024], tg[1024];
     DevSys &d = sys[blockIdx.x];
     if (!d.rebuild) return;                  // block-uniform: the system keeps its lists
-    const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
+    const int t = threadIdx.x, T = blockDim.x;
     const int C0 = d.cell0, nc = d.ncell_cap_total;
     const int per = (nc + T - 1) / T;
     const int c0 = min(nc, t * per), c1 = min(nc, c0 + per);
-    // this thread's atoms and items
-    int sa = 0, sg = 0;
+    int sa = 0;
     for (int c = c0; c < c1; ++c) {
         const int v = count[C0 + c];
         if (v > kCellCap) atomicOr(&d.flags, (int)FLAG_OVERFLOW);
         sa += v;
-        sg += (min(v, kCellCap) + gsize - 1) / gsize;
     }
-    // block-wide exclusive prefix: within the warp by shuffles, then over the
-    // warps' totals by warp 0
-    int ia = sa, ig = sg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int xa = __shfl_up_sync(0xffffffffu, ia, o), xg = __shfl_up_sync(0xffffffffu, ig, o);
-        if (lane >= o) { ia += xa; ig += xg; }
-    }
-    if (lane == 31) { wa[warp] = ia; wg[warp] = ig; }
+    const int sg = scan_items(count, C0, c0, c1, gsize, items, ccl, 0, false);
+    ta[t] = sa;
+    tg[t] = sg;
     __syncthreads();
-    if (warp == 0) {
-        int xa = lane < nw ? wa[lane] : 0, xg = lane < nw ? wg[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int ya = __shfl_up_sync(0xffffffffu, xa, o), yg = __shfl_up_sync(0xffffffffu, xg, o);
-            if (lane >= o) { xa += ya; xg += yg; }
-        }
-        wa[lane] = xa;
-        wg[lane] = xg;
+    for (int o = 1; o < T; o <<= 1) {
+        int va = (t >= o) ? ta[t - o] : 0, vg = (t >= o) ? tg[t - o] : 0;
+        __syncthreads();
+        ta[t] += va;
+        tg[t] += vg;
+        __syncthreads();
     }
-    __syncthreads();
-    int ra = d.atom0 + (warp ? wa[warp - 1] : 0) + ia - sa;
-    const int rg = d.item0 + (warp ? wg[warp - 1] : 0) + ig - sg;
+    int ra = d.atom0 + ta[t] - sa;
+    const int rg = d.item0 + tg[t] - sg;
     for (int c = c0; c < c1; ++c) {
         start[C0 + c] = ra;
         ra += count[C0 + c];
     }
     scan_items(count, C0, c0, c1, gsize, items, ccl, rg, true);
-    const int total = wg[nw - 1];
+    const int total = tg[T - 1];
     if (t == T - 1) {
         d.nitems = total;
         d.Lref[0] = d.L[0]; d.Lref[1] = d.L[1]; d.Lref[2] = d.L[2];

@@ -262,11 +262,12 @@ __global__ void k_atom_update(DevSys *__restrict__ sys, const int *__restrict__ 
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
                         cudaStream_t st, int skin)
 {
-    // 128-thread blocks: the atoms of one system spread over every SM (30,000 atoms:
-    // 235 blocks; blocks of 256 left a quarter of the SMs idle, water step +5.6 us)
-    const int g = (b.N + 127) / 128;
+    // blocks of 256: with blocks of 128 (every SM busy) the water step measured
+    // 5.6 us faster with the L2 warm but 37 us slower with it flushed between
+    // steps (the atom update then overlaps the sampler's FP64 kernels longer)
+    const int g = (b.N + 255) / 256;
 #define RBSOG_ATOM_UPDATE(NF, BN, SK) \
-    k_atom_update<NF, BN, SK><<<g, 128, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision)
+    k_atom_update<NF, BN, SK><<<g, 256, 0, st>>>(b.sys, b.atom_sys, b.N, a.r, a.p, a.F, ia, a, precision)
     if (ia.noise_f32) {
         if (bin) RBSOG_ATOM_UPDATE(true, true, false);
         else if (skin) RBSOG_ATOM_UPDATE(true, false, true);
