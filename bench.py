@@ -685,26 +685,41 @@ def main():
                          "ms_per_step": float(en_ms.mean()), "steps": n_en,
                          "p50_ms": float(np.percentile(en_ms, 50)), "p99_ms": float(np.percentile(en_ms, 99))}
 
-    # ---- e2e through the C ABI with host buffers (positions in, forces out)
+    # ---- e2e through the C ABI with host buffers: positions in, forces and
+    # virial out (the force-only evaluation an NPT step needs,
+    # rbsog_step_forces); the same with energies (rbsog_step) beside it
     e2e = None
     if not args.no_e2e:
         pos = torch.empty((n_atoms, 3), dtype=torch.float64).pin_memory()
         frc = torch.empty((n_atoms, 3), dtype=torch.float64).pin_memory()
+        vir = torch.empty((ctx.S, 9), dtype=torch.float64).pin_memory()
         R.rbsog_get_positions(ctx.ctx, pos.numpy())
         res = (R.rbsog_result * ctx.S)()
         ne = max(10, min(200, args.steps // 2))
-        for k in range(3):
-            R.rbsog_set_positions(ctx.ctx, pos.numpy())
-            R.rbsog_step(ctx.ctx, 20_000 + k, frc.numpy(), res)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(ne):
-            R.rbsog_set_positions(ctx.ctx, pos.numpy())
-            R.rbsog_step(ctx.ctx, 30_000 + k, frc.numpy(), res)
-        t1 = time.perf_counter()
-        e2e = {"value": n_atoms * ne / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": 24 * n_atoms,
-               "d2h_bytes_per_step": 24 * n_atoms + 632 * ctx.S,
-               "call": "rbsog_set_positions(host) + rbsog_step(host forces, results)"}
+
+        def e2e_loop(base, energies):
+            for k in range(3):
+                R.rbsog_set_positions(ctx.ctx, pos.numpy())
+                if energies:
+                    R.rbsog_step(ctx.ctx, base + k, frc.numpy(), res)
+                else:
+                    R.rbsog_step_forces(ctx.ctx, base + k, frc.numpy(), vir.numpy())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(ne):
+                R.rbsog_set_positions(ctx.ctx, pos.numpy())
+                if energies:
+                    R.rbsog_step(ctx.ctx, base + 100 + k, frc.numpy(), res)
+                else:
+                    R.rbsog_step_forces(ctx.ctx, base + 100 + k, frc.numpy(), vir.numpy())
+            return n_atoms * ne / (time.perf_counter() - t0)
+
+        e2e = {"value": e2e_loop(30_000, False), "unit": UNIT, "h2d_bytes_per_step": 24 * n_atoms,
+               "d2h_bytes_per_step": 24 * n_atoms + 72 * ctx.S,
+               "call": "rbsog_set_positions(host) + rbsog_step_forces(host forces, host virial)",
+               "with_energies": {"value": e2e_loop(40_000, True), "unit": UNIT,
+                                 "d2h_bytes_per_step": 24 * n_atoms + 632 * ctx.S,
+                                 "call": "rbsog_set_positions(host) + rbsog_step(host forces, results)"}}
         if world > 1:
             t = torch.tensor([e2e["value"]], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.SUM)

@@ -234,6 +234,22 @@ rbsog_status rbsog_get_velocities(rbsog_ctx *ctx, double *v, int on_device);
 rbsog_status rbsog_step(rbsog_ctx *ctx, uint64_t step, double *forces, int on_device,
                         rbsog_result *results);
 
+/* One force-only evaluation of every system at the current positions and
+ * boxes with Philox step counter `step`: the forces of eq. f_approx plus the
+ * short-range, bonded and exclusion forces (sec. 2.2, 3.1), and the virial
+ * tensor W of eqs. P_approx_r, P_approx_nr with the short-range and
+ * molecule parts, the quantities an NPT step needs; no energies.  This is
+ * the evaluation each step of rbsog_run performs (FP32 build: the cutoff
+ * decided in FP32, the virial formed from the pair kernel's force sums), so
+ * it costs less than rbsog_step.  forces: N_total x 3 (kcal/(mol A)), on the
+ * host or (on_device = 1) the device, or NULL.  virial: n_systems x 9 doubles
+ * on the host (row-major 3 x 3 per system, kcal/mol, the same tensor as
+ * rbsog_result.virial), or NULL.  The integrator state is not touched.
+ * Errors: as rbsog_step (RBSOG_EBOX, RBSOG_EOVERFLOW, RBSOG_ENONFINITE for a
+ * system whose step failed; RBSOG_ECUDA). */
+rbsog_status rbsog_step_forces(rbsog_ctx *ctx, uint64_t step, double *forces, int on_device,
+                               double *virial);
+
 /* Advance every system by nsteps Langevin NPT steps (Algorithm 1 step 8),
  * replaying a captured CUDA graph of one step.  last: n_systems results of
  * the final step, or NULL. */

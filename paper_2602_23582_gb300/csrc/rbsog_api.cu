@@ -123,8 +123,8 @@ struct rbsog_ctx {
     // graphs of one NPT step: [0] forces and virial, [1] also energies
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraph_t graph_src[2] = {nullptr, nullptr};
-    cudaGraphExec_t eval_graph = nullptr;   // one evaluation with energies (rbsog_step)
-    cudaGraph_t eval_graph_src = nullptr;
+    cudaGraphExec_t eval_graph[2] = {nullptr, nullptr};   // one evaluation: [0] force only, [1] with energies
+    cudaGraph_t eval_graph_src[2] = {nullptr, nullptr};
     // pair-kernel trace: event-record nodes around the pair kernel in each
     // graph; their events are swapped per launch to a ring of caller-visible
     // timings (placeholders when no trace is armed)
@@ -426,12 +426,11 @@ void enqueue_npt_step(rbsog_ctx *c, int energy)
     enqueue_eval(c, 1, 1, energy, 1, 1);
 }
 
-rbsog_status check_flags(rbsog_ctx *c)
+// The status flags of a host copy h of the systems' records: the first
+// failing system's error (a pool stops that system only and goes on).
+rbsog_status process_flags(rbsog_ctx *c, std::vector<DevSys> &h)
 {
-    std::vector<DevSys> h(c->S);
-    cudaError_t e = cudaMemcpyAsync(h.data(), c->sys, sizeof(DevSys) * c->S, cudaMemcpyDeviceToHost, c->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "device");
+    cudaError_t e = cudaSuccess;
     for (int s = 0; s < c->S; ++s) {
         if (!h[s].flags) continue;
         rbsog_status st = RBSOG_OK;
@@ -457,13 +456,34 @@ rbsog_status check_flags(rbsog_ctx *c)
     return RBSOG_OK;
 }
 
+rbsog_status check_flags(rbsog_ctx *c)
+{
+    std::vector<DevSys> h(c->S);
+    cudaError_t e = cudaMemcpyAsync(h.data(), c->sys, sizeof(DevSys) * c->S, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device");
+    return process_flags(c, h);
+}
+
+// 3x3 row-major from the six components xx yy zz xy xz yz
+static const int kSym[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+
+void results_from(rbsog_ctx *c, const std::vector<double> &h, rbsog_result *res);
+
 rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
 {
     std::vector<double> h((size_t)c->S * kRed);
     cudaError_t e = cudaMemcpyAsync(h.data(), c->sysred, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "results");
-    static const int sym[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};   // 3x3 row-major from xx yy zz xy xz yz
+    results_from(c, h, res);
+    return RBSOG_OK;
+}
+
+// The result records from a host copy h of the per-system reductions.
+void results_from(rbsog_ctx *c, const std::vector<double> &h, rbsog_result *res)
+{
+    const int *sym = kSym;
     for (int s = 0; s < c->S; ++s) {
         const double *o = &h[(size_t)s * kRed];
         rbsog_result &r = res[s];
@@ -487,7 +507,6 @@ rbsog_status fill_results(rbsog_ctx *c, rbsog_result *res)
         r.step = (uint64_t)o[62];
         r.list_builds = (int)o[63];
     }
-    return RBSOG_OK;
 }
 
 void free_ctx(rbsog_ctx *c)
@@ -497,8 +516,10 @@ void free_ctx(rbsog_ctx *c)
         if (g) cudaGraphExecDestroy(g);
     for (auto g : c->graph_src)
         if (g) cudaGraphDestroy(g);
-    if (c->eval_graph) cudaGraphExecDestroy(c->eval_graph);
-    if (c->eval_graph_src) cudaGraphDestroy(c->eval_graph_src);
+    for (int k = 0; k < 2; ++k) {
+        if (c->eval_graph[k]) cudaGraphExecDestroy(c->eval_graph[k]);
+        if (c->eval_graph_src[k]) cudaGraphDestroy(c->eval_graph_src[k]);
+    }
     for (auto e : c->ring_s) cudaEventDestroy(e);
     for (auto e : c->ring_e) cudaEventDestroy(e);
     for (auto e : c->ev_pair_ph)
@@ -1386,20 +1407,35 @@ rbsog_status rbsog_get_velocities(rbsog_ctx *c, double *v, int on_device)
 
 // The evaluation of rbsog_step as a CUDA graph (captured on first use; the
 // step counter is set by a kernel launched before it).
-static rbsog_status ensure_eval_graph(rbsog_ctx *c)
+static rbsog_status ensure_eval_graph(rbsog_ctx *c, int energy)
 {
-    if (c->eval_graph) return RBSOG_OK;
+    if (c->eval_graph[energy]) return RBSOG_OK;
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "capture");
     launch_clear_flags(c->b, c->st);
-    enqueue_eval(c, 0, 0, 1, 0);
+    enqueue_eval(c, 0, 0, energy, 0);
     e = cudaStreamEndCapture(c->st, &g);
     if (e != cudaSuccess) return cuda_fail(c, e, "capture end");
-    e = cudaGraphInstantiate(&c->eval_graph, g, 0);
+    e = cudaGraphInstantiate(&c->eval_graph[energy], g, 0);
     if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(c, e, "graph instantiate"); }
-    c->eval_graph_src = g;
+    c->eval_graph_src[energy] = g;
     return RBSOG_OK;
+}
+
+// Flags and (optionally) the per-system reductions of the last evaluation in
+// one read-back: the two copies are enqueued, then the stream is waited for once.
+static rbsog_status read_back(rbsog_ctx *c, std::vector<double> *red)
+{
+    std::vector<DevSys> h(c->S);
+    cudaError_t e = cudaMemcpyAsync(h.data(), c->sys, sizeof(DevSys) * c->S, cudaMemcpyDeviceToHost, c->st);
+    if (red && e == cudaSuccess) {
+        red->resize((size_t)c->S * kRed);
+        e = cudaMemcpyAsync(red->data(), c->sysred, red->size() * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device");
+    return process_flags(c, h);
 }
 
 rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_device, rbsog_result *res)
@@ -1414,9 +1450,9 @@ rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_devi
         launch_clear_flags(c->b, c->st);
         enqueue_eval(c, 0, 0, 1, 0);
     } else {
-        rbsog_status gs = ensure_eval_graph(c);
+        rbsog_status gs = ensure_eval_graph(c, 1);
         if (gs != RBSOG_OK) return gs;
-        e = cudaGraphLaunch(c->eval_graph, c->st);
+        e = cudaGraphLaunch(c->eval_graph[1], c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
     }
     c->h_step = (unsigned long long)step;
@@ -1427,7 +1463,8 @@ rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_devi
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "forces");
     }
-    rbsog_status fs = check_flags(c);
+    std::vector<double> red;
+    rbsog_status fs = read_back(c, res ? &red : nullptr);
     if (fs != RBSOG_OK) return fs;
     if (c->timing) {
         c->t_ms.clear();
@@ -1437,7 +1474,30 @@ rbsog_status rbsog_step(rbsog_ctx *c, uint64_t step, double *forces, int on_devi
             c->t_ms.push_back(ms);
         }
     }
-    if (res) return fill_results(c, res);
+    if (res) results_from(c, red, res);
+    return RBSOG_OK;
+}
+
+rbsog_status rbsog_step_forces(rbsog_ctx *c, uint64_t step, double *forces, int on_device, double *virial)
+{
+    if (!c) return RBSOG_EINVAL;
+    launch_set_step(c->b, (unsigned long long)step, c->st);
+    rbsog_status gs = ensure_eval_graph(c, 0);
+    if (gs != RBSOG_OK) return gs;
+    cudaError_t e = cudaGraphLaunch(c->eval_graph[0], c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c->h_step = (unsigned long long)step;
+    if (forces) {
+        e = cudaMemcpyAsync(forces, c->F, 3 * sizeof(double) * c->N,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "forces");
+    }
+    std::vector<double> red;
+    rbsog_status fs = read_back(c, virial ? &red : nullptr);
+    if (fs != RBSOG_OK) return fs;
+    if (virial)
+        for (int s = 0; s < c->S; ++s)
+            for (int k = 0; k < 9; ++k) virial[9 * s + k] = red[(size_t)s * kRed + 9 + kSym[k]];
     return RBSOG_OK;
 }
 
@@ -1552,9 +1612,10 @@ rbsog_status rbsog_run(rbsog_ctx *c, int nsteps, rbsog_result *last)
     launch_clear_flags(c->b, c->st);
     rbsog_status rs = run_steps(c, nsteps, true);
     if (rs != RBSOG_OK) return rs;
-    rbsog_status fs = check_flags(c);
+    std::vector<double> red;
+    rbsog_status fs = read_back(c, last ? &red : nullptr);
     if (fs != RBSOG_OK) return fs;
-    if (last) return fill_results(c, last);
+    if (last) results_from(c, red, last);
     return RBSOG_OK;
 }
 

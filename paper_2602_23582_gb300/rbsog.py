@@ -28,7 +28,7 @@ E_NAMES = ("coul_short", "coul_long", "coul_self", "coul_excl", "lj", "bond", "a
 
 EXPORTS = ("rbsog_default_params", "rbsog_create", "rbsog_destroy", "rbsog_last_error", "rbsog_n_atoms",
            "rbsog_system_range", "rbsog_set_box", "rbsog_set_positions", "rbsog_get_positions",
-           "rbsog_get_velocities", "rbsog_step", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
+           "rbsog_get_velocities", "rbsog_step", "rbsog_step_forces", "rbsog_run", "rbsog_get_state", "rbsog_set_state",
            "rbsog_debug_cells", "rbsog_debug_modes", "rbsog_debug_device_alloc_calls", "rbsog_virial_nr_shared", "rbsog_set_timing", "rbsog_get_timing",
            "rbsog_structure_factor_workspace", "rbsog_structure_factor", "rbsog_run_async",
            "rbsog_sync", "rbsog_stream", "rbsog_structure_factor_noalloc", "rbsog_trace_pair",
@@ -116,6 +116,7 @@ def lib():
     L.rbsog_get_positions.argtypes = [P, P, C.c_int]
     L.rbsog_get_velocities.argtypes = [P, P, C.c_int]
     L.rbsog_step.argtypes = [P, C.c_uint64, P, C.c_int, C.POINTER(rbsog_result)]
+    L.rbsog_step_forces.argtypes = [P, C.c_uint64, P, C.c_int, P]
     L.rbsog_run.argtypes = [P, C.c_int, C.POINTER(rbsog_result)]
     L.rbsog_run_async.argtypes = [P, C.c_int]
     L.rbsog_sync.argtypes = [P]
@@ -247,6 +248,12 @@ def rbsog_destroy(ctx):
 def rbsog_step(ctx, step, forces=None, results=None):
     p, dev = _ptr(forces)
     _check(lib().rbsog_step(ctx, step, p, dev, results), ctx)
+
+
+def rbsog_step_forces(ctx, step, forces=None, virial=None):
+    p, dev = _ptr(forces)
+    v = None if virial is None else virial.ctypes.data_as(C.c_void_p)
+    _check(lib().rbsog_step_forces(ctx, step, p, dev, v), ctx)
 
 
 def rbsog_run(ctx, nsteps, results=None):
@@ -724,6 +731,14 @@ class Context:
             forces = np.zeros((self.n_atoms, 3))
         rbsog_step(self.ctx, step, forces, res)
         return forces, [result_dict(res[k]) for k in range(self.S)]
+
+    def step_forces(self, step, forces=None):
+        """Force-only evaluation: forces (N x 3) and per-system virial (S x 3 x 3)."""
+        if forces is None:
+            forces = np.zeros((self.n_atoms, 3))
+        virial = np.zeros((self.S, 3, 3))
+        rbsog_step_forces(self.ctx, step, forces, virial)
+        return forces, virial
 
     def run(self, nsteps):
         res = (rbsog_result * self.S)()

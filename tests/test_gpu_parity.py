@@ -170,6 +170,23 @@ def test_skin_lists_match_oracle_after_npt_steps(name):
     assert abs(res["coul"] - ref["coul"]) <= 1e-6 * abs(ref["coul"])
 
 
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32])
+@pytest.mark.parametrize("name", ["electrolyte", "water_small"])
+def test_step_forces_matches_oracle(prec, name):
+    # the force-only evaluation (rbsog_step_forces, the evaluation of an NPT
+    # step, no energies): forces and virial against the oracle, at two step
+    # counters through the same captured graph
+    s = SYSTEMS[name]()
+    ctx, p = _ctx([s], prec)
+    out = {k: ctx.step_forces(k) for k in (5, 9)}
+    ctx.close()
+    tol_f, tol_w = (TOL64, TOL64) if prec == R.RBSOG_FP64 else (1e-5, 1e-6)
+    for k, (F, W) in out.items():
+        ref = O.force_eval(s, _oracle_params(p), k)
+        assert _rel(F, ref["F"]) < tol_f, k
+        assert _rel(W[0], ref["W"]) < tol_w, k
+
+
 def _state_after_steps(ctx, n):
     # step counter, positions, forces and result record of the last step,
     # from the state record (header, r, p, F, per-system records, results)
