@@ -187,6 +187,21 @@ def test_step_forces_matches_oracle(prec, name):
         assert _rel(W[0], ref["W"]) < tol_w, k
 
 
+def test_fp64_trajectory_independent_of_energy_steps():
+    # FP64 build: forces and the total virial are formed the same way with
+    # and without energies, so the trajectory does not depend on thermo_every
+    s = SYSTEMS["water_small"]()
+    out = []
+    for every in (1, 0):
+        ctx, _ = _ctx([s], R.RBSOG_FP64, thermo_every=every)
+        R.rbsog_run_async(ctx.ctx, 12)
+        R.rbsog_sync(ctx.ctx)
+        out.append((ctx.positions(), ctx.run(0)[0]["box"]))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def _state_after_steps(ctx, n):
     # step counter, positions, forces and result record of the last step,
     # from the state record (header, r, p, F, per-system records, results)
