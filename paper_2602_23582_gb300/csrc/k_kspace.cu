@@ -76,6 +76,42 @@ __device__ __forceinline__ void phase_sincos_d(const int m[3], double sx, double
     sincospi(2.0 * t, &sn, &cs);
 }
 
+// FP64 table of (cos, sin)(2 pi k / 512), k < 512, for phase_sincos_dt;
+// filled by the threads of a block (sincospi of exact arguments k / 256),
+// which must synchronise before the first use.
+constexpr int kTurnTabD = 512;
+__device__ __forceinline__ void fill_turn_table_d(double2 *tab)
+{
+    for (int k = threadIdx.x; k < kTurnTabD; k += blockDim.x) {
+        double sn, cs;
+        sincospi((double)k * (1.0 / 256.0), &sn, &cs);
+        tab[k] = make_double2(cs, sn);
+    }
+}
+
+// sin and cos of 2 pi (m . s) in FP64 from the table: t = m . s mod 1 as in
+// phase_sincos_d, 512 t = k + b with k the nearest integer (|b| <= 1/2, exact),
+// the remainder angle c = 2 pi b / 512 has |c| <= pi / 512, where
+// sin c = c (1 - c^2/6 + c^4/120) (next term below 1e-19 of c) and
+// cos c = 1 - c^2/2 + c^4/24 - c^6/720 (next term below 3e-21); the
+// angle-sum formulas combine them with the table: about half the FP64
+// instructions of sincospi, and as accurate.
+__device__ __forceinline__ void phase_sincos_dt(const int m[3], double sx, double sy, double sz,
+                                                const double2 *tab, double &sn, double &cs)
+{
+    double t = (double)m[0] * sx + (double)m[1] * sy + (double)m[2] * sz;
+    t -= rint(t);
+    const double u = t * (double)kTurnTabD;
+    const double kf = rint(u);
+    const double c = (u - kf) * (kTwoPi / (double)kTurnTabD);
+    const double c2 = c * c;
+    const double sc = c * fma(c2, fma(c2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+    const double cc = fma(c2, fma(c2, fma(c2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const double2 tb = tab[(int)kf & (kTurnTabD - 1)];
+    sn = fma(tb.y, cc, tb.x * sc);
+    cs = fma(tb.x, cc, -(tb.y * sc));
+}
+
 // rho partial sums of one chunk of atoms for a group of modes.
 // su: FP32 atom data (fixed-point s, q bits); r/q/L: FP64 atom data.
 // B: the edges L and, for a tilted cell, the tilts (xy, xz, yz) in B[3..5]
@@ -87,7 +123,9 @@ __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, cons
     __shared__ uint4 s_su[F32 ? kChunk : 1];
     __shared__ double s_sd[F32 ? 1 : kChunk][4];
     __shared__ float2 s_tab[F32 ? kTurnTab : 1];
+    __shared__ double2 s_tabd[F32 ? 1 : kTurnTabD];
     if (F32) fill_turn_table(s_tab);
+    else fill_turn_table_d(s_tabd);
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
     for (int k = tid; k < na; k += blockDim.x) {
         if (F32) {
@@ -128,7 +166,7 @@ __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, cons
             double sr = 0.0, si = 0.0;
             for (int k = lane; k < na; k += 32) {
                 double sn, cs;
-                phase_sincos_d(m, s_sd[k][0], s_sd[k][1], s_sd[k][2], sn, cs);
+                phase_sincos_dt(m, s_sd[k][0], s_sd[k][1], s_sd[k][2], s_tabd, sn, cs);
                 sr += s_sd[k][3] * cs;
                 si += s_sd[k][3] * sn;
             }
@@ -291,6 +329,7 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
     __shared__ int4 tm[kModeTile];
     __shared__ double td[F32 ? 1 : kModeTile][5];
     __shared__ float2 tab[F32 ? kTurnTab : 1];
+    __shared__ double2 tabd[F32 ? 1 : kTurnTabD];
     const int c = blockIdx.x, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int nD = d.nD, a0 = chunk_a0[c], na = min(kChunk, live_n(d) - (a0 - d.atom0));
@@ -298,6 +337,7 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
     const int k = blockIdx.y * kLrAtoms + threadIdx.x;
     if ((int)(blockIdx.y * kLrAtoms) >= na) return;   // whole block beyond the chunk
     if (F32) fill_turn_table(tab);                    // used after the tile loop's barrier
+    else fill_turn_table_d(tabd);
     const bool act = k < na;
     const int i = a0 + (act ? k : 0);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -345,7 +385,7 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
                 const int4 mm = tm[u];
                 const int m[3] = {mm.x, mm.y, mm.z};
                 double sn, cs;
-                phase_sincos_d(m, sx, sy, sz, sn, cs);
+                phase_sincos_dt(m, sx, sy, sz, tabd, sn, cs);
                 const double g = td[u][4] * cs - td[u][3] * sn;
                 gx += td[u][0] * g;
                 gy += td[u][1] * g;

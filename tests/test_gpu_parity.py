@@ -188,8 +188,10 @@ def test_step_forces_matches_oracle(prec, name):
 
 
 def test_fp64_trajectory_independent_of_energy_steps():
-    # FP64 build: forces and the total virial are formed the same way with
-    # and without energies, so the trajectory does not depend on thermo_every
+    # FP64 build: forces and the total virial are formed by the same
+    # operations with and without energies (the two kernel variants may
+    # round them differently where the compiler fuses a multiply-add), so the
+    # trajectory depends on thermo_every only at the level of FP64 rounding
     s = SYSTEMS["water_small"]()
     out = []
     for every in (1, 0):
@@ -198,8 +200,8 @@ def test_fp64_trajectory_independent_of_energy_steps():
         R.rbsog_sync(ctx.ctx)
         out.append((ctx.positions(), ctx.run(0)[0]["box"]))
         ctx.close()
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    assert _rel(out[0][0], out[1][0]) < 1e-12
+    assert _rel(out[0][1], out[1][1]) < 1e-12
 
 
 def _state_after_steps(ctx, n):
