@@ -129,17 +129,29 @@ rbsog_status rbsog_server_create(const rbsog_params *params, int n_slots, const 
     if (!s) return RBSOG_ENOMEM;
     // size the pool to the free HBM: the largest n <= n_slots whose pool fits
     // within hbm_fraction of the free memory at creation
+    // (a failed query of the free memory is a CUDA error: no pool is sized on a guess)
     size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete s;
+        return RBSOG_ECUDA;
+    }
     const double budget = hbm_fraction * (double)free_b;
     int n = n_slots;
     rbsog_status st = RBSOG_ENOMEM;
     while (n >= 1) {
         size_t f0 = 0, f1 = 0, t = 0;
-        cudaMemGetInfo(&f0, &t);
+        if (cudaMemGetInfo(&f0, &t) != cudaSuccess) {
+            st = RBSOG_ECUDA;
+            break;
+        }
         st = rbsog_pool_create(params, n, caps, stream, &s->ctx);
         if (st == RBSOG_OK) {
-            cudaMemGetInfo(&f1, &t);
+            if (cudaMemGetInfo(&f1, &t) != cudaSuccess) {
+                rbsog_destroy(s->ctx);
+                s->ctx = nullptr;
+                st = RBSOG_ECUDA;
+                break;
+            }
             if ((double)(f0 - std::min(f0, f1)) <= budget) break;
             rbsog_destroy(s->ctx);
             s->ctx = nullptr;
