@@ -352,7 +352,10 @@ rbsog_status rbsog_pool_unload(rbsog_ctx *ctx, int slot, double *r, double *v, r
  * admits queued ones into free slots that fit them (first fit), primes them,
  * then advances every running slot up to max_steps NPT steps in the same
  * launches.  Step latencies (CUDA events per step) and aggregate atom-steps/s
- * over the pumped steps are kept for rbsog_server_stats. */
+ * over the pumped steps are kept for rbsog_server_stats.  rbsog_server_create
+ * returns RBSOG_EINVAL for a null argument or hbm_fraction outside (0, 1],
+ * RBSOG_ENOMEM when not even one slot fits the budget, RBSOG_ECUDA when the
+ * free device memory cannot be queried, or the pool's own error. */
 typedef struct rbsog_server rbsog_server;
 rbsog_status rbsog_server_create(const rbsog_params *params, int n_slots, const rbsog_slot_caps *caps,
                                  double hbm_fraction, void *stream, rbsog_server **out);

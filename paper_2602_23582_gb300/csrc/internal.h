@@ -207,11 +207,23 @@ void launch_sampler(const Batch &b, const SamplerArgs &sa, int adv, int *mr, int
                     int Dcap, cudaStream_t st);
 
 // ---- k_kspace.cu
+// FP64 build: the structure factor takes sub-chunks of kChunk / kSkSubD atoms
+// per block (partials [chunk][sub][Dcap][2]), and the long-range force
+// kLrGroupsD groups of modes per atom, each into its own partial force [3N]
+// that the force assembly adds in group order.  A system of a few thousand
+// atoms then spreads its FP64 k-space work over many SMs instead of one per
+// chunk; the counts are fixed, so a system's sums run in the same order in
+// any batch.  The FP32 build keeps one of each.
+constexpr int kSkSubD = 8;
+constexpr int kLrGroupsD = 8;
+inline int sk_sub(int precision) { return precision == 1 ? 1 : kSkSubD; }
+inline int lr_groups(int precision) { return precision == 1 ? 1 : kLrGroupsD; }
+// part: [nchunks x sk_sub(precision) x Dcap x 2]
 void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
                double *part, cudaStream_t st);
 void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_sys, const int *D,
                      const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
-                     double *rho, ModeCoef *coef, double *est, cudaStream_t st);
+                     double *rho, ModeCoef *coef, double *est, cudaStream_t st, int precision);
 // mode groups of k_estimate: est holds S x estimate_blocks(Dcap) x 7 partial sums
 int estimate_blocks(int Dcap);
 // V P^F,nr by the shared-proposal estimator (sec. 3.2) over the modes of the
@@ -270,10 +282,11 @@ void launch_box_half(const Batch &b, const IntegArgs &ia, const double *sysred, 
 void launch_atom_update(const Batch &b, const AtomArrays &a, const IntegArgs &ia, int bin, int precision,
                         cudaStream_t st, int skin = 0);
 constexpr int kKinSplit = 8;   // kinetic partials per atom chunk (one per force-assembly block)
-// long-range force per atom (eq. f_approx) into Flr [3N] (beside the pair kernel)
+// long-range force per atom (eq. f_approx) into Flr [lr_groups(precision) x 3N]
+// (FP32: beside the pair kernel)
 void launch_lr_fourier(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
                        double *Flr, cudaStream_t st);
-// F = pair partials + Flr + Fmol (molecule terms; null: none), then (kick != 0)
+// F = pair partials + Flr (its groups in order) + Fmol (molecule terms; null: none), then (kick != 0)
 // the second half kick p += dt/2 F, and the kinetic tensor per kChunk /
 // kKinSplit atoms: kin_part[chunk][kKinSplit][6] = sum p (x) p / m
 void launch_force_assembly(const Batch &b, const AtomArrays &a, int precision, const double *Flr,

@@ -182,28 +182,31 @@ __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, cons
 
 }  // namespace
 
-// grid: (nchunks, ceil(Dcap / kModeGroup)); part[chunk][Dcap][2]
+// grid: (nchunks x nsub, ceil(Dcap / kModeGroup)), nsub = 1 (FP32) or kSkSubD
+// (FP64) sub-chunks of kChunk / nsub atoms; part[chunk][sub][Dcap][2]
 template <bool F32>
 __global__ void __launch_bounds__(kSkThreads)
 k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
      const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
      const double *__restrict__ q, const int *__restrict__ D, int Dcap, double *__restrict__ part)
 {
-    const int c = blockIdx.x, s = chunk_sys[c];
+    constexpr int nsub = F32 ? 1 : kSkSubD, span = kChunk / nsub;
+    const int c = blockIdx.x / nsub, sb = blockIdx.x % nsub, s = chunk_sys[c];
     const DevSys &d = sys[s];
     const int d0 = blockIdx.y * kModeGroup;
-    const int na = min(kChunk, live_n(d) - (chunk_a0[c] - d.atom0));   // <= 0: beyond the system in its slot
+    // atoms of this sub-chunk (<= 0: beyond the system in its slot)
+    const int na = min(span, live_n(d) - (chunk_a0[c] - d.atom0) - sb * span);
     if (d0 >= d.nD || na <= 0) return;
     const int nd_here = min(kModeGroup, d.nD - d0);
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
-    sk_chunk<F32>(su, r, q, L, d.tri ? d.tilt : nullptr, chunk_a0[c], na, D + (size_t)s * Dcap * 3, d0, nd_here,
-                  part + ((size_t)c * Dcap + d0) * 2);
+    sk_chunk<F32>(su, r, q, L, d.tri ? d.tilt : nullptr, chunk_a0[c] + sb * span, na, D + (size_t)s * Dcap * 3, d0,
+                  nd_here, part + ((size_t)blockIdx.x * Dcap + d0) * 2);
 }
 
 void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
                double *part, cudaStream_t st)
 {
-    dim3 grid(b.nchunks, (Dcap + kModeGroup - 1) / kModeGroup);
+    dim3 grid(b.nchunks * sk_sub(precision), (Dcap + kModeGroup - 1) / kModeGroup);
     if (precision == 1)
         k_sk<true><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
                                                D, Dcap, part);
@@ -227,14 +230,15 @@ __global__ void __launch_bounds__(32 * kEstWarps)
 k_estimate(const DevSys *sys, const int *__restrict__ first_chunk, const int *__restrict__ nchunk_sys,
            const int *__restrict__ D_all, const int *__restrict__ cr_all, const int *__restrict__ cnr_all,
            int Dcap, int P, double ke, const double *__restrict__ part, double *__restrict__ rho_all,
-           ModeCoef *__restrict__ coef_all, double *__restrict__ est)
+           ModeCoef *__restrict__ coef_all, double *__restrict__ est, int nsub)
 {
     __shared__ double2 sh[kEstWarps][kEstModes];
     const int s = blockIdx.x, g = blockIdx.y, w = threadIdx.x >> 5, lane = lane_id();
     const DevSys &d = sys[s];
     const int nD = d.nD, k = g * kEstModes + lane;
-    // chunks holding atoms of the system (its slot may have more)
-    const int c0 = first_chunk[s], nc = min(nchunk_sys[s], (live_n(d) + kChunk - 1) / kChunk);
+    // (sub-)chunks holding atoms of the system (its slot may have more), in order
+    const int span = kChunk / nsub;
+    const int c0 = first_chunk[s] * nsub, nc = min(nchunk_sys[s] * nsub, (live_n(d) + span - 1) / span);
     const int cb = (int)((long long)nc * w / kEstWarps), ce = (int)((long long)nc * (w + 1) / kEstWarps);
     double re = 0.0, im = 0.0;
     if (k < nD) {
@@ -303,18 +307,20 @@ k_estimate(const DevSys *sys, const int *__restrict__ first_chunk, const int *__
 
 void launch_estimate(const Batch &b, const int *first_chunk, const int *nchunk_sys, const int *D,
                      const int *cr, const int *cnr, int Dcap, int P, double ke, const double *part,
-                     double *rho, ModeCoef *coef, double *est, cudaStream_t st)
+                     double *rho, ModeCoef *coef, double *est, cudaStream_t st, int precision)
 {
     k_estimate<<<dim3(b.S, estimate_blocks(Dcap)), 32 * kEstWarps, 0, st>>>(
-        b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho, coef, est);
+        b.sys, first_chunk, nchunk_sys, D, cr, cnr, Dcap, P, ke, part, rho, coef, est, sk_sub(precision));
 }
 
 // Long-range force (eq. f_approx): F^lr_i = q_i sum_d alpha_d k_d
 // Im(e^{-i k_d.r_i} rho_d), written per atom to Flr.  It needs the modes'
-// coefficients and the atoms' positions only, so it runs on the sampler's
-// stream beside the pair kernel.  Blocks of kLrAtoms atoms of one chunk
-// (grid: chunks x kChunk / kLrAtoms); the system's mode coefficients are
-// staged in shared memory in tiles.
+// coefficients and the atoms' positions only, so in the FP32 build it runs on
+// the sampler's stream beside the pair kernel.  Blocks of kLrAtoms atoms of
+// one chunk and one group of modes (grid: chunks x kChunk / kLrAtoms x
+// lr_groups; the FP64 build's kLrGroupsD groups each write a partial force
+// Flr + g 3N); the group's mode coefficients are staged in shared memory in
+// tiles.
 constexpr int kModeTile = 256;
 constexpr int kLrAtoms = kChunk / kKinSplit;
 
@@ -322,7 +328,7 @@ template <bool F32>
 __global__ void __launch_bounds__(kLrAtoms)
 k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
              const uint4 *__restrict__ su, const double *__restrict__ r, const double *__restrict__ q,
-             const ModeCoef *__restrict__ coef_all, int Dcap, double *__restrict__ Flr)
+             const ModeCoef *__restrict__ coef_all, int Dcap, double *__restrict__ Flr, int N)
 {
     __shared__ float4 tf[F32 ? kModeTile : 1];      // a (FP32)
     __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
@@ -336,6 +342,12 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
     const ModeCoef *coef = coef_all + (size_t)s * Dcap;
     const int k = blockIdx.y * kLrAtoms + threadIdx.x;
     if ((int)(blockIdx.y * kLrAtoms) >= na) return;   // whole block beyond the chunk
+    // this block's modes: group blockIdx.z of lr_groups (FP32: all of them);
+    // a group without modes writes zeros
+    constexpr int G = F32 ? 1 : kLrGroupsD;
+    const int per = (nD + G - 1) / G;
+    const int mb = min(nD, (int)blockIdx.z * per), me = min(nD, mb + per);
+    Flr += (size_t)blockIdx.z * 3 * N;
     if (F32) fill_turn_table(tab);                    // used after the tile loop's barrier
     else fill_turn_table_d(tabd);
     const bool act = k < na;
@@ -351,8 +363,8 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
         frac_of(d, x, sf);
         sx = sf[0]; sy = sf[1]; sz = sf[2];
     } else { sx = r[3 * i] / d.L[0]; sy = r[3 * i + 1] / d.L[1]; sz = r[3 * i + 2] / d.L[2]; }
-    for (int t0 = 0; t0 < nD; t0 += kModeTile) {
-        const int nt = min(kModeTile, nD - t0);
+    for (int t0 = mb; t0 < me; t0 += kModeTile) {
+        const int nt = min(kModeTile, me - t0);
         __syncthreads();
         for (int u = threadIdx.x; u < nt; u += blockDim.x) {
             const ModeCoef &mc = coef[t0 + u];
@@ -410,16 +422,18 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
 void launch_lr_fourier(const Batch &b, const AtomArrays &a, int precision, const ModeCoef *coef, int Dcap,
                        double *Flr, cudaStream_t st)
 {
-    const dim3 grid(b.nchunks, kChunk / kLrAtoms);
+    const dim3 grid(b.nchunks, kChunk / kLrAtoms, lr_groups(precision));
     if (precision == 1)
-        k_lr_fourier<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr);
+        k_lr_fourier<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr,
+                                                     b.N);
     else
-        k_lr_fourier<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr);
+        k_lr_fourier<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr,
+                                                      b.N);
 }
 
 // Force assembly: F_i = the pair kernel's fixed-point sum (read and cleared)
-// + the long-range force Flr (k_lr_fourier) + the molecule terms of k_mol, in
-// that order.  The same blocks (kLrAtoms atoms of one chunk) then give the
+// + the long-range force Flr (k_lr_fourier, its mode groups in order) + the
+// molecule terms of k_mol, in that order.  The same blocks (kLrAtoms atoms of one chunk) then give the
 // atoms their second half kick (velocity Verlet B step) and sum the kinetic
 // tensor p (x) p / m of their atoms, one partial per block.
 template <bool F32>
@@ -460,9 +474,14 @@ k_force_assembly(const DevSys *__restrict__ sys, const int *__restrict__ chunk_s
                 ffix[(size_t)(3 + a) * N + ks] = 0ull;
             }
         }
-        f[0] += Flr[3 * i];
-        f[1] += Flr[3 * i + 1];
-        f[2] += Flr[3 * i + 2];
+        constexpr int G = F32 ? 1 : kLrGroupsD;     // the long-range force's mode groups, in order
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const double *fl = Flr + (size_t)g * 3 * N;
+            f[0] += fl[3 * i];
+            f[1] += fl[3 * i + 1];
+            f[2] += fl[3 * i + 2];
+        }
         if (Fmol) {
             f[0] += Fmol[3 * i];
             f[1] += Fmol[3 * i + 1];

@@ -358,7 +358,7 @@ __device__ __forceinline__ void tile(const PairConstsF &pc, float xs, float ys, 
 }  // namespace
 
 template <int NF, bool EN>
-__global__ void __launch_bounds__(32 * kCpWarps, 8)
+__global__ void __launch_bounds__(32 * kCpWarps, EN ? 5 : 8)
 k_pair_cluster(const DevSys *__restrict__ sys, const int *__restrict__ item_sys, const int2 *__restrict__ items,
                const int2 *__restrict__ ccl, const float4 *__restrict__ cbox, const float4 *__restrict__ pos4,
                const float2 *__restrict__ qt, const float2 *__restrict__ lj, const float2 *__restrict__ ljlo,

@@ -80,7 +80,7 @@ struct rbsog_ctx {
     DevSys *sys = nullptr;
     double *r = nullptr, *p = nullptr, *F = nullptr, *q = nullptr, *mass = nullptr;
     double *Fmol = nullptr;     // molecule-term forces, added by the force assembly
-    double *Flr = nullptr;      // long-range forces (beside the pair kernel), added by the force assembly
+    double *Flr = nullptr;      // long-range forces [lr_groups x 3N] (FP32: beside the pair kernel), added by the force assembly
     int *type = nullptr, *mol = nullptr, *atom_sys = nullptr, *cell = nullptr, *rank = nullptr;
     float4 *locf = nullptr, *pos4 = nullptr;
     double4 *locd = nullptr, *posd = nullptr;
@@ -305,7 +305,7 @@ void enqueue_kspace(rbsog_ctx *c, cudaStream_t st)
     launch_sk(c->b, c->a, c->prm.precision, c->D, c->Dcap, c->sk_part, st);
     record(c, "structure_factor");
     launch_estimate(c->b, c->first_chunk, c->nchunk_sys, c->D, c->cr, c->cnr, c->Dcap, c->prm.P, c->prm.ke,
-                    c->sk_part, c->rho, c->coef, c->est, st);
+                    c->sk_part, c->rho, c->coef, c->est, st, c->prm.precision);
     record(c, "estimate");
     // FP32 build: the long-range force too.  In the FP64 build it is FP64 work
     // like the pair kernel's, and beside it measured slower than after it
@@ -996,7 +996,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   upload(c, c->b_start, b_start) && upload(c, c->a_start, a_start) && upload(c, c->e_start, e_start) &&
                   upload(c, c->bonds, bonds) && upload(c, c->angles, angles) && upload(c, c->excl, excl) &&
                   upload(c, c->bk, bk) && upload(c, c->br0, br0) && upload(c, c->ak, ak) && upload(c, c->at0, at0) &&
-                  upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->Flr, 3 * (size_t)N) && dalloc(c, c->cell, N) &&
+                  upload(c, c->self_e, self_e) && dalloc(c, c->F, 3 * (size_t)N) && dalloc(c, c->Fmol, 3 * (size_t)N) && dalloc(c, c->Flr, 3 * (size_t)N * lr_groups(P.precision)) && dalloc(c, c->cell, N) &&
                   dalloc(c, c->rank, N) && dalloc(c, c->sidx, N) && dalloc(c, c->count, C) &&
                   dalloc(c, c->start, C + 1) && dalloc(c, c->items, item_cap) &&
                   dalloc(c, c->pair_part, (size_t)item_cap * pair_rec_num(P.precision, P.cell_sub) /
@@ -1009,7 +1009,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                   dalloc(c, c->cnr, (size_t)S * c->Dcap) && dalloc(c, c->pm, (size_t)S * P.P) && dalloc(c, c->samp, (size_t)S) && dalloc(c, c->nrsh, (size_t)S * 9) &&
                   dalloc(c, c->pw, (size_t)S * P.P) && dalloc(c, c->pg, (size_t)S * P.P) &&
                   dalloc(c, c->pu, (size_t)S * P.P) && dalloc(c, c->pun, (size_t)S * P.P) &&
-                  dalloc(c, c->sk_part, (size_t)c->nchunks * c->Dcap * 2) &&
+                  dalloc(c, c->sk_part, (size_t)c->nchunks * sk_sub(P.precision) * c->Dcap * 2) &&
                   dalloc(c, c->rho, (size_t)S * c->Dcap * 2) && dalloc(c, c->coef, (size_t)S * c->Dcap) &&
                   upload(c, c->ljd, ljd) && upload(c, c->ljf, ljf) && upload(c, c->ljf_lo, ljf_lo) &&
                   upload(c, c->inv_m, inv_m) && upload(c, c->sdv, sdv);
