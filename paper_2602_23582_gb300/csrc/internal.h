@@ -126,6 +126,9 @@ struct AtomArrays {
     // ti * ntypes + tj = (4 eps sig^12, 4 eps sig^6); ljf_lo: FP32 remainders
     const float2 *ljf, *ljf_lo;
     const double2 *ljd;
+    // FP64 build: (cos, sin)(2 pi k / 512), k < 512, made once by launch_turn_table_d
+    // and copied into shared memory by the k-space kernels
+    const double2 *turn_tab_d;
 };
 
 // ---- k_bin.cu
@@ -218,6 +221,9 @@ constexpr int kSkSubD = 8;
 constexpr int kLrGroupsD = 8;
 inline int sk_sub(int precision) { return precision == 1 ? 1 : kSkSubD; }
 inline int lr_groups(int precision) { return precision == 1 ? 1 : kLrGroupsD; }
+// the FP64 phase table of the k-space kernels (512 entries), filled once
+void launch_turn_table_d(double2 *tab, cudaStream_t st);
+constexpr int kTurnTabEntries = 512;
 // part: [nchunks x sk_sub(precision) x Dcap x 2]
 void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
                double *part, cudaStream_t st);

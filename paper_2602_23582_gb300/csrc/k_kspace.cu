@@ -80,6 +80,7 @@ __device__ __forceinline__ void phase_sincos_d(const int m[3], double sx, double
 // filled by the threads of a block (sincospi of exact arguments k / 256),
 // which must synchronise before the first use.
 constexpr int kTurnTabD = 512;
+static_assert(kTurnTabD == kTurnTabEntries, "the context allocates kTurnTabEntries table entries");
 __device__ __forceinline__ void fill_turn_table_d(double2 *tab)
 {
     for (int k = threadIdx.x; k < kTurnTabD; k += blockDim.x) {
@@ -87,6 +88,16 @@ __device__ __forceinline__ void fill_turn_table_d(double2 *tab)
         sincospi((double)k * (1.0 / 256.0), &sn, &cs);
         tab[k] = make_double2(cs, sn);
     }
+}
+
+// The FP64 table in shared memory: copied from gtab (the context's copy, made
+// once by k_turn_table_d with the same function) or, without one, filled here.
+__device__ __forceinline__ void load_turn_table_d(double2 *tab, const double2 *__restrict__ gtab)
+{
+    if (gtab)
+        for (int k = threadIdx.x; k < kTurnTabD; k += blockDim.x) tab[k] = gtab[k];
+    else
+        fill_turn_table_d(tab);
 }
 
 // sin and cos of 2 pi (m . s) in FP64 from the table: t = m . s mod 1 as in
@@ -118,14 +129,15 @@ __device__ __forceinline__ void phase_sincos_dt(const int m[3], double sx, doubl
 // (null: orthorhombic); the FP64 phases use s = h^{-1} r.
 template <bool F32>
 __device__ void sk_chunk(const uint4 *su, const double *r, const double *q, const double L[3], const double *tilt,
-                         int a0, int na, const int *D, int d0, int nd_here, double *out /* [nd_here][2] */)
+                         int a0, int na, const int *D, int d0, int nd_here, double *out /* [nd_here][2] */,
+                         const double2 *gtab = nullptr)
 {
     __shared__ uint4 s_su[F32 ? kChunk : 1];
     __shared__ double s_sd[F32 ? 1 : kChunk][4];
     __shared__ float2 s_tab[F32 ? kTurnTab : 1];
     __shared__ double2 s_tabd[F32 ? 1 : kTurnTabD];
     if (F32) fill_turn_table(s_tab);
-    else fill_turn_table_d(s_tabd);
+    else load_turn_table_d(s_tabd, gtab);
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
     for (int k = tid; k < na; k += blockDim.x) {
         if (F32) {
@@ -188,7 +200,8 @@ template <bool F32>
 __global__ void __launch_bounds__(kSkThreads)
 k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
      const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
-     const double *__restrict__ q, const int *__restrict__ D, int Dcap, double *__restrict__ part)
+     const double *__restrict__ q, const int *__restrict__ D, int Dcap, double *__restrict__ part,
+     const double2 *__restrict__ gtab)
 {
     constexpr int nsub = F32 ? 1 : kSkSubD, span = kChunk / nsub;
     const int c = blockIdx.x / nsub, sb = blockIdx.x % nsub, s = chunk_sys[c];
@@ -200,7 +213,7 @@ k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const in
     const int nd_here = min(kModeGroup, d.nD - d0);
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
     sk_chunk<F32>(su, r, q, L, d.tri ? d.tilt : nullptr, chunk_a0[c] + sb * span, na, D + (size_t)s * Dcap * 3, d0,
-                  nd_here, part + ((size_t)blockIdx.x * Dcap + d0) * 2);
+                  nd_here, part + ((size_t)blockIdx.x * Dcap + d0) * 2, gtab);
 }
 
 void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
@@ -209,11 +222,15 @@ void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D,
     dim3 grid(b.nchunks * sk_sub(precision), (Dcap + kModeGroup - 1) / kModeGroup);
     if (precision == 1)
         k_sk<true><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                               D, Dcap, part);
+                                               D, Dcap, part, nullptr);
     else
         k_sk<false><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                D, Dcap, part);
+                                                D, Dcap, part, a.turn_tab_d);
 }
+
+__global__ void k_turn_table_d(double2 *tab) { fill_turn_table_d(tab); }
+
+void launch_turn_table_d(double2 *tab, cudaStream_t st) { k_turn_table_d<<<1, kTurnTabD, 0, st>>>(tab); }
 
 // One block per (system, group of 32 modes).  Warp w sums its share of the
 // chunk partials of rho (fixed chunk ranges, in chunk order), warp 0 adds the
@@ -328,7 +345,8 @@ template <bool F32>
 __global__ void __launch_bounds__(kLrAtoms)
 k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
              const uint4 *__restrict__ su, const double *__restrict__ r, const double *__restrict__ q,
-             const ModeCoef *__restrict__ coef_all, int Dcap, double *__restrict__ Flr, int N)
+             const ModeCoef *__restrict__ coef_all, int Dcap, double *__restrict__ Flr, int N,
+             const double2 *__restrict__ gtab)
 {
     __shared__ float4 tf[F32 ? kModeTile : 1];      // a (FP32)
     __shared__ float2 tr[F32 ? kModeTile : 1];      // re, im
@@ -349,7 +367,7 @@ k_lr_fourier(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, 
     const int mb = min(nD, (int)blockIdx.z * per), me = min(nD, mb + per);
     Flr += (size_t)blockIdx.z * 3 * N;
     if (F32) fill_turn_table(tab);                    // used after the tile loop's barrier
-    else fill_turn_table_d(tabd);
+    else load_turn_table_d(tabd, gtab);
     const bool act = k < na;
     const int i = a0 + (act ? k : 0);
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -425,10 +443,10 @@ void launch_lr_fourier(const Batch &b, const AtomArrays &a, int precision, const
     const dim3 grid(b.nchunks, kChunk / kLrAtoms, lr_groups(precision));
     if (precision == 1)
         k_lr_fourier<true><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr,
-                                                     b.N);
+                                                     b.N, nullptr);
     else
         k_lr_fourier<false><<<grid, kLrAtoms, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, a.su, a.r, a.q, coef, Dcap, Flr,
-                                                      b.N);
+                                                      b.N, a.turn_tab_d);
 }
 
 // Force assembly: F_i = the pair kernel's fixed-point sum (read and cleared)

@@ -103,6 +103,7 @@ struct rbsog_ctx {
     double *pair_red = nullptr; // pair records reduced to kPairRedBlocks per system
     double *inv_m = nullptr, *sdv = nullptr;   // per-atom integrator constants
     double2 *ljd = nullptr;     // LJ blocks per system
+    double2 *turn_tab_d = nullptr;   // FP64 build: the k-space kernels' phase table
     float2 *ljf = nullptr, *ljf_lo = nullptr;
     int *mr = nullptr, *mnr = nullptr, *D = nullptr, *cr = nullptr, *cnr = nullptr;
     int4 *pm = nullptr;
@@ -1020,7 +1021,14 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
                      dalloc(c, c->ffix, 3 * (size_t)N) && dalloc(c, c->ccl, C) && dalloc(c, c->cbox, 2 * (size_t)item_cap);
             else
                 ok = dalloc(c, c->locd, N) && dalloc(c, c->posd, N) && dalloc(c, c->aux, N) &&
-                     dalloc(c, c->posf, N) && dalloc(c, c->ffix, 6 * (size_t)N);
+                     dalloc(c, c->posf, N) && dalloc(c, c->ffix, 6 * (size_t)N) &&
+                     dalloc(c, c->turn_tab_d, (size_t)kTurnTabEntries);
+            if (ok && c->turn_tab_d) {
+                // on the stream of dalloc's memset (the legacy default stream), after it, and
+                // finished before any kernel of the context's streams reads the table
+                launch_turn_table_d(c->turn_tab_d, 0);
+                ok = cudaStreamSynchronize(0) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+            }
             ok = ok && dalloc(c, c->xref, 3 * (size_t)N);
         }
         if (ok && P.precision == 1) {
@@ -1158,7 +1166,7 @@ rbsog_status create_impl(const rbsog_params *params, int n_systems, const rbsog_
         c->a.su = c->su; c->a.xref = c->xref; c->a.count = c->count; c->a.start = c->start; c->a.sidx = c->sidx; c->a.pos4 = c->pos4;
         c->a.qt = c->qt; c->a.posd = c->posd; c->a.aux = c->aux; c->a.items = c->items;
         c->a.posf = c->posf; c->a.ffix = c->ffix; c->a.ccl = c->ccl; c->a.cbox = c->cbox;
-        c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo;
+        c->a.ljd = c->ljd; c->a.ljf = c->ljf; c->a.ljf_lo = c->ljf_lo; c->a.turn_tab_d = c->turn_tab_d;
         c->m.nmol = nmolx; c->m.b_start = c->b_start; c->m.a_start = c->a_start; c->m.e_start = c->e_start;
         c->m.bonds = c->bonds; c->m.bk = c->bk; c->m.br0 = c->br0; c->m.angles = c->angles; c->m.ak = c->ak;
         c->m.at0 = c->at0; c->m.excl = c->excl; c->m.mchunk_sys = c->mchunk_sys; c->m.mchunk_m0 = c->mchunk_m0;
