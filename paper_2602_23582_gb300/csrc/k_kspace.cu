@@ -20,7 +20,8 @@ namespace rbsog {
 namespace {
 
 constexpr int kModeGroup = 16;   // modes per block of the S(k) kernel
-constexpr int kSkThreads = 256;
+constexpr int kSkThreads = 256;  // 8 warps: one or two modes each
+constexpr int kSkSmallGrid = 152;   // this GPU's SM count: an FP64 S(k) grid below it halves its mode groups
 
 struct Kahan {
     float s = 0.f, c = 0.f;
@@ -201,16 +202,16 @@ __global__ void __launch_bounds__(kSkThreads)
 k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const int *__restrict__ chunk_a0,
      const int *__restrict__ chunk_n, const uint4 *__restrict__ su, const double *__restrict__ r,
      const double *__restrict__ q, const int *__restrict__ D, int Dcap, double *__restrict__ part,
-     const double2 *__restrict__ gtab)
+     const double2 *__restrict__ gtab, int mg)
 {
     constexpr int nsub = F32 ? 1 : kSkSubD, span = kChunk / nsub;
     const int c = blockIdx.x / nsub, sb = blockIdx.x % nsub, s = chunk_sys[c];
     const DevSys &d = sys[s];
-    const int d0 = blockIdx.y * kModeGroup;
+    const int d0 = blockIdx.y * mg;
     // atoms of this sub-chunk (<= 0: beyond the system in its slot)
     const int na = min(span, live_n(d) - (chunk_a0[c] - d.atom0) - sb * span);
     if (d0 >= d.nD || na <= 0) return;
-    const int nd_here = min(kModeGroup, d.nD - d0);
+    const int nd_here = min(mg, d.nD - d0);
     const double L[3] = {d.L[0], d.L[1], d.L[2]};
     sk_chunk<F32>(su, r, q, L, d.tri ? d.tilt : nullptr, chunk_a0[c] + sb * span, na, D + (size_t)s * Dcap * 3, d0,
                   nd_here, part + ((size_t)blockIdx.x * Dcap + d0) * 2, gtab);
@@ -219,13 +220,19 @@ k_sk(const DevSys *__restrict__ sys, const int *__restrict__ chunk_sys, const in
 void launch_sk(const Batch &b, const AtomArrays &a, int precision, const int *D, int Dcap,
                double *part, cudaStream_t st)
 {
-    dim3 grid(b.nchunks * sk_sub(precision), (Dcap + kModeGroup - 1) / kModeGroup);
+    // modes per block: kModeGroup, or half of it for an FP64 batch whose grid
+    // would fill fewer blocks than the GPU has SMs (one warp per mode then);
+    // each mode's sum runs over the same atoms in the same order either way
+    const int nx = b.nchunks * sk_sub(precision);
+    const int mg = (precision != 1 && nx * ((Dcap + kModeGroup - 1) / kModeGroup) < kSkSmallGrid) ? kModeGroup / 2
+                                                                                                   : kModeGroup;
+    dim3 grid(nx, (Dcap + mg - 1) / mg);
     if (precision == 1)
         k_sk<true><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                               D, Dcap, part, nullptr);
+                                               D, Dcap, part, nullptr, mg);
     else
         k_sk<false><<<grid, kSkThreads, 0, st>>>(b.sys, b.chunk_sys, b.chunk_a0, b.chunk_n, a.su, a.r, a.q,
-                                                D, Dcap, part, a.turn_tab_d);
+                                                D, Dcap, part, a.turn_tab_d, mg);
 }
 
 __global__ void k_turn_table_d(double2 *tab) { fill_turn_table_d(tab); }
