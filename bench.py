@@ -452,9 +452,9 @@ def pair_roofline(half_pairs, pair_ms, prec, sm_clk, pair_trace=None, traffic=No
     peak = fp32_peak if fp32_bound else mufu_peak
     achieved = half_pairs * per / (pair_ms * 1e-3) / 1e12
     rec.update(kernel="k_pair_cluster", achieved=achieved, peak=peak,
-               limit=("instruction issue: 11 warp instructions per pair inside r_c (78 operations of "
-                      "algorithmic work at 44 % tile fill, plus candidate tests, queue and fixed-point adds), "
-                      "issue slots 68 % busy at 36 % warp occupancy (profiles/pair_kernel_cluster_water.md)"),
+               limit=("instruction issue: 9.0 warp instructions per pair inside r_c (the 4 x 4 tiles at 44 % fill, "
+                      "plus the candidate scan, queue and fixed-point adds), issue slots 64 % busy at 37 % warp "
+                      "occupancy (profiles/pair_kernel_cluster_water.md)"),
                unit="Top/s (FP32 pipe)" if fp32_bound else "Top/s (MUFU)", frac=achieved / peak,
                per_unit=f"{PAIR_MUFU_PER_UNIT} MUFU + {PAIR_FP32_PER_UNIT} FP32 ops per half-pair inside r_c",
                peak_basis=f"{SM_COUNT} SMs x ({FP32_LANES} FP32 lanes, {MUFU_PER_SM_CLK} MUFU)/clk x "
